@@ -1,0 +1,386 @@
+"""Plain FP64 CPU oracle for the MGM method -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import this
+package. It shares no code with the CUDA library (``paper_2204_06154_gb300``); the only common
+module is the seeded input generator ``paper_2204_06154_gb300.inputs``, which holds none of the
+method's arithmetic.
+
+The arithmetic lives in ``mgm_oracle.c`` (built by ``oracle.build.build_oracle``); this module
+binds it with ctypes and strings the steps together in the order of the paper's Algorithm 2
+(preprocessing) and Algorithm 3 (V-cycle), plus right-preconditioned flexible GMRES (Sec. 4.6).
+
+Parity status of every function is pinned by ``tests/test_oracle_*.py``; see the module
+docstrings there for what each pin is.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+i64 = C.c_int64
+
+
+class OracleError(RuntimeError):
+    def __init__(self, what, status, row=-1):
+        super().__init__(f"oracle {what} failed with status {status} (row {row})")
+        self.status = status
+        self.row = row
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = os.path.join(_HERE, "liboracle.so")
+        if not os.path.exists(path):
+            from .build import build_oracle
+            build_oracle()
+        L = C.CDLL(path)
+        L.or_knn.argtypes = [f64p, i64, f64p, i64, C.c_int, C.c_int, i32p, C.c_void_p]
+        L.or_phs_weights.argtypes = [f64p, f64p, i64, i32p, C.c_int, C.c_int, C.c_int, f64p]
+        L.or_gfd_weights.argtypes = [f64p, f64p, i64, i32p, C.c_int, C.c_int, C.c_double, f64p]
+        L.or_assemble.argtypes = [i64, C.c_int, i32p, f64p, C.c_double, C.c_int, i32p, i32p, f64p]
+        L.or_rcm.argtypes = [i64, i32p, i32p, i32p]
+        L.or_color.argtypes = [i64, i32p, i32p, C.c_uint64, i32p, C.POINTER(C.c_int32)]
+        L.or_priority.argtypes = [C.c_uint64, C.c_uint64]
+        L.or_priority.restype = C.c_uint64
+        L.or_wse.argtypes = [f64p, i64, i64, C.c_int, i32p, f64p]
+        L.or_interp.argtypes = [f64p, i64, f64p, i64, C.c_int, i32p, i32p, f64p]
+        L.or_transpose.argtypes = [i64, i64, i32p, i32p, f64p, i32p, i32p, f64p]
+        L.or_spgemm.argtypes = [i64, i64, i32p, i32p, f64p, i32p, i32p, f64p, i32p, C.c_void_p, C.c_void_p]
+        L.or_lu_factor.argtypes = [f64p, i64, i32p]
+        L.or_lu_solve.argtypes = [f64p, i64, i32p, f64p]
+        L.or_tangent_basis.argtypes = [f64p, f64p, f64p]
+        L.or_last_bad_row.restype = C.c_int64
+        L.or_vcycle.argtypes = [C.c_void_p, C.c_int, f64p, i32p, C.c_void_p, C.c_int, C.c_int, f64p, f64p]
+        L.or_fgmres.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_int, C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_int, C.c_double,
+                                C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
+        L.or_mgm_solve.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, f64p, i32p, C.c_void_p,
+                                   C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_double,
+                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        _LIB = L
+    return _LIB
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _check(what, st):
+    if st != 0:
+        raise OracleError(what, st, lib().or_last_bad_row())
+
+
+# ----------------------------------------------------------------------------------------------
+# Step functions (thin wrappers; the arithmetic is in mgm_oracle.c)
+# ----------------------------------------------------------------------------------------------
+def knn(data, query, k, self_first=False, return_d2=False):
+    """k nearest data points of each query point, ascending (d^2, index) (Sec. 2, Sec. 3)."""
+    data = _c(data, np.float64); query = _c(query, np.float64)
+    idx = np.empty((query.shape[0], k), np.int32)
+    d2 = np.empty((query.shape[0], k), np.float64) if return_d2 else None
+    _check("knn", lib().or_knn(data, data.shape[0], query, query.shape[0], k, int(self_first), idx,
+                               d2.ctypes.data if d2 is not None else None))
+    return (idx, d2) if return_d2 else idx
+
+
+def tangent_basis(n):
+    t1 = np.empty(3); t2 = np.empty(3)
+    lib().or_tangent_basis(_c(n, np.float64), t1, t2)
+    return t1, t2
+
+
+def phs_weights(xyz, nrm, idx, k, ell):
+    """Tangent-plane PHS RBF-FD Laplacian weights, one row per stencil (Sec. 2.2)."""
+    xyz = _c(xyz, np.float64); nrm = _c(nrm, np.float64); idx = _c(idx, np.int32)
+    w = np.empty(idx.shape, np.float64)
+    _check("phs_weights", lib().or_phs_weights(xyz, nrm, xyz.shape[0], idx, idx.shape[1], k, ell, w))
+    return w
+
+
+def gfd_weights(xyz, nrm, idx, ell, alpha):
+    """Tangent-plane GFD (weighted least squares) Laplacian weights (Sec. 2.3)."""
+    xyz = _c(xyz, np.float64); nrm = _c(nrm, np.float64); idx = _c(idx, np.int32)
+    w = np.empty(idx.shape, np.float64)
+    _check("gfd_weights", lib().or_gfd_weights(xyz, nrm, xyz.shape[0], idx, idx.shape[1], ell, alpha, w))
+    return w
+
+
+def assemble(idx, w, mu=1.0, poisson=False):
+    """L = I - mu D (or L = D) as scipy CSR with ascending columns (Sec. 2)."""
+    idx = _c(idx, np.int32); w = _c(w, np.float64)
+    N, n = idx.shape
+    rp = np.empty(N + 1, np.int32); ci = np.empty(N * n, np.int32); v = np.empty(N * n, np.float64)
+    _check("assemble", lib().or_assemble(N, n, idx, w, mu, int(poisson), rp, ci, v))
+    return sp.csr_matrix((v, ci, rp), shape=(N, N))
+
+
+def _csr(A):
+    A = sp.csr_matrix(A)
+    return _c(A.indptr, np.int32), _c(A.indices, np.int32), _c(A.data, np.float64)
+
+
+def rcm(A):
+    """Reverse Cuthill-McKee ordering perm[new] = old of the symmetrised pattern (Sec. 4.2)."""
+    rp, ci, _ = _csr(A)
+    N = A.shape[0]
+    perm = np.empty(N, np.int32)
+    _check("rcm", lib().or_rcm(N, rp, ci, perm))
+    return perm
+
+
+def color(A, seed):
+    """Greedy colouring in decreasing SplitMix64 priority (multicolour GS ordering)."""
+    rp, ci, _ = _csr(A)
+    N = A.shape[0]
+    col = np.empty(N, np.int32)
+    nc = C.c_int32(0)
+    _check("color", lib().or_color(N, rp, ci, seed, col, C.byref(nc)))
+    return col, int(nc.value)
+
+
+def priority(seed, i):
+    return int(lib().or_priority(seed, i))
+
+
+def wse(xyz, NH, mode=1):
+    """Weighted sample elimination to NH points (Sec. 4.1); mode 0 sequential, 1 rounds."""
+    xyz = _c(xyz, np.float64)
+    keep = np.empty(NH, np.int32)
+    rmax = np.empty(1)
+    _check("wse", lib().or_wse(xyz, xyz.shape[0], NH, mode, keep, rmax))
+    return keep, float(rmax[0])
+
+
+def interp(xf, xc, m=3):
+    """PHS (phi = r, constant) interpolation I_H^h, N_f x N_c CSR (Sec. 3)."""
+    xf = _c(xf, np.float64); xc = _c(xc, np.float64)
+    Nf, Nc = xf.shape[0], xc.shape[0]
+    rp = np.empty(Nf + 1, np.int32); ci = np.empty(Nf * m, np.int32); v = np.empty(Nf * m, np.float64)
+    _check("interp", lib().or_interp(xf, Nf, xc, Nc, m, rp, ci, v))
+    nnz = int(rp[-1])
+    return sp.csr_matrix((v[:nnz].copy(), ci[:nnz].copy(), rp), shape=(Nf, Nc))
+
+
+def transpose(A):
+    rp, ci, v = _csr(A)
+    nr, nc = A.shape
+    trp = np.empty(nc + 1, np.int32); tci = np.empty(len(ci), np.int32); tv = np.empty(len(ci), np.float64)
+    _check("transpose", lib().or_transpose(nr, nc, rp, ci, v, trp, tci, tv))
+    return sp.csr_matrix((tv, tci, trp), shape=(nc, nr))
+
+
+def spgemm(A, B):
+    """C = A B with per-row accumulation in A's column order (Sec. 4.2, eq. (galerkin))."""
+    ap, ac, av = _csr(A); bp, bc, bv = _csr(B)
+    nA = A.shape[0]; ncB = B.shape[1]
+    cp = np.empty(nA + 1, np.int32)
+    L = lib()
+    _check("spgemm", L.or_spgemm(nA, ncB, ap, ac, av, bp, bc, bv, cp, None, None))
+    nnz = int(cp[-1])
+    cc = np.empty(max(nnz, 1), np.int32); cv = np.empty(max(nnz, 1), np.float64)
+    _check("spgemm", L.or_spgemm(nA, ncB, ap, ac, av, bp, bc, bv, cp, cc.ctypes.data, cv.ctypes.data))
+    return sp.csr_matrix((cv[:nnz], cc[:nnz], cp), shape=(nA, ncB))
+
+
+def galerkin(L, P, R=None):
+    """L_H = R L P with R = P^T (Sec. 4.2, eq. (galerkin)), computed as R (L P)."""
+    if R is None:
+        R = transpose(P)
+    return spgemm(R, spgemm(L, P))
+
+
+def lu_factor(A):
+    a = _c(np.asarray(A.todense() if sp.issparse(A) else A), np.float64).copy()
+    n = a.shape[0]
+    piv = np.empty(n, np.int32)
+    _check("lu_factor", lib().or_lu_factor(a, n, piv))
+    return a, piv
+
+
+def lu_solve(lu, piv, b):
+    x = _c(b, np.float64).copy()
+    lib().or_lu_solve(lu, lu.shape[0], piv, x)
+    return x
+
+
+def permute(A, perm):
+    """B = A[perm][:, perm] (perm[new] = old), columns ascending; values copied exactly."""
+    B = sp.csr_matrix(A)[perm][:, perm]
+    B.sort_indices()
+    return sp.csr_matrix(B)
+
+
+def num_levels(N1, n_min):
+    """p = floor(log(N1/N_min)/log 4) + 1 (Alg. 2 line 4), evaluated exactly in integers as
+    1 + the largest t with N_min * 4**t <= N1 (so N_min <= N_p < 4 N_min)."""
+    if N1 < n_min:
+        return 1
+    t = 0
+    while n_min * 4 ** (t + 1) <= N1:
+        t += 1
+    return t + 1
+
+
+# ----------------------------------------------------------------------------------------------
+# Operator construction (Sec. 2) and hierarchy (Alg. 2)
+# ----------------------------------------------------------------------------------------------
+def build_operator(xyz, nrm, n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, poisson=False):
+    idx = knn(xyz, xyz, n, self_first=True)
+    if method == "rbf":
+        w = phs_weights(xyz, nrm, idx, k, ell)
+    elif method == "gfd":
+        w = gfd_weights(xyz, nrm, idx, ell, alpha)
+    else:
+        raise ValueError(method)
+    return idx, w, assemble(idx, w, mu, poisson)
+
+
+class _Level(C.Structure):
+    _fields_ = [("n", C.c_int64),
+                ("rp", C.c_void_p), ("ci", C.c_void_p), ("v", C.c_void_p),
+                ("cptr", C.c_void_p), ("crows", C.c_void_p), ("ncol", C.c_int32),
+                ("pp", C.c_void_p), ("pc", C.c_void_p), ("pv", C.c_void_p),
+                ("rrp", C.c_void_p), ("rc", C.c_void_p), ("rv", C.c_void_p)]
+
+
+@dataclass
+class Hierarchy:
+    X: list = field(default_factory=list)      # level point clouds, in each level's RCM order
+    L: list = field(default_factory=list)      # level operators (CSR), RCM order
+    P: list = field(default_factory=list)      # P[j]: N_j x N_{j+1} interpolation
+    R: list = field(default_factory=list)      # R[j] = P[j]^T
+    perm: list = field(default_factory=list)   # perm[j][new] = old index within the level's input order
+    keep: list = field(default_factory=list)   # keep[j]: WSE survivors of level j (indices of level j)
+    colors: list = field(default_factory=list)
+    ncolors: list = field(default_factory=list)
+    lu: np.ndarray = None
+    piv: np.ndarray = None
+    smoother: str = "mc"
+    nu1: int = 1
+    nu2: int = 1
+    _keep_alive: list = field(default_factory=list)
+
+    @property
+    def p(self):
+        return len(self.L)
+
+    def _levels(self):
+        arrs = []
+        lv = (_Level * self.p)()
+        for j in range(self.p):
+            A = self.L[j]
+            rp, ci, v = _csr(A)
+            arrs += [rp, ci, v]
+            lv[j].n = A.shape[0]
+            lv[j].rp, lv[j].ci, lv[j].v = rp.ctypes.data, ci.ctypes.data, v.ctypes.data
+            if self.smoother == "mc" and j < self.p - 1:
+                col = self.colors[j]
+                order = np.argsort(col, kind="stable").astype(np.int32)
+                cptr = np.zeros(self.ncolors[j] + 1, np.int32)
+                cptr[1:] = np.cumsum(np.bincount(col, minlength=self.ncolors[j]))
+                arrs += [order, cptr]
+                lv[j].cptr, lv[j].crows, lv[j].ncol = cptr.ctypes.data, order.ctypes.data, self.ncolors[j]
+            else:
+                lv[j].cptr, lv[j].crows, lv[j].ncol = None, None, 0
+            if j < self.p - 1:
+                pp, pc, pv = _csr(self.P[j]); rr, rc, rv = _csr(self.R[j])
+                arrs += [pp, pc, pv, rr, rc, rv]
+                lv[j].pp, lv[j].pc, lv[j].pv = pp.ctypes.data, pc.ctypes.data, pv.ctypes.data
+                lv[j].rrp, lv[j].rc, lv[j].rv = rr.ctypes.data, rc.ctypes.data, rv.ctypes.data
+        self._keep_alive = arrs + [lv]
+        return lv
+
+
+def setup(xyz, L1, n_min, m=3, seed=0, smoother="mc", nu1=1, nu2=1, wse_mode=1):
+    """MGM preprocessing (Alg. 2), in the paper's order:
+    RCM of L_1 and X_1 (lines 2-3); p (line 4); for each level: WSE coarsening to floor(N_1/4^j)
+    points (line 6), interpolation (line 7), restriction = transpose (line 8), Galerkin product
+    (line 9, eq. (galerkin) operand order), RCM of L_{j+1} and the matching reordering of the
+    coarse index of the transfers (lines 10-11); LU of L_p (line 13). Colourings for the
+    multicolour smoother are computed on the final (RCM-ordered) level operators."""
+    H = Hierarchy(smoother=smoother, nu1=nu1, nu2=nu2)
+    N1 = L1.shape[0]
+    perm1 = rcm(L1)
+    H.perm.append(perm1)
+    H.X.append(_c(xyz, np.float64)[perm1])
+    H.L.append(permute(L1, perm1))
+    p = num_levels(N1, n_min)
+    for j in range(1, p):
+        NH = N1 // 4 ** j
+        keep, _ = wse(H.X[j - 1], NH, mode=wse_mode)
+        H.keep.append(keep)
+        Xc = H.X[j - 1][keep]
+        P = interp(H.X[j - 1], Xc, m)
+        R = transpose(P)
+        Lc = galerkin(H.L[j - 1], P, R)
+        perm = rcm(Lc)
+        H.perm.append(perm)
+        H.X.append(Xc[perm])
+        H.L.append(permute(Lc, perm))
+        P = sp.csr_matrix(P[:, perm]); P.sort_indices()
+        H.P.append(P)
+        H.R.append(transpose(P))
+    for j in range(p - 1):
+        c, nc = color(H.L[j], seed)
+        H.colors.append(c); H.ncolors.append(nc)
+    H.lu, H.piv = lu_factor(H.L[-1])
+    return H
+
+
+def vcycle(H, f, u=None):
+    """One V(nu1, nu2) cycle (Alg. 3) for right-hand side f (caller order); u is the initial
+    guess (zero when None). Returns the new u."""
+    f = _c(f, np.float64)
+    u = np.zeros_like(f) if u is None else _c(u, np.float64).copy()
+    if H.p == 1:
+        return lu_solve(H.lu, H.piv, f[H.perm[0]])[np.argsort(H.perm[0])]
+    lv = H._levels()
+    _check("vcycle", lib().or_vcycle(C.addressof(lv), H.p, H.lu, H.piv, H.perm[0].ctypes.data, H.nu1, H.nu2, f, u))
+    return u
+
+
+def fgmres(A, H, f, x0=None, restart=50, maxit=200, tol=1e-10, precond=True, hist=False):
+    """Right-preconditioned FGMRES(restart) with one MGM V-cycle per iteration (Sec. 4.6).
+    Returns (x, iterations, true relative residual[, history])."""
+    rp, ci, v = _csr(A)
+    n = A.shape[0]
+    f = _c(f, np.float64)
+    x = np.zeros(n) if x0 is None else _c(x0, np.float64).copy()
+    it = C.c_int(0); rel = C.c_double(0.0)
+    hbuf = np.zeros(maxit + 1)
+    if H is not None and H.p > 1:
+        lv = H._levels(); lvp = C.addressof(lv); p = H.p
+        lu, piv, perm = H.lu.ctypes.data, H.piv.ctypes.data, H.perm[0].ctypes.data
+    else:
+        lvp, p, lu, piv, perm = None, 0, None, None, None
+        if precond:
+            raise ValueError("FGMRES with a one-level hierarchy: use a direct solve")
+    st = lib().or_fgmres(n, rp, ci, v, lvp, p, lu, piv, perm, H.nu1 if H else 1, H.nu2 if H else 1,
+                         int(precond), f, x, restart, maxit, tol, C.byref(it), C.byref(rel), hbuf.ctypes.data)
+    if st not in (0, 3):
+        _check("fgmres", st)
+    out = (x, it.value, rel.value)
+    return out + (hbuf[: it.value + 1],) if hist else out
+
+
+def mgm_solve(A, H, f, x0=None, maxit=200, tol=1e-10):
+    """MGM as a standalone solver: repeated V-cycles (Sec. 5.1)."""
+    rp, ci, v = _csr(A)
+    n = A.shape[0]
+    x = np.zeros(n) if x0 is None else _c(x0, np.float64).copy()
+    lv = H._levels()
+    it = C.c_int(0); rel = C.c_double(0.0)
+    lib().or_mgm_solve(n, rp, ci, v, C.addressof(lv), H.p, H.lu, H.piv, H.perm[0].ctypes.data, H.nu1, H.nu2,
+                       _c(f, np.float64), x, maxit, tol, C.byref(it), C.byref(rel))
+    return x, it.value, rel.value
