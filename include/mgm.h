@@ -1,0 +1,256 @@
+/*
+ * mgm.h -- C ABI of libmgm, a GB300 (sm_103a) implementation of the meshfree geometric multilevel
+ * (MGM) method of Wright, Jones & Shankar, "MGM: A meshfree geometric multilevel method for systems
+ * arising from elliptic equations on point cloud surfaces".
+ *
+ * The method: a point cloud X_h on a closed surface, the tangent-plane RBF-FD (or GFD)
+ * discretisation D_h of the Laplace-Beltrami operator (Sec. 2), the system L_h u = f with
+ * L_h = I - mu D_h (or D_h) (Sec. 2, eq. (discrete_system)), and a multilevel preconditioner built
+ * from Poisson-disk (weighted sample elimination) coarsening (Sec. 4.1), PHS interpolation and its
+ * transpose (Sec. 3), Galerkin coarse operators (Sec. 4.2), Gauss-Seidel smoothing and a direct
+ * coarsest solve (Sec. 4.3), combined into the V-cycle of Alg. 3 and used as a right preconditioner
+ * for GMRES (Sec. 4.6).
+ *
+ * Conventions for every call below:
+ *  - Array arguments are DEVICE pointers (cudaMalloc'd, or torch CUDA tensors) unless stated; the
+ *    caller owns them. Parameter structs and info structs are host pointers.
+ *  - Points are N x 3 row-major doubles (x, y, z); normals likewise (need not be unit length).
+ *  - Sparse matrices are CSR with int32 row pointers (N+1) and int32 column indices ascending
+ *    within each row; indices are 0-based.
+ *  - Work is issued on `stream` (a cudaStream_t; NULL = the legacy default stream) and is
+ *    stream-ordered; a call returns after its device work is enqueued, except where it has to read
+ *    a device result to continue (noted per call), in which case it synchronises `stream`.
+ *  - Calls never abort: they return a status. On error the outputs are unspecified, and
+ *    mgm_last_error_message() gives a one-line description (thread-local).
+ *  - Temporaries are allocated with cudaMallocAsync on `stream` and freed before return.
+ */
+#ifndef MGM_H
+#define MGM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mgm_stream; /* == cudaStream_t */
+
+typedef enum {
+    MGM_OK = 0,
+    MGM_ERR_INVALID_ARG = 1,      /* a size, pointer or parameter is out of range */
+    MGM_ERR_SINGULAR_STENCIL = 2, /* a local (stencil / interpolation) system is singular: the
+                                     stencil nodes are not unisolvent (Sec. 2.2); see
+                                     mgm_last_error_row() */
+    MGM_ERR_NOT_CONVERGED = 3,    /* the solve stopped at maxit above tol (info is filled) */
+    MGM_ERR_BREAKDOWN = 4,        /* Krylov breakdown or a non-finite value in the iteration */
+    MGM_ERR_TIMEOUT = 5,          /* a device-side bounded wait gave up */
+    MGM_ERR_CUDA = 6,             /* a CUDA runtime call failed */
+    MGM_ERR_OOM = 7,              /* device allocation failed */
+    MGM_ERR_UNSUPPORTED = 8       /* a size exceeds an internal limit (message says which) */
+} mgm_status;
+
+enum { MGM_RBF_FD = 0, MGM_GFD = 1 };              /* discretisation (Sec. 2.2 / 2.3) */
+enum { MGM_F64 = 0, MGM_F32 = 1 };                  /* V-cycle arithmetic / vector dtype */
+enum { MGM_KRYLOV_FGMRES = 0, MGM_KRYLOV_NONE = 1 }; /* outer method (Sec. 4.6 / Sec. 5.1) */
+
+/* Discretisation parameters (Sec. 2; Table 1). */
+typedef struct {
+    int method;    /* MGM_RBF_FD or MGM_GFD */
+    int k;         /* PHS order: phi(r) = r^(2k+1), 1 <= k (RBF-FD only) */
+    int ell;       /* polynomial degree, 0 <= ell, (ell+1)(ell+2)/2 <= n */
+    int n;         /* stencil size (nearest neighbours incl. the centre), n + (ell+1)(ell+2)/2 <= 128 */
+    double alpha;  /* GFD Gaussian weight parameter (Sec. 2.3), > 0 */
+    double mu;     /* L = I - mu D (shifted Poisson); ignored when poisson != 0 */
+    int poisson;   /* nonzero: L = D (the singular surface Poisson operator) */
+} mgm_stencil_params;
+
+/* Multilevel parameters (Sec. 4; Table 1). */
+typedef struct {
+    int64_t n_min;   /* minimum coarsest size N_min (Alg. 2 line 4), >= 1 */
+    int m;           /* interpolation stencil size (Sec. 3), 1 <= m <= 8; the paper uses 3 */
+    int nu1, nu2;    /* pre- and post-smoothing sweeps, 0 <= nu <= 8 */
+    int precision;   /* MGM_F32 (V-cycle in FP32, coarsest solve FP64) or MGM_F64 */
+    uint64_t seed;   /* seed of the multicolour-ordering priorities */
+} mgm_params;
+
+typedef struct {
+    int krylov;      /* MGM_KRYLOV_FGMRES or MGM_KRYLOV_NONE (repeated V-cycles) */
+    int restart;     /* FGMRES restart length, 1..200 */
+    int maxit;       /* maximum iterations (V-cycle applications), >= 0 */
+    double tol;      /* relative residual target |f - L u|_2 / |f|_2 */
+} mgm_solve_params;
+
+typedef struct {
+    int iters;          /* preconditioner applications performed */
+    double rel_res;     /* true relative residual of the returned u (FP64) */
+    double* history;    /* HOST buffer of history_len doubles (or NULL): estimated relative residual
+                           after each iteration, history[0] = initial */
+    int history_len;
+    float solve_ms;     /* device time of the solve (CUDA events) */
+} mgm_solve_info;
+
+typedef struct mgm_hierarchy mgm_hierarchy; /* opaque, library-owned */
+
+typedef struct {
+    int p;                  /* number of levels (Alg. 2 line 4) */
+    int precision;
+    int64_t n[16];          /* N_j, j = 0..p-1 (0 = finest) */
+    int64_t nnz[16];        /* nnz of L_j */
+    int32_t ncolors[16];    /* colours of L_j (0 on the coarsest) */
+    int64_t device_bytes;   /* device memory held by the hierarchy */
+} mgm_hierarchy_stats;
+
+/* ------------------------------------------------------------------------------------------- */
+/* Discretisation (Sec. 2)                                                                       */
+/* ------------------------------------------------------------------------------------------- */
+
+/* k nearest data points of each query point by Euclidean distance in R^3 (Sec. 2: stencils are
+ * "the n_i nearest neighbor nodes"; Sec. 3: the m nearest coarse nodes). Output idx_out (nq x k,
+ * row-major) lists them by ascending (d^2, index), d^2 = (dx*dx + dy*dy) + dz*dz in FP64 without
+ * contraction. self_first != 0 requires query == data and puts query q itself first (the stencil
+ * centre). Requires 1 <= k <= min(nd, 256), nd, nq < 2^31. */
+mgm_status mgm_knn(const double* data, int64_t nd, const double* query, int64_t nq, int k,
+                   int self_first, int32_t* idx_out, mgm_stream stream);
+
+/* Stencil weights c_ij of the LBO for each stencil (Sec. 2.1 tangent plane; Sec. 2.2 PHS RBF-FD,
+ * eq. (rbf_fd_lap); Sec. 2.3 GFD, eq. (wls_fd_lap)). idx (N x n) from mgm_knn(self_first=1);
+ * w_out (N x n) receives the weights in the order of idx. FP64 throughout. A singular local
+ * system returns MGM_ERR_SINGULAR_STENCIL (the lowest failing row via mgm_last_error_row());
+ * synchronises the stream to read that flag. */
+mgm_status mgm_stencil_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx,
+                               const mgm_stencil_params* sp, double* w_out, mgm_stream stream);
+
+/* Global assembly (Sec. 2, eq. (discrete_system)): L = I - mu D (or D) as CSR. rowptr_out
+ * (N+1), col_out and val_out (N*n); each row holds its n stencil columns ascending. */
+mgm_status mgm_assemble(int64_t N, int n, const int32_t* idx, const double* w, double mu, int poisson,
+                        int32_t* rowptr_out, int32_t* col_out, double* val_out, mgm_stream stream);
+
+/* mgm_knn(self_first) + mgm_stencil_weights + mgm_assemble in one call. idx_out and w_out may be
+ * NULL (then temporaries are used). */
+mgm_status mgm_build_stencils(const double* xyz, const double* nrm, int64_t N, const mgm_stencil_params* sp,
+                              int32_t* idx_out, double* w_out, int32_t* rowptr_out, int32_t* col_out,
+                              double* val_out, mgm_stream stream);
+
+/* ------------------------------------------------------------------------------------------- */
+/* Multilevel building blocks (Sec. 3, Sec. 4.1-4.2)                                            */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Poisson-disk coarsening by weighted sample elimination (Sec. 4.1): keep_out (N_coarse, device)
+ * receives the indices of the N_coarse surviving points, ascending. The elimination runs in
+ * rounds: every live point whose weight (and index, on ties) exceeds every live neighbour's is
+ * removed in the same round, the largest first when fewer removals remain (weights: Yuksel's
+ * alpha = 8 kernel with weight limiting, r_max from a hexagonal-packing area estimate). seed is
+ * reserved and must be 0 (the elimination is deterministic). 1 <= N_coarse <= N_fine.
+ * Synchronises the stream once per round. */
+mgm_status mgm_coarsen(const double* xyz, int64_t N_fine, int64_t N_coarse, uint64_t seed,
+                       int32_t* keep_out, mgm_stream stream);
+
+/* PHS interpolation operator I_H^h (Sec. 3, eq. (rbf_fd_interp)): phi(r) = r plus a constant over
+ * the m nearest coarse nodes, solved in R^3. A fine node coinciding with a coarse node gets the
+ * single entry 1. Output CSR N_f x N_c: rowptr_out (N_f+1), col_out/val_out capacity N_f*m;
+ * *nnz_out (host) receives the entry count (synchronises the stream). */
+mgm_status mgm_interp(const double* xf, int64_t Nf, const double* xc, int64_t Nc, int m,
+                      int32_t* rowptr_out, int32_t* col_out, double* val_out, int64_t* nnz_out,
+                      mgm_stream stream);
+
+/* CSR transpose (restriction I_h^H = (I_H^h)^T, Sec. 3; Alg. 2 line 8): rows x cols -> cols x rows,
+ * columns ascending. trowptr (ncols+1), tcol/tval (nnz). */
+mgm_status mgm_transpose(int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* col,
+                         const double* val, int32_t* trowptr, int32_t* tcol, double* tval, mgm_stream stream);
+
+/* Sparse product C = A B in FP64 (Galerkin operator, Sec. 4.2 eq. (galerkin), as T = L P and
+ * L_H = R T); A is nA x nB, B is nB x ncolsB. Two-phase: with c_col == NULL the call fills
+ * c_rowptr (nA+1) and *nnz_out (host) only; then call again with the same c_rowptr and c_col/c_val
+ * of that capacity. Each C entry sums its products in ascending column order of A's row with fused
+ * multiply-adds. A row of C may hold at most 1024 distinct columns (MGM_ERR_UNSUPPORTED beyond).
+ * Synchronises the stream. */
+mgm_status mgm_spgemm(int64_t nA, int64_t nB, int64_t ncolsB, const int32_t* a_rowptr, const int32_t* a_col, const double* a_val,
+                      const int32_t* b_rowptr, const int32_t* b_col, const double* b_val,
+                      int32_t* c_rowptr, int32_t* c_col, double* c_val, int64_t* nnz_out, mgm_stream stream);
+
+/* Reverse Cuthill-McKee ordering (Sec. 4.2; Alg. 2 lines 2, 10) of the symmetrised pattern of a
+ * square CSR matrix: perm_out[new] = old. Start node of each component: minimum degree, lowest
+ * index; neighbours enqueued in increasing (degree, index). Synchronises once per BFS level. */
+mgm_status mgm_rcm(int64_t N, const int32_t* rowptr, const int32_t* col, int32_t* perm_out, mgm_stream stream);
+
+/* Multicolouring of the symmetrised pattern for the multicolour Gauss-Seidel smoother: colour_out
+ * (N) in 0..*ncolors_out-1 with no two adjacent rows sharing a colour. Jones-Plassmann rounds with
+ * SplitMix64(seed) priorities (ties by index); equals greedy first-fit colouring in decreasing
+ * priority. *ncolors_out is a host int. Synchronises the stream. */
+mgm_status mgm_color(int64_t N, const int32_t* rowptr, const int32_t* col, uint64_t seed,
+                     int32_t* color_out, int32_t* ncolors_out, mgm_stream stream);
+
+/* ------------------------------------------------------------------------------------------- */
+/* Hierarchy, V-cycle, solve (Sec. 4.5-4.6; Alg. 2, Alg. 3)                                     */
+/* ------------------------------------------------------------------------------------------- */
+
+/* MGM preprocessing (Alg. 2): RCM of L_1 and X_1, p = floor(log(N/N_min)/log 4) + 1 levels, per
+ * level WSE coarsening to floor(N/4^j) points, interpolation, restriction = transpose, Galerkin
+ * L_{j+1} = R L_j P, RCM of L_{j+1}; then colourings and the coarsest factorisation (an explicit
+ * FP64 inverse). xyz (N x 3) and L (CSR, FP64, caller order) are copied; the caller may free them
+ * afterwards. On success *out owns device memory until mgm_destroy. */
+mgm_status mgm_setup(const double* xyz, int64_t N, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const mgm_params* params, mgm_hierarchy** out, mgm_stream stream);
+
+/* One V(nu1, nu2)-cycle from a zero initial guess (Alg. 3 with u^1 = 0): z = M r, the linear
+ * preconditioner. r and z are N vectors in the caller's point order, dtype MGM_F64 (double) or
+ * MGM_F32 (float); the arithmetic is the hierarchy's precision. */
+mgm_status mgm_vcycle(mgm_hierarchy* H, const void* r, void* z, int dtype, mgm_stream stream);
+
+/* Solve L u = f (Sec. 4.6): right-preconditioned flexible GMRES(restart) in FP64 with one V-cycle
+ * per iteration (or, with MGM_KRYLOV_NONE, repeated V-cycles on u). u holds the initial guess on
+ * entry and the solution on return (caller order). Returns MGM_OK when |f - L u|/|f| <= tol,
+ * MGM_ERR_NOT_CONVERGED when maxit is reached first; info (may be NULL) is filled in both cases.
+ * Synchronises the stream once per iteration (convergence test). */
+mgm_status mgm_solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp,
+                     mgm_solve_info* info, mgm_stream stream);
+
+/* Sizes of the hierarchy (host struct). */
+mgm_status mgm_hierarchy_stats_get(const mgm_hierarchy* H, mgm_hierarchy_stats* out);
+
+/* Export level j of the hierarchy (0 = finest) in the level's RCM order, FP64, into caller device
+ * buffers (any may be NULL): perm (N_j: RCM permutation relative to the level's input order: the
+ * caller's order on level 0, the WSE survivor order otherwise), keep (N_j: indices into level j-1's
+ * RCM order of the points kept by coarsening; j >= 1), xyz (N_j x 3), L (rowptr N_j+1, col/val
+ * nnz_j), P (interpolation to level j+1: rowptr N_j+1, col/val; j < p-1), colour (N_j; j < p-1).
+ * Sizes from mgm_hierarchy_stats_get and mgm_hierarchy_pnnz. */
+mgm_status mgm_hierarchy_level(const mgm_hierarchy* H, int j, int32_t* perm, int32_t* keep, double* xyz,
+                               int32_t* l_rowptr, int32_t* l_col, double* l_val,
+                               int32_t* p_rowptr, int32_t* p_col, double* p_val, int32_t* colour,
+                               mgm_stream stream);
+mgm_status mgm_hierarchy_pnnz(const mgm_hierarchy* H, int j, int64_t* nnz_out);
+
+/* Measurement (not part of the method): device time of the pieces of one solve iteration on this
+ * hierarchy, each averaged over `reps` back-to-back runs after two warm-up runs (CUDA events on
+ * `stream`), with their algorithmic bytes (each stored matrix / transfer entry and each per-row
+ * array read or written once per pass; gathered vector entries, which the RCM ordering keeps in
+ * L2, not counted). Overwrites the hierarchy's work vectors. Synchronises the stream. */
+typedef struct {
+    float vcycle_ms;         /* one V-cycle (the captured graph) */
+    int64_t vcycle_bytes;
+    int64_t vcycle_kernels;  /* kernels per V-cycle */
+    float sweep_ms;          /* one full Gauss-Seidel sweep of the finest level (all colours) */
+    int64_t sweep_bytes;
+    int32_t sweep_launches;  /* kernels per sweep (colours of the finest level) */
+    float spmv_ms;           /* the outer FP64 product w = L z on the finest level */
+    int64_t spmv_bytes;
+} mgm_profile_info;
+mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_stream stream);
+
+/* Number of kernels this library has launched in the process (a host-side count: each launch of
+ * the captured V-cycle graph adds its kernel nodes). */
+int64_t mgm_kernel_launches(void);
+
+void mgm_destroy(mgm_hierarchy* H);
+
+/* ------------------------------------------------------------------------------------------- */
+/* Errors                                                                                       */
+/* ------------------------------------------------------------------------------------------- */
+const char* mgm_status_string(mgm_status s);
+const char* mgm_last_error_message(void);
+int64_t mgm_last_error_row(void); /* lowest failing stencil / interpolation row of the last call */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGM_H */

@@ -1,0 +1,223 @@
+// extern "C" entry points of libmgm (declared in include/mgm.h): argument checks, translation of
+// internal failures into status codes, and nothing else.
+#include "hier.cuh"
+
+namespace mgm {
+void knn_device(const double* data, int64_t nd, const double* query, int64_t nq, int k, int self_first, int32_t* idx_out,
+                double* d2_out, cudaStream_t s);
+void stencil_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, const mgm_stencil_params* sp,
+                     double* w, cudaStream_t s);
+void assemble(int64_t N, int n, const int32_t* idx, const double* w, double mu, int poisson, int32_t* rp, int32_t* col,
+              double* val, cudaStream_t s);
+void build_stencils(const double* xyz, const double* nrm, int64_t N, const mgm_stencil_params* sp, int32_t* idx_out,
+                    double* w_out, int32_t* rp, int32_t* col, double* val, cudaStream_t s);
+void coarsen(const double* x, int64_t N, int64_t NH, int32_t* keep, cudaStream_t s, double* rmax_out);
+int64_t interp(const double* xf, int64_t nf, const double* xc, int64_t nc, int m, int32_t* rp, int32_t* col, double* val,
+               cudaStream_t s);
+int64_t spgemm_symbolic(int64_t nA, const int32_t* arp, const int32_t* aci, const int32_t* brp, const int32_t* bci,
+                        int32_t* crp, cudaStream_t s);
+void spgemm_numeric(int64_t nA, const int32_t* arp, const int32_t* aci, const double* av, const int32_t* brp,
+                    const int32_t* bci, const double* bv, const int32_t* crp, int32_t* cci, double* cv, cudaStream_t s);
+void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStream_t s);
+void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32_t* colour, int32_t* ncolors,
+           cudaStream_t s);
+mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int32_t* ci, const double* v,
+                     const mgm_params* prm, cudaStream_t s);
+void vcycle_api(mgm_hierarchy* H, const void* r, void* z, int dtype, cudaStream_t s);
+void hierarchy_level(const mgm_hierarchy* H, int j, int32_t* perm, int32_t* keep, double* xyz, int32_t* lrp, int32_t* lci,
+                     double* lv, int32_t* prp, int32_t* pci, double* pv, int32_t* colour, cudaStream_t s);
+}  // namespace mgm
+
+using namespace mgm;
+
+static inline cudaStream_t S(mgm_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+mgm_status mgm_knn(const double* data, int64_t nd, const double* query, int64_t nq, int k, int self_first,
+                   int32_t* idx_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(data && query && idx_out, "null array");
+        REQUIRE(nd >= 1 && nq >= 0, "sizes out of range");
+        knn_device(data, nd, query, nq, k, self_first, idx_out, nullptr, S(stream));
+    });
+}
+
+mgm_status mgm_stencil_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx,
+                               const mgm_stencil_params* sp, double* w_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(sp && idx, "null argument");
+        REQUIRE(N >= 1 && sp->n >= 1, "sizes out of range");
+        validate_index(idx, N * (int64_t)sp->n, N, "stencil indices", S(stream));
+        stencil_weights(xyz, nrm, N, idx, sp, w_out, S(stream));
+    });
+}
+
+mgm_status mgm_assemble(int64_t N, int n, const int32_t* idx, const double* w, double mu, int poisson,
+                        int32_t* rowptr_out, int32_t* col_out, double* val_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(idx && N >= 1 && n >= 1, "bad argument");
+        validate_index(idx, N * (int64_t)n, N, "stencil indices", S(stream));
+        assemble(N, n, idx, w, mu, poisson, rowptr_out, col_out, val_out, S(stream));
+    });
+}
+
+mgm_status mgm_build_stencils(const double* xyz, const double* nrm, int64_t N, const mgm_stencil_params* sp,
+                              int32_t* idx_out, double* w_out, int32_t* rowptr_out, int32_t* col_out, double* val_out,
+                              mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(xyz && nrm && rowptr_out && col_out && val_out, "null array");
+        build_stencils(xyz, nrm, N, sp, idx_out, w_out, rowptr_out, col_out, val_out, S(stream));
+    });
+}
+
+mgm_status mgm_coarsen(const double* xyz, int64_t N_fine, int64_t N_coarse, uint64_t seed, int32_t* keep_out,
+                       mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(seed == 0, "seed is reserved and must be 0");
+        coarsen(xyz, N_fine, N_coarse, keep_out, S(stream), nullptr);
+    });
+}
+
+mgm_status mgm_interp(const double* xf, int64_t Nf, const double* xc, int64_t Nc, int m, int32_t* rowptr_out,
+                      int32_t* col_out, double* val_out, int64_t* nnz_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(Nc >= 1, "N_c must be >= 1");
+        int64_t nnz = interp(xf, Nf, xc, Nc, m, rowptr_out, col_out, val_out, S(stream));
+        if (nnz_out) *nnz_out = nnz;
+    });
+}
+
+mgm_status mgm_transpose(int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* col, const double* val,
+                         int32_t* trowptr, int32_t* tcol, double* tval, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(rowptr && col && trowptr && tcol, "null array");
+        REQUIRE(nrows >= 0 && ncols >= 0 && nrows < 0x7fffffff && ncols < 0x7fffffff, "sizes out of range");
+        validate_csr(nrows, ncols, rowptr, col, "transpose input", S(stream));
+        csr_transpose(nrows, ncols, rowptr, col, val, trowptr, tcol, tval, S(stream));
+    });
+}
+
+mgm_status mgm_spgemm(int64_t nA, int64_t nB, int64_t ncolsB, const int32_t* a_rowptr, const int32_t* a_col, const double* a_val,
+                      const int32_t* b_rowptr, const int32_t* b_col, const double* b_val, int32_t* c_rowptr,
+                      int32_t* c_col, double* c_val, int64_t* nnz_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(a_rowptr && a_col && b_rowptr && b_col && c_rowptr, "null array");
+        REQUIRE(nA >= 0 && nA < 0x7fffffff && nB >= 0 && nB < 0x7fffffff && ncolsB >= 0 && ncolsB < 0x7fffffff,
+                "sizes out of range");
+        validate_csr(nA, nB, a_rowptr, a_col, "spgemm A", S(stream));
+        validate_csr(nB, ncolsB, b_rowptr, b_col, "spgemm B", S(stream));
+        if (!c_col) {
+            int64_t nnz = spgemm_symbolic(nA, a_rowptr, a_col, b_rowptr, b_col, c_rowptr, S(stream));
+            if (nnz_out) *nnz_out = nnz;
+        } else {
+            REQUIRE(a_val && b_val && c_val, "null value array");
+            spgemm_numeric(nA, a_rowptr, a_col, a_val, b_rowptr, b_col, b_val, c_rowptr, c_col, c_val, S(stream));
+            if (nnz_out) *nnz_out = csr_nnz(c_rowptr, nA, S(stream));
+        }
+    });
+}
+
+mgm_status mgm_rcm(int64_t N, const int32_t* rowptr, const int32_t* col, int32_t* perm_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(rowptr && col && N >= 1, "bad argument");
+        validate_csr(N, N, rowptr, col, "rcm input", S(stream));
+        rcm(N, rowptr, col, perm_out, S(stream));
+    });
+}
+
+mgm_status mgm_color(int64_t N, const int32_t* rowptr, const int32_t* col, uint64_t seed, int32_t* color_out,
+                     int32_t* ncolors_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(ncolors_out && rowptr && col && N >= 1, "bad argument");
+        validate_csr(N, N, rowptr, col, "colouring input", S(stream));
+        color(N, rowptr, col, seed, color_out, ncolors_out, S(stream));
+    });
+}
+
+mgm_status mgm_setup(const double* xyz, int64_t N, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const mgm_params* params, mgm_hierarchy** out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(out, "null output handle");
+        *out = nullptr;
+        REQUIRE(rowptr && col && N >= 1, "bad argument");
+        validate_csr(N, N, rowptr, col, "operator", S(stream));
+        *out = setup(xyz, N, rowptr, col, val, params, S(stream));
+    });
+}
+
+mgm_status mgm_vcycle(mgm_hierarchy* H, const void* r, void* z, int dtype, mgm_stream stream) {
+    return guarded([&] { vcycle_api(H, r, z, dtype, S(stream)); });
+}
+
+mgm_status mgm_solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp, mgm_solve_info* info,
+                     mgm_stream stream) {
+    return guarded([&] { solve(H, f, u, sp, info, S(stream)); });
+}
+
+mgm_status mgm_hierarchy_stats_get(const mgm_hierarchy* H, mgm_hierarchy_stats* out) {
+    return guarded([&] {
+        REQUIRE(H && out, "null argument");
+        *out = mgm_hierarchy_stats{};
+        out->p = H->p;
+        out->precision = H->precision;
+        for (int j = 0; j < H->p && j < 16; ++j) {
+            out->n[j] = H->lv[j].n;
+            out->nnz[j] = H->lv[j].nnz;
+            out->ncolors[j] = H->lv[j].ncolors;
+        }
+        out->device_bytes = H->device_bytes;
+    });
+}
+
+mgm_status mgm_hierarchy_level(const mgm_hierarchy* H, int j, int32_t* perm, int32_t* keep, double* xyz,
+                               int32_t* l_rowptr, int32_t* l_col, double* l_val, int32_t* p_rowptr, int32_t* p_col,
+                               double* p_val, int32_t* colour, mgm_stream stream) {
+    return guarded([&] {
+        hierarchy_level(H, j, perm, keep, xyz, l_rowptr, l_col, l_val, p_rowptr, p_col, p_val, colour, S(stream));
+    });
+}
+
+mgm_status mgm_hierarchy_pnnz(const mgm_hierarchy* H, int j, int64_t* nnz_out) {
+    return guarded([&] {
+        REQUIRE(H && nnz_out && j >= 0 && j < H->p, "bad argument");
+        *nnz_out = H->lv[j].pnnz;
+    });
+}
+
+mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(H && out && reps >= 1, "bad argument");
+        *out = mgm_profile_info{};
+        profile_vcycle(H, reps, out, S(stream));
+        profile_spmv(H, reps, out, S(stream));
+    });
+}
+
+int64_t mgm_kernel_launches(void) { return launches(); }
+
+void mgm_destroy(mgm_hierarchy* H) {
+    if (!H) return;
+    cudaDeviceSynchronize();
+    delete H;
+}
+
+const char* mgm_status_string(mgm_status s) {
+    switch (s) {
+        case MGM_OK: return "MGM_OK";
+        case MGM_ERR_INVALID_ARG: return "MGM_ERR_INVALID_ARG";
+        case MGM_ERR_SINGULAR_STENCIL: return "MGM_ERR_SINGULAR_STENCIL";
+        case MGM_ERR_NOT_CONVERGED: return "MGM_ERR_NOT_CONVERGED";
+        case MGM_ERR_BREAKDOWN: return "MGM_ERR_BREAKDOWN";
+        case MGM_ERR_TIMEOUT: return "MGM_ERR_TIMEOUT";
+        case MGM_ERR_CUDA: return "MGM_ERR_CUDA";
+        case MGM_ERR_OOM: return "MGM_ERR_OOM";
+        case MGM_ERR_UNSUPPORTED: return "MGM_ERR_UNSUPPORTED";
+    }
+    return "unknown status";
+}
+
+const char* mgm_last_error_message(void) { return error_message(); }
+int64_t mgm_last_error_row(void) { return bad_row(); }
+
+}  // extern "C"

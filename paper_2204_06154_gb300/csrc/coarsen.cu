@@ -1,0 +1,208 @@
+// Poisson-disk coarsening by weighted sample elimination (paper Sec. 4.1; the elimination weights
+// follow the cited WSE method of Yuksel: w_ij = (1 - max(d_ij, r_min)/(2 r_max))^8 for neighbours
+// closer than 2 r_max).
+//
+// GPU formulation (rounds): the sequential method removes the point of largest weight one at a
+// time. A point whose (weight, index) exceeds that of every live neighbour is removed before any
+// of its neighbours by that rule (neighbour weights only fall), so all such local maxima can go in
+// one round. Each round: count live points with positive weight, mark candidates, and if more
+// candidates than remaining removals exist keep only the largest by (weight, index) (a 96-bit
+// MSB-first threshold search in one block). Survivors adjacent to a removed point recompute their
+// weight from scratch in ascending neighbour order, so every weight is the same IEEE sum as a
+// sequential recomputation and the kept set is bit-reproducible. Built with --fmad=false.
+#include "common.cuh"
+
+namespace mgm {
+
+void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, Temp<int32_t>& rowptr,
+                  Temp<int32_t>& nbr, Temp<double>& f, cudaStream_t s);
+
+__global__ void nn_fixed_sum_k(const double* x, const int32_t* idx2, int64_t n, unsigned long long* S) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    long long v = 0;
+    if (i < n) {
+        int64_t j = idx2[2 * i + 1];
+        double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1], dz = x[3 * i + 2] - x[3 * j + 2];
+        double d = sqrt((dx * dx + dy * dy) + dz * dz);
+        v = __double2ll_rn(d * 4294967296.0);
+    }
+    v = warp_sum<long long>(v);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(S, (unsigned long long)v);
+}
+
+// r_max from the hexagonal-packing area estimate, r_min from weight limiting (beta 0.65, gamma 1.5)
+__global__ void wse_params_k(const unsigned long long* S, int64_t N, int64_t NH, double* prm) {
+    double dbar = ((double)(long long)*S / 4294967296.0) / (double)N;
+    double area = (double)N * ((sqrt(3.0) * 0.5) * (dbar * dbar));
+    double rmax = sqrt(area / ((2.0 * sqrt(3.0)) * (double)NH));
+    double ratio = (double)NH / (double)N;
+    double rmin = (rmax * (1.0 - ratio * sqrt(ratio))) * 0.65;
+    prm[0] = 2.0 * rmax;
+    prm[1] = rmin;
+    prm[2] = rmax;
+}
+
+// w_i = sum over live neighbours in ascending order; with `only_dirty`, only rows flagged dirty
+__global__ void weights_k(const int32_t* rp, const int32_t* nbr, const double* f, const char* live, char* dirty,
+                          int64_t n, int only_dirty, double* w) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !live[i]) return;
+    if (only_dirty) {
+        if (!dirty[i]) return;
+        dirty[i] = 0;
+    }
+    double acc = 0.0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
+        if (live[nbr[p]]) acc = acc + f[p];
+    w[i] = acc;
+}
+
+__global__ void count_pos_k(const char* live, const double* w, int64_t n, int* npos) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = (i < n && live[i] && w[i] > 0.0) ? 1 : 0;
+    c = warp_sum_i(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(npos, c);
+}
+
+__device__ __forceinline__ bool wgt_gt(double wa, int64_t a, double wb, int64_t b) { return wa > wb || (wa == wb && a > b); }
+
+__global__ void candidates_k(const int32_t* rp, const int32_t* nbr, const char* live, const double* w, int64_t n,
+                             const int* npos, int32_t* cand, int* ncand) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !live[i]) return;
+    if (*npos > 0) {
+        double wi = w[i];
+        if (!(wi > 0.0)) return;
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+            int32_t j = nbr[p];
+            if (live[j] && !wgt_gt(wi, i, w[j], j)) return;
+        }
+    }
+    int q = atomicAdd(ncand, 1);
+    cand[q] = (int32_t)i;
+}
+
+// Keep the `need` largest candidates by (weight, index): MSB-first search of the 96-bit key
+// (weight bits, index) for the need-th largest, then mark key >= threshold. One block.
+__global__ void __launch_bounds__(1024) select_top_k(const int32_t* cand, int nc, const double* w, int need, char* sel) {
+    __shared__ int red[32];
+    unsigned long long thi = 0;
+    unsigned tlo = 0;
+    for (int b = 95; b >= 0; --b) {
+        unsigned long long hi = thi;
+        unsigned lo = tlo;
+        if (b >= 32) hi |= 1ull << (b - 32);
+        else lo |= 1u << b;
+        int c = 0;
+        for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+            int32_t i = cand[t];
+            unsigned long long kh = (unsigned long long)__double_as_longlong(w[i]);
+            unsigned kl = (unsigned)i;
+            c += (kh > hi || (kh == hi && kl >= lo)) ? 1 : 0;
+        }
+        c = warp_sum_i(c);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+            v = warp_sum_i(v);
+            if (threadIdx.x == 0) red[0] = v;
+        }
+        __syncthreads();
+        int total = red[0];
+        __syncthreads();
+        if (total >= need) { thi = hi; tlo = lo; }
+    }
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+        int32_t i = cand[t];
+        unsigned long long kh = (unsigned long long)__double_as_longlong(w[i]);
+        unsigned kl = (unsigned)i;
+        sel[t] = (kh > thi || (kh == thi && kl >= tlo)) ? 1 : 0;
+    }
+}
+
+__global__ void remove_k(const int32_t* cand, const char* sel, int nc, const int32_t* rp, const int32_t* nbr, char* live,
+                         char* dirty) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nc || (sel && !sel[t])) return;
+    int32_t v = cand[t];
+    live[v] = 0;
+    for (int32_t p = rp[v]; p < rp[v + 1]; ++p) dirty[nbr[p]] = 1;
+}
+
+__global__ void live_flags_k(const char* live, int64_t n, int32_t* fl) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) fl[i] = live[i] ? 1 : 0;
+}
+__global__ void compact_live_k(const char* live, const int32_t* pos, int64_t n, int32_t* keep) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && live[i]) keep[pos[i]] = (int32_t)i;
+}
+
+void coarsen(const double* x, int64_t N, int64_t NH, int32_t* keep, cudaStream_t s, double* rmax_out) {
+    REQUIRE(x && keep, "null array");
+    REQUIRE(N >= 2 && N < 0x7fffffff, "N_fine must be in [2, 2^31)");
+    REQUIRE(NH >= 1 && NH <= N, "N_coarse must be in [1, N_fine]");
+    // mean nearest-neighbour distance, summed exactly in 2^-32 fixed point
+    Temp<int32_t> idx2(2 * N, s);
+    knn_device(x, N, x, N, 2, 1, idx2.get(), nullptr, s);
+    Temp<unsigned long long> S(1, s);
+    CK(cudaMemsetAsync(S.get(), 0, sizeof(unsigned long long), s));
+    nn_fixed_sum_k<<<grid_for(N, 256), 256, 0, s>>>(x, idx2.get(), N, S.get());
+    CK_LAUNCH();
+    Temp<double> prm(3, s);
+    wse_params_k<<<1, 1, 0, s>>>(S.get(), N, NH, prm.get());
+    CK_LAUNCH();
+    double hp[3];
+    to_host(hp, prm.get(), 3, s);
+    if (rmax_out) *rmax_out = hp[2];
+    if (NH == N) {
+        iota_i32(keep, N, s);
+        return;
+    }
+    Temp<int32_t> rp, nbr;
+    Temp<double> f;
+    radius_graph(x, N, prm.get(), hp[0], rp, nbr, f, s);
+    Temp<char> live(N, s), dirty(N, s), sel(N, s);
+    Temp<double> w(N, s);
+    Temp<int32_t> cand(N, s);
+    Temp<int> ctr(2, s);  // [0] npos, [1] ncand
+    CK(cudaMemsetAsync(live.get(), 1, N, s));
+    CK(cudaMemsetAsync(dirty.get(), 0, N, s));
+    weights_k<<<grid_for(N, 256), 256, 0, s>>>(rp.get(), nbr.get(), f.get(), live.get(), dirty.get(), N, 0, w.get());
+    CK_LAUNCH();
+    int64_t nlive = N;
+    for (int64_t round = 0; nlive > NH; ++round) {
+        if (round > N) fail(MGM_ERR_UNSUPPORTED, "elimination did not terminate");
+        CK(cudaMemsetAsync(ctr.get(), 0, 2 * sizeof(int), s));
+        count_pos_k<<<grid_for(N, 256), 256, 0, s>>>(live.get(), w.get(), N, ctr.get());
+        CK_LAUNCH();
+        candidates_k<<<grid_for(N, 256), 256, 0, s>>>(rp.get(), nbr.get(), live.get(), w.get(), N, ctr.get(), cand.get(),
+                                                      ctr.get() + 1);
+        CK_LAUNCH();
+        int nc = read1(ctr.get() + 1, s);
+        if (nc <= 0) fail(MGM_ERR_UNSUPPORTED, "elimination round without candidates");
+        int64_t need = nlive - NH;
+        const char* selp = nullptr;
+        int64_t removed = nc;
+        if (nc > need) {
+            select_top_k<<<1, 1024, 0, s>>>(cand.get(), nc, w.get(), (int)need, sel.get());
+            CK_LAUNCH();
+            selp = sel.get();
+            removed = need;
+        }
+        remove_k<<<grid_for(nc, 256), 256, 0, s>>>(cand.get(), selp, nc, rp.get(), nbr.get(), live.get(), dirty.get());
+        CK_LAUNCH();
+        weights_k<<<grid_for(N, 256), 256, 0, s>>>(rp.get(), nbr.get(), f.get(), live.get(), dirty.get(), N, 1, w.get());
+        CK_LAUNCH();
+        nlive -= removed;
+    }
+    Temp<int32_t> fl(N, s), pos(N + 1, s);
+    live_flags_k<<<grid_for(N, 256), 256, 0, s>>>(live.get(), N, fl.get());
+    CK_LAUNCH();
+    exclusive_scan_i32(fl.get(), pos.get(), N, s);
+    compact_live_k<<<grid_for(N, 256), 256, 0, s>>>(live.get(), pos.get(), N, keep);
+    CK_LAUNCH();
+}
+
+}  // namespace mgm

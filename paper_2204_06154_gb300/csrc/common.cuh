@@ -1,0 +1,204 @@
+// Internal helpers of libmgm: error state, stream-ordered device buffers, warp reductions,
+// device-wide scans. Not part of the public ABI (see include/mgm.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mgm.h"
+
+namespace mgm {
+
+// ---------------------------------------------------------------------------------------------
+// error state (thread-local, read through mgm_last_error_message / mgm_last_error_row)
+// ---------------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+void set_bad_row(int64_t row);
+const char* error_message();
+int64_t bad_row();
+
+struct Fail {
+    mgm_status st;
+};
+
+[[noreturn]] void fail(mgm_status st, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define CK(call) ::mgm::check_cuda((call), #call, __FILE__, __LINE__)
+// every kernel launch site is followed by exactly one CK_LAUNCH, which also counts the launch
+void note_launch(int64_t n = 1);
+int64_t launches();
+#define CK_LAUNCH() (::mgm::note_launch(), ::mgm::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
+#define REQUIRE(cond, msg)                                              \
+    do {                                                                \
+        if (!(cond)) ::mgm::fail(MGM_ERR_INVALID_ARG, std::string(msg)); \
+    } while (0)
+
+// run body, translating Fail into a status (C-ABI boundary)
+template <class F>
+mgm_status guarded(F&& body) {
+    try {
+        body();
+        return MGM_OK;
+    } catch (const Fail& f) {
+        return f.st;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return MGM_ERR_OOM;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------------------------
+// Temp<T>: stream-ordered (cudaMallocAsync/cudaFreeAsync) scratch owned by one call.
+template <class T>
+struct Temp {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    Temp() = default;
+    Temp(size_t count, cudaStream_t st) { alloc(count, st); }
+    void alloc(size_t count, cudaStream_t st) {
+        release();
+        s = st;
+        n = count;
+        if (count) {
+            cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), st);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                p = nullptr;
+                fail(MGM_ERR_OOM, "cudaMallocAsync of " + std::to_string(count * sizeof(T)) + " bytes failed");
+            }
+        }
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    ~Temp() { release(); }
+    Temp(const Temp&) = delete;
+    Temp& operator=(const Temp&) = delete;
+    Temp(Temp&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    Temp& operator=(Temp&& o) noexcept {
+        release();
+        p = o.p; n = o.n; s = o.s;
+        o.p = nullptr; o.n = 0;
+        return *this;
+    }
+    T* get() const { return p; }
+};
+
+// Buf<T>: persistent device memory (cudaMalloc) owned by a hierarchy.
+template <class T>
+struct Buf {
+    T* p = nullptr;
+    size_t n = 0;
+    Buf() = default;
+    explicit Buf(size_t count) { alloc(count); }
+    void alloc(size_t count) {
+        release();
+        n = count;
+        if (count) {
+            cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                p = nullptr;
+                fail(MGM_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+            }
+        }
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~Buf() { release(); }
+    Buf(const Buf&) = delete;
+    Buf& operator=(const Buf&) = delete;
+    Buf(Buf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    Buf& operator=(Buf&& o) noexcept {
+        release();
+        p = o.p; n = o.n;
+        o.p = nullptr; o.n = 0;
+        return *this;
+    }
+    T* get() const { return p; }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+inline unsigned grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 0x7fffffff) g = 0x7fffffff;
+    return (unsigned)g;
+}
+
+template <class T>
+inline void to_host(T* dst, const T* src, size_t count, cudaStream_t s) {
+    if (!count) return;
+    CK(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+}
+template <class T>
+inline T read1(const T* src, cudaStream_t s) {
+    T v;
+    to_host(&v, src, 1, s);
+    return v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// device-wide primitives (util.cu)
+// ---------------------------------------------------------------------------------------------
+// exclusive scan of n int32 counts into out (n+1 entries, out[n] = total as int64 is returned
+// through total_dev if non-null). in and out may alias. Totals must fit int32 (checked).
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+// same for int64
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// fill
+void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s);
+void iota_i32(int32_t* p, int64_t n, cudaStream_t s);
+// inverse permutation: inv[perm[i]] = i
+void invert_perm(const int32_t* perm, int32_t* inv, int64_t n, cudaStream_t s);
+// gather rows of an N x 3 double array: out[i] = in[idx[i]]
+void gather_xyz(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s);
+// CSR transpose with columns ascending (deterministic)
+void csr_transpose(int64_t nrows, int64_t ncols, const int32_t* rp, const int32_t* ci, const double* v,
+                   int32_t* trp, int32_t* tci, double* tv, cudaStream_t s);
+// B = A[perm][:, perm] (perm[new] = old), rows sorted by column; brp must have N+1 entries,
+// bci/bv nnz entries.
+void csr_permute(int64_t N, const int32_t* rp, const int32_t* ci, const double* v, const int32_t* perm,
+                 int32_t* brp, int32_t* bci, double* bv, cudaStream_t s);
+// symmetrised pattern of A (A + A^T without the diagonal), rows ascending. Returns arrays via Temp.
+void sym_pattern(int64_t N, const int32_t* rp, const int32_t* ci, Temp<int32_t>& srp, Temp<int32_t>& sci,
+                 cudaStream_t s);
+// nnz of a CSR from its last row pointer (synchronises)
+int64_t csr_nnz(const int32_t* rp, int64_t nrows, cudaStream_t s);
+// argument validation (synchronise): all a[i] in [0, hi); CSR row pointers monotone from 0
+void validate_index(const int32_t* a, int64_t cnt, int64_t hi, const char* what, cudaStream_t s);
+void validate_csr(int64_t nrows, int64_t ncols, const int32_t* rp, const int32_t* ci, const char* what, cudaStream_t s);
+
+// kNN (knn.cu)
+void knn_device(const double* data, int64_t nd, const double* query, int64_t nq, int k, int self_first,
+                int32_t* idx_out, double* d2_out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_max_d(double v) {
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace mgm

@@ -1,0 +1,92 @@
+// Internal layout of an MGM hierarchy on the device (not part of the public ABI).
+//
+// Every level j keeps its canonical data in its own RCM order (paper Alg. 2): points, the FP64
+// operator L_j (CSR), the RCM permutation, the coarsening survivors and the interpolation I_{j+1}^j.
+// Levels that are smoothed (all but the coarsest) also carry a "solve order": rows grouped by
+// colour (RCM order inside a colour), so that one multicolour Gauss-Seidel step is a contiguous
+// row range. In that order each row stores its off-diagonal entries split as
+//   [ columns of lower colours | pad to 4 | columns of higher colours | pad to 4 ]
+// with row starts at multiples of 4 (16-byte aligned int4 / float4 loads), the diagonal kept
+// apart (value and inverse). Interpolation rows are stored as fixed-width ELL (width m) and the
+// restriction as CSR, both indexed in the solve orders of the two levels.
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+
+namespace mgm {
+
+struct Level {
+    int64_t n = 0, nnz = 0;
+    // canonical data (RCM order, FP64)
+    Buf<double> X;
+    Buf<int32_t> rp, ci;
+    Buf<double> v;
+    Buf<int32_t> perm, keep;
+    Buf<int32_t> P_rp, P_ci;
+    Buf<double> P_v;
+    int64_t pnnz = 0;
+    Buf<int32_t> colour;
+    int ncolors = 0;
+    // solve order
+    Buf<int32_t> ord, inv;     // ord[s] = RCM index of solve row s; inv = ord^-1
+    std::vector<int32_t> cptr; // host: colour c = solve rows [cptr[c], cptr[c+1])
+    Buf<int32_t> lo, mid;      // row s: lower part [lo[s], mid[s]), upper part [mid[s], lo[s+1])
+    Buf<int32_t> sc;           // padded columns (solve order of this level)
+    Buf<float> sv32, diag32, dinv32;
+    Buf<double> sv64, diag64, dinv64;
+    int64_t snnz = 0;          // padded entry count
+    int64_t nlow = 0, nupp = 0; // unpadded lower / upper off-diagonal counts
+    // transfers in solve orders
+    int pw = 0;                // ELL width of the interpolation (= m)
+    Buf<int32_t> pc;           // n * pw
+    Buf<float> pv32;
+    Buf<double> pv64;
+    Buf<int32_t> r_rp, r_ci;   // restriction: rows = next level's solve order
+    Buf<float> r_v32;
+    Buf<double> r_v64;
+    // work vectors: b = right-hand side of the level, e = its solution, s = residual
+    Buf<float> b32, e32, s32;
+    Buf<double> b64, e64, s64;
+};
+
+}  // namespace mgm
+
+struct mgm_hierarchy {
+    int p = 0;
+    int precision = MGM_F32;
+    int nu1 = 1, nu2 = 1, m = 3;
+    uint64_t seed = 0;
+    int64_t N = 0;
+    std::vector<mgm::Level> lv;
+    mgm::Buf<double> Ainv;      // explicit inverse of L_p (RCM order), FP64
+    int64_t np = 0;
+    mgm::Buf<int32_t> ord_caller;  // level-0 solve index -> caller index
+    // V-cycle graph (captured lazily)
+    cudaGraphExec_t vgraph = nullptr;
+    int64_t graph_kernels = 0;  // kernel nodes in vgraph
+    cudaStream_t cap_stream = nullptr;
+    // Krylov workspace (allocated on first solve)
+    int krylov_m = 0;
+    mgm::Buf<double> V, f, u, w, r, part, hbuf;
+    mgm::Buf<float> Z32;
+    mgm::Buf<double> Z64;
+    mgm::Buf<double> ydev;
+    double* hhost = nullptr;    // pinned
+    int64_t device_bytes = 0;
+    ~mgm_hierarchy();
+};
+
+namespace mgm {
+// vcycle.cu
+void vcycle_core(mgm_hierarchy* H, cudaStream_t s);          // b_0 -> e_0 (graph if captured)
+void vcycle_prepare(mgm_hierarchy* H);                       // capture the graph
+void load_input(mgm_hierarchy* H, const void* src, int src_dtype, const int32_t* gather, cudaStream_t s);
+void store_output(mgm_hierarchy* H, void* dst, int dst_dtype, const int32_t* scatter, cudaStream_t s);
+void alloc_work(mgm_hierarchy* H);
+void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
+// krylov.cu
+void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
+void solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp, mgm_solve_info* info,
+           cudaStream_t s);
+}  // namespace mgm

@@ -1,0 +1,494 @@
+// MGM preprocessing on the device (paper Alg. 2) and the solve-order layouts the V-cycle runs on.
+//
+// Order of operations follows Alg. 2: RCM of L_1 and reordering of X_1 (lines 2-3); number of
+// levels (line 4); per level: weighted sample elimination to floor(N_1/4^j) points (line 6), PHS
+// interpolation (line 7), restriction = transpose (line 8), Galerkin product L_{j+1} = R (L_j P)
+// (line 9, operand order of eq. (galerkin)), RCM of L_{j+1} with the matching renumbering of the
+// coarse index of the transfers (lines 10-11); and the coarsest factorisation (line 13; an
+// explicit FP64 inverse by Gauss-Jordan elimination, so the coarsest solve is one matrix-vector
+// product per cycle). Then, for the multicolour smoother: colourings of the RCM-ordered level
+// operators, the colour-grouped solve orders, and FP32/FP64 copies of operators and transfers.
+// Built with --fmad=false (the integer decisions and FP64 setup values are bit-reproducible).
+#include <algorithm>
+#include <memory>
+
+#include "hier.cuh"
+
+namespace mgm {
+
+void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStream_t s);
+void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32_t* colour, int32_t* ncolors,
+           cudaStream_t s);
+void coarsen(const double* x, int64_t N, int64_t NH, int32_t* keep, cudaStream_t s, double* rmax_out);
+int64_t interp(const double* xf, int64_t nf, const double* xc, int64_t nc, int m, int32_t* rp, int32_t* col, double* val,
+               cudaStream_t s);
+int64_t spgemm_symbolic(int64_t nA, const int32_t* arp, const int32_t* aci, const int32_t* brp, const int32_t* bci,
+                        int32_t* crp, cudaStream_t s);
+void spgemm_numeric(int64_t nA, const int32_t* arp, const int32_t* aci, const double* av, const int32_t* brp,
+                    const int32_t* bci, const double* bv, const int32_t* crp, int32_t* cci, double* cv, cudaStream_t s);
+
+int num_levels(int64_t N1, int64_t nmin) {
+    if (N1 < nmin) return 1;
+    int t = 0;
+    __int128 pw = nmin;
+    while (pw * 4 <= N1) { pw *= 4; ++t; }
+    return t + 1;
+}
+
+// ------------------------------ helpers --------------------------------------------------------
+__global__ void remap_cols_k(const int32_t* rp, const int32_t* ci, const double* v, const int32_t* inv, int64_t n,
+                             int32_t* oci, double* ov) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t b = rp[i], e = rp[i + 1];
+    for (int32_t p = b; p < e; ++p) { oci[p] = inv[ci[p]]; ov[p] = v[p]; }
+    for (int32_t p = b + 1; p < e; ++p) {  // insertion sort by column
+        int32_t c = oci[p];
+        double x = ov[p];
+        int32_t q = p;
+        while (q > b && oci[q - 1] > c) { oci[q] = oci[q - 1]; ov[q] = ov[q - 1]; --q; }
+        oci[q] = c;
+        ov[q] = x;
+    }
+}
+
+__global__ void csr_to_dense_k(const int32_t* rp, const int32_t* ci, const double* v, int64_t n, double* A, int64_t ld) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) A[i * ld + ci[p]] = v[p];
+    A[i * ld + n + i] = 1.0;  // augmented identity
+}
+
+// Gauss-Jordan with partial pivoting on [A | I] (n x 2n): pivot step k
+__global__ void __launch_bounds__(1024) gj_pivot_k(double* A, int64_t n, int64_t k, double* mult, int* err) {
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    const int64_t ld = 2 * n;
+    double best = -1.0;
+    int64_t piv = k;
+    for (int64_t i = k + threadIdx.x; i < n; i += blockDim.x) {
+        double v = fabs(A[i * ld + k]);
+        if (v > best) { best = v; piv = i; }
+    }
+    for (int o = 16; o; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int64_t op = __shfl_xor_sync(0xffffffffu, piv, o);
+        if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+    }
+    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = (int)piv; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+        double b = threadIdx.x < nw ? sv[threadIdx.x] : -1.0;
+        int p = threadIdx.x < nw ? si[threadIdx.x] : 0x7fffffff;
+        for (int o = 16; o; o >>= 1) {
+            double ob = __shfl_xor_sync(0xffffffffu, b, o);
+            int op = __shfl_xor_sync(0xffffffffu, p, o);
+            if (ob > b || (ob == b && op < p)) { b = ob; p = op; }
+        }
+        if (threadIdx.x == 0) { sv[0] = b; si[0] = p; }
+    }
+    __syncthreads();
+    best = sv[0];
+    piv = si[0];
+    if (!(best > 0.0)) {
+        if (threadIdx.x == 0) *err = 1;
+        return;
+    }
+    if (piv != k)
+        for (int64_t j = threadIdx.x; j < ld; j += blockDim.x) {
+            double t = A[k * ld + j];
+            A[k * ld + j] = A[piv * ld + j];
+            A[piv * ld + j] = t;
+        }
+    __syncthreads();
+    double akk = A[k * ld + k];
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < ld; j += blockDim.x) A[k * ld + j] = A[k * ld + j] / akk;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mult[i] = (i == k) ? 0.0 : A[i * ld + k];
+}
+
+__global__ void gj_elim_k(double* A, int64_t n, int64_t k, const double* mult) {
+    const int64_t ld = 2 * n;
+    int64_t i = blockIdx.y;
+    double mi = mult[i];
+    if (mi == 0.0) return;
+    for (int64_t j = k + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ld; j += (int64_t)gridDim.x * blockDim.x)
+        A[i * ld + j] = fma(-mi, A[k * ld + j], A[i * ld + j]);
+}
+
+__global__ void extract_inv_k(const double* A, int64_t n, double* inv) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    int64_t i = e / n, j = e - i * n;
+    inv[e] = A[i * 2 * n + n + j];
+}
+
+static void dense_inverse(const Level& L, Buf<double>& inv, cudaStream_t s) {
+    const int64_t n = L.n;
+    if (n > 8192) fail(MGM_ERR_UNSUPPORTED, "coarsest level larger than 8192 rows");
+    Temp<double> A(2 * n * n, s), mult(n, s);
+    Temp<int> err(1, s);
+    CK(cudaMemsetAsync(A.get(), 0, sizeof(double) * 2 * n * n, s));
+    CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    csr_to_dense_k<<<grid_for(n, 128), 128, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), n, A.get(), 2 * n);
+    CK_LAUNCH();
+    for (int64_t k = 0; k < n; ++k) {
+        gj_pivot_k<<<1, 1024, 0, s>>>(A.get(), n, k, mult.get(), err.get());
+        CK_LAUNCH();
+        dim3 g((unsigned)std::min<int64_t>((2 * n - k + 255) / 256, 8), (unsigned)n);
+        gj_elim_k<<<g, 256, 0, s>>>(A.get(), n, k, mult.get());
+        CK_LAUNCH();
+    }
+    if (read1(err.get(), s)) fail(MGM_ERR_BREAKDOWN, "coarsest operator is singular");
+    inv.alloc(n * n);
+    extract_inv_k<<<grid_for(n * n, 256), 256, 0, s>>>(A.get(), n, inv.get());
+    CK_LAUNCH();
+}
+
+// ------------------------------ solve-order layout ---------------------------------------------
+__global__ void colour_hist_k(const int32_t* col, int64_t n, int32_t* hist) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&hist[col[i]], 1);
+}
+__global__ void colour_flag_k(const int32_t* col, int64_t n, int32_t c, int32_t* fl) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) fl[i] = col[i] == c ? 1 : 0;
+}
+__global__ void colour_scatter_k(const int32_t* col, int64_t n, int32_t c, const int32_t* pos, int32_t base, int32_t* ord) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && col[i] == c) ord[base + pos[i]] = (int32_t)i;
+}
+
+__device__ __forceinline__ int32_t pad4(int32_t x) { return (x + 3) & ~3; }
+
+// lengths of the split rows; err bit 1: same colour off-diagonal, bit 2: missing/zero diagonal
+__global__ void split_len_k(const int32_t* rp, const int32_t* ci, const double* v, const int32_t* col, const int32_t* ord,
+                            int64_t n, int single, int32_t* len, int32_t* nlo, int* err, unsigned long long* tot) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int32_t r = ord[s];
+    int32_t cr = single ? 0 : col[r];
+    int32_t nl = 0, nu = 0;
+    bool diag = false;
+    for (int32_t p = rp[r]; p < rp[r + 1]; ++p) {
+        int32_t j = ci[p];
+        if (j == r) { diag = v[p] != 0.0; continue; }
+        int32_t cj = single ? 1 : col[j];
+        if (cj == cr) atomicOr(err, 1);
+        if (cj < cr) ++nl; else ++nu;
+    }
+    if (!diag) atomicOr(err, 2);
+    atomicAdd(&tot[0], (unsigned long long)nl);
+    atomicAdd(&tot[1], (unsigned long long)nu);
+    len[s] = pad4(nl) + pad4(nu);
+    nlo[s] = pad4(nl);
+}
+
+__global__ void split_fill_k(const int32_t* rp, const int32_t* ci, const double* v, const int32_t* col, const int32_t* ord,
+                             const int32_t* inv, int64_t n, int single, const int32_t* lo, int32_t* mid, int32_t* sc,
+                             double* sv64, float* sv32, double* diag64, double* dinv64, float* diag32, float* dinv32) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int32_t r = ord[s];
+    int32_t cr = single ? 0 : col[r];
+    int32_t b = lo[s];
+    int32_t q = b;
+    double d = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        int32_t start = q;
+        for (int32_t p = rp[r]; p < rp[r + 1]; ++p) {
+            int32_t j = ci[p];
+            if (j == r) { d = v[p]; continue; }
+            int32_t cj = single ? 1 : col[j];
+            if ((pass == 0) != (cj < cr)) continue;
+            int32_t js = inv[j];
+            double x = v[p];
+            int32_t t = q++;
+            while (t > start && sc[t - 1] > js) { sc[t] = sc[t - 1]; sv64[t] = sv64[t - 1]; --t; }
+            sc[t] = js;
+            sv64[t] = x;
+        }
+        while ((q - b) & 3) { sc[q] = (int32_t)s; sv64[q] = 0.0; ++q; }
+        if (pass == 0) mid[s] = q;
+    }
+    for (int32_t t = b; t < q; ++t) sv32[t] = (float)sv64[t];
+    diag64[s] = d;
+    dinv64[s] = 1.0 / d;
+    diag32[s] = (float)d;
+    dinv32[s] = (float)(1.0 / d);
+}
+
+static void build_solve_layout(Level& L, bool single, cudaStream_t s) {
+    const int64_t n = L.n;
+    L.ord.alloc(n);
+    L.inv.alloc(n);
+    if (single) {
+        iota_i32(L.ord.get(), n, s);
+        L.cptr = {0, (int32_t)n};
+    } else {
+        const int nc = L.ncolors;
+        Temp<int32_t> hist(nc, s);
+        CK(cudaMemsetAsync(hist.get(), 0, sizeof(int32_t) * nc, s));
+        colour_hist_k<<<grid_for(n, 256), 256, 0, s>>>(L.colour.get(), n, hist.get());
+        CK_LAUNCH();
+        std::vector<int32_t> h(nc);
+        to_host(h.data(), hist.get(), nc, s);
+        L.cptr.assign(nc + 1, 0);
+        for (int c = 0; c < nc; ++c) L.cptr[c + 1] = L.cptr[c] + h[c];
+        Temp<int32_t> fl(n, s), pos(n + 1, s);
+        for (int c = 0; c < nc; ++c) {
+            colour_flag_k<<<grid_for(n, 256), 256, 0, s>>>(L.colour.get(), n, c, fl.get());
+            CK_LAUNCH();
+            exclusive_scan_i32(fl.get(), pos.get(), n, s);
+            colour_scatter_k<<<grid_for(n, 256), 256, 0, s>>>(L.colour.get(), n, c, pos.get(), L.cptr[c], L.ord.get());
+            CK_LAUNCH();
+        }
+    }
+    invert_perm(L.ord.get(), L.inv.get(), n, s);
+    Temp<int32_t> len(n + 1, s), nlo(n, s);
+    Temp<int> err(1, s);
+    Temp<unsigned long long> tot(2, s);
+    CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    CK(cudaMemsetAsync(tot.get(), 0, 2 * sizeof(unsigned long long), s));
+    split_len_k<<<grid_for(n, 256), 256, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(), n,
+                                                 single ? 1 : 0, len.get(), nlo.get(), err.get(), tot.get());
+    CK_LAUNCH();
+    unsigned long long th[2];
+    to_host(th, tot.get(), 2, s);
+    L.nlow = (int64_t)th[0];
+    L.nupp = (int64_t)th[1];
+    int e = read1(err.get(), s);
+    if (e & 1) fail(MGM_ERR_INVALID_ARG, "colouring is not valid for the operator pattern");
+    if (e & 2) fail(MGM_ERR_BREAKDOWN, "a level operator has a zero or missing diagonal entry");
+    L.lo.alloc(n + 1);
+    L.mid.alloc(n);
+    exclusive_scan_i32(len.get(), L.lo.get(), n, s);
+    L.snnz = csr_nnz(L.lo.get(), n, s);
+    L.sc.alloc(std::max<int64_t>(L.snnz, 4));
+    L.sv64.alloc(std::max<int64_t>(L.snnz, 4));
+    L.sv32.alloc(std::max<int64_t>(L.snnz, 4));
+    L.diag64.alloc(n); L.dinv64.alloc(n); L.diag32.alloc(n); L.dinv32.alloc(n);
+    split_fill_k<<<grid_for(n, 128), 128, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(), L.inv.get(),
+                                                  n, single ? 1 : 0, L.lo.get(), L.mid.get(), L.sc.get(), L.sv64.get(),
+                                                  L.sv32.get(), L.diag64.get(), L.dinv64.get(), L.diag32.get(), L.dinv32.get());
+    CK_LAUNCH();
+}
+
+// interpolation rows re-indexed to solve orders: compact CSR (for the transpose) and ELL
+__global__ void p_solve_len_k(const int32_t* prp, const int32_t* ord, int64_t n, int32_t* len) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) { int32_t r = ord[s]; len[s] = prp[r + 1] - prp[r]; }
+}
+__global__ void p_solve_fill_k(const int32_t* prp, const int32_t* pci, const double* pv, const int32_t* ord,
+                               const int32_t* next_inv, int64_t n, int pw, const int32_t* crp, int32_t* cci, double* cv,
+                               int32_t* ec, double* ev64, float* ev32) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int32_t r = ord[s];
+    int32_t b = prp[r], len = prp[r + 1] - b;
+    int32_t q0 = crp[s];
+    for (int t = 0; t < len; ++t) {
+        int32_t c = next_inv ? next_inv[pci[b + t]] : pci[b + t];
+        cci[q0 + t] = c;
+        cv[q0 + t] = pv[b + t];
+    }
+    for (int t = 1; t < len; ++t) {  // sort by column
+        int32_t c = cci[q0 + t];
+        double x = cv[q0 + t];
+        int u = t;
+        while (u > 0 && cci[q0 + u - 1] > c) { cci[q0 + u] = cci[q0 + u - 1]; cv[q0 + u] = cv[q0 + u - 1]; --u; }
+        cci[q0 + u] = c;
+        cv[q0 + u] = x;
+    }
+    for (int t = 0; t < pw; ++t) {
+        bool has = t < len;
+        ec[s * pw + t] = has ? cci[q0 + t] : 0;
+        ev64[s * pw + t] = has ? cv[q0 + t] : 0.0;
+        ev32[s * pw + t] = has ? (float)cv[q0 + t] : 0.0f;
+    }
+}
+__global__ void to_f32_k(const double* a, float* b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+static void build_transfers(Level& F, const Level* C, int64_t nc, int m, cudaStream_t s) {
+    const int64_t n = F.n;
+    Temp<int32_t> len(n + 1, s), crp(n + 1, s);
+    p_solve_len_k<<<grid_for(n, 256), 256, 0, s>>>(F.P_rp.get(), F.ord.get(), n, len.get());
+    CK_LAUNCH();
+    exclusive_scan_i32(len.get(), crp.get(), n, s);
+    Temp<int32_t> cci(std::max<int64_t>(F.pnnz, 1), s);
+    Temp<double> cv(std::max<int64_t>(F.pnnz, 1), s);
+    F.pw = m;
+    F.pc.alloc(n * m);
+    F.pv64.alloc(n * m);
+    F.pv32.alloc(n * m);
+    p_solve_fill_k<<<grid_for(n, 128), 128, 0, s>>>(F.P_rp.get(), F.P_ci.get(), F.P_v.get(), F.ord.get(),
+                                                    C ? C->inv.get() : nullptr, n, m, crp.get(), cci.get(), cv.get(),
+                                                    F.pc.get(), F.pv64.get(), F.pv32.get());
+    CK_LAUNCH();
+    F.r_rp.alloc(nc + 1);
+    F.r_ci.alloc(std::max<int64_t>(F.pnnz, 1));
+    F.r_v64.alloc(std::max<int64_t>(F.pnnz, 1));
+    F.r_v32.alloc(std::max<int64_t>(F.pnnz, 1));
+    csr_transpose(n, nc, crp.get(), cci.get(), cv.get(), F.r_rp.get(), F.r_ci.get(), F.r_v64.get(), s);
+    if (F.pnnz > 0) {
+        to_f32_k<<<grid_for(F.pnnz, 256), 256, 0, s>>>(F.r_v64.get(), F.r_v32.get(), F.pnnz);
+        CK_LAUNCH();
+    }
+}
+
+__global__ void compose_k(const int32_t* a, const int32_t* b, int64_t n, int32_t* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[b[i]];
+}
+
+// ------------------------------ setup driver ---------------------------------------------------
+mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int32_t* ci, const double* v,
+                     const mgm_params* prm, cudaStream_t s) {
+    REQUIRE(prm != nullptr, "null params");
+    REQUIRE(xyz && rp && ci && v, "null array");
+    REQUIRE(N >= 1 && N < 0x7fffffff, "N out of range");
+    REQUIRE(prm->n_min >= 1, "n_min must be >= 1");
+    REQUIRE(prm->m >= 1 && prm->m <= 8, "m must be in [1, 8]");
+    REQUIRE(prm->nu1 >= 0 && prm->nu1 <= 8 && prm->nu2 >= 0 && prm->nu2 <= 8, "nu1, nu2 must be in [0, 8]");
+    REQUIRE(prm->precision == MGM_F32 || prm->precision == MGM_F64, "precision must be MGM_F32 or MGM_F64");
+    std::unique_ptr<mgm_hierarchy> H(new mgm_hierarchy());
+    H->precision = prm->precision;
+    H->nu1 = prm->nu1;
+    H->nu2 = prm->nu2;
+    H->m = prm->m;
+    H->seed = prm->seed;
+    H->N = N;
+    int p = num_levels(N, prm->n_min);
+    if (p > 16) fail(MGM_ERR_UNSUPPORTED, "more than 16 levels");
+    // coarse levels must keep at least m points for the interpolation
+    while (p > 1 && N / ((int64_t)1 << (2 * (p - 1))) < prm->m) --p;
+    H->p = p;
+    H->lv.resize(p);
+    const int64_t nnz = csr_nnz(rp, N, s);
+    {   // level 1: RCM of L_1 and X_1 (Alg. 2 lines 2-3)
+        Level& L = H->lv[0];
+        L.n = N;
+        L.nnz = nnz;
+        L.perm.alloc(N);
+        rcm(N, rp, ci, L.perm.get(), s);
+        L.X.alloc(3 * N);
+        gather_xyz(xyz, L.perm.get(), L.X.get(), N, s);
+        L.rp.alloc(N + 1);
+        L.ci.alloc(nnz);
+        L.v.alloc(nnz);
+        csr_permute(N, rp, ci, v, L.perm.get(), L.rp.get(), L.ci.get(), L.v.get(), s);
+    }
+    for (int j = 1; j < p; ++j) {
+        Level& F = H->lv[j - 1];
+        Level& C = H->lv[j];
+        const int64_t NH = N / ((int64_t)1 << (2 * j));
+        C.n = NH;
+        C.keep.alloc(NH);
+        coarsen(F.X.get(), F.n, NH, C.keep.get(), s, nullptr);              // line 6
+        Temp<double> Xc(3 * NH, s);
+        gather_xyz(F.X.get(), C.keep.get(), Xc.get(), NH, s);
+        Temp<int32_t> P_rp(F.n + 1, s), P_ci(F.n * prm->m, s);
+        Temp<double> P_v(F.n * prm->m, s);
+        int64_t pnnz = interp(F.X.get(), F.n, Xc.get(), NH, prm->m, P_rp.get(), P_ci.get(), P_v.get(), s);  // line 7
+        Temp<int32_t> R_rp(NH + 1, s), R_ci(std::max<int64_t>(pnnz, 1), s);
+        Temp<double> R_v(std::max<int64_t>(pnnz, 1), s);
+        csr_transpose(F.n, NH, P_rp.get(), P_ci.get(), P_v.get(), R_rp.get(), R_ci.get(), R_v.get(), s);  // line 8
+        // line 9: L_{j+1} = R (L_j P)
+        Temp<int32_t> T_rp(F.n + 1, s);
+        int64_t tnnz = spgemm_symbolic(F.n, F.rp.get(), F.ci.get(), P_rp.get(), P_ci.get(), T_rp.get(), s);
+        Temp<int32_t> T_ci(std::max<int64_t>(tnnz, 1), s);
+        Temp<double> T_v(std::max<int64_t>(tnnz, 1), s);
+        spgemm_numeric(F.n, F.rp.get(), F.ci.get(), F.v.get(), P_rp.get(), P_ci.get(), P_v.get(), T_rp.get(), T_ci.get(),
+                       T_v.get(), s);
+        Temp<int32_t> G_rp(NH + 1, s);
+        int64_t gnnz = spgemm_symbolic(NH, R_rp.get(), R_ci.get(), T_rp.get(), T_ci.get(), G_rp.get(), s);
+        Temp<int32_t> G_ci(std::max<int64_t>(gnnz, 1), s);
+        Temp<double> G_v(std::max<int64_t>(gnnz, 1), s);
+        spgemm_numeric(NH, R_rp.get(), R_ci.get(), R_v.get(), T_rp.get(), T_ci.get(), T_v.get(), G_rp.get(), G_ci.get(),
+                       G_v.get(), s);
+        // lines 10-11: RCM of L_{j+1}; renumber coarse points and the interpolation's columns
+        C.perm.alloc(NH);
+        rcm(NH, G_rp.get(), G_ci.get(), C.perm.get(), s);
+        C.X.alloc(3 * NH);
+        gather_xyz(Xc.get(), C.perm.get(), C.X.get(), NH, s);
+        C.nnz = gnnz;
+        C.rp.alloc(NH + 1);
+        C.ci.alloc(std::max<int64_t>(gnnz, 1));
+        C.v.alloc(std::max<int64_t>(gnnz, 1));
+        csr_permute(NH, G_rp.get(), G_ci.get(), G_v.get(), C.perm.get(), C.rp.get(), C.ci.get(), C.v.get(), s);
+        Temp<int32_t> cinv(NH, s);
+        invert_perm(C.perm.get(), cinv.get(), NH, s);
+        F.pnnz = pnnz;
+        F.P_rp.alloc(F.n + 1);
+        F.P_ci.alloc(std::max<int64_t>(pnnz, 1));
+        F.P_v.alloc(std::max<int64_t>(pnnz, 1));
+        CK(cudaMemcpyAsync(F.P_rp.get(), P_rp.get(), sizeof(int32_t) * (F.n + 1), cudaMemcpyDeviceToDevice, s));
+        remap_cols_k<<<grid_for(F.n, 256), 256, 0, s>>>(P_rp.get(), P_ci.get(), P_v.get(), cinv.get(), F.n, F.P_ci.get(),
+                                                      F.P_v.get());
+        CK_LAUNCH();
+    }
+    // colourings, solve orders, transfers
+    for (int j = 0; j + 1 < p; ++j) {
+        Level& L = H->lv[j];
+        L.colour.alloc(L.n);
+        int32_t nc = 0;
+        color(L.n, L.rp.get(), L.ci.get(), prm->seed, L.colour.get(), &nc, s);
+        L.ncolors = nc;
+        build_solve_layout(L, false, s);
+    }
+    if (p == 1) build_solve_layout(H->lv[0], true, s);  // one group: serves the outer operator only
+    for (int j = 0; j + 1 < p; ++j)
+        build_transfers(H->lv[j], (j + 2 < p) ? &H->lv[j + 1] : nullptr, H->lv[j + 1].n, prm->m, s);
+    // coarsest (line 13)
+    H->np = H->lv[p - 1].n;
+    dense_inverse(H->lv[p - 1], H->Ainv, s);
+    // caller index of each level-0 solve row
+    H->ord_caller.alloc(N);
+    compose_k<<<grid_for(N, 256), 256, 0, s>>>(H->lv[0].perm.get(), H->lv[0].ord.get(), N, H->ord_caller.get());
+    CK_LAUNCH();
+    alloc_work(H.get());
+    CK(cudaStreamSynchronize(s));
+    int64_t bytes = H->Ainv.bytes() + H->ord_caller.bytes();
+    for (auto& L : H->lv)
+        bytes += L.X.bytes() + L.rp.bytes() + L.ci.bytes() + L.v.bytes() + L.perm.bytes() + L.keep.bytes() + L.P_rp.bytes() +
+                 L.P_ci.bytes() + L.P_v.bytes() + L.colour.bytes() + L.ord.bytes() + L.inv.bytes() + L.lo.bytes() +
+                 L.mid.bytes() + L.sc.bytes() + L.sv32.bytes() + L.sv64.bytes() + 3 * L.diag64.bytes() + 3 * L.diag32.bytes() +
+                 L.pc.bytes() + L.pv32.bytes() + L.pv64.bytes() + L.r_rp.bytes() + L.r_ci.bytes() + L.r_v32.bytes() +
+                 L.r_v64.bytes() + L.b32.bytes() * 3 + L.b64.bytes() * 3;
+    H->device_bytes = bytes;
+    return H.release();
+}
+
+void hierarchy_level(const mgm_hierarchy* H, int j, int32_t* perm, int32_t* keep, double* xyz, int32_t* lrp, int32_t* lci,
+                     double* lv, int32_t* prp, int32_t* pci, double* pv, int32_t* colour, cudaStream_t s) {
+    REQUIRE(H && j >= 0 && j < H->p, "level index out of range");
+    const Level& L = H->lv[j];
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        if (dst && src && bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+    };
+    cp(perm, L.perm.get(), L.perm.bytes());
+    if (j >= 1) cp(keep, L.keep.get(), L.keep.bytes());
+    cp(xyz, L.X.get(), sizeof(double) * 3 * L.n);
+    cp(lrp, L.rp.get(), sizeof(int32_t) * (L.n + 1));
+    cp(lci, L.ci.get(), sizeof(int32_t) * L.nnz);
+    cp(lv, L.v.get(), sizeof(double) * L.nnz);
+    if (j + 1 < H->p) {
+        cp(prp, L.P_rp.get(), sizeof(int32_t) * (L.n + 1));
+        cp(pci, L.P_ci.get(), sizeof(int32_t) * L.pnnz);
+        cp(pv, L.P_v.get(), sizeof(double) * L.pnnz);
+        cp(colour, L.colour.get(), sizeof(int32_t) * L.n);
+    }
+}
+
+}  // namespace mgm
+
+mgm_hierarchy::~mgm_hierarchy() {
+    if (vgraph) cudaGraphExecDestroy(vgraph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (hhost) cudaFreeHost(hhost);
+}

@@ -1,0 +1,388 @@
+// Exact k-nearest-neighbour and fixed-radius searches on a uniform grid (paper Sec. 2: stencils
+// are the n nearest nodes in Euclidean R^3; Sec. 3: the m nearest coarse nodes; Sec. 4.1: the
+// elimination weights use all neighbours within 2 r_max).
+//
+// Design: points are binned into a dense 3-D grid of about 2 N cells (counting sort by cell,
+// coordinates copied into cell order so a warp reads a cell with coalesced 24-byte loads). One
+// warp answers one query: it scans Chebyshev shells of cells around the query's cell, appending
+// (d^2, index) candidates to a per-warp shared-memory buffer (compacted to its k smallest keys
+// whenever it fills), until at least k candidates lie strictly inside the radius r*h that the
+// scanned block is guaranteed to cover. The k smallest
+// keys are then placed by rank counting. The result is therefore exactly the (d^2, index) order
+// the definition asks for, independent of the grid and of scheduling. Distances are computed as
+// (dx*dx + dy*dy) + dz*dz without contraction (this file is built with --fmad=false).
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace mgm {
+
+constexpr int KNN_WARPS = 4;
+constexpr int KNN_CAP = 2048;  // candidate buffer per warp
+
+struct Grid {
+    double x0, y0, z0, h;
+    int nx, ny, nz;
+    int64_t ncells;
+};
+
+__device__ __forceinline__ double d2_pts(double ax, double ay, double az, double bx, double by, double bz) {
+    double dx = ax - bx, dy = ay - by, dz = az - bz;
+    return (dx * dx + dy * dy) + dz * dz;
+}
+
+// ------------------------------ grid construction --------------------------------------------
+__global__ void bbox_partial_k(const double* x, int64_t n, double* part) {
+    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int c = 0; c < 3; ++c) {
+            double v = x[3 * i + c];
+            mn[c] = fmin(mn[c], v);
+            mx[c] = fmax(mx[c], v);
+        }
+    __shared__ double s[6][32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c = 0; c < 3; ++c) {
+        double a = mn[c], b = mx[c];
+        for (int o = 16; o; o >>= 1) {
+            a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) { s[c][w] = a; s[3 + c][w] = b; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = blockDim.x / 32;
+        for (int c = 0; c < 3; ++c) {
+            double a = s[c][0], b = s[3 + c][0];
+            for (int t = 1; t < nw; ++t) { a = fmin(a, s[c][t]); b = fmax(b, s[3 + c][t]); }
+            part[6 * blockIdx.x + c] = a;
+            part[6 * blockIdx.x + 3 + c] = b;
+        }
+    }
+}
+
+// one thread: reduce partial boxes, choose h so that the dense grid has at most `cells` cells
+__global__ void grid_params_k(const double* part, int nparts, int64_t cells, double h_min, Grid* g) {
+    double mn[3], mx[3];
+    for (int c = 0; c < 3; ++c) { mn[c] = part[c]; mx[c] = part[3 + c]; }
+    for (int b = 1; b < nparts; ++b)
+        for (int c = 0; c < 3; ++c) { mn[c] = fmin(mn[c], part[6 * b + c]); mx[c] = fmax(mx[c], part[6 * b + 3 + c]); }
+    double e[3], emax = 0.0;
+    for (int c = 0; c < 3; ++c) { e[c] = mx[c] - mn[c]; emax = fmax(emax, e[c]); }
+    if (!(emax > 0.0)) emax = 1.0;
+    // bisection on h: count(h) = prod(floor(e/h) + 1) <= cells
+    double lo = emax * 1e-9, hi = emax * 2.0 + 1.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double cnt = 1.0;
+        for (int c = 0; c < 3; ++c) cnt *= floor(e[c] / mid) + 1.0;
+        if (cnt <= (double)cells) hi = mid; else lo = mid;
+    }
+    double h = fmax(hi, h_min);
+    g->x0 = mn[0]; g->y0 = mn[1]; g->z0 = mn[2]; g->h = h;
+    g->nx = (int)floor(e[0] / h) + 1; g->ny = (int)floor(e[1] / h) + 1; g->nz = (int)floor(e[2] / h) + 1;
+    g->ncells = (int64_t)g->nx * g->ny * g->nz;
+}
+
+__device__ __forceinline__ int cell_coord(double v, double o, double h, int nd) {
+    double t = floor((v - o) / h);
+    int c = (int)fmax(0.0, fmin(t, (double)(nd - 1)));
+    return c;
+}
+
+__global__ void cell_count_k(const double* x, int64_t n, const Grid* gp, int32_t* cnt, int32_t* cell_of) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Grid g = *gp;
+    int cx = cell_coord(x[3 * i], g.x0, g.h, g.nx), cy = cell_coord(x[3 * i + 1], g.y0, g.h, g.ny),
+        cz = cell_coord(x[3 * i + 2], g.z0, g.h, g.nz);
+    int64_t c = ((int64_t)cz * g.ny + cy) * g.nx + cx;
+    cell_of[i] = (int32_t)c;
+    atomicAdd(&cnt[c], 1);
+}
+__global__ void cell_place_k(const double* x, int64_t n, const int32_t* cell_of, const int32_t* start, int32_t* fill,
+                             int32_t* sidx, double* sxyz) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t c = cell_of[i];
+    int32_t q = start[c] + atomicAdd(&fill[c], 1);
+    sidx[q] = (int32_t)i;
+    sxyz[3 * (int64_t)q] = x[3 * i];
+    sxyz[3 * (int64_t)q + 1] = x[3 * i + 1];
+    sxyz[3 * (int64_t)q + 2] = x[3 * i + 2];
+}
+
+struct DevGrid {
+    Temp<Grid> g;
+    Temp<int32_t> start, sidx;
+    Temp<double> sxyz;
+    int64_t cells;
+};
+
+static void build_grid(const double* x, int64_t n, int64_t cells, double h_min, DevGrid& G, cudaStream_t s) {
+    if (cells < 1) cells = 1;
+    if (cells > (int64_t)1 << 27) cells = (int64_t)1 << 27;
+    G.cells = cells;
+    int nparts = (int)std::min<int64_t>(grid_for(n, 256), 1024);
+    Temp<double> part(6 * nparts, s);
+    bbox_partial_k<<<nparts, 256, 0, s>>>(x, n, part.get());
+    CK_LAUNCH();
+    G.g.alloc(1, s);
+    grid_params_k<<<1, 1, 0, s>>>(part.get(), nparts, cells, h_min, G.g.get());
+    CK_LAUNCH();
+    Temp<int32_t> cnt(cells + 1, s), cell_of(n, s);
+    CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (cells + 1), s));
+    cell_count_k<<<grid_for(n, 256), 256, 0, s>>>(x, n, G.g.get(), cnt.get(), cell_of.get());
+    CK_LAUNCH();
+    G.start.alloc(cells + 1, s);
+    exclusive_scan_i32(cnt.get(), G.start.get(), cells, s);
+    CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (cells + 1), s));
+    G.sidx.alloc(n, s);
+    G.sxyz.alloc(3 * n, s);
+    cell_place_k<<<grid_for(n, 256), 256, 0, s>>>(x, n, cell_of.get(), G.start.get(), cnt.get(), G.sidx.get(),
+                                                    G.sxyz.get());
+    CK_LAUNCH();
+}
+
+// ------------------------------ kNN -----------------------------------------------------------
+__device__ __forceinline__ bool key_lt(double a, int ia, double b, int ib) { return a < b || (a == b && ia < ib); }
+
+// Keep only the k smallest keys of the buffer (stable, in place). A candidate outside the k
+// smallest of a subset can never enter the k smallest of the full set, so this loses nothing.
+__device__ int knn_compact(double* bd, int* bi, int count, int k, int lane) {
+    double td = 0.0;
+    int tj = 0;
+    bool found = false;
+    for (int t = lane; t < count; t += 32) {
+        int rank = 0;
+        for (int u = 0; u < count; ++u) rank += key_lt(bd[u], bi[u], bd[t], bi[t]) ? 1 : 0;
+        if (rank == k - 1) { td = bd[t]; tj = bi[t]; found = true; }
+    }
+    unsigned fm = __ballot_sync(0xffffffffu, found);
+    int src = __ffs(fm) - 1;
+    td = __shfl_sync(0xffffffffu, td, src);
+    tj = __shfl_sync(0xffffffffu, tj, src);
+    int w = 0;
+    for (int base = 0; base < count; base += 32) {
+        int t = base + lane;
+        bool has = t < count;
+        double d = has ? bd[t] : 0.0;
+        int j = has ? bi[t] : 0;
+        bool keep = has && !key_lt(td, tj, d, j);
+        __syncwarp();
+        unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            int pos = w + __popc(km & ((1u << lane) - 1u));
+            bd[pos] = d;
+            bi[pos] = j;
+        }
+        w += __popc(km);
+        __syncwarp();
+    }
+    return w;
+}
+
+__global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const int32_t* start, const int32_t* sidx,
+                                                        const double* sxyz, const double* q, int64_t nq, int k,
+                                                        int self_first, int32_t* idx_out, double* d2_out, int* err) {
+    extern __shared__ __align__(16) unsigned char knn_smem[];
+    double (*sd)[KNN_CAP] = reinterpret_cast<double (*)[KNN_CAP]>(knn_smem);
+    int (*si)[KNN_CAP] = reinterpret_cast<int (*)[KNN_CAP]>(knn_smem + sizeof(double) * KNN_WARPS * KNN_CAP);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t qi = (int64_t)blockIdx.x * KNN_WARPS + w;
+    if (qi >= nq) return;
+    const Grid g = *gp;
+    const double px = q[3 * qi], py = q[3 * qi + 1], pz = q[3 * qi + 2];
+    const int cx = cell_coord(px, g.x0, g.h, g.nx), cy = cell_coord(py, g.y0, g.h, g.ny), cz = cell_coord(pz, g.z0, g.h, g.nz);
+    const int rfull = max(max(max(cx, g.nx - 1 - cx), max(cy, g.ny - 1 - cy)), max(cz, g.nz - 1 - cz));
+    double* bd = sd[w];
+    int* bi = si[w];
+    int count = 0;
+    double lim2 = 0.0;
+    bool all = false;
+    for (int r = 0;; ++r) {
+        for (int dz = -r; dz <= r; ++dz) {
+            int z = cz + dz;
+            if (z < 0 || z >= g.nz) continue;
+            for (int dy = -r; dy <= r; ++dy) {
+                int y = cy + dy;
+                if (y < 0 || y >= g.ny) continue;
+                bool face = (dz == -r || dz == r || dy == -r || dy == r);
+                for (int dx = -r; dx <= r; dx += (face ? 1 : 2 * r)) {
+                    int x = cx + dx;
+                    if (x >= 0 && x < g.nx) {
+                        int64_t c = ((int64_t)z * g.ny + y) * g.nx + x;
+                        int b = start[c], e = start[c + 1];
+                        for (int t = b + lane; t - lane < e; t += 32) {
+                            if (count + 32 > KNN_CAP) {
+                                __syncwarp();
+                                count = knn_compact(bd, bi, count, k, lane);
+                            }
+                            bool has = t < e;
+                            double d = 0.0;
+                            int j = 0;
+                            if (has) {
+                                j = sidx[t];
+                                d = (self_first && j == (int)qi)
+                                        ? -1.0
+                                        : d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1], sxyz[3 * (int64_t)t + 2]);
+                            }
+                            unsigned m = __ballot_sync(0xffffffffu, has);
+                            int pos = count + __popc(m & ((1u << lane) - 1u));
+                            if (has) { bd[pos] = d; bi[pos] = j; }
+                            count += __popc(m);
+                        }
+                    }
+                    if (r == 0) break;
+                }
+            }
+        }
+        if (r >= rfull) { all = true; break; }
+        if (r >= 1) {
+            double R = (double)r * g.h;
+            lim2 = R * R * (1.0 - 1e-9);
+            __syncwarp();
+            int nin = 0;
+            for (int t = lane; t < count; t += 32) nin += bd[t] < lim2 ? 1 : 0;
+            nin = warp_sum_i(nin);
+            if (nin >= k) break;
+        }
+    }
+    __syncwarp();
+    if (all && count < k) {
+        if (lane == 0) atomicOr(err, 2);
+        return;
+    }
+    // rank the filtered candidates
+    for (int t = lane; t < count; t += 32) {
+        double d = bd[t];
+        int j = bi[t];
+        if (!all && !(d < lim2)) continue;
+        int rank = 0;
+        for (int u = 0; u < count; ++u) {
+            double e = bd[u];
+            if (!all && !(e < lim2)) continue;
+            rank += key_lt(e, bi[u], d, j) ? 1 : 0;
+        }
+        if (rank < k) {
+            idx_out[qi * k + rank] = j;
+            if (d2_out) d2_out[qi * k + rank] = d < 0.0 ? 0.0 : d;
+        }
+    }
+}
+
+void knn_device(const double* data, int64_t nd, const double* query, int64_t nq, int k, int self_first,
+                int32_t* idx_out, double* d2_out, cudaStream_t s) {
+    REQUIRE(k >= 1 && k <= 256, "k must be in [1, 256]");
+    REQUIRE(nd >= k, "k exceeds the number of data points");
+    REQUIRE(nd < 0x7fffffff && nq < 0x7fffffff, "point counts must be < 2^31");
+    REQUIRE(!self_first || (data == query && nd == nq), "self_first requires query == data");
+    if (nq == 0) return;
+    DevGrid G;
+    build_grid(data, nd, 2 * nd, 0.0, G, s);
+    Temp<int> err(1, s);
+    CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    const size_t smem = (sizeof(double) + sizeof(int)) * KNN_WARPS * KNN_CAP;
+    CK(cudaFuncSetAttribute(knn_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    knn_k<<<grid_for(nq, KNN_WARPS), KNN_WARPS * 32, smem, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), query,
+                                                            nq, k, self_first, idx_out, d2_out, err.get());
+    CK_LAUNCH();
+    int e = read1(err.get(), s);
+    if (e & 1) fail(MGM_ERR_UNSUPPORTED, "kNN candidate buffer overflow (points too clustered for the grid)");
+    if (e & 2) fail(MGM_ERR_INVALID_ARG, "fewer than k data points");
+}
+
+// ------------------------------ fixed-radius neighbour lists (for elimination weights) --------
+// For each point i: all j != i with sqrt(d2) < two_rmax, ascending j, with the elimination weight
+// contribution f = (1 - max(d, rmin)/two_rmax)^8 (three squarings). Two passes: count, then fill.
+constexpr int RAD_WARPS = 4;
+constexpr int RAD_CAP = 1024;
+
+template <bool FILL>
+__global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const int32_t* start, const int32_t* sidx,
+                                                           const double* sxyz, const double* x, int64_t n,
+                                                           const double* prm /* two_rmax, rmin */, int32_t* cnt,
+                                                           const int32_t* rowptr, int32_t* nbr, double* f, int* err) {
+    __shared__ int si[RAD_WARPS][RAD_CAP];
+    __shared__ double sdist[RAD_WARPS][RAD_CAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * RAD_WARPS + w;
+    if (i >= n) return;
+    const Grid g = *gp;
+    const double two_rmax = prm[0], rmin = prm[1];
+    const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    const int cx = cell_coord(px, g.x0, g.h, g.nx), cy = cell_coord(py, g.y0, g.h, g.ny), cz = cell_coord(pz, g.z0, g.h, g.nz);
+    // ring count so that the scanned block covers the radius: r*h >= two_rmax (plus one cell for
+    // rounding at the bin boundary)
+    const int R = (int)ceil(two_rmax / g.h) + 1;
+    int count = 0;
+    for (int z = max(cz - R, 0); z <= min(cz + R, g.nz - 1); ++z)
+        for (int y = max(cy - R, 0); y <= min(cy + R, g.ny - 1); ++y)
+            for (int xx = max(cx - R, 0); xx <= min(cx + R, g.nx - 1); ++xx) {
+                int64_t c = ((int64_t)z * g.ny + y) * g.nx + xx;
+                int b = start[c], e = start[c + 1];
+                for (int t = b + lane; t - lane < e; t += 32) {
+                    bool has = false;
+                    int j = 0;
+                    double d = 0.0;
+                    if (t < e) {
+                        j = sidx[t];
+                        if (j != (int)i) {
+                            d = sqrt(d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1], sxyz[3 * (int64_t)t + 2]));
+                            has = d < two_rmax;
+                        }
+                    }
+                    unsigned m = __ballot_sync(0xffffffffu, has);
+                    int pos = count + __popc(m & ((1u << lane) - 1u));
+                    if (has && pos < RAD_CAP) { si[w][pos] = j; sdist[w][pos] = d; }
+                    count += __popc(m);
+                }
+            }
+    if (count > RAD_CAP) {
+        if (lane == 0) atomicOr(err, 1);
+        return;
+    }
+    if (!FILL) {
+        if (lane == 0) cnt[i] = count;
+        return;
+    }
+    __syncwarp();
+    const int64_t base = rowptr[i];
+    for (int t = lane; t < count; t += 32) {
+        int j = si[w][t];
+        int rank = 0;
+        for (int u = 0; u < count; ++u) rank += si[w][u] < j ? 1 : 0;
+        double d = sdist[w][t];
+        double dh = d > rmin ? d : rmin;
+        double tt = 1.0 - dh / two_rmax;
+        double t2 = tt * tt, t4 = t2 * t2;
+        nbr[base + rank] = j;
+        f[base + rank] = t4 * t4;
+    }
+}
+
+// Builds the neighbour graph for the elimination. prm: device {two_rmax, rmin}; h_hint: a host
+// estimate of two_rmax used to size the grid cells.
+void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, Temp<int32_t>& rowptr,
+                  Temp<int32_t>& nbr, Temp<double>& f, cudaStream_t s) {
+    DevGrid G;
+    build_grid(x, n, 2 * n, 0.5 * h_hint, G, s);
+    Temp<int32_t> cnt(n + 1, s);
+    Temp<int> err(1, s);
+    CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    radius_k<false><<<grid_for(n, RAD_WARPS), RAD_WARPS * 32, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
+                                                                     x, n, prm, cnt.get(), nullptr, nullptr, nullptr, err.get());
+    CK_LAUNCH();
+    if (read1(err.get(), s)) fail(MGM_ERR_UNSUPPORTED, "elimination neighbour list exceeds 1024 entries");
+    rowptr.alloc(n + 1, s);
+    exclusive_scan_i32(cnt.get(), rowptr.get(), n, s);
+    int64_t nnz = csr_nnz(rowptr.get(), n, s);
+    nbr.alloc(nnz > 0 ? nnz : 1, s);
+    f.alloc(nnz > 0 ? nnz : 1, s);
+    radius_k<true><<<grid_for(n, RAD_WARPS), RAD_WARPS * 32, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
+                                                                    x, n, prm, nullptr, rowptr.get(), nbr.get(), f.get(), err.get());
+    CK_LAUNCH();
+}
+
+}  // namespace mgm

@@ -1,0 +1,348 @@
+// Outer solver (paper Sec. 4.6 and Sec. 5): right-preconditioned flexible GMRES(restart) in FP64
+// with one MGM V-cycle per iteration, or MGM as a standalone iteration (Sec. 5.1).
+//
+// All vectors live on the device in the level-0 solve order (the caller's f and u are permuted
+// once on entry and once on exit). Per iteration: z_k = M v_k (V-cycle, its precision; z_k is
+// stored in that precision, FP32 in the mixed mode), w = L z_k in FP64, classical Gram-Schmidt
+// with one reorthogonalisation (CGS2: two passes of "h = V^T w; w -= V h"), then |w|. The dot
+// products use fixed per-block partial sums and a fixed reduction order, so results repeat
+// exactly from run to run. The (k+1)-vector of coefficients goes to the host, where the Givens
+// rotations and the convergence test run (one synchronisation per iteration). The solution is
+// updated at restarts and at exit, and the true FP64 residual |f - L u| decides convergence.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "hier.cuh"
+
+namespace mgm {
+
+void add_output(mgm_hierarchy* H, double* dst, const int32_t* scatter, cudaStream_t s);
+
+constexpr int KG = 8;            // lanes per row in the FP64 operator
+constexpr int KBLOCK = 256;
+constexpr int DOT_BLOCKS = 304;  // 2 per SM on 152 SMs
+
+template <class TX>
+__device__ __forceinline__ double ldx(const TX* x, int32_t i) { return (double)x[i]; }
+
+// y = f - L x (RESID) or y = L x, L in solve order (split rows, diagonal apart)
+template <bool RESID, class TX>
+__global__ void __launch_bounds__(KBLOCK) spmv64_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ sc,
+                                                   const double* __restrict__ sv, const double* __restrict__ diag,
+                                                   const TX* __restrict__ x, const double* __restrict__ f, double* y,
+                                                   int64_t n) {
+    const int64_t t = (int64_t)blockIdx.x * KBLOCK + threadIdx.x;
+    const int64_t row = t / KG;
+    const int gl = (int)(t & (KG - 1));
+    double acc = 0.0;
+    if (row < n) {
+        const int32_t b = lo[row], e = lo[row + 1];
+        for (int32_t p = b + 4 * gl; p < e; p += 4 * KG) {
+            int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
+            double2 v0 = __ldg(reinterpret_cast<const double2*>(sv + p));
+            double2 v1 = __ldg(reinterpret_cast<const double2*>(sv + p + 2));
+            acc = fma(v0.x, ldx(x, c.x), acc);
+            acc = fma(v0.y, ldx(x, c.y), acc);
+            acc = fma(v1.x, ldx(x, c.z), acc);
+            acc = fma(v1.y, ldx(x, c.w), acc);
+        }
+    }
+    for (int o = KG / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (row < n && gl == 0) {
+        double lx = fma(diag[row], ldx(x, (int32_t)row), acc);
+        y[row] = RESID ? f[row] - lx : lx;
+    }
+}
+
+// partial[b * k1 + t] = sum over block b's chunk of V_t . w
+__global__ void __launch_bounds__(256) multidot_k(const double* __restrict__ V, int64_t ldv, int k1,
+                                                  const double* __restrict__ w, int64_t n, double* partial) {
+    __shared__ double red[8];
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    for (int t = 0; t < k1; ++t) {
+        const double* v = V + (int64_t)t * ldv;
+        double acc = 0.0;
+        for (int64_t i = b0 + threadIdx.x; i < b1; i += 256) acc = fma(v[i], w[i], acc);
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int q = 0; q < 8; ++q) s += red[q];
+            partial[(int64_t)blockIdx.x * k1 + t] = s;
+        }
+        __syncthreads();
+    }
+}
+// h[t] = sum_b partial[b * k1 + t] (one warp per t; fixed order)
+__global__ void reduce_partials_k(const double* partial, int nb, int k1, double* h) {
+    int t = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) acc += partial[(int64_t)b * k1 + t];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) h[t] = acc;
+}
+// w -= V h (k1 vectors)
+__global__ void multiaxpy_k(const double* __restrict__ V, int64_t ldv, int k1, const double* __restrict__ h, double* w,
+                            int64_t n) {
+    __shared__ double sh[256];
+    for (int t = threadIdx.x; t < k1; t += blockDim.x) sh[t] = h[t];
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = w[i];
+    for (int t = 0; t < k1; ++t) acc = fma(-sh[t], V[(int64_t)t * ldv + i], acc);
+    w[i] = acc;
+}
+// x += Z y
+template <class TZ>
+__global__ void update_x_k(const TZ* __restrict__ Z, int64_t ldz, int k, const double* __restrict__ y, double* x, int64_t n) {
+    __shared__ double sy[256];
+    for (int t = threadIdx.x; t < k; t += blockDim.x) sy[t] = y[t];
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = x[i];
+    for (int t = 0; t < k; ++t) acc = fma(sy[t], (double)Z[(int64_t)t * ldz + i], acc);
+    x[i] = acc;
+}
+__global__ void scale_k(const double* a, double s, double* b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i] * s;
+}
+__global__ void gather64_k(const double* in, const int32_t* idx, double* out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[idx[i]];
+}
+__global__ void scatter64_k(const double* in, const int32_t* idx, double* out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[idx[i]] = in[i];
+}
+
+// ------------------------------ host side -------------------------------------------------------
+struct Ops {
+    mgm_hierarchy* H;
+    cudaStream_t s;
+    int64_t n;
+    Level& L0() { return H->lv[0]; }
+
+    template <bool RESID, class TX>
+    void spmv(const TX* x, const double* f, double* y) {
+        Level& L = L0();
+        spmv64_k<RESID, TX><<<grid_for(n * KG, KBLOCK), KBLOCK, 0, s>>>(L.lo.get(), L.sc.get(), L.sv64.get(), L.diag64.get(),
+                                                                       x, f, y, n);
+        CK_LAUNCH();
+    }
+    // h (device, k1 entries) = V[0..k1)^T w
+    void dots(const double* V, int64_t ldv, int k1, const double* w, double* h) {
+        multidot_k<<<DOT_BLOCKS, 256, 0, s>>>(V, ldv, k1, w, n, H->part.get());
+        CK_LAUNCH();
+        reduce_partials_k<<<k1, 32, 0, s>>>(H->part.get(), DOT_BLOCKS, k1, h);
+        CK_LAUNCH();
+    }
+    void axpys(const double* V, int64_t ldv, int k1, const double* h, double* w) {
+        multiaxpy_k<<<grid_for(n, 256), 256, 0, s>>>(V, ldv, k1, h, w, n);
+        CK_LAUNCH();
+    }
+    double norm(const double* w) {
+        dots(w, n, 1, w, H->hbuf.get());
+        double v = read1(H->hbuf.get(), s);
+        return std::sqrt(v);
+    }
+};
+
+static void ensure_workspace(mgm_hierarchy* H, int m) {
+    const int64_t n = H->N;
+    if (H->krylov_m >= m && H->V.get()) return;
+    H->V.alloc((int64_t)(m + 1) * n);
+    if (H->precision == MGM_F32) H->Z32.alloc((int64_t)m * n);
+    else H->Z64.alloc((int64_t)m * n);
+    H->f.alloc(n); H->u.alloc(n); H->w.alloc(n); H->r.alloc(n);
+    H->part.alloc((int64_t)DOT_BLOCKS * (2 * (m + 1) + 2));
+    H->hbuf.alloc(2 * (m + 2) + 2);
+    H->ydev.alloc(m + 1);
+    if (H->hhost) cudaFreeHost(H->hhost);
+    H->hhost = nullptr;
+    CK(cudaMallocHost((void**)&H->hhost, sizeof(double) * (2 * (m + 2) + 2)));
+    H->krylov_m = m;
+}
+
+// times the FP64 operator application w = L z of the outer iteration (z in the V-cycle precision)
+void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s) {
+    ensure_workspace(H, std::max(H->krylov_m, 1));
+    const int64_t n = H->N;
+    Ops op{H, s, n};
+    Level& L = H->lv[0];
+    const bool f32 = H->precision == MGM_F32;
+    if (f32) CK(cudaMemsetAsync(H->Z32.get(), 0, sizeof(float) * n, s));
+    else CK(cudaMemsetAsync(H->Z64.get(), 0, sizeof(double) * n, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int t = 0; t < reps + 2; ++t) {
+        if (t == 2) CK(cudaEventRecord(e0, s));
+        if (f32) op.spmv<false, float>(H->Z32.get(), nullptr, H->w.get());
+        else op.spmv<false, double>(H->Z64.get(), nullptr, H->w.get());
+    }
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    out->spmv_ms = ms / reps;
+    out->spmv_bytes = (L.nlow + L.nupp) * 12 + n * (4 + 8 + 8 + (f32 ? 4 : 8));
+}
+
+void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_params* sp, mgm_solve_info* info,
+           cudaStream_t s) {
+    REQUIRE(H && f_in && u_io && sp, "null argument");
+    REQUIRE(sp->krylov == MGM_KRYLOV_FGMRES || sp->krylov == MGM_KRYLOV_NONE, "unknown krylov method");
+    REQUIRE(sp->maxit >= 0 && sp->tol >= 0.0, "maxit and tol must be >= 0");
+    REQUIRE(sp->krylov != MGM_KRYLOV_FGMRES || (sp->restart >= 1 && sp->restart <= 200), "restart must be in [1, 200]");
+    const int m = sp->krylov == MGM_KRYLOV_FGMRES ? sp->restart : 1;
+    ensure_workspace(H, m);
+    vcycle_prepare(H);
+    const int64_t n = H->N;
+    Ops op{H, s, n};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    const int32_t* ordc = H->ord_caller.get();
+    gather64_k<<<grid_for(n, 256), 256, 0, s>>>(f_in, ordc, H->f.get(), n);
+    CK_LAUNCH();
+    gather64_k<<<grid_for(n, 256), 256, 0, s>>>(u_io, ordc, H->u.get(), n);
+    CK_LAUNCH();
+    double fn = op.norm(H->f.get());
+    if (!std::isfinite(fn)) fail(MGM_ERR_INVALID_ARG, "right-hand side is not finite");
+    if (fn == 0.0) fn = 1.0;
+    std::vector<double> hist;
+    int it = 0;
+    double rel = 0.0;
+    mgm_status status = MGM_ERR_NOT_CONVERGED;
+    const bool f32 = H->precision == MGM_F32;
+    if (sp->krylov == MGM_KRYLOV_NONE) {
+        for (;;) {
+            op.spmv<true, double>(H->u.get(), H->f.get(), H->r.get());
+            rel = op.norm(H->r.get()) / fn;
+            hist.push_back(rel);
+            if (!std::isfinite(rel)) { status = MGM_ERR_BREAKDOWN; break; }
+            if (rel <= sp->tol) { status = MGM_OK; break; }
+            if (it >= sp->maxit) break;
+            load_input(H, H->r.get(), MGM_F64, nullptr, s);
+            vcycle_core(H, s);
+            add_output(H, H->u.get(), nullptr, s);
+            ++it;
+        }
+    } else {
+        std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+        double* V = H->V.get();
+        for (;;) {
+            op.spmv<true, double>(H->u.get(), H->f.get(), V);
+            double beta = op.norm(V);
+            rel = beta / fn;
+            if (hist.empty()) hist.push_back(rel);
+            if (!std::isfinite(rel)) { status = MGM_ERR_BREAKDOWN; break; }
+            if (rel <= sp->tol) { status = MGM_OK; break; }
+            if (it >= sp->maxit) break;
+            scale_k<<<grid_for(n, 256), 256, 0, s>>>(V, 1.0 / beta, V, n);
+            CK_LAUNCH();
+            std::fill(g.begin(), g.end(), 0.0);
+            g[0] = beta;
+            int k = 0;
+            bool stop = false;
+            for (; k < m && it < sp->maxit; ++k) {
+                double* vk = V + (int64_t)k * n;
+                double* w = H->w.get();
+                load_input(H, vk, MGM_F64, nullptr, s);
+                vcycle_core(H, s);
+                if (f32) {
+                    float* zk = H->Z32.get() + (int64_t)k * n;
+                    store_output(H, zk, MGM_F32, nullptr, s);
+                    op.spmv<false, float>(zk, nullptr, w);
+                } else {
+                    double* zk = H->Z64.get() + (int64_t)k * n;
+                    store_output(H, zk, MGM_F64, nullptr, s);
+                    op.spmv<false, double>(zk, nullptr, w);
+                }
+                const int k1 = k + 1;
+                double* h1 = H->hbuf.get();
+                double* h2 = h1 + (m + 1);
+                double* hn2 = h2 + (m + 1);
+                op.dots(V, n, k1, w, h1);
+                op.axpys(V, n, k1, h1, w);
+                op.dots(V, n, k1, w, h2);
+                op.axpys(V, n, k1, h2, w);
+                op.dots(w, n, 1, w, hn2);
+                CK(cudaMemcpyAsync(H->hhost, H->hbuf.get(), sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                const double* hh = H->hhost;
+                for (int i = 0; i < k1; ++i) Hm[(size_t)i * m + k] = hh[i] + hh[(m + 1) + i];
+                double hn = std::sqrt(hh[2 * (m + 1)]);
+                Hm[(size_t)k1 * m + k] = hn;
+                if (!std::isfinite(hn)) { status = MGM_ERR_BREAKDOWN; stop = true; break; }
+                if (hn > 0.0 && k1 < m + 1) {
+                    scale_k<<<grid_for(n, 256), 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)k1 * n, n);
+                    CK_LAUNCH();
+                }
+                for (int i = 0; i < k; ++i) {
+                    double a = Hm[(size_t)i * m + k], b = Hm[(size_t)(i + 1) * m + k];
+                    Hm[(size_t)i * m + k] = cs[i] * a + sn[i] * b;
+                    Hm[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
+                }
+                double a = Hm[(size_t)k * m + k], b = Hm[(size_t)k1 * m + k];
+                double rr = std::sqrt(a * a + b * b);
+                cs[k] = rr == 0.0 ? 1.0 : a / rr;
+                sn[k] = rr == 0.0 ? 0.0 : b / rr;
+                Hm[(size_t)k * m + k] = rr;
+                Hm[(size_t)k1 * m + k] = 0.0;
+                g[k1] = -sn[k] * g[k];
+                g[k] = cs[k] * g[k];
+                ++it;
+                double est = std::fabs(g[k1]) / fn;
+                hist.push_back(est);
+                if (est <= sp->tol || hn == 0.0) { ++k; break; }
+            }
+            if (stop) break;
+            for (int i = k - 1; i >= 0; --i) {
+                double acc = g[i];
+                for (int j = i + 1; j < k; ++j) acc -= Hm[(size_t)i * m + j] * y[j];
+                y[i] = acc / Hm[(size_t)i * m + i];
+            }
+            if (k > 0) {
+                CK(cudaMemcpyAsync(H->ydev.get(), y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+                if (f32) update_x_k<float><<<grid_for(n, 256), 256, 0, s>>>(H->Z32.get(), n, k, H->ydev.get(), H->u.get(), n);
+                else update_x_k<double><<<grid_for(n, 256), 256, 0, s>>>(H->Z64.get(), n, k, H->ydev.get(), H->u.get(), n);
+                CK_LAUNCH();
+                CK(cudaStreamSynchronize(s));  // y is pageable host memory
+            }
+        }
+    }
+    scatter64_k<<<grid_for(n, 256), 256, 0, s>>>(H->u.get(), ordc, u_io, n);
+    CK_LAUNCH();
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+        info->iters = it;
+        info->rel_res = rel;
+        info->solve_ms = ms;
+        if (info->history && info->history_len > 0)
+            for (int i = 0; i < info->history_len; ++i) info->history[i] = i < (int)hist.size() ? hist[i] : 0.0;
+    }
+    if (status != MGM_OK) {
+        if (status == MGM_ERR_NOT_CONVERGED)
+            set_error("not converged: relative residual " + std::to_string(rel) + " after " + std::to_string(it) + " iterations");
+        else
+            set_error("breakdown: non-finite value in the iteration");
+        throw Fail{status};
+    }
+}
+
+}  // namespace mgm

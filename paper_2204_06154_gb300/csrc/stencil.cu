@@ -1,0 +1,389 @@
+// Tangent-plane stencil weights for the Laplace-Beltrami operator (paper Sec. 2) and global
+// assembly of L = I - mu D (Sec. 2, eq. (discrete_system)).
+//
+// PHS RBF-FD (Sec. 2.2, eq. (rbf_fd_lap)): one warp per stencil. The (n+L) x (n+L+1) augmented
+// saddle matrix lives in shared memory; Gaussian elimination with partial pivoting runs with the
+// warp's lanes spread over the trailing submatrix; every entry receives the same sequence of IEEE
+// operations (fused multiply-adds where the update is a_ij - l_i a_kj) as a sequential
+// elimination, so the weights do not depend on the parallel schedule. The work is FP64-pipe bound
+// (GB300: ~0.6 TFMA/s FP64), so shared-memory staging per warp, not occupancy, is what matters.
+//
+// GFD (Sec. 2.3, eq. (wls_fd_lap)): one thread per stencil, Householder QR of W^{1/2} P.
+// This file is compiled with --fmad=false: no multiply-add is contracted unless written as fma().
+#include <climits>
+
+#include "common.cuh"
+
+namespace mgm {
+
+constexpr int MAX_M = 128;
+
+__device__ __forceinline__ double dot3d(const double* a, const double* b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+
+// Sec. 2.1: orthonormal t1, t2 of T_x M; t1 from the coordinate axis of smallest |n_a| (first on ties)
+__device__ void tangent_basis(const double* nin, double* t1, double* t2) {
+    double nn = sqrt((nin[0] * nin[0] + nin[1] * nin[1]) + nin[2] * nin[2]);
+    double n[3] = {nin[0] / nn, nin[1] / nn, nin[2] / nn};
+    int a = 0;
+    if (fabs(n[1]) < fabs(n[a])) a = 1;
+    if (fabs(n[2]) < fabs(n[a])) a = 2;
+    double v[3] = {-n[a] * n[0], -n[a] * n[1], -n[a] * n[2]};
+    v[a] = 1.0 + v[a];
+    double vn = sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+    t1[0] = v[0] / vn; t1[1] = v[1] / vn; t1[2] = v[2] / vn;
+    t2[0] = n[1] * t1[2] - n[2] * t1[1];
+    t2[1] = n[2] * t1[0] - n[0] * t1[2];
+    t2[2] = n[0] * t1[1] - n[1] * t1[0];
+}
+
+__device__ __forceinline__ double monomial(double x, double y, int a, int b) {
+    double p = 1.0;
+    for (int t = 0; t < a; ++t) p = p * x;
+    for (int t = 0; t < b; ++t) p = p * y;
+    return p;
+}
+// phi(r) = r^(2k+1) from r^2
+__device__ __forceinline__ double phs(double r2, int k) {
+    double p = 1.0;
+    for (int t = 0; t < k; ++t) p = p * r2;
+    return sqrt(r2) * p;
+}
+// 2-D Laplacian of phi(|x - c|) at x = 0: (2k+1)^2 |c|^(2k-1)
+__device__ __forceinline__ double phs_lap(double r2, int k) {
+    if (r2 == 0.0) return 0.0;
+    double p = 1.0;
+    for (int t = 0; t < k - 1; ++t) p = p * r2;
+    double c = (double)((2 * k + 1) * (2 * k + 1));
+    return c * (sqrt(r2) * p);
+}
+// monomial powers: total degree ascending, then descending power of x
+__device__ __forceinline__ void mono_pow(int t, int* a, int* b) {
+    int d = 0;
+    while ((d + 1) * (d + 2) / 2 <= t) ++d;
+    int off = t - d * (d + 1) / 2;
+    *a = d - off;
+    *b = off;
+}
+
+struct PhsArgs {
+    const double* xyz;
+    const double* nrm;
+    const int32_t* idx;
+    int64_t N;
+    int n, k, ell, L, m;
+    double* w;
+    unsigned long long* bad;  // lowest singular row
+};
+
+__global__ void phs_weights_k(PhsArgs a, int wpb) {
+    extern __shared__ __align__(16) double sm_phs[];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int n = a.n, m = a.m, ld = m + 1;
+    const size_t per = (size_t)m * ld + 2 * n + m;
+    double* A = sm_phs + per * wi;
+    double* xh = A + (size_t)m * ld;
+    double* yh = xh + n;
+    double* xs = yh + n;
+    const int64_t i = (int64_t)blockIdx.x * wpb + wi;
+    if (i >= a.N) return;
+    const int32_t* id = a.idx + i * n;
+    double t1[3], t2[3];
+    tangent_basis(a.nrm + 3 * i, t1, t2);
+    const double* xc = a.xyz + 3 * i;
+    // eq. (tp_pts): projected coordinates and support radius s
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        const double* xj = a.xyz + 3 * (int64_t)id[j];
+        double d[3] = {xj[0] - xc[0], xj[1] - xc[1], xj[2] - xc[2]};
+        double u = dot3d(t1, d), v = dot3d(t2, d);
+        xh[j] = u;
+        yh[j] = v;
+        double r = sqrt(u * u + v * v);
+        s = fmax(s, r);
+    }
+    s = warp_max_d(s);
+    if (!(s > 0.0)) {
+        if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
+        return;
+    }
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) { xh[j] = xh[j] / s; yh[j] = yh[j] / s; }
+    __syncwarp();
+    // saddle matrix [A P; P^T 0 | rhs]
+    double amax = 0.0;
+    for (int e = lane; e < m * ld; e += 32) {
+        int r = e / ld, c = e - r * ld;
+        double v;
+        if (r < n) {
+            if (c < n) {
+                double dx = xh[r] - xh[c], dy = yh[r] - yh[c];
+                v = phs(dx * dx + dy * dy, a.k);
+            } else if (c < m) {
+                int pa, pb;
+                mono_pow(c - n, &pa, &pb);
+                v = monomial(xh[r], yh[r], pa, pb);
+            } else {
+                v = phs_lap(xh[r] * xh[r] + yh[r] * yh[r], a.k);
+            }
+        } else {
+            int pa, pb;
+            mono_pow(r - n, &pa, &pb);
+            if (c < n) v = monomial(xh[c], yh[c], pa, pb);
+            else if (c < m) v = 0.0;
+            else v = ((pa == 2 && pb == 0) || (pa == 0 && pb == 2)) ? 2.0 : 0.0;
+        }
+        A[e] = v;
+        if (c < m) amax = fmax(amax, fabs(v));
+    }
+    amax = warp_max_d(amax);
+    const double tol = 1e-13 * amax;
+    __syncwarp();
+    // Gaussian elimination with partial pivoting (first row of maximal |a_ik|)
+    for (int kk = 0; kk < m; ++kk) {
+        double best = -1.0;
+        int piv = kk;
+        for (int r = kk + lane; r < m; r += 32) {
+            double v = fabs(A[r * ld + kk]);
+            if (v > best) { best = v; piv = r; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            int op = __shfl_xor_sync(0xffffffffu, piv, o);
+            if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+        }
+        if (!(best > tol)) {
+            if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
+            return;
+        }
+        if (piv != kk)
+            for (int j = lane; j < ld; j += 32) {
+                double t = A[kk * ld + j];
+                A[kk * ld + j] = A[piv * ld + j];
+                A[piv * ld + j] = t;
+            }
+        __syncwarp();
+        const double akk = A[kk * ld + kk];
+        for (int r = kk + 1 + lane; r < m; r += 32) A[r * ld + kk] = A[r * ld + kk] / akk;  // multiplier l_r
+        __syncwarp();
+        const int R = m - kk - 1, C = m - kk;  // rows kk+1..m-1, columns kk+1..m
+        int rr = lane / C, cc = lane - (lane / C) * C;
+        for (int e = lane; e < R * C; e += 32) {
+            int r = kk + 1 + rr, c = kk + 1 + cc;
+            A[r * ld + c] = fma(-A[r * ld + kk], A[kk * ld + c], A[r * ld + c]);
+            cc += 32;
+            while (cc >= C) { cc -= C; ++rr; }
+        }
+        __syncwarp();
+    }
+    // back substitution, column oriented
+    bool finite = true;
+    for (int kk = m - 1; kk >= 0; --kk) {
+        double xk = A[kk * ld + m] / A[kk * ld + kk];
+        finite = finite && isfinite(xk);
+        if (lane == 0) xs[kk] = xk;
+        for (int r = lane; r < kk; r += 32) A[r * ld + m] = fma(-A[r * ld + kk], xk, A[r * ld + m]);
+        __syncwarp();
+    }
+    if (!finite) {
+        if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
+        return;
+    }
+    __syncwarp();
+    const double s2 = s * s;
+    for (int j = lane; j < n; j += 32) a.w[i * n + j] = xs[j] / s2;
+}
+
+// ---------------------------------------------------------------------------------------------
+// GFD: support radii, then weighted least squares per stencil (thread per stencil)
+// ---------------------------------------------------------------------------------------------
+constexpr int GFD_MAXN = 48;
+constexpr int GFD_MAXL = 10;
+
+__device__ double project_support(const double* xyz, const double* nrm, int64_t i, const int32_t* id, int n,
+                                  double* xh, double* yh) {
+    double t1[3], t2[3];
+    tangent_basis(nrm + 3 * i, t1, t2);
+    const double* xc = xyz + 3 * i;
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double* xj = xyz + 3 * (int64_t)id[j];
+        double d[3] = {xj[0] - xc[0], xj[1] - xc[1], xj[2] - xc[2]};
+        double u = dot3d(t1, d), v = dot3d(t2, d);
+        if (xh) { xh[j] = u; yh[j] = v; }
+        double r = sqrt(u * u + v * v);
+        if (r > s) s = r;
+    }
+    return s;
+}
+
+__global__ void gfd_rho_k(const double* xyz, const double* nrm, const int32_t* idx, int64_t N, int n, double* rho) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    rho[i] = project_support(xyz, nrm, i, idx + i * n, n, nullptr, nullptr);
+}
+
+__global__ void gfd_weights_k(const double* xyz, const double* nrm, const int32_t* idx, const double* rho, int64_t N, int n,
+                              int ell, int L, double alpha, double* w, unsigned long long* bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double xh[GFD_MAXN], yh[GFD_MAXN], sw[GFD_MAXN], z[GFD_MAXN];
+    double B[GFD_MAXN * GFD_MAXL], V[GFD_MAXN * GFD_MAXL], y[GFD_MAXL], beta[GFD_MAXL];
+    int pa[GFD_MAXL], pb[GFD_MAXL];
+    for (int t = 0; t < L; ++t) mono_pow(t, &pa[t], &pb[t]);
+    const int32_t* id = idx + i * n;
+    double s = project_support(xyz, nrm, i, id, n, xh, yh);
+    if (!(s > 0.0)) { atomicMin(bad, (unsigned long long)i); return; }
+    const double ri = rho[i];
+    for (int j = 0; j < n; ++j) {
+        double r2 = xh[j] * xh[j] + yh[j] * yh[j];
+        double rj = rho[id[j]];
+        sw[j] = sqrt(exp(-alpha * r2 / (ri * ri + rj * rj)));
+        xh[j] = xh[j] / s;
+        yh[j] = yh[j] / s;
+    }
+    for (int j = 0; j < n; ++j)
+        for (int c = 0; c < L; ++c) B[j * L + c] = sw[j] * monomial(xh[j], yh[j], pa[c], pb[c]);
+    for (int kk = 0; kk < L; ++kk) {
+        double nrm2 = 0.0;
+        for (int r = kk; r < n; ++r) nrm2 = nrm2 + B[r * L + kk] * B[r * L + kk];
+        double nx = sqrt(nrm2);
+        if (!(nx > 0.0)) { atomicMin(bad, (unsigned long long)i); return; }
+        double alp = B[kk * L + kk] >= 0.0 ? -nx : nx;
+        for (int r = 0; r < n; ++r) V[r * L + kk] = (r < kk) ? 0.0 : B[r * L + kk];
+        V[kk * L + kk] = V[kk * L + kk] - alp;
+        double vv = 0.0;
+        for (int r = kk; r < n; ++r) vv = vv + V[r * L + kk] * V[r * L + kk];
+        beta[kk] = 2.0 / vv;
+        for (int c = kk; c < L; ++c) {
+            double dv = 0.0;
+            for (int r = kk; r < n; ++r) dv = dv + V[r * L + kk] * B[r * L + c];
+            double f = beta[kk] * dv;
+            for (int r = kk; r < n; ++r) B[r * L + c] = B[r * L + c] - f * V[r * L + kk];
+        }
+    }
+    double rmax = 0.0;
+    for (int c = 0; c < L; ++c) rmax = fmax(rmax, fabs(B[c * L + c]));
+    for (int r = 0; r < L; ++r) {
+        double rhs = ((pa[r] == 2 && pb[r] == 0) || (pa[r] == 0 && pb[r] == 2)) ? 2.0 : 0.0;
+        for (int c = 0; c < r; ++c) rhs = rhs - B[c * L + r] * y[c];
+        if (!(fabs(B[r * L + r]) > 1e-13 * rmax)) { atomicMin(bad, (unsigned long long)i); return; }
+        y[r] = rhs / B[r * L + r];
+    }
+    for (int r = 0; r < n; ++r) z[r] = r < L ? y[r] : 0.0;
+    for (int kk = L - 1; kk >= 0; --kk) {
+        double dv = 0.0;
+        for (int r = kk; r < n; ++r) dv = dv + V[r * L + kk] * z[r];
+        double f = beta[kk] * dv;
+        for (int r = kk; r < n; ++r) z[r] = z[r] - f * V[r * L + kk];
+    }
+    double s2 = s * s;
+    for (int j = 0; j < n; ++j) w[i * n + j] = (sw[j] * z[j]) / s2;
+}
+
+// ---------------------------------------------------------------------------------------------
+// assembly: one thread per row, columns sorted by insertion (rows are n long)
+// ---------------------------------------------------------------------------------------------
+__global__ void assemble_k(int64_t N, int n, const int32_t* idx, const double* w, double mu, int poisson, int32_t* rp,
+                           int32_t* col, double* val, int* dup) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > N) return;
+    rp[i] = (int32_t)(i * n);
+    if (i == N) return;
+    int32_t* c = col + i * n;
+    double* v = val + i * n;
+    for (int j = 0; j < n; ++j) {
+        int32_t cj = idx[i * n + j];
+        double wj = w[i * n + j];
+        double vj;
+        if (poisson) vj = wj;
+        else {
+            double t = mu * wj;
+            vj = (cj == i) ? 1.0 - t : -t;
+        }
+        int p = j;
+        while (p > 0 && c[p - 1] > cj) { c[p] = c[p - 1]; v[p] = v[p - 1]; --p; }
+        c[p] = cj;
+        v[p] = vj;
+    }
+    for (int j = 1; j < n; ++j)
+        if (c[j] == c[j - 1]) atomicOr(dup, 1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host entry points
+// ---------------------------------------------------------------------------------------------
+static void check_bad(unsigned long long* bad, cudaStream_t s, const char* what) {
+    unsigned long long b = read1(bad, s);
+    if (b != ULLONG_MAX) {
+        set_bad_row((int64_t)b);
+        fail(MGM_ERR_SINGULAR_STENCIL, std::string(what) + ": singular local system at row " + std::to_string(b));
+    }
+}
+
+void stencil_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, const mgm_stencil_params* sp,
+                     double* w, cudaStream_t s) {
+    REQUIRE(sp != nullptr, "null stencil params");
+    REQUIRE(N >= 1 && N < 0x7fffffff, "N out of range");
+    REQUIRE(xyz && nrm && idx && w, "null array");
+    const int n = sp->n, ell = sp->ell;
+    REQUIRE(ell >= 0 && ell <= 12, "ell out of range");
+    const int L = (ell + 1) * (ell + 2) / 2;
+    REQUIRE(n >= 1 && n <= N && L <= n, "stencil size n must satisfy (ell+1)(ell+2)/2 <= n <= N");
+    set_bad_row(-1);
+    Temp<unsigned long long> bad(1, s);
+    CK(cudaMemsetAsync(bad.get(), 0xff, sizeof(unsigned long long), s));
+    if (sp->method == MGM_RBF_FD) {
+        REQUIRE(sp->k >= 1 && sp->k <= 8, "PHS order k must be in [1, 8]");
+        const int m = n + L;
+        if (m > MAX_M) fail(MGM_ERR_UNSUPPORTED, "n + (ell+1)(ell+2)/2 must be <= 128");
+        const size_t per = sizeof(double) * ((size_t)m * (m + 1) + 2 * n + m);
+        int wpb = (int)std::min<size_t>(4, (200 * 1024) / per);
+        if (wpb < 1) wpb = 1;
+        const size_t smem = per * wpb;
+        CK(cudaFuncSetAttribute(phs_weights_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PhsArgs a{xyz, nrm, idx, N, n, sp->k, ell, L, m, w, bad.get()};
+        phs_weights_k<<<grid_for(N, wpb), 32 * wpb, smem, s>>>(a, wpb);
+        CK_LAUNCH();
+        check_bad(bad.get(), s, "PHS weights");
+    } else if (sp->method == MGM_GFD) {
+        REQUIRE(sp->alpha > 0.0, "GFD alpha must be > 0");
+        if (n > GFD_MAXN || L > GFD_MAXL) fail(MGM_ERR_UNSUPPORTED, "GFD supports n <= 48 and ell <= 3");
+        Temp<double> rho(N, s);
+        gfd_rho_k<<<grid_for(N, 128), 128, 0, s>>>(xyz, nrm, idx, N, n, rho.get());
+        CK_LAUNCH();
+        gfd_weights_k<<<grid_for(N, 64), 64, 0, s>>>(xyz, nrm, idx, rho.get(), N, n, ell, L, sp->alpha, w, bad.get());
+        CK_LAUNCH();
+        check_bad(bad.get(), s, "GFD weights");
+    } else {
+        fail(MGM_ERR_INVALID_ARG, "unknown discretisation method");
+    }
+}
+
+void assemble(int64_t N, int n, const int32_t* idx, const double* w, double mu, int poisson, int32_t* rp, int32_t* col,
+              double* val, cudaStream_t s) {
+    REQUIRE(N >= 1 && n >= 1 && N * (int64_t)n < 0x7fffffff, "sizes out of range");
+    REQUIRE(idx && w && rp && col && val, "null array");
+    Temp<int> dup(1, s);
+    CK(cudaMemsetAsync(dup.get(), 0, sizeof(int), s));
+    assemble_k<<<grid_for(N + 1, 128), 128, 0, s>>>(N, n, idx, w, mu, poisson, rp, col, val, dup.get());
+    CK_LAUNCH();
+    if (read1(dup.get(), s)) fail(MGM_ERR_INVALID_ARG, "a stencil lists the same node twice");
+}
+
+void build_stencils(const double* xyz, const double* nrm, int64_t N, const mgm_stencil_params* sp, int32_t* idx_out,
+                    double* w_out, int32_t* rp, int32_t* col, double* val, cudaStream_t s) {
+    REQUIRE(sp != nullptr, "null stencil params");
+    REQUIRE(N >= 1 && sp->n >= 1 && sp->n <= N, "n must be in [1, N]");
+    const int n = sp->n;
+    Temp<int32_t> idx_t;
+    Temp<double> w_t;
+    int32_t* idx = idx_out;
+    double* w = w_out;
+    if (!idx) { idx_t.alloc((size_t)N * n, s); idx = idx_t.get(); }
+    if (!w) { w_t.alloc((size_t)N * n, s); w = w_t.get(); }
+    knn_device(xyz, N, xyz, N, n, 1, idx, nullptr, s);
+    stencil_weights(xyz, nrm, N, idx, sp, w, s);
+    assemble(N, n, idx, w, sp->mu, sp->poisson, rp, col, val, s);
+}
+
+}  // namespace mgm

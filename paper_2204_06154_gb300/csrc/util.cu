@@ -1,0 +1,363 @@
+// Device-wide building blocks for the setup phase: scans, permutations, CSR transpose and
+// permutation, the symmetrised pattern used by RCM and colouring. Every output is deterministic
+// (independent of thread scheduling): where atomics place entries, the rows are sorted afterwards.
+#include <atomic>
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace mgm {
+
+// ---------------------------------------------------------------------------------------------
+// error state
+// ---------------------------------------------------------------------------------------------
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+static thread_local std::string g_msg;
+static thread_local int64_t g_row = -1;
+void set_error(const std::string& msg) { g_msg = msg; }
+void set_bad_row(int64_t row) { g_row = row; }
+const char* error_message() { return g_msg.c_str(); }
+int64_t bad_row() { return g_row; }
+void fail(mgm_status st, const std::string& msg) {
+    set_error(msg);
+    throw Fail{st};
+}
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+    if (e == cudaSuccess) return;
+    (void)cudaGetLastError();
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    if (e == cudaErrorMemoryAllocation) fail(MGM_ERR_OOM, buf);
+    fail(MGM_ERR_CUDA, buf);
+}
+
+// ---------------------------------------------------------------------------------------------
+// scans: block-level scan of 1024 items per block, then a scan of block totals (recursive)
+// ---------------------------------------------------------------------------------------------
+constexpr int SCAN_BLOCK = 512;
+constexpr int SCAN_ITEMS = 2;  // per thread
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+template <class T>
+__device__ T block_exclusive_scan(T v, T* smem, T* total) {
+    // smem: SCAN_BLOCK/32 entries
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < SCAN_BLOCK / 32 ? smem[lane] : T(0);
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < SCAN_BLOCK / 32) smem[lane] = t;
+    }
+    __syncthreads();
+    T before = (w > 0 ? smem[w - 1] : T(0)) + x - v;
+    if (total) *total = smem[SCAN_BLOCK / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+template <class T>
+__global__ void scan_tiles(const T* in, T* out, int64_t n, T* tile_sums) {
+    __shared__ T sm[SCAN_BLOCK / 32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    T v[SCAN_ITEMS];
+    T local = 0;
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+        int64_t i = base + t;
+        v[t] = i < n ? in[i] : T(0);
+        local += v[t];
+    }
+    T total;
+    T pre = block_exclusive_scan<T>(local, sm, &total);
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+        int64_t i = base + t;
+        if (i < n) out[i] = pre;
+        pre += v[t];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+template <class T>
+__global__ void scan_add(T* out, int64_t n, const T* tile_prefix, T* total_out) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    T add = tile_prefix[blockIdx.x];
+    for (int t = threadIdx.x; t < SCAN_TILE; t += blockDim.x) {
+        int64_t i = base + t;
+        if (i < n) out[i] += add;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total_out = tile_prefix[gridDim.x];
+}
+
+template <class T>
+static void exclusive_scan_impl(const T* in, T* out, int64_t n, cudaStream_t s) {
+    // out has n+1 entries; out[n] = total
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles < 1) tiles = 1;
+    Temp<T> sums(tiles + 1, s);
+    scan_tiles<T><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(in, out, n, sums.get());
+    CK_LAUNCH();
+    // exclusive scan of tile sums (recursive), written in place, with total at [tiles]
+    if (tiles == 1) {
+        Temp<T> tmp(2, s);
+        scan_tiles<T><<<1, SCAN_BLOCK, 0, s>>>(sums.get(), sums.get(), 1, tmp.get());
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(sums.get() + 1, tmp.get(), sizeof(T), cudaMemcpyDeviceToDevice, s));
+    } else {
+        exclusive_scan_impl<T>(sums.get(), sums.get(), tiles, s);
+    }
+    scan_add<T><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(out, n, sums.get(), out + n);
+    CK_LAUNCH();
+}
+
+__global__ void check_i32_total(const int64_t* t64, int32_t* out, int* overflow) {
+    int64_t t = *t64;
+    if (t > 0x7fffffffLL) *overflow = 1;
+    *out = (int32_t)t;
+}
+__global__ void widen_i32(const int32_t* in, int64_t* out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
+}
+__global__ void narrow_i64(const int64_t* in, int32_t* out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) out[i] = (int32_t)in[i];
+}
+
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+    exclusive_scan_impl<int64_t>(in, out, n, s);
+}
+
+void exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s) {
+    // scan in int64 so the total cannot wrap, then check and narrow
+    Temp<int64_t> w(n + 1, s);
+    widen_i32<<<grid_for(n, 256), 256, 0, s>>>(in, w.get(), n);
+    CK_LAUNCH();
+    exclusive_scan_impl<int64_t>(w.get(), w.get(), n, s);
+    int64_t total = read1(w.get() + n, s);
+    if (total > 0x7fffffffLL) fail(MGM_ERR_UNSUPPORTED, "index total exceeds int32 range");
+    narrow_i64<<<grid_for(n + 1, 256), 256, 0, s>>>(w.get(), out, n);
+    CK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------------------------
+// small element-wise helpers
+// ---------------------------------------------------------------------------------------------
+__global__ void fill_k(int32_t* p, int32_t v, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+__global__ void iota_k(int32_t* p, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (int32_t)i;
+}
+__global__ void invert_k(const int32_t* perm, int32_t* inv, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) inv[perm[i]] = (int32_t)i;
+}
+__global__ void gather_xyz_k(const double* in, const int32_t* idx, double* out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        int64_t j = idx[i];
+        out[3 * i] = in[3 * j];
+        out[3 * i + 1] = in[3 * j + 1];
+        out[3 * i + 2] = in[3 * j + 2];
+    }
+}
+void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    fill_k<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+    CK_LAUNCH();
+}
+void iota_i32(int32_t* p, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    iota_k<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+    CK_LAUNCH();
+}
+void invert_perm(const int32_t* perm, int32_t* inv, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    invert_k<<<grid_for(n, 256), 256, 0, s>>>(perm, inv, n);
+    CK_LAUNCH();
+}
+void gather_xyz(const double* in, const int32_t* idx, double* out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    gather_xyz_k<<<grid_for(n, 256), 256, 0, s>>>(in, idx, out, n);
+    CK_LAUNCH();
+}
+
+int64_t csr_nnz(const int32_t* rp, int64_t nrows, cudaStream_t s) { return (int64_t)read1(rp + nrows, s); }
+
+// ---------------------------------------------------------------------------------------------
+// validation of caller-supplied index data (so that bad input is an error, not a bad access)
+// ---------------------------------------------------------------------------------------------
+__global__ void check_rowptr_k(const int32_t* rp, int64_t n, int* err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && rp[0] != 0) atomicOr(err, 1);
+    if (i < n && rp[i + 1] < rp[i]) atomicOr(err, 1);
+}
+__global__ void check_range_k(const int32_t* a, int64_t cnt, int64_t hi, int* err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt && (a[i] < 0 || (int64_t)a[i] >= hi)) atomicOr(err, 2);
+}
+void validate_index(const int32_t* a, int64_t cnt, int64_t hi, const char* what, cudaStream_t s) {
+    if (cnt <= 0) return;
+    Temp<int> err(1, s);
+    CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    check_range_k<<<grid_for(cnt, 256), 256, 0, s>>>(a, cnt, hi, err.get());
+    CK_LAUNCH();
+    if (read1(err.get(), s)) fail(MGM_ERR_INVALID_ARG, std::string(what) + ": index out of range");
+}
+void validate_csr(int64_t nrows, int64_t ncols, const int32_t* rp, const int32_t* ci, const char* what, cudaStream_t s) {
+    Temp<int> err(1, s);
+    CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    check_rowptr_k<<<grid_for(nrows + 1, 256), 256, 0, s>>>(rp, nrows, err.get());
+    CK_LAUNCH();
+    if (read1(err.get(), s)) fail(MGM_ERR_INVALID_ARG, std::string(what) + ": row pointers must start at 0 and not decrease");
+    validate_index(ci, csr_nnz(rp, nrows, s), ncols, what, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// CSR transpose: count per column, scan, place with atomics, then sort each row by source row
+// ---------------------------------------------------------------------------------------------
+__global__ void count_cols_k(const int32_t* rp, const int32_t* ci, int64_t nrows, int32_t* cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) atomicAdd(&cnt[ci[p]], 1);
+}
+__global__ void place_t_k(const int32_t* rp, const int32_t* ci, const double* v, int64_t nrows, const int32_t* trp,
+                          int32_t* fill, int32_t* tci, double* tv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int32_t c = ci[p];
+        int32_t q = trp[c] + atomicAdd(&fill[c], 1);
+        tci[q] = (int32_t)i;
+        if (v) tv[q] = v[p];
+    }
+}
+// sort each row's (col, val) by col, insertion sort (rows are short in every use here)
+__global__ void sort_rows_k(const int32_t* rp, int32_t* ci, double* v, int64_t nrows) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    int32_t b = rp[i], e = rp[i + 1];
+    for (int32_t p = b + 1; p < e; ++p) {
+        int32_t c = ci[p];
+        double x = v ? v[p] : 0.0;
+        int32_t q = p;
+        while (q > b && ci[q - 1] > c) {
+            ci[q] = ci[q - 1];
+            if (v) v[q] = v[q - 1];
+            --q;
+        }
+        ci[q] = c;
+        if (v) v[q] = x;
+    }
+}
+
+void csr_transpose(int64_t nrows, int64_t ncols, const int32_t* rp, const int32_t* ci, const double* v,
+                   int32_t* trp, int32_t* tci, double* tv, cudaStream_t s) {
+    Temp<int32_t> cnt(ncols + 1, s);
+    CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (ncols + 1), s));
+    if (nrows > 0) {
+        count_cols_k<<<grid_for(nrows, 256), 256, 0, s>>>(rp, ci, nrows, cnt.get());
+        CK_LAUNCH();
+    }
+    exclusive_scan_i32(cnt.get(), trp, ncols, s);
+    CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (ncols + 1), s));
+    if (nrows > 0) {
+        place_t_k<<<grid_for(nrows, 256), 256, 0, s>>>(rp, ci, v, nrows, trp, cnt.get(), tci, tv);
+        CK_LAUNCH();
+    }
+    if (ncols > 0) {
+        sort_rows_k<<<grid_for(ncols, 128), 128, 0, s>>>(trp, tci, tv, ncols);
+        CK_LAUNCH();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// B = A[perm][:, perm]
+// ---------------------------------------------------------------------------------------------
+__global__ void perm_rowlen_k(const int32_t* rp, const int32_t* perm, int64_t N, int32_t* len) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        int32_t o = perm[i];
+        len[i] = rp[o + 1] - rp[o];
+    }
+}
+__global__ void perm_fill_k(const int32_t* rp, const int32_t* ci, const double* v, const int32_t* perm,
+                            const int32_t* inv, int64_t N, const int32_t* brp, int32_t* bci, double* bv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int32_t o = perm[i];
+    int32_t q = brp[i];
+    for (int32_t p = rp[o]; p < rp[o + 1]; ++p, ++q) {
+        bci[q] = inv[ci[p]];
+        if (bv) bv[q] = v[p];
+    }
+}
+void csr_permute(int64_t N, const int32_t* rp, const int32_t* ci, const double* v, const int32_t* perm,
+                 int32_t* brp, int32_t* bci, double* bv, cudaStream_t s) {
+    if (N <= 0) return;
+    Temp<int32_t> len(N + 1, s), inv(N, s);
+    perm_rowlen_k<<<grid_for(N, 256), 256, 0, s>>>(rp, perm, N, len.get());
+    CK_LAUNCH();
+    exclusive_scan_i32(len.get(), brp, N, s);
+    invert_perm(perm, inv.get(), N, s);
+    perm_fill_k<<<grid_for(N, 256), 256, 0, s>>>(rp, ci, v, perm, inv.get(), N, brp, bci, bv);
+    CK_LAUNCH();
+    sort_rows_k<<<grid_for(N, 128), 128, 0, s>>>(brp, bci, bv, N);
+    CK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------------------------
+// symmetrised pattern: union of row i of A and row i of A^T, diagonal dropped
+// ---------------------------------------------------------------------------------------------
+template <bool WRITE>
+__global__ void union_rows_k(const int32_t* rp, const int32_t* ci, const int32_t* trp, const int32_t* tci, int64_t N,
+                             int32_t* cnt, const int32_t* orp, int32_t* oci) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int32_t a = rp[i], ae = rp[i + 1], b = trp[i], be = trp[i + 1];
+    int32_t c = 0, last = -1;
+    int32_t q = WRITE ? orp[i] : 0;
+    while (a < ae || b < be) {
+        int32_t x;
+        if (b >= be || (a < ae && ci[a] <= tci[b])) x = ci[a++];
+        else x = tci[b++];
+        if (x == i || x == last) continue;
+        last = x;
+        if (WRITE) oci[q + c] = x;
+        ++c;
+    }
+    if (!WRITE) cnt[i] = c;
+}
+void sym_pattern(int64_t N, const int32_t* rp, const int32_t* ci, Temp<int32_t>& srp, Temp<int32_t>& sci,
+                 cudaStream_t s) {
+    int64_t nnz = csr_nnz(rp, N, s);
+    Temp<int32_t> trp(N + 1, s), tci(nnz > 0 ? nnz : 1, s);
+    csr_transpose(N, N, rp, ci, nullptr, trp.get(), tci.get(), nullptr, s);
+    Temp<int32_t> cnt(N + 1, s);
+    srp.alloc(N + 1, s);
+    if (N > 0) {
+        union_rows_k<false><<<grid_for(N, 256), 256, 0, s>>>(rp, ci, trp.get(), tci.get(), N, cnt.get(), nullptr, nullptr);
+        CK_LAUNCH();
+    }
+    exclusive_scan_i32(cnt.get(), srp.get(), N, s);
+    int64_t snnz = csr_nnz(srp.get(), N, s);
+    sci.alloc(snnz > 0 ? snnz : 1, s);
+    if (N > 0) {
+        union_rows_k<true><<<grid_for(N, 256), 256, 0, s>>>(rp, ci, trp.get(), tci.get(), N, nullptr, srp.get(), sci.get());
+        CK_LAUNCH();
+    }
+}
+
+}  // namespace mgm

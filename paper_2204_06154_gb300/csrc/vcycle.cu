@@ -1,0 +1,370 @@
+// The MGM V(nu1, nu2)-cycle (paper Alg. 3) on the device, as the linear preconditioner z = M r
+// (zero initial guess on every level).
+//
+// Smoother: forward Gauss-Seidel (eq. (smoother), Table 1) in multicolour order: the rows of one
+// colour are mutually independent, so a sweep is one kernel per colour over a contiguous row
+// range. Rows are stored split into lower-colour and upper-colour parts (see hier.cuh). Starting
+// from zero, the first sweep only needs the lower part (upper-colour unknowns are still zero),
+// and its residual is then exactly -U e, because (D + L_lower) e = b row by row. So pre-smoothing
+// plus the residual stream each level's matrix once, and post-smoothing streams it once more.
+//
+// Kernels assign G = 8 lanes to a row and read columns and values with 16-byte vector loads
+// (rows start at multiples of 4 entries); gathered vector entries come from L1/L2 (RCM order
+// keeps them local). The restriction (CSR of the transposed interpolation) and interpolation
+// (ELL, width m) are one thread per row; the coarsest solve multiplies by the explicit FP64
+// inverse, one warp per row. The whole cycle is captured once into a CUDA graph.
+#include "hier.cuh"
+
+namespace mgm {
+
+constexpr int G = 8;          // lanes per row
+constexpr int VBLOCK = 256;   // threads per block -> 32 rows per block
+
+template <class T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// sum_{p in [beg, end)} v_p x[c_p] over one row, G lanes cooperating; beg, end multiples of 4
+__device__ __forceinline__ float row_sum(const int32_t* __restrict__ sc, const float* __restrict__ sv, int32_t beg,
+                                         int32_t end, const float* x, int gl) {
+    float acc = 0.0f;
+    for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {
+        int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
+        float4 v = __ldg(reinterpret_cast<const float4*>(sv + p));
+        acc = fmaf(v.x, x[c.x], acc);
+        acc = fmaf(v.y, x[c.y], acc);
+        acc = fmaf(v.z, x[c.z], acc);
+        acc = fmaf(v.w, x[c.w], acc);
+    }
+    return acc;
+}
+__device__ __forceinline__ double row_sum(const int32_t* __restrict__ sc, const double* __restrict__ sv, int32_t beg,
+                                          int32_t end, const double* x, int gl) {
+    double acc = 0.0;
+    for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {
+        int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
+        double2 v0 = __ldg(reinterpret_cast<const double2*>(sv + p));
+        double2 v1 = __ldg(reinterpret_cast<const double2*>(sv + p + 2));
+        acc = fma(v0.x, x[c.x], acc);
+        acc = fma(v0.y, x[c.y], acc);
+        acc = fma(v1.x, x[c.z], acc);
+        acc = fma(v1.y, x[c.w], acc);
+    }
+    return acc;
+}
+template <class T>
+__device__ __forceinline__ T group_reduce(T v) {
+    for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// MODE 0: e = (b - lower e) dinv   (first sweep from zero)
+// MODE 1: e = (b - offdiag e) dinv (full sweep)
+// MODE 2: s = -upper e             (residual after a first sweep from zero)
+// MODE 3: s = b - diag e - offdiag e
+template <int MODE, class T>
+__global__ void __launch_bounds__(VBLOCK) row_kernel(const int32_t* __restrict__ lo, const int32_t* __restrict__ mid,
+                                                     const int32_t* __restrict__ sc, const T* __restrict__ sv,
+                                                     const T* __restrict__ dv, const T* __restrict__ b, T* e, T* s,
+                                                     int32_t r0, int32_t r1) {
+    const int t = blockIdx.x * VBLOCK + threadIdx.x;
+    const int32_t row = r0 + t / G;
+    const int gl = t & (G - 1);
+    const bool act = row < r1;
+    T acc = T(0);
+    if (act) {
+        int32_t beg, end;
+        if (MODE == 0) { beg = lo[row]; end = mid[row]; }
+        else if (MODE == 2) { beg = mid[row]; end = lo[row + 1]; }
+        else { beg = lo[row]; end = lo[row + 1]; }
+        acc = row_sum(sc, sv, beg, end, e, gl);
+    }
+    acc = group_reduce(acc);
+    if (act && gl == 0) {
+        if (MODE == 0 || MODE == 1) e[row] = (b[row] - acc) * dv[row];
+        else if (MODE == 2) s[row] = -acc;
+        else s[row] = b[row] - dv[row] * e[row] - acc;
+    }
+}
+
+template <class T>
+__global__ void restrict_k(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
+                           const T* __restrict__ s, T* bn, int64_t nc) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    T acc = T(0);
+    for (int32_t q = rp[c]; q < rp[c + 1]; ++q) acc += v[q] * s[ci[q]];
+    bn[c] = acc;
+}
+
+template <class T>
+__global__ void interp_k(const int32_t* __restrict__ pc, const T* __restrict__ pv, int pw, const T* __restrict__ en, T* e,
+                         int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T acc = e[i];
+    for (int t = 0; t < pw; ++t) acc += pv[i * pw + t] * en[pc[i * pw + t]];
+    e[i] = acc;
+}
+
+template <class T>
+__global__ void coarse_k(const double* __restrict__ Ainv, const T* __restrict__ b, T* e, int64_t n) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double acc = 0.0;
+    for (int64_t j = lane; j < n; j += 32) acc = fma(Ainv[row * n + j], (double)b[j], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) e[row] = (T)acc;
+}
+
+template <class T>
+__global__ void copy_k(const T* a, T* b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+template <class TI, class TO>
+__global__ void load_k(const TI* src, const int32_t* gather, TO* dst, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (TO)src[gather ? gather[i] : i];
+}
+template <class TI, class TO>
+__global__ void store_k(const TI* src, const int32_t* scatter, TO* dst, int64_t n, int add) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = scatter ? scatter[i] : i;
+    dst[j] = add ? (TO)((double)dst[j] + (double)src[i]) : (TO)src[i];
+}
+
+// ------------------------------ level accessors ----------------------------------------------
+template <class T> struct LV;
+template <> struct LV<float> {
+    static float* b(Level& L) { return L.b32.get(); }
+    static float* e(Level& L) { return L.e32.get(); }
+    static float* s(Level& L) { return L.s32.get(); }
+    static const float* sv(Level& L) { return L.sv32.get(); }
+    static const float* diag(Level& L) { return L.diag32.get(); }
+    static const float* dinv(Level& L) { return L.dinv32.get(); }
+    static const float* pv(Level& L) { return L.pv32.get(); }
+    static const float* rv(Level& L) { return L.r_v32.get(); }
+};
+template <> struct LV<double> {
+    static double* b(Level& L) { return L.b64.get(); }
+    static double* e(Level& L) { return L.e64.get(); }
+    static double* s(Level& L) { return L.s64.get(); }
+    static const double* sv(Level& L) { return L.sv64.get(); }
+    static const double* diag(Level& L) { return L.diag64.get(); }
+    static const double* dinv(Level& L) { return L.dinv64.get(); }
+    static const double* pv(Level& L) { return L.pv64.get(); }
+    static const double* rv(Level& L) { return L.r_v64.get(); }
+};
+
+template <int MODE, class T>
+static void launch_rows(Level& L, int32_t r0, int32_t r1, cudaStream_t s) {
+    if (r1 <= r0) return;
+    const int64_t threads = (int64_t)(r1 - r0) * G;
+    const T* dv = (MODE == 3) ? LV<T>::diag(L) : LV<T>::dinv(L);
+    row_kernel<MODE, T><<<grid_for(threads, VBLOCK), VBLOCK, 0, s>>>(L.lo.get(), L.mid.get(), L.sc.get(), LV<T>::sv(L), dv,
+                                                                    LV<T>::b(L), LV<T>::e(L), LV<T>::s(L), r0, r1);
+    CK_LAUNCH();
+}
+
+template <class T>
+static void sweep(Level& L, bool from_zero, cudaStream_t s) {
+    for (size_t c = 0; c + 1 < L.cptr.size(); ++c) {
+        if (from_zero) launch_rows<0, T>(L, L.cptr[c], L.cptr[c + 1], s);
+        else launch_rows<1, T>(L, L.cptr[c], L.cptr[c + 1], s);
+    }
+}
+
+// Alg. 3 with a zero initial guess on level 1: b_0 -> e_0
+template <class T>
+static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
+    const int p = H->p;
+    for (int j = 0; j + 1 < p; ++j) {  // lines 4-9
+        Level& L = H->lv[j];
+        Level& C = H->lv[j + 1];
+        const T* rsrc;
+        if (H->nu1 >= 1) {
+            sweep<T>(L, true, s);
+            for (int t = 1; t < H->nu1; ++t) sweep<T>(L, false, s);
+            if (H->nu1 == 1) launch_rows<2, T>(L, 0, (int32_t)L.n, s);
+            else launch_rows<3, T>(L, 0, (int32_t)L.n, s);
+            rsrc = LV<T>::s(L);
+        } else {
+            CK(cudaMemsetAsync(LV<T>::e(L), 0, sizeof(T) * L.n, s));
+            rsrc = LV<T>::b(L);
+        }
+        restrict_k<T><<<grid_for(C.n, 256), 256, 0, s>>>(L.r_rp.get(), L.r_ci.get(), LV<T>::rv(L), rsrc, LV<T>::b(C), C.n);
+        CK_LAUNCH();
+    }
+    {   // line 10
+        Level& C = H->lv[p - 1];
+        coarse_k<T><<<grid_for(C.n * 32, 256), 256, 0, s>>>(H->Ainv.get(), LV<T>::b(C), LV<T>::e(C), C.n);
+        CK_LAUNCH();
+    }
+    for (int j = p - 2; j >= 0; --j) {  // lines 11-16
+        Level& L = H->lv[j];
+        Level& C = H->lv[j + 1];
+        interp_k<T><<<grid_for(L.n, 256), 256, 0, s>>>(L.pc.get(), LV<T>::pv(L), L.pw, LV<T>::e(C), LV<T>::e(L), L.n);
+        CK_LAUNCH();
+        for (int t = 0; t < H->nu2; ++t) sweep<T>(L, false, s);
+    }
+}
+
+void alloc_work(mgm_hierarchy* H) {
+    for (int j = 0; j < H->p; ++j) {
+        Level& L = H->lv[j];
+        const bool smooth = j + 1 < H->p;
+        if (H->precision == MGM_F32) {
+            L.b32.alloc(L.n); L.e32.alloc(L.n);
+            CK(cudaMemset(L.e32.get(), 0, sizeof(float) * L.n));
+            CK(cudaMemset(L.b32.get(), 0, sizeof(float) * L.n));
+            if (smooth) { L.s32.alloc(L.n); CK(cudaMemset(L.s32.get(), 0, sizeof(float) * L.n)); }
+        } else {
+            L.b64.alloc(L.n); L.e64.alloc(L.n);
+            CK(cudaMemset(L.e64.get(), 0, sizeof(double) * L.n));
+            CK(cudaMemset(L.b64.get(), 0, sizeof(double) * L.n));
+            if (smooth) { L.s64.alloc(L.n); CK(cudaMemset(L.s64.get(), 0, sizeof(double) * L.n)); }
+        }
+    }
+}
+
+void vcycle_prepare(mgm_hierarchy* H) {
+    if (H->vgraph) return;
+    if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    const int64_t before = launches();
+    CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
+    try {
+        if (H->precision == MGM_F32) vcycle_launches<float>(H, H->cap_stream);
+        else vcycle_launches<double>(H, H->cap_stream);
+    } catch (...) {
+        cudaStreamEndCapture(H->cap_stream, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    CK(cudaStreamEndCapture(H->cap_stream, &g));
+    H->graph_kernels = launches() - before;  // captured, not executed: counted per graph launch
+    note_launch(-H->graph_kernels);
+    cudaError_t e = cudaGraphInstantiate(&H->vgraph, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+}
+
+void vcycle_core(mgm_hierarchy* H, cudaStream_t s) {
+    vcycle_prepare(H);
+    CK(cudaGraphLaunch(H->vgraph, s));
+    note_launch(H->graph_kernels);
+}
+
+void load_input(mgm_hierarchy* H, const void* src, int dt, const int32_t* gather, cudaStream_t s) {
+    Level& L = H->lv[0];
+    const int64_t n = L.n;
+    if (H->precision == MGM_F32) {
+        if (dt == MGM_F64) load_k<double, float><<<grid_for(n, 256), 256, 0, s>>>((const double*)src, gather, L.b32.get(), n);
+        else load_k<float, float><<<grid_for(n, 256), 256, 0, s>>>((const float*)src, gather, L.b32.get(), n);
+    } else {
+        if (dt == MGM_F64) load_k<double, double><<<grid_for(n, 256), 256, 0, s>>>((const double*)src, gather, L.b64.get(), n);
+        else load_k<float, double><<<grid_for(n, 256), 256, 0, s>>>((const float*)src, gather, L.b64.get(), n);
+    }
+    CK_LAUNCH();
+}
+
+void store_output(mgm_hierarchy* H, void* dst, int dt, const int32_t* scatter, cudaStream_t s) {
+    Level& L = H->lv[0];
+    const int64_t n = L.n;
+    if (H->precision == MGM_F32) {
+        if (dt == MGM_F64) store_k<float, double><<<grid_for(n, 256), 256, 0, s>>>(L.e32.get(), scatter, (double*)dst, n, 0);
+        else store_k<float, float><<<grid_for(n, 256), 256, 0, s>>>(L.e32.get(), scatter, (float*)dst, n, 0);
+    } else {
+        if (dt == MGM_F64) store_k<double, double><<<grid_for(n, 256), 256, 0, s>>>(L.e64.get(), scatter, (double*)dst, n, 0);
+        else store_k<double, float><<<grid_for(n, 256), 256, 0, s>>>(L.e64.get(), scatter, (float*)dst, n, 0);
+    }
+    CK_LAUNCH();
+}
+
+// u[scatter[i]] += e_0[i] (FP64 accumulation), for the standalone MGM iteration
+void add_output(mgm_hierarchy* H, double* dst, const int32_t* scatter, cudaStream_t s) {
+    Level& L = H->lv[0];
+    const int64_t n = L.n;
+    if (H->precision == MGM_F32) store_k<float, double><<<grid_for(n, 256), 256, 0, s>>>(L.e32.get(), scatter, dst, n, 1);
+    else store_k<double, double><<<grid_for(n, 256), 256, 0, s>>>(L.e64.get(), scatter, dst, n, 1);
+    CK_LAUNCH();
+}
+
+// Algorithmic bytes of one V-cycle: every stored off-diagonal entry (value + column) is read once
+// per pass, per-row arrays (row starts, diagonal inverse, b, e, s) once per pass, transfer
+// entries once, the coarsest inverse once; gathered vector entries are L2 hits and not counted.
+int64_t vcycle_bytes(const mgm_hierarchy* H) {
+    const int64_t vs = H->precision == MGM_F32 ? 4 : 8, is = 4, ent = vs + is;
+    int64_t b = 0;
+    for (int j = 0; j + 1 < H->p; ++j) {
+        const Level& L = H->lv[j];
+        const Level& C = H->lv[j + 1];
+        const int64_t n = L.n, nnzo = L.nlow + L.nupp;
+        if (H->nu1 >= 1) {
+            b += L.nlow * ent + n * (8 + 3 * vs);                      // first sweep from zero (lower part)
+            b += (int64_t)(H->nu1 - 1) * (nnzo * ent + n * (4 + 3 * vs));
+            b += (H->nu1 == 1 ? L.nupp * ent + n * (4 + vs)           // residual -U e
+                              : nnzo * ent + n * (4 + 4 * vs));        // residual b - A e
+        }
+        b += L.pnnz * ent + (C.n + 1) * 4 + n * vs + C.n * vs;        // restriction
+        b += L.pnnz * ent + 2 * n * vs;                               // interpolation + correction
+        b += (int64_t)H->nu2 * (nnzo * ent + n * (4 + 3 * vs));       // post-smoothing sweeps
+    }
+    b += H->np * H->np * 8 + 2 * H->np * vs;                          // coarsest solve
+    return b;
+}
+
+void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s) {
+    REQUIRE(H && out && reps >= 1, "bad argument");
+    vcycle_prepare(H);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int t = 0; t < 2; ++t) vcycle_core(H, s);
+    CK(cudaEventRecord(e0, s));
+    for (int t = 0; t < reps; ++t) vcycle_core(H, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    out->vcycle_ms = ms / reps;
+    out->vcycle_bytes = vcycle_bytes(H);
+    out->vcycle_kernels = H->graph_kernels;
+    out->sweep_ms = 0.0f;
+    out->sweep_bytes = 0;
+    out->sweep_launches = 0;
+    if (H->p >= 2) {
+        Level& L = H->lv[0];
+        const int64_t vs = H->precision == MGM_F32 ? 4 : 8;
+        for (int t = 0; t < 2; ++t) {
+            if (H->precision == MGM_F32) sweep<float>(L, false, s);
+            else sweep<double>(L, false, s);
+        }
+        CK(cudaEventRecord(e0, s));
+        for (int t = 0; t < reps; ++t) {
+            if (H->precision == MGM_F32) sweep<float>(L, false, s);
+            else sweep<double>(L, false, s);
+        }
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        out->sweep_ms = ms / reps;
+        out->sweep_bytes = (L.nlow + L.nupp) * (vs + 4) + L.n * (4 + 3 * vs);
+        out->sweep_launches = (int32_t)(L.cptr.size() - 1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+void vcycle_api(mgm_hierarchy* H, const void* r, void* z, int dtype, cudaStream_t s) {
+    REQUIRE(H && r && z, "null argument");
+    REQUIRE(dtype == MGM_F32 || dtype == MGM_F64, "dtype must be MGM_F32 or MGM_F64");
+    load_input(H, r, dtype, H->ord_caller.get(), s);
+    vcycle_core(H, s);
+    store_output(H, z, dtype, H->ord_caller.get(), s);
+}
+
+}  // namespace mgm

@@ -1,0 +1,303 @@
+"""Thin ctypes binding of libmgm (include/mgm.h): argument marshalling only.
+
+Every array is a CUDA torch tensor (device memory and the current stream come from PyTorch); all
+computation happens in the library's sm_103a kernels. If libmgm.so is missing the import-time
+loader raises -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libmgm.so")
+_lib = None
+
+MGM_RBF_FD, MGM_GFD = 0, 1
+MGM_F64, MGM_F32 = 0, 1
+MGM_KRYLOV_FGMRES, MGM_KRYLOV_NONE = 0, 1
+
+STATUS = {0: "MGM_OK", 1: "MGM_ERR_INVALID_ARG", 2: "MGM_ERR_SINGULAR_STENCIL", 3: "MGM_ERR_NOT_CONVERGED",
+          4: "MGM_ERR_BREAKDOWN", 5: "MGM_ERR_TIMEOUT", 6: "MGM_ERR_CUDA", 7: "MGM_ERR_OOM", 8: "MGM_ERR_UNSUPPORTED"}
+
+
+class MGMError(RuntimeError):
+    def __init__(self, status, message, row=-1):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.row = row
+
+
+class StencilParams(C.Structure):
+    _fields_ = [("method", C.c_int), ("k", C.c_int), ("ell", C.c_int), ("n", C.c_int), ("alpha", C.c_double),
+                ("mu", C.c_double), ("poisson", C.c_int)]
+
+
+class Params(C.Structure):
+    _fields_ = [("n_min", C.c_int64), ("m", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int),
+                ("seed", C.c_uint64)]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("krylov", C.c_int), ("restart", C.c_int), ("maxit", C.c_int), ("tol", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rel_res", C.c_double), ("history", C.POINTER(C.c_double)),
+                ("history_len", C.c_int), ("solve_ms", C.c_float)]
+
+
+class HierStats(C.Structure):
+    _fields_ = [("p", C.c_int), ("precision", C.c_int), ("n", C.c_int64 * 16), ("nnz", C.c_int64 * 16),
+                ("ncolors", C.c_int32 * 16), ("device_bytes", C.c_int64)]
+
+
+EXPORTS = ["mgm_knn", "mgm_stencil_weights", "mgm_assemble", "mgm_build_stencils", "mgm_coarsen", "mgm_interp",
+           "mgm_transpose", "mgm_spgemm", "mgm_rcm", "mgm_color", "mgm_setup", "mgm_vcycle", "mgm_solve",
+           "mgm_hierarchy_stats_get", "mgm_hierarchy_level", "mgm_hierarchy_pnnz", "mgm_destroy",
+           "mgm_status_string", "mgm_last_error_message", "mgm_last_error_row"]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIBPATH):
+            raise RuntimeError(f"{_LIBPATH} is missing: build it with paper_2204_06154_gb300.build.build()")
+        L = C.CDLL(_LIBPATH)
+        P, I64, I = C.c_void_p, C.c_int64, C.c_int
+        L.mgm_knn.argtypes = [P, I64, P, I64, I, I, P, P]
+        L.mgm_stencil_weights.argtypes = [P, P, I64, P, C.POINTER(StencilParams), P, P]
+        L.mgm_assemble.argtypes = [I64, I, P, P, C.c_double, I, P, P, P, P]
+        L.mgm_build_stencils.argtypes = [P, P, I64, C.POINTER(StencilParams), P, P, P, P, P, P]
+        L.mgm_coarsen.argtypes = [P, I64, I64, C.c_uint64, P, P]
+        L.mgm_interp.argtypes = [P, I64, P, I64, I, P, P, P, C.POINTER(C.c_int64), P]
+        L.mgm_transpose.argtypes = [I64, I64, P, P, P, P, P, P, P]
+        L.mgm_spgemm.argtypes = [I64, I64, I64, P, P, P, P, P, P, P, P, P, C.POINTER(C.c_int64), P]
+        L.mgm_rcm.argtypes = [I64, P, P, P, P]
+        L.mgm_color.argtypes = [I64, P, P, C.c_uint64, P, C.POINTER(C.c_int32), P]
+        L.mgm_setup.argtypes = [P, I64, P, P, P, C.POINTER(Params), C.POINTER(P), P]
+        L.mgm_vcycle.argtypes = [P, P, P, I, P]
+        L.mgm_solve.argtypes = [P, P, P, C.POINTER(SolveParams), C.POINTER(SolveInfo), P]
+        L.mgm_hierarchy_stats_get.argtypes = [P, C.POINTER(HierStats)]
+        L.mgm_hierarchy_level.argtypes = [P, I] + [P] * 10 + [P]
+        L.mgm_hierarchy_pnnz.argtypes = [P, I, C.POINTER(C.c_int64)]
+        L.mgm_destroy.argtypes = [P]
+        L.mgm_destroy.restype = None
+        L.mgm_status_string.restype = C.c_char_p
+        L.mgm_last_error_message.restype = C.c_char_p
+        L.mgm_last_error_row.restype = C.c_int64
+        for name in EXPORTS:
+            if name not in ("mgm_destroy", "mgm_status_string", "mgm_last_error_message", "mgm_last_error_row"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        L = lib()
+        raise MGMError(st, L.mgm_last_error_message().decode(), int(L.mgm_last_error_row()))
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    return t.contiguous()
+
+
+# ----------------------------------------------------------------------------------------------
+def knn(data, query, k, self_first=False):
+    data = _dev(data, torch.float64, "data")
+    query = data if self_first else _dev(query, torch.float64, "query")
+    out = torch.empty((query.shape[0], k), dtype=torch.int32, device=data.device)
+    _check(lib().mgm_knn(_p(data), data.shape[0], _p(query), query.shape[0], k, int(self_first), _p(out), _stream()))
+    return out
+
+
+def _sp(n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, poisson=False):
+    return StencilParams(MGM_RBF_FD if method == "rbf" else MGM_GFD, k, ell, n, alpha, mu, int(poisson))
+
+
+def stencil_weights(xyz, nrm, idx, method="rbf", k=1, ell=2, alpha=4.0):
+    xyz = _dev(xyz, torch.float64, "xyz"); nrm = _dev(nrm, torch.float64, "nrm"); idx = _dev(idx, torch.int32, "idx")
+    sp = _sp(idx.shape[1], method, k, ell, 1.0, alpha)
+    w = torch.empty(idx.shape, dtype=torch.float64, device=xyz.device)
+    _check(lib().mgm_stencil_weights(_p(xyz), _p(nrm), xyz.shape[0], _p(idx), C.byref(sp), _p(w), _stream()))
+    return w
+
+
+def assemble(idx, w, mu=1.0, poisson=False):
+    idx = _dev(idx, torch.int32, "idx"); w = _dev(w, torch.float64, "w")
+    N, n = idx.shape
+    rp = torch.empty(N + 1, dtype=torch.int32, device=idx.device)
+    ci = torch.empty(N * n, dtype=torch.int32, device=idx.device)
+    v = torch.empty(N * n, dtype=torch.float64, device=idx.device)
+    _check(lib().mgm_assemble(N, n, _p(idx), _p(w), mu, int(poisson), _p(rp), _p(ci), _p(v), _stream()))
+    return rp, ci, v
+
+
+def build_stencils(xyz, nrm, n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, poisson=False, keep_weights=True):
+    xyz = _dev(xyz, torch.float64, "xyz"); nrm = _dev(nrm, torch.float64, "nrm")
+    N = xyz.shape[0]
+    dev = xyz.device
+    sp = _sp(n, method, k, ell, mu, alpha, poisson)
+    idx = torch.empty((N, n), dtype=torch.int32, device=dev) if keep_weights else None
+    w = torch.empty((N, n), dtype=torch.float64, device=dev) if keep_weights else None
+    rp = torch.empty(N + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(N * n, dtype=torch.int32, device=dev)
+    v = torch.empty(N * n, dtype=torch.float64, device=dev)
+    _check(lib().mgm_build_stencils(_p(xyz), _p(nrm), N, C.byref(sp), _p(idx), _p(w), _p(rp), _p(ci), _p(v), _stream()))
+    return idx, w, rp, ci, v
+
+
+def coarsen(xyz, NH):
+    xyz = _dev(xyz, torch.float64, "xyz")
+    keep = torch.empty(NH, dtype=torch.int32, device=xyz.device)
+    _check(lib().mgm_coarsen(_p(xyz), xyz.shape[0], NH, 0, _p(keep), _stream()))
+    return keep
+
+
+def interp(xf, xc, m=3):
+    xf = _dev(xf, torch.float64, "xf"); xc = _dev(xc, torch.float64, "xc")
+    Nf = xf.shape[0]
+    rp = torch.empty(Nf + 1, dtype=torch.int32, device=xf.device)
+    ci = torch.empty(Nf * m, dtype=torch.int32, device=xf.device)
+    v = torch.empty(Nf * m, dtype=torch.float64, device=xf.device)
+    nnz = C.c_int64(0)
+    _check(lib().mgm_interp(_p(xf), Nf, _p(xc), xc.shape[0], m, _p(rp), _p(ci), _p(v), C.byref(nnz), _stream()))
+    return rp, ci[: nnz.value], v[: nnz.value]
+
+
+def transpose(nrows, ncols, rp, ci, v):
+    nnz = ci.numel()
+    trp = torch.empty(ncols + 1, dtype=torch.int32, device=rp.device)
+    tci = torch.empty(max(nnz, 1), dtype=torch.int32, device=rp.device)
+    tv = torch.empty(max(nnz, 1), dtype=torch.float64, device=rp.device)
+    _check(lib().mgm_transpose(nrows, ncols, _p(rp), _p(ci), _p(v), _p(trp), _p(tci), _p(tv), _stream()))
+    return trp, tci[:nnz], tv[:nnz]
+
+
+def spgemm(nA, nB, ncolsB, a, b):
+    arp, aci, av = a
+    brp, bci, bv = b
+    crp = torch.empty(nA + 1, dtype=torch.int32, device=arp.device)
+    nnz = C.c_int64(0)
+    L = lib()
+    _check(L.mgm_spgemm(nA, nB, ncolsB, _p(arp), _p(aci), _p(av), _p(brp), _p(bci), _p(bv), _p(crp), None, None,
+                        C.byref(nnz), _stream()))
+    cci = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=arp.device)
+    cv = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=arp.device)
+    _check(L.mgm_spgemm(nA, nB, ncolsB, _p(arp), _p(aci), _p(av), _p(brp), _p(bci), _p(bv), _p(crp), _p(cci), _p(cv),
+                        C.byref(nnz), _stream()))
+    return crp, cci[: nnz.value], cv[: nnz.value]
+
+
+def rcm(rp, ci):
+    N = rp.numel() - 1
+    perm = torch.empty(N, dtype=torch.int32, device=rp.device)
+    _check(lib().mgm_rcm(N, _p(rp), _p(ci), _p(perm), _stream()))
+    return perm
+
+
+def color(rp, ci, seed):
+    N = rp.numel() - 1
+    col = torch.empty(N, dtype=torch.int32, device=rp.device)
+    nc = C.c_int32(0)
+    _check(lib().mgm_color(N, _p(rp), _p(ci), seed, _p(col), C.byref(nc), _stream()))
+    return col, nc.value
+
+
+class Hierarchy:
+    """MGM hierarchy (Alg. 2) owned by the library; V-cycle (Alg. 3) and FGMRES solve on it."""
+
+    def __init__(self, xyz, rp, ci, v, n_min, m=3, nu1=1, nu2=1, precision="f32", seed=0):
+        xyz = _dev(xyz, torch.float64, "xyz"); rp = _dev(rp, torch.int32, "rowptr")
+        ci = _dev(ci, torch.int32, "col"); v = _dev(v, torch.float64, "val")
+        self.N = xyz.shape[0]
+        self.device = xyz.device
+        prm = Params(n_min, m, nu1, nu2, MGM_F32 if precision == "f32" else MGM_F64, seed)
+        h = C.c_void_p()
+        self._h = None
+        _check(lib().mgm_setup(_p(xyz), self.N, _p(rp), _p(ci), _p(v), C.byref(prm), C.byref(h), _stream()))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().mgm_destroy(self._h)
+            self._h = None
+
+    def stats(self):
+        s = HierStats()
+        _check(lib().mgm_hierarchy_stats_get(self._h, C.byref(s)))
+        p = s.p
+        return {"p": p, "n": list(s.n[:p]), "nnz": list(s.nnz[:p]), "ncolors": list(s.ncolors[:p]),
+                "device_bytes": s.device_bytes, "precision": "f32" if s.precision == MGM_F32 else "f64"}
+
+    def level(self, j):
+        st = self.stats()
+        n, nnz = st["n"][j], st["nnz"][j]
+        dev = self.device
+        out = {"perm": torch.empty(n, dtype=torch.int32, device=dev),
+               "xyz": torch.empty((n, 3), dtype=torch.float64, device=dev),
+               "rp": torch.empty(n + 1, dtype=torch.int32, device=dev),
+               "ci": torch.empty(nnz, dtype=torch.int32, device=dev),
+               "v": torch.empty(nnz, dtype=torch.float64, device=dev)}
+        keep = torch.empty(n, dtype=torch.int32, device=dev) if j >= 1 else None
+        args = [None] * 6
+        if j + 1 < st["p"]:
+            pn = C.c_int64(0)
+            _check(lib().mgm_hierarchy_pnnz(self._h, j, C.byref(pn)))
+            out["prp"] = torch.empty(n + 1, dtype=torch.int32, device=dev)
+            out["pci"] = torch.empty(pn.value, dtype=torch.int32, device=dev)
+            out["pv"] = torch.empty(pn.value, dtype=torch.float64, device=dev)
+            out["colour"] = torch.empty(n, dtype=torch.int32, device=dev)
+            args = [out["prp"], out["pci"], out["pv"], out["colour"]]
+        else:
+            args = [None, None, None, None]
+        _check(lib().mgm_hierarchy_level(self._h, j, _p(out["perm"]), _p(keep), _p(out["xyz"]), _p(out["rp"]),
+                                         _p(out["ci"]), _p(out["v"]), *[_p(a) for a in args], _stream()))
+        if keep is not None:
+            out["keep"] = keep
+        return out
+
+    def vcycle(self, r):
+        if r.dtype not in (torch.float32, torch.float64):
+            raise TypeError("r must be float32 or float64")
+        r = _dev(r, r.dtype, "r")
+        z = torch.empty_like(r)
+        _check(lib().mgm_vcycle(self._h, _p(r), _p(z), MGM_F64 if r.dtype == torch.float64 else MGM_F32, _stream()))
+        return z
+
+    def solve(self, f, u0=None, krylov="fgmres", restart=50, maxit=200, tol=1e-10, raise_on_nonconv=False):
+        f = _dev(f, torch.float64, "f")
+        u = torch.zeros_like(f) if u0 is None else _dev(u0, torch.float64, "u0").clone()
+        sp = SolveParams(MGM_KRYLOV_FGMRES if krylov == "fgmres" else MGM_KRYLOV_NONE, restart, maxit, tol)
+        hist = (C.c_double * (maxit + 2))()
+        info = SolveInfo(0, 0.0, hist, maxit + 2, 0.0)
+        st = lib().mgm_solve(self._h, _p(f), _p(u), C.byref(sp), C.byref(info), _stream())
+        if st != 0 and (st != 3 or raise_on_nonconv):
+            _check(st)
+        return u, {"iters": info.iters, "rel_res": info.rel_res, "solve_ms": info.solve_ms, "converged": st == 0,
+                   "history": [hist[i] for i in range(info.iters + 1)]}
+
+
+def solve_points(xyz, nrm, f, n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, n_min=250, m=3, precision="f32",
+                 tol=1e-10, restart=50, maxit=200, seed=0):
+    """The whole path from a point cloud to a solution: stencils (Sec. 2), hierarchy (Alg. 2),
+    MGM-preconditioned FGMRES (Sec. 4.6). Inputs are CUDA tensors; returns (u, info, hierarchy)."""
+    _, _, rp, ci, v = build_stencils(xyz, nrm, n, method, k, ell, mu, alpha, keep_weights=False)
+    H = Hierarchy(xyz, rp, ci, v, n_min, m=m, precision=precision, seed=seed)
+    u, info = H.solve(f, tol=tol, restart=restart, maxit=maxit)
+    return u, info, H
