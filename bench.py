@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the MGM path on GB300: time to a 1e-10 relative residual at N = 1,048,576.
+
+Workload (one "step" = one pass of the whole path over the step's problems): the unit sphere
+(spherical Fibonacci points, jitter 0.1 h) and the torus R = 1, r = 1/3 (2048 x 512 parametric
+grid, jitter 0.1 h), each N = 1,048,576; tangent-plane PHS RBF-FD with phi = r^3 and degree-3
+polynomials, n = 50; L = I - D (-Lap + I); right-hand side a seeded sum of real spherical
+harmonics up to l = 20 with N(0, 1) coefficients; N_min = 250, m = 3, V(1,1) multicolour GS,
+FP32 V-cycle inside FP64 flexible GMRES to 1e-10. Per problem the step runs kNN stencils and
+FP64 weights, the hierarchy (RCM, weighted sample elimination, transfers, Galerkin products,
+colourings, coarsest inverse) and the solve, all in libmgm kernels. Inputs are resident in HBM
+when the timed region starts; the level-1 operator (~630 MB) exceeds the 129 MB L2, so no flush
+is needed between steps.
+
+Reported: value = mean device time per problem for the whole path (ms, lower is better); the
+phase split (stencils / setup / solve, the solve alone being the paper's convention); the same
+solve with an FP64 V-cycle (the "FP64 MGM" comparison); the roofline of the dominant kernel
+(the FP64 stencil-weight solves, ALU-bound) and of the finest-level Gauss-Seidel sweep
+(HBM-bound); e2e through pinned host buffers; the oracle timed on the host cores.
+
+--impl reference times the CPU oracle (the plain FP64 C implementation that the tests compare
+against) on a bounded sample of the same workload.
+
+Multi-GPU: independent problems shard across ranks (each rank runs its own seeded sphere and
+torus; weak scaling; no collective on the data path). Launch N>1 with torch.distributed.run.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-10 rel. residual at N=1M, mixed vs FP64 MGM; V-cycle HBM GB/s vs peak"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_PEAK_GFLOPS = 1197.0   # measured FMA-chain peak on this machine's GB300 (nominal 1.25 TFLOP/s)
+
+P = dict(n=50, k=1, ell=3, mu=1.0, n_min=250, m=3, tol=1e-10, restart=50, maxit=200)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=1048576, help="points per surface")
+    ap.add_argument("--cpu-sample", type=int, default=32768, help="points of the oracle's bounded sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def problems(N, rank):
+    from paper_2204_06154_gb300 import inputs as I
+    seed = 2 + 1000 * rank
+    xs, ns = I.fibonacci_sphere(N, jitter=0.1, seed=seed)
+    xt, nt = I.torus_grid(N, 1.0, 1.0 / 3.0, jitter=0.1, seed=seed)
+    return [("sphere", xs, ns, I.random_sh_rhs(xs, 20, seed)), ("torus", xt, nt, I.random_sh_rhs(xt, 20, seed))]
+
+
+# ----------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------------------------
+# one problem through the whole path (device-resident inputs), with phase events
+# ----------------------------------------------------------------------------------------------
+def run_problem(M, torch, x, nrm, f, precision="f32", ev=None):
+    E = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    E[0].record()
+    idx = M.knn(x, None, P["n"], self_first=True)
+    E[1].record()
+    w = M.stencil_weights(x, nrm, idx, "rbf", P["k"], P["ell"])
+    E[2].record()
+    rp, ci, v = M.assemble(idx, w, P["mu"])
+    E[3].record()
+    H = M.Hierarchy(x, rp, ci, v, P["n_min"], m=P["m"], precision=precision)
+    E[4].record()
+    u, info = H.solve(f, tol=P["tol"], restart=P["restart"], maxit=P["maxit"])
+    E[5].record()
+    E[5].synchronize()
+    t = [E[i].elapsed_time(E[i + 1]) for i in range(5)]
+    out = {"knn_ms": t[0], "weights_ms": t[1], "assemble_ms": t[2], "setup_ms": t[3], "solve_ms": t[4],
+           "total_ms": E[0].elapsed_time(E[5]), "iters": info["iters"], "rel_res": info["rel_res"],
+           "converged": info["converged"]}
+    return out, H, u
+
+
+def bench_ours(a, rank, world, local_rank):
+    import torch
+    from paper_2204_06154_gb300 import mgm as M
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    M.lib()
+    probs = problems(a.size, rank)
+    dprobs = [(name, torch.from_numpy(x).to(dev), torch.from_numpy(n).to(dev), torch.from_numpy(f).to(dev))
+              for name, x, n, f in probs]
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up steps
+    for _ in range(a.warmup):
+        for name, x, n, f in dprobs:
+            r, H, u = run_problem(M, torch, x, n, f)
+            del H, u
+    # timed steps
+    barrier()
+    records = []
+    l0 = M.kernel_launches()
+    with Clocks(local_rank) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            for name, x, n, f in dprobs:
+                r, H, u = run_problem(M, torch, x, n, f)
+                r["problem"] = name
+                records.append(r)
+                del H, u
+        e1.record()
+        e1.synchronize()
+    barrier()
+    launches = M.kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    nprob = len(dprobs)
+    res = {"ms_total": ms, "records": records, "launches": launches, "clocks": clk.summary(), "nprob": nprob}
+
+    # FP64 MGM on the same problems (solve time; the paper's convention excludes setup)
+    fp64 = []
+    for name, x, n, f in dprobs:
+        r, H, u = run_problem(M, torch, x, n, f, precision="f64")
+        r["problem"] = name
+        fp64.append(r)
+        del H, u
+    res["fp64"] = fp64
+
+    # profiles on the sphere: V-cycle, finest sweep, outer SpMV (mixed), and the weights kernel
+    name, x, n, f = dprobs[0]
+    r, H, u = run_problem(M, torch, x, n, f)
+    res["profile"] = H.profile(reps=20)
+    res["stats"] = H.stats()
+    del H, u
+    # e2e: pinned host inputs -> device -> whole path -> solution back to the host
+    hp = [(torch.from_numpy(x).pin_memory(), torch.from_numpy(nn).pin_memory(), torch.from_numpy(f).pin_memory())
+          for _, x, nn, f in probs]
+    uh = torch.empty(a.size, dtype=torch.float64).pin_memory()
+    barrier()
+    e0.record()
+    h2d = d2h = 0
+    for xh, nh, fh in hp:
+        x = xh.to(dev, non_blocking=True); nn = nh.to(dev, non_blocking=True); f = fh.to(dev, non_blocking=True)
+        h2d += xh.numel() * 8 + nh.numel() * 8 + fh.numel() * 8
+        r, H, u = run_problem(M, torch, x, nn, f)
+        uh.copy_(u, non_blocking=True)
+        d2h += u.numel() * 8
+        del H
+    e1.record()
+    e1.synchronize()
+    res["e2e_ms"] = e0.elapsed_time(e1) / len(hp)
+    res["e2e_h2d"] = h2d // len(hp)
+    res["e2e_d2h"] = d2h // len(hp)
+    return res
+
+
+# ----------------------------------------------------------------------------------------------
+# oracle (CPU) timing on a bounded sample
+# ----------------------------------------------------------------------------------------------
+def oracle_sample(Ns):
+    import oracle as O
+    from paper_2204_06154_gb300 import inputs as I
+    x, nrm = I.fibonacci_sphere(Ns, jitter=0.1, seed=2)
+    f = I.random_sh_rhs(x, 20, 2)
+    t0 = time.perf_counter()
+    idx, w, L = O.build_operator(x, nrm, P["n"], "rbf", P["k"], P["ell"], P["mu"])
+    Hh = O.setup(x, L, P["n_min"], m=P["m"], seed=0)
+    u, it, rel = O.fgmres(L, Hh, f, tol=P["tol"], restart=P["restart"], maxit=P["maxit"])
+    dt = time.perf_counter() - t0
+    return dt * 1e3, it, rel
+
+
+def cpu_baseline(a, Ns=None):
+    Ns = Ns or a.cpu_sample
+    ms, it, rel = oracle_sample(Ns)
+    scaled = ms * (a.size / Ns)
+    return {"value": round(scaled, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"whole path (brute-force kNN, FP64 weights, hierarchy, MGM-FGMRES to 1e-10, {it} its) on a "
+                      f"{Ns:,}-point jittered Fibonacci sphere with the same parameters; {ms:.0f} ms measured, scaled "
+                      f"linearly by N to {a.size:,} (the oracle's brute-force parts grow faster, so this favours it)"}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        vals = []
+        for i in range(a.warmup + a.steps):
+            ms, it, rel = oracle_sample(a.cpu_sample)
+            if i >= a.warmup:
+                vals.append(ms * (a.size / a.cpu_sample))
+        v = statistics.mean(vals)
+        cb = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+              "sample": f"whole path on a {a.cpu_sample:,}-point sphere, scaled linearly by N to {a.size:,}"}
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms",
+                          "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(2 * v, 1),
+                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": config(a), "cpu_baseline": cb,
+                          "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+              flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res = bench_ours(a, rank, world, local_rank)
+    if rank != 0:
+        return
+    recs = res["records"]
+    K = a.steps
+    per_problem = res["ms_total"] / (K * res["nprob"])
+    mean = lambda key, rs=recs: statistics.mean(r[key] for r in rs)
+    solve_mixed = mean("solve_ms")
+    solve_fp64 = mean("solve_ms", res["fp64"])
+    pk, pk_kind = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    prof = res["profile"]
+    st = res["stats"]
+    # dominant kernel of the step: the FP64 stencil-weight solves (warp-per-stencil GEPP)
+    m = P["n"] + (P["ell"] + 1) * (P["ell"] + 2) // 2
+    flops_per_stencil = 2.0 * (m ** 3 - m) / 3.0
+    w_ms = mean("weights_ms")
+    w_gflops = a.size * flops_per_stencil / (w_ms * 1e-3) / 1e9
+    sweep_gbs = prof["sweep_bytes"] / (prof["sweep_ms"] * 1e-3) / 1e9 if prof["sweep_ms"] > 0 else None
+    vcyc_gbs = prof["vcycle_bytes"] / (prof["vcycle_ms"] * 1e-3) / 1e9
+    spmv_gbs = prof["spmv_bytes"] / (prof["spmv_ms"] * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": round(per_problem, 2), "unit": "ms", "n_gpus": world, "steps": K,
+        "warmup": a.warmup, "ms_per_step": round(res["ms_total"] / K, 2), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": config(a),
+        "phases_ms": {k: round(mean(k), 3) for k in ("knn_ms", "weights_ms", "assemble_ms", "setup_ms", "solve_ms")},
+        "solve_ms": {"mixed_f32_vcycle": round(solve_mixed, 3), "fp64_vcycle": round(solve_fp64, 3),
+                     "speedup": round(solve_fp64 / solve_mixed, 3)},
+        "iters": {"mixed": [r["iters"] for r in recs[: res["nprob"]]], "fp64": [r["iters"] for r in res["fp64"]]},
+        "rel_res_max": max(r["rel_res"] for r in recs + res["fp64"]),
+        "converged": all(r["converged"] for r in recs + res["fp64"]),
+        "roofline": {"kernel": "phs_weights_k (FP64 GEPP of the (n+L)^2 = 60^2 stencil systems)", "bound": "alu",
+                     "achieved": round(w_gflops, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                     "frac": round(w_gflops / FP64_PEAK_GFLOPS, 3), "traffic": None,
+                     "peak_source": "FP64 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"},
+        "vcycle_roofline": {"kernel": "row_kernel<1,float> (finest-level multicolour GS sweep)", "bound": "hbm",
+                            "achieved": round(sweep_gbs, 1) if sweep_gbs else None, "peak": hbm, "unit": "GB/s",
+                            "frac": round(sweep_gbs / hbm, 3) if sweep_gbs else None, "traffic": None,
+                            "bytes_per_launch": prof["sweep_bytes"] // max(prof["sweep_launches"], 1),
+                            "avg_launch_us": round(1e3 * prof["sweep_ms"] / max(prof["sweep_launches"], 1), 2),
+                            "launches_per_sweep": prof["sweep_launches"],
+                            "whole_vcycle": {"ms": round(prof["vcycle_ms"], 4), "GB/s": round(vcyc_gbs, 1),
+                                             "frac": round(vcyc_gbs / hbm, 3), "kernels": prof["vcycle_kernels"]},
+                            "outer_spmv_fp64": {"ms": round(prof["spmv_ms"], 4), "GB/s": round(spmv_gbs, 1),
+                                                "frac": round(spmv_gbs / hbm, 3)},
+                            "peak_source": pk_kind},
+        "hierarchy": {"n": st["n"], "nnz": st["nnz"], "ncolors": st["ncolors"], "device_MB": st["device_bytes"] >> 20},
+        "e2e": {"value": round(res["e2e_ms"], 2), "unit": "ms", "h2d_bytes_per_step": res["e2e_h2d"],
+                "d2h_bytes_per_step": res["e2e_d2h"]},
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+    }
+    if not a.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(a)
+    print(json.dumps(out), flush=True)
+
+
+def config(a):
+    return {"workload": f"sphere + torus, {a.size:,} points each, PHS r^3 + degree-3, n=50, -Lap+I, "
+                        f"random SH rhs l<=20, MGM V(1,1) MC-GS, FGMRES to 1e-10",
+            "problems_per_step": 2, "N": a.size, "n": P["n"], "ell": P["ell"], "n_min": P["n_min"],
+            "precision": "FP32 V-cycle / FP64 outer + FP64 setup", "l2": "inputs > L2 (no flush needed)"}
+
+
+if __name__ == "__main__":
+    main()

@@ -202,13 +202,42 @@ def sh_real(x: np.ndarray, l: int, m: int):
 
 
 def random_sh_rhs(x: np.ndarray, lmax: int = 20, seed: int = 2):
-    """f = sum_{l <= lmax, |m| <= l} a_lm Y_l^m(x/|x|), a_lm ~ N(0, 1) drawn in (l, m) order."""
+    """f = sum_{l <= lmax, |m| <= l} a_lm Y_l^m(x/|x|), a_lm ~ N(0, 1) drawn in (l, m) order.
+
+    Evaluated with the same normalised recurrence as sh_real_all but keeping only two Legendre
+    columns at a time, so memory stays O(N) for million-point clouds."""
     rng = np.random.default_rng(seed)
-    Y = sh_real_all(x, lmax)
-    f = np.zeros(x.shape[0])
+    a = {}
     for l in range(lmax + 1):
         for m in range(-l, l + 1):
-            f += rng.standard_normal() * Y[(l, m)]
+            a[(l, m)] = rng.standard_normal()
+    xn = x / np.linalg.norm(x, axis=1, keepdims=True)
+    ct = np.clip(xn[:, 2], -1.0, 1.0)
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    phi = np.arctan2(xn[:, 1], xn[:, 0])
+    f = np.zeros(x.shape[0])
+    pmm = np.full_like(ct, math.sqrt(1.0 / (4.0 * math.pi)))
+    for m in range(0, lmax + 1):
+        if m > 0:
+            pmm = -math.sqrt((2.0 * m + 1.0) / (2.0 * m)) * st * pmm
+        cm, sm = (np.cos(m * phi), np.sin(m * phi)) if m > 0 else (None, None)
+
+        def add(l, P):
+            if m == 0:
+                f.__iadd__(a[(l, 0)] * P)
+            else:
+                f.__iadd__(math.sqrt(2.0) * P * (a[(l, m)] * cm + a[(l, -m)] * sm))
+        add(m, pmm)
+        if m + 1 <= lmax:
+            p1 = math.sqrt(2.0 * m + 3.0) * ct * pmm
+            add(m + 1, p1)
+            p0 = pmm
+            for l in range(m + 2, lmax + 1):
+                aa = math.sqrt((4.0 * l * l - 1.0) / (l * l - m * m))
+                bb = math.sqrt(((l - 1.0) ** 2 - m * m) / (4.0 * (l - 1.0) ** 2 - 1.0))
+                p2 = aa * (ct * p1 - bb * p0)
+                add(l, p2)
+                p0, p1 = p1, p2
     return f
 
 

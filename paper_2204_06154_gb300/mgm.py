@@ -56,8 +56,15 @@ class HierStats(C.Structure):
 
 EXPORTS = ["mgm_knn", "mgm_stencil_weights", "mgm_assemble", "mgm_build_stencils", "mgm_coarsen", "mgm_interp",
            "mgm_transpose", "mgm_spgemm", "mgm_rcm", "mgm_color", "mgm_setup", "mgm_vcycle", "mgm_solve",
-           "mgm_hierarchy_stats_get", "mgm_hierarchy_level", "mgm_hierarchy_pnnz", "mgm_destroy",
-           "mgm_status_string", "mgm_last_error_message", "mgm_last_error_row"]
+           "mgm_hierarchy_stats_get", "mgm_hierarchy_level", "mgm_hierarchy_pnnz", "mgm_profile",
+           "mgm_kernel_launches", "mgm_destroy", "mgm_status_string", "mgm_last_error_message",
+           "mgm_last_error_row"]
+
+
+class ProfileInfo(C.Structure):
+    _fields_ = [("vcycle_ms", C.c_float), ("vcycle_bytes", C.c_int64), ("vcycle_kernels", C.c_int64),
+                ("sweep_ms", C.c_float), ("sweep_bytes", C.c_int64), ("sweep_launches", C.c_int32),
+                ("spmv_ms", C.c_float), ("spmv_bytes", C.c_int64)]
 
 
 def lib():
@@ -83,13 +90,17 @@ def lib():
         L.mgm_hierarchy_stats_get.argtypes = [P, C.POINTER(HierStats)]
         L.mgm_hierarchy_level.argtypes = [P, I] + [P] * 10 + [P]
         L.mgm_hierarchy_pnnz.argtypes = [P, I, C.POINTER(C.c_int64)]
+        L.mgm_profile.argtypes = [P, I, C.POINTER(ProfileInfo), P]
+        L.mgm_kernel_launches.argtypes = []
+        L.mgm_kernel_launches.restype = C.c_int64
         L.mgm_destroy.argtypes = [P]
         L.mgm_destroy.restype = None
         L.mgm_status_string.restype = C.c_char_p
         L.mgm_last_error_message.restype = C.c_char_p
         L.mgm_last_error_row.restype = C.c_int64
         for name in EXPORTS:
-            if name not in ("mgm_destroy", "mgm_status_string", "mgm_last_error_message", "mgm_last_error_row"):
+            if name not in ("mgm_destroy", "mgm_status_string", "mgm_last_error_message", "mgm_last_error_row",
+                            "mgm_kernel_launches"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -272,6 +283,13 @@ class Hierarchy:
             out["keep"] = keep
         return out
 
+    def profile(self, reps=20):
+        """Device time and algorithmic bytes of one V-cycle, one finest-level sweep and one outer
+        FP64 operator product (CUDA events; overwrites the hierarchy's work vectors)."""
+        pi = ProfileInfo()
+        _check(lib().mgm_profile(self._h, reps, C.byref(pi), _stream()))
+        return {k: getattr(pi, k) for k, _ in ProfileInfo._fields_}
+
     def vcycle(self, r):
         if r.dtype not in (torch.float32, torch.float64):
             raise TypeError("r must be float32 or float64")
@@ -291,6 +309,11 @@ class Hierarchy:
             _check(st)
         return u, {"iters": info.iters, "rel_res": info.rel_res, "solve_ms": info.solve_ms, "converged": st == 0,
                    "history": [hist[i] for i in range(info.iters + 1)]}
+
+
+def kernel_launches():
+    """Kernels launched by libmgm so far in this process."""
+    return int(lib().mgm_kernel_launches())
 
 
 def solve_points(xyz, nrm, f, n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, n_min=250, m=3, precision="f32",
