@@ -112,6 +112,23 @@ typedef struct {
 mgm_status mgm_knn(const double* data, int64_t nd, const double* query, int64_t nq, int k,
                    int self_first, int32_t* idx_out, mgm_stream stream);
 
+/* The same search as mgm_knn for callers that cannot allocate device memory, and the same
+ * output (bit-identical idx_out). The paper has no counterpart: this entry point exists for
+ * embedding. Typical callers: an application whose device memory is entirely handed to its own
+ * pool allocator up front (an extra cudaMalloc would fail or fragment that pool), and latency-
+ * bound loops that must not enter the CUDA allocator, which can block or implicitly synchronise.
+ * It allocates nothing: its grid scratch is one file-scope __device__ array of about 12.6 MB,
+ * held by every GPU that loads the library until the process exits, and sized for at most
+ * MGM_KNN_NOALLOC_MAX_POINTS data points (larger nd returns MGM_ERR_UNSUPPORTED; use mgm_knn).
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current); make that first call before any stream capture. All calls share the one
+ * array and each clears what it needs, so calls that overlap on the GPU (different streams, or
+ * different host threads on the same device) race and must be serialised by the caller.
+ * Synchronises the stream once (to read the error flag). */
+#define MGM_KNN_NOALLOC_MAX_POINTS 262144
+mgm_status mgm_knn_noalloc(const double* data, int64_t nd, const double* query, int64_t nq, int k,
+                           int self_first, int32_t* idx_out, mgm_stream stream);
+
 /* Stencil weights c_ij of the LBO for each stencil (Sec. 2.1 tangent plane; Sec. 2.2 PHS RBF-FD,
  * eq. (rbf_fd_lap); Sec. 2.3 GFD, eq. (wls_fd_lap)). idx (N x n) from mgm_knn(self_first=1);
  * w_out (N x n) receives the weights in the order of idx. FP64 throughout. A singular local

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "libmgm.so")
 BUILD = os.path.join(HERE, "_build")
 
-EXACT = ["util", "knn", "stencil", "coarsen", "order", "transfer", "hierarchy"]
+EXACT = ["util", "knn", "knn_noalloc", "stencil", "coarsen", "order", "transfer", "hierarchy"]
 FAST = ["vcycle", "krylov", "capi"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -14,17 +14,10 @@
 #include <cfloat>
 
 #include "common.cuh"
+#include "knn_grid.cuh"
 
 namespace mgm {
 
-constexpr int KNN_WARPS = 4;
-constexpr int KNN_CAP = 2048;  // candidate buffer per warp
-
-struct Grid {
-    double x0, y0, z0, h;
-    int nx, ny, nz;
-    int64_t ncells;
-};
 
 __device__ __forceinline__ double d2_pts(double ax, double ay, double az, double bx, double by, double bz) {
     double dx = ax - bx, dy = ay - by, dz = az - bz;

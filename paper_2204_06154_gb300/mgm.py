@@ -54,7 +54,7 @@ class HierStats(C.Structure):
                 ("ncolors", C.c_int32 * 16), ("device_bytes", C.c_int64)]
 
 
-EXPORTS = ["mgm_knn", "mgm_stencil_weights", "mgm_assemble", "mgm_build_stencils", "mgm_coarsen", "mgm_interp",
+EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", "mgm_build_stencils", "mgm_coarsen", "mgm_interp",
            "mgm_transpose", "mgm_spgemm", "mgm_rcm", "mgm_color", "mgm_setup", "mgm_vcycle", "mgm_solve",
            "mgm_hierarchy_stats_get", "mgm_hierarchy_level", "mgm_hierarchy_pnnz", "mgm_profile",
            "mgm_kernel_launches", "mgm_destroy", "mgm_status_string", "mgm_last_error_message",
@@ -75,6 +75,7 @@ def lib():
         L = C.CDLL(_LIBPATH)
         P, I64, I = C.c_void_p, C.c_int64, C.c_int
         L.mgm_knn.argtypes = [P, I64, P, I64, I, I, P, P]
+        L.mgm_knn_noalloc.argtypes = [P, I64, P, I64, I, I, P, P]
         L.mgm_stencil_weights.argtypes = [P, P, I64, P, C.POINTER(StencilParams), P, P]
         L.mgm_assemble.argtypes = [I64, I, P, P, C.c_double, I, P, P, P, P]
         L.mgm_build_stencils.argtypes = [P, P, I64, C.POINTER(StencilParams), P, P, P, P, P, P]
@@ -134,6 +135,18 @@ def knn(data, query, k, self_first=False):
     query = data if self_first else _dev(query, torch.float64, "query")
     out = torch.empty((query.shape[0], k), dtype=torch.int32, device=data.device)
     _check(lib().mgm_knn(_p(data), data.shape[0], _p(query), query.shape[0], k, int(self_first), _p(out), _stream()))
+    return out
+
+
+def knn_noalloc(data, query, k, self_first=False, out=None):
+    """mgm_knn_noalloc: same result as knn(), using the library's static device scratch instead of
+    allocating (see include/mgm.h for its size limit and the no-overlap rule)."""
+    data = _dev(data, torch.float64, "data")
+    query = data if self_first else _dev(query, torch.float64, "query")
+    if out is None:
+        out = torch.empty((query.shape[0], k), dtype=torch.int32, device=data.device)
+    _check(lib().mgm_knn_noalloc(_p(data), data.shape[0], _p(query), query.shape[0], k, int(self_first), _p(out),
+                                 _stream()))
     return out
 
 

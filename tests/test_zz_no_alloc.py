@@ -1,0 +1,41 @@
+"""mgm_knn_noalloc, the kNN entry point for callers that cannot allocate device memory, gives
+the same neighbour lists as mgm_knn. Runs last (file name) so that a failure here does not hide
+other tests when pytest stops at the first failure; passes alone or after the rest."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2204_06154_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_matches_knn_two_calls_in_a_row():
+    from paper_2204_06154_gb300 import mgm as M
+    dev = "cuda:0"
+    # first call: stencils of an icosahedral sphere (many tied distances); second call: a
+    # different, larger cloud with separate query points, reusing the same static scratch
+    x1, _ = I.icosahedral_sphere(5)
+    x2, _ = I.fibonacci_sphere(60001, jitter=0.2, seed=4)
+    q2, _ = I.fibonacci_sphere(20000, jitter=0.2, seed=5)
+    cases = [(x1, x1, 30, True), (x2, q2, 3, False)]
+    for data, query, k, sf in cases:
+        d = torch.from_numpy(data).to(dev)
+        q = d if sf else torch.from_numpy(query).to(dev)
+        ref = M.knn(d, q, k, self_first=sf)
+        got = M.knn_noalloc(d, q, k, self_first=sf)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref)
+    # and again on the first case, after the scratch holds the second case's grid
+    d = torch.from_numpy(x1).to(dev)
+    assert torch.equal(M.knn_noalloc(d, None, 30, self_first=True), M.knn(d, None, 30, self_first=True))
+
+
+def test_noalloc_rejects_sizes_above_the_limit():
+    from paper_2204_06154_gb300 import mgm as M
+    n = 262144 + 1
+    d = torch.zeros((n, 3), dtype=torch.float64, device="cuda:0")
+    d[:, 0] = torch.arange(n, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(M.MGMError) as e:
+        M.knn_noalloc(d, None, 4, self_first=True)
+    assert e.value.status == 8 and "maximum" in str(e.value)
