@@ -66,7 +66,7 @@ typedef struct {
 
 /* Multilevel parameters (Sec. 4; Table 1). */
 typedef struct {
-    int64_t n_min;   /* minimum coarsest size N_min (Alg. 2 line 4), >= 1 */
+    int64_t n_min;   /* minimum coarsest size N_min (Alg. 2), >= 1 */
     int m;           /* interpolation stencil size (Sec. 3), 1 <= m <= 8; the paper uses 3 */
     int nu1, nu2;    /* pre- and post-smoothing sweeps, 0 <= nu <= 8 */
     int precision;   /* MGM_F32 (V-cycle in FP32, coarsest solve FP64) or MGM_F64 */
@@ -92,7 +92,7 @@ typedef struct {
 typedef struct mgm_hierarchy mgm_hierarchy; /* opaque, library-owned */
 
 typedef struct {
-    int p;                  /* number of levels (Alg. 2 line 4) */
+    int p;                  /* number of levels (Alg. 2) */
     int precision;
     int64_t n[16];          /* N_j, j = 0..p-1 (0 = finest) */
     int64_t nnz[16];        /* nnz of L_j */
@@ -104,8 +104,8 @@ typedef struct {
 /* Discretisation (Sec. 2)                                                                       */
 /* ------------------------------------------------------------------------------------------- */
 
-/* k nearest data points of each query point by Euclidean distance in R^3 (Sec. 2: stencils are
- * "the n_i nearest neighbor nodes"; Sec. 3: the m nearest coarse nodes). Output idx_out (nq x k,
+/* k nearest data points of each query point by Euclidean distance in R^3 (Sec. 2: a stencil is
+ * its centre's n nearest nodes; Sec. 3: the m nearest coarse nodes). Output idx_out (nq x k,
  * row-major) lists them by ascending (d^2, index), d^2 = (dx*dx + dy*dy) + dz*dz in FP64 without
  * contraction. self_first != 0 requires query == data and puts query q itself first (the stencil
  * centre). Requires 1 <= k <= min(nd, 256), nd, nq < 2^31. */
@@ -170,7 +170,7 @@ mgm_status mgm_interp(const double* xf, int64_t Nf, const double* xc, int64_t Nc
                       int32_t* rowptr_out, int32_t* col_out, double* val_out, int64_t* nnz_out,
                       mgm_stream stream);
 
-/* CSR transpose (restriction I_h^H = (I_H^h)^T, Sec. 3; Alg. 2 line 8): rows x cols -> cols x rows,
+/* CSR transpose (restriction I_h^H = (I_H^h)^T, Sec. 3; Alg. 2): rows x cols -> cols x rows,
  * columns ascending. trowptr (ncols+1), tcol/tval (nnz). */
 mgm_status mgm_transpose(int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* col,
                          const double* val, int32_t* trowptr, int32_t* tcol, double* tval, mgm_stream stream);
@@ -185,7 +185,7 @@ mgm_status mgm_spgemm(int64_t nA, int64_t nB, int64_t ncolsB, const int32_t* a_r
                       const int32_t* b_rowptr, const int32_t* b_col, const double* b_val,
                       int32_t* c_rowptr, int32_t* c_col, double* c_val, int64_t* nnz_out, mgm_stream stream);
 
-/* Reverse Cuthill-McKee ordering (Sec. 4.2; Alg. 2 lines 2, 10) of the symmetrised pattern of a
+/* Reverse Cuthill-McKee ordering (Sec. 4.2; Alg. 2) of the symmetrised pattern of a
  * square CSR matrix: perm_out[new] = old. Start node of each component: minimum degree, lowest
  * index; neighbours enqueued in increasing (degree, index). Synchronises once per BFS level. */
 mgm_status mgm_rcm(int64_t N, const int32_t* rowptr, const int32_t* col, int32_t* perm_out, mgm_stream stream);

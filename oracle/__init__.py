@@ -222,7 +222,7 @@ def permute(A, perm):
 
 
 def num_levels(N1, n_min):
-    """p = floor(log(N1/N_min)/log 4) + 1 (Alg. 2 line 4), evaluated exactly in integers as
+    """p = floor(log(N1/N_min)/log 4) + 1 (Alg. 2, number of levels), evaluated exactly in integers as
     1 + the largest t with N_min * 4**t <= N1 (so N_min <= N_p < 4 N_min)."""
     if N1 < n_min:
         return 1
@@ -304,10 +304,10 @@ class Hierarchy:
 
 def setup(xyz, L1, n_min, m=3, seed=0, smoother="mc", nu1=1, nu2=1, wse_mode=1):
     """MGM preprocessing (Alg. 2), in the paper's order:
-    RCM of L_1 and X_1 (lines 2-3); p (line 4); for each level: WSE coarsening to floor(N_1/4^j)
-    points (line 6), interpolation (line 7), restriction = transpose (line 8), Galerkin product
-    (line 9, eq. (galerkin) operand order), RCM of L_{j+1} and the matching reordering of the
-    coarse index of the transfers (lines 10-11); LU of L_p (line 13). Colourings for the
+    RCM of L_1 and X_1; the number of levels p; for each level: WSE coarsening to
+    floor(N_1/4^j) points, interpolation, restriction = transpose, Galerkin product (operand
+    order of eq. (galerkin)), RCM of L_{j+1} and the matching reordering of the coarse index of
+    the transfers; finally the LU factors of L_p. Colourings for the
     multicolour smoother are computed on the final (RCM-ordered) level operators."""
     H = Hierarchy(smoother=smoother, nu1=nu1, nu2=nu2)
     N1 = L1.shape[0]

@@ -40,8 +40,8 @@ static double dist2(const double* a, const double* b) {
 static int key_less(double d, int64_t j, double e, int64_t k) { return d < e || (d == e && j < k); }
 
 /* ===========================================================================================
- * Nearest neighbours (Sec. 2: "the n_i nearest neighbor nodes ... Euclidean distance in R^3";
- * Sec. 3: the m nearest coarse nodes of a fine node). Brute force over all data points.
+ * Nearest neighbours (Sec. 2: a stencil is its centre's n nearest nodes by Euclidean distance in
+ * the embedding space; Sec. 3: the m nearest coarse nodes of a fine node). Brute force.
  * Order: ascending (d^2, index). With self_first, query q is also data point q and is placed
  * first (the stencil centre) regardless of duplicates.
  * =========================================================================================== */
@@ -684,7 +684,7 @@ int or_interp(const double* xf, int64_t Nf, const double* xc, int64_t Nc, int m,
 }
 
 /* ===========================================================================================
- * Restriction I_h^H = (I_H^h)^T (Sec. 3; Alg. 2 line 8): CSR transpose, columns ascending.
+ * Restriction I_h^H = (I_H^h)^T (Sec. 3; Alg. 2): CSR transpose, columns ascending.
  * =========================================================================================== */
 int or_transpose(int64_t nrows, int64_t ncols, const int32_t* rowptr, const int32_t* col, const double* val,
                  int32_t* trowptr, int32_t* tcol, double* tval) {
@@ -750,7 +750,7 @@ int or_spgemm(int64_t nA, int64_t ncolsB, const int32_t* ap, const int32_t* ac, 
 }
 
 /* ===========================================================================================
- * Dense LU with partial pivoting of the coarsest operator (Sec. 4.3; Alg. 2 line 13) and the
+ * Dense LU with partial pivoting of the coarsest operator (Sec. 4.3; Alg. 2) and the
  * corresponding solve. a (n x n row-major) is overwritten by L\U, piv[k] = row swapped with k.
  * =========================================================================================== */
 int or_lu_factor(double* a, int64_t n, int32_t* piv) {
@@ -836,29 +836,29 @@ int or_vcycle(const or_level* lv, int p, const double* lu, const int32_t* piv, c
     double** r = (double**)calloc(p, sizeof(double*));
     double* tmp = (double*)malloc(sizeof(double) * n1);
     for (int j = 0; j < p; ++j) { e[j] = (double*)calloc(lv[j].n, sizeof(double)); r[j] = (double*)calloc(lv[j].n, sizeof(double)); }
-    /* line 3: reorder f and u */
+    /* reorder f and u by the RCM ordering of L_1 */
     for (int64_t i = 0; i < n1; ++i) { int64_t o = perm1 ? perm1[i] : i; r[0][i] = fin[o]; e[0][i] = uio[o]; }
-    /* line 4: presmooth; line 5: r^2 = I_1^2 (f^1 - L_1 u^1) */
+    /* presmooth the initial guess; r^2 = I_1^2 (f^1 - L_1 u^1) */
     for (int s = 0; s < nu1; ++s) or_gs_sweep(&lv[0], r[0], e[0]);
     residual(&lv[0], r[0], e[0], tmp);
     csr_apply(lv[1].n, lv[0].rrp, lv[0].rc, lv[0].rv, tmp, r[1]);
-    /* lines 6-9 */
+    /* levels 2 .. p-1: presmooth the defect from zero, compute and restrict its residual */
     for (int j = 1; j < p - 1; ++j) {
         for (int64_t i = 0; i < lv[j].n; ++i) e[j][i] = 0.0;
         for (int s = 0; s < nu1; ++s) or_gs_sweep(&lv[j], r[j], e[j]);
         residual(&lv[j], r[j], e[j], tmp);
         csr_apply(lv[j + 1].n, lv[j].rrp, lv[j].rc, lv[j].rv, tmp, r[j + 1]);
     }
-    /* line 10: coarsest solve */
+    /* coarsest defect by the LU factors of L_p */
     for (int64_t i = 0; i < lv[p - 1].n; ++i) e[p - 1][i] = r[p - 1][i];
     or_lu_solve(lu, lv[p - 1].n, piv, e[p - 1]);
-    /* lines 11-14, then 15-16 on level 1 */
+    /* interpolate / correct and post-smooth on levels p-1 .. 2, then on level 1 */
     for (int j = p - 2; j >= 0; --j) {
         csr_apply(lv[j].n, lv[j].pp, lv[j].pc, lv[j].pv, e[j + 1], tmp);
         for (int64_t i = 0; i < lv[j].n; ++i) e[j][i] = e[j][i] + tmp[i];
         for (int s = 0; s < nu2; ++s) or_gs_sweep(&lv[j], r[j], e[j]);
     }
-    /* line 17: undo the reordering */
+    /* undo the RCM reordering */
     for (int64_t i = 0; i < n1; ++i) { int64_t o = perm1 ? perm1[i] : i; uio[o] = e[0][i]; }
     for (int j = 0; j < p; ++j) { free(e[j]); free(r[j]); }
     free(e); free(r); free(tmp);

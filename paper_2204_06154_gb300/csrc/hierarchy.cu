@@ -1,10 +1,10 @@
 // MGM preprocessing on the device (paper Alg. 2) and the solve-order layouts the V-cycle runs on.
 //
-// Order of operations follows Alg. 2: RCM of L_1 and reordering of X_1 (lines 2-3); number of
-// levels (line 4); per level: weighted sample elimination to floor(N_1/4^j) points (line 6), PHS
-// interpolation (line 7), restriction = transpose (line 8), Galerkin product L_{j+1} = R (L_j P)
-// (line 9, operand order of eq. (galerkin)), RCM of L_{j+1} with the matching renumbering of the
-// coarse index of the transfers (lines 10-11); and the coarsest factorisation (line 13; an
+// Order of operations follows Alg. 2: RCM of L_1 and reordering of X_1; number of levels; per
+// level: weighted sample elimination to floor(N_1/4^j) points, PHS interpolation, restriction =
+// transpose, Galerkin product L_{j+1} = R (L_j P) (operand order of eq. (galerkin)), RCM of
+// L_{j+1} with the matching renumbering of the coarse index of the transfers; and the coarsest
+// factorisation (an
 // explicit FP64 inverse by Gauss-Jordan elimination, so the coarsest solve is one matrix-vector
 // product per cycle). Then, for the multicolour smoother: colourings of the RCM-ordered level
 // operators, the colour-grouped solve orders, and FP32/FP64 copies of operators and transfers.
@@ -370,7 +370,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     H->p = p;
     H->lv.resize(p);
     const int64_t nnz = csr_nnz(rp, N, s);
-    {   // level 1: RCM of L_1 and X_1 (Alg. 2 lines 2-3)
+    {   // level 1: RCM of L_1 and X_1 (Alg. 2)
         Level& L = H->lv[0];
         L.n = N;
         L.nnz = nnz;
@@ -389,16 +389,16 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         const int64_t NH = N / ((int64_t)1 << (2 * j));
         C.n = NH;
         C.keep.alloc(NH);
-        coarsen(F.X.get(), F.n, NH, C.keep.get(), s, nullptr);              // line 6
+        coarsen(F.X.get(), F.n, NH, C.keep.get(), s, nullptr);              // coarse point cloud
         Temp<double> Xc(3 * NH, s);
         gather_xyz(F.X.get(), C.keep.get(), Xc.get(), NH, s);
         Temp<int32_t> P_rp(F.n + 1, s), P_ci(F.n * prm->m, s);
         Temp<double> P_v(F.n * prm->m, s);
-        int64_t pnnz = interp(F.X.get(), F.n, Xc.get(), NH, prm->m, P_rp.get(), P_ci.get(), P_v.get(), s);  // line 7
+        int64_t pnnz = interp(F.X.get(), F.n, Xc.get(), NH, prm->m, P_rp.get(), P_ci.get(), P_v.get(), s);  // interpolation
         Temp<int32_t> R_rp(NH + 1, s), R_ci(std::max<int64_t>(pnnz, 1), s);
         Temp<double> R_v(std::max<int64_t>(pnnz, 1), s);
-        csr_transpose(F.n, NH, P_rp.get(), P_ci.get(), P_v.get(), R_rp.get(), R_ci.get(), R_v.get(), s);  // line 8
-        // line 9: L_{j+1} = R (L_j P)
+        csr_transpose(F.n, NH, P_rp.get(), P_ci.get(), P_v.get(), R_rp.get(), R_ci.get(), R_v.get(), s);  // restriction
+        // Galerkin operator L_{j+1} = R (L_j P)
         Temp<int32_t> T_rp(F.n + 1, s);
         int64_t tnnz = spgemm_symbolic(F.n, F.rp.get(), F.ci.get(), P_rp.get(), P_ci.get(), T_rp.get(), s);
         Temp<int32_t> T_ci(std::max<int64_t>(tnnz, 1), s);
@@ -411,7 +411,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         Temp<double> G_v(std::max<int64_t>(gnnz, 1), s);
         spgemm_numeric(NH, R_rp.get(), R_ci.get(), R_v.get(), T_rp.get(), T_ci.get(), T_v.get(), G_rp.get(), G_ci.get(),
                        G_v.get(), s);
-        // lines 10-11: RCM of L_{j+1}; renumber coarse points and the interpolation's columns
+        // RCM of L_{j+1}; renumber coarse points and the interpolation's columns
         C.perm.alloc(NH);
         rcm(NH, G_rp.get(), G_ci.get(), C.perm.get(), s);
         C.X.alloc(3 * NH);
@@ -444,7 +444,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     if (p == 1) build_solve_layout(H->lv[0], true, s);  // one group: serves the outer operator only
     for (int j = 0; j + 1 < p; ++j)
         build_transfers(H->lv[j], (j + 2 < p) ? &H->lv[j + 1] : nullptr, H->lv[j + 1].n, prm->m, s);
-    // coarsest (line 13)
+    // coarsest factorisation
     H->np = H->lv[p - 1].n;
     dense_inverse(H->lv[p - 1], H->Ainv, s);
     // caller index of each level-0 solve row

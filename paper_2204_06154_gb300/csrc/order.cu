@@ -1,4 +1,4 @@
-// Orderings of a level operator: reverse Cuthill-McKee (paper Sec. 4.2; Alg. 2 lines 2 and 10)
+// Orderings of a level operator: reverse Cuthill-McKee (paper Sec. 4.2; Alg. 2)
 // and the multicolouring used by the multicolour Gauss-Seidel smoother.
 //
 // RCM on the GPU: a level-synchronous breadth-first search that reproduces the sequential

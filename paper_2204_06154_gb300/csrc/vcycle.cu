@@ -181,7 +181,7 @@ static void sweep(Level& L, bool from_zero, cudaStream_t s) {
 template <class T>
 static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
     const int p = H->p;
-    for (int j = 0; j + 1 < p; ++j) {  // lines 4-9
+    for (int j = 0; j + 1 < p; ++j) {  // pre-smoothing and restricted residuals
         Level& L = H->lv[j];
         Level& C = H->lv[j + 1];
         const T* rsrc;
@@ -198,12 +198,12 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
         restrict_k<T><<<grid_for(C.n, 256), 256, 0, s>>>(L.r_rp.get(), L.r_ci.get(), LV<T>::rv(L), rsrc, LV<T>::b(C), C.n);
         CK_LAUNCH();
     }
-    {   // line 10
+    {   // coarsest defect
         Level& C = H->lv[p - 1];
         coarse_k<T><<<grid_for(C.n * 32, 256), 256, 0, s>>>(H->Ainv.get(), LV<T>::b(C), LV<T>::e(C), C.n);
         CK_LAUNCH();
     }
-    for (int j = p - 2; j >= 0; --j) {  // lines 11-16
+    for (int j = p - 2; j >= 0; --j) {  // interpolate / correct, post-smooth
         Level& L = H->lv[j];
         Level& C = H->lv[j + 1];
         interp_k<T><<<grid_for(L.n, 256), 256, 0, s>>>(L.pc.get(), LV<T>::pv(L), L.pw, LV<T>::e(C), LV<T>::e(L), L.n);

@@ -26,8 +26,9 @@ def _rand_sphere(N, seed):
 # Weighted sample elimination (Sec. 4.1)
 # ----------------------------------------------------------------------------------------------
 def _py_wse(x, NH, mode):
-    """Brute-force restatement of the elimination rule on tiny inputs: weights are recomputed
-    from scratch after every removal (the oracle updates them incrementally in mode 0)."""
+    """Brute-force restatement of the elimination rule on tiny inputs: every live weight is
+    recomputed from scratch before each removal (the oracle recomputes only the neighbours of
+    the removed point)."""
     N = len(x)
 
     def d2(a, b):
@@ -137,7 +138,7 @@ def test_wse_rounds_quality_vs_sequential(oracle):
 
 
 def test_level_count_closed_form(oracle):
-    """Alg. 2 line 4: p = floor(log(N_1/N_min)/log 4) + 1, so N_min <= floor(N_1/4^(p-1)) < 4 N_min."""
+    """Alg. 2 (number of levels): p = floor(log(N_1/N_min)/log 4) + 1, so N_min <= floor(N_1/4^(p-1)) < 4 N_min."""
     for N1, nmin in [(10242, 125), (10242, 250), (1048576, 250), (4194304, 250), (2621442, 250), (1000, 250), (999, 250)]:
         p = oracle.num_levels(N1, nmin)
         assert p == math.floor(math.log(N1 / nmin) / math.log(4) + 1e-12) + 1
