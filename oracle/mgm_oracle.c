@@ -74,8 +74,9 @@ int or_knn(const double* data, int64_t nd, const double* query, int64_t nq, int 
 /* ===========================================================================================
  * Dense solve by Gaussian elimination with partial pivoting on the augmented m x (m+1) matrix
  * (row-major, last column = right-hand side). Pivot: largest |a_ik|, first row on ties.
- * Update a_ij <- fma(-l_ik, a_kj, a_ij). Back substitution column by column. The system is
- * declared singular when the pivot magnitude is <= tol.
+ * Multipliers l_ik = a_ik * (1/a_kk) (one reciprocal per pivot, as in LAPACK's unblocked LU; the
+ * paper does not fix the local solver); update a_ij <- fma(-l_ik, a_kj, a_ij). Back substitution
+ * column by column. The system is declared singular when the pivot magnitude is <= tol.
  * =========================================================================================== */
 static int gepp_solve(double* a, int m, double tol, double* x) {
     const int ld = m + 1;
@@ -89,8 +90,9 @@ static int gepp_solve(double* a, int m, double tol, double* x) {
         if (!(best > tol)) return OR_ERR_SINGULAR;
         if (piv != k)
             for (int j = 0; j < ld; ++j) { double t = a[k * ld + j]; a[k * ld + j] = a[piv * ld + j]; a[piv * ld + j] = t; }
+        double rinv = 1.0 / a[k * ld + k];
         for (int i = k + 1; i < m; ++i) {
-            double l = a[i * ld + k] / a[k * ld + k];
+            double l = a[i * ld + k] * rinv;
             for (int j = k + 1; j < ld; ++j) a[i * ld + j] = fma(-l, a[k * ld + j], a[i * ld + j]);
         }
     }
@@ -179,7 +181,7 @@ static double phs_lap(double r2, int k) {
  * PHS RBF-FD weights for the LBO (Sec. 2.2, eq. (rbf_fd_lap)): for each stencil solve
  *   [A P; P^T 0][c; lambda] = [Lap phi; Lap p]
  * with A_ij = |xh_i - xh_j|^(2k+1), P_ij = p_j(xh_i), in tangent-plane coordinates scaled by the
- * stencil support s (xh / s); the weights for the unscaled Laplacian are c / s^2 (PHS with
+ * stencil support s (xh * (1/s)); the weights for the unscaled Laplacian are c / s^2 (PHS with
  * polynomials of degree >= k is scale-invariant). Singular when a pivot is <= 1e-13 max|M|.
  * =========================================================================================== */
 int or_phs_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, int n, int k, int ell,
@@ -197,7 +199,8 @@ int or_phs_weights(const double* xyz, const double* nrm, int64_t N, const int32_
         const int32_t* id = idx + i * n;
         double s = project_stencil(xyz, nrm, i, id, n, xh, yh);
         if (!(s > 0.0)) { g_bad_row = i; free(a); return OR_ERR_SINGULAR; }
-        for (int j = 0; j < n; ++j) { xh[j] = xh[j] / s; yh[j] = yh[j] / s; }
+        double sinv = 1.0 / s;
+        for (int j = 0; j < n; ++j) { xh[j] = xh[j] * sinv; yh[j] = yh[j] * sinv; }
         const int ld = m + 1;
         double amax = 0.0;
         for (int r = 0; r < n; ++r) {

@@ -10,6 +10,9 @@
 // operators, the colour-grouped solve orders, and FP32/FP64 copies of operators and transfers.
 // Built with --fmad=false (the integer decisions and FP64 setup values are bit-reproducible).
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <memory>
 
 #include "hier.cuh"
@@ -347,6 +350,23 @@ __global__ void compose_k(const int32_t* a, const int32_t* b, int64_t n, int32_t
 }
 
 // ------------------------------ setup driver ---------------------------------------------------
+// With MGM_TRACE set in the environment, setup synchronises at each phase boundary and prints the
+// phase's wall time to stderr (tracing only; off by default, no effect on results).
+struct Trace {
+    bool on;
+    cudaStream_t s;
+    std::chrono::steady_clock::time_point t;
+    explicit Trace(cudaStream_t st) : on(std::getenv("MGM_TRACE") != nullptr), s(st), t(std::chrono::steady_clock::now()) {}
+    void mark(const char* what, int level) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        auto now = std::chrono::steady_clock::now();
+        double ms = std::chrono::duration<double, std::milli>(now - t).count();
+        std::fprintf(stderr, "[mgm setup] level %d %-12s %9.3f ms\n", level, what, ms);
+        t = now;
+    }
+};
+
 mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int32_t* ci, const double* v,
                      const mgm_params* prm, cudaStream_t s) {
     REQUIRE(prm != nullptr, "null params");
@@ -370,6 +390,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     H->p = p;
     H->lv.resize(p);
     const int64_t nnz = csr_nnz(rp, N, s);
+    Trace tr(s);
     {   // level 1: RCM of L_1 and X_1 (Alg. 2)
         Level& L = H->lv[0];
         L.n = N;
@@ -382,6 +403,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         L.ci.alloc(nnz);
         L.v.alloc(nnz);
         csr_permute(N, rp, ci, v, L.perm.get(), L.rp.get(), L.ci.get(), L.v.get(), s);
+        tr.mark("rcm+permute", 0);
     }
     for (int j = 1; j < p; ++j) {
         Level& F = H->lv[j - 1];
@@ -390,11 +412,13 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         C.n = NH;
         C.keep.alloc(NH);
         coarsen(F.X.get(), F.n, NH, C.keep.get(), s, nullptr);              // coarse point cloud
+        tr.mark("coarsen", j);
         Temp<double> Xc(3 * NH, s);
         gather_xyz(F.X.get(), C.keep.get(), Xc.get(), NH, s);
         Temp<int32_t> P_rp(F.n + 1, s), P_ci(F.n * prm->m, s);
         Temp<double> P_v(F.n * prm->m, s);
         int64_t pnnz = interp(F.X.get(), F.n, Xc.get(), NH, prm->m, P_rp.get(), P_ci.get(), P_v.get(), s);  // interpolation
+        tr.mark("interp", j);
         Temp<int32_t> R_rp(NH + 1, s), R_ci(std::max<int64_t>(pnnz, 1), s);
         Temp<double> R_v(std::max<int64_t>(pnnz, 1), s);
         csr_transpose(F.n, NH, P_rp.get(), P_ci.get(), P_v.get(), R_rp.get(), R_ci.get(), R_v.get(), s);  // restriction
@@ -411,6 +435,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         Temp<double> G_v(std::max<int64_t>(gnnz, 1), s);
         spgemm_numeric(NH, R_rp.get(), R_ci.get(), R_v.get(), T_rp.get(), T_ci.get(), T_v.get(), G_rp.get(), G_ci.get(),
                        G_v.get(), s);
+        tr.mark("galerkin", j);
         // RCM of L_{j+1}; renumber coarse points and the interpolation's columns
         C.perm.alloc(NH);
         rcm(NH, G_rp.get(), G_ci.get(), C.perm.get(), s);
@@ -431,6 +456,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         remap_cols_k<<<grid_for(F.n, 256), 256, 0, s>>>(P_rp.get(), P_ci.get(), P_v.get(), cinv.get(), F.n, F.P_ci.get(),
                                                       F.P_v.get());
         CK_LAUNCH();
+        tr.mark("rcm+permute", j);
     }
     // colourings, solve orders, transfers
     for (int j = 0; j + 1 < p; ++j) {
@@ -439,14 +465,18 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         int32_t nc = 0;
         color(L.n, L.rp.get(), L.ci.get(), prm->seed, L.colour.get(), &nc, s);
         L.ncolors = nc;
+        tr.mark("colour", j);
         build_solve_layout(L, false, s);
+        tr.mark("layout", j);
     }
     if (p == 1) build_solve_layout(H->lv[0], true, s);  // one group: serves the outer operator only
     for (int j = 0; j + 1 < p; ++j)
         build_transfers(H->lv[j], (j + 2 < p) ? &H->lv[j + 1] : nullptr, H->lv[j + 1].n, prm->m, s);
+    tr.mark("transfers", -1);
     // coarsest factorisation
     H->np = H->lv[p - 1].n;
     dense_inverse(H->lv[p - 1], H->Ainv, s);
+    tr.mark("coarse-inv", p - 1);
     // caller index of each level-0 solve row
     H->ord_caller.alloc(N);
     compose_k<<<grid_for(N, 256), 256, 0, s>>>(H->lv[0].perm.get(), H->lv[0].ord.get(), N, H->ord_caller.get());

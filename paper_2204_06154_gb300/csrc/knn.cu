@@ -139,12 +139,17 @@ static void build_grid(const double* x, int64_t n, int64_t cells, double h_min, 
 }
 
 // ------------------------------ kNN -----------------------------------------------------------
-__device__ __forceinline__ bool key_lt(double a, int ia, double b, int ib) { return a < b || (a == b && ia < ib); }
+// Candidate keys are integers: the bit pattern of a non-negative double orders like its value, so
+// key = bits(d^2) + 1 (0 for the query itself when it is the stencil centre) ranks exactly as
+// (d^2, index) with integer compares, which GB300 executes far faster than FP64 compares.
+typedef unsigned long long ukey;
+__device__ __forceinline__ bool key_lt(ukey a, int ia, ukey b, int ib) { return a < b || (a == b && ia < ib); }
+__device__ __forceinline__ ukey d2_key(double d2) { return (ukey)__double_as_longlong(d2) + 1ull; }
 
 // Keep only the k smallest keys of the buffer (stable, in place). A candidate outside the k
 // smallest of a subset can never enter the k smallest of the full set, so this loses nothing.
-__device__ int knn_compact(double* bd, int* bi, int count, int k, int lane) {
-    double td = 0.0;
+__device__ int knn_compact(ukey* bd, int* bi, int count, int k, int lane) {
+    ukey td = 0;
     int tj = 0;
     bool found = false;
     for (int t = lane; t < count; t += 32) {
@@ -160,7 +165,7 @@ __device__ int knn_compact(double* bd, int* bi, int count, int k, int lane) {
     for (int base = 0; base < count; base += 32) {
         int t = base + lane;
         bool has = t < count;
-        double d = has ? bd[t] : 0.0;
+        ukey d = has ? bd[t] : 0;
         int j = has ? bi[t] : 0;
         bool keep = has && !key_lt(td, tj, d, j);
         __syncwarp();
@@ -180,8 +185,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
                                                         const double* sxyz, const double* q, int64_t nq, int k,
                                                         int self_first, int32_t* idx_out, double* d2_out, int* err) {
     extern __shared__ __align__(16) unsigned char knn_smem[];
-    double (*sd)[KNN_CAP] = reinterpret_cast<double (*)[KNN_CAP]>(knn_smem);
-    int (*si)[KNN_CAP] = reinterpret_cast<int (*)[KNN_CAP]>(knn_smem + sizeof(double) * KNN_WARPS * KNN_CAP);
+    ukey (*sd)[KNN_CAP] = reinterpret_cast<ukey (*)[KNN_CAP]>(knn_smem);
+    int (*si)[KNN_CAP] = reinterpret_cast<int (*)[KNN_CAP]>(knn_smem + sizeof(ukey) * KNN_WARPS * KNN_CAP);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t qi = (int64_t)blockIdx.x * KNN_WARPS + w;
     if (qi >= nq) return;
@@ -189,10 +194,10 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
     const double px = q[3 * qi], py = q[3 * qi + 1], pz = q[3 * qi + 2];
     const int cx = cell_coord(px, g.x0, g.h, g.nx), cy = cell_coord(py, g.y0, g.h, g.ny), cz = cell_coord(pz, g.z0, g.h, g.nz);
     const int rfull = max(max(max(cx, g.nx - 1 - cx), max(cy, g.ny - 1 - cy)), max(cz, g.nz - 1 - cz));
-    double* bd = sd[w];
+    ukey* bd = sd[w];
     int* bi = si[w];
     int count = 0;
-    double lim2 = 0.0;
+    ukey lim2 = 0;
     bool all = false;
     for (int r = 0;; ++r) {
         for (int dz = -r; dz <= r; ++dz) {
@@ -213,13 +218,14 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
                                 count = knn_compact(bd, bi, count, k, lane);
                             }
                             bool has = t < e;
-                            double d = 0.0;
+                            ukey d = 0;
                             int j = 0;
                             if (has) {
                                 j = sidx[t];
                                 d = (self_first && j == (int)qi)
-                                        ? -1.0
-                                        : d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1], sxyz[3 * (int64_t)t + 2]);
+                                        ? 0ull
+                                        : d2_key(d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1],
+                                                        sxyz[3 * (int64_t)t + 2]));
                             }
                             unsigned m = __ballot_sync(0xffffffffu, has);
                             int pos = count + __popc(m & ((1u << lane) - 1u));
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
         if (r >= rfull) { all = true; break; }
         if (r >= 1) {
             double R = (double)r * g.h;
-            lim2 = R * R * (1.0 - 1e-9);
+            lim2 = d2_key(R * R * (1.0 - 1e-9));
             __syncwarp();
             int nin = 0;
             for (int t = lane; t < count; t += 32) nin += bd[t] < lim2 ? 1 : 0;
@@ -249,18 +255,17 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
     }
     // rank the filtered candidates
     for (int t = lane; t < count; t += 32) {
-        double d = bd[t];
+        ukey d = bd[t];
         int j = bi[t];
         if (!all && !(d < lim2)) continue;
         int rank = 0;
         for (int u = 0; u < count; ++u) {
-            double e = bd[u];
-            if (!all && !(e < lim2)) continue;
-            rank += key_lt(e, bi[u], d, j) ? 1 : 0;
+            ukey e = bd[u];
+            rank += ((all || e < lim2) && key_lt(e, bi[u], d, j)) ? 1 : 0;
         }
         if (rank < k) {
             idx_out[qi * k + rank] = j;
-            if (d2_out) d2_out[qi * k + rank] = d < 0.0 ? 0.0 : d;
+            if (d2_out) d2_out[qi * k + rank] = d == 0ull ? 0.0 : __longlong_as_double((long long)(d - 1ull));
         }
     }
 }
@@ -276,7 +281,7 @@ void knn_device(const double* data, int64_t nd, const double* query, int64_t nq,
     build_grid(data, nd, 2 * nd, 0.0, G, s);
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
-    const size_t smem = (sizeof(double) + sizeof(int)) * KNN_WARPS * KNN_CAP;
+    const size_t smem = (sizeof(ukey) + sizeof(int)) * KNN_WARPS * KNN_CAP;
     CK(cudaFuncSetAttribute(knn_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     knn_k<<<grid_for(nq, KNN_WARPS), KNN_WARPS * 32, smem, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), query,
                                                             nq, k, self_first, idx_out, d2_out, err.get());
@@ -304,6 +309,7 @@ __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const
     if (i >= n) return;
     const Grid g = *gp;
     const double two_rmax = prm[0], rmin = prm[1];
+    const double lim_sq = two_rmax * two_rmax * (1.0 + 1e-9);
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
     const int cx = cell_coord(px, g.x0, g.h, g.nx), cy = cell_coord(py, g.y0, g.h, g.ny), cz = cell_coord(pz, g.z0, g.h, g.nz);
     // ring count so that the scanned block covers the radius: r*h >= two_rmax (plus one cell for
@@ -322,8 +328,13 @@ __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const
                     if (t < e) {
                         j = sidx[t];
                         if (j != (int)i) {
-                            d = sqrt(d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1], sxyz[3 * (int64_t)t + 2]));
-                            has = d < two_rmax;
+                            double dd = d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1], sxyz[3 * (int64_t)t + 2]);
+                            // sqrt(dd) < two_rmax is decided exactly below; skip the sqrt where dd is
+                            // clearly beyond (the factor leaves a margin far above rounding)
+                            if (dd <= lim_sq) {
+                                d = sqrt(dd);
+                                has = d < two_rmax;
+                            }
                         }
                     }
                     unsigned m = __ballot_sync(0xffffffffu, has);

@@ -75,10 +75,10 @@ struct PhsArgs {
     unsigned long long* bad;  // lowest singular row
 };
 
-__global__ void phs_weights_k(PhsArgs a, int wpb) {
+__global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
     extern __shared__ __align__(16) double sm_phs[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const int n = a.n, m = a.m, ld = m + 1;
+    const int n = a.n, m = a.m, L = a.L, ld = m + 1;
     const size_t per = (size_t)m * ld + 2 * n + m;
     double* A = sm_phs + per * wi;
     double* xh = A + (size_t)m * ld;
@@ -106,39 +106,49 @@ __global__ void phs_weights_k(PhsArgs a, int wpb) {
         if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
         return;
     }
+    const double sinv = 1.0 / s;
     __syncwarp();
-    for (int j = lane; j < n; j += 32) { xh[j] = xh[j] / s; yh[j] = yh[j] / s; }
+    for (int j = lane; j < n; j += 32) { xh[j] = xh[j] * sinv; yh[j] = yh[j] * sinv; }
     __syncwarp();
-    // saddle matrix [A P; P^T 0 | rhs]
+    // saddle matrix [A P; P^T 0 | rhs]. The PHS block is symmetric: each pair is evaluated once
+    // (xh_c - xh_r is exactly -(xh_r - xh_c), so the mirrored value is the same IEEE result).
     double amax = 0.0;
-    for (int e = lane; e < m * ld; e += 32) {
-        int r = e / ld, c = e - r * ld;
-        double v;
-        if (r < n) {
-            if (c < n) {
-                double dx = xh[r] - xh[c], dy = yh[r] - yh[c];
-                v = phs(dx * dx + dy * dy, a.k);
-            } else if (c < m) {
-                int pa, pb;
-                mono_pow(c - n, &pa, &pb);
-                v = monomial(xh[r], yh[r], pa, pb);
-            } else {
-                v = phs_lap(xh[r] * xh[r] + yh[r] * yh[r], a.k);
-            }
-        } else {
-            int pa, pb;
-            mono_pow(r - n, &pa, &pb);
-            if (c < n) v = monomial(xh[c], yh[c], pa, pb);
-            else if (c < m) v = 0.0;
-            else v = ((pa == 2 && pb == 0) || (pa == 0 && pb == 2)) ? 2.0 : 0.0;
+    for (int r = 0; r < n; ++r)
+        for (int c = r + lane; c < n; c += 32) {
+            double dx = xh[r] - xh[c], dy = yh[r] - yh[c];
+            double v = phs(dx * dx + dy * dy, a.k);
+            A[r * ld + c] = v;
+            A[c * ld + r] = v;
+            amax = fmax(amax, fabs(v));
         }
-        A[e] = v;
-        if (c < m) amax = fmax(amax, fabs(v));
+    for (int e = lane; e < n * (L + 1); e += 32) {
+        int r = e / (L + 1), t = e - r * (L + 1);
+        if (t < L) {
+            int pa, pb;
+            mono_pow(t, &pa, &pb);
+            double v = monomial(xh[r], yh[r], pa, pb);
+            A[r * ld + n + t] = v;
+            A[(n + t) * ld + r] = v;
+            amax = fmax(amax, fabs(v));
+        } else {
+            A[r * ld + m] = phs_lap(xh[r] * xh[r] + yh[r] * yh[r], a.k);
+        }
+    }
+    for (int e = lane; e < L * (L + 1); e += 32) {
+        int t = e / (L + 1), c = e - t * (L + 1);
+        double v = 0.0;
+        if (c == L) {
+            int pa, pb;
+            mono_pow(t, &pa, &pb);
+            v = ((pa == 2 && pb == 0) || (pa == 0 && pb == 2)) ? 2.0 : 0.0;
+        }
+        A[(n + t) * ld + n + c] = v;
     }
     amax = warp_max_d(amax);
     const double tol = 1e-13 * amax;
     __syncwarp();
-    // Gaussian elimination with partial pivoting (first row of maximal |a_ik|)
+    // Gaussian elimination with partial pivoting (first row of maximal |a_ik|); multipliers
+    // l_r = a_rk * (1/a_kk); lanes own columns of the trailing block, rows unrolled by 4
     for (int kk = 0; kk < m; ++kk) {
         double best = -1.0;
         int piv = kk;
@@ -162,16 +172,29 @@ __global__ void phs_weights_k(PhsArgs a, int wpb) {
                 A[piv * ld + j] = t;
             }
         __syncwarp();
-        const double akk = A[kk * ld + kk];
-        for (int r = kk + 1 + lane; r < m; r += 32) A[r * ld + kk] = A[r * ld + kk] / akk;  // multiplier l_r
+        const double rinv = 1.0 / A[kk * ld + kk];
+        for (int r = kk + 1 + lane; r < m; r += 32) A[r * ld + kk] = A[r * ld + kk] * rinv;
         __syncwarp();
-        const int R = m - kk - 1, C = m - kk;  // rows kk+1..m-1, columns kk+1..m
-        int rr = lane / C, cc = lane - (lane / C) * C;
-        for (int e = lane; e < R * C; e += 32) {
-            int r = kk + 1 + rr, c = kk + 1 + cc;
-            A[r * ld + c] = fma(-A[r * ld + kk], A[kk * ld + c], A[r * ld + c]);
-            cc += 32;
-            while (cc >= C) { cc -= C; ++rr; }
+        for (int cb = kk + 1; cb < ld; cb += 32) {
+            const int c = cb + lane;
+            const bool act = c < ld;
+            const double pk = act ? A[kk * ld + c] : 0.0;
+            int r = kk + 1;
+            for (; r + 3 < m; r += 4) {
+                const double l0 = A[r * ld + kk], l1 = A[(r + 1) * ld + kk], l2 = A[(r + 2) * ld + kk],
+                             l3 = A[(r + 3) * ld + kk];
+                if (act) {
+                    double v0 = A[r * ld + c], v1 = A[(r + 1) * ld + c], v2 = A[(r + 2) * ld + c], v3 = A[(r + 3) * ld + c];
+                    A[r * ld + c] = fma(-l0, pk, v0);
+                    A[(r + 1) * ld + c] = fma(-l1, pk, v1);
+                    A[(r + 2) * ld + c] = fma(-l2, pk, v2);
+                    A[(r + 3) * ld + c] = fma(-l3, pk, v3);
+                }
+            }
+            for (; r < m; ++r) {
+                const double l0 = A[r * ld + kk];
+                if (act) A[r * ld + c] = fma(-l0, pk, A[r * ld + c]);
+            }
         }
         __syncwarp();
     }
@@ -337,7 +360,7 @@ void stencil_weights(const double* xyz, const double* nrm, int64_t N, const int3
         const int m = n + L;
         if (m > MAX_M) fail(MGM_ERR_UNSUPPORTED, "n + (ell+1)(ell+2)/2 must be <= 128");
         const size_t per = sizeof(double) * ((size_t)m * (m + 1) + 2 * n + m);
-        int wpb = (int)std::min<size_t>(4, (200 * 1024) / per);
+        int wpb = (int)std::min<size_t>(8, (227 * 1024) / per);
         if (wpb < 1) wpb = 1;
         const size_t smem = per * wpb;
         CK(cudaFuncSetAttribute(phs_weights_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

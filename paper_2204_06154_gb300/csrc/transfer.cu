@@ -31,8 +31,9 @@ __device__ int gepp_small(double* a, int m, double tol, double* x) {
         if (!(best > tol)) return 1;
         if (piv != k)
             for (int j = 0; j < ld; ++j) { double t = a[k * ld + j]; a[k * ld + j] = a[piv * ld + j]; a[piv * ld + j] = t; }
+        const double rinv = 1.0 / a[k * ld + k];
         for (int i = k + 1; i < m; ++i) {
-            double l = a[i * ld + k] / a[k * ld + k];
+            double l = a[i * ld + k] * rinv;
             for (int j = k + 1; j < ld; ++j) a[i * ld + j] = fma(-l, a[k * ld + j], a[i * ld + j]);
         }
     }
