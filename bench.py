@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--size", type=int, default=1048576, help="points per surface")
     ap.add_argument("--cpu-sample", type=int, default=32768, help="points of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single", action="store_true",
+                    help="one pass of the path on the sphere only (a small driver for profilers); prints its phases")
     return ap.parse_args()
 
 
@@ -280,6 +282,17 @@ def main():
                           "data": "synthetic", "config": config(a), "cpu_baseline": cb,
                           "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
               flush=True)
+        return
+    if a.single:
+        import torch
+        from paper_2204_06154_gb300 import mgm as M
+        from paper_2204_06154_gb300 import inputs as I
+        x, nrm = I.fibonacci_sphere(a.size, jitter=0.1, seed=2)
+        f = I.random_sh_rhs(x, 20, 2)
+        d = [torch.from_numpy(v).cuda() for v in (x, nrm, f)]
+        r, H, u = run_problem(M, torch, *d)
+        print(json.dumps({"single": True, "N": a.size, **{k: (round(v, 3) if isinstance(v, float) else v)
+                                                         for k, v in r.items()}}), flush=True)
         return
     if world > 1:
         import torch

@@ -179,7 +179,7 @@ mgm_status mgm_transpose(int64_t nrows, int64_t ncols, const int32_t* rowptr, co
  * L_H = R T); A is nA x nB, B is nB x ncolsB. Two-phase: with c_col == NULL the call fills
  * c_rowptr (nA+1) and *nnz_out (host) only; then call again with the same c_rowptr and c_col/c_val
  * of that capacity. Each C entry sums its products in ascending column order of A's row with fused
- * multiply-adds. A row of C may hold at most 1024 distinct columns (MGM_ERR_UNSUPPORTED beyond).
+ * multiply-adds. A row of C may hold at most 2048 distinct columns (MGM_ERR_UNSUPPORTED beyond).
  * Synchronises the stream. */
 mgm_status mgm_spgemm(int64_t nA, int64_t nB, int64_t ncolsB, const int32_t* a_rowptr, const int32_t* a_col, const double* a_val,
                       const int32_t* b_rowptr, const int32_t* b_col, const double* b_val,

@@ -26,6 +26,7 @@
 #define OR_ERR_SINGULAR 2
 #define OR_ERR_NOTCONV 3
 #define OR_ERR_NOMEM 7
+#define MAXM 160
 
 static int64_t g_bad_row = -1;
 int64_t or_last_bad_row(void) { return g_bad_row; }
@@ -76,10 +77,12 @@ int or_knn(const double* data, int64_t nd, const double* query, int64_t nq, int 
  * (row-major, last column = right-hand side). Pivot: largest |a_ik|, first row on ties.
  * Multipliers l_ik = a_ik * (1/a_kk) (one reciprocal per pivot, as in LAPACK's unblocked LU; the
  * paper does not fix the local solver); update a_ij <- fma(-l_ik, a_kj, a_ij). Back substitution
- * column by column. The system is declared singular when the pivot magnitude is <= tol.
+ * column by column, x_k = b_k * (1/a_kk) with the pivot's reciprocal saved during elimination.
+ * The system is declared singular when the pivot magnitude is <= tol.
  * =========================================================================================== */
 static int gepp_solve(double* a, int m, double tol, double* x) {
     const int ld = m + 1;
+    double rinvs[MAXM + 1];
     for (int k = 0; k < m; ++k) {
         int piv = k;
         double best = fabs(a[k * ld + k]);
@@ -91,13 +94,14 @@ static int gepp_solve(double* a, int m, double tol, double* x) {
         if (piv != k)
             for (int j = 0; j < ld; ++j) { double t = a[k * ld + j]; a[k * ld + j] = a[piv * ld + j]; a[piv * ld + j] = t; }
         double rinv = 1.0 / a[k * ld + k];
+        rinvs[k] = rinv;
         for (int i = k + 1; i < m; ++i) {
             double l = a[i * ld + k] * rinv;
             for (int j = k + 1; j < ld; ++j) a[i * ld + j] = fma(-l, a[k * ld + j], a[i * ld + j]);
         }
     }
     for (int k = m - 1; k >= 0; --k) {
-        double xk = a[k * ld + m] / a[k * ld + k];
+        double xk = a[k * ld + m] * rinvs[k];
         x[k] = xk;
         for (int i = 0; i < k; ++i) a[i * ld + m] = fma(-a[i * ld + k], xk, a[i * ld + m]);
     }
@@ -175,7 +179,6 @@ static double phs_lap(double r2, int k) {
     return c * (sqrt(r2) * p);
 }
 
-#define MAXM 160
 
 /* ===========================================================================================
  * PHS RBF-FD weights for the LBO (Sec. 2.2, eq. (rbf_fd_lap)): for each stencil solve

@@ -10,6 +10,8 @@
 // MSB-first threshold search in one block). Survivors adjacent to a removed point recompute their
 // weight from scratch in ascending neighbour order, so every weight is the same IEEE sum as a
 // sequential recomputation and the kept set is bit-reproducible. Built with --fmad=false.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace mgm {
@@ -57,35 +59,61 @@ __global__ void weights_k(const int32_t* rp, const int32_t* nbr, const double* f
     w[i] = acc;
 }
 
-__global__ void count_pos_k(const char* live, const double* w, int64_t n, int* npos) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int c = (i < n && live[i] && w[i] > 0.0) ? 1 : 0;
+// Device-resident round state: the host enqueues rounds without reading anything back and
+// checks the live count every WSE_BATCH rounds; a round with nothing left to remove is a no-op.
+struct WseState {
+    long long nlive, need;
+    int npos, ncand, selective;
+};
+constexpr int WSE_BATCH = 8;
+
+__global__ void wse_round_begin_k(WseState* st, long long NH) {
+    st->need = st->nlive - NH;
+    st->npos = 0;
+    st->ncand = 0;
+    st->selective = 0;
+}
+
+__global__ void count_pos_k(const char* live, const double* w, int64_t n, WseState* st) {
+    if (st->need <= 0) return;
+    int c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += (live[i] && w[i] > 0.0) ? 1 : 0;
     c = warp_sum_i(c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(npos, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st->npos, c);
 }
 
 __device__ __forceinline__ bool wgt_gt(double wa, int64_t a, double wb, int64_t b) { return wa > wb || (wa == wb && a > b); }
 
 __global__ void candidates_k(const int32_t* rp, const int32_t* nbr, const char* live, const double* w, int64_t n,
-                             const int* npos, int32_t* cand, int* ncand) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !live[i]) return;
-    if (*npos > 0) {
-        double wi = w[i];
-        if (!(wi > 0.0)) return;
-        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-            int32_t j = nbr[p];
-            if (live[j] && !wgt_gt(wi, i, w[j], j)) return;
+                             WseState* st, int32_t* cand) {
+    if (st->need <= 0) return;
+    const bool anypos = st->npos > 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!live[i]) continue;
+        if (anypos) {
+            double wi = w[i];
+            if (!(wi > 0.0)) continue;
+            bool top = true;
+            for (int32_t p = rp[i]; p < rp[i + 1] && top; ++p) {
+                int32_t j = nbr[p];
+                if (live[j] && !wgt_gt(wi, i, w[j], j)) top = false;
+            }
+            if (!top) continue;
         }
+        int q = atomicAdd(&st->ncand, 1);
+        cand[q] = (int32_t)i;
     }
-    int q = atomicAdd(ncand, 1);
-    cand[q] = (int32_t)i;
 }
 
-// Keep the `need` largest candidates by (weight, index): MSB-first search of the 96-bit key
-// (weight bits, index) for the need-th largest, then mark key >= threshold. One block.
-__global__ void __launch_bounds__(1024) select_top_k(const int32_t* cand, int nc, const double* w, int need, char* sel) {
+// When more candidates than remaining removals exist, keep only the `need` largest by
+// (weight, index): MSB-first search of the 96-bit key (weight bits, index) for the need-th
+// largest, then mark key >= threshold. One block.
+__global__ void __launch_bounds__(1024) select_top_k(const int32_t* cand, const double* w, WseState* st, char* sel) {
     __shared__ int red[32];
+    const long long need = st->need;
+    const int nc = st->ncand;
+    if (need <= 0 || nc <= need) return;
     unsigned long long thi = 0;
     unsigned tlo = 0;
     for (int b = 95; b >= 0; --b) {
@@ -119,15 +147,25 @@ __global__ void __launch_bounds__(1024) select_top_k(const int32_t* cand, int nc
         unsigned kl = (unsigned)i;
         sel[t] = (kh > thi || (kh == thi && kl >= tlo)) ? 1 : 0;
     }
+    if (threadIdx.x == 0) st->selective = 1;
 }
 
-__global__ void remove_k(const int32_t* cand, const char* sel, int nc, const int32_t* rp, const int32_t* nbr, char* live,
-                         char* dirty) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nc || (sel && !sel[t])) return;
-    int32_t v = cand[t];
-    live[v] = 0;
-    for (int32_t p = rp[v]; p < rp[v + 1]; ++p) dirty[nbr[p]] = 1;
+__global__ void remove_k(const int32_t* cand, const char* sel, const WseState* st, const int32_t* rp, const int32_t* nbr,
+                         char* live, char* dirty) {
+    if (st->need <= 0) return;
+    const int nc = st->ncand;
+    const bool selective = st->selective != 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += gridDim.x * blockDim.x) {
+        if (selective && !sel[t]) continue;
+        int32_t v = cand[t];
+        live[v] = 0;
+        for (int32_t p = rp[v]; p < rp[v + 1]; ++p) dirty[nbr[p]] = 1;
+    }
+}
+
+__global__ void wse_round_end_k(WseState* st) {
+    if (st->need <= 0) return;
+    st->nlive -= st->selective ? st->need : (long long)st->ncand;
 }
 
 __global__ void live_flags_k(const char* live, int64_t n, int32_t* fl) {
@@ -166,36 +204,36 @@ void coarsen(const double* x, int64_t N, int64_t NH, int32_t* keep, cudaStream_t
     Temp<char> live(N, s), dirty(N, s), sel(N, s);
     Temp<double> w(N, s);
     Temp<int32_t> cand(N, s);
-    Temp<int> ctr(2, s);  // [0] npos, [1] ncand
+    Temp<WseState> st(1, s);
+    WseState init{(long long)N, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(st.get(), &init, sizeof(WseState), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(live.get(), 1, N, s));
     CK(cudaMemsetAsync(dirty.get(), 0, N, s));
     weights_k<<<grid_for(N, 256), 256, 0, s>>>(rp.get(), nbr.get(), f.get(), live.get(), dirty.get(), N, 0, w.get());
     CK_LAUNCH();
-    int64_t nlive = N;
-    for (int64_t round = 0; nlive > NH; ++round) {
-        if (round > N) fail(MGM_ERR_UNSUPPORTED, "elimination did not terminate");
-        CK(cudaMemsetAsync(ctr.get(), 0, 2 * sizeof(int), s));
-        count_pos_k<<<grid_for(N, 256), 256, 0, s>>>(live.get(), w.get(), N, ctr.get());
-        CK_LAUNCH();
-        candidates_k<<<grid_for(N, 256), 256, 0, s>>>(rp.get(), nbr.get(), live.get(), w.get(), N, ctr.get(), cand.get(),
-                                                      ctr.get() + 1);
-        CK_LAUNCH();
-        int nc = read1(ctr.get() + 1, s);
-        if (nc <= 0) fail(MGM_ERR_UNSUPPORTED, "elimination round without candidates");
-        int64_t need = nlive - NH;
-        const char* selp = nullptr;
-        int64_t removed = nc;
-        if (nc > need) {
-            select_top_k<<<1, 1024, 0, s>>>(cand.get(), nc, w.get(), (int)need, sel.get());
-            CK_LAUNCH();
-            selp = sel.get();
-            removed = need;
+    const unsigned grid = (unsigned)std::min<int64_t>(grid_for(N, 256), 152 * 8);
+    for (int64_t round = 0;; ++round) {
+        if (round % WSE_BATCH == 0) {
+            WseState h;
+            to_host(&h, st.get(), 1, s);
+            if (h.nlive <= NH) break;
+            if (round > 0 && h.ncand <= 0 && h.need > 0) fail(MGM_ERR_UNSUPPORTED, "elimination round without candidates");
+            if (round > N + WSE_BATCH) fail(MGM_ERR_UNSUPPORTED, "elimination did not terminate");
         }
-        remove_k<<<grid_for(nc, 256), 256, 0, s>>>(cand.get(), selp, nc, rp.get(), nbr.get(), live.get(), dirty.get());
+        wse_round_begin_k<<<1, 1, 0, s>>>(st.get(), (long long)NH);
+        CK_LAUNCH();
+        count_pos_k<<<grid, 256, 0, s>>>(live.get(), w.get(), N, st.get());
+        CK_LAUNCH();
+        candidates_k<<<grid, 256, 0, s>>>(rp.get(), nbr.get(), live.get(), w.get(), N, st.get(), cand.get());
+        CK_LAUNCH();
+        select_top_k<<<1, 1024, 0, s>>>(cand.get(), w.get(), st.get(), sel.get());
+        CK_LAUNCH();
+        remove_k<<<grid, 256, 0, s>>>(cand.get(), sel.get(), st.get(), rp.get(), nbr.get(), live.get(), dirty.get());
         CK_LAUNCH();
         weights_k<<<grid_for(N, 256), 256, 0, s>>>(rp.get(), nbr.get(), f.get(), live.get(), dirty.get(), N, 1, w.get());
         CK_LAUNCH();
-        nlive -= removed;
+        wse_round_end_k<<<1, 1, 0, s>>>(st.get());
+        CK_LAUNCH();
     }
     Temp<int32_t> fl(N, s), pos(N + 1, s);
     live_flags_k<<<grid_for(N, 256), 256, 0, s>>>(live.get(), N, fl.get());

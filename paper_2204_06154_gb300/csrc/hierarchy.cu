@@ -151,17 +151,38 @@ static void dense_inverse(const Level& L, Buf<double>& inv, cudaStream_t s) {
 }
 
 // ------------------------------ solve-order layout ---------------------------------------------
-__global__ void colour_hist_k(const int32_t* col, int64_t n, int32_t* hist) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(&hist[col[i]], 1);
+// Stable grouping of rows by colour in one pass: blocks of 256 rows rank each row among the
+// earlier rows of its colour in the block and count colours per block; a scan of the
+// (colour, block) counts in colour-major order gives each block's base for each colour.
+__global__ void __launch_bounds__(256) colour_rank_k(const int32_t* col, int64_t n, int nc, int nblocks, int32_t* lrank,
+                                                      int32_t* hist) {
+    extern __shared__ int32_t crk_sh[];
+    int32_t* scol = crk_sh;
+    int32_t* cnt = crk_sh + 256;
+    const int t = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * 256 + t;
+    const int c = i < n ? col[i] : -1;
+    scol[t] = c;
+    for (int q = t; q < nc; q += 256) cnt[q] = 0;
+    __syncthreads();
+    if (i < n) {
+        int r = 0;
+        for (int u = 0; u < t; ++u) r += scol[u] == c ? 1 : 0;
+        lrank[i] = r;
+        atomicAdd(&cnt[c], 1);
+    }
+    __syncthreads();
+    for (int q = t; q < nc; q += 256) hist[(int64_t)q * nblocks + blockIdx.x] = cnt[q];
 }
-__global__ void colour_flag_k(const int32_t* col, int64_t n, int32_t c, int32_t* fl) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) fl[i] = col[i] == c ? 1 : 0;
+__global__ void colour_place_k(const int32_t* col, const int32_t* lrank, const int32_t* off, int64_t n, int nblocks,
+                               int32_t* ord) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i < n) ord[off[(int64_t)col[i] * nblocks + blockIdx.x] + lrank[i]] = (int32_t)i;
 }
-__global__ void colour_scatter_k(const int32_t* col, int64_t n, int32_t c, const int32_t* pos, int32_t base, int32_t* ord) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && col[i] == c) ord[base + pos[i]] = (int32_t)i;
+__global__ void colour_bounds_k(const int32_t* off, int nc, int nblocks, int64_t n, int32_t* cp) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nc) cp[c] = off[(int64_t)c * nblocks];
+    if (c == nc) cp[c] = (int32_t)n;
 }
 
 __device__ __forceinline__ int32_t pad4(int32_t x) { return (x + 3) & ~3; }
@@ -232,22 +253,18 @@ static void build_solve_layout(Level& L, bool single, cudaStream_t s) {
         L.cptr = {0, (int32_t)n};
     } else {
         const int nc = L.ncolors;
-        Temp<int32_t> hist(nc, s);
-        CK(cudaMemsetAsync(hist.get(), 0, sizeof(int32_t) * nc, s));
-        colour_hist_k<<<grid_for(n, 256), 256, 0, s>>>(L.colour.get(), n, hist.get());
+        const int nblocks = (int)grid_for(n, 256);
+        Temp<int32_t> lrank(n, s), hist((int64_t)nc * nblocks + 1, s), off((int64_t)nc * nblocks + 1, s), cp(nc + 1, s);
+        colour_rank_k<<<nblocks, 256, sizeof(int32_t) * (256 + nc), s>>>(L.colour.get(), n, nc, nblocks, lrank.get(),
+                                                                         hist.get());
         CK_LAUNCH();
-        std::vector<int32_t> h(nc);
-        to_host(h.data(), hist.get(), nc, s);
+        exclusive_scan_i32(hist.get(), off.get(), (int64_t)nc * nblocks, s);
+        colour_place_k<<<nblocks, 256, 0, s>>>(L.colour.get(), lrank.get(), off.get(), n, nblocks, L.ord.get());
+        CK_LAUNCH();
+        colour_bounds_k<<<grid_for(nc + 1, 128), 128, 0, s>>>(off.get(), nc, nblocks, n, cp.get());
+        CK_LAUNCH();
         L.cptr.assign(nc + 1, 0);
-        for (int c = 0; c < nc; ++c) L.cptr[c + 1] = L.cptr[c] + h[c];
-        Temp<int32_t> fl(n, s), pos(n + 1, s);
-        for (int c = 0; c < nc; ++c) {
-            colour_flag_k<<<grid_for(n, 256), 256, 0, s>>>(L.colour.get(), n, c, fl.get());
-            CK_LAUNCH();
-            exclusive_scan_i32(fl.get(), pos.get(), n, s);
-            colour_scatter_k<<<grid_for(n, 256), 256, 0, s>>>(L.colour.get(), n, c, pos.get(), L.cptr[c], L.ord.get());
-            CK_LAUNCH();
-        }
+        to_host(L.cptr.data(), cp.get(), nc + 1, s);
     }
     invert_perm(L.ord.get(), L.inv.get(), n, s);
     Temp<int32_t> len(n + 1, s), nlo(n, s);

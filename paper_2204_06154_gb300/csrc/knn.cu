@@ -11,6 +11,7 @@
 // keys are then placed by rank counting. The result is therefore exactly the (d^2, index) order
 // the definition asks for, independent of the grid and of scheduling. Distances are computed as
 // (dx*dx + dy*dy) + dz*dz without contraction (this file is built with --fmad=false).
+#include <algorithm>
 #include <cfloat>
 
 #include "common.cuh"
@@ -253,16 +254,32 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
         if (lane == 0) atomicOr(err, 2);
         return;
     }
-    // rank the filtered candidates
+    if (!all) {  // keep only candidates strictly inside the covered radius (stable, in place)
+        int wpos = 0;
+        for (int base = 0; base < count; base += 32) {
+            int t = base + lane;
+            bool has = t < count;
+            ukey d = has ? bd[t] : 0;
+            int j = has ? bi[t] : 0;
+            bool keep = has && d < lim2;
+            __syncwarp();
+            unsigned km = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                int pos = wpos + __popc(km & ((1u << lane) - 1u));
+                bd[pos] = d;
+                bi[pos] = j;
+            }
+            wpos += __popc(km);
+            __syncwarp();
+        }
+        count = wpos;
+    }
+    // rank the remaining candidates; the k smallest keys take their places
     for (int t = lane; t < count; t += 32) {
         ukey d = bd[t];
         int j = bi[t];
-        if (!all && !(d < lim2)) continue;
         int rank = 0;
-        for (int u = 0; u < count; ++u) {
-            ukey e = bd[u];
-            rank += ((all || e < lim2) && key_lt(e, bi[u], d, j)) ? 1 : 0;
-        }
+        for (int u = 0; u < count; ++u) rank += key_lt(bd[u], bi[u], d, j) ? 1 : 0;
         if (rank < k) {
             idx_out[qi * k + rank] = j;
             if (d2_out) d2_out[qi * k + rank] = d == 0ull ? 0.0 : __longlong_as_double((long long)(d - 1ull));
@@ -278,7 +295,10 @@ void knn_device(const double* data, int64_t nd, const double* query, int64_t nq,
     REQUIRE(!self_first || (data == query && nd == nq), "self_first requires query == data");
     if (nq == 0) return;
     DevGrid G;
-    build_grid(data, nd, 2 * nd, 0.0, G, s);
+    // about 2 N cells for small k; fewer, larger cells for large k so that one ring of cells
+    // usually covers the k-th neighbour
+    const int64_t cells = std::max<int64_t>(1, (int64_t)((2.0 * nd) * std::min(1.0, 12.0 / k)));
+    build_grid(data, nd, cells, 0.0, G, s);
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
     const size_t smem = (sizeof(ukey) + sizeof(int)) * KNN_WARPS * KNN_CAP;
@@ -312,9 +332,10 @@ __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const
     const double lim_sq = two_rmax * two_rmax * (1.0 + 1e-9);
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
     const int cx = cell_coord(px, g.x0, g.h, g.nx), cy = cell_coord(py, g.y0, g.h, g.ny), cz = cell_coord(pz, g.z0, g.h, g.nz);
-    // ring count so that the scanned block covers the radius: r*h >= two_rmax (plus one cell for
-    // rounding at the bin boundary)
-    const int R = (int)ceil(two_rmax / g.h) + 1;
+    // rings so that the scanned block covers the radius: with cells wider than 2 r_max (by far
+    // more than rounding), neighbours differ by at most one cell per axis; otherwise one extra
+    // ring absorbs rounding at the bin boundaries
+    const int R = (g.h >= two_rmax * (1.0 + 1e-6)) ? 1 : (int)ceil(two_rmax / g.h) + 1;
     int count = 0;
     for (int z = max(cz - R, 0); z <= min(cz + R, g.nz - 1); ++z)
         for (int y = max(cy - R, 0); y <= min(cy + R, g.ny - 1); ++y)
@@ -371,7 +392,7 @@ __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const
 void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, Temp<int32_t>& rowptr,
                   Temp<int32_t>& nbr, Temp<double>& f, cudaStream_t s) {
     DevGrid G;
-    build_grid(x, n, 2 * n, 0.5 * h_hint, G, s);
+    build_grid(x, n, 2 * n, h_hint * (1.0 + 1e-5), G, s);
     Temp<int32_t> cnt(n + 1, s);
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));

@@ -12,82 +12,141 @@
 // exceeds that of all uncoloured neighbours takes the smallest colour absent from its coloured
 // neighbours. Such vertices are never adjacent, and the result equals sequential first-fit
 // colouring in decreasing priority.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
 
 namespace mgm {
 
-// sort each row of the symmetrised adjacency by (degree, index): warp per row, rank placement
-__global__ void sort_by_degree_k(const int32_t* rp, const int32_t* ci, int64_t N, int32_t* out) {
-    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+// sort each row of the symmetrised adjacency by (degree, index): warp per row; the (degree,
+// index) keys of a row (up to 256) are staged in shared memory and placed by rank
+constexpr int SBD_WARPS = 8, SBD_MAX = 256;
+__global__ void __launch_bounds__(SBD_WARPS * 32) sort_by_degree_k(const int32_t* rp, const int32_t* ci, int64_t N,
+                                                                    int32_t* out) {
+    __shared__ unsigned long long keys[SBD_WARPS][SBD_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * SBD_WARPS + w;
     if (row >= N) return;
-    int32_t b = rp[row], e = rp[row + 1];
-    for (int32_t p = b + lane; p < e; p += 32) {
-        int32_t u = ci[p];
-        int32_t du = rp[u + 1] - rp[u];
-        int rank = 0;
-        for (int32_t q = b; q < e; ++q) {
-            int32_t v = ci[q];
-            int32_t dv = rp[v + 1] - rp[v];
-            rank += (dv < du || (dv == du && v < u)) ? 1 : 0;
+    const int32_t b = rp[row], e = rp[row + 1], len = e - b;
+    auto key = [&](int32_t u) { return ((unsigned long long)(uint32_t)(rp[u + 1] - rp[u]) << 32) | (uint32_t)u; };
+    if (len <= SBD_MAX) {
+        for (int32_t t = lane; t < len; t += 32) keys[w][t] = key(ci[b + t]);
+        __syncwarp();
+        for (int32_t t = lane; t < len; t += 32) {
+            const unsigned long long k = keys[w][t];
+            int rank = 0;
+            for (int32_t q = 0; q < len; ++q) rank += keys[w][q] < k ? 1 : 0;
+            out[b + rank] = (int32_t)(k & 0xffffffffull);
         }
-        out[b + rank] = u;
+    } else {
+        for (int32_t p = b + lane; p < e; p += 32) {
+            const unsigned long long k = key(ci[p]);
+            int rank = 0;
+            for (int32_t q = b; q < e; ++q) rank += key(ci[q]) < k ? 1 : 0;
+            out[b + rank] = (int32_t)(k & 0xffffffffull);
+        }
     }
 }
 
-__global__ void rcm_start_k(const int32_t* rp, const int32_t* pos, int64_t N, unsigned long long* best) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N || pos[i] >= 0) return;
-    unsigned long long key = ((unsigned long long)(uint32_t)(rp[i + 1] - rp[i]) << 32) | (uint32_t)i;
-    atomicMin(best, key);
+// Device-resident BFS state: the host enqueues levels without reading anything back and checks
+// for completion only every RCM_BATCH levels; kernels of an exhausted search return at once.
+struct RcmState {
+    int32_t fs, fe, tail, total;   // current frontier [fs, fe) in `order`, next free slot, children found
+    unsigned long long best;       // (degree, index) key of the next component's start
+};
+constexpr int RCM_BATCH = 16;
+constexpr int RCM_GRID = 152 * 8;
+
+__global__ void rcm_start_k(const int32_t* rp, const int32_t* pos, int64_t N, RcmState* st) {
+    if (st->fs != st->fe || st->tail >= N) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        if (pos[i] >= 0) continue;
+        unsigned long long key = ((unsigned long long)(uint32_t)(rp[i + 1] - rp[i]) << 32) | (uint32_t)i;
+        atomicMin(&st->best, key);
+    }
 }
 
-__global__ void rcm_seed_k(const unsigned long long* best, int32_t* order, int32_t* pos, int32_t tail) {
-    int32_t s = (int32_t)(*best & 0xffffffffull);
-    order[tail] = s;
-    pos[s] = tail;
+__global__ void rcm_seed_k(int32_t* order, int32_t* pos, int64_t N, RcmState* st) {
+    if (st->fs != st->fe || st->tail >= N) return;
+    int32_t s = (int32_t)(st->best & 0xffffffffull);
+    order[st->tail] = s;
+    pos[s] = st->tail;
+    st->fs = st->tail;
+    st->fe = st->tail + 1;
+    st->tail += 1;
+    st->best = ~0ull;
 }
 
-__global__ void rcm_claim_k(const int32_t* rp, const int32_t* adj, const int32_t* order, const int32_t* pos, int32_t fs,
-                            int32_t fe, int32_t* claim) {
-    int32_t t = fs + blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= fe) return;
-    int32_t v = order[t];
-    for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
-        int32_t u = adj[p];
-        if (pos[u] < 0) atomicMin(&claim[u], t);
+__global__ void rcm_claim_k(const int32_t* rp, const int32_t* adj, const int32_t* order, const int32_t* pos,
+                            const RcmState* st, int32_t* claim) {
+    const int32_t fs = st->fs, fe = st->fe;
+    for (int32_t t = fs + blockIdx.x * blockDim.x + threadIdx.x; t < fe; t += gridDim.x * blockDim.x) {
+        int32_t v = order[t];
+        for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
+            int32_t u = adj[p];
+            if (pos[u] < 0) atomicMin(&claim[u], t);
+        }
     }
 }
 
 __global__ void rcm_count_k(const int32_t* rp, const int32_t* adj, const int32_t* order, const int32_t* pos,
-                            const int32_t* claim, int32_t fs, int32_t fe, int32_t* cnt) {
-    int32_t t = fs + blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= fe) return;
-    int32_t v = order[t];
-    int32_t c = 0;
-    for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
-        int32_t u = adj[p];
-        if (pos[u] < 0 && claim[u] == t) ++c;
+                            const int32_t* claim, const RcmState* st, int32_t* cnt) {
+    const int32_t fs = st->fs, fe = st->fe;
+    for (int32_t t = fs + blockIdx.x * blockDim.x + threadIdx.x; t < fe; t += gridDim.x * blockDim.x) {
+        int32_t v = order[t];
+        int32_t c = 0;
+        for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
+            int32_t u = adj[p];
+            if (pos[u] < 0 && claim[u] == t) ++c;
+        }
+        cnt[t - fs] = c;
     }
-    cnt[t - fs] = c;
+}
+
+// exclusive scan of the frontier's child counts by one block; total into the state
+__global__ void __launch_bounds__(1024) rcm_scan_k(const int32_t* cnt, int32_t* off, RcmState* st) {
+    __shared__ int32_t part[1024];
+    const int32_t n = st->fe - st->fs;
+    const int32_t per = (n + 1023) / 1024;
+    const int32_t b = threadIdx.x * per, e = min(n, b + per);
+    int32_t sum = 0;
+    for (int32_t i = b; i < e; ++i) sum += cnt[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t acc = 0;
+        for (int t = 0; t < 1024; ++t) { int32_t v = part[t]; part[t] = acc; acc += v; }
+        st->total = acc;
+    }
+    __syncthreads();
+    int32_t acc = part[threadIdx.x];
+    for (int32_t i = b; i < e; ++i) { off[i] = acc; acc += cnt[i]; }
 }
 
 __global__ void rcm_write_k(const int32_t* rp, const int32_t* adj, int32_t* order, int32_t* pos, const int32_t* claim,
-                            int32_t fs, int32_t fe, const int32_t* off, int32_t tail) {
-    int32_t t = fs + blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= fe) return;
-    int32_t v = order[t];
-    int32_t q = tail + off[t - fs];
-    for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
-        int32_t u = adj[p];
-        if (pos[u] < 0 && claim[u] == t) {
-            order[q] = u;
-            pos[u] = q;
-            ++q;
+                            const int32_t* off, const RcmState* st) {
+    const int32_t fs = st->fs, fe = st->fe, tail = st->tail;
+    for (int32_t t = fs + blockIdx.x * blockDim.x + threadIdx.x; t < fe; t += gridDim.x * blockDim.x) {
+        int32_t v = order[t];
+        int32_t q = tail + off[t - fs];
+        for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
+            int32_t u = adj[p];
+            if (pos[u] < 0 && claim[u] == t) {
+                order[q] = u;
+                pos[u] = q;
+                ++q;
+            }
         }
     }
+}
+
+__global__ void rcm_advance_k(RcmState* st) {
+    if (st->fs == st->fe) return;
+    st->fs = st->tail;
+    st->fe = st->tail + st->total;
+    st->tail += st->total;
+    st->total = 0;
 }
 
 __global__ void reverse_k(const int32_t* order, int64_t N, int32_t* perm) {
@@ -102,37 +161,36 @@ void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStr
     sym_pattern(N, rp, ci, srp, sci, s);
     int64_t snnz = csr_nnz(srp.get(), N, s);
     Temp<int32_t> adj(snnz > 0 ? snnz : 1, s);
-    sort_by_degree_k<<<grid_for(N * 32, 256), 256, 0, s>>>(srp.get(), sci.get(), N, adj.get());
+    sort_by_degree_k<<<grid_for(N, SBD_WARPS), SBD_WARPS * 32, 0, s>>>(srp.get(), sci.get(), N, adj.get());
     CK_LAUNCH();
     Temp<int32_t> order(N, s), pos(N, s), claim(N, s), cnt(N + 1, s), off(N + 1, s);
     fill_i32(pos.get(), -1, N, s);
     fill_i32(claim.get(), INT_MAX, N, s);
-    Temp<unsigned long long> best(1, s);
-    int32_t tail = 0;
-    while (tail < N) {
-        CK(cudaMemsetAsync(best.get(), 0xff, sizeof(unsigned long long), s));
-        rcm_start_k<<<grid_for(N, 256), 256, 0, s>>>(srp.get(), pos.get(), N, best.get());
-        CK_LAUNCH();
-        rcm_seed_k<<<1, 1, 0, s>>>(best.get(), order.get(), pos.get(), tail);
-        CK_LAUNCH();
-        int32_t fs = tail, fe = tail + 1;
-        tail = fe;
-        while (fe > fs) {
-            int32_t nf = fe - fs;
-            rcm_claim_k<<<grid_for(nf, 128), 128, 0, s>>>(srp.get(), adj.get(), order.get(), pos.get(), fs, fe, claim.get());
-            CK_LAUNCH();
-            rcm_count_k<<<grid_for(nf, 128), 128, 0, s>>>(srp.get(), adj.get(), order.get(), pos.get(), claim.get(), fs, fe,
-                                                          cnt.get());
-            CK_LAUNCH();
-            exclusive_scan_i32(cnt.get(), off.get(), nf, s);  // synchronises (reads the total)
-            int32_t total = read1(off.get() + nf, s);
-            rcm_write_k<<<grid_for(nf, 128), 128, 0, s>>>(srp.get(), adj.get(), order.get(), pos.get(), claim.get(), fs, fe,
-                                                          off.get(), tail);
-            CK_LAUNCH();
-            fs = tail;
-            fe = tail + total;
-            tail = fe;
+    Temp<RcmState> st(1, s);
+    RcmState init{0, 0, 0, 0, ~0ull};
+    CK(cudaMemcpyAsync(st.get(), &init, sizeof(RcmState), cudaMemcpyHostToDevice, s));
+    const unsigned grid = (unsigned)std::min<int64_t>(grid_for(N, 128), RCM_GRID);
+    for (int64_t level = 0;; ++level) {
+        if (level % RCM_BATCH == 0) {
+            RcmState h;
+            to_host(&h, st.get(), 1, s);
+            if (h.tail >= N && h.fs == h.fe) break;
+            if (level > 4 * N + 64) fail(MGM_ERR_UNSUPPORTED, "RCM did not terminate");
         }
+        rcm_start_k<<<grid, 128, 0, s>>>(srp.get(), pos.get(), N, st.get());
+        CK_LAUNCH();
+        rcm_seed_k<<<1, 1, 0, s>>>(order.get(), pos.get(), N, st.get());
+        CK_LAUNCH();
+        rcm_claim_k<<<grid, 128, 0, s>>>(srp.get(), adj.get(), order.get(), pos.get(), st.get(), claim.get());
+        CK_LAUNCH();
+        rcm_count_k<<<grid, 128, 0, s>>>(srp.get(), adj.get(), order.get(), pos.get(), claim.get(), st.get(), cnt.get());
+        CK_LAUNCH();
+        rcm_scan_k<<<1, 1024, 0, s>>>(cnt.get(), off.get(), st.get());
+        CK_LAUNCH();
+        rcm_write_k<<<grid, 128, 0, s>>>(srp.get(), adj.get(), order.get(), pos.get(), claim.get(), off.get(), st.get());
+        CK_LAUNCH();
+        rcm_advance_k<<<1, 1, 0, s>>>(st.get());
+        CK_LAUNCH();
     }
     reverse_k<<<grid_for(N, 256), 256, 0, s>>>(order.get(), N, perm);
     CK_LAUNCH();

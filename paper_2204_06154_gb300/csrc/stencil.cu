@@ -65,6 +65,12 @@ __device__ __forceinline__ void mono_pow(int t, int* a, int* b) {
     *b = off;
 }
 
+// bits of |v| (ordered like |v|); a NaN counts as 0, so it never wins a magnitude comparison
+__device__ __forceinline__ unsigned long long mag_bits(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    return b > 0x7ff0000000000000ull ? 0ull : b;
+}
+
 struct PhsArgs {
     const double* xyz;
     const double* nrm;
@@ -79,11 +85,12 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
     extern __shared__ __align__(16) double sm_phs[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int n = a.n, m = a.m, L = a.L, ld = m + 1;
-    const size_t per = (size_t)m * ld + 2 * n + m;
+    const size_t per = (size_t)m * ld + 2 * n + 2 * m;
     double* A = sm_phs + per * wi;
     double* xh = A + (size_t)m * ld;
     double* yh = xh + n;
     double* xs = yh + n;
+    double* rinvs = xs + m;
     const int64_t i = (int64_t)blockIdx.x * wpb + wi;
     if (i >= a.N) return;
     const int32_t* id = a.idx + i * n;
@@ -110,17 +117,26 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
     __syncwarp();
     for (int j = lane; j < n; j += 32) { xh[j] = xh[j] * sinv; yh[j] = yh[j] * sinv; }
     __syncwarp();
-    // saddle matrix [A P; P^T 0 | rhs]. The PHS block is symmetric: each pair is evaluated once
-    // (xh_c - xh_r is exactly -(xh_r - xh_c), so the mirrored value is the same IEEE result).
-    double amax = 0.0;
-    for (int r = 0; r < n; ++r)
-        for (int c = r + lane; c < n; c += 32) {
-            double dx = xh[r] - xh[c], dy = yh[r] - yh[c];
-            double v = phs(dx * dx + dy * dy, a.k);
-            A[r * ld + c] = v;
-            A[c * ld + r] = v;
-            amax = fmax(amax, fabs(v));
-        }
+    // saddle matrix [A P; P^T 0 | rhs]. The PHS block is symmetric: each pair (r <= c) is
+    // evaluated once (xh_c - xh_r is exactly -(xh_r - xh_c), so the mirror holds the same IEEE
+    // value); the triangle is enumerated flat so all lanes stay busy. Magnitudes are compared as
+    // integers (the bits of |x| order like |x|), keeping compares off the FP64 pipe.
+    unsigned long long amaxb = 0;
+    const int tri = n * (n + 1) / 2;
+    for (int e = lane; e < tri; e += 32) {
+        // row r of the upper triangle starts at r*n - r*(r-1)/2
+        const float nf = 2.0f * n + 1.0f;
+        int r = (int)((nf - sqrtf(nf * nf - 8.0f * (float)e)) * 0.5f);
+        r = max(0, min(r, n - 1));
+        while (r > 0 && r * n - r * (r - 1) / 2 > e) --r;
+        while (r + 1 < n && (r + 1) * n - (r + 1) * r / 2 <= e) ++r;
+        const int c = r + (e - (r * n - r * (r - 1) / 2));
+        double dx = xh[r] - xh[c], dy = yh[r] - yh[c];
+        double v = phs(dx * dx + dy * dy, a.k);
+        A[r * ld + c] = v;
+        A[c * ld + r] = v;
+        amaxb = max(amaxb, mag_bits(v));
+    }
     for (int e = lane; e < n * (L + 1); e += 32) {
         int r = e / (L + 1), t = e - r * (L + 1);
         if (t < L) {
@@ -129,7 +145,7 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
             double v = monomial(xh[r], yh[r], pa, pb);
             A[r * ld + n + t] = v;
             A[(n + t) * ld + r] = v;
-            amax = fmax(amax, fabs(v));
+            amaxb = max(amaxb, mag_bits(v));
         } else {
             A[r * ld + m] = phs_lap(xh[r] * xh[r] + yh[r] * yh[r], a.k);
         }
@@ -144,24 +160,28 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
         }
         A[(n + t) * ld + n + c] = v;
     }
-    amax = warp_max_d(amax);
-    const double tol = 1e-13 * amax;
+    for (int o = 16; o; o >>= 1) amaxb = max(amaxb, __shfl_xor_sync(0xffffffffu, amaxb, o));
+    const double tol = 1e-13 * __longlong_as_double((long long)amaxb);
+    const unsigned long long tolb = (unsigned long long)__double_as_longlong(tol);
     __syncwarp();
     // Gaussian elimination with partial pivoting (first row of maximal |a_ik|); multipliers
     // l_r = a_rk * (1/a_kk); lanes own columns of the trailing block, rows unrolled by 4
     for (int kk = 0; kk < m; ++kk) {
-        double best = -1.0;
-        int piv = kk;
+        // pivot: first row of maximal |a_rk| (a NaN magnitude never wins)
+        unsigned long long best = 0;
+        int piv = m;  // no row yet
         for (int r = kk + lane; r < m; r += 32) {
-            double v = fabs(A[r * ld + kk]);
-            if (v > best) { best = v; piv = r; }
+            unsigned long long v = mag_bits(A[r * ld + kk]);
+            if (piv == m || v > best) { best = v; piv = r; }
         }
         for (int o = 16; o; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
             int op = __shfl_xor_sync(0xffffffffu, piv, o);
             if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
         }
-        if (!(best > tol)) {
+        const bool nan_diag =
+            ((unsigned long long)__double_as_longlong(A[kk * ld + kk]) & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+        if (!(best > tolb) || nan_diag) {
             if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
             return;
         }
@@ -173,6 +193,7 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
             }
         __syncwarp();
         const double rinv = 1.0 / A[kk * ld + kk];
+        if (lane == 0) rinvs[kk] = rinv;
         for (int r = kk + 1 + lane; r < m; r += 32) A[r * ld + kk] = A[r * ld + kk] * rinv;
         __syncwarp();
         for (int cb = kk + 1; cb < ld; cb += 32) {
@@ -201,7 +222,7 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
     // back substitution, column oriented
     bool finite = true;
     for (int kk = m - 1; kk >= 0; --kk) {
-        double xk = A[kk * ld + m] / A[kk * ld + kk];
+        double xk = A[kk * ld + m] * rinvs[kk];
         finite = finite && isfinite(xk);
         if (lane == 0) xs[kk] = xk;
         for (int r = lane; r < kk; r += 32) A[r * ld + m] = fma(-A[r * ld + kk], xk, A[r * ld + m]);
@@ -359,7 +380,7 @@ void stencil_weights(const double* xyz, const double* nrm, int64_t N, const int3
         REQUIRE(sp->k >= 1 && sp->k <= 8, "PHS order k must be in [1, 8]");
         const int m = n + L;
         if (m > MAX_M) fail(MGM_ERR_UNSUPPORTED, "n + (ell+1)(ell+2)/2 must be <= 128");
-        const size_t per = sizeof(double) * ((size_t)m * (m + 1) + 2 * n + m);
+        const size_t per = sizeof(double) * ((size_t)m * (m + 1) + 2 * n + 2 * m);
         int wpb = (int)std::min<size_t>(8, (227 * 1024) / per);
         if (wpb < 1) wpb = 1;
         const size_t smem = per * wpb;

@@ -21,6 +21,7 @@ constexpr int MAX_INTERP_M = 8;
 
 __device__ int gepp_small(double* a, int m, double tol, double* x) {
     const int ld = m + 1;
+    double rinvs[MAX_INTERP_M + 1];
     for (int k = 0; k < m; ++k) {
         int piv = k;
         double best = fabs(a[k * ld + k]);
@@ -32,13 +33,14 @@ __device__ int gepp_small(double* a, int m, double tol, double* x) {
         if (piv != k)
             for (int j = 0; j < ld; ++j) { double t = a[k * ld + j]; a[k * ld + j] = a[piv * ld + j]; a[piv * ld + j] = t; }
         const double rinv = 1.0 / a[k * ld + k];
+        rinvs[k] = rinv;
         for (int i = k + 1; i < m; ++i) {
             double l = a[i * ld + k] * rinv;
             for (int j = k + 1; j < ld; ++j) a[i * ld + j] = fma(-l, a[k * ld + j], a[i * ld + j]);
         }
     }
     for (int k = m - 1; k >= 0; --k) {
-        double xk = a[k * ld + m] / a[k * ld + k];
+        double xk = a[k * ld + m] * rinvs[k];
         x[k] = xk;
         for (int i = 0; i < k; ++i) a[i * ld + m] = fma(-a[i * ld + k], xk, a[i * ld + m]);
     }
@@ -123,51 +125,61 @@ int64_t interp(const double* xf, int64_t nf, const double* xc, int64_t nc, int m
 }
 
 // ------------------------------ SpGEMM ---------------------------------------------------------
+// Hash-set size per warp: the next power of two >= 2x the largest product count of any row
+// (64..4096 slots); at most half the slots may be filled (distinct columns of one row).
 constexpr int SG_WARPS = 4;
-constexpr int SG_HASH = 2048;  // slots per warp
-constexpr int SG_MAXU = 1024;  // unique columns per row
+constexpr int SG_MAX_HASH = 4096;
 
-__device__ __forceinline__ int sg_insert(int* slots, int col) {
-    unsigned h = ((unsigned)col * 2654435761u) >> (32 - 11);
-    for (int probe = 0; probe < SG_HASH; ++probe) {
+__device__ __forceinline__ int sg_insert(int* slots, int hs, int col) {
+    const int shift = 32 - (31 - __clz(hs));
+    unsigned h = ((unsigned)col * 2654435761u) >> shift;
+    for (int probe = 0; probe < hs; ++probe) {
         int old = atomicCAS(&slots[h], -1, col);
         if (old == -1) return 1;
         if (old == col) return 0;
-        h = (h + 1) & (SG_HASH - 1);
+        h = (h + 1) & (hs - 1);
     }
     return -1;
 }
 
 // per-warp: build the hash set of row i's columns; returns the unique count (warp-uniform)
-__device__ int sg_collect(int* slots, const int32_t* arp, const int32_t* aci, const int32_t* brp, const int32_t* bci,
-                          int64_t i, int lane, bool* overflow) {
-    for (int t = lane; t < SG_HASH; t += 32) slots[t] = -1;
+__device__ int sg_collect(int* slots, int hs, const int32_t* arp, const int32_t* aci, const int32_t* brp,
+                          const int32_t* bci, int64_t i, int lane, bool* overflow) {
+    for (int t = lane; t < hs; t += 32) slots[t] = -1;
     __syncwarp();
     int added = 0;
     bool ovf = false;
     for (int32_t p = arp[i]; p < arp[i + 1]; ++p) {
         int32_t l = aci[p];
         for (int32_t q = brp[l] + lane; q < brp[l + 1]; q += 32) {
-            int r = sg_insert(slots, bci[q]);
+            int r = sg_insert(slots, hs, bci[q]);
             if (r < 0) ovf = true;
             else added += r;
         }
     }
     __syncwarp();
     added = warp_sum_i(added);
-    *overflow = __any_sync(0xffffffffu, ovf) || added > SG_MAXU;
+    *overflow = __any_sync(0xffffffffu, ovf) || added > hs / 2;
     return added;
+}
+
+__global__ void sg_maxprod_k(int64_t nA, const int32_t* arp, const int32_t* aci, const int32_t* brp, int* mx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nA) return;
+    int c = 0;
+    for (int32_t p = arp[i]; p < arp[i + 1]; ++p) c += brp[aci[p] + 1] - brp[aci[p]];
+    atomicMax(mx, c);
 }
 
 __global__ void __launch_bounds__(SG_WARPS * 32) spgemm_symbolic_k(int64_t nA, const int32_t* arp, const int32_t* aci,
                                                                    const int32_t* brp, const int32_t* bci, int32_t* cnt,
-                                                                   int* err) {
-    __shared__ int hs[SG_WARPS][SG_HASH];
+                                                                   int hs, int* err) {
+    extern __shared__ int sg_smem[];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int64_t i = (int64_t)blockIdx.x * SG_WARPS + w;
     if (i >= nA) return;
     bool ovf;
-    int u = sg_collect(hs[w], arp, aci, brp, bci, i, lane, &ovf);
+    int u = sg_collect(sg_smem + w * hs, hs, arp, aci, brp, bci, i, lane, &ovf);
     if (lane == 0) {
         cnt[i] = u;
         if (ovf) atomicOr(err, 1);
@@ -177,33 +189,34 @@ __global__ void __launch_bounds__(SG_WARPS * 32) spgemm_symbolic_k(int64_t nA, c
 __global__ void __launch_bounds__(SG_WARPS * 32) spgemm_numeric_k(int64_t nA, const int32_t* arp, const int32_t* aci,
                                                                   const double* av, const int32_t* brp, const int32_t* bci,
                                                                   const double* bv, const int32_t* crp, int32_t* cci,
-                                                                  double* cv, int* err) {
-    __shared__ int hs[SG_WARPS][SG_HASH];
-    __shared__ int lst[SG_WARPS][SG_MAXU];
+                                                                  double* cv, int hs, int* err) {
+    extern __shared__ int sg_smem[];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int* slots = sg_smem + w * hs;
+    int* lst = sg_smem + SG_WARPS * hs + w * (hs / 2);
     int64_t i = (int64_t)blockIdx.x * SG_WARPS + w;
     if (i >= nA) return;
     bool ovf;
-    int u = sg_collect(hs[w], arp, aci, brp, bci, i, lane, &ovf);
+    int u = sg_collect(slots, hs, arp, aci, brp, bci, i, lane, &ovf);
     if (ovf || u != crp[i + 1] - crp[i]) {
         if (lane == 0) atomicOr(err, 2);
         return;
     }
     // compact the set into lst
     int base = 0;
-    for (int t = lane; t - lane < SG_HASH; t += 32) {
-        int c = t < SG_HASH ? hs[w][t] : -1;
+    for (int t = lane; t - lane < hs; t += 32) {
+        int c = t < hs ? slots[t] : -1;
         unsigned m = __ballot_sync(0xffffffffu, c >= 0);
-        if (c >= 0) lst[w][base + __popc(m & ((1u << lane) - 1u))] = c;
+        if (c >= 0) lst[base + __popc(m & ((1u << lane) - 1u))] = c;
         base += __popc(m);
     }
     __syncwarp();
-    // rank sort into hs (reused as the sorted column list)
-    int* sorted = hs[w];
+    // rank sort into the slot array (reused as the sorted column list)
+    int* sorted = slots;
     for (int t = lane; t < u; t += 32) {
-        int c = lst[w][t];
+        int c = lst[t];
         int r = 0;
-        for (int q = 0; q < u; ++q) r += lst[w][q] < c ? 1 : 0;
+        for (int q = 0; q < u; ++q) r += lst[q] < c ? 1 : 0;
         sorted[r] = c;
     }
     __syncwarp();
@@ -227,6 +240,19 @@ __global__ void __launch_bounds__(SG_WARPS * 32) spgemm_numeric_k(int64_t nA, co
     }
 }
 
+static int sg_hash_size(int64_t nA, const int32_t* arp, const int32_t* aci, const int32_t* brp, cudaStream_t s) {
+    Temp<int> mx(1, s);
+    CK(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
+    if (nA > 0) {
+        sg_maxprod_k<<<grid_for(nA, 256), 256, 0, s>>>(nA, arp, aci, brp, mx.get());
+        CK_LAUNCH();
+    }
+    int m = read1(mx.get(), s);
+    int hs = 64;
+    while (hs < 2 * m && hs < SG_MAX_HASH) hs *= 2;
+    return hs;
+}
+
 // symbolic phase: fills crp (nA+1), returns nnz
 int64_t spgemm_symbolic(int64_t nA, const int32_t* arp, const int32_t* aci, const int32_t* brp, const int32_t* bci,
                         int32_t* crp, cudaStream_t s) {
@@ -234,10 +260,14 @@ int64_t spgemm_symbolic(int64_t nA, const int32_t* arp, const int32_t* aci, cons
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
     if (nA > 0) {
-        spgemm_symbolic_k<<<grid_for(nA, SG_WARPS), SG_WARPS * 32, 0, s>>>(nA, arp, aci, brp, bci, cnt.get(), err.get());
+        const int hs = sg_hash_size(nA, arp, aci, brp, s);
+        const size_t smem = sizeof(int) * SG_WARPS * hs;
+        CK(cudaFuncSetAttribute(spgemm_symbolic_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        spgemm_symbolic_k<<<grid_for(nA, SG_WARPS), SG_WARPS * 32, smem, s>>>(nA, arp, aci, brp, bci, cnt.get(), hs,
+                                                                             err.get());
         CK_LAUNCH();
     }
-    if (read1(err.get(), s)) fail(MGM_ERR_UNSUPPORTED, "SpGEMM row exceeds 1024 distinct columns");
+    if (read1(err.get(), s)) fail(MGM_ERR_UNSUPPORTED, "SpGEMM row exceeds 2048 distinct columns");
     exclusive_scan_i32(cnt.get(), crp, nA, s);
     return csr_nnz(crp, nA, s);
 }
@@ -247,7 +277,11 @@ void spgemm_numeric(int64_t nA, const int32_t* arp, const int32_t* aci, const do
     if (nA <= 0) return;
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
-    spgemm_numeric_k<<<grid_for(nA, SG_WARPS), SG_WARPS * 32, 0, s>>>(nA, arp, aci, av, brp, bci, bv, crp, cci, cv, err.get());
+    const int hs = sg_hash_size(nA, arp, aci, brp, s);
+    const size_t smem = sizeof(int) * SG_WARPS * (hs + hs / 2);
+    CK(cudaFuncSetAttribute(spgemm_numeric_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    spgemm_numeric_k<<<grid_for(nA, SG_WARPS), SG_WARPS * 32, smem, s>>>(nA, arp, aci, av, brp, bci, bv, crp, cci, cv, hs,
+                                                                        err.get());
     CK_LAUNCH();
     if (read1(err.get(), s)) fail(MGM_ERR_INVALID_ARG, "SpGEMM: row pointer does not match the product pattern");
 }

@@ -244,22 +244,42 @@ __global__ void place_t_k(const int32_t* rp, const int32_t* ci, const double* v,
         if (v) tv[q] = v[p];
     }
 }
-// sort each row's (col, val) by col, insertion sort (rows are short in every use here)
-__global__ void sort_rows_k(const int32_t* rp, int32_t* ci, double* v, int64_t nrows) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// sort each row's (col, val) by col: warp per row, rank placement through shared memory for
+// rows of up to 256 entries (columns within a row are distinct), insertion sort beyond
+constexpr int SR_WARPS = 8, SR_MAX = 256;
+__global__ void __launch_bounds__(SR_WARPS * 32) sort_rows_k(const int32_t* rp, int32_t* ci, double* v, int64_t nrows) {
+    __shared__ int32_t sc[SR_WARPS][SR_MAX];
+    __shared__ double sv[SR_WARPS][SR_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * SR_WARPS + w;
     if (i >= nrows) return;
-    int32_t b = rp[i], e = rp[i + 1];
-    for (int32_t p = b + 1; p < e; ++p) {
-        int32_t c = ci[p];
-        double x = v ? v[p] : 0.0;
-        int32_t q = p;
-        while (q > b && ci[q - 1] > c) {
-            ci[q] = ci[q - 1];
-            if (v) v[q] = v[q - 1];
-            --q;
+    const int32_t b = rp[i], e = rp[i + 1], len = e - b;
+    if (len <= SR_MAX) {
+        for (int32_t t = lane; t < len; t += 32) {
+            sc[w][t] = ci[b + t];
+            if (v) sv[w][t] = v[b + t];
         }
-        ci[q] = c;
-        if (v) v[q] = x;
+        __syncwarp();
+        for (int32_t t = lane; t < len; t += 32) {
+            const int32_t c = sc[w][t];
+            int rank = 0;
+            for (int32_t q = 0; q < len; ++q) rank += sc[w][q] < c ? 1 : 0;
+            ci[b + rank] = c;
+            if (v) v[b + rank] = sv[w][t];
+        }
+    } else if (lane == 0) {
+        for (int32_t p = b + 1; p < e; ++p) {
+            int32_t c = ci[p];
+            double x = v ? v[p] : 0.0;
+            int32_t q = p;
+            while (q > b && ci[q - 1] > c) {
+                ci[q] = ci[q - 1];
+                if (v) v[q] = v[q - 1];
+                --q;
+            }
+            ci[q] = c;
+            if (v) v[q] = x;
+        }
     }
 }
 
@@ -278,7 +298,7 @@ void csr_transpose(int64_t nrows, int64_t ncols, const int32_t* rp, const int32_
         CK_LAUNCH();
     }
     if (ncols > 0) {
-        sort_rows_k<<<grid_for(ncols, 128), 128, 0, s>>>(trp, tci, tv, ncols);
+        sort_rows_k<<<grid_for(ncols, SR_WARPS), SR_WARPS * 32, 0, s>>>(trp, tci, tv, ncols);
         CK_LAUNCH();
     }
 }
@@ -314,7 +334,7 @@ void csr_permute(int64_t N, const int32_t* rp, const int32_t* ci, const double* 
     invert_perm(perm, inv.get(), N, s);
     perm_fill_k<<<grid_for(N, 256), 256, 0, s>>>(rp, ci, v, perm, inv.get(), N, brp, bci, bv);
     CK_LAUNCH();
-    sort_rows_k<<<grid_for(N, 128), 128, 0, s>>>(brp, bci, bv, N);
+    sort_rows_k<<<grid_for(N, SR_WARPS), SR_WARPS * 32, 0, s>>>(brp, bci, bv, N);
     CK_LAUNCH();
 }
 
