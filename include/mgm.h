@@ -71,6 +71,10 @@ typedef struct {
     int nu1, nu2;    /* pre- and post-smoothing sweeps, 0 <= nu <= 8 */
     int precision;   /* MGM_F32 (V-cycle in FP32, coarsest solve FP64) or MGM_F64 */
     uint64_t seed;   /* seed of the multicolour-ordering priorities */
+    int persistent_sweeps; /* 0 (default): one kernel launch per colour of each Gauss-Seidel sweep;
+                              nonzero: each sweep is one persistent cooperative launch with a bounded
+                              grid barrier between colours. Both give bit-identical results; on
+                              GB300 the per-colour launches (captured in a CUDA graph) are faster. */
 } mgm_params;
 
 typedef struct {
@@ -257,6 +261,12 @@ mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_st
 /* Number of kernels this library has launched in the process (a host-side count: each launch of
  * the captured V-cycle graph adds its kernel nodes). */
 int64_t mgm_kernel_launches(void);
+
+/* Self-test of the failure-detection path of the device-side waits (not part of the method):
+ * launches a grid barrier on `nblocks` co-resident blocks that one arrival short of complete, with
+ * a spin limit of `spin_limit` polls, and stores in *status_out the status the library reports for
+ * it: MGM_ERR_TIMEOUT when the bounded wait gave up and returned, as it must. Synchronises. */
+mgm_status mgm_check_bounded_wait(int nblocks, int64_t spin_limit, int* status_out, mgm_stream stream);
 
 void mgm_destroy(mgm_hierarchy* H);
 

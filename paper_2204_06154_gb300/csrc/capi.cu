@@ -196,6 +196,14 @@ mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_st
 
 int64_t mgm_kernel_launches(void) { return launches(); }
 
+mgm_status mgm_check_bounded_wait(int nblocks, int64_t spin_limit, int* status_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(status_out && nblocks >= 1 && nblocks <= 152 && spin_limit >= 1, "bad argument");
+        int e = barrier_timeout_probe(nblocks, (unsigned long long)spin_limit, S(stream));
+        *status_out = e ? MGM_ERR_TIMEOUT : MGM_OK;
+    });
+}
+
 void mgm_destroy(mgm_hierarchy* H) {
     if (!H) return;
     cudaDeviceSynchronize();

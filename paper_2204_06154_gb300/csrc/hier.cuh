@@ -31,6 +31,8 @@ struct Level {
     // solve order
     Buf<int32_t> ord, inv;     // ord[s] = RCM index of solve row s; inv = ord^-1
     std::vector<int32_t> cptr; // host: colour c = solve rows [cptr[c], cptr[c+1])
+    Buf<int32_t> cptr_dev;     // the same on the device (persistent sweeps)
+    Buf<unsigned> bar;         // grid-barrier counter of this level's persistent sweeps
     Buf<int32_t> lo, mid;      // row s: lower part [lo[s], mid[s]), upper part [mid[s], lo[s+1])
     Buf<int32_t> sc;           // padded columns (solve order of this level)
     Buf<float> sv32, diag32, dinv32;
@@ -62,6 +64,10 @@ struct mgm_hierarchy {
     mgm::Buf<double> Ainv;      // explicit inverse of L_p (RCM order), FP64
     int64_t np = 0;
     mgm::Buf<int32_t> ord_caller;  // level-0 solve index -> caller index
+    // persistent multicolour sweeps (one cooperative launch per sweep) instead of one launch
+    // per colour; error word of their bounded waits
+    bool persistent = false;
+    mgm::Buf<int> err;
     // V-cycle graph (captured lazily)
     cudaGraphExec_t vgraph = nullptr;
     int64_t graph_kernels = 0;  // kernel nodes in vgraph
@@ -84,6 +90,8 @@ void vcycle_prepare(mgm_hierarchy* H);                       // capture the grap
 void load_input(mgm_hierarchy* H, const void* src, int src_dtype, const int32_t* gather, cudaStream_t s);
 void store_output(mgm_hierarchy* H, void* dst, int dst_dtype, const int32_t* scatter, cudaStream_t s);
 void alloc_work(mgm_hierarchy* H);
+void check_device_error(mgm_hierarchy* H, cudaStream_t s);
+int barrier_timeout_probe(int nblocks, unsigned long long limit, cudaStream_t s);
 void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
 // krylov.cu
 void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);

@@ -399,6 +399,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     H->nu2 = prm->nu2;
     H->m = prm->m;
     H->seed = prm->seed;
+    H->persistent = prm->persistent_sweeps != 0;
     H->N = N;
     int p = num_levels(N, prm->n_min);
     if (p > 16) fail(MGM_ERR_UNSUPPORTED, "more than 16 levels");

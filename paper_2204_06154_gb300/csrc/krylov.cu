@@ -323,6 +323,7 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
     }
     scatter64_k<<<grid_for(n, 256), 256, 0, s>>>(H->u.get(), ordc, u_io, n);
     CK_LAUNCH();
+    if (H->persistent) check_device_error(H, s);
     CK(cudaEventRecord(e1, s));
     CK(cudaEventSynchronize(e1));
     float ms = 0.0f;

@@ -13,6 +13,8 @@
 // keeps them local). The restriction (CSR of the transposed interpolation) and interpolation
 // (ELL, width m) are one thread per row; the coarsest solve multiplies by the explicit FP64
 // inverse, one warp per row. The whole cycle is captured once into a CUDA graph.
+#include <algorithm>
+
 #include "hier.cuh"
 
 namespace mgm {
@@ -51,6 +53,36 @@ __device__ __forceinline__ double row_sum(const int32_t* __restrict__ sc, const 
     }
     return acc;
 }
+// same sums with L2-coherent loads of x (ld.global.cg): inside one persistent launch, x is written
+// by other blocks between grid barriers, so it must not be served from a stale L1 line
+__device__ __forceinline__ float row_sum_cg(const int32_t* __restrict__ sc, const float* __restrict__ sv, int32_t beg,
+                                            int32_t end, const float* x, int gl) {
+    float acc = 0.0f;
+    for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {
+        int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
+        float4 v = __ldg(reinterpret_cast<const float4*>(sv + p));
+        acc = fmaf(v.x, __ldcg(x + c.x), acc);
+        acc = fmaf(v.y, __ldcg(x + c.y), acc);
+        acc = fmaf(v.z, __ldcg(x + c.z), acc);
+        acc = fmaf(v.w, __ldcg(x + c.w), acc);
+    }
+    return acc;
+}
+__device__ __forceinline__ double row_sum_cg(const int32_t* __restrict__ sc, const double* __restrict__ sv, int32_t beg,
+                                             int32_t end, const double* x, int gl) {
+    double acc = 0.0;
+    for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {
+        int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
+        double2 v0 = __ldg(reinterpret_cast<const double2*>(sv + p));
+        double2 v1 = __ldg(reinterpret_cast<const double2*>(sv + p + 2));
+        acc = fma(v0.x, __ldcg(x + c.x), acc);
+        acc = fma(v0.y, __ldcg(x + c.y), acc);
+        acc = fma(v1.x, __ldcg(x + c.z), acc);
+        acc = fma(v1.y, __ldcg(x + c.w), acc);
+    }
+    return acc;
+}
+
 template <class T>
 __device__ __forceinline__ T group_reduce(T v) {
     for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -84,6 +116,78 @@ __global__ void __launch_bounds__(VBLOCK) row_kernel(const int32_t* __restrict__
         else if (MODE == 2) s[row] = -acc;
         else s[row] = b[row] - dv[row] * e[row] - acc;
     }
+}
+
+// ------------------------------ persistent multicolour sweep ----------------------------------
+// One cooperative launch runs every colour of a sweep; blocks meet at a grid barrier between
+// colours. The barrier is a counter in global memory; each wait is bounded (spin limit), after
+// which the block records MGM_ERR_TIMEOUT in the error word and every block leaves.
+constexpr int PS_THREADS = 512;
+constexpr int PS_ROWS = PS_THREADS / G;   // rows per block pass
+constexpr unsigned long long PS_SPIN_LIMIT = 4000000ull;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// returns false (for every thread of the block) when the wait timed out or another block failed
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, unsigned long long limit, int* err, int* ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        unsigned long long it = 0;
+        int good = 1;
+        while (ld_acquire_u32(bar) < target) {
+            if (*(volatile int*)err) { good = 0; break; }
+            if (++it > limit) { atomicOr(err, MGM_ERR_TIMEOUT); good = 0; break; }
+            __nanosleep(32);
+        }
+        __threadfence();
+        *ok = good;
+    }
+    __syncthreads();
+    return *ok != 0;
+}
+
+template <int MODE, class T>
+__global__ void __launch_bounds__(PS_THREADS) psweep_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ mid,
+                                                       const int32_t* __restrict__ sc, const T* __restrict__ sv,
+                                                       const T* __restrict__ dinv, const T* __restrict__ b, T* e,
+                                                       const int32_t* __restrict__ cptr, int ncolors, unsigned* bar,
+                                                       int* err, unsigned long long limit) {
+    __shared__ int ok;
+    const int gl = threadIdx.x & (G - 1);
+    const int rloc = threadIdx.x / G;
+    unsigned target = 0;
+    for (int c = 0; c < ncolors; ++c) {
+        const int32_t r0 = cptr[c], r1 = cptr[c + 1];
+        for (int32_t base = r0 + (int32_t)blockIdx.x * PS_ROWS; base < r1; base += (int32_t)gridDim.x * PS_ROWS) {
+            const int32_t row = base + rloc;
+            const bool act = row < r1;
+            T acc = T(0);
+            if (act) {
+                const int32_t beg = lo[row];
+                const int32_t end = MODE == 0 ? mid[row] : lo[row + 1];
+                acc = row_sum_cg(sc, sv, beg, end, e, gl);
+            }
+            acc = group_reduce(acc);
+            if (act && gl == 0) e[row] = (b[row] - acc) * dinv[row];
+        }
+        if (c + 1 < ncolors) {
+            target += gridDim.x;
+            if (gridDim.x == 1) __syncthreads();
+            else if (!grid_barrier(bar, target, limit, err, &ok)) return;
+        }
+    }
+}
+
+// a barrier that nobody completes: the wait must end at its limit with MGM_ERR_TIMEOUT
+__global__ void barrier_timeout_probe_k(unsigned* bar, int* err, unsigned long long limit) {
+    __shared__ int ok;
+    grid_barrier(bar, gridDim.x + 1, limit, err, &ok);
 }
 
 template <class T>
@@ -169,6 +273,41 @@ static void launch_rows(Level& L, int32_t r0, int32_t r1, cudaStream_t s) {
     CK_LAUNCH();
 }
 
+// blocks for a persistent sweep: enough to cover the largest colour in one pass, at most what can
+// be co-resident (a cooperative launch requires all blocks resident)
+template <int MODE, class T>
+static void launch_psweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
+    const int nc = (int)L.cptr.size() - 1;
+    if (nc <= 0) return;
+    int maxrows = 0;
+    for (int c = 0; c < nc; ++c) maxrows = std::max(maxrows, L.cptr[c + 1] - L.cptr[c]);
+    static int mb = 0;  // per instantiation (MODE, T)
+    if (!mb) {
+        int per_sm = 0, dev = 0, sms = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, psweep_k<MODE, T>, PS_THREADS, 0));
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        mb = std::max(1, per_sm * sms);
+    }
+    const int nblocks = std::max(1, std::min(mb, (maxrows + PS_ROWS - 1) / PS_ROWS));
+    CK(cudaMemsetAsync(L.bar.get(), 0, sizeof(unsigned), s));
+    const int32_t* lo = L.lo.get();
+    const int32_t* mid = L.mid.get();
+    const int32_t* sc = L.sc.get();
+    const T* sv = LV<T>::sv(L);
+    const T* dv = LV<T>::dinv(L);
+    const T* b = LV<T>::b(L);
+    T* e = LV<T>::e(L);
+    const int32_t* cp = L.cptr_dev.get();
+    unsigned* bar = L.bar.get();
+    int* err = H->err.get();
+    unsigned long long limit = PS_SPIN_LIMIT;
+    void* args[] = {(void*)&lo, (void*)&mid, (void*)&sc, (void*)&sv, (void*)&dv, (void*)&b, (void*)&e, (void*)&cp,
+                    (void*)&nc, (void*)&bar, (void*)&err, (void*)&limit};
+    CK(cudaLaunchCooperativeKernel((const void*)psweep_k<MODE, T>, dim3(nblocks), dim3(PS_THREADS), args, 0, s));
+    CK_LAUNCH();
+}
+
 template <class T>
 static void sweep(Level& L, bool from_zero, cudaStream_t s) {
     for (size_t c = 0; c + 1 < L.cptr.size(); ++c) {
@@ -179,6 +318,16 @@ static void sweep(Level& L, bool from_zero, cudaStream_t s) {
 
 // Alg. 3 with a zero initial guess on level 1: b_0 -> e_0
 template <class T>
+static void sweep_any(mgm_hierarchy* H, Level& L, bool from_zero, cudaStream_t s) {
+    if (H->persistent) {
+        if (from_zero) launch_psweep<0, T>(H, L, s);
+        else launch_psweep<1, T>(H, L, s);
+    } else {
+        sweep<T>(L, from_zero, s);
+    }
+}
+
+template <class T>
 static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
     const int p = H->p;
     for (int j = 0; j + 1 < p; ++j) {  // pre-smoothing and restricted residuals
@@ -186,8 +335,8 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
         Level& C = H->lv[j + 1];
         const T* rsrc;
         if (H->nu1 >= 1) {
-            sweep<T>(L, true, s);
-            for (int t = 1; t < H->nu1; ++t) sweep<T>(L, false, s);
+            sweep_any<T>(H, L, true, s);
+            for (int t = 1; t < H->nu1; ++t) sweep_any<T>(H, L, false, s);
             if (H->nu1 == 1) launch_rows<2, T>(L, 0, (int32_t)L.n, s);
             else launch_rows<3, T>(L, 0, (int32_t)L.n, s);
             rsrc = LV<T>::s(L);
@@ -208,14 +357,21 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
         Level& C = H->lv[j + 1];
         interp_k<T><<<grid_for(L.n, 256), 256, 0, s>>>(L.pc.get(), LV<T>::pv(L), L.pw, LV<T>::e(C), LV<T>::e(L), L.n);
         CK_LAUNCH();
-        for (int t = 0; t < H->nu2; ++t) sweep<T>(L, false, s);
+        for (int t = 0; t < H->nu2; ++t) sweep_any<T>(H, L, false, s);
     }
 }
 
 void alloc_work(mgm_hierarchy* H) {
+    H->err.alloc(1);
+    CK(cudaMemset(H->err.get(), 0, sizeof(int)));
     for (int j = 0; j < H->p; ++j) {
         Level& L = H->lv[j];
         const bool smooth = j + 1 < H->p;
+        if (smooth) {
+            L.bar.alloc(1);
+            L.cptr_dev.alloc(L.cptr.size());
+            CK(cudaMemcpy(L.cptr_dev.get(), L.cptr.data(), sizeof(int32_t) * L.cptr.size(), cudaMemcpyHostToDevice));
+        }
         if (H->precision == MGM_F32) {
             L.b32.alloc(L.n); L.e32.alloc(L.n);
             CK(cudaMemset(L.e32.get(), 0, sizeof(float) * L.n));
@@ -340,23 +496,47 @@ void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStrea
         Level& L = H->lv[0];
         const int64_t vs = H->precision == MGM_F32 ? 4 : 8;
         for (int t = 0; t < 2; ++t) {
-            if (H->precision == MGM_F32) sweep<float>(L, false, s);
-            else sweep<double>(L, false, s);
+            if (H->precision == MGM_F32) sweep_any<float>(H, L, false, s);
+            else sweep_any<double>(H, L, false, s);
         }
         CK(cudaEventRecord(e0, s));
         for (int t = 0; t < reps; ++t) {
-            if (H->precision == MGM_F32) sweep<float>(L, false, s);
-            else sweep<double>(L, false, s);
+            if (H->precision == MGM_F32) sweep_any<float>(H, L, false, s);
+            else sweep_any<double>(H, L, false, s);
         }
         CK(cudaEventRecord(e1, s));
         CK(cudaEventSynchronize(e1));
         CK(cudaEventElapsedTime(&ms, e0, e1));
         out->sweep_ms = ms / reps;
         out->sweep_bytes = (L.nlow + L.nupp) * (vs + 4) + L.n * (4 + 3 * vs);
-        out->sweep_launches = (int32_t)(L.cptr.size() - 1);
+        out->sweep_launches = H->persistent ? 1 : (int32_t)(L.cptr.size() - 1);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+}
+
+// reads and clears the device error word of the persistent kernels
+void check_device_error(mgm_hierarchy* H, cudaStream_t s) {
+    int e = read1(H->err.get(), s);
+    if (e) {
+        CK(cudaMemsetAsync(H->err.get(), 0, sizeof(int), s));
+        fail(MGM_ERR_TIMEOUT, "a device-side barrier wait gave up (spin limit reached)");
+    }
+}
+
+// Runs a grid barrier that can never complete (one arrival short) with the given spin limit and
+// returns the error word: exercises the bounded-wait path without hanging anything.
+int barrier_timeout_probe(int nblocks, unsigned long long limit, cudaStream_t s) {
+    Temp<unsigned> bar(1, s);
+    Temp<int> err(1, s);
+    CK(cudaMemsetAsync(bar.get(), 0, sizeof(unsigned), s));
+    CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    unsigned* b = bar.get();
+    int* e = err.get();
+    void* args[] = {(void*)&b, (void*)&e, (void*)&limit};
+    CK(cudaLaunchCooperativeKernel((const void*)barrier_timeout_probe_k, dim3(nblocks), dim3(32), args, 0, s));
+    CK_LAUNCH();
+    return read1(err.get(), s);
 }
 
 void vcycle_api(mgm_hierarchy* H, const void* r, void* z, int dtype, cudaStream_t s) {
@@ -365,6 +545,7 @@ void vcycle_api(mgm_hierarchy* H, const void* r, void* z, int dtype, cudaStream_
     load_input(H, r, dtype, H->ord_caller.get(), s);
     vcycle_core(H, s);
     store_output(H, z, dtype, H->ord_caller.get(), s);
+    if (H->persistent) check_device_error(H, s);
 }
 
 }  // namespace mgm

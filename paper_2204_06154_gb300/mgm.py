@@ -37,7 +37,7 @@ class StencilParams(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("n_min", C.c_int64), ("m", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("persistent_sweeps", C.c_int)]
 
 
 class SolveParams(C.Structure):
@@ -57,7 +57,7 @@ class HierStats(C.Structure):
 EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", "mgm_build_stencils", "mgm_coarsen", "mgm_interp",
            "mgm_transpose", "mgm_spgemm", "mgm_rcm", "mgm_color", "mgm_setup", "mgm_vcycle", "mgm_solve",
            "mgm_hierarchy_stats_get", "mgm_hierarchy_level", "mgm_hierarchy_pnnz", "mgm_profile",
-           "mgm_kernel_launches", "mgm_destroy", "mgm_status_string", "mgm_last_error_message",
+           "mgm_kernel_launches", "mgm_check_bounded_wait", "mgm_destroy", "mgm_status_string", "mgm_last_error_message",
            "mgm_last_error_row"]
 
 
@@ -92,6 +92,7 @@ def lib():
         L.mgm_hierarchy_level.argtypes = [P, I] + [P] * 10 + [P]
         L.mgm_hierarchy_pnnz.argtypes = [P, I, C.POINTER(C.c_int64)]
         L.mgm_profile.argtypes = [P, I, C.POINTER(ProfileInfo), P]
+        L.mgm_check_bounded_wait.argtypes = [I, I64, C.POINTER(C.c_int), P]
         L.mgm_kernel_launches.argtypes = []
         L.mgm_kernel_launches.restype = C.c_int64
         L.mgm_destroy.argtypes = [P]
@@ -246,12 +247,12 @@ def color(rp, ci, seed):
 class Hierarchy:
     """MGM hierarchy (Alg. 2) owned by the library; V-cycle (Alg. 3) and FGMRES solve on it."""
 
-    def __init__(self, xyz, rp, ci, v, n_min, m=3, nu1=1, nu2=1, precision="f32", seed=0):
+    def __init__(self, xyz, rp, ci, v, n_min, m=3, nu1=1, nu2=1, precision="f32", seed=0, persistent_sweeps=False):
         xyz = _dev(xyz, torch.float64, "xyz"); rp = _dev(rp, torch.int32, "rowptr")
         ci = _dev(ci, torch.int32, "col"); v = _dev(v, torch.float64, "val")
         self.N = xyz.shape[0]
         self.device = xyz.device
-        prm = Params(n_min, m, nu1, nu2, MGM_F32 if precision == "f32" else MGM_F64, seed)
+        prm = Params(n_min, m, nu1, nu2, MGM_F32 if precision == "f32" else MGM_F64, seed, int(persistent_sweeps))
         h = C.c_void_p()
         self._h = None
         _check(lib().mgm_setup(_p(xyz), self.N, _p(rp), _p(ci), _p(v), C.byref(prm), C.byref(h), _stream()))
@@ -322,6 +323,14 @@ class Hierarchy:
             _check(st)
         return u, {"iters": info.iters, "rel_res": info.rel_res, "solve_ms": info.solve_ms, "converged": st == 0,
                    "history": [hist[i] for i in range(info.iters + 1)]}
+
+
+def check_bounded_wait(nblocks=4, spin_limit=20000):
+    """Run a device barrier that cannot complete; returns the status the library reports
+    (MGM_ERR_TIMEOUT = 5 when the bounded wait gave up as designed)."""
+    st = C.c_int(-1)
+    _check(lib().mgm_check_bounded_wait(nblocks, spin_limit, C.byref(st), _stream()))
+    return st.value
 
 
 def kernel_launches():

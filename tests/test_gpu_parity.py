@@ -273,3 +273,23 @@ def test_single_level_and_small(M, oracle):
     u, info = Hg.solve(T(f), tol=1e-12)
     ref = np.linalg.solve(L.toarray(), f)
     assert info["converged"] and np.linalg.norm(H(u) - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_persistent_and_per_colour_sweeps_identical(M, oracle, ico5):
+    """The persistent multicolour sweep (one cooperative launch per sweep, grid barriers between
+    colours) computes every row exactly as the one-launch-per-colour schedule does."""
+    x, nrm, idx, w, L = ico5
+    Lt = (T(L.indptr.astype(np.int32)), T(L.indices.astype(np.int32)), T(L.data))
+    r = T(np.random.default_rng(5).standard_normal(x.shape[0]))
+    for prec in ("f32", "f64"):
+        Ha = M.Hierarchy(T(x), *Lt, n_min=125, precision=prec)
+        Hb = M.Hierarchy(T(x), *Lt, n_min=125, precision=prec, persistent_sweeps=True)
+        assert torch.equal(Ha.vcycle(r), Hb.vcycle(r))
+
+
+def test_bounded_wait_reports_timeout(M):
+    """A device barrier that can never complete gives up at its spin limit and the host reads
+    MGM_ERR_TIMEOUT; the context stays usable afterwards."""
+    assert M.check_bounded_wait(nblocks=4, spin_limit=20000) == 5
+    x = torch.ones(10, device=DEV)
+    assert float(x.sum()) == 10.0
