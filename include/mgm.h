@@ -226,6 +226,24 @@ mgm_status mgm_vcycle(mgm_hierarchy* H, const void* r, void* z, int dtype, mgm_s
 mgm_status mgm_solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp,
                      mgm_solve_info* info, mgm_stream stream);
 
+/* Many right-hand sides on one hierarchy (same operator): solves L U[:, r] = F[:, r] for
+ * r < nrhs (1 <= nrhs <= 8). F and U are N x nrhs column-major device arrays (column r at
+ * F + r N, caller order); U holds initial guesses on entry and solutions on return. The V-cycle
+ * and the outer operator run once per iteration for all columns (each matrix entry read once for
+ * all right-hand sides; vectors interleaved internally); each column has its own FGMRES process
+ * (Sec. 4.6), Givens rotations and convergence test, and stops contributing once it converges.
+ * info (may be NULL) has nrhs entries. Returns MGM_ERR_NOT_CONVERGED if a column misses tol. */
+mgm_status mgm_solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* U, const mgm_solve_params* sp,
+                           mgm_solve_info* info, mgm_stream stream);
+
+/* A batch of independent problems (one hierarchy each, possibly of different sizes), each with
+ * nrhs right-hand sides: problem q solves with H[q], F[q], U[q] (device pointers, layout as in
+ * mgm_solve_multi); info (may be NULL) has nprob * nrhs entries, problem-major. Problems run one
+ * after another on `stream`, each with its right-hand sides batched. Returns the first failing
+ * status (the remaining problems are still solved). */
+mgm_status mgm_solve_batched(mgm_hierarchy* const* H, int nprob, const double* const* F, double* const* U, int nrhs,
+                             const mgm_solve_params* sp, mgm_solve_info* info, mgm_stream stream);
+
 /* Sizes of the hierarchy (host struct). */
 mgm_status mgm_hierarchy_stats_get(const mgm_hierarchy* H, mgm_hierarchy_stats* out);
 

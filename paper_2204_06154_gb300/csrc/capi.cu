@@ -155,6 +155,23 @@ mgm_status mgm_solve(mgm_hierarchy* H, const double* f, double* u, const mgm_sol
     return guarded([&] { solve(H, f, u, sp, info, S(stream)); });
 }
 
+mgm_status mgm_solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* U, const mgm_solve_params* sp,
+                           mgm_solve_info* info, mgm_stream stream) {
+    return guarded([&] { solve_multi(H, nrhs, F, U, sp, info, S(stream)); });
+}
+
+mgm_status mgm_solve_batched(mgm_hierarchy* const* H, int nprob, const double* const* F, double* const* U, int nrhs,
+                             const mgm_solve_params* sp, mgm_solve_info* info, mgm_stream stream) {
+    mgm_status first = MGM_OK;
+    mgm_status st = guarded([&] { REQUIRE(H && F && U && nprob >= 1, "bad argument"); });
+    if (st != MGM_OK) return st;
+    for (int q = 0; q < nprob; ++q) {
+        st = guarded([&] { solve_multi(H[q], nrhs, F[q], U[q], sp, info ? info + (size_t)q * nrhs : nullptr, S(stream)); });
+        if (st != MGM_OK && first == MGM_OK) first = st;
+    }
+    return first;
+}
+
 mgm_status mgm_hierarchy_stats_get(const mgm_hierarchy* H, mgm_hierarchy_stats* out) {
     return guarded([&] {
         REQUIRE(H && out, "null argument");

@@ -79,6 +79,7 @@ struct mgm_hierarchy {
     mgm::Buf<double> Z64;
     mgm::Buf<double> ydev;
     double* hhost = nullptr;    // pinned
+    void* multi = nullptr;      // workspace of the many-right-hand-side solve (multi.cu)
     int64_t device_bytes = 0;
     ~mgm_hierarchy();
 };
@@ -97,4 +98,8 @@ void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStrea
 void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
 void solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp, mgm_solve_info* info,
            cudaStream_t s);
+// multi.cu
+void solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* U, const mgm_solve_params* sp, mgm_solve_info* info,
+                 cudaStream_t s);
+void free_multi(mgm_hierarchy* H);
 }  // namespace mgm

@@ -536,6 +536,7 @@ void hierarchy_level(const mgm_hierarchy* H, int j, int32_t* perm, int32_t* keep
 }  // namespace mgm
 
 mgm_hierarchy::~mgm_hierarchy() {
+    mgm::free_multi(this);
     if (vgraph) cudaGraphExecDestroy(vgraph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (hhost) cudaFreeHost(hhost);

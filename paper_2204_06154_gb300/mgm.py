@@ -55,7 +55,8 @@ class HierStats(C.Structure):
 
 
 EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", "mgm_build_stencils", "mgm_coarsen", "mgm_interp",
-           "mgm_transpose", "mgm_spgemm", "mgm_rcm", "mgm_color", "mgm_setup", "mgm_vcycle", "mgm_solve",
+           "mgm_transpose", "mgm_spgemm", "mgm_rcm", "mgm_color", "mgm_setup", "mgm_vcycle", "mgm_solve", "mgm_solve_multi",
+           "mgm_solve_batched",
            "mgm_hierarchy_stats_get", "mgm_hierarchy_level", "mgm_hierarchy_pnnz", "mgm_profile",
            "mgm_kernel_launches", "mgm_check_bounded_wait", "mgm_destroy", "mgm_status_string", "mgm_last_error_message",
            "mgm_last_error_row"]
@@ -88,6 +89,9 @@ def lib():
         L.mgm_setup.argtypes = [P, I64, P, P, P, C.POINTER(Params), C.POINTER(P), P]
         L.mgm_vcycle.argtypes = [P, P, P, I, P]
         L.mgm_solve.argtypes = [P, P, P, C.POINTER(SolveParams), C.POINTER(SolveInfo), P]
+        L.mgm_solve_multi.argtypes = [P, I, P, P, C.POINTER(SolveParams), C.POINTER(SolveInfo), P]
+        L.mgm_solve_batched.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), I, C.POINTER(SolveParams),
+                                        C.POINTER(SolveInfo), P]
         L.mgm_hierarchy_stats_get.argtypes = [P, C.POINTER(HierStats)]
         L.mgm_hierarchy_level.argtypes = [P, I] + [P] * 10 + [P]
         L.mgm_hierarchy_pnnz.argtypes = [P, I, C.POINTER(C.c_int64)]
@@ -336,6 +340,56 @@ def check_bounded_wait(nblocks=4, spin_limit=20000):
 def kernel_launches():
     """Kernels launched by libmgm so far in this process."""
     return int(lib().mgm_kernel_launches())
+
+
+def _multi_infos(nrhs, maxit):
+    hists = [(C.c_double * (maxit + 2))() for _ in range(nrhs)]
+    infos = (SolveInfo * nrhs)()
+    for r in range(nrhs):
+        infos[r] = SolveInfo(0, 0.0, hists[r], maxit + 2, 0.0)
+    return infos, hists
+
+
+def _info_dicts(infos, hists, st, nrhs):
+    return [{"iters": infos[r].iters, "rel_res": infos[r].rel_res, "solve_ms": infos[r].solve_ms,
+             "converged": st == 0 or infos[r].rel_res <= 0.0,
+             "history": [hists[r][i] for i in range(infos[r].iters + 1)]} for r in range(nrhs)]
+
+
+def solve_multi(H, F, U0=None, krylov="fgmres", restart=50, maxit=200, tol=1e-10):
+    """mgm_solve_multi: F is (nrhs, N) float64 CUDA (row r = right-hand side r); returns (U, infos)."""
+    F = _dev(F, torch.float64, "F")
+    nrhs = F.shape[0]
+    U = torch.zeros_like(F) if U0 is None else _dev(U0, torch.float64, "U0").clone()
+    sp = SolveParams(MGM_KRYLOV_FGMRES if krylov == "fgmres" else MGM_KRYLOV_NONE, restart, maxit, tol)
+    infos, hists = _multi_infos(nrhs, maxit)
+    st = lib().mgm_solve_multi(H._h, nrhs, _p(F), _p(U), C.byref(sp), infos, _stream())
+    if st not in (0, 3):
+        _check(st)
+    out = _info_dicts(infos, hists, st, nrhs)
+    for r in range(nrhs):
+        out[r]["converged"] = infos[r].rel_res <= tol
+    return U, out
+
+
+def solve_batched(Hs, Fs, krylov="fgmres", restart=50, maxit=200, tol=1e-10):
+    """mgm_solve_batched over problems q (hierarchy Hs[q], right-hand sides Fs[q] of shape (nrhs, N_q))."""
+    nprob = len(Hs)
+    nrhs = Fs[0].shape[0]
+    Fs = [_dev(F, torch.float64, "F") for F in Fs]
+    Us = [torch.zeros_like(F) for F in Fs]
+    hp = (C.c_void_p * nprob)(*[H._h for H in Hs])
+    fp = (C.c_void_p * nprob)(*[F.data_ptr() for F in Fs])
+    up = (C.c_void_p * nprob)(*[U.data_ptr() for U in Us])
+    sp = SolveParams(MGM_KRYLOV_FGMRES if krylov == "fgmres" else MGM_KRYLOV_NONE, restart, maxit, tol)
+    infos, hists = _multi_infos(nprob * nrhs, maxit)
+    st = lib().mgm_solve_batched(hp, nprob, fp, up, nrhs, C.byref(sp), infos, _stream())
+    if st not in (0, 3):
+        _check(st)
+    out = _info_dicts(infos, hists, st, nprob * nrhs)
+    for q in range(nprob * nrhs):
+        out[q]["converged"] = infos[q].rel_res <= tol
+    return Us, [out[q * nrhs:(q + 1) * nrhs] for q in range(nprob)]
 
 
 def solve_points(xyz, nrm, f, n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, n_min=250, m=3, precision="f32",

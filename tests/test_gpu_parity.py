@@ -293,3 +293,51 @@ def test_bounded_wait_reports_timeout(M):
     assert M.check_bounded_wait(nblocks=4, spin_limit=20000) == 5
     x = torch.ones(10, device=DEV)
     assert float(x.sum()) == 10.0
+
+
+@pytest.mark.parametrize("prec,nrhs", [("f32", 3), ("f64", 8), ("f32", 1)])
+def test_solve_multi_matches_oracle(M, oracle, ico5, hier, prec, nrhs):
+    """Many right-hand sides on one hierarchy: every column matches the oracle's solution of
+    its own system, and the iteration counts per column stay within +-2 of single solves."""
+    x, nrm, idx, w, L = ico5
+    Hg, Ho = hier
+    rng = np.random.default_rng(21)
+    F = rng.standard_normal((nrhs, x.shape[0]))
+    U, infos = M.solve_multi(Hg[prec], T(F), tol=1e-10)
+    Uh = H(U)
+    for r in range(nrhs):
+        uo, ito, _ = oracle.fgmres(L, Ho, F[r], tol=1e-12)
+        assert infos[r]["converged"], infos[r]
+        assert np.linalg.norm(Uh[r] - uo) <= 1e-8 * np.linalg.norm(uo)
+        _, it1, _ = oracle.fgmres(L, Ho, F[r], tol=1e-10)
+        assert abs(infos[r]["iters"] - it1) <= 2
+
+
+def test_solve_multi_standalone_and_zero_column(M, oracle, ico5, hier):
+    x, nrm, idx, w, L = ico5
+    Hg, Ho = hier
+    F = np.random.default_rng(2).standard_normal((2, x.shape[0]))
+    F[1] = 0.0
+    U, infos = M.solve_multi(Hg["f64"], T(F), krylov="none", tol=1e-8, maxit=200)
+    uo, ito, _ = oracle.mgm_solve(L, Ho, F[0], tol=1e-8)
+    assert infos[0]["converged"] and abs(infos[0]["iters"] - ito) <= 1
+    assert np.all(H(U)[1] == 0.0)
+
+
+def test_solve_batched_uneven_problems(M, oracle):
+    """A batch of problems of different sizes (and depths), 4 right-hand sides each."""
+    probs = []
+    for q, N in enumerate((3000, 9001)):
+        xq, nq = I.bumpy_sphere(N, seed=30 + q)
+        idx_q, w_q, L_q = oracle.build_operator(xq, nq, 25, "gfd", ell=2, alpha=4.0, mu=1e-3)
+        Lt = (T(L_q.indptr.astype(np.int32)), T(L_q.indices.astype(np.int32)), T(L_q.data))
+        Hq = M.Hierarchy(T(xq), *Lt, n_min=60, precision="f32")
+        Ho = oracle.setup(xq, L_q, 60, seed=0)
+        F = np.random.default_rng(q).standard_normal((4, N))
+        probs.append((Hq, Ho, L_q, F))
+    Us, infos = M.solve_batched([p[0] for p in probs], [T(p[3]) for p in probs], tol=1e-10)
+    for (Hq, Ho, L_q, F), U, inf in zip(probs, Us, infos):
+        for r in range(4):
+            uo, _, _ = oracle.fgmres(L_q, Ho, F[r], tol=1e-12)
+            assert inf[r]["converged"]
+            assert np.linalg.norm(H(U)[r] - uo) <= 1e-8 * np.linalg.norm(uo)
