@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--size", type=int, default=1048576, help="points per surface")
     ap.add_argument("--cpu-sample", type=int, default=32768, help="points of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: the N=1M sphere/torus time-to-solution line; c3: the full 64-surface batched line")
+    ap.add_argument("--batch-problems", type=int, default=16, help="surfaces in the batched measurement of the c2 line")
     ap.add_argument("--single", action="store_true",
                     help="one pass of the path on the sphere only (a small driver for profilers); prints its phases")
     return ap.parse_args()
@@ -223,6 +226,8 @@ def bench_ours(a, rank, world, local_rank):
     res["e2e_ms"] = e0.elapsed_time(e1) / len(hp)
     res["e2e_h2d"] = h2d // len(hp)
     res["e2e_d2h"] = d2h // len(hp)
+    if a.batch_problems > 0:
+        res["batched"] = bench_batched(a.batch_problems, dev)
     return res
 
 
@@ -240,6 +245,66 @@ def oracle_sample(Ns):
     u, it, rel = O.fgmres(L, Hh, f, tol=P["tol"], restart=P["restart"], maxit=P["maxit"])
     dt = time.perf_counter() - t0
     return dt * 1e3, it, rel
+
+
+# ----------------------------------------------------------------------------------------------
+# batched heat-step solves on bumpy spheres (GFD), many right-hand sides per surface
+# ----------------------------------------------------------------------------------------------
+C3 = dict(n=25, ell=2, alpha=4.0, n_min=250, tol=1e-8, nrhs=8)
+
+
+def c3_problems(nprob, seed=3):
+    from paper_2204_06154_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(20000), np.log(400000), nprob)).astype(int)
+    out = []
+    for q, N in enumerate(sizes):
+        x, nrm = I.bumpy_sphere(int(N), seed=seed * 1000 + q)
+        h2 = 4.0 * math.pi / N                       # t = h^2 with h the mean spacing of a unit sphere
+        dirs = rng.standard_normal((C3["nrhs"], 3))
+        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+        xn = x / np.linalg.norm(x, axis=1, keepdims=True)
+        F = np.zeros((C3["nrhs"], N))
+        for r in range(C3["nrhs"]):
+            F[r, int(np.argmax(xn @ dirs[r]))] = 1.0   # delta source at the node nearest the direction
+        out.append((x, nrm, F, h2))
+    return out
+
+
+def bench_batched(nprob, dev):
+    import torch
+    from paper_2204_06154_gb300 import mgm as M
+    probs = c3_problems(nprob)
+    d = [(torch.from_numpy(x).to(dev), torch.from_numpy(n).to(dev), torch.from_numpy(F).to(dev), h2)
+         for x, n, F, h2 in probs]
+    E = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    E[0].record()
+    Hs = []
+    for x, n, F, h2 in d:
+        _, _, rp, ci, v = M.build_stencils(x, n, C3["n"], "gfd", ell=C3["ell"], mu=h2, alpha=C3["alpha"],
+                                           keep_weights=False)
+        Hs.append(M.Hierarchy(x, rp, ci, v, C3["n_min"], precision="f32"))
+    E[1].record()
+    Us, infos = M.solve_batched(Hs, [F for _, _, F, _ in d], tol=C3["tol"], restart=30)
+    E[2].record()
+    single_iters = []
+    for H, (x, n, F, h2) in zip(Hs, d):
+        for r in range(F.shape[0]):
+            u, inf = H.solve(F[r].contiguous(), tol=C3["tol"], restart=30)
+            single_iters.append(inf["iters"])
+    E[3].record()
+    E[3].synchronize()
+    flat = [i for inf in infos for i in inf]
+    nrhs_total = len(flat)
+    return {"problems": nprob, "points": int(sum(x.shape[0] for x, _, _, _ in probs)), "rhs_per_problem": C3["nrhs"],
+            "discretisation": "GFD ell=2 n=25 alpha=4, (I - h^2 Lap) u = delta, tol 1e-8",
+            "setup_ms": round(E[0].elapsed_time(E[1]), 1), "batched_solve_ms": round(E[1].elapsed_time(E[2]), 2),
+            "one_rhs_at_a_time_ms": round(E[2].elapsed_time(E[3]), 2),
+            "batching_speedup": round(E[2].elapsed_time(E[3]) / E[1].elapsed_time(E[2]), 2),
+            "ms_per_rhs": round(E[1].elapsed_time(E[2]) / nrhs_total, 3),
+            "iters_max": max(i["iters"] for i in flat), "iters_single_max": max(single_iters),
+            "converged": all(i["converged"] for i in flat)}
 
 
 def cpu_baseline(a, Ns=None):
@@ -293,6 +358,17 @@ def main():
         r, H, u = run_problem(M, torch, *d)
         print(json.dumps({"single": True, "N": a.size, **{k: (round(v, 3) if isinstance(v, float) else v)
                                                          for k, v in r.items()}}), flush=True)
+        return
+    if a.workload == "c3":
+        import torch
+        torch.cuda.set_device(local_rank)
+        from paper_2204_06154_gb300 import mgm as M
+        M.lib()
+        b = bench_batched(64, torch.device("cuda", local_rank))
+        print(json.dumps({"metric": "batched heat-step solves: ms per right-hand side", "value": b["ms_per_rhs"],
+                          "unit": "ms", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+                          "config": {"workload": "64 bumpy spheres, N log-uniform 20k-400k, 8 delta RHS each"},
+                          "batched": b}), flush=True)
         return
     if world > 1:
         import torch
@@ -349,6 +425,7 @@ def main():
         "e2e": {"value": round(res["e2e_ms"], 2), "unit": "ms", "h2d_bytes_per_step": res["e2e_h2d"],
                 "d2h_bytes_per_step": res["e2e_d2h"]},
         "gpu_launches": res["launches"],
+        "batched": res.get("batched"),
         "clocks": res["clocks"],
     }
     if not a.no_cpu_baseline and world == 1:

@@ -68,6 +68,9 @@ def lib():
         L.or_mgm_solve.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, f64p, i32p, C.c_void_p,
                                    C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_double,
                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.or_mlp_features.argtypes = [i64, C.c_int, i32p, f64p, f64p, f64p, f64p, f64p, f64p]
+        L.or_mlp_forward.argtypes = [i64, C.c_int, f64p, f64p, f64p, f64p, f64p, C.c_void_p, C.c_void_p]
+        L.or_mlp_backward.argtypes = [i64, C.c_int, f64p, f64p, f64p, f64p, f64p, f64p, f64p, f64p, f64p]
         _LIB = L
     return _LIB
 
@@ -384,3 +387,32 @@ def mgm_solve(A, H, f, x0=None, maxit=200, tol=1e-10):
     lib().or_mgm_solve(n, rp, ci, v, C.addressof(lv), H.p, H.lu, H.piv, H.perm[0].ctypes.data, H.nu1, H.nu2,
                        _c(f, np.float64), x, maxit, tol, C.byref(it), C.byref(rel))
     return x, it.value, rel.value
+
+
+# ----------------------------------------------------------------------------------------------
+# Learned smoother (an addition to the paper's method; see mgm_oracle.c for the definitions)
+# ----------------------------------------------------------------------------------------------
+def mlp_features(idx, xyz, nrm, w, r):
+    """Per-point features (N x 4n) and residual scales rho (N)."""
+    idx = _c(idx, np.int32); N, n = idx.shape
+    feat = np.empty((N, 4 * n)); rho = np.empty(N)
+    _check("mlp_features", lib().or_mlp_features(N, n, idx, _c(xyz, np.float64), _c(nrm, np.float64),
+                                                 _c(w, np.float64), _c(r, np.float64), feat, rho))
+    return feat, rho
+
+
+def mlp_forward(W1, W2, w3, feat):
+    feat = _c(feat, np.float64); N, din = feat.shape
+    out = np.empty(N)
+    _check("mlp_forward", lib().or_mlp_forward(N, din, _c(W1, np.float64), _c(W2, np.float64), _c(w3, np.float64),
+                                               feat, out, None, None))
+    return out
+
+
+def mlp_backward(W1, W2, w3, feat, target):
+    """Mean-squared-error loss and its gradients with respect to W1, W2, w3."""
+    feat = _c(feat, np.float64); N, din = feat.shape
+    g1 = np.empty((64, din)); g2 = np.empty((64, 64)); g3 = np.empty(64); loss = np.empty(1)
+    _check("mlp_backward", lib().or_mlp_backward(N, din, _c(W1, np.float64), _c(W2, np.float64), _c(w3, np.float64),
+                                                 feat, _c(target, np.float64), g1, g2, g3, loss))
+    return float(loss[0]), g1, g2, g3

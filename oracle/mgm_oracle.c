@@ -977,3 +977,98 @@ int or_mgm_solve(int64_t n, const int32_t* arp, const int32_t* aci, const double
     *iters_out = it; *relres_out = rel;
     return rel <= tol ? OR_OK : OR_ERR_NOTCONV;
 }
+
+/* ===========================================================================================
+ * Learned smoother (not in the paper; an addition of this project's scope, judged by this
+ * oracle). Per point i of the finest level, with stencil idx[i][0..n) (centre first):
+ *   features f[4j..4j+3] = ( xh_j / s, yh_j / s, c_ij s^2, r_{idx_ij} / rho_i ),  j < n,
+ * with (xh, yh) the tangent-plane offsets of Sec. 2.1, s the stencil support, c_ij the LBO
+ * weights, r the residual and rho_i = sqrt(mean_j r_{idx_ij}^2) (features 0 when rho_i = 0);
+ * network out = w3 . relu(W2 relu(W1 f)) (no biases, 4n -> 64 -> 64 -> 1); correction
+ * delta_i = rho_i * out_i / l_ii. Row-major weights: W1 [64][4n], W2 [64][64], w3 [64].
+ * =========================================================================================== */
+int or_mlp_features(int64_t N, int n, const int32_t* idx, const double* xyz, const double* nrm, const double* w,
+                    const double* r, double* feat, double* rho) {
+    if (n < 1 || n > MAXM) return OR_ERR_ARG;
+    double xh[MAXM], yh[MAXM];
+    for (int64_t i = 0; i < N; ++i) {
+        const int32_t* id = idx + i * n;
+        double s = project_stencil(xyz, nrm, i, id, n, xh, yh);
+        double ss = 0.0;
+        for (int j = 0; j < n; ++j) ss = ss + r[id[j]] * r[id[j]];
+        double rh = sqrt(ss / (double)n);
+        rho[i] = rh;
+        double* f = feat + i * 4 * n;
+        for (int j = 0; j < n; ++j) {
+            f[4 * j + 0] = s > 0.0 ? xh[j] / s : 0.0;
+            f[4 * j + 1] = s > 0.0 ? yh[j] / s : 0.0;
+            f[4 * j + 2] = w[i * n + j] * (s * s);
+            f[4 * j + 3] = rh > 0.0 ? r[id[j]] / rh : 0.0;
+        }
+    }
+    return OR_OK;
+}
+
+/* forward: out[i]; h1, h2 (N x 64 each, may be NULL) keep the post-ReLU activations */
+int or_mlp_forward(int64_t N, int din, const double* W1, const double* W2, const double* w3, const double* feat,
+                   double* out, double* h1o, double* h2o) {
+    double h1[64], h2[64];
+    for (int64_t i = 0; i < N; ++i) {
+        const double* f = feat + i * din;
+        for (int a = 0; a < 64; ++a) {
+            double acc = 0.0;
+            for (int k = 0; k < din; ++k) acc = acc + W1[a * din + k] * f[k];
+            h1[a] = acc > 0.0 ? acc : 0.0;
+        }
+        for (int a = 0; a < 64; ++a) {
+            double acc = 0.0;
+            for (int k = 0; k < 64; ++k) acc = acc + W2[a * 64 + k] * h1[k];
+            h2[a] = acc > 0.0 ? acc : 0.0;
+        }
+        double o = 0.0;
+        for (int k = 0; k < 64; ++k) o = o + w3[k] * h2[k];
+        out[i] = o;
+        if (h1o) for (int a = 0; a < 64; ++a) h1o[i * 64 + a] = h1[a];
+        if (h2o) for (int a = 0; a < 64; ++a) h2o[i * 64 + a] = h2[a];
+    }
+    return OR_OK;
+}
+
+/* backward of loss = mean_i (out_i - t_i)^2 over N points: gradients summed into gW1, gW2, gw3
+ * (overwritten); returns the loss through *loss */
+int or_mlp_backward(int64_t N, int din, const double* W1, const double* W2, const double* w3, const double* feat,
+                    const double* target, double* gW1, double* gW2, double* gw3, double* loss) {
+    double h1[64], h2[64], z1[64], z2[64], d2[64], d1[64];
+    for (int k = 0; k < 64 * din; ++k) gW1[k] = 0.0;
+    for (int k = 0; k < 64 * 64; ++k) gW2[k] = 0.0;
+    for (int k = 0; k < 64; ++k) gw3[k] = 0.0;
+    double L = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        const double* f = feat + i * din;
+        for (int a = 0; a < 64; ++a) {
+            double acc = 0.0;
+            for (int k = 0; k < din; ++k) acc = acc + W1[a * din + k] * f[k];
+            z1[a] = acc; h1[a] = acc > 0.0 ? acc : 0.0;
+        }
+        for (int a = 0; a < 64; ++a) {
+            double acc = 0.0;
+            for (int k = 0; k < 64; ++k) acc = acc + W2[a * 64 + k] * h1[k];
+            z2[a] = acc; h2[a] = acc > 0.0 ? acc : 0.0;
+        }
+        double o = 0.0;
+        for (int k = 0; k < 64; ++k) o = o + w3[k] * h2[k];
+        double e = o - target[i];
+        L = L + e * e;
+        double g = 2.0 * e / (double)N;             /* d loss / d out_i */
+        for (int k = 0; k < 64; ++k) { gw3[k] = gw3[k] + g * h2[k]; d2[k] = (z2[k] > 0.0) ? g * w3[k] : 0.0; }
+        for (int a = 0; a < 64; ++a) for (int k = 0; k < 64; ++k) gW2[a * 64 + k] = gW2[a * 64 + k] + d2[a] * h1[k];
+        for (int k = 0; k < 64; ++k) {
+            double acc = 0.0;
+            for (int a = 0; a < 64; ++a) acc = acc + W2[a * 64 + k] * d2[a];
+            d1[k] = (z1[k] > 0.0) ? acc : 0.0;
+        }
+        for (int a = 0; a < 64; ++a) for (int k = 0; k < din; ++k) gW1[a * din + k] = gW1[a * din + k] + d1[a] * f[k];
+    }
+    *loss = L / (double)N;
+    return OR_OK;
+}
