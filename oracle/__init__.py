@@ -70,7 +70,7 @@ def lib():
                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.or_mlp_features.argtypes = [i64, C.c_int, i32p, f64p, f64p, f64p, f64p, f64p, f64p]
         L.or_mlp_forward.argtypes = [i64, C.c_int, f64p, f64p, f64p, f64p, f64p, C.c_void_p, C.c_void_p]
-        L.or_mlp_backward.argtypes = [i64, C.c_int, f64p, f64p, f64p, f64p, f64p, f64p, f64p, f64p, f64p]
+        L.or_mlp_vjp.argtypes = [i64, C.c_int, f64p, f64p, f64p, f64p, f64p, f64p, f64p, f64p]
         _LIB = L
     return _LIB
 
@@ -409,10 +409,39 @@ def mlp_forward(W1, W2, w3, feat):
     return out
 
 
-def mlp_backward(W1, W2, w3, feat, target):
-    """Mean-squared-error loss and its gradients with respect to W1, W2, w3."""
+def mlp_vjp(W1, W2, w3, feat, gout):
+    """Gradients of sum_i gout_i * out_i with respect to (W1, W2, w3)."""
     feat = _c(feat, np.float64); N, din = feat.shape
-    g1 = np.empty((64, din)); g2 = np.empty((64, 64)); g3 = np.empty(64); loss = np.empty(1)
-    _check("mlp_backward", lib().or_mlp_backward(N, din, _c(W1, np.float64), _c(W2, np.float64), _c(w3, np.float64),
-                                                 feat, _c(target, np.float64), g1, g2, g3, loss))
-    return float(loss[0]), g1, g2, g3
+    g1 = np.empty((64, din)); g2 = np.empty((64, 64)); g3 = np.empty(64)
+    _check("mlp_vjp", lib().or_mlp_vjp(N, din, _c(W1, np.float64), _c(W2, np.float64), _c(w3, np.float64),
+                                       feat, _c(gout, np.float64), g1, g2, g3))
+    return g1, g2, g3
+
+
+def mlp_backward(W1, W2, w3, feat, target):
+    """Mean-squared-error loss mean_i (out_i - t_i)^2 and its gradients (through mlp_vjp)."""
+    out = mlp_forward(W1, W2, w3, feat)
+    e = out - _c(target, np.float64)
+    g1, g2, g3 = mlp_vjp(W1, W2, w3, feat, 2.0 * e / len(e))
+    return float(np.mean(e * e)), g1, g2, g3
+
+
+def learned_correction(L, idx, xyz, nrm, w, r, W1, W2, w3):
+    """delta_i = rho_i * out_i / l_ii for residual r (caller order)."""
+    feat, rho = mlp_features(idx, xyz, nrm, w, r)
+    return rho * mlp_forward(W1, W2, w3, feat) / L.diagonal()
+
+
+def learned_loss(L, idx, xyz, nrm, w, r, W1, W2, w3):
+    """Training objective of the learned correction: the residual it leaves, relative,
+    J = |r - L delta|^2 / |r|^2, and dJ/d(W1, W2, w3). With s = r - L delta,
+    dJ/d out_i = -2 (rho_i / l_ii) (L^T s)_i / |r|^2 (the SpMVs are scipy's)."""
+    r = _c(r, np.float64)
+    feat, rho = mlp_features(idx, xyz, nrm, w, r)
+    sc = rho / L.diagonal()
+    d = sc * mlp_forward(W1, W2, w3, feat)
+    s = r - L @ d
+    rr = float(r @ r)
+    gout = -2.0 * sc * (L.T @ s) / rr
+    g1, g2, g3 = mlp_vjp(W1, W2, w3, feat, gout)
+    return float(s @ s) / rr, g1, g2, g3

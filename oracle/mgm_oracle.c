@@ -986,6 +986,8 @@ int or_mgm_solve(int64_t n, const int32_t* arp, const int32_t* aci, const double
  * weights, r the residual and rho_i = sqrt(mean_j r_{idx_ij}^2) (features 0 when rho_i = 0);
  * network out = w3 . relu(W2 relu(W1 f)) (no biases, 4n -> 64 -> 64 -> 1); correction
  * delta_i = rho_i * out_i / l_ii. Row-major weights: W1 [64][4n], W2 [64][64], w3 [64].
+ * Training objective (composed in the Python wrapper from or_mlp_vjp and library SpMVs): the
+ * relative residual left by the correction, J = |r - L delta|^2 / |r|^2.
  * =========================================================================================== */
 int or_mlp_features(int64_t N, int n, const int32_t* idx, const double* xyz, const double* nrm, const double* w,
                     const double* r, double* feat, double* rho) {
@@ -1034,15 +1036,14 @@ int or_mlp_forward(int64_t N, int din, const double* W1, const double* W2, const
     return OR_OK;
 }
 
-/* backward of loss = mean_i (out_i - t_i)^2 over N points: gradients summed into gW1, gW2, gw3
- * (overwritten); returns the loss through *loss */
-int or_mlp_backward(int64_t N, int din, const double* W1, const double* W2, const double* w3, const double* feat,
-                    const double* target, double* gW1, double* gW2, double* gw3, double* loss) {
-    double h1[64], h2[64], z1[64], z2[64], d2[64], d1[64];
+/* vector-Jacobian product: gradients of sum_i gout_i * out_i with respect to W1, W2, w3
+ * (overwritten). Any loss built on the outputs reduces to this with gout = d loss / d out. */
+int or_mlp_vjp(int64_t N, int din, const double* W1, const double* W2, const double* w3, const double* feat,
+               const double* gout, double* gW1, double* gW2, double* gw3) {
+    double h1[64], z1[64], z2[64], d2[64], d1[64];
     for (int k = 0; k < 64 * din; ++k) gW1[k] = 0.0;
     for (int k = 0; k < 64 * 64; ++k) gW2[k] = 0.0;
     for (int k = 0; k < 64; ++k) gw3[k] = 0.0;
-    double L = 0.0;
     for (int64_t i = 0; i < N; ++i) {
         const double* f = feat + i * din;
         for (int a = 0; a < 64; ++a) {
@@ -1053,14 +1054,14 @@ int or_mlp_backward(int64_t N, int din, const double* W1, const double* W2, cons
         for (int a = 0; a < 64; ++a) {
             double acc = 0.0;
             for (int k = 0; k < 64; ++k) acc = acc + W2[a * 64 + k] * h1[k];
-            z2[a] = acc; h2[a] = acc > 0.0 ? acc : 0.0;
+            z2[a] = acc;
         }
-        double o = 0.0;
-        for (int k = 0; k < 64; ++k) o = o + w3[k] * h2[k];
-        double e = o - target[i];
-        L = L + e * e;
-        double g = 2.0 * e / (double)N;             /* d loss / d out_i */
-        for (int k = 0; k < 64; ++k) { gw3[k] = gw3[k] + g * h2[k]; d2[k] = (z2[k] > 0.0) ? g * w3[k] : 0.0; }
+        const double g = gout[i];
+        /* out = w3 . relu(z2): d out / d w3 = relu(z2); d out / d z2 = w3 where z2 > 0 */
+        for (int k = 0; k < 64; ++k) {
+            gw3[k] = gw3[k] + g * (z2[k] > 0.0 ? z2[k] : 0.0);
+            d2[k] = (z2[k] > 0.0) ? g * w3[k] : 0.0;
+        }
         for (int a = 0; a < 64; ++a) for (int k = 0; k < 64; ++k) gW2[a * 64 + k] = gW2[a * 64 + k] + d2[a] * h1[k];
         for (int k = 0; k < 64; ++k) {
             double acc = 0.0;
@@ -1069,6 +1070,5 @@ int or_mlp_backward(int64_t N, int din, const double* W1, const double* W2, cons
         }
         for (int a = 0; a < 64; ++a) for (int k = 0; k < din; ++k) gW1[a * din + k] = gW1[a * din + k] + d1[a] * f[k];
     }
-    *loss = L / (double)N;
     return OR_OK;
 }

@@ -64,3 +64,52 @@ def test_features_invariances(oracle):
     # residual features are the stencil residuals over their RMS
     i = 123
     np.testing.assert_allclose(f[i, 3::4], r[idx[i]] / np.sqrt(np.mean(r[idx[i]] ** 2)), rtol=1e-14)
+
+
+def _jacobi_weights(n):
+    """Weights whose network output is the centre residual feature r_i / rho_i:
+    out = relu(f_3) - relu(-f_3)."""
+    din = 4 * n
+    W1 = np.zeros((64, din)); W1[0, 3] = 1.0; W1[1, 3] = -1.0
+    W2 = np.zeros((64, 64)); W2[0, 0] = 1.0; W2[1, 1] = 1.0
+    w3 = np.zeros(64); w3[0] = 1.0; w3[1] = -1.0
+    return W1, W2, w3
+
+
+def test_correction_reduces_to_jacobi(oracle):
+    # out_i = r_i / rho_i makes the correction rho_i * out_i / l_ii a Jacobi step D^-1 r
+    x, nrm = I.fibonacci_sphere(1500, jitter=0.2, seed=9)
+    n = 20
+    idx, w, L = oracle.build_operator(x, nrm, n, "rbf", 1, 2, 1.0)
+    r = np.random.default_rng(6).standard_normal(1500)
+    W1, W2, w3 = _jacobi_weights(n)
+    d = oracle.learned_correction(L, idx, x, nrm, w, r, W1, W2, w3)
+    np.testing.assert_allclose(d, r / L.diagonal(), rtol=1e-13, atol=0)
+    J, *_ = oracle.learned_loss(L, idx, x, nrm, w, r, W1, W2, w3)
+    s = r - L @ (r / L.diagonal())
+    assert abs(J - (s @ s) / (r @ r)) <= 1e-12 * J
+    # zero weights: no correction, J = 1
+    J0, *_ = oracle.learned_loss(L, idx, x, nrm, w, r, 0 * W1, 0 * W2, 0 * w3)
+    assert J0 == 1.0
+
+
+def test_residual_loss_gradient_matches_finite_differences(oracle):
+    x, nrm = I.fibonacci_sphere(800, jitter=0.2, seed=10)
+    n = 12
+    idx, w, L = oracle.build_operator(x, nrm, n, "rbf", 1, 2, 1.0)
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal(800)
+    W1, W2, w3 = _weights(4 * n, 12)
+    J, g1, g2, g3 = oracle.learned_loss(L, idx, x, nrm, w, r, W1, W2, w3)
+    eps = 1e-6
+    for (W, G) in ((W1, g1), (W2, g2), (w3, g3)):
+        flat = W.reshape(-1)
+        for k in rng.choice(flat.size, 10, replace=False):
+            old = flat[k]
+            flat[k] = old + eps
+            jp = oracle.learned_loss(L, idx, x, nrm, w, r, W1, W2, w3)[0]
+            flat[k] = old - eps
+            jm = oracle.learned_loss(L, idx, x, nrm, w, r, W1, W2, w3)[0]
+            flat[k] = old
+            fd = (jp - jm) / (2 * eps)
+            assert abs(fd - G.reshape(-1)[k]) <= 1e-6 * max(1e-3, abs(fd)), (k, fd, G.reshape(-1)[k])
