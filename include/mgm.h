@@ -71,10 +71,13 @@ typedef struct {
     int nu1, nu2;    /* pre- and post-smoothing sweeps, 0 <= nu <= 8 */
     int precision;   /* MGM_F32 (V-cycle in FP32, coarsest solve FP64) or MGM_F64 */
     uint64_t seed;   /* seed of the multicolour-ordering priorities */
-    int persistent_sweeps; /* 0 (default): one kernel launch per colour of each Gauss-Seidel sweep;
-                              nonzero: each sweep is one persistent cooperative launch with a bounded
-                              grid barrier between colours. Both give bit-identical results; on
-                              GB300 the per-colour launches (captured in a CUDA graph) are faster. */
+    int persistent_sweeps; /* How a multicolour Gauss-Seidel sweep is launched; all three give
+                              bit-identical results. 0: one kernel launch per colour (captured in
+                              a CUDA graph). 1: one persistent cooperative launch with a bounded grid
+                              barrier between colours. 2: one persistent cooperative launch in which
+                              each group of rows starts as soon as the rows it reads from earlier
+                              colours carry their ready flags (bounded waits). Other values:
+                              MGM_ERR_INVALID_ARG. */
 } mgm_params;
 
 typedef struct {
@@ -287,6 +290,68 @@ int64_t mgm_kernel_launches(void);
 mgm_status mgm_check_bounded_wait(int nblocks, int64_t spin_limit, int* status_out, mgm_stream stream);
 
 void mgm_destroy(mgm_hierarchy* H);
+
+/* ------------------------------------------------------------------------------------------- */
+/* Learned correction after the V-cycle (an addition to the paper's method; the plain cycle of  */
+/* Alg. 3 is unchanged when it is off and is its fallback)                                     */
+/* ------------------------------------------------------------------------------------------- */
+/* For level 0, stencil idx_i (centre first), tangent-plane offsets (xh, yh) and support s_i of
+ * Sec. 2.1, LBO weights c_ij and the residual r = b - L e after the cycle's last post-smoothing:
+ *   features f_i[4j..4j+3] = (xh_j / s_i, yh_j / s_i, c_ij s_i^2, r_{idx_ij} / rho_i),  j < n,
+ *   rho_i = sqrt(mean_j r_{idx_ij}^2) (residual features 0 when rho_i = 0),
+ *   out_i = w3 . relu(W2 relu(W1 f_i))   (4n -> 64 -> 64 -> 1, no biases),
+ *   e_i  += rho_i out_i / l_ii.
+ * Weights are one FP32 array, row-major: W1 (64 x 4n), then W2 (64 x 64), then w3 (64);
+ * mgm_mlp_size(n) floats. Training minimises J = |r - L delta|^2 / |r|^2 (the relative residual
+ * left by the correction) with Adam (beta 0.9 / 0.999, eps 1e-8) on the FP32 master weights; the
+ * V-cycle uses a BF16 copy of the weights with FP32 accumulation. */
+typedef struct mgm_mlp mgm_mlp; /* opaque network (device weights + Adam state) */
+
+/* Floats in the weight array for stencil size n (1 <= n <= 48), or -1 for another n. */
+int64_t mgm_mlp_size(int n);
+/* New network for stencil size n, weights uniform in +-1/sqrt(fan_in) from a SplitMix64 stream
+ * seeded with `seed` (W1, W2, w3 in order). *out owns device memory until mgm_mlp_destroy. */
+mgm_status mgm_mlp_create(int n, uint64_t seed, mgm_mlp** out);
+void mgm_mlp_destroy(mgm_mlp* M);
+/* Copy the FP32 weights to / from host memory (mgm_mlp_size(n) floats); set resets Adam. */
+mgm_status mgm_mlp_get(const mgm_mlp* M, float* W_host);
+mgm_status mgm_mlp_set(mgm_mlp* M, const float* W_host);
+/* FP32 forward pass of B rows of features (device, B x 4n row-major) into out (device, B). */
+mgm_status mgm_mlp_forward(const mgm_mlp* M, const float* feat, int64_t B, float* out, mgm_stream stream);
+/* Gradients of sum_b gout_b out_b with respect to the weights (device, mgm_mlp_size(n) floats, the
+ * weight layout), for device features (B x 4n) and gout (B). Deterministic (fixed row chunks). */
+mgm_status mgm_mlp_vjp(const mgm_mlp* M, const float* feat, const float* gout, int64_t B, float* grad,
+                       mgm_stream stream);
+
+/* Attach the stencils of level 0 to an FP32 hierarchy with p >= 2: xyz, nrm (N x 3 FP64), idx
+ * (N x n int32, centre first) and w (N x n FP64 LBO weights), all device arrays in caller order,
+ * as given to mgm_assemble (1 <= n <= 48). Copies what it needs. The correction stays off until
+ * mgm_learned_enable. MGM_ERR_INVALID_ARG for an FP64 hierarchy, p = 1 or indices out of range. */
+mgm_status mgm_learned_attach(mgm_hierarchy* H, const double* xyz, const double* nrm, const int32_t* idx,
+                              const double* w, int n, mgm_stream stream);
+/* Features (device N x 4n FP32, rows in caller order) and rho (device N, may be NULL) for the
+ * residual r (device N FP64, caller order). */
+mgm_status mgm_learned_features(mgm_hierarchy* H, const double* r, float* feat, float* rho, mgm_stream stream);
+/* Training sample: r_out = r - L M r with M the plain V-cycle (device N FP64, caller order). */
+mgm_status mgm_learned_cycle_residual(mgm_hierarchy* H, const double* r, double* r_out, mgm_stream stream);
+/* J for the sample r (device N FP64, caller order) into *loss (host) and, if grad is not NULL,
+ * dJ/dW (device, mgm_mlp_size(n) floats). */
+mgm_status mgm_learned_loss(mgm_hierarchy* H, const mgm_mlp* M, const double* r, double* loss, float* grad,
+                            mgm_stream stream);
+/* One Adam step of size lr on the sample r; *loss (host, may be NULL) = J before the step. */
+mgm_status mgm_learned_train_step(mgm_hierarchy* H, mgm_mlp* M, const double* r, float lr, double* loss,
+                                  mgm_stream stream);
+/* Use M's current weights (copied, BF16) in this hierarchy's V-cycle after the level-0
+ * post-smoothing, for mgm_vcycle and mgm_solve; M = NULL switches the correction off. The
+ * nonlinear preconditioner needs the flexible outer iteration: mgm_solve switches the correction
+ * off for the rest of a solve when an iteration reduces the residual estimate by less than 1%
+ * (FGMRES) or not at all (MGM_KRYLOV_NONE). mgm_solve_multi / _batched do not use it. */
+mgm_status mgm_learned_enable(mgm_hierarchy* H, const mgm_mlp* M, mgm_stream stream);
+/* delta (device N FP64, caller order) = the enabled correction for residual r (device N FP64),
+ * through the V-cycle's inference kernel. */
+mgm_status mgm_learned_correction(mgm_hierarchy* H, const double* r, double* delta, mgm_stream stream);
+/* Whether a correction is enabled, and how many solves fell back to the plain cycle. */
+mgm_status mgm_learned_info(const mgm_hierarchy* H, int* enabled, int64_t* fallbacks);
 
 /* ------------------------------------------------------------------------------------------- */
 /* Errors                                                                                       */

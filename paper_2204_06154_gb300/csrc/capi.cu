@@ -26,6 +26,22 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
 void vcycle_api(mgm_hierarchy* H, const void* r, void* z, int dtype, cudaStream_t s);
 void hierarchy_level(const mgm_hierarchy* H, int j, int32_t* perm, int32_t* keep, double* xyz, int32_t* lrp, int32_t* lci,
                      double* lv, int32_t* prp, int32_t* pci, double* pv, int32_t* colour, cudaStream_t s);
+// learned.cu
+void learned_attach(mgm_hierarchy* H, const double* xyz, const double* nrm, const int32_t* idx, const double* w, int n,
+                    cudaStream_t s);
+void learned_features(mgm_hierarchy* H, const double* r, float* feat, float* rho, cudaStream_t s);
+void learned_cycle_residual(mgm_hierarchy* H, const double* r, double* rout, cudaStream_t s);
+double learned_loss(mgm_hierarchy* H, const mgm_mlp* M, const double* r, float* grad, cudaStream_t s);
+double learned_train_step(mgm_hierarchy* H, mgm_mlp* M, const double* r, float lr, cudaStream_t s);
+void learned_enable(mgm_hierarchy* H, const mgm_mlp* M, cudaStream_t s);
+void learned_correction(mgm_hierarchy* H, const double* r, double* delta, cudaStream_t s);
+mgm_mlp* mlp_create(int n, uint64_t seed);
+void mlp_destroy(mgm_mlp* M);
+void mlp_get(const mgm_mlp* M, float* W);
+void mlp_set(mgm_mlp* M, const float* W);
+int64_t mlp_size(int n);
+void mlp_forward_api(const mgm_mlp* M, const float* feat, int64_t B, float* out, cudaStream_t s);
+void mlp_vjp_api(const mgm_mlp* M, const float* feat, const float* gout, int64_t B, float* grad, cudaStream_t s);
 }  // namespace mgm
 
 using namespace mgm;
@@ -246,3 +262,78 @@ const char* mgm_last_error_message(void) { return error_message(); }
 int64_t mgm_last_error_row(void) { return bad_row(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// learned correction
+// ---------------------------------------------------------------------------------------------
+int64_t mgm_mlp_size(int n) { return mlp_size(n); }
+
+mgm_status mgm_mlp_create(int n, uint64_t seed, mgm_mlp** out) {
+    return guarded([&] {
+        REQUIRE(out, "null argument");
+        *out = nullptr;
+        *out = mlp_create(n, seed);
+    });
+}
+
+void mgm_mlp_destroy(mgm_mlp* M) {
+    if (!M) return;
+    cudaDeviceSynchronize();
+    mlp_destroy(M);
+}
+
+mgm_status mgm_mlp_get(const mgm_mlp* M, float* W_host) { return guarded([&] { mlp_get(M, W_host); }); }
+mgm_status mgm_mlp_set(mgm_mlp* M, const float* W_host) { return guarded([&] { mlp_set(M, W_host); }); }
+
+mgm_status mgm_mlp_forward(const mgm_mlp* M, const float* feat, int64_t B, float* out, mgm_stream stream) {
+    return guarded([&] { mlp_forward_api(M, feat, B, out, S(stream)); });
+}
+
+mgm_status mgm_mlp_vjp(const mgm_mlp* M, const float* feat, const float* gout, int64_t B, float* grad, mgm_stream stream) {
+    return guarded([&] { mlp_vjp_api(M, feat, gout, B, grad, S(stream)); });
+}
+
+mgm_status mgm_learned_attach(mgm_hierarchy* H, const double* xyz, const double* nrm, const int32_t* idx, const double* w,
+                              int n, mgm_stream stream) {
+    return guarded([&] { learned_attach(H, xyz, nrm, idx, w, n, S(stream)); });
+}
+
+mgm_status mgm_learned_features(mgm_hierarchy* H, const double* r, float* feat, float* rho, mgm_stream stream) {
+    return guarded([&] { learned_features(H, r, feat, rho, S(stream)); });
+}
+
+mgm_status mgm_learned_cycle_residual(mgm_hierarchy* H, const double* r, double* r_out, mgm_stream stream) {
+    return guarded([&] { learned_cycle_residual(H, r, r_out, S(stream)); });
+}
+
+mgm_status mgm_learned_loss(mgm_hierarchy* H, const mgm_mlp* M, const double* r, double* loss, float* grad,
+                            mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(loss, "null argument");
+        *loss = learned_loss(H, M, r, grad, S(stream));
+    });
+}
+
+mgm_status mgm_learned_train_step(mgm_hierarchy* H, mgm_mlp* M, const double* r, float lr, double* loss,
+                                  mgm_stream stream) {
+    return guarded([&] {
+        double J = learned_train_step(H, M, r, lr, S(stream));
+        if (loss) *loss = J;
+    });
+}
+
+mgm_status mgm_learned_enable(mgm_hierarchy* H, const mgm_mlp* M, mgm_stream stream) {
+    return guarded([&] { learned_enable(H, M, S(stream)); });
+}
+
+mgm_status mgm_learned_correction(mgm_hierarchy* H, const double* r, double* delta, mgm_stream stream) {
+    return guarded([&] { learned_correction(H, r, delta, S(stream)); });
+}
+
+mgm_status mgm_learned_info(const mgm_hierarchy* H, int* enabled, int64_t* fallbacks) {
+    return guarded([&] {
+        REQUIRE(H, "null hierarchy");
+        if (enabled) *enabled = H->learned ? 1 : 0;
+        if (fallbacks) *fallbacks = H->learned_fallbacks;
+    });
+}

@@ -33,6 +33,11 @@ struct Level {
     std::vector<int32_t> cptr; // host: colour c = solve rows [cptr[c], cptr[c+1])
     Buf<int32_t> cptr_dev;     // the same on the device (persistent sweeps)
     Buf<unsigned> bar;         // grid-barrier counter of this level's persistent sweeps
+    Buf<int32_t> gptr;         // dependency-driven sweeps: row groups (<= 4 rows of one colour)
+    int32_t ngroups = 0;
+    Buf<int> flag;             // per-row ready flags of the current sweep
+    Buf<float> eold32;         // e before a full sweep (read for the upper-part columns)
+    Buf<double> eold64;
     Buf<int32_t> lo, mid;      // row s: lower part [lo[s], mid[s]), upper part [mid[s], lo[s+1])
     Buf<int32_t> sc;           // padded columns (solve order of this level)
     Buf<float> sv32, diag32, dinv32;
@@ -66,7 +71,8 @@ struct mgm_hierarchy {
     mgm::Buf<int32_t> ord_caller;  // level-0 solve index -> caller index
     // persistent multicolour sweeps (one cooperative launch per sweep) instead of one launch
     // per colour; error word of their bounded waits
-    bool persistent = false;
+    int sweep_mode = 0;         // 0: a launch per colour, 1: grid barriers, 2: per-row ready flags
+    bool persistent = false;    // sweep_mode != 0
     mgm::Buf<int> err;
     // V-cycle graph (captured lazily)
     cudaGraphExec_t vgraph = nullptr;
@@ -80,6 +86,19 @@ struct mgm_hierarchy {
     mgm::Buf<double> ydev;
     double* hhost = nullptr;    // pinned
     void* multi = nullptr;      // workspace of the many-right-hand-side solve (multi.cu)
+    // learned correction after the V-cycle (learned.cu); level-0 solve order throughout
+    int ln = 0;                          // stencil size of the attached features (0: not attached)
+    mgm::Buf<int32_t> lnbr;              // N x n stencil members, centre first
+    mgm::Buf<float> lgeo;                // N x n x 3: xh/s, yh/s, c s^2
+    mgm::Buf<float> lhg;                 // N x 64: first layer applied to the geometric features
+    mgm::Buf<uint16_t> lw;               // BF16 [n x 64 residual columns of W1 | W2 | w3]
+    mgm::Buf<int32_t> lrp, lci, ltrp, ltci;  // L_0 and L_0^T as plain CSR (training)
+    mgm::Buf<float> lval, ltval;
+    bool learned = false;                // correction enabled
+    bool learned_active = true;          // cleared by a solve that falls back to the plain cycle
+    int64_t learned_fallbacks = 0;
+    cudaGraphExec_t lgraph = nullptr;    // V-cycle + correction
+    int64_t lgraph_kernels = 0;
     int64_t device_bytes = 0;
     ~mgm_hierarchy();
 };
@@ -87,6 +106,7 @@ struct mgm_hierarchy {
 namespace mgm {
 // vcycle.cu
 void vcycle_core(mgm_hierarchy* H, cudaStream_t s);          // b_0 -> e_0 (graph if captured)
+void vcycle_plain(mgm_hierarchy* H, cudaStream_t s);         // the same without the learned correction
 void vcycle_prepare(mgm_hierarchy* H);                       // capture the graph
 void load_input(mgm_hierarchy* H, const void* src, int src_dtype, const int32_t* gather, cudaStream_t s);
 void store_output(mgm_hierarchy* H, void* dst, int dst_dtype, const int32_t* scatter, cudaStream_t s);
@@ -98,6 +118,8 @@ void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStrea
 void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
 void solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp, mgm_solve_info* info,
            cudaStream_t s);
+// learned.cu
+void learned_correct(mgm_hierarchy* H, cudaStream_t s);     // e_0 += correction from s_0 = b_0 - L_0 e_0
 // multi.cu
 void solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* U, const mgm_solve_params* sp, mgm_solve_info* info,
                  cudaStream_t s);

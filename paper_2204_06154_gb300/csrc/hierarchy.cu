@@ -399,6 +399,8 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     H->nu2 = prm->nu2;
     H->m = prm->m;
     H->seed = prm->seed;
+    REQUIRE(prm->persistent_sweeps >= 0 && prm->persistent_sweeps <= 2, "persistent_sweeps must be 0, 1 or 2");
+    H->sweep_mode = prm->persistent_sweeps;
     H->persistent = prm->persistent_sweeps != 0;
     H->N = N;
     int p = num_levels(N, prm->n_min);
@@ -538,6 +540,7 @@ void hierarchy_level(const mgm_hierarchy* H, int j, int32_t* perm, int32_t* keep
 mgm_hierarchy::~mgm_hierarchy() {
     mgm::free_multi(this);
     if (vgraph) cudaGraphExecDestroy(vgraph);
+    if (lgraph) cudaGraphExecDestroy(lgraph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (hhost) cudaFreeHost(hhost);
 }

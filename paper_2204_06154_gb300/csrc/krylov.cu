@@ -224,10 +224,20 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
     double rel = 0.0;
     mgm_status status = MGM_ERR_NOT_CONVERGED;
     const bool f32 = H->precision == MGM_F32;
+    // a learned correction that stops reducing the residual is switched off for the rest of the
+    // solve (the flexible outer iteration tolerates the change of preconditioner)
+    H->learned_active = true;
+    auto fallback_if = [&](bool stalled) {
+        if (H->learned && H->learned_active && stalled) {
+            H->learned_active = false;
+            ++H->learned_fallbacks;
+        }
+    };
     if (sp->krylov == MGM_KRYLOV_NONE) {
         for (;;) {
             op.spmv<true, double>(H->u.get(), H->f.get(), H->r.get());
             rel = op.norm(H->r.get()) / fn;
+            if (!hist.empty()) fallback_if(!(rel < hist.back()));
             hist.push_back(rel);
             if (!std::isfinite(rel)) { status = MGM_ERR_BREAKDOWN; break; }
             if (rel <= sp->tol) { status = MGM_OK; break; }
@@ -303,6 +313,7 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
                 g[k] = cs[k] * g[k];
                 ++it;
                 double est = std::fabs(g[k1]) / fn;
+                fallback_if(!(est < 0.99 * hist.back()));
                 hist.push_back(est);
                 if (est <= sp->tol || hn == 0.0) { ++k; break; }
             }

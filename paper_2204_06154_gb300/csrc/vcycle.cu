@@ -184,6 +184,109 @@ __global__ void __launch_bounds__(PS_THREADS) psweep_k(const int32_t* __restrict
     }
 }
 
+// ------------------------------ dependency-driven multicolour sweep ---------------------------
+// One launch per sweep. Rows are taken in groups of at most four consecutive rows of one colour,
+// one warp per group (G lanes per row), the groups dealt round-robin to the resident warps; each
+// warp takes its groups in increasing order, so the lowest unfinished group always finds its
+// inputs ready and the sweep cannot deadlock. A group starts once every lower-part column of its
+// rows carries its ready flag, which a row sets (release) right after storing its new value;
+// upper-part columns are read from eold, a copy of e taken before the sweep. Every row therefore
+// reads exactly the values it reads under per-colour launches, in the same order: the result is
+// bit-identical. Waits are bounded: past the spin limit the warp records MGM_ERR_TIMEOUT in the
+// error word and every warp leaves at its next wait.
+constexpr int DS_THREADS = 256;
+constexpr int DS_WARPS = DS_THREADS / 32;
+
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_i32(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <class T>
+struct Quad;
+template <>
+struct Quad<float> {
+    float x, y, z, w;
+    __device__ __forceinline__ static Quad load(const float* p) {
+        float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        return {v.x, v.y, v.z, v.w};
+    }
+};
+template <>
+struct Quad<double> {
+    double x, y, z, w;
+    __device__ __forceinline__ static Quad load(const double* p) {
+        double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+        return {a.x, a.y, b.x, b.y};
+    }
+};
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+template <int MODE, class T>
+__global__ void __launch_bounds__(DS_THREADS) dsweep_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ mid,
+                                                       const int32_t* __restrict__ sc, const T* __restrict__ sv,
+                                                       const T* __restrict__ dinv, const T* __restrict__ b, T* e,
+                                                       const T* __restrict__ eold, const int32_t* __restrict__ gptr,
+                                                       int32_t ngroups, int* flag, int* err, unsigned long long limit) {
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int64_t W = (int64_t)gridDim.x * DS_WARPS;
+    for (int64_t g = (int64_t)blockIdx.x * DS_WARPS + (threadIdx.x >> 5); g < ngroups; g += W) {
+        const int32_t row = gptr[g] + lane / G;
+        const bool act = row < gptr[g + 1];
+        int32_t beg = 0, m = 0, end = 0;
+        if (act) {
+            beg = lo[row];
+            m = mid[row];
+            end = MODE == 0 ? m : lo[row + 1];
+        }
+        unsigned long long it = 0;
+        for (;;) {  // every lower-part column final? (padding entries point at the row itself)
+            bool ready = true;
+            for (int32_t p = beg + 4 * gl; p < m && ready; p += 4 * G) {
+                const int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
+                ready = (c.x == row || ld_acquire_i32(flag + c.x)) && (c.y == row || ld_acquire_i32(flag + c.y)) &&
+                        (c.z == row || ld_acquire_i32(flag + c.z)) && (c.w == row || ld_acquire_i32(flag + c.w));
+            }
+            if (__all_sync(0xffffffffu, ready)) break;
+            int quit = 0;
+            if (lane == 0) {
+                if (*(volatile int*)err) quit = 1;
+                else if (++it > limit) { atomicOr(err, MGM_ERR_TIMEOUT); quit = 1; }
+            }
+            if (__shfl_sync(0xffffffffu, quit, 0)) return;
+            __nanosleep(64);
+        }
+        T acc = T(0);
+        for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {  // the order of row_sum
+            const int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
+            const Quad<T> v = Quad<T>::load(sv + p);
+            if (p < m) {
+                acc = fma_t(v.x, __ldcg(e + c.x), acc);
+                acc = fma_t(v.y, __ldcg(e + c.y), acc);
+                acc = fma_t(v.z, __ldcg(e + c.z), acc);
+                acc = fma_t(v.w, __ldcg(e + c.w), acc);
+            } else {
+                acc = fma_t(v.x, __ldg(eold + c.x), acc);
+                acc = fma_t(v.y, __ldg(eold + c.y), acc);
+                acc = fma_t(v.z, __ldg(eold + c.z), acc);
+                acc = fma_t(v.w, __ldg(eold + c.w), acc);
+            }
+        }
+        acc = group_reduce(acc);
+        if (act && gl == 0) {
+            e[row] = (b[row] - acc) * dinv[row];
+            st_release_i32(flag + row, 1);
+        }
+    }
+}
+
 // a barrier that nobody completes: the wait must end at its limit with MGM_ERR_TIMEOUT
 __global__ void barrier_timeout_probe_k(unsigned* bar, int* err, unsigned long long limit) {
     __shared__ int ok;
@@ -251,6 +354,7 @@ template <> struct LV<float> {
     static const float* dinv(Level& L) { return L.dinv32.get(); }
     static const float* pv(Level& L) { return L.pv32.get(); }
     static const float* rv(Level& L) { return L.r_v32.get(); }
+    static float* eold(Level& L) { return L.eold32.get(); }
 };
 template <> struct LV<double> {
     static double* b(Level& L) { return L.b64.get(); }
@@ -261,6 +365,7 @@ template <> struct LV<double> {
     static const double* dinv(Level& L) { return L.dinv64.get(); }
     static const double* pv(Level& L) { return L.pv64.get(); }
     static const double* rv(Level& L) { return L.r_v64.get(); }
+    static double* eold(Level& L) { return L.eold64.get(); }
 };
 
 template <int MODE, class T>
@@ -308,6 +413,40 @@ static void launch_psweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
     CK_LAUNCH();
 }
 
+template <int MODE, class T>
+static void launch_dsweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
+    if (L.ngroups <= 0) return;
+    static int mb = 0;  // co-resident blocks, per instantiation (MODE, T)
+    if (!mb) {
+        int per_sm = 0, dev = 0, sms = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dsweep_k<MODE, T>, DS_THREADS, 0));
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        mb = std::max(1, per_sm * sms);
+    }
+    const int nblocks = std::max(1, std::min(mb, (L.ngroups + DS_WARPS - 1) / DS_WARPS));
+    CK(cudaMemsetAsync(L.flag.get(), 0, sizeof(int) * L.n, s));
+    T* e = LV<T>::e(L);
+    T* eold = LV<T>::eold(L);
+    if (MODE == 1) CK(cudaMemcpyAsync(eold, e, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
+    const int32_t* lo = L.lo.get();
+    const int32_t* mid = L.mid.get();
+    const int32_t* sc = L.sc.get();
+    const T* sv = LV<T>::sv(L);
+    const T* dv = LV<T>::dinv(L);
+    const T* b = LV<T>::b(L);
+    const T* eo = eold;
+    const int32_t* gp = L.gptr.get();
+    int32_t ng = L.ngroups;
+    int* flag = L.flag.get();
+    int* err = H->err.get();
+    unsigned long long limit = PS_SPIN_LIMIT;
+    void* args[] = {(void*)&lo, (void*)&mid, (void*)&sc, (void*)&sv, (void*)&dv, (void*)&b, (void*)&e, (void*)&eo,
+                    (void*)&gp, (void*)&ng, (void*)&flag, (void*)&err, (void*)&limit};
+    CK(cudaLaunchCooperativeKernel((const void*)dsweep_k<MODE, T>, dim3(nblocks), dim3(DS_THREADS), args, 0, s));
+    CK_LAUNCH();
+}
+
 template <class T>
 static void sweep(Level& L, bool from_zero, cudaStream_t s) {
     for (size_t c = 0; c + 1 < L.cptr.size(); ++c) {
@@ -319,7 +458,10 @@ static void sweep(Level& L, bool from_zero, cudaStream_t s) {
 // Alg. 3 with a zero initial guess on level 1: b_0 -> e_0
 template <class T>
 static void sweep_any(mgm_hierarchy* H, Level& L, bool from_zero, cudaStream_t s) {
-    if (H->persistent) {
+    if (H->sweep_mode == 2) {
+        if (from_zero) launch_dsweep<0, T>(H, L, s);
+        else launch_dsweep<1, T>(H, L, s);
+    } else if (H->sweep_mode == 1) {
         if (from_zero) launch_psweep<0, T>(H, L, s);
         else launch_psweep<1, T>(H, L, s);
     } else {
@@ -372,6 +514,18 @@ void alloc_work(mgm_hierarchy* H) {
             L.cptr_dev.alloc(L.cptr.size());
             CK(cudaMemcpy(L.cptr_dev.get(), L.cptr.data(), sizeof(int32_t) * L.cptr.size(), cudaMemcpyHostToDevice));
         }
+        if (smooth && H->sweep_mode == 2) {  // groups of <= 4 rows that never straddle a colour
+            std::vector<int32_t> gp;
+            for (size_t c = 0; c + 1 < L.cptr.size(); ++c)
+                for (int32_t r = L.cptr[c]; r < L.cptr[c + 1]; r += 4) gp.push_back(r);
+            gp.push_back((int32_t)L.n);
+            L.ngroups = (int32_t)gp.size() - 1;
+            L.gptr.alloc(gp.size());
+            CK(cudaMemcpy(L.gptr.get(), gp.data(), sizeof(int32_t) * gp.size(), cudaMemcpyHostToDevice));
+            L.flag.alloc(L.n);
+            if (H->precision == MGM_F32) L.eold32.alloc(L.n);
+            else L.eold64.alloc(L.n);
+        }
         if (H->precision == MGM_F32) {
             L.b32.alloc(L.n); L.e32.alloc(L.n);
             CK(cudaMemset(L.e32.get(), 0, sizeof(float) * L.n));
@@ -386,32 +540,57 @@ void alloc_work(mgm_hierarchy* H) {
     }
 }
 
-void vcycle_prepare(mgm_hierarchy* H) {
-    if (H->vgraph) return;
-    if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+static cudaGraphExec_t capture(mgm_hierarchy* H, bool learned, int64_t* kernels) {
     cudaGraph_t g = nullptr;
     const int64_t before = launches();
     CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
     try {
-        if (H->precision == MGM_F32) vcycle_launches<float>(H, H->cap_stream);
-        else vcycle_launches<double>(H, H->cap_stream);
+        if (H->precision == MGM_F32) {
+            vcycle_launches<float>(H, H->cap_stream);
+            if (learned) {  // s_0 = b_0 - L_0 e_0, then the learned correction of e_0
+                Level& L0 = H->lv[0];
+                launch_rows<3, float>(L0, 0, (int32_t)L0.n, H->cap_stream);
+                learned_correct(H, H->cap_stream);
+            }
+        } else {
+            vcycle_launches<double>(H, H->cap_stream);
+        }
     } catch (...) {
         cudaStreamEndCapture(H->cap_stream, &g);
         if (g) cudaGraphDestroy(g);
         throw;
     }
     CK(cudaStreamEndCapture(H->cap_stream, &g));
-    H->graph_kernels = launches() - before;  // captured, not executed: counted per graph launch
-    note_launch(-H->graph_kernels);
-    cudaError_t e = cudaGraphInstantiate(&H->vgraph, g, 0);
+    *kernels = launches() - before;  // captured, not executed: counted per graph launch
+    note_launch(-*kernels);
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     CK(e);
+    return ex;
+}
+
+void vcycle_prepare(mgm_hierarchy* H) {
+    if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+    if (!H->vgraph) H->vgraph = capture(H, false, &H->graph_kernels);
+    if (H->learned && !H->lgraph) H->lgraph = capture(H, true, &H->lgraph_kernels);
+}
+
+void vcycle_plain(mgm_hierarchy* H, cudaStream_t s) {
+    vcycle_prepare(H);
+    CK(cudaGraphLaunch(H->vgraph, s));
+    note_launch(H->graph_kernels);
 }
 
 void vcycle_core(mgm_hierarchy* H, cudaStream_t s) {
     vcycle_prepare(H);
-    CK(cudaGraphLaunch(H->vgraph, s));
-    note_launch(H->graph_kernels);
+    if (H->learned && H->learned_active) {
+        CK(cudaGraphLaunch(H->lgraph, s));
+        note_launch(H->lgraph_kernels);
+    } else {
+        CK(cudaGraphLaunch(H->vgraph, s));
+        note_launch(H->graph_kernels);
+    }
 }
 
 void load_input(mgm_hierarchy* H, const void* src, int dt, const int32_t* gather, cudaStream_t s) {
@@ -509,7 +688,7 @@ void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStrea
         CK(cudaEventElapsedTime(&ms, e0, e1));
         out->sweep_ms = ms / reps;
         out->sweep_bytes = (L.nlow + L.nupp) * (vs + 4) + L.n * (4 + 3 * vs);
-        out->sweep_launches = H->persistent ? 1 : (int32_t)(L.cptr.size() - 1);
+        out->sweep_launches = H->persistent ? 1 : (int32_t)(L.cptr.size() - 1);  // kernels (copies not counted)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -543,6 +722,7 @@ void vcycle_api(mgm_hierarchy* H, const void* r, void* z, int dtype, cudaStream_
     REQUIRE(H && r && z, "null argument");
     REQUIRE(dtype == MGM_F32 || dtype == MGM_F64, "dtype must be MGM_F32 or MGM_F64");
     load_input(H, r, dtype, H->ord_caller.get(), s);
+    H->learned_active = true;
     vcycle_core(H, s);
     store_output(H, z, dtype, H->ord_caller.get(), s);
     if (H->persistent) check_device_error(H, s);

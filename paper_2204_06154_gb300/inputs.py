@@ -310,5 +310,52 @@ def bumpy_sphere(N: int, seed: int = 3, amp: float = 0.2, jitter: float = 0.1):
     return np.ascontiguousarray(p), np.ascontiguousarray(n)
 
 
+def bumpy_torus(N: int, seed: int = 5, amp: float = 0.2, R: float = 1.0, r: float = 1.0 / 3.0, jitter: float = 0.1):
+    """Torus whose tube radius varies: X(u, v) = ((R + rho cos v) cos u, (R + rho cos v) sin u,
+    rho sin v) with rho(u, v) = r (1 + amp g(u, v) / max|g|), g = sum of 5 seeded modes
+    c cos(a u + b v + phase) (a in 1..6, b in 1..4, c ~ N(0, 1)). The (u, v) samples are those of
+    torus_grid (jittered parametric grid). Normals: cross product of centred finite differences
+    of X in u and v (step 1e-6), oriented away from the tube's centre line."""
+    rng = np.random.default_rng(seed)
+    modes = [(int(rng.integers(1, 7)), int(rng.integers(1, 5)), float(rng.uniform(0, 2 * np.pi)),
+              float(rng.standard_normal())) for _ in range(5)]
+
+    def g(u, v):
+        out = np.zeros(np.broadcast(u, v).shape)
+        for (a, b, ph, c) in modes:
+            out = out + c * np.cos(a * u + b * v + ph)
+        return out
+
+    pu = np.linspace(0, 2 * np.pi, 400, endpoint=False)
+    PU, PV = np.meshgrid(pu, pu, indexing="ij")
+    scale = amp / np.max(np.abs(g(PU, PV)))
+    nu, nv = _torus_shape(N, R, r)
+    u = 2.0 * np.pi * (np.arange(nu, dtype=np.float64) + 0.5) / nu
+    v = 2.0 * np.pi * (np.arange(nv, dtype=np.float64) + 0.5) / nv
+    U, V = np.meshgrid(u, v, indexing="ij")
+    U = U.reshape(-1).copy()
+    V = V.reshape(-1).copy()
+    if jitter > 0.0:
+        h = math.sqrt(4.0 * np.pi ** 2 * R * r / U.size)
+        d = np.random.default_rng(seed + 1).uniform(-jitter * h, jitter * h, size=(U.size, 2))
+        U = U + d[:, 0] / (R + r * np.cos(V))
+        V = V + d[:, 1] / r
+
+    def X(u, v):
+        rho = r * (1.0 + scale * g(u, v))
+        return np.stack([(R + rho * np.cos(v)) * np.cos(u), (R + rho * np.cos(v)) * np.sin(u), rho * np.sin(v)], axis=1)
+
+    p = X(U, V)
+    eps = 1e-6
+    tu = (X(U + eps, V) - X(U - eps, V)) / (2 * eps)
+    tv = (X(U, V + eps) - X(U, V - eps)) / (2 * eps)
+    n = np.cross(tu, tv)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    centre = np.stack([R * np.cos(U), R * np.sin(U), np.zeros_like(U)], axis=1)
+    flip = np.sum(n * (p - centre), axis=1) < 0
+    n[flip] *= -1.0
+    return np.ascontiguousarray(p), np.ascontiguousarray(n)
+
+
 def mean_spacing(x: np.ndarray, area: float) -> float:
     return math.sqrt(area / x.shape[0])

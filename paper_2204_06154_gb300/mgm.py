@@ -59,7 +59,10 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_solve_batched",
            "mgm_hierarchy_stats_get", "mgm_hierarchy_level", "mgm_hierarchy_pnnz", "mgm_profile",
            "mgm_kernel_launches", "mgm_check_bounded_wait", "mgm_destroy", "mgm_status_string", "mgm_last_error_message",
-           "mgm_last_error_row"]
+           "mgm_last_error_row",
+           "mgm_mlp_size", "mgm_mlp_create", "mgm_mlp_destroy", "mgm_mlp_get", "mgm_mlp_set", "mgm_mlp_forward",
+           "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
+           "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info"]
 
 
 class ProfileInfo(C.Structure):
@@ -101,12 +104,29 @@ def lib():
         L.mgm_kernel_launches.restype = C.c_int64
         L.mgm_destroy.argtypes = [P]
         L.mgm_destroy.restype = None
+        L.mgm_mlp_size.argtypes = [I]
+        L.mgm_mlp_size.restype = C.c_int64
+        L.mgm_mlp_create.argtypes = [I, C.c_uint64, C.POINTER(P)]
+        L.mgm_mlp_destroy.argtypes = [P]
+        L.mgm_mlp_destroy.restype = None
+        L.mgm_mlp_get.argtypes = [P, P]
+        L.mgm_mlp_set.argtypes = [P, P]
+        L.mgm_mlp_forward.argtypes = [P, P, I64, P, P]
+        L.mgm_mlp_vjp.argtypes = [P, P, P, I64, P, P]
+        L.mgm_learned_attach.argtypes = [P, P, P, P, P, I, P]
+        L.mgm_learned_features.argtypes = [P, P, P, P, P]
+        L.mgm_learned_cycle_residual.argtypes = [P, P, P, P]
+        L.mgm_learned_loss.argtypes = [P, P, P, C.POINTER(C.c_double), P, P]
+        L.mgm_learned_train_step.argtypes = [P, P, P, C.c_float, C.POINTER(C.c_double), P]
+        L.mgm_learned_enable.argtypes = [P, P, P]
+        L.mgm_learned_correction.argtypes = [P, P, P, P]
+        L.mgm_learned_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
         L.mgm_status_string.restype = C.c_char_p
         L.mgm_last_error_message.restype = C.c_char_p
         L.mgm_last_error_row.restype = C.c_int64
         for name in EXPORTS:
             if name not in ("mgm_destroy", "mgm_status_string", "mgm_last_error_message", "mgm_last_error_row",
-                            "mgm_kernel_launches"):
+                            "mgm_kernel_launches", "mgm_mlp_size", "mgm_mlp_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -327,6 +347,106 @@ class Hierarchy:
             _check(st)
         return u, {"iters": info.iters, "rel_res": info.rel_res, "solve_ms": info.solve_ms, "converged": st == 0,
                    "history": [hist[i] for i in range(info.iters + 1)]}
+
+
+    # ---- learned correction after the V-cycle (an addition to the paper's method)
+    def learned_attach(self, xyz, nrm, idx, w):
+        """Attach level-0 stencils (device tensors in caller order: xyz, nrm N x 3 float64, idx
+        N x n int32 centre first, w N x n float64 LBO weights)."""
+        xyz = _dev(xyz, torch.float64, "xyz"); nrm = _dev(nrm, torch.float64, "nrm")
+        idx = _dev(idx, torch.int32, "idx"); w = _dev(w, torch.float64, "w")
+        self.ln = idx.shape[1]
+        _check(lib().mgm_learned_attach(self._h, _p(xyz), _p(nrm), _p(idx), _p(w), self.ln, _stream()))
+
+    def learned_features(self, r):
+        r = _dev(r, torch.float64, "r")
+        feat = torch.empty((self.N, 4 * self.ln), dtype=torch.float32, device=r.device)
+        rho = torch.empty(self.N, dtype=torch.float32, device=r.device)
+        _check(lib().mgm_learned_features(self._h, _p(r), _p(feat), _p(rho), _stream()))
+        return feat, rho
+
+    def learned_cycle_residual(self, r):
+        """r - L M r with the plain V-cycle M (a training sample)."""
+        r = _dev(r, torch.float64, "r")
+        out = torch.empty_like(r)
+        _check(lib().mgm_learned_cycle_residual(self._h, _p(r), _p(out), _stream()))
+        return out
+
+    def learned_loss(self, net, r, grad=False):
+        r = _dev(r, torch.float64, "r")
+        J = C.c_double(0.0)
+        g = torch.empty(net.size, dtype=torch.float32, device=r.device) if grad else None
+        _check(lib().mgm_learned_loss(self._h, net._h, _p(r), C.byref(J), _p(g), _stream()))
+        return (J.value, g) if grad else J.value
+
+    def learned_train_step(self, net, r, lr):
+        r = _dev(r, torch.float64, "r")
+        J = C.c_double(0.0)
+        _check(lib().mgm_learned_train_step(self._h, net._h, _p(r), float(lr), C.byref(J), _stream()))
+        return J.value
+
+    def learned_enable(self, net):
+        """Use net (its current weights, BF16) after each V-cycle; None switches it off."""
+        _check(lib().mgm_learned_enable(self._h, net._h if net is not None else None, _stream()))
+
+    def learned_correction(self, r):
+        r = _dev(r, torch.float64, "r")
+        d = torch.empty_like(r)
+        _check(lib().mgm_learned_correction(self._h, _p(r), _p(d), _stream()))
+        return d
+
+    def learned_info(self):
+        en = C.c_int(0); fb = C.c_int64(0)
+        _check(lib().mgm_learned_info(self._h, C.byref(en), C.byref(fb)))
+        return {"enabled": bool(en.value), "fallbacks": int(fb.value)}
+
+
+class MLP:
+    """The learned correction's network (4n -> 64 -> 64 -> 1, no biases), owned by the library:
+    FP32 master weights and Adam state on the device."""
+
+    def __init__(self, n, seed=0):
+        self.n = n
+        self.size = int(lib().mgm_mlp_size(n))
+        if self.size < 0:
+            raise ValueError("stencil size must be in [1, 48]")
+        h = C.c_void_p()
+        self._h = None
+        _check(lib().mgm_mlp_create(n, seed, C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().mgm_mlp_destroy(self._h)
+            self._h = None
+
+    def get(self):
+        """(W1 64 x 4n, W2 64 x 64, w3 64) as float32 numpy arrays."""
+        import numpy as np
+        w = np.empty(self.size, np.float32)
+        _check(lib().mgm_mlp_get(self._h, w.ctypes.data))
+        d = 4 * self.n
+        return w[:64 * d].reshape(64, d).copy(), w[64 * d:64 * d + 4096].reshape(64, 64).copy(), w[64 * d + 4096:].copy()
+
+    def set(self, W1, W2, w3):
+        import numpy as np
+        w = np.ascontiguousarray(np.concatenate([np.ravel(W1), np.ravel(W2), np.ravel(w3)]).astype(np.float32))
+        if w.size != self.size:
+            raise ValueError("weight shapes do not match the stencil size")
+        _check(lib().mgm_mlp_set(self._h, w.ctypes.data))
+
+    def forward(self, feat):
+        feat = _dev(feat, torch.float32, "feat")
+        out = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+        _check(lib().mgm_mlp_forward(self._h, _p(feat), feat.shape[0], _p(out), _stream()))
+        return out
+
+    def vjp(self, feat, gout):
+        feat = _dev(feat, torch.float32, "feat"); gout = _dev(gout, torch.float32, "gout")
+        g = torch.empty(self.size, dtype=torch.float32, device=feat.device)
+        _check(lib().mgm_mlp_vjp(self._h, _p(feat), _p(gout), feat.shape[0], _p(g), _stream()))
+        d = 4 * self.n
+        return g[:64 * d].reshape(64, d), g[64 * d:64 * d + 4096].reshape(64, 64), g[64 * d + 4096:]
 
 
 def check_bounded_wait(nblocks=4, spin_limit=20000):

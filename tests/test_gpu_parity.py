@@ -275,16 +275,38 @@ def test_single_level_and_small(M, oracle):
     assert info["converged"] and np.linalg.norm(H(u) - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
-def test_persistent_and_per_colour_sweeps_identical(M, oracle, ico5):
-    """The persistent multicolour sweep (one cooperative launch per sweep, grid barriers between
-    colours) computes every row exactly as the one-launch-per-colour schedule does."""
+@pytest.mark.parametrize("nu", [1, 2])
+def test_persistent_and_per_colour_sweeps_identical(M, oracle, ico5, nu):
+    """The persistent multicolour sweeps (one cooperative launch per sweep: grid barriers between
+    colours, or per-row ready flags) compute every row exactly as the one-launch-per-colour
+    schedule does."""
     x, nrm, idx, w, L = ico5
     Lt = (T(L.indptr.astype(np.int32)), T(L.indices.astype(np.int32)), T(L.data))
     r = T(np.random.default_rng(5).standard_normal(x.shape[0]))
     for prec in ("f32", "f64"):
-        Ha = M.Hierarchy(T(x), *Lt, n_min=125, precision=prec)
-        Hb = M.Hierarchy(T(x), *Lt, n_min=125, precision=prec, persistent_sweeps=True)
+        Ha = M.Hierarchy(T(x), *Lt, n_min=125, nu1=nu, nu2=nu, precision=prec)
+        za = Ha.vcycle(r)
+        for mode in (1, 2):
+            Hb = M.Hierarchy(T(x), *Lt, n_min=125, nu1=nu, nu2=nu, precision=prec, persistent_sweeps=mode)
+            assert torch.equal(za, Hb.vcycle(r)), (prec, mode)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_flag_driven_sweeps_identical_at_scale(M, prec):
+    """Per-row ready flags at a size where every resident warp takes many row groups and rows of
+    several colours are in flight at once: V-cycles and solves bit-identical to per-colour
+    launches."""
+    x, nrm = I.fibonacci_sphere(300000, 0.1, 9)
+    _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 30, "rbf", 1, 2, 1.0, keep_weights=False)
+    Ha = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec)
+    Hb = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec, persistent_sweeps=2)
+    r = T(np.random.default_rng(6).standard_normal(x.shape[0]))
+    for _ in range(3):
         assert torch.equal(Ha.vcycle(r), Hb.vcycle(r))
+    f = T(I.random_sh_rhs(x, lmax=12, seed=7))
+    ua, ia = Ha.solve(f, tol=1e-10)
+    ub, ib = Hb.solve(f, tol=1e-10)
+    assert ia["converged"] and ia["iters"] == ib["iters"] and torch.equal(ua, ub)
 
 
 def test_bounded_wait_reports_timeout(M):
