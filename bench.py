@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
                     help="c2: the N=1M sphere/torus time-to-solution line; c3: the full 64-surface batched line")
     ap.add_argument("--batch-problems", type=int, default=16, help="surfaces in the batched measurement of the c2 line")
+    ap.add_argument("--learned-surfaces", type=int, default=24,
+                    help="training surfaces of the learned-correction measurement (0 skips it)")
+    ap.add_argument("--learned-eval-size", type=int, default=1 << 20, help="points of the held-out bumpy torus")
     ap.add_argument("--single", action="store_true",
                     help="one pass of the path on the sphere only (a small driver for profilers); prints its phases")
     return ap.parse_args()
@@ -228,6 +231,8 @@ def bench_ours(a, rank, world, local_rank):
     res["e2e_d2h"] = d2h // len(hp)
     if a.batch_problems > 0:
         res["batched"] = bench_batched(a.batch_problems, dev)
+        if a.learned_surfaces > 0:
+            res["learned"] = bench_learned(a.learned_surfaces, a.learned_eval_size, dev)
     return res
 
 
@@ -305,6 +310,61 @@ def bench_batched(nprob, dev):
             "ms_per_rhs": round(E[1].elapsed_time(E[2]) / nrhs_total, 3),
             "iters_max": max(i["iters"] for i in flat), "iters_single_max": max(single_iters),
             "converged": all(i["converged"] for i in flat)}
+
+
+C4 = dict(n=30, ell=2, k=1, n_min=250, tol=1e-10, Nlo=50000, Nhi=200000, passes=4, lr=2e-3, lr_final=2e-4)
+
+
+def bench_learned(nsurf, Neval, dev):
+    """Learned correction after the V-cycle: trained on the GPU on nsurf seeded bumpy spheres and
+    tori (N log-uniform in [50k, 200k]; PHS r^3, degree 2, n = 30, -Lap + I), each surface's
+    samples used as it is built; evaluated on a held-out bumpy torus of Neval points against the
+    plain cycle (FGMRES to 1e-10)."""
+    import torch
+    from paper_2204_06154_gb300 import inputs as I
+    from paper_2204_06154_gb300 import learned as LR
+    from paper_2204_06154_gb300 import mgm as M
+    rng = np.random.default_rng(404)
+    net = M.MLP(C4["n"], seed=1)
+    total = nsurf * 6 * C4["passes"]
+    t0 = time.time()
+    step = 0
+    losses = []
+    for sidx in range(nsurf):
+        N = int(np.exp(rng.uniform(np.log(C4["Nlo"]), np.log(C4["Nhi"]))))
+        x, nrm = (I.bumpy_sphere(N, seed=1000 + sidx) if sidx % 2 == 0 else I.bumpy_torus(N, seed=1000 + sidx))
+        P = LR.Problem(x, nrm, n=C4["n"], k=C4["k"], ell=C4["ell"], n_min=C4["n_min"], device=dev)
+        items = [(P, r) for r in P.samples(seed=2000 + sidx, smooth="poly")]
+        for _ in range(C4["passes"]):
+            for (Q, r) in items:
+                lr = C4["lr"] * (C4["lr_final"] / C4["lr"]) ** (step / max(1, total - 1))
+                losses.append(Q.H.learned_train_step(net, r, lr))
+                step += 1
+        del P, items
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    x, nrm = I.bumpy_torus(Neval, seed=77)
+    P = LR.Problem(x, nrm, n=C4["n"], k=C4["k"], ell=C4["ell"], n_min=C4["n_min"], device=dev)
+    f = torch.from_numpy(I.random_sh_rhs(x, lmax=20, seed=78)).to(dev)
+    out = {}
+    for name, use in (("plain", None), ("learned", net)):
+        P.H.learned_enable(use)
+        P.H.solve(f, tol=C4["tol"])  # warm-up (graph capture)
+        u, info = P.H.solve(f, tol=C4["tol"])
+        out[name] = {"iters": info["iters"], "solve_ms": round(info["solve_ms"], 2), "rel_res": info["rel_res"],
+                     "converged": info["converged"]}
+    pr = P.H.profile(reps=20)
+    li = P.H.learned_info()
+    P.H.learned_enable(None)
+    return {"training": {"surfaces": nsurf, "points_range": [C4["Nlo"], C4["Nhi"]], "steps": step,
+                         "seconds": round(train_s, 1), "J_first": round(float(np.mean(losses[:12])), 4),
+                         "J_last": round(float(np.mean(losses[-48:])), 4)},
+            "eval": {"surface": f"bumpy torus, {Neval} points, PHS r^3 + degree 2, n=30, -Lap+I, SH rhs l<=20",
+                     **out, "speedup": round(out["plain"]["solve_ms"] / out["learned"]["solve_ms"], 3),
+                     "fallbacks": li["fallbacks"]},
+            "vcycle_ms": {"plain": round(pr["vcycle_ms"], 4), "with_correction": round(pr["learned_vcycle_ms"], 4)},
+            "correction_kernel": {"ms": round(pr["learned_ms"], 4), "bytes": pr["learned_bytes"],
+                                  "GB/s": round(pr["learned_bytes"] / pr["learned_ms"] / 1e6, 1) if pr["learned_ms"] else None}}
 
 
 def cpu_baseline(a, Ns=None):
@@ -426,6 +486,7 @@ def main():
                 "d2h_bytes_per_step": res["e2e_d2h"]},
         "gpu_launches": res["launches"],
         "batched": res.get("batched"),
+        "learned": res.get("learned"),
         "clocks": res["clocks"],
     }
     if not a.no_cpu_baseline and world == 1:

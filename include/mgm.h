@@ -268,7 +268,7 @@ mgm_status mgm_hierarchy_pnnz(const mgm_hierarchy* H, int j, int64_t* nnz_out);
  * array read or written once per pass; gathered vector entries, which the RCM ordering keeps in
  * L2, not counted). Overwrites the hierarchy's work vectors. Synchronises the stream. */
 typedef struct {
-    float vcycle_ms;         /* one V-cycle (the captured graph) */
+    float vcycle_ms;         /* one plain V-cycle (the captured graph) */
     int64_t vcycle_bytes;
     int64_t vcycle_kernels;  /* kernels per V-cycle */
     float sweep_ms;          /* one full Gauss-Seidel sweep of the finest level (all colours) */
@@ -276,6 +276,9 @@ typedef struct {
     int32_t sweep_launches;  /* kernels per sweep (colours of the finest level) */
     float spmv_ms;           /* the outer FP64 product w = L z on the finest level */
     int64_t spmv_bytes;
+    float learned_vcycle_ms; /* with a learned correction enabled: the cycle including it */
+    float learned_ms;        /* the correction kernel alone */
+    int64_t learned_bytes;   /* its algorithmic bytes (0 when no correction is enabled) */
 } mgm_profile_info;
 mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_stream stream);
 

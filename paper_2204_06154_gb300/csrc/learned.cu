@@ -332,7 +332,7 @@ __global__ void pack_k(const float* W, int n, uint16_t* lw) {
     lw[t] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
-// hg[a][s] = sum_j sum_{q<3} bf16(W1[a][4j+q]) geo[3j+q][s]
+// hg[s][a] = sum_j sum_{q<3} bf16(W1[a][4j+q]) geo[3j+q][s]   (row-major: 256 contiguous bytes a row)
 __global__ void __launch_bounds__(128) hg_k(const float* __restrict__ geo, int n, int64_t N, const float* __restrict__ W,
                                             float* hg) {
     extern __shared__ __align__(16) float gsm[];  // [3n][64]
@@ -360,66 +360,165 @@ __global__ void __launch_bounds__(128) hg_k(const float* __restrict__ geo, int n
             h[4 * q + 3] = fmaf(c.w, g, h[4 * q + 3]);
         }
     }
+    float4* out = reinterpret_cast<float4*>(hg + s * HID);
 #pragma unroll
-    for (int a = 0; a < HID; ++a) hg[(int64_t)a * N + s] = h[a];
+    for (int q = 0; q < HID / 4; ++q) out[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
 }
 
-// e[s] += rho out / l_ss from the residual r (solve order); rows with a zero stencil residual
-// are left unchanged
-__global__ void __launch_bounds__(128) correct_k(const int32_t* __restrict__ nbr, const float* __restrict__ r,
-                                                 const float* __restrict__ hg, const float* __restrict__ diag,
-                                                 const uint16_t* __restrict__ lw, int n, int64_t N, float* e) {
-    extern __shared__ __align__(16) float csm[];  // [n][64] | [64][64] | [64], expanded from BF16
-    const int tot = n * HID + HID * HID + HID;
-    for (int q = threadIdx.x; q < tot; q += blockDim.x) csm[q] = __uint_as_float((uint32_t)lw[q] << 16);
+// e[s] += rho out / l_ss from the residual r (solve order); rows with a zero stencil residual are
+// left unchanged. Tensor cores (mma.sync m16n8k16, BF16 in, FP32 accumulate), one warp per tile of
+// 16 rows:
+//   GEMM1  D1 = X W1_r^T   X = r_stencil / rho (16 x K1, K1 = n rounded up to 16), W1_r 64 x K1
+//   h1 = relu(D1 + hg)     (hg: the geometric part, FP32, row-major [N][64])
+//   GEMM2  D2 = h1 W2^T,   out = w3 . relu(D2)
+// Activations are split into BF16 hi + lo parts (x = hi + lo to ~2^-16 relative), each multiplied
+// by the exact BF16 weights, so the products carry FP32-like accuracy. GEMM2's A fragments are
+// GEMM1's accumulators, re-packed in registers (the m16n8 accumulator layout of two adjacent
+// n-tiles is the m16k16 operand layout).
+constexpr int CW = 4;                 // warps per block
+constexpr int W2S = HID + 8;          // shared-memory row strides (bf16 units), padded against
+__host__ __device__ constexpr int k1_of(int n) { return (n + 15) / 16 * 16; }   // bank conflicts
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {  // element k in the low half
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo_k)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi_k)) << 16);
+}
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const float ha = __bfloat162float(__float2bfloat16_rn(a)), hb = __bfloat162float(__float2bfloat16_rn(b));
+    hi = pack_bf16(ha, hb);
+    lo = pack_bf16(a - ha, b - hb);
+}
+__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(CW * 32) correct_k(const int32_t* __restrict__ nbr, const float* __restrict__ r,
+                                                    const float* __restrict__ hg, const float* __restrict__ diag,
+                                                    const uint16_t* __restrict__ lw, int n, int64_t N, float* e) {
+    extern __shared__ __align__(16) uint16_t lsm[];
+    const int K1 = k1_of(n), S1 = K1 + 8;
+    uint16_t* w1 = lsm;                       // [64][S1]: W1_r as [unit][stencil member]
+    uint16_t* w2 = w1 + HID * S1;             // [64][W2S]
+    float* w3 = reinterpret_cast<float*>(w2 + HID * W2S);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint16_t* xs = reinterpret_cast<uint16_t*>(w3 + HID) + warp * 2 * 16 * S1;  // [hi|lo][16][S1]
+    for (int q = threadIdx.x; q < HID * S1; q += blockDim.x) {
+        const int a = q / S1, k = q - a * S1;
+        w1[q] = k < n ? lw[k * HID + a] : (uint16_t)0;
+    }
+    for (int q = threadIdx.x; q < HID * W2S; q += blockDim.x) {
+        const int a = q / W2S, k = q - a * W2S;
+        w2[q] = k < HID ? lw[n * HID + a * HID + k] : (uint16_t)0;
+    }
+    for (int q = threadIdx.x; q < HID; q += blockDim.x) w3[q] = __uint_as_float((uint32_t)lw[n * HID + HID * HID + q] << 16);
     __syncthreads();
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const float* W1r = csm;
-    const float* W2 = csm + n * HID;
-    const float* w3 = W2 + HID * HID;
-    float h[HID];
+    const int g = lane >> 2, tg = lane & 3;
+    const int64_t ntiles = (N + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * CW + warp; tile < ntiles; tile += (int64_t)gridDim.x * CW) {
+        const int64_t r0 = tile * 16;
+        // gather the stencil residuals: lane -> row (lane & 15), members j = (lane >> 4) + 2t
+        const int64_t grow = r0 + (lane & 15);
+        const bool gact = grow < N;
+        float vals[(LMAX_N + 1) / 2];
+        float ss = 0.0f;
 #pragma unroll
-    for (int a = 0; a < HID; ++a) h[a] = 0.0f;
-    float ss = 0.0f;
-    for (int j = 0; j < n; ++j) {
-        const float rj = r[nbr[(int64_t)j * N + s]];
-        ss = fmaf(rj, rj, ss);
-        const float4* w4 = reinterpret_cast<const float4*>(W1r + j * HID);
-#pragma unroll
-        for (int q = 0; q < HID / 4; ++q) {
-            const float4 c = w4[q];
-            h[4 * q + 0] = fmaf(c.x, rj, h[4 * q + 0]);
-            h[4 * q + 1] = fmaf(c.y, rj, h[4 * q + 1]);
-            h[4 * q + 2] = fmaf(c.z, rj, h[4 * q + 2]);
-            h[4 * q + 3] = fmaf(c.w, rj, h[4 * q + 3]);
+        for (int t = 0; t < (LMAX_N + 1) / 2; ++t) {
+            const int j = (lane >> 4) + 2 * t;
+            float v = 0.0f;
+            if (gact && j < n) v = r[nbr[(int64_t)j * N + grow]];
+            vals[t] = v;
+            ss = fmaf(v, v, ss);
         }
-    }
-    if (!(ss > 0.0f)) return;
-    const float rho = sqrtf(ss / (float)n);
-    const float ir = 1.0f / rho;
+        ss += __shfl_xor_sync(0xffffffffu, ss, 16);
+        const float rho = sqrtf(ss / (float)n);
+        const float ir = rho > 0.0f ? 1.0f / rho : 0.0f;
+        __syncwarp();
 #pragma unroll
-    for (int a = 0; a < HID; ++a) h[a] = fmaxf(fmaf(h[a], ir, hg[(int64_t)a * N + s]), 0.0f);
-    float o = 0.0f;
-    for (int a = 0; a < HID; ++a) {
-        const float4* wa = reinterpret_cast<const float4*>(W2 + a * HID);
-        float z = 0.0f;
-#pragma unroll
-        for (int q = 0; q < HID / 4; ++q) {
-            const float4 c = wa[q];
-            z = fmaf(c.x, h[4 * q + 0], z);
-            z = fmaf(c.y, h[4 * q + 1], z);
-            z = fmaf(c.z, h[4 * q + 2], z);
-            z = fmaf(c.w, h[4 * q + 3], z);
+        for (int t = 0; t < (LMAX_N + 1) / 2; ++t) {
+            const int j = (lane >> 4) + 2 * t;
+            if (j < K1) {
+                const float x = vals[t] * ir;
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                xs[(lane & 15) * S1 + j] = __bfloat16_as_ushort(h);
+                xs[16 * S1 + (lane & 15) * S1 + j] = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+            }
         }
-        o = fmaf(w3[a], fmaxf(z, 0.0f), o);
+        __syncwarp();
+        // GEMM1: D1 (16 x 64) = X (16 x K1) W1_r^T, hi and lo parts of X
+        float d1[8][4];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) d1[t][0] = d1[t][1] = d1[t][2] = d1[t][3] = 0.0f;
+        for (int kk = 0; kk < K1; kk += 16) {
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                const uint16_t* xp = xs + part * 16 * S1;
+                uint32_t a[4];
+                a[0] = *reinterpret_cast<const uint32_t*>(xp + g * S1 + kk + 2 * tg);
+                a[1] = *reinterpret_cast<const uint32_t*>(xp + (g + 8) * S1 + kk + 2 * tg);
+                a[2] = *reinterpret_cast<const uint32_t*>(xp + g * S1 + kk + 8 + 2 * tg);
+                a[3] = *reinterpret_cast<const uint32_t*>(xp + (g + 8) * S1 + kk + 8 + 2 * tg);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const uint16_t* bp = w1 + (8 * t + g) * S1 + kk + 2 * tg;
+                    mma16816(d1[t], a, *reinterpret_cast<const uint32_t*>(bp), *reinterpret_cast<const uint32_t*>(bp + 8));
+                }
+            }
+        }
+        // h1 = relu(D1 + hg), re-packed as GEMM2's A operand (hi and lo)
+        const int64_t ra = r0 + g, rb = r0 + g + 8;
+        uint32_t ah[4][4], al[4][4];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int c = 8 * t + 2 * tg;
+            float2 ga = make_float2(0.0f, 0.0f), gb = make_float2(0.0f, 0.0f);
+            if (ra < N) ga = __ldg(reinterpret_cast<const float2*>(hg + ra * HID + c));
+            if (rb < N) gb = __ldg(reinterpret_cast<const float2*>(hg + rb * HID + c));
+            const float h0 = fmaxf(d1[t][0] + ga.x, 0.0f), h1v = fmaxf(d1[t][1] + ga.y, 0.0f);
+            const float h2 = fmaxf(d1[t][2] + gb.x, 0.0f), h3 = fmaxf(d1[t][3] + gb.y, 0.0f);
+            const int kb = t >> 1, half = (t & 1) * 2;   // k-step and register pair of the A fragment
+            split2(h0, h1v, ah[kb][half + 0], al[kb][half + 0]);
+            split2(h2, h3, ah[kb][half + 1], al[kb][half + 1]);
+        }
+        // GEMM2 per output n-tile, then relu, times w3, summed over the thread's columns
+        float oa = 0.0f, ob = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            float d2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+                const uint16_t* bp = w2 + (8 * t + g) * W2S + 16 * kb + 2 * tg;
+                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bp), b1 = *reinterpret_cast<const uint32_t*>(bp + 8);
+                mma16816(d2, ah[kb], b0, b1);
+                mma16816(d2, al[kb], b0, b1);
+            }
+            const int c = 8 * t + 2 * tg;
+            oa = fmaf(w3[c], fmaxf(d2[0], 0.0f), fmaf(w3[c + 1], fmaxf(d2[1], 0.0f), oa));
+            ob = fmaf(w3[c], fmaxf(d2[2], 0.0f), fmaf(w3[c + 1], fmaxf(d2[3], 0.0f), ob));
+        }
+        oa += __shfl_xor_sync(0xffffffffu, oa, 1);
+        oa += __shfl_xor_sync(0xffffffffu, oa, 2);
+        ob += __shfl_xor_sync(0xffffffffu, ob, 1);
+        ob += __shfl_xor_sync(0xffffffffu, ob, 2);
+        const float rho_a = __shfl_sync(0xffffffffu, rho, g);       // lane g holds row g's rho
+        const float rho_b = __shfl_sync(0xffffffffu, rho, g + 8);
+        if (tg == 0) {
+            if (ra < N && rho_a > 0.0f) e[ra] += rho_a * oa / diag[ra];
+            if (rb < N && rho_b > 0.0f) e[rb] += rho_b * ob / diag[rb];
+        }
+        __syncwarp();
     }
-    e[s] += rho * o / diag[s];
 }
 
 // ------------------------------ host side ------------------------------------------------------
 static size_t fwd_smem(int din) { return sizeof(float) * (size_t)mlp_count(din); }
-static size_t correct_smem(int n) { return sizeof(float) * (size_t)(n * HID + HID * HID + HID); }
+static size_t correct_smem(int n) {
+    return sizeof(uint16_t) * (size_t)(HID * (k1_of(n) + 8) + HID * W2S) + sizeof(float) * HID +
+           sizeof(uint16_t) * (size_t)CW * 2 * 16 * (k1_of(n) + 8);
+}
 
 static void set_smem_limits() {
     static bool done = false;
@@ -621,8 +720,18 @@ void learned_enable(mgm_hierarchy* H, const mgm_mlp* M, cudaStream_t s) {
 void learned_correct(mgm_hierarchy* H, cudaStream_t s) {
     set_smem_limits();
     Level& L0 = H->lv[0];
-    correct_k<<<grid_for(H->N, 128), 128, correct_smem(H->ln), s>>>(H->lnbr.get(), L0.s32.get(), H->lhg.get(),
-                                                                   L0.diag32.get(), H->lw.get(), H->ln, H->N, L0.e32.get());
+    static int blocks = 0;
+    if (!blocks) {
+        int per_sm = 0, dev = 0, sms = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, correct_k, CW * 32, correct_smem(LMAX_N)));
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        blocks = std::max(1, per_sm * sms);
+    }
+    const int64_t tiles = (H->N + 15) / 16;
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (tiles + CW - 1) / CW));
+    correct_k<<<nb, CW * 32, correct_smem(H->ln), s>>>(H->lnbr.get(), L0.s32.get(), H->lhg.get(), L0.diag32.get(),
+                                                     H->lw.get(), H->ln, H->N, L0.e32.get());
     CK_LAUNCH();
 }
 

@@ -658,12 +658,34 @@ void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStrea
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int t = 0; t < 2; ++t) vcycle_core(H, s);
+    float ms = 0.0f;
+    out->learned_vcycle_ms = 0.0f;
+    out->learned_ms = 0.0f;
+    out->learned_bytes = 0;
+    if (H->learned) {  // the cycle with the learned correction, and the correction kernel alone
+        H->learned_active = true;
+        for (int t = 0; t < 2; ++t) vcycle_core(H, s);
+        CK(cudaEventRecord(e0, s));
+        for (int t = 0; t < reps; ++t) vcycle_core(H, s);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        out->learned_vcycle_ms = ms / reps;
+        for (int t = 0; t < 2; ++t) learned_correct(H, s);
+        CK(cudaEventRecord(e0, s));
+        for (int t = 0; t < reps; ++t) learned_correct(H, s);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        out->learned_ms = ms / reps;
+        // per row: n stencil indices, 64 first-layer geometric terms, diagonal, e read and written
+        out->learned_bytes = H->N * (4 * (int64_t)H->ln + 64 * 4 + 4 + 8);
+    }
+    for (int t = 0; t < 2; ++t) vcycle_plain(H, s);
     CK(cudaEventRecord(e0, s));
-    for (int t = 0; t < reps; ++t) vcycle_core(H, s);
+    for (int t = 0; t < reps; ++t) vcycle_plain(H, s);
     CK(cudaEventRecord(e1, s));
     CK(cudaEventSynchronize(e1));
-    float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
     out->vcycle_ms = ms / reps;
     out->vcycle_bytes = vcycle_bytes(H);

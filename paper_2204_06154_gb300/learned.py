@@ -24,10 +24,21 @@ class Problem:
         self.H.learned_attach(self.xyz, self.nrm, self.idx, self.w)
         self.N = self.xyz.shape[0]
 
-    def samples(self, seed, cycles=3, lmax=20):
-        """Residuals after 1..cycles plain V-cycles from a harmonic and a white-noise start."""
-        rhs = [I.random_sh_rhs(self.xyz_host, lmax=lmax, seed=seed),
-               np.random.default_rng(seed).standard_normal(self.N)]
+    def samples(self, seed, cycles=3, lmax=20, smooth="sh"):
+        """Residuals after 1..cycles plain V-cycles from a smooth start (a random spherical-harmonic
+        sum up to degree lmax, or with smooth="poly" a random polynomial of degree <= 4 in the
+        coordinates, cheaper for large clouds) and from a white-noise start."""
+        rng = np.random.default_rng(seed)
+        if smooth == "sh":
+            f0 = I.random_sh_rhs(self.xyz_host, lmax=lmax, seed=seed)
+        else:
+            x = self.xyz_host
+            f0 = np.zeros(self.N)
+            for a in range(5):
+                for b in range(5 - a):
+                    for c in range(5 - a - b):
+                        f0 += rng.standard_normal() * x[:, 0] ** a * x[:, 1] ** b * x[:, 2] ** c
+        rhs = [f0, rng.standard_normal(self.N)]
         out = []
         for r0 in rhs:
             r = torch.tensor(r0, dtype=torch.float64, device=self.xyz.device)

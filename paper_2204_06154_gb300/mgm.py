@@ -68,7 +68,8 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
 class ProfileInfo(C.Structure):
     _fields_ = [("vcycle_ms", C.c_float), ("vcycle_bytes", C.c_int64), ("vcycle_kernels", C.c_int64),
                 ("sweep_ms", C.c_float), ("sweep_bytes", C.c_int64), ("sweep_launches", C.c_int32),
-                ("spmv_ms", C.c_float), ("spmv_bytes", C.c_int64)]
+                ("spmv_ms", C.c_float), ("spmv_bytes", C.c_int64),
+                ("learned_vcycle_ms", C.c_float), ("learned_ms", C.c_float), ("learned_bytes", C.c_int64)]
 
 
 def lib():

@@ -49,7 +49,7 @@ def bf16(a):
 
 @pytest.fixture(scope="module")
 def prob(M, LR, oracle):
-    x, nrm = I.bumpy_sphere(6000, seed=21)
+    x, nrm = I.bumpy_sphere(6007, seed=21)   # not a multiple of the 16-row inference tile
     idx, w, L = oracle.build_operator(x, nrm, N_ST, "rbf", 1, 2, 1.0)
     P = LR.Problem(x, nrm, n=N_ST, ell=2)
     assert np.array_equal(H(P.idx), idx)
@@ -151,7 +151,7 @@ def test_bf16_inference_matches_oracle(prob, oracle, M):
         net.set(J1, J2, J3)
         P.H.learned_enable(net)
         d = H(P.H.learned_correction(T(r)))
-        np.testing.assert_allclose(d, r / L.diagonal(), rtol=2e-6, atol=0)
+        np.testing.assert_allclose(d, r / L.diagonal(), rtol=1e-4, atol=0)  # activations split in two BF16 parts
     finally:
         P.H.learned_enable(None)
 
