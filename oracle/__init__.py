@@ -65,6 +65,9 @@ def lib():
         L.or_fgmres.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_int, C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_int, C.c_double,
                                 C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
+        L.or_bicgstab.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_int, C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_double,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
         L.or_mgm_solve.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, f64p, i32p, C.c_void_p,
                                    C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_double,
                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]
@@ -373,6 +376,30 @@ def fgmres(A, H, f, x0=None, restart=50, maxit=200, tol=1e-10, precond=True, his
                          int(precond), f, x, restart, maxit, tol, C.byref(it), C.byref(rel), hbuf.ctypes.data)
     if st not in (0, 3):
         _check("fgmres", st)
+    out = (x, it.value, rel.value)
+    return out + (hbuf[: it.value + 1],) if hist else out
+
+
+def bicgstab(A, H, f, x0=None, maxit=200, tol=1e-10, precond=True, hist=False):
+    """Right-preconditioned BiCGSTAB with one MGM V-cycle per preconditioner application
+    (Sec. 4.6). Returns (x, preconditioner applications, true relative residual[, history])."""
+    rp, ci, v = _csr(A)
+    n = A.shape[0]
+    f = _c(f, np.float64)
+    x = np.zeros(n) if x0 is None else _c(x0, np.float64).copy()
+    it = C.c_int(0); rel = C.c_double(0.0)
+    hbuf = np.zeros(maxit + 1)
+    if H is not None and H.p > 1:
+        lv = H._levels(); lvp = C.addressof(lv); p = H.p
+        lu, piv, perm = H.lu.ctypes.data, H.piv.ctypes.data, H.perm[0].ctypes.data
+    else:
+        lvp, p, lu, piv, perm = None, 0, None, None, None
+        if precond:
+            raise ValueError("BiCGSTAB with a one-level hierarchy: use a direct solve")
+    st = lib().or_bicgstab(n, rp, ci, v, lvp, p, lu, piv, perm, H.nu1 if H else 1, H.nu2 if H else 1,
+                           int(precond), f, x, maxit, tol, C.byref(it), C.byref(rel), hbuf.ctypes.data)
+    if st not in (0, 3):
+        _check("bicgstab", st)
     out = (x, it.value, rel.value)
     return out + (hbuf[: it.value + 1],) if hist else out
 

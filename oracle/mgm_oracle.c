@@ -872,6 +872,7 @@ int or_vcycle(const or_level* lv, int p, const double* lu, const int32_t* piv, c
 }
 
 static double nrm2(int64_t n, const double* x) { double s = 0.0; for (int64_t i = 0; i < n; ++i) s = s + x[i] * x[i]; return sqrt(s); }
+static double dot(int64_t n, const double* a, const double* b) { double s = 0.0; for (int64_t i = 0; i < n; ++i) s = s + a[i] * b[i]; return s; }
 
 /* ===========================================================================================
  * Right-preconditioned flexible GMRES(restart) with modified Gram-Schmidt (Sec. 4.6; Sec. 5:
@@ -953,6 +954,75 @@ int or_fgmres(int64_t n, const int32_t* arp, const int32_t* aci, const double* a
     }
     *iters_out = it; *relres_out = rel;
     free(V); free(Z); free(H); free(cs); free(sn); free(g); free(w); free(y);
+    return status;
+}
+
+/* Right-preconditioned BiCGSTAB (Sec. 4.6; the method of van der Vorst as given in Saad's book)
+ * with one MGM V-cycle from a zero guess per preconditioner application, in FP64. Each step
+ * applies the preconditioner twice; iters_out counts applications, the convention of Sec. 5.2.
+ * Per step: rho = rh.r; beta = (rho/rho_old)(alpha/omega); p = r + beta (p - omega v);
+ * ph = M p; v = L ph; alpha = rho / rh.v; s = r - alpha v (stop here when |s|/|f| <= tol, with
+ * x += alpha ph); sh = M s; t = L sh; omega = t.s / t.t; x += alpha ph + omega sh;
+ * r = s - omega t. rh = r_0. Stops on the recurred residual; relres_out is the true residual
+ * |f - L x|/|f| at exit. Breakdown (rho = 0 or t.t = 0) returns OR_ERR_NOTCONV. */
+int or_bicgstab(int64_t n, const int32_t* arp, const int32_t* aci, const double* av,
+                const or_level* lv, int p, const double* lu, const int32_t* piv, const int32_t* perm1, int nu1, int nu2,
+                int precond, const double* f, double* x, int maxit, double tol,
+                int* iters_out, double* relres_out, double* hist) {
+    double* r = (double*)malloc(sizeof(double) * n);
+    double* rh = (double*)malloc(sizeof(double) * n);
+    double* pv = (double*)calloc(n, sizeof(double));
+    double* v = (double*)calloc(n, sizeof(double));
+    double* ph = (double*)malloc(sizeof(double) * n);
+    double* sv = (double*)malloc(sizeof(double) * n);
+    double* sh = (double*)malloc(sizeof(double) * n);
+    double* t = (double*)malloc(sizeof(double) * n);
+    if (!r || !rh || !pv || !v || !ph || !sv || !sh || !t) return OR_ERR_NOMEM;
+    double fn = nrm2(n, f);
+    if (fn == 0.0) fn = 1.0;
+    csr_apply(n, arp, aci, av, x, t);
+    for (int64_t i = 0; i < n; ++i) { r[i] = f[i] - t[i]; rh[i] = r[i]; }
+    double rel = nrm2(n, r) / fn;
+    if (hist) hist[0] = rel;
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    int apps = 0, status = rel <= tol ? OR_OK : OR_ERR_NOTCONV;
+    while (status != OR_OK && apps + 1 <= maxit) {
+        double rho = dot(n, rh, r);
+        if (rho == 0.0) break;
+        double beta = (rho / rho_old) * (alpha / omega);
+        for (int64_t i = 0; i < n; ++i) pv[i] = r[i] + beta * (pv[i] - omega * v[i]);
+        if (precond) { for (int64_t i = 0; i < n; ++i) ph[i] = 0.0; or_vcycle(lv, p, lu, piv, perm1, nu1, nu2, pv, ph); }
+        else for (int64_t i = 0; i < n; ++i) ph[i] = pv[i];
+        ++apps;
+        csr_apply(n, arp, aci, av, ph, v);
+        alpha = rho / dot(n, rh, v);
+        for (int64_t i = 0; i < n; ++i) sv[i] = r[i] - alpha * v[i];
+        rel = nrm2(n, sv) / fn;
+        if (hist) hist[apps] = rel;
+        if (rel <= tol) {
+            for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * ph[i];
+            status = OR_OK;
+            break;
+        }
+        if (apps + 1 > maxit) { for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * ph[i]; break; }
+        if (precond) { for (int64_t i = 0; i < n; ++i) sh[i] = 0.0; or_vcycle(lv, p, lu, piv, perm1, nu1, nu2, sv, sh); }
+        else for (int64_t i = 0; i < n; ++i) sh[i] = sv[i];
+        ++apps;
+        csr_apply(n, arp, aci, av, sh, t);
+        double tt = dot(n, t, t);
+        if (tt == 0.0) { for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * ph[i]; break; }
+        omega = dot(n, t, sv) / tt;
+        for (int64_t i = 0; i < n; ++i) { x[i] = x[i] + alpha * ph[i] + omega * sh[i]; r[i] = sv[i] - omega * t[i]; }
+        rel = nrm2(n, r) / fn;
+        if (hist) hist[apps] = rel;
+        if (rel <= tol) status = OR_OK;
+        rho_old = rho;
+    }
+    csr_apply(n, arp, aci, av, x, t);
+    for (int64_t i = 0; i < n; ++i) t[i] = f[i] - t[i];
+    *relres_out = nrm2(n, t) / fn;
+    *iters_out = apps;
+    free(r); free(rh); free(pv); free(v); free(ph); free(sv); free(sh); free(t);
     return status;
 }
 

@@ -410,12 +410,12 @@ def _golden_table2():
     with open(os.path.join(GOLDEN, "table2_sphere_rbffd.txt")) as fh:
         for line in fh:
             if line.strip() and not line.startswith("#"):
-                N, ell, it = map(int, line.split())
-                rows.append((N, ell, it))
+                N, ell, it, bi = map(int, line.split())
+                rows.append((N, ell, it, bi))
     return rows
 
 
-@pytest.mark.parametrize("N,ell,paper_it", [r for r in _golden_table2() if r[0] == 10242 and r[1] in (3, 5)])
+@pytest.mark.parametrize("N,ell,paper_it", [r[:3] for r in _golden_table2() if r[0] == 10242 and r[1] in (3, 5)])
 def test_paper_table2_band(oracle, N, ell, paper_it):
     """Sec. 5.2 Table 2 (MGM GMRES, sphere, RBF-FD): with the paper's own parameters (Table 1:
     k = ell, n = (ell+1)(ell+2), N_min = 250, m = 3, forward lexicographic GS, V(1,1)) and a random
@@ -430,3 +430,32 @@ def test_paper_table2_band(oracle, N, ell, paper_it):
     u, it, rel = oracle.fgmres(L, H, f, tol=1e-12, maxit=100)
     assert rel <= 1e-12
     assert abs(it - paper_it) <= 2, (it, paper_it)
+
+
+@pytest.mark.parametrize("N,ell,paper_apps", [(r[0], r[1], r[3]) for r in _golden_table2() if r[0] == 10242])
+def test_paper_table2_bicgstab_band(oracle, N, ell, paper_apps):
+    """Sec. 5.2 Table 2, BiCGSTAB (numbers in parentheses, counted as preconditioner applications):
+    the oracle's right-preconditioned MGM BiCGSTAB needs the printed count within +-2, and its
+    solution agrees with GMRES's."""
+    x, nrm = I.icosahedral_sphere(5)
+    n = (ell + 1) * (ell + 2)
+    idx, w, L = oracle.build_operator(x, nrm, n, "rbf", ell, ell, 1.0)
+    H = oracle.setup(x, L, 250, seed=0, smoother="lex")
+    f = np.random.default_rng(0).standard_normal(N)
+    u, apps, rel = oracle.bicgstab(L, H, f, tol=1e-12, maxit=200)
+    assert rel <= 2e-12
+    assert abs(apps - paper_apps) <= 2, (apps, paper_apps)
+    ug, _, _ = oracle.fgmres(L, H, f, tol=1e-12, maxit=100)
+    assert np.linalg.norm(u - ug) <= 1e-10 * np.linalg.norm(ug)
+
+
+def test_bicgstab_unpreconditioned_matches_direct_and_counts(oracle):
+    """Without a preconditioner BiCGSTAB is the textbook method on L itself: it reaches the direct
+    solution, applies the identity twice per step, and an exact initial guess stops at once."""
+    x, L = _small_problem(3)
+    f = np.random.default_rng(4).standard_normal(L.shape[0])
+    ue = spla.spsolve(L.tocsc(), f)
+    u, apps, rel = oracle.bicgstab(L, None, f, tol=1e-11, maxit=4000, precond=False)
+    assert rel <= 1e-11 and np.linalg.norm(u - ue) <= 1e-8 * np.linalg.norm(ue)
+    u0, apps0, rel0 = oracle.bicgstab(L, None, f, x0=ue, tol=1e-9, maxit=10, precond=False)
+    assert apps0 == 0 and rel0 <= 1e-9
