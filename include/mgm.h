@@ -51,7 +51,7 @@ typedef enum {
 
 enum { MGM_RBF_FD = 0, MGM_GFD = 1 };              /* discretisation (Sec. 2.2 / 2.3) */
 enum { MGM_F64 = 0, MGM_F32 = 1 };                  /* V-cycle arithmetic / vector dtype */
-enum { MGM_KRYLOV_FGMRES = 0, MGM_KRYLOV_NONE = 1 }; /* outer method (Sec. 4.6 / Sec. 5.1) */
+enum { MGM_KRYLOV_FGMRES = 0, MGM_KRYLOV_NONE = 1, MGM_KRYLOV_BICGSTAB = 2 }; /* outer method (Sec. 4.6 / Sec. 5.1) */
 
 /* Discretisation parameters (Sec. 2; Table 1). */
 typedef struct {
@@ -81,9 +81,9 @@ typedef struct {
 } mgm_params;
 
 typedef struct {
-    int krylov;      /* MGM_KRYLOV_FGMRES or MGM_KRYLOV_NONE (repeated V-cycles) */
-    int restart;     /* FGMRES restart length, 1..200 */
-    int maxit;       /* maximum iterations (V-cycle applications), >= 0 */
+    int krylov;      /* MGM_KRYLOV_FGMRES, MGM_KRYLOV_BICGSTAB or MGM_KRYLOV_NONE (repeated V-cycles) */
+    int restart;     /* FGMRES restart length, 1..200 (ignored by the other methods) */
+    int maxit;       /* maximum V-cycle applications (BiCGSTAB: two per step), >= 0 */
     double tol;      /* relative residual target |f - L u|_2 / |f|_2 */
 } mgm_solve_params;
 
@@ -222,10 +222,13 @@ mgm_status mgm_setup(const double* xyz, int64_t N, const int32_t* rowptr, const 
 mgm_status mgm_vcycle(mgm_hierarchy* H, const void* r, void* z, int dtype, mgm_stream stream);
 
 /* Solve L u = f (Sec. 4.6): right-preconditioned flexible GMRES(restart) in FP64 with one V-cycle
- * per iteration (or, with MGM_KRYLOV_NONE, repeated V-cycles on u). u holds the initial guess on
- * entry and the solution on return (caller order). Returns MGM_OK when |f - L u|/|f| <= tol,
- * MGM_ERR_NOT_CONVERGED when maxit is reached first; info (may be NULL) is filled in both cases.
- * Synchronises the stream once per iteration (convergence test). */
+ * per iteration; or right-preconditioned BiCGSTAB in FP64 with two V-cycles per step, counted as
+ * two iterations (the convention of Sec. 5.2); or, with MGM_KRYLOV_NONE, repeated V-cycles on u.
+ * u holds the initial guess on entry and the solution on return (caller order). Returns MGM_OK
+ * when |f - L u|/|f| <= tol, MGM_ERR_NOT_CONVERGED when maxit is reached first, MGM_ERR_BREAKDOWN
+ * when BiCGSTAB's rho or t.t vanishes or a value is not finite; info (may be NULL) is filled in
+ * every case. BiCGSTAB needs a linear preconditioner: it runs the plain cycle even when a learned
+ * correction is enabled. Synchronises the stream once per iteration (convergence test). */
 mgm_status mgm_solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp,
                      mgm_solve_info* info, mgm_stream stream);
 
@@ -341,14 +344,15 @@ mgm_status mgm_learned_cycle_residual(mgm_hierarchy* H, const double* r, double*
  * dJ/dW (device, mgm_mlp_size(n) floats). */
 mgm_status mgm_learned_loss(mgm_hierarchy* H, const mgm_mlp* M, const double* r, double* loss, float* grad,
                             mgm_stream stream);
-/* One Adam step of size lr on the sample r; *loss (host, may be NULL) = J before the step. */
+/* One Adam step of size lr on the sample r; *loss (host, may be NULL) = J before the step. A
+ * sample whose J or gradient is not finite (FP32 overflow) leaves the network unchanged. */
 mgm_status mgm_learned_train_step(mgm_hierarchy* H, mgm_mlp* M, const double* r, float lr, double* loss,
                                   mgm_stream stream);
 /* Use M's current weights (copied, BF16) in this hierarchy's V-cycle after the level-0
  * post-smoothing, for mgm_vcycle and mgm_solve; M = NULL switches the correction off. The
  * nonlinear preconditioner needs the flexible outer iteration: mgm_solve switches the correction
- * off for the rest of a solve when an iteration reduces the residual estimate by less than 1%
- * (FGMRES) or not at all (MGM_KRYLOV_NONE). mgm_solve_multi / _batched do not use it. */
+ * off for the rest of a solve when five FGMRES iterations reduce the residual estimate by less
+ * than 20% in all, or a standalone iteration (MGM_KRYLOV_NONE) does not reduce the residual. mgm_solve_multi / _batched do not use it. */
 mgm_status mgm_learned_enable(mgm_hierarchy* H, const mgm_mlp* M, mgm_stream stream);
 /* delta (device N FP64, caller order) = the enabled correction for residual r (device N FP64),
  * through the V-cycle's inference kernel. */

@@ -90,7 +90,7 @@ struct mgm_hierarchy {
     int ln = 0;                          // stencil size of the attached features (0: not attached)
     mgm::Buf<int32_t> lnbr;              // N x n stencil members, centre first
     mgm::Buf<float> lgeo;                // N x n x 3: xh/s, yh/s, c s^2
-    mgm::Buf<float> lhg;                 // N x 64: first layer applied to the geometric features
+    mgm::Buf<uint16_t> lhg;              // N x 64 FP16: first layer applied to the geometric features
     mgm::Buf<uint16_t> lw;               // BF16 [n x 64 residual columns of W1 | W2 | w3]
     mgm::Buf<int32_t> lrp, lci, ltrp, ltci;  // L_0 and L_0^T as plain CSR (training)
     mgm::Buf<float> lval, ltval;

@@ -121,6 +121,24 @@ __global__ void scatter64_k(const double* in, const int32_t* idx, double* out, i
     if (i < n) out[idx[i]] = in[i];
 }
 
+// BiCGSTAB updates: p = r + beta (p - omega v); s = r - alpha v; x += alpha ph + omega sh, r = s - omega t
+__global__ void bicg_p_k(const double* r, const double* v, double* p, double beta, double omega, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+}
+__global__ void bicg_s_k(const double* r, const double* v, double* sv, double alpha, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) sv[i] = r[i] - alpha * v[i];
+}
+__global__ void bicg_x_k(double* x, const double* ph, const double* sh, double alpha, double omega, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = x[i] + alpha * ph[i] + omega * (sh ? sh[i] : 0.0);
+}
+__global__ void bicg_r_k(const double* sv, const double* t, double* r, double omega, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = sv[i] - omega * t[i];
+}
+
 // ------------------------------ host side -------------------------------------------------------
 struct Ops {
     mgm_hierarchy* H;
@@ -151,7 +169,86 @@ struct Ops {
         double v = read1(H->hbuf.get(), s);
         return std::sqrt(v);
     }
+    double dot(const double* a, const double* b) {
+        dots(a, n, 1, b, H->hbuf.get());
+        return read1(H->hbuf.get(), s);
+    }
+    // z = M v (the V-cycle, FP64 in and out, solve order)
+    void precondition(const double* v, double* z) {
+        load_input(H, v, MGM_F64, nullptr, s);
+        vcycle_core(H, s);
+        store_output(H, z, MGM_F64, nullptr, s);
+    }
 };
+
+// Right-preconditioned BiCGSTAB (paper Sec. 4.6: MGM as the preconditioner of BiCGSTAB), FP64,
+// two V-cycles per step; `it` counts V-cycles. Returns the status; u, rel, hist updated.
+static mgm_status bicgstab(mgm_hierarchy* H, Ops& op, const mgm_solve_params* sp, double fn, std::vector<double>& hist,
+                           int& it, double& rel) {
+    const int64_t n = op.n;
+    cudaStream_t s = op.s;
+    double* W = H->V.get();  // 8 work vectors
+    double *r = W, *rh = W + n, *p = W + 2 * n, *v = W + 3 * n, *ph = W + 4 * n, *sv = W + 5 * n, *sh = W + 6 * n,
+           *t = W + 7 * n;
+    double* u = H->u.get();
+    const unsigned gb = grid_for(n, 256);
+    op.spmv<true, double>(u, H->f.get(), r);
+    CK(cudaMemcpyAsync(rh, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(p, 0, sizeof(double) * n, s));
+    CK(cudaMemsetAsync(v, 0, sizeof(double) * n, s));
+    rel = op.norm(r) / fn;
+    hist.push_back(rel);
+    if (!std::isfinite(rel)) return MGM_ERR_BREAKDOWN;
+    if (rel <= sp->tol) return MGM_OK;
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    mgm_status st = MGM_ERR_NOT_CONVERGED;
+    while (it + 1 <= sp->maxit) {
+        const double rho = op.dot(rh, r);
+        if (rho == 0.0 || !std::isfinite(rho)) { st = MGM_ERR_BREAKDOWN; break; }
+        const double beta = (rho / rho_old) * (alpha / omega);
+        bicg_p_k<<<gb, 256, 0, s>>>(r, v, p, beta, omega, n);
+        CK_LAUNCH();
+        op.precondition(p, ph);
+        ++it;
+        op.spmv<false, double>(ph, nullptr, v);
+        alpha = rho / op.dot(rh, v);
+        bicg_s_k<<<gb, 256, 0, s>>>(r, v, sv, alpha, n);
+        CK_LAUNCH();
+        rel = op.norm(sv) / fn;
+        hist.push_back(rel);
+        if (!std::isfinite(rel)) { st = MGM_ERR_BREAKDOWN; break; }
+        if (rel <= sp->tol || it + 1 > sp->maxit) {
+            bicg_x_k<<<gb, 256, 0, s>>>(u, ph, nullptr, alpha, 0.0, n);
+            CK_LAUNCH();
+            break;
+        }
+        op.precondition(sv, sh);
+        ++it;
+        op.spmv<false, double>(sh, nullptr, t);
+        const double tt = op.dot(t, t);
+        if (tt == 0.0 || !std::isfinite(tt)) {
+            bicg_x_k<<<gb, 256, 0, s>>>(u, ph, nullptr, alpha, 0.0, n);
+            CK_LAUNCH();
+            st = MGM_ERR_BREAKDOWN;
+            break;
+        }
+        omega = op.dot(t, sv) / tt;
+        bicg_x_k<<<gb, 256, 0, s>>>(u, ph, sh, alpha, omega, n);
+        CK_LAUNCH();
+        bicg_r_k<<<gb, 256, 0, s>>>(sv, t, r, omega, n);
+        CK_LAUNCH();
+        rel = op.norm(r) / fn;
+        hist.push_back(rel);
+        if (!std::isfinite(rel)) { st = MGM_ERR_BREAKDOWN; break; }
+        if (rel <= sp->tol) break;
+        rho_old = rho;
+    }
+    // the true residual decides
+    op.spmv<true, double>(u, H->f.get(), r);
+    rel = op.norm(r) / fn;
+    if (st != MGM_ERR_BREAKDOWN) st = rel <= sp->tol ? MGM_OK : MGM_ERR_NOT_CONVERGED;
+    return st;
+}
 
 static void ensure_workspace(mgm_hierarchy* H, int m) {
     const int64_t n = H->N;
@@ -199,10 +296,11 @@ void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_
 void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_params* sp, mgm_solve_info* info,
            cudaStream_t s) {
     REQUIRE(H && f_in && u_io && sp, "null argument");
-    REQUIRE(sp->krylov == MGM_KRYLOV_FGMRES || sp->krylov == MGM_KRYLOV_NONE, "unknown krylov method");
+    REQUIRE(sp->krylov == MGM_KRYLOV_FGMRES || sp->krylov == MGM_KRYLOV_NONE || sp->krylov == MGM_KRYLOV_BICGSTAB,
+            "unknown krylov method");
     REQUIRE(sp->maxit >= 0 && sp->tol >= 0.0, "maxit and tol must be >= 0");
     REQUIRE(sp->krylov != MGM_KRYLOV_FGMRES || (sp->restart >= 1 && sp->restart <= 200), "restart must be in [1, 200]");
-    const int m = sp->krylov == MGM_KRYLOV_FGMRES ? sp->restart : 1;
+    const int m = sp->krylov == MGM_KRYLOV_FGMRES ? sp->restart : sp->krylov == MGM_KRYLOV_BICGSTAB ? 8 : 1;
     ensure_workspace(H, m);
     vcycle_prepare(H);
     const int64_t n = H->N;
@@ -225,7 +323,10 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
     mgm_status status = MGM_ERR_NOT_CONVERGED;
     const bool f32 = H->precision == MGM_F32;
     // a learned correction that stops reducing the residual is switched off for the rest of the
-    // solve (the flexible outer iteration tolerates the change of preconditioner)
+    // solve (the flexible outer iteration tolerates the change of preconditioner): FGMRES when
+    // five iterations reduce the estimate by less than 20% (GMRES estimates never increase, and
+    // the first iterations of a good preconditioner may reduce little), the standalone iteration
+    // as soon as the residual grows
     H->learned_active = true;
     auto fallback_if = [&](bool stalled) {
         if (H->learned && H->learned_active && stalled) {
@@ -233,7 +334,10 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
             ++H->learned_fallbacks;
         }
     };
-    if (sp->krylov == MGM_KRYLOV_NONE) {
+    if (sp->krylov == MGM_KRYLOV_BICGSTAB) {
+        H->learned_active = false;  // BiCGSTAB needs a linear preconditioner
+        status = bicgstab(H, op, sp, fn, hist, it, rel);
+    } else if (sp->krylov == MGM_KRYLOV_NONE) {
         for (;;) {
             op.spmv<true, double>(H->u.get(), H->f.get(), H->r.get());
             rel = op.norm(H->r.get()) / fn;
@@ -313,7 +417,7 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
                 g[k] = cs[k] * g[k];
                 ++it;
                 double est = std::fabs(g[k1]) / fn;
-                fallback_if(!(est < 0.99 * hist.back()));
+                if (hist.size() >= 5) fallback_if(!(est < 0.8 * hist[hist.size() - 5]));
                 hist.push_back(est);
                 if (est <= sp->tol || hn == 0.0) { ++k; break; }
             }

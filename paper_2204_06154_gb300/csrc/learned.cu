@@ -16,6 +16,7 @@
 // expanded exactly to FP32 in shared memory; all arithmetic accumulates in FP32. Per-row arrays
 // are stored column-major ([j][N]) so one-thread-per-row loads coalesce.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -235,6 +236,11 @@ __global__ void reduce_partials_k(const float* partial, int nchunks, int total, 
     G[t] = s;
 }
 
+__global__ void nonfinite_k(const float* G, int64_t cnt, int* bad) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt && !isfinite(G[t])) atomicOr(bad, 1);
+}
+
 __global__ void adam_k(float* W, const float* G, float* m, float* v, int64_t cnt, float lr, float b1, float b2, float eps,
                        float bc1, float bc2) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -332,9 +338,11 @@ __global__ void pack_k(const float* W, int n, uint16_t* lw) {
     lw[t] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
-// hg[s][a] = sum_j sum_{q<3} bf16(W1[a][4j+q]) geo[3j+q][s]   (row-major: 256 contiguous bytes a row)
+// hg[s][a] = sum_j sum_{q<3} bf16(W1[a][4j+q]) geo[3j+q][s], accumulated in FP32 and stored as FP16
+// (row-major: 128 contiguous bytes a row; |hg| stays far below the FP16 range, relative rounding
+// 2^-11)
 __global__ void __launch_bounds__(128) hg_k(const float* __restrict__ geo, int n, int64_t N, const float* __restrict__ W,
-                                            float* hg) {
+                                            __half* hg) {
     extern __shared__ __align__(16) float gsm[];  // [3n][64]
     const int din = 4 * n;
     for (int q = threadIdx.x; q < 3 * n * HID; q += blockDim.x) {
@@ -360,16 +368,16 @@ __global__ void __launch_bounds__(128) hg_k(const float* __restrict__ geo, int n
             h[4 * q + 3] = fmaf(c.w, g, h[4 * q + 3]);
         }
     }
-    float4* out = reinterpret_cast<float4*>(hg + s * HID);
+    __half2* out = reinterpret_cast<__half2*>(hg + s * HID);
 #pragma unroll
-    for (int q = 0; q < HID / 4; ++q) out[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+    for (int q = 0; q < HID / 2; ++q) out[q] = __floats2half2_rn(h[2 * q], h[2 * q + 1]);
 }
 
 // e[s] += rho out / l_ss from the residual r (solve order); rows with a zero stencil residual are
 // left unchanged. Tensor cores (mma.sync m16n8k16, BF16 in, FP32 accumulate), one warp per tile of
 // 16 rows:
 //   GEMM1  D1 = X W1_r^T   X = r_stencil / rho (16 x K1, K1 = n rounded up to 16), W1_r 64 x K1
-//   h1 = relu(D1 + hg)     (hg: the geometric part, FP32, row-major [N][64])
+//   h1 = relu(D1 + hg)     (hg: the geometric part, FP16, row-major [N][64])
 //   GEMM2  D2 = h1 W2^T,   out = w3 . relu(D2)
 // Activations are split into BF16 hi + lo parts (x = hi + lo to ~2^-16 relative), each multiplied
 // by the exact BF16 weights, so the products carry FP32-like accuracy. GEMM2's A fragments are
@@ -397,7 +405,7 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b
 }
 
 __global__ void __launch_bounds__(CW * 32) correct_k(const int32_t* __restrict__ nbr, const float* __restrict__ r,
-                                                    const float* __restrict__ hg, const float* __restrict__ diag,
+                                                    const __half* __restrict__ hg, const float* __restrict__ diag,
                                                     const uint16_t* __restrict__ lw, int n, int64_t N, float* e) {
     extern __shared__ __align__(16) uint16_t lsm[];
     const int K1 = k1_of(n), S1 = K1 + 8;
@@ -475,8 +483,8 @@ __global__ void __launch_bounds__(CW * 32) correct_k(const int32_t* __restrict__
         for (int t = 0; t < 8; ++t) {
             const int c = 8 * t + 2 * tg;
             float2 ga = make_float2(0.0f, 0.0f), gb = make_float2(0.0f, 0.0f);
-            if (ra < N) ga = __ldg(reinterpret_cast<const float2*>(hg + ra * HID + c));
-            if (rb < N) gb = __ldg(reinterpret_cast<const float2*>(hg + rb * HID + c));
+            if (ra < N) ga = __half22float2(__ldg(reinterpret_cast<const __half2*>(hg + ra * HID + c)));
+            if (rb < N) gb = __half22float2(__ldg(reinterpret_cast<const __half2*>(hg + rb * HID + c)));
             const float h0 = fmaxf(d1[t][0] + ga.x, 0.0f), h1v = fmaxf(d1[t][1] + ga.y, 0.0f);
             const float h2 = fmaxf(d1[t][2] + gb.x, 0.0f), h3 = fmaxf(d1[t][3] + gb.y, 0.0f);
             const int kb = t >> 1, half = (t & 1) * 2;   // k-step and register pair of the A fragment
@@ -674,16 +682,22 @@ static double learned_objective(mgm_hierarchy* H, mgm_mlp* M, const double* r, f
     CK_LAUNCH();
     gradients(feat.get(), gout.get(), din, N, M->W.get(), h1.get(), h2.get(), G.get(), s);
     if (grad_out) CK(cudaMemcpyAsync(grad_out, G.get(), sizeof(float) * cnt, cudaMemcpyDeviceToDevice, s));
-    if (update) {
+    Temp<int> bad(1, s);
+    CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    nonfinite_k<<<grid_for(cnt, 256), 256, 0, s>>>(G.get(), cnt, bad.get());
+    CK_LAUNCH();
+    double hs[2];
+    to_host(hs, sums.get(), 2, s);
+    const int nonfinite = read1(bad.get(), s);
+    const double J = hs[1] > 0.0 ? hs[0] / hs[1] : 0.0;
+    if (update && std::isfinite(J) && hs[1] > 0.0 && !nonfinite) {  // a sample that overflowed FP32 is skipped
         M->step += 1;
         const float bc1 = (float)(1.0 - std::pow(0.9, M->step)), bc2 = (float)(1.0 - std::pow(0.999, M->step));
         adam_k<<<grid_for(cnt, 256), 256, 0, s>>>(M->W.get(), G.get(), M->m.get(), M->v.get(), cnt, lr, 0.9f, 0.999f, 1e-8f,
                                                   bc1, bc2);
         CK_LAUNCH();
     }
-    double hs[2];
-    to_host(hs, sums.get(), 2, s);
-    return hs[1] > 0.0 ? hs[0] / hs[1] : 0.0;
+    return J;
 }
 
 double learned_loss(mgm_hierarchy* H, const mgm_mlp* M, const double* r, float* grad, cudaStream_t s) {
@@ -710,7 +724,8 @@ void learned_enable(mgm_hierarchy* H, const mgm_mlp* M, cudaStream_t s) {
     const int tot = n * HID + HID * HID + HID;
     pack_k<<<grid_for(tot, 256), 256, 0, s>>>(M->W.get(), n, H->lw.get());
     CK_LAUNCH();
-    hg_k<<<grid_for(N, 128), 128, sizeof(float) * 3 * n * HID, s>>>(H->lgeo.get(), n, N, M->W.get(), H->lhg.get());
+    hg_k<<<grid_for(N, 128), 128, sizeof(float) * 3 * n * HID, s>>>(H->lgeo.get(), n, N, M->W.get(),
+                                                                     reinterpret_cast<__half*>(H->lhg.get()));
     CK_LAUNCH();
     CK(cudaStreamSynchronize(s));
     H->learned = true;
@@ -730,7 +745,8 @@ void learned_correct(mgm_hierarchy* H, cudaStream_t s) {
     }
     const int64_t tiles = (H->N + 15) / 16;
     const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (tiles + CW - 1) / CW));
-    correct_k<<<nb, CW * 32, correct_smem(H->ln), s>>>(H->lnbr.get(), L0.s32.get(), H->lhg.get(), L0.diag32.get(),
+    correct_k<<<nb, CW * 32, correct_smem(H->ln), s>>>(H->lnbr.get(), L0.s32.get(), reinterpret_cast<const __half*>(H->lhg.get()),
+                                                     L0.diag32.get(),
                                                      H->lw.get(), H->ln, H->N, L0.e32.get());
     CK_LAUNCH();
 }

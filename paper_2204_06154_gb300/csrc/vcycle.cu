@@ -25,34 +25,6 @@ constexpr int VBLOCK = 256;   // threads per block -> 32 rows per block
 template <class T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
-// sum_{p in [beg, end)} v_p x[c_p] over one row, G lanes cooperating; beg, end multiples of 4
-__device__ __forceinline__ float row_sum(const int32_t* __restrict__ sc, const float* __restrict__ sv, int32_t beg,
-                                         int32_t end, const float* x, int gl) {
-    float acc = 0.0f;
-    for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {
-        int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
-        float4 v = __ldg(reinterpret_cast<const float4*>(sv + p));
-        acc = fmaf(v.x, x[c.x], acc);
-        acc = fmaf(v.y, x[c.y], acc);
-        acc = fmaf(v.z, x[c.z], acc);
-        acc = fmaf(v.w, x[c.w], acc);
-    }
-    return acc;
-}
-__device__ __forceinline__ double row_sum(const int32_t* __restrict__ sc, const double* __restrict__ sv, int32_t beg,
-                                          int32_t end, const double* x, int gl) {
-    double acc = 0.0;
-    for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {
-        int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
-        double2 v0 = __ldg(reinterpret_cast<const double2*>(sv + p));
-        double2 v1 = __ldg(reinterpret_cast<const double2*>(sv + p + 2));
-        acc = fma(v0.x, x[c.x], acc);
-        acc = fma(v0.y, x[c.y], acc);
-        acc = fma(v1.x, x[c.z], acc);
-        acc = fma(v1.y, x[c.w], acc);
-    }
-    return acc;
-}
 // same sums with L2-coherent loads of x (ld.global.cg): inside one persistent launch, x is written
 // by other blocks between grid barriers, so it must not be served from a stale L1 line
 __device__ __forceinline__ float row_sum_cg(const int32_t* __restrict__ sc, const float* __restrict__ sv, int32_t beg,
@@ -89,6 +61,89 @@ __device__ __forceinline__ T group_reduce(T v) {
     return v;
 }
 
+// Programmatic dependent launch: every kernel of the cycle lets its successor be scheduled as soon
+// as all of its own blocks are running (launch_dependents), and waits for its predecessor's
+// completion and memory (wait) before it reads anything the predecessor writes. Work that only
+// reads the level's static operators (row structure, columns, values) is issued before the wait,
+// so it overlaps the predecessor's tail. Without a programmatic predecessor, wait returns at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Streamed operator data (columns, values, row structure) is loaded with an L2 evict-first policy,
+// so that it does not push the gathered vector out of L2 (the matrix of a level is far larger than
+// L2; the vector is a few MB and is gathered ~50 times per pass).
+__device__ __forceinline__ uint64_t stream_policy() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int4 ld_stream(const int4* q, uint64_t pol) {
+    int4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(q), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4* q, uint64_t pol) {
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(q), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2* q, uint64_t pol) {
+    double2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(q), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* q, uint64_t pol) {
+    int32_t v;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(q), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ float ld_stream_t(const float* q, uint64_t pol) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(q), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_stream_t(const double* q, uint64_t pol) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(q), "l"(pol));
+    return v;
+}
+
+template <class T>
+struct Quad;
+template <>
+struct Quad<float> {
+    float x, y, z, w;
+    __device__ __forceinline__ static Quad load(const float* p) {
+        float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        return {v.x, v.y, v.z, v.w};
+    }
+    __device__ __forceinline__ static Quad load(const float* p, uint64_t pol) {
+        float4 v = ld_stream(reinterpret_cast<const float4*>(p), pol);
+        return {v.x, v.y, v.z, v.w};
+    }
+};
+template <>
+struct Quad<double> {
+    double x, y, z, w;
+    __device__ __forceinline__ static Quad load(const double* p) {
+        double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+        return {a.x, a.y, b.x, b.y};
+    }
+    __device__ __forceinline__ static Quad load(const double* p, uint64_t pol) {
+        double2 a = ld_stream(reinterpret_cast<const double2*>(p), pol);
+        double2 b = ld_stream(reinterpret_cast<const double2*>(p + 2), pol);
+        return {a.x, a.y, b.x, b.y};
+    }
+};
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 // MODE 0: e = (b - lower e) dinv   (first sweep from zero)
 // MODE 1: e = (b - offdiag e) dinv (full sweep)
 // MODE 2: s = -upper e             (residual after a first sweep from zero)
@@ -98,17 +153,47 @@ __global__ void __launch_bounds__(VBLOCK) row_kernel(const int32_t* __restrict__
                                                      const int32_t* __restrict__ sc, const T* __restrict__ sv,
                                                      const T* __restrict__ dv, const T* __restrict__ b, T* e, T* s,
                                                      int32_t r0, int32_t r1) {
+    pdl_trigger();
+    const uint64_t pol = stream_policy();
     const int t = blockIdx.x * VBLOCK + threadIdx.x;
     const int32_t row = r0 + t / G;
     const int gl = t & (G - 1);
     const bool act = row < r1;
-    T acc = T(0);
+    int32_t beg = 0, end = 0;
     if (act) {
-        int32_t beg, end;
-        if (MODE == 0) { beg = lo[row]; end = mid[row]; }
-        else if (MODE == 2) { beg = mid[row]; end = lo[row + 1]; }
-        else { beg = lo[row]; end = lo[row + 1]; }
-        acc = row_sum(sc, sv, beg, end, e, gl);
+        if (MODE == 0) { beg = ld_stream(lo + row, pol); end = ld_stream(mid + row, pol); }
+        else if (MODE == 2) { beg = ld_stream(mid + row, pol); end = ld_stream(lo + row + 1, pol); }
+        else { beg = ld_stream(lo + row, pol); end = ld_stream(lo + row + 1, pol); }
+    }
+    // the lane's first two quads of columns and values (static data) before the wait
+    const int32_t p0 = beg + 4 * gl, p1 = p0 + 4 * G;
+    const bool h0 = p0 < end, h1 = p1 < end;
+    int4 c0 = make_int4(0, 0, 0, 0), c1 = make_int4(0, 0, 0, 0);
+    Quad<T> v0{}, v1{};
+    if (h0) { c0 = ld_stream(reinterpret_cast<const int4*>(sc + p0), pol); v0 = Quad<T>::load(sv + p0, pol); }
+    if (h1) { c1 = ld_stream(reinterpret_cast<const int4*>(sc + p1), pol); v1 = Quad<T>::load(sv + p1, pol); }
+    pdl_wait();
+    // the products in storage order: quad p0, quad p1, then the rest
+    T acc = T(0);
+    if (h0) {
+        acc = fma_t(v0.x, e[c0.x], acc);
+        acc = fma_t(v0.y, e[c0.y], acc);
+        acc = fma_t(v0.z, e[c0.z], acc);
+        acc = fma_t(v0.w, e[c0.w], acc);
+    }
+    if (h1) {
+        acc = fma_t(v1.x, e[c1.x], acc);
+        acc = fma_t(v1.y, e[c1.y], acc);
+        acc = fma_t(v1.z, e[c1.z], acc);
+        acc = fma_t(v1.w, e[c1.w], acc);
+    }
+    for (int32_t p = p1 + 4 * G; p < end; p += 4 * G) {
+        const int4 c = ld_stream(reinterpret_cast<const int4*>(sc + p), pol);
+        const Quad<T> v = Quad<T>::load(sv + p, pol);
+        acc = fma_t(v.x, e[c.x], acc);
+        acc = fma_t(v.y, e[c.y], acc);
+        acc = fma_t(v.z, e[c.z], acc);
+        acc = fma_t(v.w, e[c.w], acc);
     }
     acc = group_reduce(acc);
     if (act && gl == 0) {
@@ -206,27 +291,7 @@ __device__ __forceinline__ void st_release_i32(int* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <class T>
-struct Quad;
-template <>
-struct Quad<float> {
-    float x, y, z, w;
-    __device__ __forceinline__ static Quad load(const float* p) {
-        float4 v = __ldg(reinterpret_cast<const float4*>(p));
-        return {v.x, v.y, v.z, v.w};
-    }
-};
-template <>
-struct Quad<double> {
-    double x, y, z, w;
-    __device__ __forceinline__ static Quad load(const double* p) {
-        double2 a = __ldg(reinterpret_cast<const double2*>(p));
-        double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
-        return {a.x, a.y, b.x, b.y};
-    }
-};
-__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 
 template <int MODE, class T>
 __global__ void __launch_bounds__(DS_THREADS) dsweep_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ mid,
@@ -264,7 +329,7 @@ __global__ void __launch_bounds__(DS_THREADS) dsweep_k(const int32_t* __restrict
             __nanosleep(64);
         }
         T acc = T(0);
-        for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {  // the order of row_sum
+        for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {  // the order of row_kernel
             const int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
             const Quad<T> v = Quad<T>::load(sv + p);
             if (p < m) {
@@ -296,25 +361,33 @@ __global__ void barrier_timeout_probe_k(unsigned* bar, int* err, unsigned long l
 template <class T>
 __global__ void restrict_k(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
                            const T* __restrict__ s, T* bn, int64_t nc) {
+    pdl_trigger();
+    pdl_wait();
+    const uint64_t pol = stream_policy();
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
     T acc = T(0);
-    for (int32_t q = rp[c]; q < rp[c + 1]; ++q) acc += v[q] * s[ci[q]];
+    for (int32_t q = rp[c]; q < rp[c + 1]; ++q) acc += ld_stream_t(v + q, pol) * s[ld_stream(ci + q, pol)];
     bn[c] = acc;
 }
 
 template <class T>
 __global__ void interp_k(const int32_t* __restrict__ pc, const T* __restrict__ pv, int pw, const T* __restrict__ en, T* e,
                          int64_t n) {
+    pdl_trigger();
+    pdl_wait();
+    const uint64_t pol = stream_policy();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T acc = e[i];
-    for (int t = 0; t < pw; ++t) acc += pv[i * pw + t] * en[pc[i * pw + t]];
+    for (int t = 0; t < pw; ++t) acc += ld_stream_t(pv + i * pw + t, pol) * en[ld_stream(pc + i * pw + t, pol)];
     e[i] = acc;
 }
 
 template <class T>
 __global__ void coarse_k(const double* __restrict__ Ainv, const T* __restrict__ b, T* e, int64_t n) {
+    pdl_trigger();
+    pdl_wait();
     int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (row >= n) return;
@@ -368,14 +441,31 @@ template <> struct LV<double> {
     static double* eold(Level& L) { return L.eold64.get(); }
 };
 
+// launch with programmatic stream serialization (see pdl_trigger / pdl_wait)
+template <class... KArgs, class... Args>
+static void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, kern, args...));
+    CK_LAUNCH();
+}
+
 template <int MODE, class T>
 static void launch_rows(Level& L, int32_t r0, int32_t r1, cudaStream_t s) {
     if (r1 <= r0) return;
     const int64_t threads = (int64_t)(r1 - r0) * G;
     const T* dv = (MODE == 3) ? LV<T>::diag(L) : LV<T>::dinv(L);
-    row_kernel<MODE, T><<<grid_for(threads, VBLOCK), VBLOCK, 0, s>>>(L.lo.get(), L.mid.get(), L.sc.get(), LV<T>::sv(L), dv,
-                                                                    LV<T>::b(L), LV<T>::e(L), LV<T>::s(L), r0, r1);
-    CK_LAUNCH();
+    launch_pdl(row_kernel<MODE, T>, grid_for(threads, VBLOCK), VBLOCK, s, (const int32_t*)L.lo.get(),
+               (const int32_t*)L.mid.get(), (const int32_t*)L.sc.get(), LV<T>::sv(L), dv, (const T*)LV<T>::b(L),
+               LV<T>::e(L), LV<T>::s(L), r0, r1);
 }
 
 // blocks for a persistent sweep: enough to cover the largest colour in one pass, at most what can
@@ -486,19 +576,19 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
             CK(cudaMemsetAsync(LV<T>::e(L), 0, sizeof(T) * L.n, s));
             rsrc = LV<T>::b(L);
         }
-        restrict_k<T><<<grid_for(C.n, 256), 256, 0, s>>>(L.r_rp.get(), L.r_ci.get(), LV<T>::rv(L), rsrc, LV<T>::b(C), C.n);
-        CK_LAUNCH();
+        launch_pdl(restrict_k<T>, grid_for(C.n, 256), 256, s, (const int32_t*)L.r_rp.get(), (const int32_t*)L.r_ci.get(),
+                   LV<T>::rv(L), rsrc, LV<T>::b(C), (int64_t)C.n);
     }
-    {   // coarsest defect
+    {  // coarsest defect
         Level& C = H->lv[p - 1];
-        coarse_k<T><<<grid_for(C.n * 32, 256), 256, 0, s>>>(H->Ainv.get(), LV<T>::b(C), LV<T>::e(C), C.n);
-        CK_LAUNCH();
+        launch_pdl(coarse_k<T>, grid_for(C.n * 32, 256), 256, s, (const double*)H->Ainv.get(), (const T*)LV<T>::b(C),
+                   LV<T>::e(C), (int64_t)C.n);
     }
     for (int j = p - 2; j >= 0; --j) {  // interpolate / correct, post-smooth
         Level& L = H->lv[j];
         Level& C = H->lv[j + 1];
-        interp_k<T><<<grid_for(L.n, 256), 256, 0, s>>>(L.pc.get(), LV<T>::pv(L), L.pw, LV<T>::e(C), LV<T>::e(L), L.n);
-        CK_LAUNCH();
+        launch_pdl(interp_k<T>, grid_for(L.n, 256), 256, s, (const int32_t*)L.pc.get(), LV<T>::pv(L), L.pw,
+                   (const T*)LV<T>::e(C), LV<T>::e(L), (int64_t)L.n);
         for (int t = 0; t < H->nu2; ++t) sweep_any<T>(H, L, false, s);
     }
 }
@@ -678,8 +768,8 @@ void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStrea
         CK(cudaEventSynchronize(e1));
         CK(cudaEventElapsedTime(&ms, e0, e1));
         out->learned_ms = ms / reps;
-        // per row: n stencil indices, 64 first-layer geometric terms, diagonal, e read and written
-        out->learned_bytes = H->N * (4 * (int64_t)H->ln + 64 * 4 + 4 + 8);
+        // per row: n stencil indices, 64 FP16 first-layer geometric terms, diagonal, e read and written
+        out->learned_bytes = H->N * (4 * (int64_t)H->ln + 64 * 2 + 4 + 8);
     }
     for (int t = 0; t < 2; ++t) vcycle_plain(H, s);
     CK(cudaEventRecord(e0, s));

@@ -114,8 +114,11 @@ def fibonacci_sphere(N: int, jitter: float = 0.1, seed: int = 2):
 
 
 def _torus_shape(N: int, R: float, r: float):
-    """Factor N = nu * nv (nu around the central circle, nv around the tube) with nu/nv closest
-    (in log scale) to R/r."""
+    """Grid shape nu x nv (nu around the central circle, nv around the tube) with nu/nv close to
+    R/r: the exact factorisation N = nu * nv whose log-ratio is nearest to log(R/r), if it is within
+    0.35 of it (2048 x 512 at N = 2^20); otherwise nv = round(sqrt(N r / R)), nu = N // nv, and
+    nu * nv <= N points (an exact but lopsided factorisation, such as 7211 x 15, would leave a few
+    points around the tube)."""
     best = None
     target = math.log(R / r)
     for nv in range(3, int(math.isqrt(N)) + 1):
@@ -125,7 +128,7 @@ def _torus_shape(N: int, R: float, r: float):
         s = abs(math.log(nu / nv) - target)
         if best is None or s < best[0]:
             best = (s, nu, nv)
-    if best is None:
+    if best is None or best[0] > 0.35:
         nv = max(3, int(round(math.sqrt(N * r / R))))
         nu = max(3, N // nv)
         return nu, nv

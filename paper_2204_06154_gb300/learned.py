@@ -42,8 +42,12 @@ class Problem:
         out = []
         for r0 in rhs:
             r = torch.tensor(r0, dtype=torch.float64, device=self.xyz.device)
+            n0 = float(r.norm())
             for _ in range(cycles):
                 r = self.H.learned_cycle_residual(r)
+                nk = float(r.norm())
+                if not np.isfinite(nk) or nk > 1e3 * n0:  # a cycle that diverges here gives no samples
+                    break
                 out.append(r)
         return out
 

@@ -17,7 +17,8 @@ _lib = None
 
 MGM_RBF_FD, MGM_GFD = 0, 1
 MGM_F64, MGM_F32 = 0, 1
-MGM_KRYLOV_FGMRES, MGM_KRYLOV_NONE = 0, 1
+MGM_KRYLOV_FGMRES, MGM_KRYLOV_NONE, MGM_KRYLOV_BICGSTAB = 0, 1, 2
+_KRYLOV = {"fgmres": MGM_KRYLOV_FGMRES, "none": MGM_KRYLOV_NONE, "bicgstab": MGM_KRYLOV_BICGSTAB}
 
 STATUS = {0: "MGM_OK", 1: "MGM_ERR_INVALID_ARG", 2: "MGM_ERR_SINGULAR_STENCIL", 3: "MGM_ERR_NOT_CONVERGED",
           4: "MGM_ERR_BREAKDOWN", 5: "MGM_ERR_TIMEOUT", 6: "MGM_ERR_CUDA", 7: "MGM_ERR_OOM", 8: "MGM_ERR_UNSUPPORTED"}
@@ -340,7 +341,7 @@ class Hierarchy:
     def solve(self, f, u0=None, krylov="fgmres", restart=50, maxit=200, tol=1e-10, raise_on_nonconv=False):
         f = _dev(f, torch.float64, "f")
         u = torch.zeros_like(f) if u0 is None else _dev(u0, torch.float64, "u0").clone()
-        sp = SolveParams(MGM_KRYLOV_FGMRES if krylov == "fgmres" else MGM_KRYLOV_NONE, restart, maxit, tol)
+        sp = SolveParams(_KRYLOV[krylov], restart, maxit, tol)
         hist = (C.c_double * (maxit + 2))()
         info = SolveInfo(0, 0.0, hist, maxit + 2, 0.0)
         st = lib().mgm_solve(self._h, _p(f), _p(u), C.byref(sp), C.byref(info), _stream())

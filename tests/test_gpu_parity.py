@@ -249,6 +249,44 @@ def test_solve_matches_oracle(M, oracle, ico5, hier, prec):
     assert res <= 1.5e-10
 
 
+def test_vcycle_60k_matches_oracle(M, oracle):
+    """A five-level hierarchy built from GPU stencils of a 60k-point cloud: the cycle matches the
+    oracle's on the same operator (FP64 1e-12, FP32 1e-4)."""
+    import scipy.sparse as sp
+    x, nrm = I.fibonacci_sphere(60000, 0.1, 12)
+    _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 30, "rbf", 1, 2, 1.0, keep_weights=False)
+    L = sp.csr_matrix((H(v), H(ci), H(rp)), shape=(60000, 60000))
+    Ho = oracle.setup(x, L, 250, seed=0)
+    r = np.random.default_rng(13).standard_normal(60000)
+    zo = oracle.vcycle(Ho, r)
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-4)):
+        Hg = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec)
+        assert Hg.stats()["n"] == [l.shape[0] for l in Ho.L]
+        z = H(Hg.vcycle(T(r)))
+        assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo), prec
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_bicgstab_matches_oracle(M, oracle, ico5, hier, prec):
+    """Right-preconditioned MGM BiCGSTAB (Sec. 4.6): the solution matches the oracle's, and the
+    V-cycle applications (two per step, the count of Sec. 5.2) match the oracle's within 2."""
+    x, nrm, idx, w, L = ico5
+    Hg, Ho = hier
+    f = np.random.default_rng(31).standard_normal(x.shape[0])
+    uo, appo, _ = oracle.bicgstab(L, Ho, f, tol=1e-12)
+    u, info = Hg[prec].solve(T(f), krylov="bicgstab", tol=1e-10, maxit=200)
+    assert info["converged"] and info["rel_res"] <= 1e-10
+    assert np.linalg.norm(H(u) - uo) <= 1e-8 * np.linalg.norm(uo)
+    _, app10, _ = oracle.bicgstab(L, Ho, f, tol=1e-10)
+    assert abs(info["iters"] - app10) <= 2, (info["iters"], app10)
+    assert np.linalg.norm(f - L @ H(u)) / np.linalg.norm(f) <= 1.5e-10
+    # an exact initial guess needs no V-cycle; a cap of 3 applications reports non-convergence
+    u2, info2 = Hg[prec].solve(T(f), u0=T(uo), krylov="bicgstab", tol=1e-9)
+    assert info2["converged"] and info2["iters"] == 0
+    u3, info3 = Hg[prec].solve(T(f), krylov="bicgstab", tol=1e-10, maxit=3)
+    assert not info3["converged"] and info3["iters"] == 3
+
+
 def test_standalone_mgm_and_nonconvergence(M, oracle, ico5, hier):
     x, nrm, idx, w, L = ico5
     Hg, Ho = hier
