@@ -65,6 +65,11 @@ def lib():
         L.or_fgmres.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_int, C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_int, C.c_double,
                                 C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
+        L.or_vcycle_bordered.argtypes = [C.c_void_p, C.c_int, C.c_void_p, f64p, i32p, C.c_void_p, C.c_int, C.c_int,
+                                         f64p, C.c_double, f64p, C.POINTER(C.c_double)]
+        L.or_fgmres_bordered.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, f64p, i32p, C.c_void_p,
+                                         C.c_int, C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_int, C.c_double,
+                                         C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
         L.or_bicgstab.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_int, C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_double,
                                   C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
@@ -272,6 +277,9 @@ class Hierarchy:
     ncolors: list = field(default_factory=list)
     lu: np.ndarray = None
     piv: np.ndarray = None
+    cvec: list = field(default_factory=list)   # bordered (Poisson) hierarchies: border vector per level
+    blu: np.ndarray = None                     # LU factors of the bordered coarsest matrix
+    bpiv: np.ndarray = None
     smoother: str = "mc"
     nu1: int = 1
     nu2: int = 1
@@ -308,7 +316,7 @@ class Hierarchy:
         return lv
 
 
-def setup(xyz, L1, n_min, m=3, seed=0, smoother="mc", nu1=1, nu2=1, wse_mode=1):
+def setup(xyz, L1, n_min, m=3, seed=0, smoother="mc", nu1=1, nu2=1, wse_mode=1, bordered=False):
     """MGM preprocessing (Alg. 2), in the paper's order:
     RCM of L_1 and X_1; the number of levels p; for each level: WSE coarsening to
     floor(N_1/4^j) points, interpolation, restriction = transpose, Galerkin product (operand
@@ -341,6 +349,17 @@ def setup(xyz, L1, n_min, m=3, seed=0, smoother="mc", nu1=1, nu2=1, wse_mode=1):
         c, nc = color(H.L[j], seed)
         H.colors.append(c); H.ncolors.append(nc)
     H.lu, H.piv = lu_factor(H.L[-1])
+    if bordered:
+        # eq. (gco_saddle_point): c_0 = 1, c_{j+1} = R_j c_j; coarsest [L_p c_p; c_p^T 0]
+        H.cvec.append(np.ones(N1))
+        for j in range(p - 1):
+            H.cvec.append(np.ascontiguousarray(H.R[j] @ H.cvec[j]))
+        np_ = H.L[-1].shape[0]
+        B = np.zeros((np_ + 1, np_ + 1))
+        B[:np_, :np_] = H.L[-1].toarray()
+        B[:np_, np_] = H.cvec[-1]
+        B[np_, :np_] = H.cvec[-1]
+        H.blu, H.bpiv = lu_factor(B)
     return H
 
 
@@ -377,6 +396,42 @@ def fgmres(A, H, f, x0=None, restart=50, maxit=200, tol=1e-10, precond=True, his
     if st not in (0, 3):
         _check("fgmres", st)
     out = (x, it.value, rel.value)
+    return out + (hbuf[: it.value + 1],) if hist else out
+
+
+def _cvec_ptrs(H):
+    arr = (C.c_void_p * H.p)(*[c.ctypes.data for c in H.cvec])
+    return arr
+
+
+def vcycle_bordered(H, r, s):
+    """One bordered V-cycle (Sec. 4.4) from a zero guess: (r, s) -> (e, mu), r in caller order."""
+    r = _c(r, np.float64)
+    e = np.zeros_like(r); mu = C.c_double(0.0)
+    lv = H._levels(); cv = _cvec_ptrs(H)
+    _check("vcycle_bordered", lib().or_vcycle_bordered(C.addressof(lv), H.p, C.addressof(cv), H.blu, H.bpiv,
+                                                       H.perm[0].ctypes.data, H.nu1, H.nu2, r, float(s), e,
+                                                       C.byref(mu)))
+    return e, mu.value
+
+
+def fgmres_bordered(A, H, f, tol=1e-10, restart=50, maxit=200, precond=True, hist=False):
+    """FGMRES on the bordered system [A 1; 1^T 0][u; lambda] = [f; 0] (eq. (saddle_point)) with the
+    bordered MGM V-cycle as right preconditioner. Returns (u, lambda, iterations, true relative
+    residual of the bordered system[, history])."""
+    rp, ci, v = _csr(A)
+    n = A.shape[0]
+    fb = np.zeros(n + 1); fb[:n] = _c(f, np.float64)
+    x = np.zeros(n + 1)
+    it = C.c_int(0); rel = C.c_double(0.0)
+    hbuf = np.zeros(maxit + 1)
+    lv = H._levels(); cv = _cvec_ptrs(H)
+    st = lib().or_fgmres_bordered(n, rp, ci, v, C.addressof(lv), H.p, C.addressof(cv), H.blu, H.bpiv,
+                                  H.perm[0].ctypes.data, H.nu1, H.nu2, int(precond), fb, x, restart, maxit, tol,
+                                  C.byref(it), C.byref(rel), hbuf.ctypes.data)
+    if st not in (0, 3):
+        _check("fgmres_bordered", st)
+    out = (x[:n].copy(), float(x[n]), it.value, rel.value)
     return out + (hbuf[: it.value + 1],) if hist else out
 
 

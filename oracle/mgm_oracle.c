@@ -882,10 +882,13 @@ static double dot(int64_t n, const double* a, const double* b) { double s = 0.0;
  * The operator is the level-1 CSR in the caller's ordering (A_*); precond = 0 runs plain GMRES.
  * hist (length maxit + 1, may be NULL) receives the estimated relative residual per iteration.
  * =========================================================================================== */
-int or_fgmres(int64_t n, const int32_t* arp, const int32_t* aci, const double* av,
-              const or_level* lv, int p, const double* lu, const int32_t* piv, const int32_t* perm1, int nu1, int nu2,
-              int precond, const double* f, double* x, int restart, int maxit, double tol,
-              int* iters_out, double* relres_out, double* hist) {
+typedef void (*or_apply_fn)(void* ctx, const double* x, double* y);
+typedef void (*or_precond_fn)(void* ctx, const double* v, double* z);
+
+/* FGMRES body shared by the plain and the bordered systems (precond NULL: z = v) */
+static int fgmres_core(int64_t n, or_apply_fn apply, void* actx, or_precond_fn precond, void* pctx,
+                       const double* f, double* x, int restart, int maxit, double tol,
+                       int* iters_out, double* relres_out, double* hist) {
     if (restart < 1) return OR_ERR_ARG;
     int m = restart;
     double* V = (double*)malloc(sizeof(double) * n * (m + 1));
@@ -901,7 +904,7 @@ int or_fgmres(int64_t n, const int32_t* arp, const int32_t* aci, const double* a
     int it = 0, status = OR_ERR_NOTCONV;
     double rel = 0.0;
     for (;;) {
-        csr_apply(n, arp, aci, av, x, w);
+        apply(actx, x, w);
         for (int64_t i = 0; i < n; ++i) V[i] = f[i] - w[i];
         double beta = nrm2(n, V);
         rel = beta / fn;
@@ -915,9 +918,9 @@ int or_fgmres(int64_t n, const int32_t* arp, const int32_t* aci, const double* a
         for (; k < m && it < maxit; ++k) {
             double* vk = V + (int64_t)k * n;
             double* zk = Z + (int64_t)k * n;
-            if (precond) { for (int64_t i = 0; i < n; ++i) zk[i] = 0.0; or_vcycle(lv, p, lu, piv, perm1, nu1, nu2, vk, zk); }
+            if (precond) precond(pctx, vk, zk);
             else for (int64_t i = 0; i < n; ++i) zk[i] = vk[i];
-            csr_apply(n, arp, aci, av, zk, w);
+            apply(actx, zk, w);
             for (int i = 0; i <= k; ++i) {
                 double* vi = V + (int64_t)i * n;
                 double h = 0.0;
@@ -955,6 +958,108 @@ int or_fgmres(int64_t n, const int32_t* arp, const int32_t* aci, const double* a
     *iters_out = it; *relres_out = rel;
     free(V); free(Z); free(H); free(cs); free(sn); free(g); free(w); free(y);
     return status;
+}
+
+typedef struct { int64_t n; const int32_t *rp, *ci; const double* v; } or_csr_ctx;
+static void csr_apply_cb(void* c, const double* x, double* y) {
+    const or_csr_ctx* a = (const or_csr_ctx*)c;
+    csr_apply(a->n, a->rp, a->ci, a->v, x, y);
+}
+typedef struct { const or_level* lv; int p; const double* lu; const int32_t* piv; const int32_t* perm1; int nu1, nu2; int64_t n; } or_mgm_ctx;
+static void vcycle_cb(void* c, const double* v, double* z) {
+    const or_mgm_ctx* m = (const or_mgm_ctx*)c;
+    for (int64_t i = 0; i < m->n; ++i) z[i] = 0.0;
+    or_vcycle(m->lv, m->p, m->lu, m->piv, m->perm1, m->nu1, m->nu2, v, z);
+}
+
+int or_fgmres(int64_t n, const int32_t* arp, const int32_t* aci, const double* av,
+              const or_level* lv, int p, const double* lu, const int32_t* piv, const int32_t* perm1, int nu1, int nu2,
+              int precond, const double* f, double* x, int restart, int maxit, double tol,
+              int* iters_out, double* relres_out, double* hist) {
+    or_csr_ctx a = {n, arp, aci, av};
+    or_mgm_ctx m = {lv, p, lu, piv, perm1, nu1, nu2, n};
+    return fgmres_core(n, csr_apply_cb, &a, precond ? vcycle_cb : NULL, &m, f, x, restart, maxit, tol, iters_out, relres_out,
+                       hist);
+}
+
+/* ===========================================================================================
+ * Surface Poisson problem (L_h = D_h, singular) with the mean-zero constraint of Sec. 4.4:
+ * the bordered system of eq. (saddle_point), [L b^T; b 0][u; lambda] = [f; 0], b = (1, ..., 1).
+ * Coarse operators follow eq. (gco_saddle_point): the restriction and interpolation carry lambda
+ * unchanged, so on level j the border column is c_j = R_{j-1} c_{j-1} and the border row is
+ * b P_0 ... P_{j-1}, which is the same vector (R = P^T), with c_0 = b^T. Smoothing updates u only,
+ * u <- u + B^{-1}(r - L u - c lambda) (the smoother of Sec. 4.4), and the coarsest bordered system
+ * is solved directly with the LU factors of [L_p c_p; c_p^T 0].
+ * One bordered V-cycle from a zero guess: (r, s) -> (e, mu), with r in the caller's ordering and
+ * s the constraint component; cvec[j] holds c_j in level j's (RCM) ordering.
+ * =========================================================================================== */
+int or_vcycle_bordered(const or_level* lv, int p, const double* const* cvec, const double* blu, const int32_t* bpiv,
+                       const int32_t* perm1, int nu1, int nu2, const double* rin, double sin, double* eout,
+                       double* muout) {
+    if (p < 2) return OR_ERR_ARG;
+    int64_t n1 = lv[0].n;
+    double** e = (double**)calloc(p, sizeof(double*));
+    double** r = (double**)calloc(p, sizeof(double*));
+    double* sres = (double*)calloc(p, sizeof(double));
+    double* tmp = (double*)malloc(sizeof(double) * n1);
+    double* tmp2 = (double*)malloc(sizeof(double) * n1);
+    for (int j = 0; j < p; ++j) { e[j] = (double*)calloc(lv[j].n + 1, sizeof(double)); r[j] = (double*)calloc(lv[j].n + 1, sizeof(double)); }
+    for (int64_t i = 0; i < n1; ++i) { int64_t o = perm1 ? perm1[i] : i; r[0][i] = rin[o]; }
+    sres[0] = sin;
+    /* descent: mu_j = 0, so pre-smoothing sees r_j; residual r_j - L_j e_j; constraint s_j - c_j . e_j */
+    for (int j = 0; j < p - 1; ++j) {
+        for (int64_t i = 0; i < lv[j].n; ++i) e[j][i] = 0.0;
+        for (int t = 0; t < nu1; ++t) or_gs_sweep(&lv[j], r[j], e[j]);
+        residual(&lv[j], r[j], e[j], tmp);
+        csr_apply(lv[j + 1].n, lv[j].rrp, lv[j].rc, lv[j].rv, tmp, r[j + 1]);
+        sres[j + 1] = sres[j] - dot(lv[j].n, cvec[j], e[j]);
+    }
+    /* coarsest bordered solve: [e_p; mu] */
+    const int64_t np = lv[p - 1].n;
+    for (int64_t i = 0; i < np; ++i) e[p - 1][i] = r[p - 1][i];
+    e[p - 1][np] = sres[p - 1];
+    or_lu_solve(blu, np + 1, bpiv, e[p - 1]);
+    const double mu = e[p - 1][np];
+    /* ascent: e_j += P_j e_{j+1}; mu passes unchanged; post-smoothing on r_j - c_j mu */
+    for (int j = p - 2; j >= 0; --j) {
+        csr_apply(lv[j].n, lv[j].pp, lv[j].pc, lv[j].pv, e[j + 1], tmp);
+        for (int64_t i = 0; i < lv[j].n; ++i) e[j][i] = e[j][i] + tmp[i];
+        for (int64_t i = 0; i < lv[j].n; ++i) tmp2[i] = r[j][i] - cvec[j][i] * mu;
+        for (int t = 0; t < nu2; ++t) or_gs_sweep(&lv[j], tmp2, e[j]);
+    }
+    for (int64_t i = 0; i < n1; ++i) { int64_t o = perm1 ? perm1[i] : i; eout[o] = e[0][i]; }
+    *muout = mu;
+    for (int j = 0; j < p; ++j) { free(e[j]); free(r[j]); }
+    free(e); free(r); free(sres); free(tmp); free(tmp2);
+    return OR_OK;
+}
+
+typedef struct { int64_t n; const int32_t *rp, *ci; const double* v; } or_bord_ctx;
+/* y = [L u + lambda 1; 1 . u] on an (n+1)-vector */
+static void bordered_apply_cb(void* c, const double* x, double* y) {
+    const or_bord_ctx* a = (const or_bord_ctx*)c;
+    csr_apply(a->n, a->rp, a->ci, a->v, x, y);
+    double sum = 0.0;
+    for (int64_t i = 0; i < a->n; ++i) { y[i] = y[i] + x[a->n]; sum = sum + x[i]; }
+    y[a->n] = sum;
+}
+typedef struct { const or_level* lv; int p; const double* const* cvec; const double* blu; const int32_t* bpiv;
+                 const int32_t* perm1; int nu1, nu2; int64_t n; } or_bmgm_ctx;
+static void bordered_vcycle_cb(void* c, const double* v, double* z) {
+    const or_bmgm_ctx* m = (const or_bmgm_ctx*)c;
+    or_vcycle_bordered(m->lv, m->p, m->cvec, m->blu, m->bpiv, m->perm1, m->nu1, m->nu2, v, v[m->n], z, z + m->n);
+}
+
+/* FGMRES (as or_fgmres) on the bordered system of size n + 1: f and x have n + 1 entries (the
+ * last is the constraint right-hand side / the multiplier lambda). */
+int or_fgmres_bordered(int64_t n, const int32_t* arp, const int32_t* aci, const double* av, const or_level* lv, int p,
+                       const double* const* cvec, const double* blu, const int32_t* bpiv, const int32_t* perm1, int nu1,
+                       int nu2, int precond, const double* f, double* x, int restart, int maxit, double tol,
+                       int* iters_out, double* relres_out, double* hist) {
+    or_bord_ctx a = {n, arp, aci, av};
+    or_bmgm_ctx m = {lv, p, cvec, blu, bpiv, perm1, nu1, nu2, n};
+    return fgmres_core(n + 1, bordered_apply_cb, &a, precond ? bordered_vcycle_cb : NULL, &m, f, x, restart, maxit, tol,
+                       iters_out, relres_out, hist);
 }
 
 /* Right-preconditioned BiCGSTAB (Sec. 4.6; the method of van der Vorst as given in Saad's book)
