@@ -65,6 +65,11 @@ def parse():
     ap.add_argument("--learned-eval-size", type=int, default=1 << 20, help="points of the held-out bumpy torus")
     ap.add_argument("--single", action="store_true",
                     help="one pass of the path on the sphere only (a small driver for profilers); prints its phases")
+    ap.add_argument("--vcycles", type=int, default=0,
+                    help="profiling driver: build the sphere problem of --size, then run this many V-cycles "
+                         "(FP32 unless --fp64-cycle; --learned-n attaches an untrained correction of that stencil size)")
+    ap.add_argument("--fp64-cycle", action="store_true")
+    ap.add_argument("--learned-n", type=int, default=0)
     return ap.parse_args()
 
 
@@ -407,6 +412,24 @@ def main():
                           "data": "synthetic", "config": config(a), "cpu_baseline": cb,
                           "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
               flush=True)
+        return
+    if a.vcycles > 0:
+        import torch
+        from paper_2204_06154_gb300 import mgm as M
+        from paper_2204_06154_gb300 import inputs as I
+        x, nrm = I.fibonacci_sphere(a.size, jitter=0.1, seed=2)
+        X = torch.from_numpy(x).cuda(); Nr = torch.from_numpy(nrm).cuda()
+        n, ell = (a.learned_n, 2) if a.learned_n else (50, 3)
+        idx, w, rp, ci, v = M.build_stencils(X, Nr, n, "rbf", 1, ell, 1.0)
+        H = M.Hierarchy(X, rp, ci, v, 250, precision="f64" if a.fp64_cycle else "f32")
+        if a.learned_n:
+            H.learned_attach(X, Nr, idx, w)
+            H.learned_enable(M.MLP(a.learned_n, seed=1))
+        r = torch.from_numpy(np.random.default_rng(5).standard_normal(a.size)).cuda()
+        for _ in range(a.vcycles):
+            z = H.vcycle(r)
+        torch.cuda.synchronize()
+        print(json.dumps({"vcycles": a.vcycles, "N": a.size, "levels": H.stats()["n"], "max|z|": float(z.abs().max())}))
         return
     if a.single:
         import torch

@@ -78,6 +78,12 @@ typedef struct {
                               each group of rows starts as soon as the rows it reads from earlier
                               colours carry their ready flags (bounded waits). Other values:
                               MGM_ERR_INVALID_ARG. */
+    int constraint;  /* 0: solve L u = f. 1: surface Poisson (L = D, singular; build the operator with
+                        mgm_stencil_params.poisson = 1) with the mean-zero constraint of Sec. 4.4: the
+                        bordered system [L 1; 1^T 0][u; lambda] = [f; 0] (eq. (saddle_point)), coarse
+                        operators bordered as eq. (gco_saddle_point), smoothing on u only, the
+                        coarsest bordered system inverted directly. Solved by mgm_solve (FGMRES); the
+                        multiplier is returned in mgm_solve_info.multiplier. */
 } mgm_params;
 
 typedef struct {
@@ -94,6 +100,7 @@ typedef struct {
                            after each iteration, history[0] = initial */
     int history_len;
     float solve_ms;     /* device time of the solve (CUDA events) */
+    double multiplier;  /* constrained (bordered) hierarchies: the Lagrange multiplier lambda; else 0 */
 } mgm_solve_info;
 
 typedef struct mgm_hierarchy mgm_hierarchy; /* opaque, library-owned */
@@ -218,7 +225,9 @@ mgm_status mgm_setup(const double* xyz, int64_t N, const int32_t* rowptr, const 
 
 /* One V(nu1, nu2)-cycle from a zero initial guess (Alg. 3 with u^1 = 0): z = M r, the linear
  * preconditioner. r and z are N vectors in the caller's point order, dtype MGM_F64 (double) or
- * MGM_F32 (float); the arithmetic is the hierarchy's precision. */
+ * MGM_F32 (float); the arithmetic is the hierarchy's precision. For a constrained hierarchy
+ * (mgm_params.constraint = 1) r and z have N + 1 entries: the last is the constraint component of
+ * the residual and the multiplier correction of the bordered cycle (Sec. 4.4). */
 mgm_status mgm_vcycle(mgm_hierarchy* H, const void* r, void* z, int dtype, mgm_stream stream);
 
 /* Solve L u = f (Sec. 4.6): right-preconditioned flexible GMRES(restart) in FP64 with one V-cycle

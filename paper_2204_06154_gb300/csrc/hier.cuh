@@ -52,9 +52,15 @@ struct Level {
     Buf<int32_t> r_rp, r_ci;   // restriction: rows = next level's solve order
     Buf<float> r_v32;
     Buf<double> r_v64;
-    // work vectors: b = right-hand side of the level, e = its solution, s = residual
+    // work vectors: b = right-hand side of the level, e = its solution, s = residual (on the
+    // coarsest level of a constrained hierarchy b and e carry one more entry: the constraint
+    // residual and the multiplier)
     Buf<float> b32, e32, s32;
     Buf<double> b64, e64, s64;
+    // constrained (bordered) hierarchies: the border vector c_j of this level (c_0 = 1,
+    // c_{j+1} = R_j c_j), in the level's vector order
+    Buf<double> c64;
+    Buf<float> c32;
 };
 
 }  // namespace mgm
@@ -66,8 +72,12 @@ struct mgm_hierarchy {
     uint64_t seed = 0;
     int64_t N = 0;
     std::vector<mgm::Level> lv;
-    mgm::Buf<double> Ainv;      // explicit inverse of L_p (RCM order), FP64
+    mgm::Buf<double> Ainv;      // explicit inverse of L_p (RCM order), FP64; bordered: of [L_p c; c^T 0]
     int64_t np = 0;
+    int64_t nb = 0;             // dimension of Ainv: np, or np + 1 for a constrained hierarchy
+    bool bordered = false;      // mean-zero constrained surface Poisson (Sec. 4.4)
+    mgm::Buf<double> sres;      // constraint residual per level (bordered cycle)
+    mgm::Buf<double> bpart;     // partial sums of the bordered cycle's dot products
     mgm::Buf<int32_t> ord_caller;  // level-0 solve index -> caller index
     // persistent multicolour sweeps (one cooperative launch per sweep) instead of one launch
     // per colour; error word of their bounded waits

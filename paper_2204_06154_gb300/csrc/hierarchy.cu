@@ -55,12 +55,29 @@ __global__ void remap_cols_k(const int32_t* rp, const int32_t* ci, const double*
     }
 }
 
-__global__ void csr_to_dense_k(const int32_t* rp, const int32_t* ci, const double* v, int64_t n, double* A, int64_t ld) {
+// rows of L into the left half of the augmented [A | I] (dimension nt >= n), identity on the right
+__global__ void csr_to_dense_k(const int32_t* rp, const int32_t* ci, const double* v, int64_t n, double* A, int64_t ld,
+                               int64_t nt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) A[i * ld + ci[p]] = v[p];
-    A[i * ld + n + i] = 1.0;  // augmented identity
+    A[i * ld + nt + i] = 1.0;  // augmented identity
 }
+
+// y = R x for the restriction stored with the level (rows: next level's vector order)
+__global__ void restrict_vec_k(const int32_t* rp, const int32_t* ci, const double* v, const double* x, int64_t n,
+                               double* y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) acc = fma(v[p], x[ci[p]], acc);
+    y[i] = acc;
+}
+__global__ void fill_ones_k(double* x, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 1.0;
+}
+
 
 // Gauss-Jordan with partial pivoting on [A | I] (n x 2n): pivot step k
 __global__ void __launch_bounds__(1024) gj_pivot_k(double* A, int64_t n, int64_t k, double* mult, int* err) {
@@ -128,15 +145,35 @@ __global__ void extract_inv_k(const double* A, int64_t n, double* inv) {
     inv[e] = A[i * 2 * n + n + j];
 }
 
-static void dense_inverse(const Level& L, Buf<double>& inv, cudaStream_t s) {
-    const int64_t n = L.n;
+// border of the coarsest constrained operator: [L c; c^T 0] in an (n+1) x 2(n+1) augmented matrix
+__global__ void border_dense_k(const double* c, int64_t n, double* A) {
+    const int64_t ld = 2 * (n + 1);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    if (i < n) {
+        A[i * ld + n] = c[i];
+        A[n * ld + i] = c[i];
+    } else {
+        A[n * ld + n] = 0.0;
+        A[n * ld + (n + 1) + n] = 1.0;
+    }
+}
+
+// inverse of L (border == nullptr) or of the bordered [L c; c^T 0]
+static void dense_inverse(const Level& L, const double* border, Buf<double>& inv, cudaStream_t s) {
+    const int64_t nl = L.n;
+    const int64_t n = nl + (border ? 1 : 0);
     if (n > 8192) fail(MGM_ERR_UNSUPPORTED, "coarsest level larger than 8192 rows");
     Temp<double> A(2 * n * n, s), mult(n, s);
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(A.get(), 0, sizeof(double) * 2 * n * n, s));
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
-    csr_to_dense_k<<<grid_for(n, 128), 128, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), n, A.get(), 2 * n);
+    csr_to_dense_k<<<grid_for(nl, 128), 128, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), nl, A.get(), 2 * n, n);
     CK_LAUNCH();
+    if (border) {
+        border_dense_k<<<grid_for(n, 128), 128, 0, s>>>(border, nl, A.get());
+        CK_LAUNCH();
+    }
     for (int64_t k = 0; k < n; ++k) {
         gj_pivot_k<<<1, 1024, 0, s>>>(A.get(), n, k, mult.get(), err.get());
         CK_LAUNCH();
@@ -402,6 +439,8 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     REQUIRE(prm->persistent_sweeps >= 0 && prm->persistent_sweeps <= 2, "persistent_sweeps must be 0, 1 or 2");
     H->sweep_mode = prm->persistent_sweeps;
     H->persistent = prm->persistent_sweeps != 0;
+    REQUIRE(prm->constraint == 0 || prm->constraint == 1, "constraint must be 0 or 1");
+    H->bordered = prm->constraint == 1;
     H->N = N;
     int p = num_levels(N, prm->n_min);
     if (p > 16) fail(MGM_ERR_UNSUPPORTED, "more than 16 levels");
@@ -493,9 +532,34 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     for (int j = 0; j + 1 < p; ++j)
         build_transfers(H->lv[j], (j + 2 < p) ? &H->lv[j + 1] : nullptr, H->lv[j + 1].n, prm->m, s);
     tr.mark("transfers", -1);
+    // constrained Poisson (Sec. 4.4): border vectors c_0 = 1, c_{j+1} = R_j c_j (eq. (gco_saddle_point))
+    if (H->bordered) {
+        REQUIRE(p >= 2, "a constrained hierarchy needs at least two levels");
+        for (int j = 0; j < p; ++j) {
+            Level& L = H->lv[j];
+            L.c64.alloc(L.n);
+            if (j == 0) {
+                fill_ones_k<<<grid_for(L.n, 256), 256, 0, s>>>(L.c64.get(), L.n);
+            } else {
+                Level& F = H->lv[j - 1];
+                restrict_vec_k<<<grid_for(L.n, 256), 256, 0, s>>>(F.r_rp.get(), F.r_ci.get(), F.r_v64.get(), F.c64.get(),
+                                                                L.n, L.c64.get());
+            }
+            CK_LAUNCH();
+            if (H->precision == MGM_F32) {
+                L.c32.alloc(L.n);
+                to_f32_k<<<grid_for(L.n, 256), 256, 0, s>>>(L.c64.get(), L.c32.get(), L.n);
+                CK_LAUNCH();
+            }
+        }
+        H->sres.alloc(p + 1);
+        CK(cudaMemsetAsync(H->sres.get(), 0, sizeof(double) * (p + 1), s));
+        H->bpart.alloc(1024);
+    }
     // coarsest factorisation
     H->np = H->lv[p - 1].n;
-    dense_inverse(H->lv[p - 1], H->Ainv, s);
+    H->nb = H->np + (H->bordered ? 1 : 0);
+    dense_inverse(H->lv[p - 1], H->bordered ? H->lv[p - 1].c64.get() : nullptr, H->Ainv, s);
     tr.mark("coarse-inv", p - 1);
     // caller index of each level-0 solve row
     H->ord_caller.alloc(N);

@@ -11,6 +11,7 @@
 // updated at restarts and at exit, and the true FP64 residual |f - L u| decides convergence.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "hier.cuh"
@@ -121,6 +122,39 @@ __global__ void scatter64_k(const double* in, const int32_t* idx, double* out, i
     if (i < n) out[idx[i]] = in[i];
 }
 
+// Bordered operator of Sec. 4.4 on (n+1)-vectors [u; lambda]: [L u + lambda 1; 1 . u]. The border
+// sum uses fixed block partials (deterministic); y_n = f_n - sum for the residual form.
+template <class TX>
+__global__ void __launch_bounds__(256) bsum_k(const TX* __restrict__ x, int64_t n, double* part) {
+    __shared__ double red[8];
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    double acc = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += 256) acc += (double)x[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q];
+        part[blockIdx.x] = t;
+    }
+}
+__global__ void bsum_final_k(const double* part, int nb, const double* f_last, double* y_last) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) acc += part[b];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) *y_last = f_last ? *f_last - acc : acc;
+}
+// y_i += sign * lambda, lambda = x[n]
+template <class TX>
+__global__ void badd_k(const TX* lam, double* y, int64_t n, double sign) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = y[i] + sign * (double)*lam;
+}
+template <class TA, class TB>
+__global__ void copy1_k(const TA* a, TB* b) { *b = (TB)*a; }
+
 // BiCGSTAB updates: p = r + beta (p - omega v); s = r - alpha v; x += alpha ph + omega sh, r = s - omega t
 __global__ void bicg_p_k(const double* r, const double* v, double* p, double beta, double omega, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,7 +177,8 @@ __global__ void bicg_r_k(const double* sv, const double* t, double* r, double om
 struct Ops {
     mgm_hierarchy* H;
     cudaStream_t s;
-    int64_t n;
+    int64_t n;   // rows of L
+    int64_t nv;  // length of the outer vectors: n, or n + 1 (bordered: [u; lambda])
     Level& L0() { return H->lv[0]; }
 
     template <bool RESID, class TX>
@@ -153,31 +188,54 @@ struct Ops {
                                                                        x, f, y, n);
         CK_LAUNCH();
     }
+    // y = f - L~ x (RESID) or y = L~ x, with the border of Sec. 4.4 when the hierarchy has one
+    template <bool RESID, class TX>
+    void op_apply(const TX* x, const double* f, double* y) {
+        spmv<RESID, TX>(x, f, y);
+        if (!H->bordered) return;
+        badd_k<TX><<<grid_for(n, 256), 256, 0, s>>>(x + n, y, n, RESID ? -1.0 : 1.0);
+        CK_LAUNCH();
+        bsum_k<TX><<<DOT_BLOCKS, 256, 0, s>>>(x, n, H->part.get());
+        CK_LAUNCH();
+        bsum_final_k<<<1, 32, 0, s>>>(H->part.get(), DOT_BLOCKS, RESID ? f + n : nullptr, y + n);
+        CK_LAUNCH();
+    }
+    // z = M v: one V-cycle (bordered: v_n is the constraint component, z_n the multiplier)
+    template <class TZ>
+    void precondition(const double* v, TZ* z) {
+        load_input(H, v, MGM_F64, nullptr, s);
+        if (H->bordered) {
+            copy1_k<double, double><<<1, 1, 0, s>>>(v + n, H->sres.get());
+            CK_LAUNCH();
+        }
+        vcycle_core(H, s);
+        store_output(H, z, std::is_same<TZ, float>::value ? MGM_F32 : MGM_F64, nullptr, s);
+        if (H->bordered) {
+            Level& C = H->lv[H->p - 1];
+            if (H->precision == MGM_F32) copy1_k<float, TZ><<<1, 1, 0, s>>>(C.e32.get() + H->np, z + n);
+            else copy1_k<double, TZ><<<1, 1, 0, s>>>(C.e64.get() + H->np, z + n);
+            CK_LAUNCH();
+        }
+    }
     // h (device, k1 entries) = V[0..k1)^T w
     void dots(const double* V, int64_t ldv, int k1, const double* w, double* h) {
-        multidot_k<<<DOT_BLOCKS, 256, 0, s>>>(V, ldv, k1, w, n, H->part.get());
+        multidot_k<<<DOT_BLOCKS, 256, 0, s>>>(V, ldv, k1, w, nv, H->part.get());
         CK_LAUNCH();
         reduce_partials_k<<<k1, 32, 0, s>>>(H->part.get(), DOT_BLOCKS, k1, h);
         CK_LAUNCH();
     }
     void axpys(const double* V, int64_t ldv, int k1, const double* h, double* w) {
-        multiaxpy_k<<<grid_for(n, 256), 256, 0, s>>>(V, ldv, k1, h, w, n);
+        multiaxpy_k<<<grid_for(nv, 256), 256, 0, s>>>(V, ldv, k1, h, w, nv);
         CK_LAUNCH();
     }
     double norm(const double* w) {
-        dots(w, n, 1, w, H->hbuf.get());
+        dots(w, nv, 1, w, H->hbuf.get());
         double v = read1(H->hbuf.get(), s);
         return std::sqrt(v);
     }
     double dot(const double* a, const double* b) {
-        dots(a, n, 1, b, H->hbuf.get());
+        dots(a, nv, 1, b, H->hbuf.get());
         return read1(H->hbuf.get(), s);
-    }
-    // z = M v (the V-cycle, FP64 in and out, solve order)
-    void precondition(const double* v, double* z) {
-        load_input(H, v, MGM_F64, nullptr, s);
-        vcycle_core(H, s);
-        store_output(H, z, MGM_F64, nullptr, s);
     }
 };
 
@@ -251,7 +309,7 @@ static mgm_status bicgstab(mgm_hierarchy* H, Ops& op, const mgm_solve_params* sp
 }
 
 static void ensure_workspace(mgm_hierarchy* H, int m) {
-    const int64_t n = H->N;
+    const int64_t n = H->N + (H->bordered ? 1 : 0);
     if (H->krylov_m >= m && H->V.get()) return;
     H->V.alloc((int64_t)(m + 1) * n);
     if (H->precision == MGM_F32) H->Z32.alloc((int64_t)m * n);
@@ -270,7 +328,7 @@ static void ensure_workspace(mgm_hierarchy* H, int m) {
 void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s) {
     ensure_workspace(H, std::max(H->krylov_m, 1));
     const int64_t n = H->N;
-    Ops op{H, s, n};
+    Ops op{H, s, n, n};
     Level& L = H->lv[0];
     const bool f32 = H->precision == MGM_F32;
     if (f32) CK(cudaMemsetAsync(H->Z32.get(), 0, sizeof(float) * n, s));
@@ -300,11 +358,13 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
             "unknown krylov method");
     REQUIRE(sp->maxit >= 0 && sp->tol >= 0.0, "maxit and tol must be >= 0");
     REQUIRE(sp->krylov != MGM_KRYLOV_FGMRES || (sp->restart >= 1 && sp->restart <= 200), "restart must be in [1, 200]");
+    REQUIRE(!H->bordered || sp->krylov == MGM_KRYLOV_FGMRES, "a constrained hierarchy is solved with FGMRES");
     const int m = sp->krylov == MGM_KRYLOV_FGMRES ? sp->restart : sp->krylov == MGM_KRYLOV_BICGSTAB ? 8 : 1;
     ensure_workspace(H, m);
     vcycle_prepare(H);
     const int64_t n = H->N;
-    Ops op{H, s, n};
+    const int64_t nv = n + (H->bordered ? 1 : 0);  // bordered: [u; lambda], f = [f; 0], lambda_0 = 0
+    Ops op{H, s, n, nv};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -314,6 +374,10 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
     CK_LAUNCH();
     gather64_k<<<grid_for(n, 256), 256, 0, s>>>(u_io, ordc, H->u.get(), n);
     CK_LAUNCH();
+    if (H->bordered) {
+        CK(cudaMemsetAsync(H->f.get() + n, 0, sizeof(double), s));
+        CK(cudaMemsetAsync(H->u.get() + n, 0, sizeof(double), s));
+    }
     double fn = op.norm(H->f.get());
     if (!std::isfinite(fn)) fail(MGM_ERR_INVALID_ARG, "right-hand side is not finite");
     if (fn == 0.0) fn = 1.0;
@@ -355,42 +419,40 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
         std::vector<double> Hm((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
         double* V = H->V.get();
         for (;;) {
-            op.spmv<true, double>(H->u.get(), H->f.get(), V);
+            op.op_apply<true, double>(H->u.get(), H->f.get(), V);
             double beta = op.norm(V);
             rel = beta / fn;
             if (hist.empty()) hist.push_back(rel);
             if (!std::isfinite(rel)) { status = MGM_ERR_BREAKDOWN; break; }
             if (rel <= sp->tol) { status = MGM_OK; break; }
             if (it >= sp->maxit) break;
-            scale_k<<<grid_for(n, 256), 256, 0, s>>>(V, 1.0 / beta, V, n);
+            scale_k<<<grid_for(nv, 256), 256, 0, s>>>(V, 1.0 / beta, V, nv);
             CK_LAUNCH();
             std::fill(g.begin(), g.end(), 0.0);
             g[0] = beta;
             int k = 0;
             bool stop = false;
             for (; k < m && it < sp->maxit; ++k) {
-                double* vk = V + (int64_t)k * n;
+                double* vk = V + (int64_t)k * nv;
                 double* w = H->w.get();
-                load_input(H, vk, MGM_F64, nullptr, s);
-                vcycle_core(H, s);
                 if (f32) {
-                    float* zk = H->Z32.get() + (int64_t)k * n;
-                    store_output(H, zk, MGM_F32, nullptr, s);
-                    op.spmv<false, float>(zk, nullptr, w);
+                    float* zk = H->Z32.get() + (int64_t)k * nv;
+                    op.precondition(vk, zk);
+                    op.op_apply<false, float>(zk, nullptr, w);
                 } else {
-                    double* zk = H->Z64.get() + (int64_t)k * n;
-                    store_output(H, zk, MGM_F64, nullptr, s);
-                    op.spmv<false, double>(zk, nullptr, w);
+                    double* zk = H->Z64.get() + (int64_t)k * nv;
+                    op.precondition(vk, zk);
+                    op.op_apply<false, double>(zk, nullptr, w);
                 }
                 const int k1 = k + 1;
                 double* h1 = H->hbuf.get();
                 double* h2 = h1 + (m + 1);
                 double* hn2 = h2 + (m + 1);
-                op.dots(V, n, k1, w, h1);
-                op.axpys(V, n, k1, h1, w);
-                op.dots(V, n, k1, w, h2);
-                op.axpys(V, n, k1, h2, w);
-                op.dots(w, n, 1, w, hn2);
+                op.dots(V, nv, k1, w, h1);
+                op.axpys(V, nv, k1, h1, w);
+                op.dots(V, nv, k1, w, h2);
+                op.axpys(V, nv, k1, h2, w);
+                op.dots(w, nv, 1, w, hn2);
                 CK(cudaMemcpyAsync(H->hhost, H->hbuf.get(), sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
                 const double* hh = H->hhost;
@@ -399,7 +461,7 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
                 Hm[(size_t)k1 * m + k] = hn;
                 if (!std::isfinite(hn)) { status = MGM_ERR_BREAKDOWN; stop = true; break; }
                 if (hn > 0.0 && k1 < m + 1) {
-                    scale_k<<<grid_for(n, 256), 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)k1 * n, n);
+                    scale_k<<<grid_for(nv, 256), 256, 0, s>>>(w, 1.0 / hn, V + (int64_t)k1 * nv, nv);
                     CK_LAUNCH();
                 }
                 for (int i = 0; i < k; ++i) {
@@ -429,8 +491,8 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
             }
             if (k > 0) {
                 CK(cudaMemcpyAsync(H->ydev.get(), y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
-                if (f32) update_x_k<float><<<grid_for(n, 256), 256, 0, s>>>(H->Z32.get(), n, k, H->ydev.get(), H->u.get(), n);
-                else update_x_k<double><<<grid_for(n, 256), 256, 0, s>>>(H->Z64.get(), n, k, H->ydev.get(), H->u.get(), n);
+                if (f32) update_x_k<float><<<grid_for(nv, 256), 256, 0, s>>>(H->Z32.get(), nv, k, H->ydev.get(), H->u.get(), nv);
+                else update_x_k<double><<<grid_for(nv, 256), 256, 0, s>>>(H->Z64.get(), nv, k, H->ydev.get(), H->u.get(), nv);
                 CK_LAUNCH();
                 CK(cudaStreamSynchronize(s));  // y is pageable host memory
             }
@@ -449,6 +511,7 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
         info->iters = it;
         info->rel_res = rel;
         info->solve_ms = ms;
+        info->multiplier = H->bordered ? read1(H->u.get() + n, s) : 0.0;
         if (info->history && info->history_len > 0)
             for (int i = 0; i < info->history_len; ++i) info->history[i] = i < (int)hist.size() ? hist[i] : 0.0;
     }

@@ -586,6 +586,7 @@ void learned_attach(mgm_hierarchy* H, const double* xyz, const double* nrm, cons
     REQUIRE(n >= 1 && n <= LMAX_N, "learned correction: stencil size must be in [1, 48]");
     REQUIRE(H->p >= 2, "learned correction needs a hierarchy with at least two levels");
     REQUIRE(H->precision == MGM_F32, "learned correction runs in FP32 V-cycles (precision MGM_F32)");
+    REQUIRE(!H->bordered, "learned correction: not for constrained (bordered) hierarchies");
     const int64_t N = H->N;
     validate_index(idx, N * n, N, "stencil indices", s);
     Level& L0 = H->lv[0];

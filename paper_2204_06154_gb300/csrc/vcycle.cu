@@ -428,6 +428,7 @@ template <> struct LV<float> {
     static const float* pv(Level& L) { return L.pv32.get(); }
     static const float* rv(Level& L) { return L.r_v32.get(); }
     static float* eold(Level& L) { return L.eold32.get(); }
+    static const float* c(Level& L) { return L.c32.get(); }
 };
 template <> struct LV<double> {
     static double* b(Level& L) { return L.b64.get(); }
@@ -439,6 +440,7 @@ template <> struct LV<double> {
     static const double* pv(Level& L) { return L.pv64.get(); }
     static const double* rv(Level& L) { return L.r_v64.get(); }
     static double* eold(Level& L) { return L.eold64.get(); }
+    static const double* c(Level& L) { return L.c64.get(); }
 };
 
 // launch with programmatic stream serialization (see pdl_trigger / pdl_wait)
@@ -559,6 +561,45 @@ static void sweep_any(mgm_hierarchy* H, Level& L, bool from_zero, cudaStream_t s
     }
 }
 
+// ------------------------------ the bordered cycle (Sec. 4.4) -------------------------------------
+// Constraint residual chain of the descent: s_{j+1} = s_j - c_j . e_j (the border row of level j
+// is c_j^T), accumulated in FP64 with fixed block partials; the coarsest right-hand side carries
+// s_p in its last entry. Before post-smoothing, b_j <- b_j - c_j mu with mu the coarsest
+// multiplier (passed up unchanged by the interpolation), so the sweep smooths u only.
+constexpr int BDOT_BLOCKS = 256;
+template <class T>
+__global__ void __launch_bounds__(256) bdot_k(const T* __restrict__ c, const T* __restrict__ e, int64_t n, double* part) {
+    __shared__ double red[8];
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    double acc = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += 256) acc = fma((double)c[i], (double)e[i], acc);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q];
+        part[blockIdx.x] = t;
+    }
+}
+template <class T>
+__global__ void bdot_final_k(const double* part, int nb, double* sres, int j, T* bcoarse) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) acc += part[b];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) {
+        const double v = sres[j] - acc;
+        sres[j + 1] = v;
+        if (bcoarse) *bcoarse = (T)v;
+    }
+}
+template <class T>
+__global__ void bshift_k(T* b, const T* __restrict__ c, const T* mu, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = b[i] - c[i] * *mu;
+}
+
 template <class T>
 static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
     const int p = H->p;
@@ -576,19 +617,31 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
             CK(cudaMemsetAsync(LV<T>::e(L), 0, sizeof(T) * L.n, s));
             rsrc = LV<T>::b(L);
         }
+        if (H->bordered) {  // s_{j+1} = s_j - c_j . e_j
+            bdot_k<T><<<BDOT_BLOCKS, 256, 0, s>>>(LV<T>::c(L), LV<T>::e(L), L.n, H->bpart.get());
+            CK_LAUNCH();
+            bdot_final_k<T><<<1, 32, 0, s>>>(H->bpart.get(), BDOT_BLOCKS, H->sres.get(), j,
+                                             j + 2 == p ? LV<T>::b(C) + C.n : nullptr);
+            CK_LAUNCH();
+        }
         launch_pdl(restrict_k<T>, grid_for(C.n, 256), 256, s, (const int32_t*)L.r_rp.get(), (const int32_t*)L.r_ci.get(),
                    LV<T>::rv(L), rsrc, LV<T>::b(C), (int64_t)C.n);
     }
-    {  // coarsest defect
+    {   // coarsest defect (bordered: with the multiplier in the last entry)
         Level& C = H->lv[p - 1];
-        launch_pdl(coarse_k<T>, grid_for(C.n * 32, 256), 256, s, (const double*)H->Ainv.get(), (const T*)LV<T>::b(C),
-                   LV<T>::e(C), (int64_t)C.n);
+        launch_pdl(coarse_k<T>, grid_for(H->nb * 32, 256), 256, s, (const double*)H->Ainv.get(), (const T*)LV<T>::b(C),
+                   LV<T>::e(C), (int64_t)H->nb);
     }
     for (int j = p - 2; j >= 0; --j) {  // interpolate / correct, post-smooth
         Level& L = H->lv[j];
         Level& C = H->lv[j + 1];
         launch_pdl(interp_k<T>, grid_for(L.n, 256), 256, s, (const int32_t*)L.pc.get(), LV<T>::pv(L), L.pw,
                    (const T*)LV<T>::e(C), LV<T>::e(L), (int64_t)L.n);
+        if (H->bordered) {  // smooth u only: b_j <- b_j - c_j mu
+            const T* mu = LV<T>::e(H->lv[p - 1]) + H->np;
+            bshift_k<T><<<grid_for(L.n, 256), 256, 0, s>>>(LV<T>::b(L), LV<T>::c(L), mu, L.n);
+            CK_LAUNCH();
+        }
         for (int t = 0; t < H->nu2; ++t) sweep_any<T>(H, L, false, s);
     }
 }
@@ -616,15 +669,16 @@ void alloc_work(mgm_hierarchy* H) {
             if (H->precision == MGM_F32) L.eold32.alloc(L.n);
             else L.eold64.alloc(L.n);
         }
+        const int64_t nv = L.n + ((H->bordered && !smooth) ? 1 : 0);  // coarsest bordered: + multiplier
         if (H->precision == MGM_F32) {
-            L.b32.alloc(L.n); L.e32.alloc(L.n);
-            CK(cudaMemset(L.e32.get(), 0, sizeof(float) * L.n));
-            CK(cudaMemset(L.b32.get(), 0, sizeof(float) * L.n));
+            L.b32.alloc(nv); L.e32.alloc(nv);
+            CK(cudaMemset(L.e32.get(), 0, sizeof(float) * nv));
+            CK(cudaMemset(L.b32.get(), 0, sizeof(float) * nv));
             if (smooth) { L.s32.alloc(L.n); CK(cudaMemset(L.s32.get(), 0, sizeof(float) * L.n)); }
         } else {
-            L.b64.alloc(L.n); L.e64.alloc(L.n);
-            CK(cudaMemset(L.e64.get(), 0, sizeof(double) * L.n));
-            CK(cudaMemset(L.b64.get(), 0, sizeof(double) * L.n));
+            L.b64.alloc(nv); L.e64.alloc(nv);
+            CK(cudaMemset(L.e64.get(), 0, sizeof(double) * nv));
+            CK(cudaMemset(L.b64.get(), 0, sizeof(double) * nv));
             if (smooth) { L.s64.alloc(L.n); CK(cudaMemset(L.s64.get(), 0, sizeof(double) * L.n)); }
         }
     }
@@ -830,13 +884,32 @@ int barrier_timeout_probe(int nblocks, unsigned long long limit, cudaStream_t s)
     return read1(err.get(), s);
 }
 
+template <class TA, class TB>
+__global__ void cast1_k(const TA* a, TB* b) { *b = (TB)*a; }
+
 void vcycle_api(mgm_hierarchy* H, const void* r, void* z, int dtype, cudaStream_t s) {
     REQUIRE(H && r && z, "null argument");
     REQUIRE(dtype == MGM_F32 || dtype == MGM_F64, "dtype must be MGM_F32 or MGM_F64");
     load_input(H, r, dtype, H->ord_caller.get(), s);
+    if (H->bordered) {  // r_N: the constraint component
+        if (dtype == MGM_F64) cast1_k<double, double><<<1, 1, 0, s>>>((const double*)r + H->N, H->sres.get());
+        else cast1_k<float, double><<<1, 1, 0, s>>>((const float*)r + H->N, H->sres.get());
+        CK_LAUNCH();
+    }
     H->learned_active = true;
     vcycle_core(H, s);
     store_output(H, z, dtype, H->ord_caller.get(), s);
+    if (H->bordered) {  // z_N: the multiplier correction
+        Level& C = H->lv[H->p - 1];
+        if (H->precision == MGM_F32) {
+            if (dtype == MGM_F64) cast1_k<float, double><<<1, 1, 0, s>>>(C.e32.get() + H->np, (double*)z + H->N);
+            else cast1_k<float, float><<<1, 1, 0, s>>>(C.e32.get() + H->np, (float*)z + H->N);
+        } else {
+            if (dtype == MGM_F64) cast1_k<double, double><<<1, 1, 0, s>>>(C.e64.get() + H->np, (double*)z + H->N);
+            else cast1_k<double, float><<<1, 1, 0, s>>>(C.e64.get() + H->np, (float*)z + H->N);
+        }
+        CK_LAUNCH();
+    }
     if (H->persistent) check_device_error(H, s);
 }
 

@@ -38,7 +38,7 @@ class StencilParams(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("n_min", C.c_int64), ("m", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int),
-                ("seed", C.c_uint64), ("persistent_sweeps", C.c_int)]
+                ("seed", C.c_uint64), ("persistent_sweeps", C.c_int), ("constraint", C.c_int)]
 
 
 class SolveParams(C.Structure):
@@ -47,7 +47,7 @@ class SolveParams(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("rel_res", C.c_double), ("history", C.POINTER(C.c_double)),
-                ("history_len", C.c_int), ("solve_ms", C.c_float)]
+                ("history_len", C.c_int), ("solve_ms", C.c_float), ("multiplier", C.c_double)]
 
 
 class HierStats(C.Structure):
@@ -273,12 +273,16 @@ def color(rp, ci, seed):
 class Hierarchy:
     """MGM hierarchy (Alg. 2) owned by the library; V-cycle (Alg. 3) and FGMRES solve on it."""
 
-    def __init__(self, xyz, rp, ci, v, n_min, m=3, nu1=1, nu2=1, precision="f32", seed=0, persistent_sweeps=False):
+    def __init__(self, xyz, rp, ci, v, n_min, m=3, nu1=1, nu2=1, precision="f32", seed=0, persistent_sweeps=False,
+                 constraint=False):
+        """constraint=True: surface Poisson (L = D) with the mean-zero constraint of Sec. 4.4."""
         xyz = _dev(xyz, torch.float64, "xyz"); rp = _dev(rp, torch.int32, "rowptr")
         ci = _dev(ci, torch.int32, "col"); v = _dev(v, torch.float64, "val")
         self.N = xyz.shape[0]
         self.device = xyz.device
-        prm = Params(n_min, m, nu1, nu2, MGM_F32 if precision == "f32" else MGM_F64, seed, int(persistent_sweeps))
+        self.constraint = bool(constraint)
+        prm = Params(n_min, m, nu1, nu2, MGM_F32 if precision == "f32" else MGM_F64, seed, int(persistent_sweeps),
+                     int(constraint))
         h = C.c_void_p()
         self._h = None
         _check(lib().mgm_setup(_p(xyz), self.N, _p(rp), _p(ci), _p(v), C.byref(prm), C.byref(h), _stream()))
@@ -343,12 +347,12 @@ class Hierarchy:
         u = torch.zeros_like(f) if u0 is None else _dev(u0, torch.float64, "u0").clone()
         sp = SolveParams(_KRYLOV[krylov], restart, maxit, tol)
         hist = (C.c_double * (maxit + 2))()
-        info = SolveInfo(0, 0.0, hist, maxit + 2, 0.0)
+        info = SolveInfo(0, 0.0, hist, maxit + 2, 0.0, 0.0)
         st = lib().mgm_solve(self._h, _p(f), _p(u), C.byref(sp), C.byref(info), _stream())
         if st != 0 and (st != 3 or raise_on_nonconv):
             _check(st)
         return u, {"iters": info.iters, "rel_res": info.rel_res, "solve_ms": info.solve_ms, "converged": st == 0,
-                   "history": [hist[i] for i in range(info.iters + 1)]}
+                   "history": [hist[i] for i in range(info.iters + 1)], "multiplier": info.multiplier}
 
 
     # ---- learned correction after the V-cycle (an addition to the paper's method)
@@ -468,7 +472,7 @@ def _multi_infos(nrhs, maxit):
     hists = [(C.c_double * (maxit + 2))() for _ in range(nrhs)]
     infos = (SolveInfo * nrhs)()
     for r in range(nrhs):
-        infos[r] = SolveInfo(0, 0.0, hists[r], maxit + 2, 0.0)
+        infos[r] = SolveInfo(0, 0.0, hists[r], maxit + 2, 0.0, 0.0)
     return infos, hists
 
 
