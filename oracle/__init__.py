@@ -70,6 +70,9 @@ def lib():
         L.or_fgmres_bordered.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, f64p, i32p, C.c_void_p,
                                          C.c_int, C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_int, C.c_double,
                                          C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
+        L.or_phs_grad_weights.argtypes = [f64p, f64p, i64, i32p, C.c_int, C.c_int, C.c_int, f64p, f64p]
+        L.or_surface_grad.argtypes = [f64p, i64, i32p, C.c_int, f64p, f64p, f64p, f64p]
+        L.or_surface_div.argtypes = [f64p, i64, i32p, C.c_int, f64p, f64p, f64p, f64p]
         L.or_bicgstab.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_int, C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_double,
                                   C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
@@ -117,6 +120,31 @@ def phs_weights(xyz, nrm, idx, k, ell):
     w = np.empty(idx.shape, np.float64)
     _check("phs_weights", lib().or_phs_weights(xyz, nrm, xyz.shape[0], idx, idx.shape[1], k, ell, w))
     return w
+
+
+def phs_grad_weights(xyz, nrm, idx, k, ell):
+    """Tangent-plane RBF-FD weights of d/dx^ and d/dy^ at each centre (Sec. 6.3)."""
+    idx = _c(idx, np.int32); N, n = idx.shape
+    wx = np.empty((N, n)); wy = np.empty((N, n))
+    _check("phs_grad_weights", lib().or_phs_grad_weights(_c(xyz, np.float64), _c(nrm, np.float64), N, idx, n, k, ell,
+                                                         wx, wy))
+    return wx, wy
+
+
+def surface_grad(nrm, idx, wx, wy, u):
+    idx = _c(idx, np.int32); N, n = idx.shape
+    g = np.empty((N, 3))
+    _check("surface_grad", lib().or_surface_grad(_c(nrm, np.float64), N, idx, n, _c(wx, np.float64), _c(wy, np.float64),
+                                                 _c(u, np.float64), g))
+    return g
+
+
+def surface_div(nrm, idx, wx, wy, eta):
+    idx = _c(idx, np.int32); N, n = idx.shape
+    d = np.empty(N)
+    _check("surface_div", lib().or_surface_div(_c(nrm, np.float64), N, idx, n, _c(wx, np.float64), _c(wy, np.float64),
+                                               _c(eta, np.float64), d))
+    return d
 
 
 def gfd_weights(xyz, nrm, idx, ell, alpha):
@@ -527,3 +555,34 @@ def learned_loss(L, idx, xyz, nrm, w, r, W1, W2, w3):
     gout = -2.0 * sc * (L.T @ s) / rr
     g1, g2, g3 = mlp_vjp(W1, W2, w3, feat, gout)
     return float(s @ s) / rr, g1, g2, g3
+
+
+# ----------------------------------------------------------------------------------------------
+# Heat method for geodesic distance (Sec. 6.3)
+# ----------------------------------------------------------------------------------------------
+def heat_geodesic(xyz, nrm, source, n=30, ell_lap=2, ell_grad=2, k=1, dt=0.01, steps=3, n_min=250, tol=1e-10):
+    """The three steps of Sec. 6.3: backward-Euler heat steps (I - dt D) u^{k+1} = u^k from a unit
+    spike at `source`; eta = -grad u / |grad u|; the mean-zero Poisson problem D phi = div eta
+    (the bordered system of Sec. 4.4). Returns phi - phi[source] (the distance estimate), and the
+    iteration counts. The time step must let the heat reach the whole surface above the solver's
+    noise floor (u far away ~ exp(-d / sqrt(dt)) against a relative tolerance tol): dt = 0.01 on
+    a unit-size surface; dt = h^2 leaves the far-field gradient direction to round-off."""
+    N = len(xyz)
+    idx = knn(xyz, xyz, n, self_first=True)
+    w = phs_weights(xyz, nrm, idx, k, ell_lap)
+    Lh = assemble(idx, w, dt)
+    H1 = setup(xyz, Lh, n_min)
+    u = np.zeros(N); u[source] = 1.0
+    its = []
+    for _ in range(steps):
+        u, it, rel = fgmres(Lh, H1, u, tol=tol)
+        its.append(it)
+    wx, wy = phs_grad_weights(xyz, nrm, idx, k, ell_grad)
+    g = surface_grad(nrm, idx, wx, wy, u)
+    eta = -g / np.maximum(np.linalg.norm(g, axis=1, keepdims=True), 1e-300)
+    div = surface_div(nrm, idx, wx, wy, eta)
+    D = assemble(idx, w, 1.0, poisson=True)
+    H2 = setup(xyz, D, n_min, bordered=True)
+    phi, lam, it, rel = fgmres_bordered(D, H2, div, tol=tol)
+    its.append(it)
+    return phi - phi[source], its

@@ -231,6 +231,91 @@ int or_phs_weights(const double* xyz, const double* nrm, int64_t N, const int32_
 }
 
 /* ===========================================================================================
+ * Tangent-plane RBF-FD first derivatives (Sec. 6.3: the surface gradient and divergence of the
+ * heat method, RBF-FD in the tangent plane): the saddle system of eq. (rbf_fd_lap) with the
+ * right-hand sides d/dx^ and d/dy^ at the centre: for the PHS part
+ * d/dx^ phi(|x^ - x^_j|) at 0 = -(2k+1) |x^_j|^(2k-1) x^_j, for the monomials 1 for x^ (resp. y^)
+ * and 0 otherwise. Scaled coordinates as for the Laplacian; the weights are divided by s. Each
+ * right-hand side is solved by its own GEPP (the eliminations of the two are identical).
+ * The surface gradient of u at x_i is then t1 sum_j wx_ij u_j + t2 sum_j wy_ij u_j.
+ * =========================================================================================== */
+int or_phs_grad_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, int n, int k, int ell,
+                        double* wx_out, double* wy_out) {
+    int L = n_monomials(ell);
+    int m = n + L;
+    if (n < 1 || k < 1 || ell < 1 || m > MAXM || L > n) return OR_ERR_ARG;
+    int pa[64], pb[64];
+    monomial_powers(ell, pa, pb);
+    double* a = (double*)malloc(sizeof(double) * m * (m + 1));
+    double xh[MAXM], yh[MAXM], x[MAXM];
+    if (!a) return OR_ERR_NOMEM;
+    g_bad_row = -1;
+    for (int64_t i = 0; i < N; ++i) {
+        const int32_t* id = idx + i * n;
+        double s = project_stencil(xyz, nrm, i, id, n, xh, yh);
+        if (!(s > 0.0)) { g_bad_row = i; free(a); return OR_ERR_SINGULAR; }
+        double sinv = 1.0 / s;
+        for (int j = 0; j < n; ++j) { xh[j] = xh[j] * sinv; yh[j] = yh[j] * sinv; }
+        const int ld = m + 1;
+        for (int dir = 0; dir < 2; ++dir) {
+            double amax = 0.0;
+            for (int r = 0; r < n; ++r) {
+                for (int c = 0; c < n; ++c) {
+                    double dx = xh[r] - xh[c], dy = yh[r] - yh[c];
+                    a[r * ld + c] = phs(dx * dx + dy * dy, k);
+                }
+                for (int c = 0; c < L; ++c) a[r * ld + n + c] = monomial(xh[r], yh[r], pa[c], pb[c]);
+                /* -(2k+1) r^(2k-1) x_r with r^(2k-1) = sqrt(r2) r2^(k-1) */
+                double r2 = xh[r] * xh[r] + yh[r] * yh[r];
+                double rp = sqrt(r2);
+                for (int t = 1; t < k; ++t) rp = rp * r2;
+                a[r * ld + m] = -(double)(2 * k + 1) * rp * (dir == 0 ? xh[r] : yh[r]);
+            }
+            for (int r = 0; r < L; ++r) {
+                for (int c = 0; c < n; ++c) a[(n + r) * ld + c] = a[c * ld + n + r];
+                for (int c = 0; c < L; ++c) a[(n + r) * ld + n + c] = 0.0;
+                a[(n + r) * ld + m] = (dir == 0 ? (pa[r] == 1 && pb[r] == 0) : (pa[r] == 0 && pb[r] == 1)) ? 1.0 : 0.0;
+            }
+            for (int r = 0; r < m; ++r)
+                for (int c = 0; c < m; ++c) { double v = fabs(a[r * ld + c]); if (v > amax) amax = v; }
+            int st = gepp_solve(a, m, 1e-13 * amax, x);
+            if (st) { g_bad_row = i; free(a); return st; }
+            double* w = dir == 0 ? wx_out : wy_out;
+            for (int j = 0; j < n; ++j) w[i * n + j] = x[j] / s;
+        }
+    }
+    free(a);
+    return OR_OK;
+}
+
+/* Surface gradient (N x 3) of u and surface divergence of a field eta (N x 3), from the derivative
+ * weights: grad_i = t1_i (wx_i . u) + t2_i (wy_i . u); div_i = sum_j wx_ij (eta_j . t1_i) +
+ * wy_ij (eta_j . t2_i) (neighbour vectors projected onto the tangent plane of x_i). */
+int or_surface_grad(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx, const double* wy,
+                    const double* u, double* g) {
+    for (int64_t i = 0; i < N; ++i) {
+        double t1[3], t2[3], dx = 0.0, dy = 0.0;
+        or_tangent_basis(nrm + 3 * i, t1, t2);
+        for (int j = 0; j < n; ++j) { double v = u[idx[i * n + j]]; dx = dx + wx[i * n + j] * v; dy = dy + wy[i * n + j] * v; }
+        for (int a = 0; a < 3; ++a) g[3 * i + a] = t1[a] * dx + t2[a] * dy;
+    }
+    return OR_OK;
+}
+int or_surface_div(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx, const double* wy,
+                   const double* eta, double* d) {
+    for (int64_t i = 0; i < N; ++i) {
+        double t1[3], t2[3], acc = 0.0;
+        or_tangent_basis(nrm + 3 * i, t1, t2);
+        for (int j = 0; j < n; ++j) {
+            const double* e = eta + 3 * (int64_t)idx[i * n + j];
+            acc = acc + wx[i * n + j] * dot3(t1, e) + wy[i * n + j] * dot3(t2, e);
+        }
+        d[i] = acc;
+    }
+    return OR_OK;
+}
+
+/* ===========================================================================================
  * GFD weights (Sec. 2.3, eqs. (wls_fd_approx_system), (wls_fd_lap)): weighted least squares with
  * w_j = exp(-alpha |xh_1 - xh_j|^2 / (rho_1^2 + rho_j^2)), rho_k the support radius of stencil k in
  * its own tangent plane. c = W P (P^T W P)^{-1} Lap p, computed as c = W^{1/2} Q R^{-T} Lap p with
