@@ -307,6 +307,27 @@ mgm_status mgm_check_bounded_wait(int nblocks, int64_t spin_limit, int* status_o
 void mgm_destroy(mgm_hierarchy* H);
 
 /* ------------------------------------------------------------------------------------------- */
+/* Surface gradient and divergence (Sec. 6.3, the heat method)                                  */
+/* ------------------------------------------------------------------------------------------- */
+/* Tangent-plane RBF-FD first-derivative weights: for each centre, with the stencil, basis and
+ * scaling of mgm_stencil_weights (PHS r^(2k+1) plus monomials of degree <= ell, ell >= 1), the
+ * weights of d/dx^ (wx_out) and d/dy^ (wy_out) at the centre, x^ and y^ along the tangent basis
+ * t1, t2 of Sec. 2.1: right-hand sides -(2k+1) |x^_j|^(2k-1) (x^_j, y^_j) and the first-degree
+ * monomials. N x n FP64 each (device). sp->method must be MGM_RBF_FD. Errors as for
+ * mgm_stencil_weights (MGM_ERR_SINGULAR_STENCIL with the lowest bad row). */
+mgm_status mgm_gradient_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx,
+                                const mgm_stencil_params* sp, double* wx_out, double* wy_out, mgm_stream stream);
+/* Surface gradient of the nodal field u (device N FP64): g_out (device N x 3) with
+ * g_i = t1_i (wx_i . u) + t2_i (wy_i . u); with normalize != 0, g_out = -grad / |grad| (the unit
+ * field eta of the heat method; a zero gradient gives a huge vector, not a NaN). */
+mgm_status mgm_surface_gradient(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx,
+                                const double* wy, const double* u, double* g_out, int normalize, mgm_stream stream);
+/* Surface divergence of a nodal tangent field eta (device N x 3): div_i = sum_j wx_ij (eta_j . t1_i)
+ * + wy_ij (eta_j . t2_i), the neighbours' vectors projected onto the tangent plane of x_i. */
+mgm_status mgm_surface_divergence(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx,
+                                  const double* wy, const double* eta, double* div_out, mgm_stream stream);
+
+/* ------------------------------------------------------------------------------------------- */
 /* Learned correction after the V-cycle (an addition to the paper's method; the plain cycle of  */
 /* Alg. 3 is unchanged when it is off and is its fallback)                                     */
 /* ------------------------------------------------------------------------------------------- */

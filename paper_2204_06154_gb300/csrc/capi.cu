@@ -26,6 +26,13 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
 void vcycle_api(mgm_hierarchy* H, const void* r, void* z, int dtype, cudaStream_t s);
 void hierarchy_level(const mgm_hierarchy* H, int j, int32_t* perm, int32_t* keep, double* xyz, int32_t* lrp, int32_t* lci,
                      double* lv, int32_t* prp, int32_t* pci, double* pv, int32_t* colour, cudaStream_t s);
+// stencil.cu: first derivatives (heat method)
+void gradient_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, const mgm_stencil_params* sp,
+                      double* wx, double* wy, cudaStream_t s);
+void surface_gradient(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx, const double* wy,
+                      const double* u, double* g, int normalize, cudaStream_t s);
+void surface_divergence(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx, const double* wy,
+                        const double* eta, double* d, cudaStream_t s);
 // learned.cu
 void learned_attach(mgm_hierarchy* H, const double* xyz, const double* nrm, const int32_t* idx, const double* w, int n,
                     cudaStream_t s);
@@ -336,4 +343,26 @@ mgm_status mgm_learned_info(const mgm_hierarchy* H, int* enabled, int64_t* fallb
         if (enabled) *enabled = H->learned ? 1 : 0;
         if (fallbacks) *fallbacks = H->learned_fallbacks;
     });
+}
+
+// ---------------------------------------------------------------------------------------------
+// surface gradient and divergence (heat method)
+// ---------------------------------------------------------------------------------------------
+mgm_status mgm_gradient_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx,
+                                const mgm_stencil_params* sp, double* wx_out, double* wy_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(sp && idx, "null argument");
+        validate_index(idx, N * (int64_t)sp->n, N, "stencil indices", S(stream));
+        gradient_weights(xyz, nrm, N, idx, sp, wx_out, wy_out, S(stream));
+    });
+}
+
+mgm_status mgm_surface_gradient(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx,
+                                const double* wy, const double* u, double* g_out, int normalize, mgm_stream stream) {
+    return guarded([&] { surface_gradient(nrm, N, idx, n, wx, wy, u, g_out, normalize, S(stream)); });
+}
+
+mgm_status mgm_surface_divergence(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx,
+                                  const double* wy, const double* eta, double* div_out, mgm_stream stream) {
+    return guarded([&] { surface_divergence(nrm, N, idx, n, wx, wy, eta, div_out, S(stream)); });
 }

@@ -61,14 +61,16 @@ struct PhsArgs {
     const int32_t* idx;
     int64_t N;
     int n, k, ell, L, m;
-    double* w;
+    double* w;                // Laplacian weights, or d/dx^ weights when grad
+    double* wy;               // d/dy^ weights (grad only)
+    int grad;                 // 0: Laplace-Beltrami (Sec. 2.2); 1: tangent-plane first derivatives
     unsigned long long* bad;  // lowest singular row
 };
 
 __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
     extern __shared__ __align__(16) double sm_phs[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const int n = a.n, m = a.m, L = a.L, ld = m + 1;
+    const int n = a.n, m = a.m, L = a.L, nr = a.grad ? 2 : 1, ld = m + nr;
     const size_t per = (size_t)m * ld + 2 * n + 2 * m;
     double* A = sm_phs + per * wi;
     double* xh = A + (size_t)m * ld;
@@ -130,17 +132,25 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
             A[r * ld + n + t] = v;
             A[(n + t) * ld + r] = v;
             amaxb = max(amaxb, mag_bits(v));
-        } else {
+        } else if (!a.grad) {
             A[r * ld + m] = phs_lap(xh[r] * xh[r] + yh[r] * yh[r], a.k);
+        } else {  // d/dx^, d/dy^ of phi(|x^ - x^_r|) at 0: -(2k+1) |x^_r|^(2k-1) (x^_r, y^_r)
+            const double r2 = xh[r] * xh[r] + yh[r] * yh[r];
+            double rp = sqrt(r2);
+            for (int q = 1; q < a.k; ++q) rp = rp * r2;
+            A[r * ld + m] = -(double)(2 * a.k + 1) * rp * xh[r];
+            A[r * ld + m + 1] = -(double)(2 * a.k + 1) * rp * yh[r];
         }
     }
-    for (int e = lane; e < L * (L + 1); e += 32) {
-        int t = e / (L + 1), c = e - t * (L + 1);
+    for (int e = lane; e < L * (L + nr); e += 32) {
+        int t = e / (L + nr), c = e - t * (L + nr);
         double v = 0.0;
-        if (c == L) {
+        if (c >= L) {
             int pa, pb;
             mono_pow(t, &pa, &pb);
-            v = ((pa == 2 && pb == 0) || (pa == 0 && pb == 2)) ? 2.0 : 0.0;
+            if (!a.grad) v = ((pa == 2 && pb == 0) || (pa == 0 && pb == 2)) ? 2.0 : 0.0;
+            else if (c == L) v = (pa == 1 && pb == 0) ? 1.0 : 0.0;
+            else v = (pa == 0 && pb == 1) ? 1.0 : 0.0;
         }
         A[(n + t) * ld + n + c] = v;
     }
@@ -203,22 +213,30 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
         }
         __syncwarp();
     }
-    // back substitution, column oriented
-    bool finite = true;
-    for (int kk = m - 1; kk >= 0; --kk) {
-        double xk = A[kk * ld + m] * rinvs[kk];
-        finite = finite && isfinite(xk);
-        if (lane == 0) xs[kk] = xk;
-        for (int r = lane; r < kk; r += 32) A[r * ld + m] = fma(-A[r * ld + kk], xk, A[r * ld + m]);
+    // back substitution, column oriented, for each right-hand side column
+    for (int rc = m; rc < ld; ++rc) {
+        bool finite = true;
+        for (int kk = m - 1; kk >= 0; --kk) {
+            double xk = A[kk * ld + rc] * rinvs[kk];
+            finite = finite && isfinite(xk);
+            if (lane == 0) xs[kk] = xk;
+            for (int r = lane; r < kk; r += 32) A[r * ld + rc] = fma(-A[r * ld + kk], xk, A[r * ld + rc]);
+            __syncwarp();
+        }
+        if (!finite) {
+            if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
+            return;
+        }
+        __syncwarp();
+        if (!a.grad) {
+            const double s2 = s * s;
+            for (int j = lane; j < n; j += 32) a.w[i * n + j] = xs[j] / s2;
+        } else {
+            double* out = rc == m ? a.w : a.wy;
+            for (int j = lane; j < n; j += 32) out[i * n + j] = xs[j] / s;
+        }
         __syncwarp();
     }
-    if (!finite) {
-        if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
-        return;
-    }
-    __syncwarp();
-    const double s2 = s * s;
-    for (int j = lane; j < n; j += 32) a.w[i * n + j] = xs[j] / s2;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -331,6 +349,92 @@ static void check_bad(unsigned long long* bad, cudaStream_t s, const char* what)
     }
 }
 
+// Surface gradient grad_i = t1_i (wx_i . u) + t2_i (wy_i . u) (optionally eta = -grad / |grad|) and
+// surface divergence div_i = sum_j wx_ij (eta_j . t1_i) + wy_ij (eta_j . t2_i) of a tangent field
+// given at the nodes (neighbour vectors projected onto the tangent plane of x_i), Sec. 6.3.
+__global__ void surface_grad_k(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx, const double* wy,
+                               const double* u, double* g, int normalize) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double t1[3], t2[3], dx = 0.0, dy = 0.0;
+    tangent_basis(nrm + 3 * i, t1, t2);
+    for (int j = 0; j < n; ++j) {
+        const double v = u[idx[i * n + j]];
+        dx = dx + wx[i * n + j] * v;
+        dy = dy + wy[i * n + j] * v;
+    }
+    double o[3];
+    for (int a = 0; a < 3; ++a) o[a] = t1[a] * dx + t2[a] * dy;
+    if (normalize) {
+        const double nn = sqrt((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]);
+        const double sc = nn > 1e-300 ? -1.0 / nn : -1e300;
+        for (int a = 0; a < 3; ++a) o[a] = o[a] * sc;
+    }
+    for (int a = 0; a < 3; ++a) g[3 * i + a] = o[a];
+}
+__global__ void surface_div_k(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx, const double* wy,
+                              const double* eta, double* d) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double t1[3], t2[3], acc = 0.0;
+    tangent_basis(nrm + 3 * i, t1, t2);
+    for (int j = 0; j < n; ++j) {
+        const double* e = eta + 3 * (int64_t)idx[i * n + j];
+        acc = acc + wx[i * n + j] * dot3d(t1, e) + wy[i * n + j] * dot3d(t2, e);
+    }
+    d[i] = acc;
+}
+
+void surface_gradient(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx, const double* wy,
+                      const double* u, double* g, int normalize, cudaStream_t s) {
+    REQUIRE(nrm && idx && wx && wy && u && g, "null array");
+    REQUIRE(N >= 1 && n >= 1, "bad size");
+    validate_index(idx, N * n, N, "stencil indices", s);
+    surface_grad_k<<<grid_for(N, 128), 128, 0, s>>>(nrm, N, idx, n, wx, wy, u, g, normalize);
+    CK_LAUNCH();
+}
+void surface_divergence(const double* nrm, int64_t N, const int32_t* idx, int n, const double* wx, const double* wy,
+                        const double* eta, double* d, cudaStream_t s) {
+    REQUIRE(nrm && idx && wx && wy && eta && d, "null array");
+    REQUIRE(N >= 1 && n >= 1, "bad size");
+    validate_index(idx, N * n, N, "stencil indices", s);
+    surface_div_k<<<grid_for(N, 128), 128, 0, s>>>(nrm, N, idx, n, wx, wy, eta, d);
+    CK_LAUNCH();
+}
+
+static void phs_launch(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, int n, int k, int ell, int L,
+                       double* w, double* wy, int grad, unsigned long long* bad, cudaStream_t s) {
+    const int m = n + L, ld = m + (grad ? 2 : 1);
+    if (m > MAX_M) fail(MGM_ERR_UNSUPPORTED, "n + (ell+1)(ell+2)/2 must be <= 128");
+    const size_t per = sizeof(double) * ((size_t)m * ld + 2 * n + 2 * m);
+    int wpb = (int)std::min<size_t>(8, (227 * 1024) / per);
+    if (wpb < 1) wpb = 1;
+    const size_t smem = per * wpb;
+    CK(cudaFuncSetAttribute(phs_weights_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PhsArgs a{xyz, nrm, idx, N, n, k, ell, L, m, w, wy, grad, bad};
+    phs_weights_k<<<grid_for(N, wpb), 32 * wpb, smem, s>>>(a, wpb);
+    CK_LAUNCH();
+}
+
+// tangent-plane first-derivative weights (PHS RBF-FD with the first-derivative right-hand sides)
+void gradient_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, const mgm_stencil_params* sp,
+                      double* wx, double* wy, cudaStream_t s) {
+    REQUIRE(sp != nullptr, "null stencil params");
+    REQUIRE(N >= 1 && N < 0x7fffffff, "N out of range");
+    REQUIRE(xyz && nrm && idx && wx && wy, "null array");
+    REQUIRE(sp->method == MGM_RBF_FD, "gradient weights: RBF-FD only");
+    const int n = sp->n, ell = sp->ell;
+    REQUIRE(ell >= 1 && ell <= 12, "ell out of range");
+    const int L = (ell + 1) * (ell + 2) / 2;
+    REQUIRE(n >= 1 && n <= N && L <= n, "stencil size n must satisfy (ell+1)(ell+2)/2 <= n <= N");
+    REQUIRE(sp->k >= 1 && sp->k <= 8, "PHS order k must be in [1, 8]");
+    set_bad_row(-1);
+    Temp<unsigned long long> bad(1, s);
+    CK(cudaMemsetAsync(bad.get(), 0xff, sizeof(unsigned long long), s));
+    phs_launch(xyz, nrm, N, idx, n, sp->k, ell, L, wx, wy, 1, bad.get(), s);
+    check_bad(bad.get(), s, "PHS gradient weights");
+}
+
 void stencil_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, const mgm_stencil_params* sp,
                      double* w, cudaStream_t s) {
     REQUIRE(sp != nullptr, "null stencil params");
@@ -345,16 +449,7 @@ void stencil_weights(const double* xyz, const double* nrm, int64_t N, const int3
     CK(cudaMemsetAsync(bad.get(), 0xff, sizeof(unsigned long long), s));
     if (sp->method == MGM_RBF_FD) {
         REQUIRE(sp->k >= 1 && sp->k <= 8, "PHS order k must be in [1, 8]");
-        const int m = n + L;
-        if (m > MAX_M) fail(MGM_ERR_UNSUPPORTED, "n + (ell+1)(ell+2)/2 must be <= 128");
-        const size_t per = sizeof(double) * ((size_t)m * (m + 1) + 2 * n + 2 * m);
-        int wpb = (int)std::min<size_t>(8, (227 * 1024) / per);
-        if (wpb < 1) wpb = 1;
-        const size_t smem = per * wpb;
-        CK(cudaFuncSetAttribute(phs_weights_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PhsArgs a{xyz, nrm, idx, N, n, sp->k, ell, L, m, w, bad.get()};
-        phs_weights_k<<<grid_for(N, wpb), 32 * wpb, smem, s>>>(a, wpb);
-        CK_LAUNCH();
+        phs_launch(xyz, nrm, N, idx, n, sp->k, ell, L, w, nullptr, 0, bad.get(), s);
         check_bad(bad.get(), s, "PHS weights");
     } else if (sp->method == MGM_GFD) {
         REQUIRE(sp->alpha > 0.0, "GFD alpha must be > 0");

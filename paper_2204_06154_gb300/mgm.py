@@ -63,7 +63,8 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_last_error_row",
            "mgm_mlp_size", "mgm_mlp_create", "mgm_mlp_destroy", "mgm_mlp_get", "mgm_mlp_set", "mgm_mlp_forward",
            "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
-           "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info"]
+           "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
+           "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence"]
 
 
 class ProfileInfo(C.Structure):
@@ -106,6 +107,9 @@ def lib():
         L.mgm_kernel_launches.restype = C.c_int64
         L.mgm_destroy.argtypes = [P]
         L.mgm_destroy.restype = None
+        L.mgm_gradient_weights.argtypes = [P, P, I64, P, C.POINTER(StencilParams), P, P, P]
+        L.mgm_surface_gradient.argtypes = [P, I64, P, I, P, P, P, P, I, P]
+        L.mgm_surface_divergence.argtypes = [P, I64, P, I, P, P, P, P, P]
         L.mgm_mlp_size.argtypes = [I]
         L.mgm_mlp_size.restype = C.c_int64
         L.mgm_mlp_create.argtypes = [I, C.c_uint64, C.POINTER(P)]
@@ -187,6 +191,34 @@ def stencil_weights(xyz, nrm, idx, method="rbf", k=1, ell=2, alpha=4.0):
     w = torch.empty(idx.shape, dtype=torch.float64, device=xyz.device)
     _check(lib().mgm_stencil_weights(_p(xyz), _p(nrm), xyz.shape[0], _p(idx), C.byref(sp), _p(w), _stream()))
     return w
+
+
+def gradient_weights(xyz, nrm, idx, k=1, ell=2):
+    """Tangent-plane RBF-FD weights of d/dx^ and d/dy^ (Sec. 6.3)."""
+    xyz = _dev(xyz, torch.float64, "xyz"); nrm = _dev(nrm, torch.float64, "nrm"); idx = _dev(idx, torch.int32, "idx")
+    sp = _sp(idx.shape[1], "rbf", k, ell, 1.0, 4.0)
+    wx = torch.empty(idx.shape, dtype=torch.float64, device=xyz.device)
+    wy = torch.empty_like(wx)
+    _check(lib().mgm_gradient_weights(_p(xyz), _p(nrm), xyz.shape[0], _p(idx), C.byref(sp), _p(wx), _p(wy), _stream()))
+    return wx, wy
+
+
+def surface_gradient(nrm, idx, wx, wy, u, normalize=False):
+    nrm = _dev(nrm, torch.float64, "nrm"); idx = _dev(idx, torch.int32, "idx")
+    wx = _dev(wx, torch.float64, "wx"); wy = _dev(wy, torch.float64, "wy"); u = _dev(u, torch.float64, "u")
+    g = torch.empty((idx.shape[0], 3), dtype=torch.float64, device=u.device)
+    _check(lib().mgm_surface_gradient(_p(nrm), idx.shape[0], _p(idx), idx.shape[1], _p(wx), _p(wy), _p(u), _p(g),
+                                      int(normalize), _stream()))
+    return g
+
+
+def surface_divergence(nrm, idx, wx, wy, eta):
+    nrm = _dev(nrm, torch.float64, "nrm"); idx = _dev(idx, torch.int32, "idx")
+    wx = _dev(wx, torch.float64, "wx"); wy = _dev(wy, torch.float64, "wy"); eta = _dev(eta, torch.float64, "eta")
+    d = torch.empty(idx.shape[0], dtype=torch.float64, device=eta.device)
+    _check(lib().mgm_surface_divergence(_p(nrm), idx.shape[0], _p(idx), idx.shape[1], _p(wx), _p(wy), _p(eta), _p(d),
+                                        _stream()))
+    return d
 
 
 def assemble(idx, w, mu=1.0, poisson=False):
