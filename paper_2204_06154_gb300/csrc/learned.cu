@@ -396,6 +396,14 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
     hi = pack_bf16(ha, hb);
     lo = pack_bf16(a - ha, b - hb);
 }
+// four 8x8 b16 matrices from shared memory; lane l gives the address of row l % 8 of matrix l / 8
+// (16 contiguous bytes, 16-byte aligned) and receives row l / 4, elements 2 (l % 4), +1 of each
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const uint16_t* p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -460,20 +468,25 @@ __global__ void __launch_bounds__(CW * 32) correct_k(const int32_t* __restrict__
         float d1[8][4];
 #pragma unroll
         for (int t = 0; t < 8; ++t) d1[t][0] = d1[t][1] = d1[t][2] = d1[t][3] = 0.0f;
+        // fragments by ldmatrix: lane l addresses row (l % 8) + 8 ((l / 8) & 1) at column 8 (l / 16) of
+        // the A tile (a0..a3), and for B rows n = 8 (l / 16) + l % 8 of a pair of n-tiles at
+        // k + 8 ((l / 8) & 1) (b0, b1 of tile t, then of tile t + 1)
+        const int lr = (lane & 7) + 8 * ((lane >> 3) & 1), lc = 8 * (lane >> 4);
+        const int bn = 8 * (lane >> 4) + (lane & 7), bk = 8 * ((lane >> 3) & 1);
         for (int kk = 0; kk < K1; kk += 16) {
+            uint32_t b[8][2];
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                uint32_t q[4];
+                ldsm_x4(q, w1 + (8 * t + bn) * S1 + kk + bk);
+                b[t][0] = q[0]; b[t][1] = q[1]; b[t + 1][0] = q[2]; b[t + 1][1] = q[3];
+            }
 #pragma unroll
             for (int part = 0; part < 2; ++part) {
-                const uint16_t* xp = xs + part * 16 * S1;
                 uint32_t a[4];
-                a[0] = *reinterpret_cast<const uint32_t*>(xp + g * S1 + kk + 2 * tg);
-                a[1] = *reinterpret_cast<const uint32_t*>(xp + (g + 8) * S1 + kk + 2 * tg);
-                a[2] = *reinterpret_cast<const uint32_t*>(xp + g * S1 + kk + 8 + 2 * tg);
-                a[3] = *reinterpret_cast<const uint32_t*>(xp + (g + 8) * S1 + kk + 8 + 2 * tg);
+                ldsm_x4(a, xs + part * 16 * S1 + lr * S1 + kk + lc);
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const uint16_t* bp = w1 + (8 * t + g) * S1 + kk + 2 * tg;
-                    mma16816(d1[t], a, *reinterpret_cast<const uint32_t*>(bp), *reinterpret_cast<const uint32_t*>(bp + 8));
-                }
+                for (int t = 0; t < 8; ++t) mma16816(d1[t], a, b[t][0], b[t][1]);
             }
         }
         // h1 = relu(D1 + hg), re-packed as GEMM2's A operand (hi and lo)
@@ -491,21 +504,26 @@ __global__ void __launch_bounds__(CW * 32) correct_k(const int32_t* __restrict__
             split2(h0, h1v, ah[kb][half + 0], al[kb][half + 0]);
             split2(h2, h3, ah[kb][half + 1], al[kb][half + 1]);
         }
-        // GEMM2 per output n-tile, then relu, times w3, summed over the thread's columns
+        // GEMM2 per pair of output n-tiles, then relu, times w3, summed over the thread's columns
         float oa = 0.0f, ob = 0.0f;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            float d2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int t = 0; t < 8; t += 2) {
+            float d2[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
 #pragma unroll
             for (int kb = 0; kb < 4; ++kb) {
-                const uint16_t* bp = w2 + (8 * t + g) * W2S + 16 * kb + 2 * tg;
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bp), b1 = *reinterpret_cast<const uint32_t*>(bp + 8);
-                mma16816(d2, ah[kb], b0, b1);
-                mma16816(d2, al[kb], b0, b1);
+                uint32_t q[4];
+                ldsm_x4(q, w2 + (8 * t + bn) * W2S + 16 * kb + bk);
+                mma16816(d2[0], ah[kb], q[0], q[1]);
+                mma16816(d2[0], al[kb], q[0], q[1]);
+                mma16816(d2[1], ah[kb], q[2], q[3]);
+                mma16816(d2[1], al[kb], q[2], q[3]);
             }
-            const int c = 8 * t + 2 * tg;
-            oa = fmaf(w3[c], fmaxf(d2[0], 0.0f), fmaf(w3[c + 1], fmaxf(d2[1], 0.0f), oa));
-            ob = fmaf(w3[c], fmaxf(d2[2], 0.0f), fmaf(w3[c + 1], fmaxf(d2[3], 0.0f), ob));
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int c = 8 * (t + u) + 2 * tg;
+                oa = fmaf(w3[c], fmaxf(d2[u][0], 0.0f), fmaf(w3[c + 1], fmaxf(d2[u][1], 0.0f), oa));
+                ob = fmaf(w3[c], fmaxf(d2[u][2], 0.0f), fmaf(w3[c + 1], fmaxf(d2[u][3], 0.0f), ob));
+            }
         }
         oa += __shfl_xor_sync(0xffffffffu, oa, 1);
         oa += __shfl_xor_sync(0xffffffffu, oa, 2);
