@@ -7,16 +7,17 @@ grid, jitter 0.1 h), each N = 1,048,576; tangent-plane PHS RBF-FD with phi = r^3
 polynomials, n = 50; L = I - D (-Lap + I); right-hand side a seeded sum of real spherical
 harmonics up to l = 20 with N(0, 1) coefficients; N_min = 250, m = 3, V(1,1) multicolour GS,
 FP32 V-cycle inside FP64 flexible GMRES to 1e-10. Per problem the step runs kNN stencils and
-FP64 weights, the hierarchy (RCM, weighted sample elimination, transfers, Galerkin products,
+weights (FP32 LU with FP64 iterative refinement: the FP64 solution of each stencil system), the
+hierarchy (RCM, weighted sample elimination, transfers, Galerkin products,
 colourings, coarsest inverse) and the solve, all in libmgm kernels. Inputs are resident in HBM
 when the timed region starts; the level-1 operator (~630 MB) exceeds the 129 MB L2, so no flush
 is needed between steps.
 
 Reported: value = mean device time per problem for the whole path (ms, lower is better); the
 phase split (stencils / setup / solve, the solve alone being the paper's convention); the same
-solve with an FP64 V-cycle (the "FP64 MGM" comparison); the roofline of the dominant kernel
-(the FP64 stencil-weight solves, ALU-bound) and of the finest-level Gauss-Seidel sweep
-(HBM-bound); e2e through pinned host buffers; the oracle timed on the host cores.
+solve with an FP64 V-cycle and the whole path with FP64 weights and cycle (the "FP64 MGM"
+comparison); the roofline of the dominant kernel (the stencil-weight solves, FP64-pipe-bound)
+and of the finest-level Gauss-Seidel sweep (HBM-bound); e2e through pinned host buffers; the oracle timed on the host cores.
 
 --impl reference times the CPU oracle (the plain FP64 C implementation that the tests compare
 against) on a bounded sample of the same workload.
@@ -131,11 +132,13 @@ class Clocks:
 # one problem through the whole path (device-resident inputs), with phase events
 # ----------------------------------------------------------------------------------------------
 def run_problem(M, torch, x, nrm, f, precision="f32", ev=None):
+    """precision "f32": the mixed pipeline (FP32 LU + FP64 refinement for the stencil weights, FP32
+    V-cycle, FP64 FGMRES); "f64": FP64 elimination and an FP64 V-cycle."""
     E = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     E[0].record()
     idx = M.knn(x, None, P["n"], self_first=True)
     E[1].record()
-    w = M.stencil_weights(x, nrm, idx, "rbf", P["k"], P["ell"])
+    w = M.stencil_weights(x, nrm, idx, "rbf", P["k"], P["ell"], weights="mixed" if precision == "f32" else "f64")
     E[2].record()
     rp, ci, v = M.assemble(idx, w, P["mu"])
     E[3].record()
@@ -470,11 +473,17 @@ def main():
     hbm = float(pk.get("hbm_gbs", 6800.0))
     prof = res["profile"]
     st = res["stats"]
-    # dominant kernel of the step: the FP64 stencil-weight solves (warp-per-stencil GEPP)
+    # dominant kernel of the step: the stencil-weight solves, FP32 LU in registers with FP64
+    # refinement (phs_weights_rl_k<60>), bound by the FP64 pipe. Algorithmic FP64 work per stencil:
+    # the n(n+1)/2 PHS entries (2 differences, 2 squares, 1 sum, 1 square root, 1 product = 7 flops),
+    # the n L monomials (ell - 1 products each on average, taken as 2), and 3 residual evaluations
+    # of 2 (m n + n L) flops (3 is the typical count; convergence is tested after each).
     m = P["n"] + (P["ell"] + 1) * (P["ell"] + 2) // 2
-    flops_per_stencil = 2.0 * (m ** 3 - m) / 3.0
+    L = m - P["n"]
+    flops_per_stencil = 7.0 * P["n"] * (P["n"] + 1) / 2 + 2.0 * P["n"] * L + 3 * 2.0 * (m * P["n"] + P["n"] * L)
     w_ms = mean("weights_ms")
     w_gflops = a.size * flops_per_stencil / (w_ms * 1e-3) / 1e9
+    total_fp64 = mean("total_ms", res["fp64"])
     sweep_gbs = prof["sweep_bytes"] / (prof["sweep_ms"] * 1e-3) / 1e9 if prof["sweep_ms"] > 0 else None
     vcyc_gbs = prof["vcycle_bytes"] / (prof["vcycle_ms"] * 1e-3) / 1e9
     spmv_gbs = prof["spmv_bytes"] / (prof["spmv_ms"] * 1e-3) / 1e9
@@ -486,12 +495,17 @@ def main():
         "phases_ms": {k: round(mean(k), 3) for k in ("knn_ms", "weights_ms", "assemble_ms", "setup_ms", "solve_ms")},
         "solve_ms": {"mixed_f32_vcycle": round(solve_mixed, 3), "fp64_vcycle": round(solve_fp64, 3),
                      "speedup": round(solve_fp64 / solve_mixed, 3)},
+        "whole_path_ms": {"mixed": round(mean("total_ms"), 2), "fp64": round(total_fp64, 2),
+                          "fp64_weights_ms": round(mean("weights_ms", res["fp64"]), 2),
+                          "speedup": round(total_fp64 / mean("total_ms"), 3)},
         "iters": {"mixed": [r["iters"] for r in recs[: res["nprob"]]], "fp64": [r["iters"] for r in res["fp64"]]},
         "rel_res_max": max(r["rel_res"] for r in recs + res["fp64"]),
         "converged": all(r["converged"] for r in recs + res["fp64"]),
-        "roofline": {"kernel": "phs_weights_k (FP64 GEPP of the (n+L)^2 = 60^2 stencil systems)", "bound": "alu",
+        "roofline": {"kernel": "phs_weights_rl_k<60> (60 x 60 stencil systems: FP32 LU in registers, FP64 "
+                               "entries and refinement residuals)", "bound": "alu",
                      "achieved": round(w_gflops, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                      "frac": round(w_gflops / FP64_PEAK_GFLOPS, 3), "traffic": None,
+                     "fp64_flops_per_stencil": flops_per_stencil,
                      "peak_source": "FP64 FMA-chain probe on this pool's GB300 (not in MEASURED_PEAKS.json)"},
         "vcycle_roofline": {"kernel": "row_kernel<1,float> (finest-level multicolour GS sweep)", "bound": "hbm",
                             "achieved": round(sweep_gbs, 1) if sweep_gbs else None, "peak": hbm, "unit": "GB/s",
@@ -521,7 +535,8 @@ def config(a):
     return {"workload": f"sphere + torus, {a.size:,} points each, PHS r^3 + degree-3, n=50, -Lap+I, "
                         f"random SH rhs l<=20, MGM V(1,1) MC-GS, FGMRES to 1e-10",
             "problems_per_step": 2, "N": a.size, "n": P["n"], "ell": P["ell"], "n_min": P["n_min"],
-            "precision": "FP32 V-cycle / FP64 outer + FP64 setup", "l2": "inputs > L2 (no flush needed)"}
+            "precision": "FP32 LU + FP64 refinement for the stencil weights, FP32 V-cycle / FP64 outer, "
+                         "FP64 hierarchy setup", "l2": "inputs > L2 (no flush needed)"}
 
 
 if __name__ == "__main__":

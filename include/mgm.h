@@ -62,7 +62,17 @@ typedef struct {
     double alpha;  /* GFD Gaussian weight parameter (Sec. 2.3), > 0 */
     double mu;     /* L = I - mu D (shifted Poisson); ignored when poisson != 0 */
     int poisson;   /* nonzero: L = D (the singular surface Poisson operator) */
+    int weights;   /* how the PHS RBF-FD saddle systems (Sec. 2.2) are solved; GFD ignores it.
+                      MGM_WEIGHTS_F64 (0): FP64 Gaussian elimination with partial pivoting.
+                      MGM_WEIGHTS_MIXED (1): FP32 LU with partial pivoting and iterative refinement
+                      with FP64 residuals until the weight correction is below 1e-12 of the weights
+                      (at most 8 steps); stencils that do not converge, or meet an FP32 pivot below
+                      2^-20 of the largest entry, are solved again by the FP64 path (counted by
+                      mgm_last_weights_fp64_rows()). The weights agree with the FP64 path to about
+                      cond(K) * 1e-16 relative. Other values: MGM_ERR_INVALID_ARG. */
 } mgm_stencil_params;
+
+enum { MGM_WEIGHTS_F64 = 0, MGM_WEIGHTS_MIXED = 1 };
 
 /* Multilevel parameters (Sec. 4; Table 1). */
 typedef struct {
@@ -145,7 +155,8 @@ mgm_status mgm_knn_noalloc(const double* data, int64_t nd, const double* query, 
 
 /* Stencil weights c_ij of the LBO for each stencil (Sec. 2.1 tangent plane; Sec. 2.2 PHS RBF-FD,
  * eq. (rbf_fd_lap); Sec. 2.3 GFD, eq. (wls_fd_lap)). idx (N x n) from mgm_knn(self_first=1);
- * w_out (N x n) receives the weights in the order of idx. FP64 throughout. A singular local
+ * w_out (N x n) receives the weights in the order of idx. FP64 results (sp->weights selects
+ * FP64 elimination or FP32 LU with FP64 refinement for the PHS systems). A singular local
  * system returns MGM_ERR_SINGULAR_STENCIL (the lowest failing row via mgm_last_error_row());
  * synchronises the stream to read that flag. */
 mgm_status mgm_stencil_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx,
@@ -396,6 +407,9 @@ mgm_status mgm_learned_info(const mgm_hierarchy* H, int* enabled, int64_t* fallb
 const char* mgm_status_string(mgm_status s);
 const char* mgm_last_error_message(void);
 int64_t mgm_last_error_row(void); /* lowest failing stencil / interpolation row of the last call */
+/* Stencils that the last mgm_stencil_weights / mgm_build_stencils call on this host thread with
+ * weights = MGM_WEIGHTS_MIXED solved again in FP64 (0 after an MGM_WEIGHTS_F64 call). */
+int64_t mgm_last_weights_fp64_rows(void);
 
 #ifdef __cplusplus
 }

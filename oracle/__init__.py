@@ -47,6 +47,7 @@ def lib():
         L = C.CDLL(path)
         L.or_knn.argtypes = [f64p, i64, f64p, i64, C.c_int, C.c_int, i32p, C.c_void_p]
         L.or_phs_weights.argtypes = [f64p, f64p, i64, i32p, C.c_int, C.c_int, C.c_int, f64p]
+        L.or_phs_weights_rows.argtypes = [f64p, f64p, i64, i32p, C.c_int, C.c_int, C.c_int, i32p, i64, f64p]
         L.or_gfd_weights.argtypes = [f64p, f64p, i64, i32p, C.c_int, C.c_int, C.c_double, f64p]
         L.or_assemble.argtypes = [i64, C.c_int, i32p, f64p, C.c_double, C.c_int, i32p, i32p, f64p]
         L.or_rcm.argtypes = [i64, i32p, i32p, i32p]
@@ -114,11 +115,22 @@ def tangent_basis(n):
     return t1, t2
 
 
-def phs_weights(xyz, nrm, idx, k, ell):
-    """Tangent-plane PHS RBF-FD Laplacian weights, one row per stencil (Sec. 2.2)."""
+def phs_weights(xyz, nrm, idx, k, ell, rows=None):
+    """Tangent-plane PHS RBF-FD Laplacian weights, one row per stencil (Sec. 2.2). idx holds one
+    stencil per point; with rows given, idx holds the stencils of the centres rows (len(rows) x n)
+    and the result their weights."""
     xyz = _c(xyz, np.float64); nrm = _c(nrm, np.float64); idx = _c(idx, np.int32)
-    w = np.empty(idx.shape, np.float64)
-    _check("phs_weights", lib().or_phs_weights(xyz, nrm, xyz.shape[0], idx, idx.shape[1], k, ell, w))
+    nst = xyz.shape[0] if rows is None else len(rows)
+    if idx.ndim != 2 or idx.shape[0] != nst or nrm.shape != xyz.shape:
+        raise ValueError("phs_weights: idx must hold one stencil per centre and nrm one normal per point")
+    if rows is None:
+        w = np.empty(idx.shape, np.float64)
+        _check("phs_weights", lib().or_phs_weights(xyz, nrm, xyz.shape[0], idx, idx.shape[1], k, ell, w))
+    else:
+        rows = _c(rows, np.int32)
+        w = np.empty((rows.shape[0], idx.shape[1]), np.float64)
+        _check("phs_weights", lib().or_phs_weights_rows(xyz, nrm, xyz.shape[0], idx, idx.shape[1], k, ell, rows,
+                                                        rows.shape[0], w))
     return w
 
 

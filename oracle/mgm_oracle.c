@@ -187,8 +187,10 @@ static double phs_lap(double r2, int k) {
  * stencil support s (xh * (1/s)); the weights for the unscaled Laplacian are c / s^2 (PHS with
  * polynomials of degree >= k is scale-invariant). Singular when a pivot is <= 1e-13 max|M|.
  * =========================================================================================== */
-int or_phs_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, int n, int k, int ell,
-                   double* w_out) {
+/* Weights of all N stencils (rows NULL; idx is N x n), or of the stencils centred at rows[0..nrows-1]
+ * with neighbours idx[t*n..] (idx is nrows x n), into w_out (one row per stencil). */
+static int phs_weights_rows(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, int n, int k, int ell,
+                            const int32_t* rows, int64_t nrows, double* w_out) {
     int L = n_monomials(ell);
     int m = n + L;
     if (n < 1 || k < 1 || ell < 0 || m > MAXM || L > n) return OR_ERR_ARG;
@@ -198,8 +200,11 @@ int or_phs_weights(const double* xyz, const double* nrm, int64_t N, const int32_
     double xh[MAXM], yh[MAXM], x[MAXM];
     if (!a) return OR_ERR_NOMEM;
     g_bad_row = -1;
-    for (int64_t i = 0; i < N; ++i) {
-        const int32_t* id = idx + i * n;
+    const int64_t cnt = rows ? nrows : N;
+    for (int64_t t = 0; t < cnt; ++t) {
+        const int64_t i = rows ? (int64_t)rows[t] : t;
+        if (i < 0 || i >= N) { free(a); return OR_ERR_ARG; }
+        const int32_t* id = idx + t * n;
         double s = project_stencil(xyz, nrm, i, id, n, xh, yh);
         if (!(s > 0.0)) { g_bad_row = i; free(a); return OR_ERR_SINGULAR; }
         double sinv = 1.0 / s;
@@ -224,10 +229,20 @@ int or_phs_weights(const double* xyz, const double* nrm, int64_t N, const int32_
         int st = gepp_solve(a, m, 1e-13 * amax, x);
         if (st) { g_bad_row = i; free(a); return st; }
         double s2 = s * s;
-        for (int j = 0; j < n; ++j) w_out[i * n + j] = x[j] / s2;
+        for (int j = 0; j < n; ++j) w_out[t * n + j] = x[j] / s2;
     }
     free(a);
     return OR_OK;
+}
+
+int or_phs_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, int n, int k, int ell,
+                   double* w_out) {
+    return phs_weights_rows(xyz, nrm, N, idx, n, k, ell, NULL, 0, w_out);
+}
+
+int or_phs_weights_rows(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, int n, int k, int ell,
+                        const int32_t* rows, int64_t nrows, double* w_out) {
+    return phs_weights_rows(xyz, nrm, N, idx, n, k, ell, rows, nrows, w_out);
 }
 
 /* ===========================================================================================

@@ -267,6 +267,7 @@ const char* mgm_status_string(mgm_status s) {
 
 const char* mgm_last_error_message(void) { return error_message(); }
 int64_t mgm_last_error_row(void) { return bad_row(); }
+int64_t mgm_last_weights_fp64_rows(void) { return fp64_rows(); }
 
 }  // extern "C"
 

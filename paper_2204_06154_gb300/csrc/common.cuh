@@ -18,6 +18,8 @@ void set_error(const std::string& msg);
 void set_bad_row(int64_t row);
 const char* error_message();
 int64_t bad_row();
+void set_fp64_rows(int64_t n);
+int64_t fp64_rows();
 
 struct Fail {
     mgm_status st;

@@ -65,25 +65,18 @@ struct PhsArgs {
     double* wy;               // d/dy^ weights (grad only)
     int grad;                 // 0: Laplace-Beltrami (Sec. 2.2); 1: tangent-plane first derivatives
     unsigned long long* bad;  // lowest singular row
+    const int32_t* rows;      // nullptr: stencils 0..N-1; else the nrows stencils rows[0..nrows-1]
+    int64_t nrows;
 };
 
-__global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
-    extern __shared__ __align__(16) double sm_phs[];
-    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const int n = a.n, m = a.m, L = a.L, nr = a.grad ? 2 : 1, ld = m + nr;
-    const size_t per = (size_t)m * ld + 2 * n + 2 * m;
-    double* A = sm_phs + per * wi;
-    double* xh = A + (size_t)m * ld;
-    double* yh = xh + n;
-    double* xs = yh + n;
-    double* rinvs = xs + m;
-    const int64_t i = (int64_t)blockIdx.x * wpb + wi;
-    if (i >= a.N) return;
+// Tangent-plane coordinates of stencil i (eq. (tp_pts)), divided by the support radius s, which is
+// returned (0 when the stencil is degenerate). Warp-cooperative; xh, yh in shared memory.
+__device__ __forceinline__ double stencil_coords(const PhsArgs& a, int64_t i, int lane, double* xh, double* yh) {
+    const int n = a.n;
     const int32_t* id = a.idx + i * n;
     double t1[3], t2[3];
     tangent_basis(a.nrm + 3 * i, t1, t2);
     const double* xc = a.xyz + 3 * i;
-    // eq. (tp_pts): projected coordinates and support radius s
     double s = 0.0;
     for (int j = lane; j < n; j += 32) {
         const double* xj = a.xyz + 3 * (int64_t)id[j];
@@ -95,14 +88,45 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
         s = fmax(s, r);
     }
     s = warp_max_d(s);
-    if (!(s > 0.0)) {
-        if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
-        return;
-    }
+    if (!(s > 0.0)) return 0.0;
     const double sinv = 1.0 / s;
     __syncwarp();
     for (int j = lane; j < n; j += 32) { xh[j] = xh[j] * sinv; yh[j] = yh[j] * sinv; }
     __syncwarp();
+    return s;
+}
+
+// row r and column c of the flat index e of the upper triangle (r <= c) of an n x n matrix
+__device__ __forceinline__ void tri_rc(int e, int n, int* rr, int* cc) {
+    // row r of the upper triangle starts at r*n - r*(r-1)/2
+    const float nf = 2.0f * n + 1.0f;
+    int r = (int)((nf - sqrtf(nf * nf - 8.0f * (float)e)) * 0.5f);
+    r = max(0, min(r, n - 1));
+    while (r > 0 && r * n - r * (r - 1) / 2 > e) --r;
+    while (r + 1 < n && (r + 1) * n - (r + 1) * r / 2 <= e) ++r;
+    *rr = r;
+    *cc = r + (e - (r * n - r * (r - 1) / 2));
+}
+
+__global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
+    extern __shared__ __align__(16) double sm_phs[];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int n = a.n, m = a.m, L = a.L, nr = a.grad ? 2 : 1, ld = m + nr;
+    const size_t per = (size_t)m * ld + 2 * n + 2 * m;
+    double* A = sm_phs + per * wi;
+    double* xh = A + (size_t)m * ld;
+    double* yh = xh + n;
+    double* xs = yh + n;
+    double* rinvs = xs + m;
+    const int64_t t = (int64_t)blockIdx.x * wpb + wi;
+    if (t >= (a.rows ? a.nrows : a.N)) return;
+    const int64_t i = a.rows ? (int64_t)a.rows[t] : t;
+    // eq. (tp_pts): projected coordinates and support radius s
+    const double s = stencil_coords(a, i, lane, xh, yh);
+    if (!(s > 0.0)) {
+        if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
+        return;
+    }
     // saddle matrix [A P; P^T 0 | rhs]. The PHS block is symmetric: each pair (r <= c) is
     // evaluated once (xh_c - xh_r is exactly -(xh_r - xh_c), so the mirror holds the same IEEE
     // value); the triangle is enumerated flat so all lanes stay busy. Magnitudes are compared as
@@ -110,13 +134,8 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
     unsigned long long amaxb = 0;
     const int tri = n * (n + 1) / 2;
     for (int e = lane; e < tri; e += 32) {
-        // row r of the upper triangle starts at r*n - r*(r-1)/2
-        const float nf = 2.0f * n + 1.0f;
-        int r = (int)((nf - sqrtf(nf * nf - 8.0f * (float)e)) * 0.5f);
-        r = max(0, min(r, n - 1));
-        while (r > 0 && r * n - r * (r - 1) / 2 > e) --r;
-        while (r + 1 < n && (r + 1) * n - (r + 1) * r / 2 <= e) ++r;
-        const int c = r + (e - (r * n - r * (r - 1) / 2));
+        int r, c;
+        tri_rc(e, n, &r, &c);
         double dx = xh[r] - xh[c], dy = yh[r] - yh[c];
         double v = phs(dx * dx + dy * dy, a.k);
         A[r * ld + c] = v;
@@ -236,6 +255,502 @@ __global__ void __launch_bounds__(256) phs_weights_k(PhsArgs a, int wpb) {
             for (int j = lane; j < n; j += 32) out[i * n + j] = xs[j] / s;
         }
         __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Mixed-precision PHS weights: the same saddle system K x = b, factorised once in FP32 (LU with
+// partial pivoting) and solved by iterative refinement with FP64 residuals (the classical scheme
+// analysed by Wilkinson and by Moler, 1967): x_0 = LU \ b, then r = b - K x_j in FP64,
+// d = LU \ r in FP32, x_{j+1} = x_j + d, until the correction of the weight block is below 1e-12
+// of the weights. Each step shrinks the error by about cond(K) eps_32 (~1e-3 for these stencils,
+// cond(K) ~ 1e4 with scaled coordinates), so three or four steps reach the FP64 solution; what
+// remains is FP64 rounding, of the same size as that of the elimination in phs_weights_k.
+// The work moves from the FP64 pipe (2(m^3)/3 flops of elimination) to the FP32 pipes; FP64 keeps
+// the matrix entries (m^2/2 square roots) and m n + n L multiply-adds per residual.
+// A stencil that does not converge in IR_MAXIT steps, or meets an FP32 pivot below 2^-20 of its
+// largest entry, is listed and solved again by phs_weights_k, which also decides singularity.
+// Per warp in shared memory: the rows 0..n-1 of K = [A P] in FP64 (A is symmetric, so column i of
+// these rows is row i of K restricted to its first n columns), the m x m FP32 copy that is
+// factorised (multipliers below the diagonal), x, b, r in FP64, 1/u_kk and the row permutation.
+// Strides are odd so that a warp reading a column touches distinct banks.
+// ---------------------------------------------------------------------------------------------
+constexpr int IR_MAXIT = 8;
+
+struct IrLayout {
+    size_t kd, xs, bd, rd, xh, yh, f, rinv, perm, bytes;
+};
+__host__ __device__ inline IrLayout ir_layout(int n, int m) {
+    IrLayout o;
+    const size_t ldd = (size_t)(m | 1), ldf = (size_t)(m | 1);
+    size_t off = 0;
+    o.kd = off; off += 8 * n * ldd;
+    o.xs = off; off += 8 * (size_t)m;
+    o.bd = off; off += 8 * (size_t)m;
+    o.rd = off; off += 8 * (size_t)m;
+    o.xh = off; off += 8 * (size_t)n;
+    o.yh = off; off += 8 * (size_t)n;
+    o.f = off; off += 4 * m * ldf;
+    o.rinv = off; off += 4 * (size_t)m;
+    o.perm = off; off += 4 * (size_t)m;
+    o.bytes = (off + 15) & ~(size_t)15;
+    return o;
+}
+
+__device__ __forceinline__ unsigned mag_bits_f(float v) {
+    unsigned b = __float_as_uint(v) & 0x7fffffffu;
+    return b > 0x7f800000u ? 0u : b;
+}
+
+template <int Q>
+__device__ __forceinline__ float pick(const float (&z)[Q], int q) {
+    float v = z[0];
+#pragma unroll
+    for (int p = 1; p < Q; ++p)
+        if (q == p) v = z[p];
+    return v;
+}
+
+// z = U^-1 L^-1 (P src) in FP32 with the factors in F (unit lower triangle below the diagonal);
+// lane holds rows lane + 32 q in z[q]
+template <int Q>
+__device__ __forceinline__ void ir_solve(const float* F, int ldf, const float* rinv, const int* perm, const double* src,
+                                         int m, int lane, float (&z)[Q]) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int r = lane + 32 * q;
+        z[q] = r < m ? (float)src[perm[r]] : 0.0f;
+    }
+    for (int kk = 0; kk < m; ++kk) {
+        const float zk = __shfl_sync(0xffffffffu, pick(z, kk >> 5), kk & 31);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int r = lane + 32 * q;
+            if (r > kk && r < m) z[q] = fmaf(-F[r * ldf + kk], zk, z[q]);
+        }
+    }
+    for (int kk = m - 1; kk >= 0; --kk) {
+        const float xk = __shfl_sync(0xffffffffu, pick(z, kk >> 5), kk & 31) * rinv[kk];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int r = lane + 32 * q;
+            if (r == kk) z[q] = xk;
+            else if (r < kk) z[q] = fmaf(-F[r * ldf + kk], xk, z[q]);
+        }
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) phs_weights_ir_k(PhsArgs a, int wpb, int32_t* retry, int* nretry) {
+    extern __shared__ __align__(16) unsigned char sm_ir[];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int n = a.n, m = a.m, L = a.L, ldd = m | 1, ldf = m | 1;
+    const IrLayout lay = ir_layout(n, m);
+    unsigned char* base = sm_ir + lay.bytes * wi;
+    double* Kd = (double*)(base + lay.kd);
+    double* xs = (double*)(base + lay.xs);
+    double* bd = (double*)(base + lay.bd);
+    double* rd = (double*)(base + lay.rd);
+    double* xh = (double*)(base + lay.xh);
+    double* yh = (double*)(base + lay.yh);
+    float* F = (float*)(base + lay.f);
+    float* rinv = (float*)(base + lay.rinv);
+    int* perm = (int*)(base + lay.perm);
+    const int64_t i = (int64_t)blockIdx.x * wpb + wi;
+    if (i >= a.N) return;
+    const double s = stencil_coords(a, i, lane, xh, yh);
+    if (!(s > 0.0)) {
+        if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
+        return;
+    }
+    // K and b (eq. (rbf_fd_lap)), in FP64 and as the FP32 copy
+    unsigned amaxb = 0;
+    const int tri = n * (n + 1) / 2;
+    for (int e = lane; e < tri; e += 32) {
+        int r, c;
+        tri_rc(e, n, &r, &c);
+        double dx = xh[r] - xh[c], dy = yh[r] - yh[c];
+        double v = phs(dx * dx + dy * dy, a.k);
+        Kd[r * ldd + c] = v;
+        Kd[c * ldd + r] = v;
+        const float f = (float)v;
+        F[r * ldf + c] = f;
+        F[c * ldf + r] = f;
+        amaxb = max(amaxb, mag_bits_f(f));
+    }
+    for (int e = lane; e < n * (L + 1); e += 32) {
+        int r = e / (L + 1), t = e - r * (L + 1);
+        if (t < L) {
+            int pa, pb;
+            mono_pow(t, &pa, &pb);
+            double v = monomial(xh[r], yh[r], pa, pb);
+            Kd[r * ldd + n + t] = v;
+            const float f = (float)v;
+            F[r * ldf + n + t] = f;
+            F[(n + t) * ldf + r] = f;
+            amaxb = max(amaxb, mag_bits_f(f));
+        } else {
+            bd[r] = phs_lap(xh[r] * xh[r] + yh[r] * yh[r], a.k);
+        }
+    }
+    for (int e = lane; e < L * L; e += 32) {
+        int t = e / L, c = e - t * L;
+        F[(n + t) * ldf + n + c] = 0.0f;
+    }
+    for (int t = lane; t < L; t += 32) {
+        int pa, pb;
+        mono_pow(t, &pa, &pb);
+        bd[n + t] = ((pa == 2 && pb == 0) || (pa == 0 && pb == 2)) ? 2.0 : 0.0;
+    }
+    for (int j = lane; j < m; j += 32) perm[j] = j;
+    for (int o = 16; o; o >>= 1) amaxb = max(amaxb, __shfl_xor_sync(0xffffffffu, amaxb, o));
+    const unsigned tolb = __float_as_uint(ldexpf(__uint_as_float(amaxb), -20));
+    __syncwarp();
+    // FP32 LU with partial pivoting (first row of maximal |f_rk|)
+    bool ok = true;
+    for (int kk = 0; kk < m; ++kk) {
+        unsigned best = 0;
+        int piv = m;
+        for (int r = kk + lane; r < m; r += 32) {
+            unsigned v = mag_bits_f(F[r * ldf + kk]);
+            if (piv == m || v > best) { best = v; piv = r; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            unsigned ob = __shfl_xor_sync(0xffffffffu, best, o);
+            int op = __shfl_xor_sync(0xffffffffu, piv, o);
+            if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+        }
+        if (!(best > tolb)) { ok = false; break; }  // warp-uniform after the reduction
+        if (piv != kk) {
+            for (int j = lane; j < m; j += 32) {
+                float t = F[kk * ldf + j];
+                F[kk * ldf + j] = F[piv * ldf + j];
+                F[piv * ldf + j] = t;
+            }
+            if (lane == 0) {
+                int t = perm[kk];
+                perm[kk] = perm[piv];
+                perm[piv] = t;
+            }
+        }
+        __syncwarp();
+        const float rk = 1.0f / F[kk * ldf + kk];
+        if (lane == 0) rinv[kk] = rk;
+        for (int r = kk + 1 + lane; r < m; r += 32) F[r * ldf + kk] = F[r * ldf + kk] * rk;
+        __syncwarp();
+        for (int cb = kk + 1; cb < m; cb += 32) {
+            const int c = cb + lane;
+            const bool act = c < m;
+            const float pk = act ? F[kk * ldf + c] : 0.0f;
+            int r = kk + 1;
+            for (; r + 3 < m; r += 4) {
+                const float l0 = F[r * ldf + kk], l1 = F[(r + 1) * ldf + kk], l2 = F[(r + 2) * ldf + kk],
+                            l3 = F[(r + 3) * ldf + kk];
+                if (act) {
+                    float v0 = F[r * ldf + c], v1 = F[(r + 1) * ldf + c], v2 = F[(r + 2) * ldf + c],
+                          v3 = F[(r + 3) * ldf + c];
+                    F[r * ldf + c] = fmaf(-l0, pk, v0);
+                    F[(r + 1) * ldf + c] = fmaf(-l1, pk, v1);
+                    F[(r + 2) * ldf + c] = fmaf(-l2, pk, v2);
+                    F[(r + 3) * ldf + c] = fmaf(-l3, pk, v3);
+                }
+            }
+            for (; r < m; ++r) {
+                const float l0 = F[r * ldf + kk];
+                if (act) F[r * ldf + c] = fmaf(-l0, pk, F[r * ldf + c]);
+            }
+        }
+        __syncwarp();
+    }
+    bool conv = false;
+    if (ok) {
+        float z[Q];
+        ir_solve<Q>(F, ldf, rinv, perm, bd, m, lane, z);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            if (lane + 32 * q < m) xs[lane + 32 * q] = (double)z[q];
+        __syncwarp();
+        for (int it = 0; it < IR_MAXIT; ++it) {
+            // r = b - K x in FP64; row i reads column i of the stored rows (A symmetric)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int r = lane + 32 * q;
+                if (r < m) {
+                    double acc = bd[r];
+                    for (int j = 0; j < n; ++j) acc = fma(-Kd[j * ldd + r], xs[j], acc);
+                    if (r < n)
+                        for (int t = 0; t < L; ++t) acc = fma(-Kd[r * ldd + n + t], xs[n + t], acc);
+                    rd[r] = acc;
+                }
+            }
+            __syncwarp();
+            ir_solve<Q>(F, ldf, rinv, perm, rd, m, lane, z);
+            double dmax = 0.0, xmax = 0.0;
+            bool fin = true;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int r = lane + 32 * q;
+                if (r < m) {
+                    const double d = (double)z[q];
+                    const double xn = xs[r] + d;
+                    xs[r] = xn;
+                    fin = fin && isfinite(xn);
+                    if (r < n) {
+                        dmax = fmax(dmax, fabs(d));
+                        xmax = fmax(xmax, fabs(xn));
+                    }
+                }
+            }
+            dmax = warp_max_d(dmax);
+            xmax = warp_max_d(xmax);
+            fin = __all_sync(0xffffffffu, fin);
+            __syncwarp();
+            if (!fin) break;
+            if (dmax <= 1e-12 * xmax) {
+                conv = true;
+                break;
+            }
+        }
+    }
+    if (conv) {
+        const double s2 = s * s;
+        for (int j = lane; j < n; j += 32) a.w[i * n + j] = xs[j] / s2;
+    } else if (lane == 0) {
+        retry[atomicAdd(nretry, 1)] = (int32_t)i;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The same refinement with the FP32 factorisation held in registers, for the two stencil shapes
+// used most (m = 36: n = 30, ell = 2; m = 60: n = 50, ell = 3). Lane l holds rows l and l + 32 of
+// the saddle matrix (all m columns, fully unrolled so every register index is static). Partial
+// pivoting is implicit: rows stay in their lanes, a row chosen as pivot is marked done and keeps
+// its U row, the others store their multipliers in place; the triangular solves follow the
+// recorded pivot order. Shared memory keeps only the FP64 rows of [A P] for the residuals, so
+// several times more warps fit on an SM than with the shared-memory factorisation.
+// ---------------------------------------------------------------------------------------------
+// FP32 value of an FP64 number rounded toward zero, by integer operations on its IEEE-754 fields
+// (the FP64 pipe is the scarce one). Magnitudes below FP32's normal range give a signed zero, above
+// it infinity; the factorisation only needs K to FP32 accuracy.
+__device__ __forceinline__ float d2f_trunc(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((unsigned)e << 23) | mant);
+}
+
+struct RlLayout {
+    size_t kd, xs, bd, xh, yh, rinv, piv, bytes;
+};
+__host__ __device__ inline RlLayout rl_layout(int n, int m) {
+    RlLayout o;
+    const size_t ldd = (size_t)(m | 1);
+    size_t off = 0;
+    o.kd = off; off += 8 * n * ldd;
+    o.xs = off; off += 8 * (size_t)m;
+    o.bd = off; off += 8 * (size_t)m;
+    o.xh = off; off += 8 * (size_t)n;
+    o.yh = off; off += 8 * (size_t)n;
+    o.rinv = off; off += 4 * (size_t)m;
+    o.piv = off; off += 4 * (size_t)m;
+    o.bytes = (off + 15) & ~(size_t)15;
+    return o;
+}
+
+// z <- U^-1 L^-1 P z with the register factors; on return x0, x1 hold solution components lane and
+// lane + 32. s0, s1: the step at which each row became the pivot (M: never).
+template <int M>
+__device__ __forceinline__ void rl_solve(const float (&a0)[M], const float (&a1)[M], int s0, int s1, const int* piv,
+                                         const float* rinv, float z0, float z1, float& x0, float& x1, int lane) {
+#pragma unroll
+    for (int kk = 0; kk < M; ++kk) {
+        const int p = piv[kk];
+        const float y = __shfl_sync(0xffffffffu, p >= 32 ? z1 : z0, p & 31);
+        if (s0 > kk) z0 = fmaf(-a0[kk], y, z0);
+        if (s1 > kk) z1 = fmaf(-a1[kk], y, z1);
+    }
+#pragma unroll
+    for (int kk = M - 1; kk >= 0; --kk) {
+        const int p = piv[kk];
+        const float xk = __shfl_sync(0xffffffffu, p >= 32 ? z1 : z0, p & 31) * rinv[kk];
+        if (s0 < kk) z0 = fmaf(-a0[kk], xk, z0);
+        if (s1 < kk) z1 = fmaf(-a1[kk], xk, z1);
+        if (lane == (kk & 31)) {
+            if (kk < 32) x0 = xk;
+            else x1 = xk;
+        }
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) phs_weights_rl_k(PhsArgs a, int wpb, int32_t* retry, int* nretry) {
+    static_assert(M <= 64, "two rows a lane");
+    constexpr int LDD = M | 1;
+    extern __shared__ __align__(16) unsigned char sm_rl[];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int n = a.n, L = M - n;
+    const RlLayout lay = rl_layout(n, M);
+    unsigned char* base = sm_rl + lay.bytes * wi;
+    double* Kd = (double*)(base + lay.kd);
+    double* xs = (double*)(base + lay.xs);
+    double* bd = (double*)(base + lay.bd);
+    double* xh = (double*)(base + lay.xh);
+    double* yh = (double*)(base + lay.yh);
+    float* rinv = (float*)(base + lay.rinv);
+    int* piv = (int*)(base + lay.piv);
+    const int64_t i = (int64_t)blockIdx.x * wpb + wi;
+    if (i >= a.N) return;
+    const double s = stencil_coords(a, i, lane, xh, yh);
+    if (!(s > 0.0)) {
+        if (lane == 0) atomicMin(a.bad, (unsigned long long)i);
+        return;
+    }
+    // rows 0..n-1 of K = [A P] and b in FP64 (eq. (rbf_fd_lap))
+    unsigned long long amaxb = 0;
+    const int tri = n * (n + 1) / 2;
+    for (int e = lane; e < tri; e += 32) {
+        int r, c;
+        tri_rc(e, n, &r, &c);
+        double dx = xh[r] - xh[c], dy = yh[r] - yh[c];
+        double v = phs(dx * dx + dy * dy, a.k);
+        Kd[r * LDD + c] = v;
+        Kd[c * LDD + r] = v;
+        amaxb = max(amaxb, mag_bits(v));
+    }
+    for (int e = lane; e < n * L; e += 32) {  // separate loops: no divergent FP64 paths
+        int r = e / L, t = e - r * L;
+        int pa, pb;
+        mono_pow(t, &pa, &pb);
+        double v = monomial(xh[r], yh[r], pa, pb);
+        Kd[r * LDD + n + t] = v;
+        amaxb = max(amaxb, mag_bits(v));
+    }
+    for (int r = lane; r < n; r += 32) bd[r] = phs_lap(xh[r] * xh[r] + yh[r] * yh[r], a.k);
+    for (int t = lane; t < L; t += 32) {
+        int pa, pb;
+        mono_pow(t, &pa, &pb);
+        bd[n + t] = ((pa == 2 && pb == 0) || (pa == 0 && pb == 2)) ? 2.0 : 0.0;
+    }
+    for (int o = 16; o; o >>= 1) amaxb = max(amaxb, __shfl_xor_sync(0xffffffffu, amaxb, o));
+    const unsigned tolb = __float_as_uint(ldexpf((float)__longlong_as_double((long long)amaxb), -20));
+    __syncwarp();
+    // FP32 copy into registers: row r < n is row r of [A P]; row n + t is column n + t of it
+    // (P^T, then the zero block); rows >= M are absent
+    const int r0 = lane, r1 = lane + 32;
+    float a0[M], a1[M];
+    {
+        const double* p0 = r0 < n ? Kd + r0 * LDD : Kd + r0;
+        const double* p1 = r1 < n ? Kd + r1 * LDD : Kd + r1;
+        const int st0 = r0 < n ? 1 : LDD, st1 = r1 < n ? 1 : LDD;
+        const int lim0 = r0 < n ? M : (r0 < M ? n : 0), lim1 = r1 < n ? M : (r1 < M ? n : 0);
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            a0[c] = c < lim0 ? d2f_trunc(p0[c * st0]) : 0.0f;
+            a1[c] = c < lim1 ? d2f_trunc(p1[c * st1]) : 0.0f;
+        }
+    }
+    // FP32 LU with implicit partial pivoting (first row of maximal |a_rk| among rows not yet used)
+    bool d0 = r0 >= M, d1 = r1 >= M;
+    int s0 = M, s1 = M;
+    bool ok = true;
+#pragma unroll
+    for (int kk = 0; kk < M; ++kk) {
+        const unsigned b0 = d0 ? 0u : mag_bits_f(a0[kk]);
+        const unsigned b1 = d1 ? 0u : mag_bits_f(a1[kk]);
+        unsigned best = b0;
+        int prow = r0;
+        if (b1 > best) { best = b1; prow = r1; }
+        for (int o = 16; o; o >>= 1) {
+            const unsigned ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int op = __shfl_xor_sync(0xffffffffu, prow, o);
+            if (ob > best || (ob == best && op < prow)) { best = ob; prow = op; }
+        }
+        ok = ok && best > tolb;  // warp-uniform after the reduction; a failed factorisation is discarded
+        const int p = prow, pl = p & 31;
+        const bool hi = p >= 32;
+        if (p == r0) { d0 = true; s0 = kk; }
+        if (p == r1) { d1 = true; s1 = kk; }
+        const float rk = 1.0f / __shfl_sync(0xffffffffu, hi ? a1[kk] : a0[kk], pl);
+        if (lane == 0) {
+            piv[kk] = p;
+            rinv[kk] = rk;
+        }
+        const float l0 = d0 ? 0.0f : a0[kk] * rk;
+        const float l1 = d1 ? 0.0f : a1[kk] * rk;
+        if (!d0) a0[kk] = l0;
+        if (!d1) a1[kk] = l1;
+#pragma unroll
+        for (int c = 1; c < M; ++c) {  // constant bounds, so that both loops unroll fully
+            if (c > kk) {
+                const float v = __shfl_sync(0xffffffffu, hi ? a1[c] : a0[c], pl);
+                a0[c] = fmaf(-l0, v, a0[c]);
+                a1[c] = fmaf(-l1, v, a1[c]);
+            }
+        }
+    }
+    __syncwarp();
+    bool conv = false;
+    if (ok) {
+        for (int it = 0; it <= IR_MAXIT; ++it) {
+            // r = b - K x in FP64 (x = 0 at it = 0); row i reads column i of the stored rows
+            double q0 = 0.0, q1 = 0.0;
+            if (r0 < M) q0 = bd[r0];
+            if (r1 < M) q1 = bd[r1];
+            if (it > 0) {
+                for (int j = 0; j < n; ++j) {
+                    const double xj = xs[j];
+                    if (r0 < M) q0 = fma(-Kd[j * LDD + r0], xj, q0);
+                    if (r1 < M) q1 = fma(-Kd[j * LDD + r1], xj, q1);
+                }
+                for (int t = 0; t < L; ++t) {
+                    const double xt = xs[n + t];
+                    if (r0 < n) q0 = fma(-Kd[r0 * LDD + n + t], xt, q0);
+                    if (r1 < n) q1 = fma(-Kd[r1 * LDD + n + t], xt, q1);
+                }
+            }
+            float x0 = 0.0f, x1 = 0.0f;
+            rl_solve<M>(a0, a1, s0, s1, piv, rinv, (float)q0, (float)q1, x0, x1, lane);
+            __syncwarp();
+            // magnitudes compared as bits (FP32 for the correction), keeping the FP64 pipe free
+            unsigned dmb = 0;
+            unsigned long long xmb = 0;
+            bool fin = true;
+            if (r0 < M) {
+                const double xn = (it > 0 ? xs[r0] : 0.0) + (double)x0;
+                xs[r0] = xn;
+                const unsigned long long b = (unsigned long long)__double_as_longlong(xn) & 0x7fffffffffffffffull;
+                fin = fin && b < 0x7ff0000000000000ull && mag_bits_f(x0) == (__float_as_uint(x0) & 0x7fffffffu);
+                if (r0 < n) { dmb = max(dmb, mag_bits_f(x0)); xmb = max(xmb, b); }
+            }
+            if (r1 < M) {
+                const double xn = (it > 0 ? xs[r1] : 0.0) + (double)x1;
+                xs[r1] = xn;
+                const unsigned long long b = (unsigned long long)__double_as_longlong(xn) & 0x7fffffffffffffffull;
+                fin = fin && b < 0x7ff0000000000000ull && mag_bits_f(x1) == (__float_as_uint(x1) & 0x7fffffffu);
+                if (r1 < n) { dmb = max(dmb, mag_bits_f(x1)); xmb = max(xmb, b); }
+            }
+            for (int o = 16; o; o >>= 1) {
+                dmb = max(dmb, __shfl_xor_sync(0xffffffffu, dmb, o));
+                xmb = max(xmb, __shfl_xor_sync(0xffffffffu, xmb, o));
+            }
+            fin = __all_sync(0xffffffffu, fin);
+            __syncwarp();
+            if (!fin) break;
+            if (it > 0 && (double)__uint_as_float(dmb) <= 1e-12 * __longlong_as_double((long long)xmb)) {
+                conv = true;
+                break;
+            }
+        }
+    }
+    if (conv) {
+        const double s2 = s * s;
+        for (int j = lane; j < n; j += 32) a.w[i * n + j] = xs[j] / s2;
+    } else if (lane == 0) {
+        retry[atomicAdd(nretry, 1)] = (int32_t)i;
     }
 }
 
@@ -403,7 +918,8 @@ void surface_divergence(const double* nrm, int64_t N, const int32_t* idx, int n,
 }
 
 static void phs_launch(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, int n, int k, int ell, int L,
-                       double* w, double* wy, int grad, unsigned long long* bad, cudaStream_t s) {
+                       double* w, double* wy, int grad, unsigned long long* bad, cudaStream_t s,
+                       const int32_t* rows = nullptr, int64_t nrows = 0) {
     const int m = n + L, ld = m + (grad ? 2 : 1);
     if (m > MAX_M) fail(MGM_ERR_UNSUPPORTED, "n + (ell+1)(ell+2)/2 must be <= 128");
     const size_t per = sizeof(double) * ((size_t)m * ld + 2 * n + 2 * m);
@@ -411,9 +927,48 @@ static void phs_launch(const double* xyz, const double* nrm, int64_t N, const in
     if (wpb < 1) wpb = 1;
     const size_t smem = per * wpb;
     CK(cudaFuncSetAttribute(phs_weights_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PhsArgs a{xyz, nrm, idx, N, n, k, ell, L, m, w, wy, grad, bad};
-    phs_weights_k<<<grid_for(N, wpb), 32 * wpb, smem, s>>>(a, wpb);
+    PhsArgs a{xyz, nrm, idx, N, n, k, ell, L, m, w, wy, grad, bad, rows, nrows};
+    phs_weights_k<<<grid_for(rows ? nrows : N, wpb), 32 * wpb, smem, s>>>(a, wpb);
     CK_LAUNCH();
+}
+
+// FP32 LU + FP64 refinement, then FP64 elimination for the stencils it lists; returns their count
+static int64_t phs_mixed(const double* xyz, const double* nrm, int64_t N, const int32_t* idx, int n, int k, int ell,
+                         int L, double* w, unsigned long long* bad, cudaStream_t s) {
+    const int m = n + L;
+    if (m > MAX_M) fail(MGM_ERR_UNSUPPORTED, "n + (ell+1)(ell+2)/2 must be <= 128");
+    const IrLayout lay = ir_layout(n, m);
+    int wpb = (int)std::min<size_t>(8, (227 * 1024) / lay.bytes);
+    if (wpb < 1) wpb = 1;
+    const size_t smem = lay.bytes * wpb;
+    Temp<int32_t> retry(N, s);
+    Temp<int> nretry(1, s);
+    CK(cudaMemsetAsync(nretry.get(), 0, sizeof(int), s));
+    PhsArgs a{xyz, nrm, idx, N, n, k, ell, L, m, w, nullptr, 0, bad, nullptr, 0};
+    if (m == 36 || m == 60) {
+        // four warps a block: m = 60 takes 255 registers a thread (two blocks an SM), m = 36 about
+        // 160 (three blocks)
+        const RlLayout rl = rl_layout(n, m);
+        const int wr = (int)std::min<size_t>(4, (227 * 1024) / rl.bytes);
+        const size_t sm = rl.bytes * wr;
+        if (m == 36) {
+            CK(cudaFuncSetAttribute(phs_weights_rl_k<36>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            phs_weights_rl_k<36><<<grid_for(N, wr), 32 * wr, sm, s>>>(a, wr, retry.get(), nretry.get());
+        } else {
+            CK(cudaFuncSetAttribute(phs_weights_rl_k<60>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            phs_weights_rl_k<60><<<grid_for(N, wr), 32 * wr, sm, s>>>(a, wr, retry.get(), nretry.get());
+        }
+    } else if (m <= 64) {
+        CK(cudaFuncSetAttribute(phs_weights_ir_k<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        phs_weights_ir_k<2><<<grid_for(N, wpb), 32 * wpb, smem, s>>>(a, wpb, retry.get(), nretry.get());
+    } else {
+        CK(cudaFuncSetAttribute(phs_weights_ir_k<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        phs_weights_ir_k<4><<<grid_for(N, wpb), 32 * wpb, smem, s>>>(a, wpb, retry.get(), nretry.get());
+    }
+    CK_LAUNCH();
+    const int cnt = read1(nretry.get(), s);
+    if (cnt > 0) phs_launch(xyz, nrm, N, idx, n, k, ell, L, w, nullptr, 0, bad, s, retry.get(), cnt);
+    return cnt;
 }
 
 // tangent-plane first-derivative weights (PHS RBF-FD with the first-derivative right-hand sides)
@@ -444,12 +999,15 @@ void stencil_weights(const double* xyz, const double* nrm, int64_t N, const int3
     REQUIRE(ell >= 0 && ell <= 12, "ell out of range");
     const int L = (ell + 1) * (ell + 2) / 2;
     REQUIRE(n >= 1 && n <= N && L <= n, "stencil size n must satisfy (ell+1)(ell+2)/2 <= n <= N");
+    REQUIRE(sp->weights == MGM_WEIGHTS_F64 || sp->weights == MGM_WEIGHTS_MIXED, "unknown weights mode");
     set_bad_row(-1);
+    set_fp64_rows(0);
     Temp<unsigned long long> bad(1, s);
     CK(cudaMemsetAsync(bad.get(), 0xff, sizeof(unsigned long long), s));
     if (sp->method == MGM_RBF_FD) {
         REQUIRE(sp->k >= 1 && sp->k <= 8, "PHS order k must be in [1, 8]");
-        phs_launch(xyz, nrm, N, idx, n, sp->k, ell, L, w, nullptr, 0, bad.get(), s);
+        if (sp->weights == MGM_WEIGHTS_MIXED) set_fp64_rows(phs_mixed(xyz, nrm, N, idx, n, sp->k, ell, L, w, bad.get(), s));
+        else phs_launch(xyz, nrm, N, idx, n, sp->k, ell, L, w, nullptr, 0, bad.get(), s);
         check_bad(bad.get(), s, "PHS weights");
     } else if (sp->method == MGM_GFD) {
         REQUIRE(sp->alpha > 0.0, "GFD alpha must be > 0");

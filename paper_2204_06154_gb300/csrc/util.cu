@@ -20,6 +20,9 @@ void set_error(const std::string& msg) { g_msg = msg; }
 void set_bad_row(int64_t row) { g_row = row; }
 const char* error_message() { return g_msg.c_str(); }
 int64_t bad_row() { return g_row; }
+static thread_local int64_t g_fp64_rows = 0;
+void set_fp64_rows(int64_t n) { g_fp64_rows = n; }
+int64_t fp64_rows() { return g_fp64_rows; }
 void fail(mgm_status st, const std::string& msg) {
     set_error(msg);
     throw Fail{st};

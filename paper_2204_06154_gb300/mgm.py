@@ -33,7 +33,7 @@ class MGMError(RuntimeError):
 
 class StencilParams(C.Structure):
     _fields_ = [("method", C.c_int), ("k", C.c_int), ("ell", C.c_int), ("n", C.c_int), ("alpha", C.c_double),
-                ("mu", C.c_double), ("poisson", C.c_int)]
+                ("mu", C.c_double), ("poisson", C.c_int), ("weights", C.c_int)]
 
 
 class Params(C.Structure):
@@ -60,7 +60,7 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_solve_batched",
            "mgm_hierarchy_stats_get", "mgm_hierarchy_level", "mgm_hierarchy_pnnz", "mgm_profile",
            "mgm_kernel_launches", "mgm_check_bounded_wait", "mgm_destroy", "mgm_status_string", "mgm_last_error_message",
-           "mgm_last_error_row",
+           "mgm_last_error_row", "mgm_last_weights_fp64_rows",
            "mgm_mlp_size", "mgm_mlp_create", "mgm_mlp_destroy", "mgm_mlp_get", "mgm_mlp_set", "mgm_mlp_forward",
            "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
            "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
@@ -130,8 +130,11 @@ def lib():
         L.mgm_status_string.restype = C.c_char_p
         L.mgm_last_error_message.restype = C.c_char_p
         L.mgm_last_error_row.restype = C.c_int64
+        L.mgm_last_weights_fp64_rows.argtypes = []
+        L.mgm_last_weights_fp64_rows.restype = C.c_int64
         for name in EXPORTS:
             if name not in ("mgm_destroy", "mgm_status_string", "mgm_last_error_message", "mgm_last_error_row",
+                            "mgm_last_weights_fp64_rows",
                             "mgm_kernel_launches", "mgm_mlp_size", "mgm_mlp_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
@@ -181,13 +184,25 @@ def knn_noalloc(data, query, k, self_first=False, out=None):
     return out
 
 
-def _sp(n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, poisson=False):
-    return StencilParams(MGM_RBF_FD if method == "rbf" else MGM_GFD, k, ell, n, alpha, mu, int(poisson))
+_WEIGHTS = {"f64": 0, "mixed": 1}
 
 
-def stencil_weights(xyz, nrm, idx, method="rbf", k=1, ell=2, alpha=4.0):
+def _sp(n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, poisson=False, weights="f64"):
+    if weights not in _WEIGHTS:
+        raise ValueError(f"weights must be one of {sorted(_WEIGHTS)}")
+    return StencilParams(MGM_RBF_FD if method == "rbf" else MGM_GFD, k, ell, n, alpha, mu, int(poisson),
+                         _WEIGHTS[weights])
+
+
+def last_weights_fp64_rows():
+    """Stencils that the last weights call with weights="mixed" solved again in FP64."""
+    return int(lib().mgm_last_weights_fp64_rows())
+
+
+def stencil_weights(xyz, nrm, idx, method="rbf", k=1, ell=2, alpha=4.0, weights="f64"):
+    """weights="f64": FP64 elimination; "mixed": FP32 LU with FP64 iterative refinement (PHS only)."""
     xyz = _dev(xyz, torch.float64, "xyz"); nrm = _dev(nrm, torch.float64, "nrm"); idx = _dev(idx, torch.int32, "idx")
-    sp = _sp(idx.shape[1], method, k, ell, 1.0, alpha)
+    sp = _sp(idx.shape[1], method, k, ell, 1.0, alpha, weights=weights)
     w = torch.empty(idx.shape, dtype=torch.float64, device=xyz.device)
     _check(lib().mgm_stencil_weights(_p(xyz), _p(nrm), xyz.shape[0], _p(idx), C.byref(sp), _p(w), _stream()))
     return w
@@ -231,11 +246,12 @@ def assemble(idx, w, mu=1.0, poisson=False):
     return rp, ci, v
 
 
-def build_stencils(xyz, nrm, n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, poisson=False, keep_weights=True):
+def build_stencils(xyz, nrm, n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, poisson=False, keep_weights=True,
+                   weights="f64"):
     xyz = _dev(xyz, torch.float64, "xyz"); nrm = _dev(nrm, torch.float64, "nrm")
     N = xyz.shape[0]
     dev = xyz.device
-    sp = _sp(n, method, k, ell, mu, alpha, poisson)
+    sp = _sp(n, method, k, ell, mu, alpha, poisson, weights)
     idx = torch.empty((N, n), dtype=torch.int32, device=dev) if keep_weights else None
     w = torch.empty((N, n), dtype=torch.float64, device=dev) if keep_weights else None
     rp = torch.empty(N + 1, dtype=torch.int32, device=dev)

@@ -74,6 +74,55 @@ def test_phs_weights(M, oracle, case):
     assert rel.max() <= 1e-12, rel.max()
 
 
+@pytest.mark.parametrize("case", ["c1", "c2like", "k3ell3", "m91"])
+def test_phs_weights_mixed(M, oracle, case):
+    """FP32 LU with FP64 iterative refinement: the FP64 solution of the same saddle systems, within
+    1e-12 of the oracle's elimination. m91 (n = 70, ell = 5) takes the four-rows-a-lane solve."""
+    if case == "c1":
+        x, nrm = I.icosahedral_sphere(5); n, k, ell = 30, 1, 2
+    elif case == "c2like":
+        x, nrm = I.torus_grid(12000, jitter=0.1, seed=2); n, k, ell = 50, 1, 3
+    elif case == "k3ell3":
+        x, nrm = I.fibonacci_sphere(6000, 0.1, 9); n, k, ell = 20, 3, 3
+    else:
+        x, nrm = I.fibonacci_sphere(5003, 0.1, 4); n, k, ell = 70, 1, 5
+    idx = oracle.knn(x, x, n, self_first=True)
+    ref = oracle.phs_weights(x, nrm, idx, k, ell)
+    got = H(M.stencil_weights(T(x), T(nrm), T(idx), "rbf", k, ell, weights="mixed"))
+    fb = M.last_weights_fp64_rows()
+    rel = _rowrel(got, ref)
+    assert rel.max() <= 1e-12, (rel.max(), fb)
+    if case in ("c1", "c2like"):
+        assert fb <= 0.001 * x.shape[0], fb   # the refinement converges on these stencils
+
+
+def test_phs_weights_mixed_fallback(M, oracle):
+    """Near-twin nodes (1e-9 apart, spacing ~0.06) make stencils that FP32 cannot factorise; they
+    are solved again by FP64 elimination, and every row still matches the oracle."""
+    x, nrm = I.fibonacci_sphere(3001, 0.1, 5)
+    rng = np.random.default_rng(3)
+    src = rng.choice(3001, 40, replace=False)
+    t1 = np.cross(nrm[src], [0.0, 0.0, 1.0])
+    t1 /= np.linalg.norm(t1, axis=1, keepdims=True)
+    tw = x[src] + 1e-9 * t1
+    x = np.concatenate([x, tw / np.linalg.norm(tw, axis=1, keepdims=True)])
+    nrm = x / np.linalg.norm(x, axis=1, keepdims=True)
+    idx = oracle.knn(x, x, 30, self_first=True)
+    ref = oracle.phs_weights(x, nrm, idx, 1, 2)
+    got = H(M.stencil_weights(T(x), T(nrm), T(idx), "rbf", 1, 2, weights="mixed"))
+    fb = M.last_weights_fp64_rows()
+    g64 = H(M.stencil_weights(T(x), T(nrm), T(idx), "rbf", 1, 2))
+    assert M.last_weights_fp64_rows() == 0
+    # stencils holding a node and its twin (cond(K) ~ 1e10)
+    pair = np.zeros(x.shape[0], bool)
+    for t, s0 in enumerate(src):
+        pair |= np.isin(idx, [s0, 3001 + t]).sum(axis=1) == 2
+    assert fb >= pair.sum() > 0, (fb, pair.sum())
+    assert np.array_equal(got[pair], g64[pair])          # solved by the FP64 path
+    assert _rowrel(got[~pair], ref[~pair]).max() <= 1e-12
+    assert _rowrel(g64[pair], ref[pair]).max() <= 1e-5   # FP64 rounding times cond(K)
+
+
 def test_gfd_weights(M, oracle):
     x, nrm = I.bumpy_sphere(8000, seed=3)
     idx = oracle.knn(x, x, 25, self_first=True)
@@ -90,11 +139,12 @@ def test_build_stencils_assembly_exact(M, oracle, ico5):
     assert np.max(np.abs(H(v) - L.data)) <= 1e-12 * np.max(np.abs(L.data))
 
 
-def test_singular_stencil_row(M):
+@pytest.mark.parametrize("weights", ["f64", "mixed"])
+def test_singular_stencil_row(M, weights):
     x = np.zeros((64, 3)); x[:, 0] = np.linspace(0, 1, 64)
     nrm = np.tile([0.0, 0.0, 1.0], (64, 1))
     with pytest.raises(M.MGMError) as e:
-        M.build_stencils(T(x), T(nrm), 20, "rbf", 1, 2, 1.0)
+        M.build_stencils(T(x), T(nrm), 20, "rbf", 1, 2, 1.0, weights=weights)
     assert e.value.status == 2 and e.value.row == 0
 
 

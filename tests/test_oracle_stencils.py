@@ -199,3 +199,19 @@ def test_singular_stencil_reported(oracle):
     with pytest.raises(oracle.OracleError) as e:
         oracle.phs_weights(x, nrm, idx, 1, 2)
     assert e.value.status == 2 and e.value.row == 0
+
+
+def test_weights_of_a_row_subset(oracle):
+    """The row-subset entry returns the same rows as the full computation, and rejects a stencil
+    table that does not hold one row per centre."""
+    x, nrm = I.fibonacci_sphere(1500, jitter=0.1, seed=4)
+    idx = oracle.knn(x, x, 30, self_first=True)
+    w = oracle.phs_weights(x, nrm, idx, 1, 2)
+    rows = np.array([1499, 0, 17, 17, 800], np.int32)
+    assert np.array_equal(oracle.phs_weights(x, nrm, idx[rows], 1, 2, rows=rows), w[rows])
+    with pytest.raises(ValueError):
+        oracle.phs_weights(x, nrm, idx[:100], 1, 2)
+    with pytest.raises(ValueError):
+        oracle.phs_weights(x, nrm, idx, 1, 2, rows=rows)
+    with pytest.raises(oracle.OracleError):
+        oracle.phs_weights(x, nrm, idx[:1], 1, 2, rows=np.array([1500], np.int32))
