@@ -224,35 +224,118 @@ __global__ void colour_bounds_k(const int32_t* off, int nc, int nblocks, int64_t
 
 __device__ __forceinline__ int32_t pad4(int32_t x) { return (x + 3) & ~3; }
 
-// lengths of the split rows; err bit 1: same colour off-diagonal, bit 2: missing/zero diagonal
-__global__ void split_len_k(const int32_t* rp, const int32_t* ci, const double* v, const int32_t* col, const int32_t* ord,
-                            int64_t n, int single, int32_t* len, int32_t* nlo, int* err, unsigned long long* tot) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int32_t r = ord[s];
-    int32_t cr = single ? 0 : col[r];
-    int32_t nl = 0, nu = 0;
-    bool diag = false;
-    for (int32_t p = rp[r]; p < rp[r + 1]; ++p) {
-        int32_t j = ci[p];
-        if (j == r) { diag = v[p] != 0.0; continue; }
-        int32_t cj = single ? 1 : col[j];
-        if (cj == cr) atomicOr(err, 1);
-        if (cj < cr) ++nl; else ++nu;
+// lengths of the split rows; err bit 1: same colour off-diagonal, bit 2: missing/zero diagonal.
+// One warp per row (lanes over its entries); the block sums its rows' counts before one atomic.
+__global__ void __launch_bounds__(256) split_len_k(const int32_t* rp, const int32_t* ci, const double* v,
+                                                   const int32_t* col, const int32_t* ord, int64_t n, int single,
+                                                   int32_t* len, int32_t* nlo, int* err, unsigned long long* tot) {
+    __shared__ unsigned long long bt[2];
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 2) bt[threadIdx.x] = 0;
+    __syncthreads();
+    if (s < n) {
+        const int32_t r = ord[s];
+        const int32_t cr = single ? 0 : col[r];
+        int nl = 0, nu = 0;
+        bool diag = false, same = false;
+        for (int32_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+            const int32_t j = ci[p];
+            if (j == r) { diag = v[p] != 0.0; continue; }
+            const int32_t cj = single ? 1 : col[j];
+            same = same || cj == cr;
+            if (cj < cr) ++nl; else ++nu;
+        }
+        nl = warp_sum_i(nl);
+        nu = warp_sum_i(nu);
+        diag = __any_sync(0xffffffffu, diag);
+        same = __any_sync(0xffffffffu, same);
+        if (lane == 0) {
+            if (same) atomicOr(err, 1);
+            if (!diag) atomicOr(err, 2);
+            len[s] = pad4(nl) + pad4(nu);
+            nlo[s] = pad4(nl);
+            atomicAdd(&bt[0], (unsigned long long)nl);
+            atomicAdd(&bt[1], (unsigned long long)nu);
+        }
     }
-    if (!diag) atomicOr(err, 2);
-    atomicAdd(&tot[0], (unsigned long long)nl);
-    atomicAdd(&tot[1], (unsigned long long)nu);
-    len[s] = pad4(nl) + pad4(nu);
-    nlo[s] = pad4(nl);
+    __syncthreads();
+    if (threadIdx.x < 2 && bt[threadIdx.x]) atomicAdd(&tot[threadIdx.x], bt[threadIdx.x]);
 }
 
-__global__ void split_fill_k(const int32_t* rp, const int32_t* ci, const double* v, const int32_t* col, const int32_t* ord,
-                             const int32_t* inv, int64_t n, int single, const int32_t* lo, int32_t* mid, int32_t* sc,
-                             double* sv64, float* sv32, double* diag64, double* dinv64, float* diag32, float* dinv32) {
+// Rows in solve order: the lower part (earlier colours) then the upper part, each sorted by
+// solve-order column and padded to a multiple of 4 with (own row, 0). One warp per row; the
+// entries are staged in shared memory and placed by rank (rows of up to SPLIT_MAX entries; longer
+// rows take the thread path below).
+constexpr int SPLIT_WARPS = 4, SPLIT_MAX = 256;
+__global__ void __launch_bounds__(SPLIT_WARPS * 32) split_fill_k(
+    const int32_t* rp, const int32_t* ci, const double* v, const int32_t* col, const int32_t* ord, const int32_t* inv,
+    int64_t n, int single, const int32_t* lo, int32_t* mid, int32_t* sc, double* sv64, float* sv32, double* diag64,
+    double* dinv64, float* diag32, float* dinv32, int* longrows) {
+    __shared__ unsigned long long key[SPLIT_WARPS][SPLIT_MAX];  // (upper?, solve column) of each entry
+    __shared__ double val[SPLIT_WARPS][SPLIT_MAX];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * SPLIT_WARPS + w;
+    if (s >= n) return;
+    const int32_t r = ord[s];
+    const int32_t b = rp[r], e = rp[r + 1];
+    if (e - b > SPLIT_MAX) {
+        if (lane == 0) atomicAdd(longrows, 1);
+        return;
+    }
+    const int32_t cr = single ? 0 : col[r];
+    double d = 0.0;
+    int nl = 0;
+    for (int32_t p = b + lane; p < e; p += 32) {
+        const int32_t j = ci[p];
+        unsigned long long k = ~0ull;  // the diagonal sorts last and is not placed
+        if (j == r) d = v[p];
+        else {
+            const int32_t cj = single ? 1 : col[j];
+            const unsigned long long up = cj < cr ? 0ull : 1ull;
+            if (!up) ++nl;
+            k = (up << 32) | (unsigned)inv[j];
+        }
+        key[w][p - b] = k;
+        val[w][p - b] = v[p];
+    }
+    nl = warp_sum_i(nl);
+    for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);  // one lane holds it, the others 0
+    __syncwarp();
+    const int32_t len = e - b, q0 = lo[s], qm = q0 + pad4(nl);
+    for (int32_t t = lane; t < len; t += 32) {
+        const unsigned long long k = key[w][t];
+        if (k == ~0ull) continue;
+        int rank = 0;
+        for (int32_t u = 0; u < len; ++u) rank += key[w][u] < k ? 1 : 0;
+        const bool up = (k >> 32) != 0;
+        const int32_t pos = up ? qm + (rank - nl) : q0 + rank;
+        sc[pos] = (int32_t)(k & 0xffffffffull);
+        sv64[pos] = val[w][t];
+        sv32[pos] = (float)val[w][t];
+    }
+    const int32_t nu = len - nl - 1 >= 0 ? len - nl - 1 : 0;
+    const int32_t qe = qm + pad4(nu);
+    for (int32_t t = q0 + nl + lane; t < qm; t += 32) { sc[t] = (int32_t)s; sv64[t] = 0.0; sv32[t] = 0.0f; }
+    for (int32_t t = qm + nu + lane; t < qe; t += 32) { sc[t] = (int32_t)s; sv64[t] = 0.0; sv32[t] = 0.0f; }
+    if (lane == 0) {
+        mid[s] = qm;
+        diag64[s] = d;
+        dinv64[s] = 1.0 / d;
+        diag32[s] = (float)d;
+        dinv32[s] = (float)(1.0 / d);
+    }
+}
+
+// rows longer than SPLIT_MAX: one thread per row, insertion into place
+__global__ void split_fill_long_k(const int32_t* rp, const int32_t* ci, const double* v, const int32_t* col,
+                                  const int32_t* ord, const int32_t* inv, int64_t n, int single, const int32_t* lo,
+                                  int32_t* mid, int32_t* sc, double* sv64, float* sv32, double* diag64, double* dinv64,
+                                  float* diag32, float* dinv32) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int32_t r = ord[s];
+    if (rp[r + 1] - rp[r] <= SPLIT_MAX) return;
     int32_t cr = single ? 0 : col[r];
     int32_t b = lo[s];
     int32_t q = b;
@@ -309,8 +392,8 @@ static void build_solve_layout(Level& L, bool single, cudaStream_t s) {
     Temp<unsigned long long> tot(2, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
     CK(cudaMemsetAsync(tot.get(), 0, 2 * sizeof(unsigned long long), s));
-    split_len_k<<<grid_for(n, 256), 256, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(), n,
-                                                 single ? 1 : 0, len.get(), nlo.get(), err.get(), tot.get());
+    split_len_k<<<grid_for(n, 8), 256, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(), n,
+                                               single ? 1 : 0, len.get(), nlo.get(), err.get(), tot.get());
     CK_LAUNCH();
     unsigned long long th[2];
     to_host(th, tot.get(), 2, s);
@@ -327,10 +410,20 @@ static void build_solve_layout(Level& L, bool single, cudaStream_t s) {
     L.sv64.alloc(std::max<int64_t>(L.snnz, 4));
     L.sv32.alloc(std::max<int64_t>(L.snnz, 4));
     L.diag64.alloc(n); L.dinv64.alloc(n); L.diag32.alloc(n); L.dinv32.alloc(n);
-    split_fill_k<<<grid_for(n, 128), 128, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(), L.inv.get(),
-                                                  n, single ? 1 : 0, L.lo.get(), L.mid.get(), L.sc.get(), L.sv64.get(),
-                                                  L.sv32.get(), L.diag64.get(), L.dinv64.get(), L.diag32.get(), L.dinv32.get());
+    Temp<int> longrows(1, s);
+    CK(cudaMemsetAsync(longrows.get(), 0, sizeof(int), s));
+    split_fill_k<<<grid_for(n, SPLIT_WARPS), SPLIT_WARPS * 32, 0, s>>>(
+        L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(), L.inv.get(), n, single ? 1 : 0, L.lo.get(),
+        L.mid.get(), L.sc.get(), L.sv64.get(), L.sv32.get(), L.diag64.get(), L.dinv64.get(), L.diag32.get(),
+        L.dinv32.get(), longrows.get());
     CK_LAUNCH();
+    if (read1(longrows.get(), s) > 0) {
+        split_fill_long_k<<<grid_for(n, 128), 128, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(),
+                                                           L.inv.get(), n, single ? 1 : 0, L.lo.get(), L.mid.get(),
+                                                           L.sc.get(), L.sv64.get(), L.sv32.get(), L.diag64.get(),
+                                                           L.dinv64.get(), L.diag32.get(), L.dinv32.get());
+        CK_LAUNCH();
+    }
 }
 
 // interpolation rows re-indexed to solve orders: compact CSR (for the transpose) and ELL

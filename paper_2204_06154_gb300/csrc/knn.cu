@@ -12,6 +12,7 @@
 // the definition asks for, independent of the grid and of scheduling. Distances are computed as
 // (dx*dx + dy*dy) + dz*dz without contraction (this file is built with --fmad=false).
 #include <algorithm>
+#include <cmath>
 #include <cfloat>
 
 #include "common.cuh"
@@ -287,6 +288,14 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
     }
 }
 
+__global__ void nonempty_cells_k(const int32_t* start, int64_t cells, int* out) {
+    int c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x)
+        c += start[i + 1] > start[i] ? 1 : 0;
+    c = warp_sum_i(c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 void knn_device(const double* data, int64_t nd, const double* query, int64_t nq, int k, int self_first,
                 int32_t* idx_out, double* d2_out, cudaStream_t s) {
     REQUIRE(k >= 1 && k <= 256, "k must be in [1, 256]");
@@ -301,6 +310,33 @@ void knn_device(const double* data, int64_t nd, const double* query, int64_t nq,
     build_grid(data, nd, cells, 0.0, G, s);
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    // Resize for the occupancy that suits the search. A surface crosses a cell over about h^2/1.5
+    // of its area on average, so a non-empty cell holds occ ~ rho h^2 / 1.5 points (rho: points per
+    // unit area), the disc of radius h about 4.7 occ and the 27-cell block about 16 occ. With
+    // occ ~ 0.35 k the first ring covers the k-th neighbour (~1.6 k points within h) while the
+    // candidates stay near 6 k. Occupancy scales with h^2 on surfaces, hence the exponent 3/2 on
+    // the cell count. The result does not depend on the grid; only the work does.
+    if (nd >= 4096) {
+        nonempty_cells_k<<<(unsigned)std::min<int64_t>(grid_for(G.cells, 256), 152 * 8), 256, 0, s>>>(G.start.get(), G.cells,
+                                                                                                     err.get());
+        CK_LAUNCH();
+        const int64_t ne = std::max(1, read1(err.get(), s));
+        CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+        const double occ = (double)nd / (double)ne, target = std::max(1.0, 0.35 * k);
+        if (occ > 1.5 * target || occ < target / 1.5) {
+            const double want = (double)G.cells * std::pow(occ / target, 1.5);
+            const int64_t c2 = std::max<int64_t>(1, std::min<int64_t>((int64_t)want, std::min<int64_t>(8 * nd, (int64_t)1 << 27)));
+            if (c2 > G.cells * 5 / 4 || c2 < G.cells * 4 / 5) {
+                DevGrid G2;
+                build_grid(data, nd, c2, 0.0, G2, s);
+                G.g = std::move(G2.g);
+                G.start = std::move(G2.start);
+                G.sidx = std::move(G2.sidx);
+                G.sxyz = std::move(G2.sxyz);
+                G.cells = G2.cells;
+            }
+        }
+    }
     const size_t smem = (sizeof(ukey) + sizeof(int)) * KNN_WARPS * KNN_CAP;
     CK(cudaFuncSetAttribute(knn_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     knn_k<<<grid_for(nq, KNN_WARPS), KNN_WARPS * 32, smem, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), query,

@@ -5,7 +5,7 @@
 namespace mgm {
 
 constexpr int KNN_WARPS = 4;
-constexpr int KNN_CAP = 2048;  // candidate buffer per warp
+constexpr int KNN_CAP = 1024;  // candidate buffer per warp (>= k + 32 for k <= 256: compaction keeps k)
 
 struct Grid {
     double x0, y0, z0, h;

@@ -56,9 +56,11 @@ struct RcmState {
     unsigned long long best;       // (degree, index) key of the next component's start
 };
 constexpr int RCM_BATCH = 16;
-constexpr int RCM_GRID = 152 * 8;
+constexpr int RCM_GRID = 152 * 8;  // blocks of 128 threads: 4 frontier nodes a block at a time
 
 __global__ void rcm_start_k(const int32_t* rp, const int32_t* pos, int64_t N, RcmState* st) {
+    pdl_trigger();
+    pdl_wait();
     if (st->fs != st->fe || st->tail >= N) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         if (pos[i] >= 0) continue;
@@ -68,6 +70,8 @@ __global__ void rcm_start_k(const int32_t* rp, const int32_t* pos, int64_t N, Rc
 }
 
 __global__ void rcm_seed_k(int32_t* order, int32_t* pos, int64_t N, RcmState* st) {
+    pdl_trigger();
+    pdl_wait();
     if (st->fs != st->fe || st->tail >= N) return;
     int32_t s = (int32_t)(st->best & 0xffffffffull);
     order[st->tail] = s;
@@ -78,13 +82,20 @@ __global__ void rcm_seed_k(int32_t* order, int32_t* pos, int64_t N, RcmState* st
     st->best = ~0ull;
 }
 
+// claim / count / write: one warp per frontier node, lanes over its (degree, index)-sorted
+// neighbours, so the dependent loads of a node's neighbours overlap instead of forming one long
+// chain per thread
 __global__ void rcm_claim_k(const int32_t* rp, const int32_t* adj, const int32_t* order, const int32_t* pos,
                             const RcmState* st, int32_t* claim) {
+    pdl_trigger();
+    pdl_wait();
     const int32_t fs = st->fs, fe = st->fe;
-    for (int32_t t = fs + blockIdx.x * blockDim.x + threadIdx.x; t < fe; t += gridDim.x * blockDim.x) {
-        int32_t v = order[t];
-        for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
-            int32_t u = adj[p];
+    const int lane = threadIdx.x & 31;
+    const int32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (int32_t t = fs + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < fe; t += nw) {
+        const int32_t v = order[t];
+        for (int32_t p = rp[v] + lane; p < rp[v + 1]; p += 32) {
+            const int32_t u = adj[p];
             if (pos[u] < 0) atomicMin(&claim[u], t);
         }
     }
@@ -92,56 +103,92 @@ __global__ void rcm_claim_k(const int32_t* rp, const int32_t* adj, const int32_t
 
 __global__ void rcm_count_k(const int32_t* rp, const int32_t* adj, const int32_t* order, const int32_t* pos,
                             const int32_t* claim, const RcmState* st, int32_t* cnt) {
+    pdl_trigger();
+    pdl_wait();
     const int32_t fs = st->fs, fe = st->fe;
-    for (int32_t t = fs + blockIdx.x * blockDim.x + threadIdx.x; t < fe; t += gridDim.x * blockDim.x) {
-        int32_t v = order[t];
+    const int lane = threadIdx.x & 31;
+    const int32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (int32_t t = fs + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < fe; t += nw) {
+        const int32_t v = order[t];
         int32_t c = 0;
-        for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
-            int32_t u = adj[p];
-            if (pos[u] < 0 && claim[u] == t) ++c;
+        for (int32_t p0 = rp[v]; p0 < rp[v + 1]; p0 += 32) {
+            const int32_t p = p0 + lane;
+            bool mine = false;
+            if (p < rp[v + 1]) {
+                const int32_t u = adj[p];
+                mine = pos[u] < 0 && claim[u] == t;
+            }
+            c += __popc(__ballot_sync(0xffffffffu, mine));
         }
-        cnt[t - fs] = c;
+        if (lane == 0) cnt[t - fs] = c;
     }
 }
 
-// exclusive scan of the frontier's child counts by one block; total into the state
+// exclusive scan of the frontier's child counts by one block (chunk sums, then a two-level
+// shuffle scan of the 1024 chunk sums); total into the state
 __global__ void __launch_bounds__(1024) rcm_scan_k(const int32_t* cnt, int32_t* off, RcmState* st) {
-    __shared__ int32_t part[1024];
+    pdl_trigger();
+    pdl_wait();
+    __shared__ int32_t wsum[32];
     const int32_t n = st->fe - st->fs;
     const int32_t per = (n + 1023) / 1024;
     const int32_t b = threadIdx.x * per, e = min(n, b + per);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t sum = 0;
     for (int32_t i = b; i < e; ++i) sum += cnt[i];
-    part[threadIdx.x] = sum;
+    int32_t x = sum;  // inclusive scan within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t acc = 0;
-        for (int t = 0; t < 1024; ++t) { int32_t v = part[t]; part[t] = acc; acc += v; }
-        st->total = acc;
+    if (w == 0) {
+        int32_t t = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wsum[lane] = t;  // inclusive over warps
+        if (lane == 31) st->total = t;
     }
     __syncthreads();
-    int32_t acc = part[threadIdx.x];
+    int32_t acc = (w > 0 ? wsum[w - 1] : 0) + x - sum;
     for (int32_t i = b; i < e; ++i) { off[i] = acc; acc += cnt[i]; }
 }
 
 __global__ void rcm_write_k(const int32_t* rp, const int32_t* adj, int32_t* order, int32_t* pos, const int32_t* claim,
                             const int32_t* off, const RcmState* st) {
+    pdl_trigger();
+    pdl_wait();
     const int32_t fs = st->fs, fe = st->fe, tail = st->tail;
-    for (int32_t t = fs + blockIdx.x * blockDim.x + threadIdx.x; t < fe; t += gridDim.x * blockDim.x) {
-        int32_t v = order[t];
+    const int lane = threadIdx.x & 31;
+    const int32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (int32_t t = fs + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < fe; t += nw) {
+        const int32_t v = order[t];
         int32_t q = tail + off[t - fs];
-        for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
-            int32_t u = adj[p];
-            if (pos[u] < 0 && claim[u] == t) {
-                order[q] = u;
-                pos[u] = q;
-                ++q;
+        for (int32_t p0 = rp[v]; p0 < rp[v + 1]; p0 += 32) {
+            const int32_t p = p0 + lane;
+            int32_t u = -1;
+            bool mine = false;
+            if (p < rp[v + 1]) {
+                u = adj[p];
+                mine = pos[u] < 0 && claim[u] == t;
             }
+            const unsigned m = __ballot_sync(0xffffffffu, mine);
+            if (mine) {
+                const int32_t qq = q + __popc(m & ((1u << lane) - 1u));
+                order[qq] = u;
+                pos[u] = qq;
+            }
+            q += __popc(m);
         }
     }
 }
 
 __global__ void rcm_advance_k(RcmState* st) {
+    pdl_trigger();
+    pdl_wait();
     if (st->fs == st->fe) return;
     st->fs = st->tail;
     st->fe = st->tail + st->total;
@@ -153,6 +200,45 @@ __global__ void reverse_k(const int32_t* order, int64_t N, int32_t* perm) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) perm[i] = order[N - 1 - i];
 }
+
+// A fixed sequence of launches captured once on a private stream and replayed as a CUDA graph.
+// Captured launches are not counted; each replay counts them.
+struct GraphBatch {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    template <class F>
+    void capture(F&& body) {
+        cudaStream_t cs = nullptr;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        const int64_t before = launches();
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            try {
+                body(cs);
+            } catch (...) {
+                cudaStreamEndCapture(cs, &g);
+                if (g) cudaGraphDestroy(g);
+                cudaStreamDestroy(cs);
+                throw;
+            }
+            e = cudaStreamEndCapture(cs, &g);
+        }
+        kernels = launches() - before;
+        note_launch(-kernels);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        CK(e);
+    }
+    void launch(cudaStream_t s) {
+        CK(cudaGraphLaunch(exec, s));
+        note_launch(kernels);
+    }
+    ~GraphBatch() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
 
 void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStream_t s) {
     REQUIRE(N >= 1 && N < 0x7fffffff, "N out of range");
@@ -169,28 +255,33 @@ void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStr
     Temp<RcmState> st(1, s);
     RcmState init{0, 0, 0, 0, ~0ull};
     CK(cudaMemcpyAsync(st.get(), &init, sizeof(RcmState), cudaMemcpyHostToDevice, s));
-    const unsigned grid = (unsigned)std::min<int64_t>(grid_for(N, 128), RCM_GRID);
-    for (int64_t level = 0;; ++level) {
-        if (level % RCM_BATCH == 0) {
-            RcmState h;
-            to_host(&h, st.get(), 1, s);
-            if (h.tail >= N && h.fs == h.fe) break;
-            if (level > 4 * N + 64) fail(MGM_ERR_UNSUPPORTED, "RCM did not terminate");
-        }
-        rcm_start_k<<<grid, 128, 0, s>>>(srp.get(), pos.get(), N, st.get());
-        CK_LAUNCH();
-        rcm_seed_k<<<1, 1, 0, s>>>(order.get(), pos.get(), N, st.get());
-        CK_LAUNCH();
-        rcm_claim_k<<<grid, 128, 0, s>>>(srp.get(), adj.get(), order.get(), pos.get(), st.get(), claim.get());
-        CK_LAUNCH();
-        rcm_count_k<<<grid, 128, 0, s>>>(srp.get(), adj.get(), order.get(), pos.get(), claim.get(), st.get(), cnt.get());
-        CK_LAUNCH();
-        rcm_scan_k<<<1, 1024, 0, s>>>(cnt.get(), off.get(), st.get());
-        CK_LAUNCH();
-        rcm_write_k<<<grid, 128, 0, s>>>(srp.get(), adj.get(), order.get(), pos.get(), claim.get(), off.get(), st.get());
-        CK_LAUNCH();
-        rcm_advance_k<<<1, 1, 0, s>>>(st.get());
-        CK_LAUNCH();
+    const unsigned grid = (unsigned)std::min<int64_t>(grid_for(N, 4), RCM_GRID);
+    // one BFS level: seven kernels chained by programmatic dependent launch
+    auto level = [&](cudaStream_t q) {
+        launch_pdl(rcm_start_k, grid, 128, q, (const int32_t*)srp.get(), (const int32_t*)pos.get(), N, st.get());
+        launch_pdl(rcm_seed_k, 1, 1, q, order.get(), pos.get(), N, st.get());
+        launch_pdl(rcm_claim_k, grid, 128, q, (const int32_t*)srp.get(), (const int32_t*)adj.get(),
+                   (const int32_t*)order.get(), (const int32_t*)pos.get(), (const RcmState*)st.get(), claim.get());
+        launch_pdl(rcm_count_k, grid, 128, q, (const int32_t*)srp.get(), (const int32_t*)adj.get(),
+                   (const int32_t*)order.get(), (const int32_t*)pos.get(), (const int32_t*)claim.get(),
+                   (const RcmState*)st.get(), cnt.get());
+        launch_pdl(rcm_scan_k, 1, 1024, q, (const int32_t*)cnt.get(), off.get(), st.get());
+        launch_pdl(rcm_write_k, grid, 128, q, (const int32_t*)srp.get(), (const int32_t*)adj.get(), order.get(),
+                   pos.get(), (const int32_t*)claim.get(), (const int32_t*)off.get(), (const RcmState*)st.get());
+        launch_pdl(rcm_advance_k, 1, 1, q, st.get());
+    };
+    // Large graphs: RCM_BATCH levels captured once as a CUDA graph and replayed (levels after the
+    // last are no-ops); the host reads the state between replays.
+    GraphBatch gb;
+    if (N >= 32768) gb.capture([&](cudaStream_t q) { for (int l = 0; l < RCM_BATCH; ++l) level(q); });
+    for (int64_t lv = 0;; lv += RCM_BATCH) {
+        RcmState h;
+        to_host(&h, st.get(), 1, s);
+        if (h.tail >= N && h.fs == h.fe) break;
+        if (lv > 4 * N + 64) fail(MGM_ERR_UNSUPPORTED, "RCM did not terminate");
+        if (gb.exec) gb.launch(s);
+        else
+            for (int l = 0; l < RCM_BATCH; ++l) level(s);
     }
     reverse_k<<<grid_for(N, 256), 256, 0, s>>>(order.get(), N, perm);
     CK_LAUNCH();
@@ -206,45 +297,71 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed
     return z ^ (z >> 31);
 }
 
+// One thread per vertex; coloured vertices return at once. Neighbours are examined eight at a
+// time (indices, then their colours, then priorities) so that the dependent loads of a vertex
+// overlap. `left` is set (not counted) while uncoloured vertices remain.
+constexpr int JP_BATCH = 8;
 __global__ void jp_select_k(const int32_t* rp, const int32_t* adj, const int32_t* col, int64_t N, unsigned long long seed,
-                            char* sel, int* nleft) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int left = 0;
-    if (v < N) {
+                            char* sel, int* left) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    if (col[v] >= 0) {
         sel[v] = 0;
-        if (col[v] < 0) {
-            left = 1;
-            unsigned long long pv = splitmix64(seed, (unsigned long long)v);
-            bool top = true;
-            for (int32_t p = rp[v]; p < rp[v + 1] && top; ++p) {
-                int32_t u = adj[p];
-                if (col[u] >= 0) continue;
-                unsigned long long pu = splitmix64(seed, (unsigned long long)u);
-                if (!(pv > pu || (pv == pu && v > u))) top = false;
+        return;
+    }
+    const unsigned am = __activemask();  // the uncoloured vertices of this warp
+    if ((threadIdx.x & 31) == __ffs(am) - 1) *left = 1;
+    const unsigned long long pv = splitmix64(seed, (unsigned long long)v);
+    const int32_t e = rp[v + 1];
+    bool top = true;
+    for (int32_t p = rp[v]; p < e && top; p += JP_BATCH) {
+        int32_t u[JP_BATCH];
+        int32_t cu[JP_BATCH];
+#pragma unroll
+        for (int q = 0; q < JP_BATCH; ++q) u[q] = p + q < e ? adj[p + q] : -1;
+#pragma unroll
+        for (int q = 0; q < JP_BATCH; ++q) cu[q] = u[q] >= 0 ? col[u[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < JP_BATCH; ++q) {
+            if (u[q] >= 0 && cu[q] < 0) {
+                const unsigned long long pu = splitmix64(seed, (unsigned long long)u[q]);
+                if (!(pv > pu || (pv == pu && v > u[q]))) top = false;
             }
-            sel[v] = top ? 1 : 0;
         }
     }
-    left = warp_sum_i(left);
-    if ((threadIdx.x & 31) == 0 && left) atomicAdd(nleft, left);
+    sel[v] = top ? 1 : 0;
 }
 
-__global__ void jp_assign_k(const int32_t* rp, const int32_t* adj, int32_t* col, const char* sel, int64_t N, int* maxc) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// smallest colour absent from the coloured neighbours, 64 candidate colours at a time
+__global__ void jp_assign_k(const int32_t* rp, const int32_t* adj, int32_t* col, const char* sel, int64_t N) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N || !sel[v]) return;
+    const int32_t b = rp[v], e = rp[v + 1];
     for (int base = 0;; base += 64) {
         unsigned long long used = 0;
-        for (int32_t p = rp[v]; p < rp[v + 1]; ++p) {
-            int32_t c = col[adj[p]];
-            if (c >= base && c < base + 64) used |= 1ull << (c - base);
+        for (int32_t p = b; p < e; p += JP_BATCH) {
+            int32_t c[JP_BATCH];
+#pragma unroll
+            for (int q = 0; q < JP_BATCH; ++q) c[q] = p + q < e ? adj[p + q] : -1;
+#pragma unroll
+            for (int q = 0; q < JP_BATCH; ++q) c[q] = c[q] >= 0 ? col[c[q]] : -1;
+#pragma unroll
+            for (int q = 0; q < JP_BATCH; ++q)
+                if (c[q] >= base && c[q] < base + 64) used |= 1ull << (c[q] - base);
         }
         if (~used) {
-            int c = base + __ffsll((long long)~used) - 1;
-            col[v] = c;
-            atomicMax(maxc, c);
+            col[v] = base + __ffsll((long long)~used) - 1;
             return;
         }
     }
+}
+
+__global__ void max_i32_k(const int32_t* a, int64_t n, int* out) {
+    int m = -1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, a[i]);
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32_t* colour, int32_t* ncolors,
@@ -254,20 +371,23 @@ void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32
     Temp<int32_t> srp, sci;
     sym_pattern(N, rp, ci, srp, sci, s);
     Temp<char> sel(N, s);
-    Temp<int> ctr(2, s);  // [0] uncoloured count, [1] max colour
+    Temp<int> ctr(2, s);  // [0] uncoloured vertices remain, [1] max colour
     fill_i32(colour, -1, N, s);
-    CK(cudaMemsetAsync(ctr.get() + 1, 0, sizeof(int), s));
+    const unsigned wgrid = grid_for(N, 256);
     for (int64_t round = 0;; ++round) {
         if (round > N) fail(MGM_ERR_UNSUPPORTED, "colouring did not terminate");
         CK(cudaMemsetAsync(ctr.get(), 0, sizeof(int), s));
-        jp_select_k<<<grid_for(N, 256), 256, 0, s>>>(srp.get(), sci.get(), colour, N, seed, sel.get(), ctr.get());
+        jp_select_k<<<wgrid, 256, 0, s>>>(srp.get(), sci.get(), colour, N, seed, sel.get(), ctr.get());
         CK_LAUNCH();
         if (round % 4 == 3 || round < 2) {
             if (read1(ctr.get(), s) == 0) break;
         }
-        jp_assign_k<<<grid_for(N, 256), 256, 0, s>>>(srp.get(), sci.get(), colour, sel.get(), N, ctr.get() + 1);
+        jp_assign_k<<<wgrid, 256, 0, s>>>(srp.get(), sci.get(), colour, sel.get(), N);
         CK_LAUNCH();
     }
+    CK(cudaMemsetAsync(ctr.get() + 1, 0xff, sizeof(int), s));
+    max_i32_k<<<(unsigned)std::min<int64_t>(grid_for(N, 256), 152 * 4), 256, 0, s>>>(colour, N, ctr.get() + 1);
+    CK_LAUNCH();
     *ncolors = read1(ctr.get() + 1, s) + 1;
 }
 

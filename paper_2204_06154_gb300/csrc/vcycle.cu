@@ -61,13 +61,11 @@ __device__ __forceinline__ T group_reduce(T v) {
     return v;
 }
 
-// Programmatic dependent launch: every kernel of the cycle lets its successor be scheduled as soon
-// as all of its own blocks are running (launch_dependents), and waits for its predecessor's
-// completion and memory (wait) before it reads anything the predecessor writes. Work that only
-// reads the level's static operators (row structure, columns, values) is issued before the wait,
-// so it overlaps the predecessor's tail. Without a programmatic predecessor, wait returns at once.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Programmatic dependent launch (pdl_trigger / pdl_wait / launch_pdl in common.cuh): every kernel
+// of the cycle lets its successor be scheduled as soon as all of its own blocks are running, and
+// waits for its predecessor's completion and memory before it reads anything the predecessor
+// writes. Work that only reads the level's static operators (row structure, columns, values) is
+// issued before the wait, so it overlaps the predecessor's tail.
 
 // Streamed operator data (columns, values, row structure) is loaded with an L2 evict-first policy,
 // so that it does not push the gathered vector out of L2 (the matrix of a level is far larger than
@@ -442,23 +440,6 @@ template <> struct LV<double> {
     static double* eold(Level& L) { return L.eold64.get(); }
     static const double* c(Level& L) { return L.c64.get(); }
 };
-
-// launch with programmatic stream serialization (see pdl_trigger / pdl_wait)
-template <class... KArgs, class... Args>
-static void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, kern, args...));
-    CK_LAUNCH();
-}
 
 template <int MODE, class T>
 static void launch_rows(Level& L, int32_t r0, int32_t r1, cudaStream_t s) {
