@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cfloat>
+#include <climits>
 
 #include "common.cuh"
 #include "knn_grid.cuh"
@@ -64,19 +65,40 @@ __global__ void grid_params_k(const double* part, int nparts, int64_t cells, dou
     for (int b = 1; b < nparts; ++b)
         for (int c = 0; c < 3; ++c) { mn[c] = fmin(mn[c], part[6 * b + c]); mx[c] = fmax(mx[c], part[6 * b + 3 + c]); }
     double e[3], emax = 0.0;
-    for (int c = 0; c < 3; ++c) { e[c] = mx[c] - mn[c]; emax = fmax(emax, e[c]); }
+    for (int c = 0; c < 3; ++c) {
+        e[c] = mx[c] - mn[c];
+        if (!(e[c] >= 0.0 && e[c] < 1e300)) e[c] = 0.0;  // non-finite coordinates: one cell along this axis
+        emax = fmax(emax, e[c]);
+    }
     if (!(emax > 0.0)) emax = 1.0;
     // bisection on h: count(h) = prod(floor(e/h) + 1) <= cells
+    // (64 halvings take the bracket below one part in 1e9 of emax; one reciprocal per step, as a
+    // single thread's FP64 divisions are slow)
     double lo = emax * 1e-9, hi = emax * 2.0 + 1.0;
-    for (int it = 0; it < 200; ++it) {
+    for (int it = 0; it < 64; ++it) {
         double mid = 0.5 * (lo + hi);
+        const double inv = 1.0 / mid;
         double cnt = 1.0;
-        for (int c = 0; c < 3; ++c) cnt *= floor(e[c] / mid) + 1.0;
+        for (int c = 0; c < 3; ++c) cnt *= floor(e[c] * inv) + 1.0;
         if (cnt <= (double)cells) hi = mid; else lo = mid;
     }
+    // The dimensions use the same expression as the test above (floor(e * (1/h)) + 1, monotone in
+    // h), so nx ny nz <= cells, the size of the arrays indexed by cell; the loop only guards that.
     double h = fmax(hi, h_min);
+    int n3[3];
+    for (int it = 0;; ++it) {
+        const double inv = 1.0 / h;
+        double cnt = 1.0;
+        for (int c = 0; c < 3; ++c) {
+            const double f = floor(e[c] * inv) + 1.0;
+            n3[c] = (int)f;
+            cnt *= f;
+        }
+        if (cnt <= (double)cells) break;
+        h = it < 200 ? h * 1.0001 : emax * 2.0 + 1.0;  // the last: one cell
+    }
     g->x0 = mn[0]; g->y0 = mn[1]; g->z0 = mn[2]; g->h = h;
-    g->nx = (int)floor(e[0] / h) + 1; g->ny = (int)floor(e[1] / h) + 1; g->nz = (int)floor(e[2] / h) + 1;
+    g->nx = n3[0]; g->ny = n3[1]; g->nz = n3[2];
     g->ncells = (int64_t)g->nx * g->ny * g->nz;
 }
 
@@ -148,6 +170,62 @@ typedef unsigned long long ukey;
 __device__ __forceinline__ bool key_lt(ukey a, int ia, ukey b, int ib) { return a < b || (a == b && ia < ib); }
 __device__ __forceinline__ ukey d2_key(double d2) { return (ukey)__double_as_longlong(d2) + 1ull; }
 
+// Cells around (cx, cy, cz), 32 at a time: the cube of side W = 2R+1 (`shell` false; dz slowest,
+// dx fastest), or only its surface, the cells with max(|dx|,|dy|,|dz|) = R (`shell` true: the two
+// z faces, then the square rings of the layers between). Lane l takes cell c0 + l, loads its point
+// range, and a warp scan flattens the ranges, so that the warp then walks all their points 32 at
+// a time instead of one cell after another; chunk_slot maps a flattened position to the point's
+// slot in the cell-sorted arrays.
+struct CellChunk {
+    int b, excl, total;
+};
+__host__ __device__ __forceinline__ int block_cells(int R, bool shell) {
+    const int W = 2 * R + 1;
+    return (!shell || R == 0) ? W * W * W : W * W * W - (W - 2) * (W - 2) * (W - 2);
+}
+__device__ __forceinline__ CellChunk cell_chunk(const Grid& g, const int32_t* start, int cx, int cy, int cz, int R,
+                                                bool shell, int c0, int lane) {
+    const int W = 2 * R + 1, cl = c0 + lane;
+    int b = 0, len = 0;
+    if (cl < block_cells(R, shell)) {
+        int dz, dy, dx;
+        if (!shell || R == 0) {
+            dz = cl / (W * W) - R; dy = (cl / W) % W - R; dx = cl % W - R;
+        } else if (cl < 2 * W * W) {
+            const int q = cl % (W * W);
+            dz = cl < W * W ? -R : R; dy = q / W - R; dx = q % W - R;
+        } else {
+            const int ring = 4 * (W - 1), q0 = cl - 2 * W * W, q = q0 % ring;
+            dz = -R + 1 + q0 / ring;
+            if (q < W) { dy = -R; dx = q - R; }
+            else if (q < 2 * W) { dy = R; dx = q - W - R; }
+            else { dy = -R + 1 + (q - 2 * W) / 2; dx = ((q - 2 * W) & 1) ? R : -R; }
+        }
+        const int z = cz + dz, y = cy + dy, x = cx + dx;
+        if (z >= 0 && z < g.nz && y >= 0 && y < g.ny && x >= 0 && x < g.nx) {
+            const int64_t c = ((int64_t)z * g.ny + y) * g.nx + x;
+            b = start[c];
+            len = start[c + 1] - b;
+        }
+    }
+    int incl = len;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    return CellChunk{b, incl - len, __shfl_sync(0xffffffffu, incl, 31)};
+}
+// slot of flattened position t (all lanes take part; t is clamped by the caller)
+__device__ __forceinline__ int chunk_slot(const CellChunk& ch, int t) {
+    int lo = 0;
+    for (int step = 16; step; step >>= 1) {
+        const int probe = lo + step;
+        const int ex = __shfl_sync(0xffffffffu, ch.excl, probe & 31);
+        if (probe < 32 && ex <= t) lo = probe;
+    }
+    return __shfl_sync(0xffffffffu, ch.b, lo) + (t - __shfl_sync(0xffffffffu, ch.excl, lo));
+}
+
 // Keep only the k smallest keys of the buffer (stable, in place). A candidate outside the k
 // smallest of a subset can never enter the k smallest of the full set, so this loses nothing.
 __device__ int knn_compact(ukey* bd, int* bi, int count, int k, int lane) {
@@ -202,41 +280,30 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
     ukey lim2 = 0;
     bool all = false;
     for (int r = 0;; ++r) {
-        for (int dz = -r; dz <= r; ++dz) {
-            int z = cz + dz;
-            if (z < 0 || z >= g.nz) continue;
-            for (int dy = -r; dy <= r; ++dy) {
-                int y = cy + dy;
-                if (y < 0 || y >= g.ny) continue;
-                bool face = (dz == -r || dz == r || dy == -r || dy == r);
-                for (int dx = -r; dx <= r; dx += (face ? 1 : 2 * r)) {
-                    int x = cx + dx;
-                    if (x >= 0 && x < g.nx) {
-                        int64_t c = ((int64_t)z * g.ny + y) * g.nx + x;
-                        int b = start[c], e = start[c + 1];
-                        for (int t = b + lane; t - lane < e; t += 32) {
-                            if (count + 32 > KNN_CAP) {
-                                __syncwarp();
-                                count = knn_compact(bd, bi, count, k, lane);
-                            }
-                            bool has = t < e;
-                            ukey d = 0;
-                            int j = 0;
-                            if (has) {
-                                j = sidx[t];
-                                d = (self_first && j == (int)qi)
-                                        ? 0ull
-                                        : d2_key(d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1],
-                                                        sxyz[3 * (int64_t)t + 2]));
-                            }
-                            unsigned m = __ballot_sync(0xffffffffu, has);
-                            int pos = count + __popc(m & ((1u << lane) - 1u));
-                            if (has) { bd[pos] = d; bi[pos] = j; }
-                            count += __popc(m);
-                        }
-                    }
-                    if (r == 0) break;
+        const int ncell = block_cells(r, true);
+        for (int c0 = 0; c0 < ncell; c0 += 32) {
+            const CellChunk ch = cell_chunk(g, start, cx, cy, cz, r, true, c0, lane);
+            for (int t0 = 0; t0 < ch.total; t0 += 32) {
+                if (count + 32 > KNN_CAP) {
+                    __syncwarp();
+                    count = knn_compact(bd, bi, count, k, lane);
                 }
+                const int t = t0 + lane;
+                const bool has = t < ch.total;
+                const int slot = chunk_slot(ch, has ? t : ch.total - 1);
+                ukey d = 0;
+                int j = 0;
+                if (has) {
+                    j = sidx[slot];
+                    d = (self_first && j == (int)qi)
+                            ? 0ull
+                            : d2_key(d2_pts(px, py, pz, sxyz[3 * (int64_t)slot], sxyz[3 * (int64_t)slot + 1],
+                                            sxyz[3 * (int64_t)slot + 2]));
+                }
+                unsigned m = __ballot_sync(0xffffffffu, has);
+                int pos = count + __popc(m & ((1u << lane) - 1u));
+                if (has) { bd[pos] = d; bi[pos] = j; }
+                count += __popc(m);
             }
         }
         if (r >= rfull) { all = true; break; }
@@ -285,6 +352,77 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
             idx_out[qi * k + rank] = j;
             if (d2_out) d2_out[qi * k + rank] = d == 0ull ? 0.0 : __longlong_as_double((long long)(d - 1ull));
         }
+    }
+}
+
+// k <= 4: one thread per query, its k best (key, index) pairs kept sorted in registers. Same
+// search and stopping rule as knn_k (the k best lie strictly inside the covered radius), so the
+// same result.
+template <int K>
+__global__ void __launch_bounds__(128) knn_small_k(const Grid* gp, const int32_t* start, const int32_t* sidx,
+                                                   const double* sxyz, const double* q, int64_t nq, int self_first,
+                                                   int32_t* idx_out, double* d2_out, int* err) {
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= nq) return;
+    const Grid g = *gp;
+    const double px = q[3 * qi], py = q[3 * qi + 1], pz = q[3 * qi + 2];
+    const int cx = cell_coord(px, g.x0, g.h, g.nx), cy = cell_coord(py, g.y0, g.h, g.ny), cz = cell_coord(pz, g.z0, g.h, g.nz);
+    const int rfull = max(max(max(cx, g.nx - 1 - cx), max(cy, g.ny - 1 - cy)), max(cz, g.nz - 1 - cz));
+    ukey bk[K];
+    int bj[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) { bk[t] = ~0ull; bj[t] = INT_MAX; }
+    int found = 0;
+    for (int r = 0;; ++r) {
+        for (int dz = -r; dz <= r; ++dz) {
+            const int z = cz + dz;
+            if (z < 0 || z >= g.nz) continue;
+            for (int dy = -r; dy <= r; ++dy) {
+                const int y = cy + dy;
+                if (y < 0 || y >= g.ny) continue;
+                const bool face = (dz == -r || dz == r || dy == -r || dy == r);
+                for (int dx = -r; dx <= r; dx += (face ? 1 : 2 * r)) {
+                    const int x = cx + dx;
+                    if (x >= 0 && x < g.nx) {
+                        const int64_t c = ((int64_t)z * g.ny + y) * g.nx + x;
+                        const int b = start[c], e = start[c + 1];
+                        for (int t = b; t < e; ++t) {
+                            const int j = sidx[t];
+                            const ukey d = (self_first && j == (int)qi)
+                                               ? 0ull
+                                               : d2_key(d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1],
+                                                               sxyz[3 * (int64_t)t + 2]));
+                            ++found;
+                            if (key_lt(d, j, bk[K - 1], bj[K - 1])) {
+                                bk[K - 1] = d;
+                                bj[K - 1] = j;
+#pragma unroll
+                                for (int u = K - 1; u > 0; --u)
+                                    if (key_lt(bk[u], bj[u], bk[u - 1], bj[u - 1])) {
+                                        const ukey tk = bk[u]; bk[u] = bk[u - 1]; bk[u - 1] = tk;
+                                        const int tj = bj[u]; bj[u] = bj[u - 1]; bj[u - 1] = tj;
+                                    }
+                            }
+                        }
+                    }
+                    if (r == 0) break;
+                }
+            }
+        }
+        if (r >= rfull) break;
+        if (r >= 1 && found >= K) {
+            const double R = (double)r * g.h;
+            if (bk[K - 1] < d2_key(R * R * (1.0 - 1e-9))) break;
+        }
+    }
+    if (found < K) {
+        atomicOr(err, 2);
+        return;
+    }
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        idx_out[qi * K + t] = bj[t];
+        if (d2_out) d2_out[qi * K + t] = bk[t] == 0ull ? 0.0 : __longlong_as_double((long long)(bk[t] - 1ull));
     }
 }
 
@@ -337,11 +475,18 @@ void knn_device(const double* data, int64_t nd, const double* query, int64_t nq,
             }
         }
     }
-    const size_t smem = (sizeof(ukey) + sizeof(int)) * KNN_WARPS * KNN_CAP;
-    CK(cudaFuncSetAttribute(knn_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    knn_k<<<grid_for(nq, KNN_WARPS), KNN_WARPS * 32, smem, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), query,
-                                                            nq, k, self_first, idx_out, d2_out, err.get());
-    CK_LAUNCH();
+    if (k <= 4) {
+        auto kern = k == 1 ? knn_small_k<1> : k == 2 ? knn_small_k<2> : k == 3 ? knn_small_k<3> : knn_small_k<4>;
+        kern<<<grid_for(nq, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), query, nq, self_first,
+                                               idx_out, d2_out, err.get());
+        CK_LAUNCH();
+    } else {
+        const size_t smem = (sizeof(ukey) + sizeof(int)) * KNN_WARPS * KNN_CAP;
+        CK(cudaFuncSetAttribute(knn_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        knn_k<<<grid_for(nq, KNN_WARPS), KNN_WARPS * 32, smem, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
+                                                                query, nq, k, self_first, idx_out, d2_out, err.get());
+        CK_LAUNCH();
+    }
     int e = read1(err.get(), s);
     if (e & 1) fail(MGM_ERR_UNSUPPORTED, "kNN candidate buffer overflow (points too clustered for the grid)");
     if (e & 2) fail(MGM_ERR_INVALID_ARG, "fewer than k data points");
@@ -373,33 +518,34 @@ __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const
     // ring absorbs rounding at the bin boundaries
     const int R = (g.h >= two_rmax * (1.0 + 1e-6)) ? 1 : (int)ceil(two_rmax / g.h) + 1;
     int count = 0;
-    for (int z = max(cz - R, 0); z <= min(cz + R, g.nz - 1); ++z)
-        for (int y = max(cy - R, 0); y <= min(cy + R, g.ny - 1); ++y)
-            for (int xx = max(cx - R, 0); xx <= min(cx + R, g.nx - 1); ++xx) {
-                int64_t c = ((int64_t)z * g.ny + y) * g.nx + xx;
-                int b = start[c], e = start[c + 1];
-                for (int t = b + lane; t - lane < e; t += 32) {
-                    bool has = false;
-                    int j = 0;
-                    double d = 0.0;
-                    if (t < e) {
-                        j = sidx[t];
-                        if (j != (int)i) {
-                            double dd = d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1], sxyz[3 * (int64_t)t + 2]);
-                            // sqrt(dd) < two_rmax is decided exactly below; skip the sqrt where dd is
-                            // clearly beyond (the factor leaves a margin far above rounding)
-                            if (dd <= lim_sq) {
-                                d = sqrt(dd);
-                                has = d < two_rmax;
-                            }
-                        }
+    const int ncell = block_cells(R, false);
+    for (int c0 = 0; c0 < ncell; c0 += 32) {
+        const CellChunk ch = cell_chunk(g, start, cx, cy, cz, R, false, c0, lane);
+        for (int t0 = 0; t0 < ch.total; t0 += 32) {
+            const int t = t0 + lane;
+            const int slot = chunk_slot(ch, t < ch.total ? t : ch.total - 1);
+            bool has = false;
+            int j = 0;
+            double d = 0.0;
+            if (t < ch.total) {
+                j = sidx[slot];
+                if (j != (int)i) {
+                    double dd = d2_pts(px, py, pz, sxyz[3 * (int64_t)slot], sxyz[3 * (int64_t)slot + 1],
+                                       sxyz[3 * (int64_t)slot + 2]);
+                    // sqrt(dd) < two_rmax is decided exactly below; skip the sqrt where dd is
+                    // clearly beyond (the factor leaves a margin far above rounding)
+                    if (dd <= lim_sq) {
+                        d = sqrt(dd);
+                        has = d < two_rmax;
                     }
-                    unsigned m = __ballot_sync(0xffffffffu, has);
-                    int pos = count + __popc(m & ((1u << lane) - 1u));
-                    if (has && pos < RAD_CAP) { si[w][pos] = j; sdist[w][pos] = d; }
-                    count += __popc(m);
                 }
             }
+            unsigned m = __ballot_sync(0xffffffffu, has);
+            int pos = count + __popc(m & ((1u << lane) - 1u));
+            if (has && pos < RAD_CAP) { si[w][pos] = j; sdist[w][pos] = d; }
+            count += __popc(m);
+        }
+    }
     if (count > RAD_CAP) {
         if (lane == 0) atomicOr(err, 1);
         return;
@@ -428,7 +574,7 @@ __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const
 void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, Temp<int32_t>& rowptr,
                   Temp<int32_t>& nbr, Temp<double>& f, cudaStream_t s) {
     DevGrid G;
-    build_grid(x, n, 2 * n, h_hint * (1.0 + 1e-5), G, s);
+    build_grid(x, n, 8 * n, h_hint * (1.0 + 1e-5), G, s);  // cells no narrower than 2 r_max: one ring
     Temp<int32_t> cnt(n + 1, s);
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));

@@ -825,32 +825,44 @@ __global__ void gfd_weights_k(const double* xyz, const double* nrm, const int32_
 }
 
 // ---------------------------------------------------------------------------------------------
-// assembly: one thread per row, columns sorted by insertion (rows are n long)
+// assembly: one warp per row; the row's (column, position) keys are staged in shared memory and
+// each entry is placed by rank, so columns come out ascending (stable for repeats, which are
+// reported)
 // ---------------------------------------------------------------------------------------------
-__global__ void assemble_k(int64_t N, int n, const int32_t* idx, const double* w, double mu, int poisson, int32_t* rp,
-                           int32_t* col, double* val, int* dup) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int ASM_WARPS = 8, ASM_MAX = 256;
+__global__ void __launch_bounds__(ASM_WARPS * 32) assemble_k(int64_t N, int n, const int32_t* idx, const double* w,
+                                                             double mu, int poisson, int32_t* rp, int32_t* col,
+                                                             double* val, int* dup) {
+    __shared__ unsigned long long key[ASM_WARPS][ASM_MAX];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * ASM_WARPS + wi;
     if (i > N) return;
-    rp[i] = (int32_t)(i * n);
+    if (lane == 0) rp[i] = (int32_t)(i * n);
     if (i == N) return;
-    int32_t* c = col + i * n;
-    double* v = val + i * n;
-    for (int j = 0; j < n; ++j) {
-        int32_t cj = idx[i * n + j];
-        double wj = w[i * n + j];
+    for (int j = lane; j < n; j += 32)
+        key[wi][j] = ((unsigned long long)(uint32_t)idx[i * n + j] << 32) | (unsigned)j;
+    __syncwarp();
+    bool rep = false;
+    for (int j = lane; j < n; j += 32) {
+        const unsigned long long k = key[wi][j];
+        const int32_t cj = (int32_t)(k >> 32);
+        int rank = 0;
+        for (int u = 0; u < n; ++u) {
+            const unsigned long long ku = key[wi][u];
+            rank += ku < k ? 1 : 0;
+            rep = rep || (u != j && (int32_t)(ku >> 32) == cj);
+        }
+        const double wj = w[i * n + j];
         double vj;
         if (poisson) vj = wj;
         else {
-            double t = mu * wj;
+            const double t = mu * wj;
             vj = (cj == i) ? 1.0 - t : -t;
         }
-        int p = j;
-        while (p > 0 && c[p - 1] > cj) { c[p] = c[p - 1]; v[p] = v[p - 1]; --p; }
-        c[p] = cj;
-        v[p] = vj;
+        col[i * n + rank] = cj;
+        val[i * n + rank] = vj;
     }
-    for (int j = 1; j < n; ++j)
-        if (c[j] == c[j - 1]) atomicOr(dup, 1);
+    if (__any_sync(0xffffffffu, rep) && lane == 0) atomicOr(dup, 1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1029,7 +1041,8 @@ void assemble(int64_t N, int n, const int32_t* idx, const double* w, double mu, 
     REQUIRE(idx && w && rp && col && val, "null array");
     Temp<int> dup(1, s);
     CK(cudaMemsetAsync(dup.get(), 0, sizeof(int), s));
-    assemble_k<<<grid_for(N + 1, 128), 128, 0, s>>>(N, n, idx, w, mu, poisson, rp, col, val, dup.get());
+    REQUIRE(n <= ASM_MAX, "stencil size above 256");
+    assemble_k<<<grid_for(N + 1, ASM_WARPS), ASM_WARPS * 32, 0, s>>>(N, n, idx, w, mu, poisson, rp, col, val, dup.get());
     CK_LAUNCH();
     if (read1(dup.get(), s)) fail(MGM_ERR_INVALID_ARG, "a stencil lists the same node twice");
 }
