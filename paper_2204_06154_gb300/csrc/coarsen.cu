@@ -107,44 +107,57 @@ __global__ void candidates_k(const int32_t* rp, const int32_t* nbr, const char* 
 }
 
 // When more candidates than remaining removals exist, keep only the `need` largest by
-// (weight, index): MSB-first search of the 96-bit key (weight bits, index) for the need-th
-// largest, then mark key >= threshold. One block.
+// (weight, index): the need-th largest 96-bit key (weight bits, index) is found digit by digit,
+// 8 bits at a time from the top (a histogram of the candidates that match the digits found so far,
+// then the digit at which the count from the top reaches the number still wanted), and every key
+// >= it is marked. Keys are distinct, so exactly `need` are kept. One block.
 __global__ void __launch_bounds__(1024) select_top_k(const int32_t* cand, const double* w, WseState* st, char* sel) {
-    __shared__ int red[32];
+    __shared__ int hist[256];
+    __shared__ int s_digit, s_rem;
     const long long need = st->need;
     const int nc = st->ncand;
     if (need <= 0 || nc <= need) return;
-    unsigned long long thi = 0;
-    unsigned tlo = 0;
-    for (int b = 95; b >= 0; --b) {
-        unsigned long long hi = thi;
-        unsigned lo = tlo;
-        if (b >= 32) hi |= 1ull << (b - 32);
-        else lo |= 1u << b;
-        int c = 0;
+    unsigned long long thi = 0;  // digits found so far (key bits 95..32)
+    unsigned tlo = 0;            // (key bits 31..0)
+    if (threadIdx.x == 0) s_rem = (int)need;
+    for (int p = 0; p < 12; ++p) {
+        const int top = 95 - 8 * p;  // highest bit of this digit
+        for (int q = threadIdx.x; q < 256; q += blockDim.x) hist[q] = 0;
+        __syncthreads();
         for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-            int32_t i = cand[t];
-            unsigned long long kh = (unsigned long long)__double_as_longlong(w[i]);
-            unsigned kl = (unsigned)i;
-            c += (kh > hi || (kh == hi && kl >= lo)) ? 1 : 0;
+            const int32_t i = cand[t];
+            const unsigned long long kh = (unsigned long long)__double_as_longlong(w[i]);
+            const unsigned kl = (unsigned)i;
+            // match the digits above this one
+            bool match;
+            if (top == 95) match = true;
+            else if (top + 1 >= 32 + 64) match = true;
+            else if (top + 1 > 32) match = (kh >> (top + 1 - 32)) == (thi >> (top + 1 - 32));
+            else match = kh == thi && (top + 1 == 32 || (kl >> (top + 1)) == (tlo >> (top + 1)));
+            if (!match) continue;
+            const int d = top >= 32 ? (int)((kh >> (top - 7 - 32)) & 0xffull) : (int)((kl >> (top - 7)) & 0xffu);
+            atomicAdd(&hist[d], 1);
         }
-        c = warp_sum_i(c);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
         __syncthreads();
-        if (threadIdx.x < 32) {
-            int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
-            v = warp_sum_i(v);
-            if (threadIdx.x == 0) red[0] = v;
+        if (threadIdx.x == 0) {
+            int rem = s_rem, d = 255;
+            for (; d > 0; --d) {
+                if (hist[d] >= rem) break;
+                rem -= hist[d];
+            }
+            s_digit = d;
+            s_rem = rem;
         }
         __syncthreads();
-        int total = red[0];
+        const unsigned dg = (unsigned)s_digit;
+        if (top >= 32) thi |= (unsigned long long)dg << (top - 7 - 32);
+        else tlo |= dg << (top - 7);
         __syncthreads();
-        if (total >= need) { thi = hi; tlo = lo; }
     }
     for (int t = threadIdx.x; t < nc; t += blockDim.x) {
-        int32_t i = cand[t];
-        unsigned long long kh = (unsigned long long)__double_as_longlong(w[i]);
-        unsigned kl = (unsigned)i;
+        const int32_t i = cand[t];
+        const unsigned long long kh = (unsigned long long)__double_as_longlong(w[i]);
+        const unsigned kl = (unsigned)i;
         sel[t] = (kh > thi || (kh == thi && kl >= tlo)) ? 1 : 0;
     }
     if (threadIdx.x == 0) st->selective = 1;

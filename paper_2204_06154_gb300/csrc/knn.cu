@@ -58,12 +58,26 @@ __global__ void bbox_partial_k(const double* x, int64_t n, double* part) {
     }
 }
 
-// one thread: reduce partial boxes, choose h so that the dense grid has at most `cells` cells
-__global__ void grid_params_k(const double* part, int nparts, int64_t cells, double h_min, Grid* g) {
-    double mn[3], mx[3];
-    for (int c = 0; c < 3; ++c) { mn[c] = part[c]; mx[c] = part[3 + c]; }
-    for (int b = 1; b < nparts; ++b)
+// one block of GRID_PARAMS_THREADS: reduce the partial boxes; then one thread chooses h so that the
+// dense grid has at most `cells` cells
+__global__ void __launch_bounds__(GRID_PARAMS_THREADS) grid_params_k(const double* part, int nparts, int64_t cells,
+                                                                     double h_min, Grid* g) {
+    __shared__ double red[6][GRID_PARAMS_THREADS / 32];
+    double mn[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, mx[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x)
         for (int c = 0; c < 3; ++c) { mn[c] = fmin(mn[c], part[6 * b + c]); mx[c] = fmax(mx[c], part[6 * b + 3 + c]); }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c = 0; c < 3; ++c)
+        for (int o = 16; o; o >>= 1) {
+            mn[c] = fmin(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
+            mx[c] = fmax(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+        }
+    if (lane == 0)
+        for (int c = 0; c < 3; ++c) { red[c][w] = mn[c]; red[3 + c][w] = mx[c]; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int c = 0; c < 3; ++c)
+        for (int t = 1; t < (int)(blockDim.x / 32); ++t) { mn[c] = fmin(mn[c], red[c][t]); mx[c] = fmax(mx[c], red[3 + c][t]); }
     double e[3], emax = 0.0;
     for (int c = 0; c < 3; ++c) {
         e[c] = mx[c] - mn[c];
@@ -146,7 +160,7 @@ static void build_grid(const double* x, int64_t n, int64_t cells, double h_min, 
     bbox_partial_k<<<nparts, 256, 0, s>>>(x, n, part.get());
     CK_LAUNCH();
     G.g.alloc(1, s);
-    grid_params_k<<<1, 1, 0, s>>>(part.get(), nparts, cells, h_min, G.g.get());
+    grid_params_k<<<1, GRID_PARAMS_THREADS, 0, s>>>(part.get(), nparts, cells, h_min, G.g.get());
     CK_LAUNCH();
     Temp<int32_t> cnt(cells + 1, s), cell_of(n, s);
     CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (cells + 1), s));

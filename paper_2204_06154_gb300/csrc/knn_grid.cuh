@@ -5,6 +5,7 @@
 namespace mgm {
 
 constexpr int KNN_WARPS = 4;
+constexpr int GRID_PARAMS_THREADS = 256;  // block size grid_params_k must be launched with
 constexpr int KNN_CAP = 1024;  // candidate buffer per warp (>= k + 32 for k <= 256: compaction keeps k)
 
 struct Grid {

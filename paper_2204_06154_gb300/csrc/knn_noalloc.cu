@@ -90,7 +90,7 @@ void knn_noalloc(const double* data, int64_t nd, const double* query, int64_t nq
     const int nparts = (int)std::min<int64_t>(grid_for(nd, 256), NOALLOC_PARTS);
     bbox_partial_k<<<nparts, 256, 0, s>>>(data, nd, part);
     CK_LAUNCH();
-    grid_params_k<<<1, 1, 0, s>>>(part, nparts, cells, 0.0, g);
+    grid_params_k<<<1, GRID_PARAMS_THREADS, 0, s>>>(part, nparts, cells, 0.0, g);
     CK_LAUNCH();
     cell_count_k<<<grid_for(nd, 256), 256, 0, s>>>(data, nd, g, cnt, cell_of);
     CK_LAUNCH();
