@@ -189,6 +189,35 @@ void knn_device(const double* data, int64_t nd, const double* query, int64_t nq,
 // ---------------------------------------------------------------------------------------------
 // warp helpers
 // ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier of a cooperative launch: a monotone arrival counter in global memory (`target` =
+// blocks x barriers passed so far). Each wait is bounded: past `limit` polls the block records
+// MGM_ERR_TIMEOUT in `err`; a block that sees `err` set stops waiting. Returns false (for every
+// thread of the block) in either case, and the caller leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, unsigned long long limit, int* err, int* ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        unsigned long long it = 0;
+        int good = 1;
+        while (ld_acquire_u32(bar) < target) {
+            if (*(volatile int*)err) { good = 0; break; }
+            if (++it > limit) { atomicOr(err, MGM_ERR_TIMEOUT); good = 0; break; }
+            __nanosleep(32);
+        }
+        __threadfence();
+        *ok = good;
+    }
+    __syncthreads();
+    return *ok != 0;
+}
+
 // Programmatic dependent launch: a kernel launched with launch_pdl may be scheduled while its
 // predecessor in the stream is still running. pdl_trigger lets the successor start; pdl_wait blocks
 // until the predecessor has completed and its memory is visible (it returns at once when the

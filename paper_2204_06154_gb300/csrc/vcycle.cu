@@ -209,31 +209,6 @@ constexpr int PS_THREADS = 512;
 constexpr int PS_ROWS = PS_THREADS / G;   // rows per block pass
 constexpr unsigned long long PS_SPIN_LIMIT = 4000000ull;
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// returns false (for every thread of the block) when the wait timed out or another block failed
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, unsigned long long limit, int* err, int* ok) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
-        unsigned long long it = 0;
-        int good = 1;
-        while (ld_acquire_u32(bar) < target) {
-            if (*(volatile int*)err) { good = 0; break; }
-            if (++it > limit) { atomicOr(err, MGM_ERR_TIMEOUT); good = 0; break; }
-            __nanosleep(32);
-        }
-        __threadfence();
-        *ok = good;
-    }
-    __syncthreads();
-    return *ok != 0;
-}
 
 template <int MODE, class T>
 __global__ void __launch_bounds__(PS_THREADS) psweep_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ mid,
