@@ -74,9 +74,30 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(rank):
+    """Seed of a rank's problems: ranks solve different seeded surfaces (weak scaling)."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(ms, world, device=None):
+    """Timing of the whole job: the slowest rank's (a MAX all-reduce; the identity on one rank)."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_ms_per_problem(ms_total, steps, nprob, world):
+    """Time per problem of the whole job: every rank solves nprob problems a step."""
+    return ms_total / (steps * nprob * world)
+
+
 def problems(N, rank):
     from paper_2204_06154_gb300 import inputs as I
-    seed = 2 + 1000 * rank
+    seed = rank_seed(rank)
     xs, ns = I.fibonacci_sphere(N, jitter=0.1, seed=seed)
     xt, nt = I.torus_grid(N, 1.0, 1.0 / 3.0, jitter=0.1, seed=seed)
     return [("sphere", xs, ns, I.random_sh_rhs(xs, 20, seed)), ("torus", xt, nt, I.random_sh_rhs(xt, 20, seed))]
@@ -195,11 +216,7 @@ def bench_ours(a, rank, world, local_rank):
         e1.synchronize()
     barrier()
     launches = M.kernel_launches() - l0
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     nprob = len(dprobs)
     res = {"ms_total": ms, "records": records, "launches": launches, "clocks": clk.summary(), "nprob": nprob}
 
@@ -465,7 +482,7 @@ def main():
         return
     recs = res["records"]
     K = a.steps
-    per_problem = res["ms_total"] / (K * res["nprob"])
+    per_problem = whole_job_ms_per_problem(res["ms_total"], K, res["nprob"], world)
     mean = lambda key, rs=recs: statistics.mean(r[key] for r in rs)
     solve_mixed = mean("solve_ms")
     solve_fp64 = mean("solve_ms", res["fp64"])
