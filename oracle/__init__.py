@@ -598,3 +598,13 @@ def heat_geodesic(xyz, nrm, source, n=30, ell_lap=2, ell_grad=2, k=1, dt=0.01, s
     phi, lam, it, rel = fgmres_bordered(D, H2, div, tol=tol)
     its.append(it)
     return phi - phi[source], its
+
+
+def eigs_smallest(L, nev):
+    """Eigenpairs of L of smallest magnitude, by the plain definition: a dense eigen-decomposition
+    (small N only). Sec. 6.1 finds the same pairs by Arnoldi on the shifted inverse (shift -1 for
+    the operator -D, i.e. L = I - D). Returns (eigenvalues, N x nev eigenvectors), increasing |lambda|."""
+    A = L.toarray() if sp.issparse(L) else np.asarray(L)
+    lam, V = np.linalg.eig(A)
+    o = np.argsort(np.abs(lam), kind="stable")[:nev]
+    return lam[o], V[:, o]
