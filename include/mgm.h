@@ -270,6 +270,23 @@ mgm_status mgm_solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* 
 mgm_status mgm_solve_batched(mgm_hierarchy* const* H, int nprob, const double* const* F, double* const* U, int nrhs,
                              const mgm_solve_params* sp, mgm_solve_info* info, mgm_stream stream);
 
+/* Eigenpairs of the hierarchy's operator L of smallest magnitude (Sec. 6.1: Arnoldi on the shifted
+ * inverse, each application of L^-1 an MGM-preconditioned FGMRES solve with sp). With L = I - D
+ * (mgm_stencil_params.mu = 1) they are 1 + the eigenvalues of -D nearest 0: the shift
+ * sigma = -1 of Sec. 6.1 for the operator -D. Method: block Krylov subspace of A = L^-1 with
+ * thick restarts and Rayleigh-Ritz; b (1..8) right-hand sides per mgm_solve_multi call, s blocks
+ * per cycle, nev + b Ritz vectors kept at a restart; nev + (s + 1) b <= 96 and <= N.
+ * Outputs: lam_re, lam_im (HOST, nev): eigenvalues of L in increasing magnitude; resid (HOST, nev,
+ * may be NULL): relative Ritz residual ||A v - theta v|| / |theta| of each pair, theta = 1/lambda;
+ * evec (DEVICE, N x nev column-major, caller order, may be NULL): eigenvectors of unit 2-norm; a
+ * complex pair (lambda, conj lambda) in columns j, j+1 holds the real and imaginary parts of the
+ * eigenvector of lambda; *nconv: pairs among the nev with resid <= tol; *nsolves: right-hand sides
+ * solved. Not for constrained hierarchies. Stops after max_cycles cycles (then *nconv < nev,
+ * status MGM_OK). */
+mgm_status mgm_eigs(mgm_hierarchy* H, int nev, int b, int s, int max_cycles, double tol, const mgm_solve_params* sp,
+                    uint64_t seed, double* lam_re, double* lam_im, double* resid, double* evec, int* nconv,
+                    int* nsolves, mgm_stream stream);
+
 /* Sizes of the hierarchy (host struct). */
 mgm_status mgm_hierarchy_stats_get(const mgm_hierarchy* H, mgm_hierarchy_stats* out);
 

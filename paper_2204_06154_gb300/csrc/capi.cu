@@ -195,6 +195,14 @@ mgm_status mgm_solve_batched(mgm_hierarchy* const* H, int nprob, const double* c
     return first;
 }
 
+mgm_status mgm_eigs(mgm_hierarchy* H, int nev, int b, int s, int max_cycles, double tol, const mgm_solve_params* sp,
+                    uint64_t seed, double* lam_re, double* lam_im, double* resid, double* evec, int* nconv,
+                    int* nsolves, mgm_stream stream) {
+    return guarded([&] {
+        eigs(H, nev, b, s, max_cycles, tol, sp, seed, lam_re, lam_im, evec, resid, nconv, nsolves, S(stream));
+    });
+}
+
 mgm_status mgm_hierarchy_stats_get(const mgm_hierarchy* H, mgm_hierarchy_stats* out) {
     return guarded([&] {
         REQUIRE(H && out, "null argument");

@@ -134,4 +134,8 @@ void learned_correct(mgm_hierarchy* H, cudaStream_t s);     // e_0 += correction
 void solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* U, const mgm_solve_params* sp, mgm_solve_info* info,
                  cudaStream_t s);
 void free_multi(mgm_hierarchy* H);
+// eigs.cu
+void eigs(mgm_hierarchy* H, int nev, int b, int s_steps, int max_cycles, double tol, const mgm_solve_params* sp,
+          uint64_t seed, double* lam_re, double* lam_im, double* evec, double* resid, int* nconv, int* nsolves,
+          cudaStream_t s);
 }  // namespace mgm

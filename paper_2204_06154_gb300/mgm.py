@@ -64,7 +64,7 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_mlp_size", "mgm_mlp_create", "mgm_mlp_destroy", "mgm_mlp_get", "mgm_mlp_set", "mgm_mlp_forward",
            "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
            "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
-           "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence"]
+           "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs"]
 
 
 class ProfileInfo(C.Structure):
@@ -127,6 +127,8 @@ def lib():
         L.mgm_learned_enable.argtypes = [P, P, P]
         L.mgm_learned_correction.argtypes = [P, P, P, P]
         L.mgm_learned_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
+        L.mgm_eigs.argtypes = [P, I, I, I, I, C.c_double, C.POINTER(SolveParams), C.c_uint64, P, P, P, P,
+                               C.POINTER(C.c_int), C.POINTER(C.c_int), P]
         L.mgm_status_string.restype = C.c_char_p
         L.mgm_last_error_message.restype = C.c_char_p
         L.mgm_last_error_row.restype = C.c_int64
@@ -402,6 +404,21 @@ class Hierarchy:
         return u, {"iters": info.iters, "rel_res": info.rel_res, "solve_ms": info.solve_ms, "converged": st == 0,
                    "history": [hist[i] for i in range(info.iters + 1)], "multiplier": info.multiplier}
 
+
+    def eigs(self, nev=16, block=8, steps=3, max_cycles=20, tol=1e-8, solve_tol=1e-10, restart=50, maxit=200,
+             seed=0, vectors=True):
+        """Eigenpairs of L of smallest magnitude by shift-invert (Sec. 6.1; see mgm_eigs). Returns
+        (eigenvalues as complex numpy array, eigenvectors N x nev device tensor or None, info)."""
+        import numpy as np
+        N = self.stats()["n"][0]
+        sp = SolveParams(_KRYLOV["fgmres"], restart, maxit, solve_tol)
+        lr = (C.c_double * nev)(); li = (C.c_double * nev)(); rs = (C.c_double * nev)()
+        vec = torch.empty((nev, N), dtype=torch.float64, device=self.device) if vectors else None
+        nconv = C.c_int(0); nsol = C.c_int(0)
+        _check(lib().mgm_eigs(self._h, nev, block, steps, max_cycles, tol, C.byref(sp), seed, lr, li, rs,
+                              _p(vec) if vectors else None, C.byref(nconv), C.byref(nsol), _stream()))
+        lam = np.array(lr[:]) + 1j * np.array(li[:])
+        return lam, (vec.T if vectors else None), {"resid": list(rs[:]), "nconv": nconv.value, "solves": nsol.value}
 
     # ---- learned correction after the V-cycle (an addition to the paper's method)
     def learned_attach(self, xyz, nrm, idx, w):
