@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
                     help="c2: the N=1M sphere/torus time-to-solution line; c3: the full 64-surface batched line")
     ap.add_argument("--batch-problems", type=int, default=16, help="surfaces in the batched measurement of the c2 line")
+    ap.add_argument("--eigs", type=int, default=16, help="shift-invert eigenpairs computed on the 1M sphere (0: none)")
     ap.add_argument("--learned-surfaces", type=int, default=24,
                     help="training surfaces of the learned-correction measurement (0 skips it)")
     ap.add_argument("--learned-eval-size", type=int, default=1 << 20, help="points of the held-out bumpy torus")
@@ -234,6 +235,8 @@ def bench_ours(a, rank, world, local_rank):
     r, H, u = run_problem(M, torch, x, n, f)
     res["profile"] = H.profile(reps=20)
     res["stats"] = H.stats()
+    if a.eigs > 0:
+        res["eigs"] = bench_eigs(torch, H, a.eigs)
     del H, u
     # e2e: pinned host inputs -> device -> whole path -> solution back to the host
     hp = [(torch.from_numpy(x).pin_memory(), torch.from_numpy(nn).pin_memory(), torch.from_numpy(f).pin_memory())
@@ -392,6 +395,23 @@ def bench_learned(nsurf, Neval, dev):
                                   "GB/s": round(pr["learned_bytes"] / pr["learned_ms"] / 1e6, 1) if pr["learned_ms"] else None}}
 
 
+def bench_eigs(torch, H, nev):
+    """Shift-invert eigenpairs (Sec. 6.1) of L = I - D on the sphere: the nev of smallest magnitude,
+    each application of L^-1 a batched MGM-FGMRES solve to 1e-10. Eigenvalues of -D = lambda - 1
+    against l(l+1)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lam, _, info = H.eigs(nev=nev, block=8, steps=3, max_cycles=20, tol=1e-8, solve_tol=1e-10, vectors=False)
+    e1.record()
+    e1.synchronize()
+    lap = sorted(float(z.real) - 1.0 for z in lam)
+    exact = [l * (l + 1) for l in range(8) for _ in range(2 * l + 1)][:nev]
+    return {"nev": nev, "ms": round(e0.elapsed_time(e1), 1), "solves": info["solves"], "converged": info["nconv"],
+            "max_resid": max(info["resid"]), "eigenvalues_of_minus_D": [round(v, 5) for v in lap],
+            "max_rel_dev_from_l(l+1)": round(max(abs(v - e) / max(e, 1) for v, e in zip(lap, exact)), 5)}
+
+
 def cpu_baseline(a, Ns=None):
     Ns = Ns or a.cpu_sample
     ms, it, rel = oracle_sample(Ns)
@@ -541,6 +561,7 @@ def main():
         "gpu_launches": res["launches"],
         "batched": res.get("batched"),
         "learned": res.get("learned"),
+        "eigs": res.get("eigs"),
         "clocks": res["clocks"],
     }
     if not a.no_cpu_baseline and world == 1:
