@@ -94,7 +94,13 @@ typedef struct {
                         operators bordered as eq. (gco_saddle_point), smoothing on u only, the
                         coarsest bordered system inverted directly. Solved by mgm_solve (FGMRES); the
                         multiplier is returned in mgm_solve_info.multiplier. */
+    int smoother;    /* MGM_SMOOTHER_MC (0): multicolour Gauss-Seidel (colours by Jones-Plassmann).
+                        MGM_SMOOTHER_LEX (1): lexicographic Gauss-Seidel in the level's RCM order, the
+                        paper's smoother (Sec. 4.3, Alg. 3); run as one flag-driven launch per sweep
+                        (each row waits for its lower neighbours; persistent_sweeps is then ignored). */
 } mgm_params;
+
+enum { MGM_SMOOTHER_MC = 0, MGM_SMOOTHER_LEX = 1 };
 
 typedef struct {
     int krylov;      /* MGM_KRYLOV_FGMRES, MGM_KRYLOV_BICGSTAB or MGM_KRYLOV_NONE (repeated V-cycles) */

@@ -364,13 +364,17 @@ __global__ void split_fill_long_k(const int32_t* rp, const int32_t* ci, const do
     dinv32[s] = (float)(1.0 / d);
 }
 
-static void build_solve_layout(Level& L, bool single, cudaStream_t s) {
+static void build_solve_layout(Level& L, bool single, cudaStream_t s, bool lex = false) {
     const int64_t n = L.n;
     L.ord.alloc(n);
     L.inv.alloc(n);
     if (single) {
         iota_i32(L.ord.get(), n, s);
         L.cptr = {0, (int32_t)n};
+    } else if (lex) {  // the rows in their own order, one class each
+        iota_i32(L.ord.get(), n, s);
+        L.cptr.resize(n + 1);
+        for (int64_t i = 0; i <= n; ++i) L.cptr[i] = (int32_t)i;
     } else {
         const int nc = L.ncolors;
         const int nblocks = (int)grid_for(n, 256);
@@ -530,8 +534,10 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     H->m = prm->m;
     H->seed = prm->seed;
     REQUIRE(prm->persistent_sweeps >= 0 && prm->persistent_sweeps <= 2, "persistent_sweeps must be 0, 1 or 2");
-    H->sweep_mode = prm->persistent_sweeps;
-    H->persistent = prm->persistent_sweeps != 0;
+    REQUIRE(prm->smoother == MGM_SMOOTHER_MC || prm->smoother == MGM_SMOOTHER_LEX, "unknown smoother");
+    const bool lex = prm->smoother == MGM_SMOOTHER_LEX;
+    H->sweep_mode = lex ? 2 : prm->persistent_sweeps;  // lexicographic: one row per group, flag-driven
+    H->persistent = H->sweep_mode != 0;
     REQUIRE(prm->constraint == 0 || prm->constraint == 1, "constraint must be 0 or 1");
     H->bordered = prm->constraint == 1;
     H->N = N;
@@ -615,10 +621,15 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         Level& L = H->lv[j];
         L.colour.alloc(L.n);
         int32_t nc = 0;
-        color(L.n, L.rp.get(), L.ci.get(), prm->seed, L.colour.get(), &nc, s);
+        if (lex) {  // every row its own class, in the level's (RCM) order
+            iota_i32(L.colour.get(), L.n, s);
+            nc = (int32_t)L.n;
+        } else {
+            color(L.n, L.rp.get(), L.ci.get(), prm->seed, L.colour.get(), &nc, s);
+        }
         L.ncolors = nc;
         tr.mark("colour", j);
-        build_solve_layout(L, false, s);
+        build_solve_layout(L, false, s, lex);
         tr.mark("layout", j);
     }
     if (p == 1) build_solve_layout(H->lv[0], true, s);  // one group: serves the outer operator only
