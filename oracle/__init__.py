@@ -63,9 +63,11 @@ def lib():
         L.or_tangent_basis.argtypes = [f64p, f64p, f64p]
         L.or_last_bad_row.restype = C.c_int64
         L.or_vcycle.argtypes = [C.c_void_p, C.c_int, f64p, i32p, C.c_void_p, C.c_int, C.c_int, f64p, f64p]
+        L.or_mgcycle.argtypes = [C.c_void_p, C.c_int, f64p, i32p, C.c_void_p, C.c_int, C.c_int, C.c_int, f64p, f64p]
         L.or_fgmres.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_int, C.c_int, C.c_int, f64p, f64p, C.c_int, C.c_int, C.c_double,
                                 C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_void_p]
+        L.or_fgmres_cycle.argtypes = L.or_fgmres.argtypes
         L.or_vcycle_bordered.argtypes = [C.c_void_p, C.c_int, C.c_void_p, f64p, i32p, C.c_void_p, C.c_int, C.c_int,
                                          f64p, C.c_double, f64p, C.POINTER(C.c_double)]
         L.or_fgmres_bordered.argtypes = [i64, i32p, i32p, f64p, C.c_void_p, C.c_int, C.c_void_p, f64p, i32p, C.c_void_p,
@@ -415,9 +417,20 @@ def vcycle(H, f, u=None):
     return u
 
 
-def fgmres(A, H, f, x0=None, restart=50, maxit=200, tol=1e-10, precond=True, hist=False):
-    """Right-preconditioned FGMRES(restart) with one MGM V-cycle per iteration (Sec. 4.6).
-    Returns (x, iterations, true relative residual[, history])."""
+def mgcycle(H, f, cycle="V", u=None):
+    """One multigrid cycle of type "V", "W" or "F" (recursive definitions; see or_mgcycle) for the
+    right-hand side f (caller order) from the initial guess u (zero when None)."""
+    f = _c(f, np.float64)
+    u = np.zeros_like(f) if u is None else _c(u, np.float64).copy()
+    lv = H._levels()
+    _check("mgcycle", lib().or_mgcycle(C.addressof(lv), H.p, H.lu, H.piv, H.perm[0].ctypes.data, H.nu1, H.nu2,
+                                       {"V": 0, "W": 1, "F": 2}[cycle], f, u))
+    return u
+
+
+def fgmres(A, H, f, x0=None, restart=50, maxit=200, tol=1e-10, precond=True, hist=False, cycle="V"):
+    """Right-preconditioned FGMRES(restart) with one MGM cycle per iteration (Sec. 4.6; a V-cycle,
+    or with cycle="W" / "F" a W- or F-cycle). Returns (x, iterations, true relative residual[, history])."""
     rp, ci, v = _csr(A)
     n = A.shape[0]
     f = _c(f, np.float64)
@@ -431,8 +444,14 @@ def fgmres(A, H, f, x0=None, restart=50, maxit=200, tol=1e-10, precond=True, his
         lvp, p, lu, piv, perm = None, 0, None, None, None
         if precond:
             raise ValueError("FGMRES with a one-level hierarchy: use a direct solve")
-    st = lib().or_fgmres(n, rp, ci, v, lvp, p, lu, piv, perm, H.nu1 if H else 1, H.nu2 if H else 1,
-                         int(precond), f, x, restart, maxit, tol, C.byref(it), C.byref(rel), hbuf.ctypes.data)
+    if cycle == "V":
+        st = lib().or_fgmres(n, rp, ci, v, lvp, p, lu, piv, perm, H.nu1 if H else 1, H.nu2 if H else 1,
+                             int(precond), f, x, restart, maxit, tol, C.byref(it), C.byref(rel), hbuf.ctypes.data)
+    else:
+        if not precond or p < 2:
+            raise ValueError("W and F cycles need a multilevel preconditioner")
+        st = lib().or_fgmres_cycle(n, rp, ci, v, lvp, p, lu, piv, perm, H.nu1, H.nu2, {"W": 1, "F": 2}[cycle], f, x,
+                                   restart, maxit, tol, C.byref(it), C.byref(rel), hbuf.ctypes.data)
     if st not in (0, 3):
         _check("fgmres", st)
     out = (x, it.value, rel.value)

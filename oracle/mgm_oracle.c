@@ -971,6 +971,69 @@ int or_vcycle(const or_level* lv, int p, const double* lu, const int32_t* piv, c
     return OR_OK;
 }
 
+/* ===========================================================================================
+ * Multigrid cycles in recursive form (Sec. 4.5 names V, W and F cycles; Alg. 3 is the V-cycle).
+ * Level j with right-hand side f_j and iterate e_j: nu1 GS sweeps, f_{j+1} = R_j (f_j - L_j e_j),
+ * e_{j+1} = 0, then the coarse visits -- V: one V-cycle; W: two W-cycles, the second from the
+ * first's result; F: one F-cycle, then one V-cycle from its result -- then e_j += P_j e_{j+1} and
+ * nu2 sweeps. The coarsest level is solved by the LU factors. type: 0 V, 1 W, 2 F. With a zero
+ * initial guess the V form performs the operations of or_vcycle in the same order.
+ * =========================================================================================== */
+typedef struct {
+    const or_level* lv;
+    int p, nu1, nu2;
+    const double* lu;
+    const int32_t* piv;
+    double **f, **e, **tmp;
+} mg_ctx;
+
+static void mg_rec(const mg_ctx* c, int j, int type, int zero_start) {
+    const or_level* L = &c->lv[j];
+    if (j == c->p - 1) {
+        for (int64_t i = 0; i < L->n; ++i) c->e[j][i] = c->f[j][i];
+        or_lu_solve(c->lu, L->n, c->piv, c->e[j]);
+        return;
+    }
+    if (zero_start)
+        for (int64_t i = 0; i < L->n; ++i) c->e[j][i] = 0.0;
+    for (int s = 0; s < c->nu1; ++s) or_gs_sweep(L, c->f[j], c->e[j]);
+    residual(L, c->f[j], c->e[j], c->tmp[j]);
+    csr_apply(c->lv[j + 1].n, L->rrp, L->rc, L->rv, c->tmp[j], c->f[j + 1]);
+    if (type == 0) {
+        mg_rec(c, j + 1, 0, 1);
+    } else if (type == 1) {
+        mg_rec(c, j + 1, 1, 1);
+        mg_rec(c, j + 1, 1, 0);
+    } else {
+        mg_rec(c, j + 1, 2, 1);
+        mg_rec(c, j + 1, 0, 0);
+    }
+    csr_apply(L->n, L->pp, L->pc, L->pv, c->e[j + 1], c->tmp[j]);
+    for (int64_t i = 0; i < L->n; ++i) c->e[j][i] = c->e[j][i] + c->tmp[j][i];
+    for (int s = 0; s < c->nu2; ++s) or_gs_sweep(L, c->f[j], c->e[j]);
+}
+
+int or_mgcycle(const or_level* lv, int p, const double* lu, const int32_t* piv, const int32_t* perm1, int nu1, int nu2,
+               int type, const double* fin, double* uio) {
+    if (p < 2 || type < 0 || type > 2) return OR_ERR_ARG;
+    const int64_t n1 = lv[0].n;
+    mg_ctx c = {lv, p, nu1, nu2, lu, piv, NULL, NULL, NULL};
+    c.f = (double**)calloc(p, sizeof(double*));
+    c.e = (double**)calloc(p, sizeof(double*));
+    c.tmp = (double**)calloc(p, sizeof(double*));
+    for (int j = 0; j < p; ++j) {
+        c.f[j] = (double*)calloc(lv[j].n, sizeof(double));
+        c.e[j] = (double*)calloc(lv[j].n, sizeof(double));
+        c.tmp[j] = (double*)calloc(lv[j].n, sizeof(double));
+    }
+    for (int64_t i = 0; i < n1; ++i) { int64_t o = perm1 ? perm1[i] : i; c.f[0][i] = fin[o]; c.e[0][i] = uio[o]; }
+    mg_rec(&c, 0, type, 0);
+    for (int64_t i = 0; i < n1; ++i) { int64_t o = perm1 ? perm1[i] : i; uio[o] = c.e[0][i]; }
+    for (int j = 0; j < p; ++j) { free(c.f[j]); free(c.e[j]); free(c.tmp[j]); }
+    free(c.f); free(c.e); free(c.tmp);
+    return OR_OK;
+}
+
 static double nrm2(int64_t n, const double* x) { double s = 0.0; for (int64_t i = 0; i < n; ++i) s = s + x[i] * x[i]; return sqrt(s); }
 static double dot(int64_t n, const double* a, const double* b) { double s = 0.0; for (int64_t i = 0; i < n; ++i) s = s + a[i] * b[i]; return s; }
 
@@ -1065,11 +1128,12 @@ static void csr_apply_cb(void* c, const double* x, double* y) {
     const or_csr_ctx* a = (const or_csr_ctx*)c;
     csr_apply(a->n, a->rp, a->ci, a->v, x, y);
 }
-typedef struct { const or_level* lv; int p; const double* lu; const int32_t* piv; const int32_t* perm1; int nu1, nu2; int64_t n; } or_mgm_ctx;
+typedef struct { const or_level* lv; int p; const double* lu; const int32_t* piv; const int32_t* perm1; int nu1, nu2; int64_t n; int type; } or_mgm_ctx;
 static void vcycle_cb(void* c, const double* v, double* z) {
     const or_mgm_ctx* m = (const or_mgm_ctx*)c;
     for (int64_t i = 0; i < m->n; ++i) z[i] = 0.0;
-    or_vcycle(m->lv, m->p, m->lu, m->piv, m->perm1, m->nu1, m->nu2, v, z);
+    if (m->type == 0) or_vcycle(m->lv, m->p, m->lu, m->piv, m->perm1, m->nu1, m->nu2, v, z);
+    else or_mgcycle(m->lv, m->p, m->lu, m->piv, m->perm1, m->nu1, m->nu2, m->type, v, z);
 }
 
 int or_fgmres(int64_t n, const int32_t* arp, const int32_t* aci, const double* av,
@@ -1077,9 +1141,20 @@ int or_fgmres(int64_t n, const int32_t* arp, const int32_t* aci, const double* a
               int precond, const double* f, double* x, int restart, int maxit, double tol,
               int* iters_out, double* relres_out, double* hist) {
     or_csr_ctx a = {n, arp, aci, av};
-    or_mgm_ctx m = {lv, p, lu, piv, perm1, nu1, nu2, n};
+    or_mgm_ctx m = {lv, p, lu, piv, perm1, nu1, nu2, n, 0};
     return fgmres_core(n, csr_apply_cb, &a, precond ? vcycle_cb : NULL, &m, f, x, restart, maxit, tol, iters_out, relres_out,
                        hist);
+}
+
+/* or_fgmres with one multigrid cycle of type `cycle` (0 V, 1 W, 2 F; or_mgcycle) per iteration */
+int or_fgmres_cycle(int64_t n, const int32_t* arp, const int32_t* aci, const double* av,
+                    const or_level* lv, int p, const double* lu, const int32_t* piv, const int32_t* perm1, int nu1,
+                    int nu2, int cycle, const double* f, double* x, int restart, int maxit, double tol,
+                    int* iters_out, double* relres_out, double* hist) {
+    if (cycle < 0 || cycle > 2) return OR_ERR_ARG;
+    or_csr_ctx a = {n, arp, aci, av};
+    or_mgm_ctx m = {lv, p, lu, piv, perm1, nu1, nu2, n, cycle};
+    return fgmres_core(n, csr_apply_cb, &a, vcycle_cb, &m, f, x, restart, maxit, tol, iters_out, relres_out, hist);
 }
 
 /* ===========================================================================================

@@ -459,3 +459,46 @@ def test_bicgstab_unpreconditioned_matches_direct_and_counts(oracle):
     assert rel <= 1e-11 and np.linalg.norm(u - ue) <= 1e-8 * np.linalg.norm(ue)
     u0, apps0, rel0 = oracle.bicgstab(L, None, f, x0=ue, tol=1e-9, maxit=10, precond=False)
     assert apps0 == 0 and rel0 <= 1e-9
+
+
+# ----------------------------------------------------------------------------------------------
+# W- and F-cycles (Sec. 4.5 names them; Alg. 3 is the V-cycle)
+# ----------------------------------------------------------------------------------------------
+def test_recursive_v_cycle_is_alg3(oracle):
+    """The recursive cycle of type V performs Alg. 3's operations in the same order."""
+    x, L = _small_problem(4)
+    H = oracle.setup(x, L, 40, seed=1)
+    assert H.p >= 3
+    f = np.random.default_rng(2).standard_normal(L.shape[0])
+    assert np.array_equal(oracle.mgcycle(H, f, "V"), oracle.vcycle(H, f))
+
+
+def test_two_levels_all_cycles_agree(oracle):
+    """With two levels the coarse problem is solved exactly, so a second coarse visit changes
+    nothing: V, W and F cycles coincide."""
+    x, L = _small_problem(3)
+    H = oracle.setup(x, L, L.shape[0] // 4, seed=5)
+    assert H.p == 2
+    f = np.random.default_rng(0).standard_normal(L.shape[0])
+    z = oracle.mgcycle(H, f, "V")
+    assert np.array_equal(oracle.mgcycle(H, f, "W"), z) and np.array_equal(oracle.mgcycle(H, f, "F"), z)
+
+
+def test_w_and_f_cycles_contract_at_least_as_well_as_v(oracle):
+    """More coarse work per cycle: three cycles as a stationary iteration on L u = 0 from a random
+    error leave W <= F <= V (each coarse visit of W and F repeats or extends the V-cycle's)."""
+    x, L = _small_problem(4)
+    H = oracle.setup(x, L, 40, seed=1)
+    assert H.p >= 3
+    e0 = np.random.default_rng(1).standard_normal(L.shape[0])
+    red = {}
+    for cyc in "VFW":
+        u = e0.copy()
+        for _ in range(3):
+            u = u + oracle.mgcycle(H, -(L @ u), cyc)
+        red[cyc] = np.linalg.norm(u) / np.linalg.norm(e0)
+    assert red["W"] <= red["F"] * (1 + 1e-12) and red["F"] < red["V"], red
+    f = np.random.default_rng(0).standard_normal(L.shape[0])
+    for cyc in "WF":
+        u, it, rel = oracle.fgmres(L, H, f, tol=1e-10, cycle=cyc)
+        assert rel <= 1e-10
