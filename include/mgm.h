@@ -98,9 +98,14 @@ typedef struct {
                         MGM_SMOOTHER_LEX (1): lexicographic Gauss-Seidel in the level's RCM order, the
                         paper's smoother (Sec. 4.3, Alg. 3); run as one flag-driven launch per sweep
                         (each row waits for its lower neighbours; persistent_sweeps is then ignored). */
+    int cycle;       /* MGM_CYCLE_V (0): the V-cycle of Alg. 3. MGM_CYCLE_W (1): W-cycle, two visits of
+                        every coarse level from each finer one (the second from the first's result).
+                        MGM_CYCLE_F (2): F-cycle, an F-cycle then a V-cycle on each coarse level
+                        (Sec. 4.5 names both). Not for constrained hierarchies. */
 } mgm_params;
 
 enum { MGM_SMOOTHER_MC = 0, MGM_SMOOTHER_LEX = 1 };
+enum { MGM_CYCLE_V = 0, MGM_CYCLE_W = 1, MGM_CYCLE_F = 2 };
 
 typedef struct {
     int krylov;      /* MGM_KRYLOV_FGMRES, MGM_KRYLOV_BICGSTAB or MGM_KRYLOV_NONE (repeated V-cycles) */

@@ -67,6 +67,7 @@ struct Level {
 
 struct mgm_hierarchy {
     int p = 0;
+    int cycle = 0;     // MGM_CYCLE_V / W / F
     int precision = MGM_F32;
     int nu1 = 1, nu2 = 1, m = 3;
     uint64_t seed = 0;

@@ -540,6 +540,9 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     H->persistent = H->sweep_mode != 0;
     REQUIRE(prm->constraint == 0 || prm->constraint == 1, "constraint must be 0 or 1");
     H->bordered = prm->constraint == 1;
+    REQUIRE(prm->cycle >= MGM_CYCLE_V && prm->cycle <= MGM_CYCLE_F, "unknown cycle type");
+    REQUIRE(prm->cycle == MGM_CYCLE_V || !H->bordered, "W and F cycles: not for constrained hierarchies");
+    H->cycle = prm->cycle;
     H->N = N;
     int p = num_levels(N, prm->n_min);
     if (p > 16) fail(MGM_ERR_UNSUPPORTED, "more than 16 levels");

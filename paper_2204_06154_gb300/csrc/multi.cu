@@ -565,6 +565,7 @@ void solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* U, const m
     REQUIRE(H && F && U && sp, "null argument");
     REQUIRE(nrhs >= 1 && nrhs <= 8, "nrhs must be in [1, 8]");
     REQUIRE(!H->bordered, "many right-hand sides: not for constrained (bordered) hierarchies");
+    REQUIRE(H->cycle == MGM_CYCLE_V, "many right-hand sides: V-cycle hierarchies only");
     REQUIRE(sp->krylov == MGM_KRYLOV_FGMRES || sp->krylov == MGM_KRYLOV_NONE, "unknown krylov method");
     REQUIRE(sp->maxit >= 0 && sp->tol >= 0.0, "maxit and tol must be >= 0");
     REQUIRE(sp->krylov != MGM_KRYLOV_FGMRES || (sp->restart >= 1 && sp->restart <= 200), "restart must be in [1, 200]");

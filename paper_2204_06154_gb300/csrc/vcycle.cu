@@ -557,7 +557,14 @@ __global__ void bshift_k(T* b, const T* __restrict__ c, const T* mu, int64_t n) 
 }
 
 template <class T>
+static void cycle_rec(mgm_hierarchy* H, int j, int type, bool zero_start, cudaStream_t s);
+
+template <class T>
 static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
+    if (H->cycle != MGM_CYCLE_V) {
+        cycle_rec<T>(H, 0, H->cycle, true, s);
+        return;
+    }
     const int p = H->p;
     for (int j = 0; j + 1 < p; ++j) {  // pre-smoothing and restricted residuals
         Level& L = H->lv[j];
@@ -600,6 +607,53 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
         }
         for (int t = 0; t < H->nu2; ++t) sweep_any<T>(H, L, false, s);
     }
+}
+
+// W- and F-cycles (Sec. 4.5), recursive: level j smooths (from zero on a first visit, with the
+// lower-part sweep and the -U e residual identity, as the V-cycle; otherwise full sweeps from the
+// current iterate and the full residual), restricts, visits level j+1 (V: once; W: twice, the second
+// from the first's result; F: an F-cycle, then a V-cycle from its result), interpolates and
+// post-smooths. The coarsest visit applies the inverse, which ignores the starting iterate.
+template <class T>
+static void cycle_rec(mgm_hierarchy* H, int j, int type, bool zero_start, cudaStream_t s) {
+    const int p = H->p;
+    if (j == p - 1) {
+        Level& C = H->lv[p - 1];
+        launch_pdl(coarse_k<T>, grid_for(H->nb * 32, 256), 256, s, (const double*)H->Ainv.get(), (const T*)LV<T>::b(C),
+                   LV<T>::e(C), (int64_t)H->nb);
+        return;
+    }
+    Level& L = H->lv[j];
+    Level& C = H->lv[j + 1];
+    const T* rsrc;
+    if (zero_start && H->nu1 >= 1) {
+        sweep_any<T>(H, L, true, s);
+        for (int t = 1; t < H->nu1; ++t) sweep_any<T>(H, L, false, s);
+        if (H->nu1 == 1) launch_rows<2, T>(L, 0, (int32_t)L.n, s);
+        else launch_rows<3, T>(L, 0, (int32_t)L.n, s);
+        rsrc = LV<T>::s(L);
+    } else if (zero_start) {
+        CK(cudaMemsetAsync(LV<T>::e(L), 0, sizeof(T) * L.n, s));
+        rsrc = LV<T>::b(L);
+    } else {
+        for (int t = 0; t < H->nu1; ++t) sweep_any<T>(H, L, false, s);
+        launch_rows<3, T>(L, 0, (int32_t)L.n, s);  // s = b - L e
+        rsrc = LV<T>::s(L);
+    }
+    launch_pdl(restrict_k<T>, grid_for(C.n, 256), 256, s, (const int32_t*)L.r_rp.get(), (const int32_t*)L.r_ci.get(),
+               LV<T>::rv(L), rsrc, LV<T>::b(C), (int64_t)C.n);
+    if (type == MGM_CYCLE_V) {
+        cycle_rec<T>(H, j + 1, MGM_CYCLE_V, true, s);
+    } else if (type == MGM_CYCLE_W) {
+        cycle_rec<T>(H, j + 1, MGM_CYCLE_W, true, s);
+        cycle_rec<T>(H, j + 1, MGM_CYCLE_W, false, s);
+    } else {
+        cycle_rec<T>(H, j + 1, MGM_CYCLE_F, true, s);
+        cycle_rec<T>(H, j + 1, MGM_CYCLE_V, false, s);
+    }
+    launch_pdl(interp_k<T>, grid_for(L.n, 256), 256, s, (const int32_t*)L.pc.get(), LV<T>::pv(L), L.pw,
+               (const T*)LV<T>::e(C), LV<T>::e(L), (int64_t)L.n);
+    for (int t = 0; t < H->nu2; ++t) sweep_any<T>(H, L, false, s);
 }
 
 void alloc_work(mgm_hierarchy* H) {

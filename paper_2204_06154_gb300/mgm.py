@@ -38,7 +38,8 @@ class StencilParams(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("n_min", C.c_int64), ("m", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int),
-                ("seed", C.c_uint64), ("persistent_sweeps", C.c_int), ("constraint", C.c_int), ("smoother", C.c_int)]
+                ("seed", C.c_uint64), ("persistent_sweeps", C.c_int), ("constraint", C.c_int), ("smoother", C.c_int),
+                ("cycle", C.c_int)]
 
 
 class SolveParams(C.Structure):
@@ -324,18 +325,21 @@ class Hierarchy:
     """MGM hierarchy (Alg. 2) owned by the library; V-cycle (Alg. 3) and FGMRES solve on it."""
 
     def __init__(self, xyz, rp, ci, v, n_min, m=3, nu1=1, nu2=1, precision="f32", seed=0, persistent_sweeps=False,
-                 constraint=False, smoother="mc"):
+                 constraint=False, smoother="mc", cycle="V"):
         """constraint=True: surface Poisson (L = D) with the mean-zero constraint of Sec. 4.4.
-        smoother: "mc" multicolour Gauss-Seidel or "lex" lexicographic Gauss-Seidel (the paper's)."""
+        smoother: "mc" multicolour Gauss-Seidel or "lex" lexicographic Gauss-Seidel (the paper's).
+        cycle: "V" (Alg. 3), "W" or "F" (Sec. 4.5)."""
         if smoother not in ("mc", "lex"):
             raise ValueError("smoother must be 'mc' or 'lex'")
+        if cycle not in ("V", "W", "F"):
+            raise ValueError("cycle must be 'V', 'W' or 'F'")
         xyz = _dev(xyz, torch.float64, "xyz"); rp = _dev(rp, torch.int32, "rowptr")
         ci = _dev(ci, torch.int32, "col"); v = _dev(v, torch.float64, "val")
         self.N = xyz.shape[0]
         self.device = xyz.device
         self.constraint = bool(constraint)
         prm = Params(n_min, m, nu1, nu2, MGM_F32 if precision == "f32" else MGM_F64, seed, int(persistent_sweeps),
-                     int(constraint), 1 if smoother == "lex" else 0)
+                     int(constraint), 1 if smoother == "lex" else 0, {"V": 0, "W": 1, "F": 2}[cycle])
         h = C.c_void_p()
         self._h = None
         _check(lib().mgm_setup(_p(xyz), self.N, _p(rp), _p(ci), _p(v), C.byref(prm), C.byref(h), _stream()))
