@@ -661,16 +661,12 @@ __global__ void __launch_bounds__(256) phs_weights_rl_k(PhsArgs a, int wpb, int3
     for (int kk = 0; kk < M; ++kk) {
         const unsigned b0 = d0 ? 0u : mag_bits_f(a0[kk]);
         const unsigned b1 = d1 ? 0u : mag_bits_f(a1[kk]);
-        unsigned best = b0;
-        int prow = r0;
-        if (b1 > best) { best = b1; prow = r1; }
-        for (int o = 16; o; o >>= 1) {
-            const unsigned ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int op = __shfl_xor_sync(0xffffffffu, prow, o);
-            if (ob > best || (ob == best && op < prow)) { best = ob; prow = op; }
-        }
-        ok = ok && best > tolb;  // warp-uniform after the reduction; a failed factorisation is discarded
-        const int p = prow, pl = p & 31;
+        // warp maximum in one reduction; the first row holding it (rows lane, then lane + 32)
+        const unsigned best = __reduce_max_sync(0xffffffffu, max(b0, b1));
+        const unsigned m0 = __ballot_sync(0xffffffffu, !d0 && b0 == best);
+        const unsigned m1 = __ballot_sync(0xffffffffu, !d1 && b1 == best);
+        ok = ok && best > tolb;  // warp-uniform; a failed factorisation is discarded
+        const int p = m0 ? __ffs(m0) - 1 : 32 + __ffs(m1) - 1, pl = p & 31;
         const bool hi = p >= 32;
         if (p == r0) { d0 = true; s0 = kk; }
         if (p == r1) { d1 = true; s1 = kk; }
