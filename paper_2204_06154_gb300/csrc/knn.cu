@@ -516,12 +516,14 @@ template <bool FILL>
 __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const int32_t* start, const int32_t* sidx,
                                                            const double* sxyz, const double* x, int64_t n,
                                                            const double* prm /* two_rmax, rmin */, int32_t* cnt,
-                                                           const int32_t* rowptr, int32_t* nbr, double* f, int* err) {
+                                                           const int32_t* rowptr, int32_t* nbr, double* f, int* err,
+                                                           const int32_t* rows, int64_t nrows) {
     __shared__ int si[RAD_WARPS][RAD_CAP];
     __shared__ double sdist[RAD_WARPS][RAD_CAP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * RAD_WARPS + w;
-    if (i >= n) return;
+    const int64_t t_ = (int64_t)blockIdx.x * RAD_WARPS + w;
+    if (t_ >= (rows ? nrows : n)) return;
+    const int64_t i = rows ? (int64_t)rows[t_] : t_;
     const Grid g = *gp;
     const double two_rmax = prm[0], rmin = prm[1];
     const double lim_sq = two_rmax * two_rmax * (1.0 + 1e-9);
@@ -583,27 +585,95 @@ __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const
     }
 }
 
+// The same lists with one thread per point (the lists are short: ~15 entries on the surfaces here):
+// the count pass counts every point and lists those above RT_CAP; the fill pass keeps each list
+// sorted by index in local memory as it is found and writes rows of at most RT_CAP entries (the
+// warp kernel above fills the listed longer ones). Same candidates and tests, so the same lists.
+constexpr int RT_CAP = 48;
+template <bool FILL>
+__global__ void __launch_bounds__(128) radius_thread_k(const Grid* gp, const int32_t* start, const int32_t* sidx,
+                                                       const double* sxyz, const double* x, int64_t n, const double* prm,
+                                                       int32_t* cnt, const int32_t* rowptr, int32_t* nbr, double* f,
+                                                       int32_t* longrows, int* nlong) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Grid g = *gp;
+    const double two_rmax = prm[0], rmin = prm[1];
+    const double lim_sq = two_rmax * two_rmax * (1.0 + 1e-9);
+    const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    const int cx = cell_coord(px, g.x0, g.h, g.nx), cy = cell_coord(py, g.y0, g.h, g.ny), cz = cell_coord(pz, g.z0, g.h, g.nz);
+    const int R = (g.h >= two_rmax * (1.0 + 1e-6)) ? 1 : (int)ceil(two_rmax / g.h) + 1;
+    int count = 0;
+    int jl[RT_CAP];
+    double dl[RT_CAP];
+    for (int z = max(cz - R, 0); z <= min(cz + R, g.nz - 1); ++z)
+        for (int y = max(cy - R, 0); y <= min(cy + R, g.ny - 1); ++y)
+            for (int xx = max(cx - R, 0); xx <= min(cx + R, g.nx - 1); ++xx) {
+                const int64_t c = ((int64_t)z * g.ny + y) * g.nx + xx;
+                const int b = start[c], e = start[c + 1];
+                for (int t = b; t < e; ++t) {
+                    const int j = sidx[t];
+                    if (j == (int)i) continue;
+                    const double dd = d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1],
+                                             sxyz[3 * (int64_t)t + 2]);
+                    if (!(dd <= lim_sq)) continue;
+                    const double d = sqrt(dd);
+                    if (!(d < two_rmax)) continue;
+                    if (FILL && count < RT_CAP) {  // insert by index
+                        int q = count;
+                        while (q > 0 && jl[q - 1] > j) { jl[q] = jl[q - 1]; dl[q] = dl[q - 1]; --q; }
+                        jl[q] = j;
+                        dl[q] = d;
+                    }
+                    ++count;
+                }
+            }
+    if (!FILL) {
+        cnt[i] = count;
+        if (count > RT_CAP) longrows[atomicAdd(nlong, 1)] = (int32_t)i;
+        return;
+    }
+    if (count > RT_CAP) return;
+    const int64_t base = rowptr[i];
+    for (int q = 0; q < count; ++q) {
+        const double dh = dl[q] > rmin ? dl[q] : rmin;
+        const double tt = 1.0 - dh / two_rmax;
+        const double t2 = tt * tt, t4 = t2 * t2;
+        nbr[base + q] = jl[q];
+        f[base + q] = t4 * t4;
+    }
+}
+
 // Builds the neighbour graph for the elimination. prm: device {two_rmax, rmin}; h_hint: a host
 // estimate of two_rmax used to size the grid cells.
 void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, Temp<int32_t>& rowptr,
                   Temp<int32_t>& nbr, Temp<double>& f, cudaStream_t s) {
     DevGrid G;
     build_grid(x, n, 8 * n, h_hint * (1.0 + 1e-5), G, s);  // cells no narrower than 2 r_max: one ring
-    Temp<int32_t> cnt(n + 1, s);
-    Temp<int> err(1, s);
-    CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
-    radius_k<false><<<grid_for(n, RAD_WARPS), RAD_WARPS * 32, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
-                                                                     x, n, prm, cnt.get(), nullptr, nullptr, nullptr, err.get());
+    Temp<int32_t> cnt(n + 1, s), longrows(n, s);
+    Temp<int> err(2, s);  // [0] warp-kernel overflow, [1] rows above RT_CAP
+    CK(cudaMemsetAsync(err.get(), 0, 2 * sizeof(int), s));
+    radius_thread_k<false><<<grid_for(n, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), x, n,
+                                                            prm, cnt.get(), nullptr, nullptr, nullptr, longrows.get(),
+                                                            err.get() + 1);
     CK_LAUNCH();
-    if (read1(err.get(), s)) fail(MGM_ERR_UNSUPPORTED, "elimination neighbour list exceeds 1024 entries");
+    int ecnt[2];
+    to_host(ecnt, err.get(), 2, s);
     rowptr.alloc(n + 1, s);
     exclusive_scan_i32(cnt.get(), rowptr.get(), n, s);
     int64_t nnz = csr_nnz(rowptr.get(), n, s);
     nbr.alloc(nnz > 0 ? nnz : 1, s);
     f.alloc(nnz > 0 ? nnz : 1, s);
-    radius_k<true><<<grid_for(n, RAD_WARPS), RAD_WARPS * 32, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
-                                                                    x, n, prm, nullptr, rowptr.get(), nbr.get(), f.get(), err.get());
+    radius_thread_k<true><<<grid_for(n, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), x, n, prm,
+                                                           nullptr, rowptr.get(), nbr.get(), f.get(), nullptr, nullptr);
     CK_LAUNCH();
+    if (ecnt[1] > 0) {  // the longer lists, one warp each
+        radius_k<true><<<grid_for(ecnt[1], RAD_WARPS), RAD_WARPS * 32, 0, s>>>(
+            G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), x, n, prm, nullptr, rowptr.get(), nbr.get(), f.get(),
+            err.get(), longrows.get(), (int64_t)ecnt[1]);
+        CK_LAUNCH();
+        if (read1(err.get(), s)) fail(MGM_ERR_UNSUPPORTED, "elimination neighbour list exceeds 1024 entries");
+    }
 }
 
 }  // namespace mgm
