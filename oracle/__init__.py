@@ -627,3 +627,58 @@ def eigs_smallest(L, nev):
     lam, V = np.linalg.eig(A)
     o = np.argsort(np.abs(lam), kind="stable")[:nev]
     return lam[o], V[:, o]
+
+
+# ----------------------------------------------------------------------------------------------
+# Reaction-diffusion pattern formation (Sec. 6.2)
+# ----------------------------------------------------------------------------------------------
+def reaction_terms(model, u, v, prm):
+    """Reaction terms (f, g) of u_t = Du Lap u + f, v_t = Dv Lap v + g.
+    "gm": Gierer-Meinhardt, eq. (turing): f = A - B u + u^2 / (v (1 + C u^2)), g = u^2 - v,
+    prm = (A, B, C). "schnakenberg": f = gamma (a - u + u^2 v), g = gamma (b - u^2 v),
+    prm = (gamma, a, b)."""
+    if model == "gm":
+        A, B, Cc = prm
+        return A - B * u + u * u / (v * (1.0 + Cc * u * u)), u * u - v
+    gamma, a, b = prm
+    return gamma * (a - u + u * u * v), gamma * (b - u * u * v)
+
+
+def reaction_diffusion(xyz, nrm, model, prm, Du, Dv, dt, steps, u0, v0, scheme="sbdf2", n=30, ell=3, k=1, n_min=250,
+                       tol=1e-8):
+    """Semi-implicit time stepping of Sec. 6.2: diffusion implicit, reactions explicit, each step
+    two screened-Poisson solves (MGM-FGMRES from the previous step's values). scheme "sbdf2"
+    (the paper's): (3 w^{n+1} - 4 w^n + w^{n-1}) / (2 dt) = D Lap w^{n+1} + 2 r^n - r^{n-1}, i.e.
+    (I - (2/3) dt D Lap) w^{n+1} = (4 w^n - w^{n-1}) / 3 + (2/3) dt (2 r^n - r^{n-1}), its first step
+    by IMEX Euler; scheme "euler": (I - dt D Lap) w^{n+1} = w^n + dt r^n. Returns (u, v, iterations
+    of every solve)."""
+    idx = knn(xyz, xyz, n, self_first=True)
+    w = phs_weights(xyz, nrm, idx, k, ell)
+    ops = {}
+
+    def op(mu):
+        if mu not in ops:
+            Lm = assemble(idx, w, mu)
+            ops[mu] = (Lm, setup(xyz, Lm, n_min))
+        return ops[mu]
+
+    u, v = np.array(u0, np.float64), np.array(v0, np.float64)
+    up = vp = None
+    its = []
+    for step in range(steps):
+        f, g = reaction_terms(model, u, v, prm)
+        if scheme == "euler" or step == 0:
+            ru, rv = u + dt * f, v + dt * g
+            cu, cv = dt * Du, dt * Dv
+        else:
+            fp, gp = reaction_terms(model, up, vp, prm)
+            ru = (4.0 * u - up) / 3.0 + (2.0 / 3.0) * dt * (2.0 * f - fp)
+            rv = (4.0 * v - vp) / 3.0 + (2.0 / 3.0) * dt * (2.0 * g - gp)
+            cu, cv = (2.0 / 3.0) * dt * Du, (2.0 / 3.0) * dt * Dv
+        Lu, Hu = op(cu)
+        Lv, Hv = op(cv)
+        un, itu, _ = fgmres(Lu, Hu, ru, x0=u, tol=tol)
+        vn, itv, _ = fgmres(Lv, Hv, rv, x0=v, tol=tol)
+        its.append((itu, itv))
+        up, vp, u, v = u, v, un, vn
+    return u, v, its
