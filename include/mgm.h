@@ -298,6 +298,20 @@ mgm_status mgm_eigs(mgm_hierarchy* H, int nev, int b, int s, int max_cycles, dou
                     uint64_t seed, double* lam_re, double* lam_im, double* resid, double* evec, int* nconv,
                     int* nsolves, mgm_stream stream);
 
+/* Right-hand sides of one semi-implicit reaction-diffusion step (Sec. 6.2), fused over the points:
+ * u_t = Du Lap u + f(u, v), v_t = Dv Lap v + g(u, v), diffusion implicit, reactions explicit.
+ * model MGM_RD_GIERER_MEINHARDT: f = A - B u + u^2 / (v (1 + C u^2)), g = u^2 - v (eq. (turing)),
+ * prm = {A, B, C}; MGM_RD_SCHNAKENBERG: f = gamma (a - u + u^2 v), g = gamma (b - u^2 v),
+ * prm = {gamma, a, b} (HOST array of 3). scheme MGM_RD_EULER: r_w = w^n + dt f_w(u^n, v^n), to be
+ * solved with L = I - dt D_w Lap; MGM_RD_SBDF2 (the paper's scheme): r_w = (4 w^n - w^{n-1}) / 3 +
+ * (2/3) dt (2 f_w^n - f_w^{n-1}), to be solved with L = I - (2/3) dt D_w Lap (u_prev, v_prev: the
+ * previous step; NULL allowed for Euler). All vectors DEVICE, N doubles, caller order. */
+mgm_status mgm_reaction_rhs(int model, int scheme, int64_t N, const double* u, const double* v, const double* u_prev,
+                            const double* v_prev, const double* prm, double dt, double* ru, double* rv,
+                            mgm_stream stream);
+enum { MGM_RD_GIERER_MEINHARDT = 0, MGM_RD_SCHNAKENBERG = 1 };
+enum { MGM_RD_EULER = 1, MGM_RD_SBDF2 = 2 };
+
 /* Sizes of the hierarchy (host struct). */
 mgm_status mgm_hierarchy_stats_get(const mgm_hierarchy* H, mgm_hierarchy_stats* out);
 

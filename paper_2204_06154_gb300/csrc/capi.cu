@@ -203,6 +203,12 @@ mgm_status mgm_eigs(mgm_hierarchy* H, int nev, int b, int s, int max_cycles, dou
     });
 }
 
+mgm_status mgm_reaction_rhs(int model, int scheme, int64_t N, const double* u, const double* v, const double* u_prev,
+                            const double* v_prev, const double* prm, double dt, double* ru, double* rv,
+                            mgm_stream stream) {
+    return guarded([&] { reaction_rhs(model, scheme, N, u, v, u_prev, v_prev, prm, dt, ru, rv, S(stream)); });
+}
+
 mgm_status mgm_hierarchy_stats_get(const mgm_hierarchy* H, mgm_hierarchy_stats* out) {
     return guarded([&] {
         REQUIRE(H && out, "null argument");

@@ -135,6 +135,9 @@ void learned_correct(mgm_hierarchy* H, cudaStream_t s);     // e_0 += correction
 void solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* U, const mgm_solve_params* sp, mgm_solve_info* info,
                  cudaStream_t s);
 void free_multi(mgm_hierarchy* H);
+// pattern.cu
+void reaction_rhs(int model, int scheme, int64_t n, const double* u, const double* v, const double* up, const double* vp,
+                  const double* prm, double dt, double* ru, double* rv, cudaStream_t s);
 // eigs.cu
 void eigs(mgm_hierarchy* H, int nev, int b, int s_steps, int max_cycles, double tol, const mgm_solve_params* sp,
           uint64_t seed, double* lam_re, double* lam_im, double* evec, double* resid, int* nconv, int* nsolves,

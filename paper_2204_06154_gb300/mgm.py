@@ -65,7 +65,7 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_mlp_size", "mgm_mlp_create", "mgm_mlp_destroy", "mgm_mlp_get", "mgm_mlp_set", "mgm_mlp_forward",
            "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
            "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
-           "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs"]
+           "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs", "mgm_reaction_rhs"]
 
 
 class ProfileInfo(C.Structure):
@@ -130,6 +130,7 @@ def lib():
         L.mgm_learned_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]
         L.mgm_eigs.argtypes = [P, I, I, I, I, C.c_double, C.POINTER(SolveParams), C.c_uint64, P, P, P, P,
                                C.POINTER(C.c_int), C.POINTER(C.c_int), P]
+        L.mgm_reaction_rhs.argtypes = [I, I, I64, P, P, P, P, C.POINTER(C.c_double), C.c_double, P, P, P]
         L.mgm_status_string.restype = C.c_char_p
         L.mgm_last_error_message.restype = C.c_char_p
         L.mgm_last_error_row.restype = C.c_int64
@@ -209,6 +210,21 @@ def stencil_weights(xyz, nrm, idx, method="rbf", k=1, ell=2, alpha=4.0, weights=
     w = torch.empty(idx.shape, dtype=torch.float64, device=xyz.device)
     _check(lib().mgm_stencil_weights(_p(xyz), _p(nrm), xyz.shape[0], _p(idx), C.byref(sp), _p(w), _stream()))
     return w
+
+
+_RD_MODEL = {"gm": 0, "schnakenberg": 1}
+_RD_SCHEME = {"euler": 1, "sbdf2": 2}
+
+
+def reaction_rhs(model, scheme, u, v, prm, dt, u_prev=None, v_prev=None, out=None):
+    """Right-hand sides of one semi-implicit reaction-diffusion step (see mgm_reaction_rhs)."""
+    u = _dev(u, torch.float64, "u"); v = _dev(v, torch.float64, "v")
+    ru, rv = out if out is not None else (torch.empty_like(u), torch.empty_like(v))
+    p3 = (C.c_double * 3)(*[float(t) for t in prm])
+    _check(lib().mgm_reaction_rhs(_RD_MODEL[model], _RD_SCHEME[scheme], u.numel(), _p(u), _p(v),
+                                  _p(u_prev) if u_prev is not None else None, _p(v_prev) if v_prev is not None else None,
+                                  p3, float(dt), _p(ru), _p(rv), _stream()))
+    return ru, rv
 
 
 def gradient_weights(xyz, nrm, idx, k=1, ell=2):
