@@ -58,8 +58,11 @@ def parse():
     ap.add_argument("--size", type=int, default=1048576, help="points per surface")
     ap.add_argument("--cpu-sample", type=int, default=32768, help="points of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: the N=1M sphere/torus time-to-solution line; c3: the full 64-surface batched line")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
+                    help="c2: the N=1M sphere/torus time-to-solution line; c3: the full 64-surface batched line; "
+                         "c5: Schnakenberg pattern formation on a 4M-point bumpy sphere (ms per time step)")
+    ap.add_argument("--c5-steps", type=int, default=100, help="time steps timed in the c5 line")
+    ap.add_argument("--c5-size", type=int, default=1 << 22, help="points of the c5 bumpy sphere")
     ap.add_argument("--batch-problems", type=int, default=16, help="surfaces in the batched measurement of the c2 line")
     ap.add_argument("--eigs", type=int, default=16, help="shift-invert eigenpairs computed on the 1M sphere (0: none)")
     ap.add_argument("--learned-surfaces", type=int, default=24,
@@ -412,6 +415,39 @@ def bench_eigs(torch, H, nev):
             "max_rel_dev_from_l(l+1)": round(max(abs(v - e) / max(e, 1) for v, e in zip(lap, exact)), 5)}
 
 
+def bench_pattern(N, steps, warmup):
+    """Schnakenberg reaction-diffusion (Sec. 6.2's scheme class; gamma = 1, a = 0.1, b = 0.9) on a
+    seeded bumpy sphere: IMEX Euler, dt = 0.01, D = (1, 10), FP32 cycles, FGMRES to 1e-8 from the
+    previous step. Setup (stencils, two hierarchies) and the timed steps are reported apart."""
+    import torch
+    from paper_2204_06154_gb300 import inputs as I
+    from paper_2204_06154_gb300.pattern import ReactionDiffusion
+    x, nrm = I.bumpy_sphere(N, seed=3)
+    X, NR = torch.from_numpy(x).cuda(), torch.from_numpy(nrm).cuda()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    rd = ReactionDiffusion(X, NR, "schnakenberg", (1.0, 0.1, 0.9), 1.0, 10.0, 0.01, scheme="euler", n=60, ell=3,
+                           n_min=250, precision="f32")
+    rd.hierarchy(0.01 * 1.0), rd.hierarchy(0.01 * 10.0)
+    e[1].record()
+    rng = np.random.default_rng(5)
+    us, vs = 1.0, 0.9
+    u0 = torch.from_numpy(us + 0.01 * rng.uniform(-1, 1, N)).cuda()
+    v0 = torch.from_numpy(vs + 0.01 * rng.uniform(-1, 1, N)).cuda()
+    u, v, _ = rd.run(u0, v0, warmup, tol=1e-8)
+    e[2].record()
+    u, v, its = rd.run(u, v, steps, tol=1e-8)
+    e[3].record()
+    e[3].synchronize()
+    ms = e[2].elapsed_time(e[3])
+    iu = [a for a, _ in its]
+    iv = [b for _, b in its]
+    return {"N": N, "setup_ms": round(e[0].elapsed_time(e[1]), 1), "steps": steps, "ms_per_step": round(ms / steps, 3),
+            "iters_u": {"max": max(iu), "mean": round(sum(iu) / len(iu), 2)},
+            "iters_v": {"max": max(iv), "mean": round(sum(iv) / len(iv), 2)},
+            "u_range": [round(float(u.min()), 4), round(float(u.max()), 4)]}
+
+
 def cpu_baseline(a, Ns=None):
     Ns = Ns or a.cpu_sample
     ms, it, rel = oracle_sample(Ns)
@@ -481,6 +517,17 @@ def main():
         r, H, u = run_problem(M, torch, *d)
         print(json.dumps({"single": True, "N": a.size, **{k: (round(v, 3) if isinstance(v, float) else v)
                                                          for k, v in r.items()}}), flush=True)
+        return
+    if a.workload == "c5":
+        import torch
+        torch.cuda.set_device(local_rank)
+        r = bench_pattern(a.c5_size, a.c5_steps, max(a.warmup, 3))
+        print(json.dumps({"metric": "pattern formation: ms per semi-implicit time step (two warm-started solves)",
+                          "value": r["ms_per_step"], "unit": "ms", "n_gpus": 1, "steps": a.c5_steps,
+                          "higher_is_better": False, "data": "synthetic",
+                          "config": {"workload": f"Schnakenberg IMEX Euler on a {a.c5_size:,}-point bumpy sphere, PHS r^3 "
+                                                 "+ degree 3, n = 60, dt = 0.01, D = (1, 10), tol 1e-8, warm start"},
+                          "pattern": r}), flush=True)
         return
     if a.workload == "c3":
         import torch
