@@ -451,3 +451,24 @@ def test_solve_batched_uneven_problems(M, oracle):
             uo, _, _ = oracle.fgmres(L_q, Ho, F[r], tol=1e-12)
             assert inf[r]["converged"]
             assert np.linalg.norm(H(U)[r] - uo) <= 1e-8 * np.linalg.norm(uo)
+
+
+def test_config1_exact_solution(M, oracle, ico5):
+    """The small workload as specified: icosahedral level-5 sphere (10,242 points), PHS r^3 +
+    degree 2, n = 30, -Lap u + u = 21 Y_4^3 (so u = Y_4^3), FP64 throughout, N_min = 125 (levels
+    10,242 / 2,560 / 640 / 160), MGM-FGMRES to 1e-10: the GPU solution is the oracle's to 1e-8 and
+    Y_4^3 to the discretisation error (2.5e-3 relative in the oracle)."""
+    x, nrm, idx, w, L = ico5
+    y = I.sh_real(x, 4, 3)
+    f = 21.0 * y
+    _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 30, "rbf", 1, 2, 1.0, keep_weights=False)
+    Hg = M.Hierarchy(T(x), rp, ci, v, n_min=125, precision="f64")
+    assert Hg.stats()["n"] == [10242, 2560, 640, 160]
+    u, info = Hg.solve(T(f), tol=1e-10)
+    assert info["converged"] and info["rel_res"] <= 1e-10
+    Ho = oracle.setup(x, L, 125, seed=0)
+    uo, ito, _ = oracle.fgmres(L, Ho, f, tol=1e-10)
+    u = H(u)
+    assert abs(info["iters"] - ito) <= 1
+    assert np.linalg.norm(u - uo) <= 1e-8 * np.linalg.norm(uo)
+    assert np.abs(u - y).max() <= 3e-3 * np.abs(y).max()
