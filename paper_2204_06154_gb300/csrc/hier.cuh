@@ -93,6 +93,7 @@ struct mgm_hierarchy {
     int krylov_m = 0;
     mgm::Buf<double> V, f, u, w, r, part, hbuf;
     mgm::Buf<float> Z32;
+    mgm::Buf<double> zd;        // FP64 copy of an FP32 z_k for the outer product (mixed mode)
     mgm::Buf<double> Z64;
     mgm::Buf<double> ydev;
     double* hhost = nullptr;    // pinned

@@ -24,14 +24,11 @@ constexpr int KG = 8;            // lanes per row in the FP64 operator
 constexpr int KBLOCK = 256;
 constexpr int DOT_BLOCKS = 304;  // 2 per SM on 152 SMs
 
-template <class TX>
-__device__ __forceinline__ double ldx(const TX* x, int32_t i) { return (double)x[i]; }
-
 // y = f - L x (RESID) or y = L x, L in solve order (split rows, diagonal apart)
-template <bool RESID, class TX>
+template <bool RESID>
 __global__ void __launch_bounds__(KBLOCK) spmv64_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ sc,
                                                    const double* __restrict__ sv, const double* __restrict__ diag,
-                                                   const TX* __restrict__ x, const double* __restrict__ f, double* y,
+                                                   const double* __restrict__ x, const double* __restrict__ f, double* y,
                                                    int64_t n) {
     const int64_t t = (int64_t)blockIdx.x * KBLOCK + threadIdx.x;
     const int64_t row = t / KG;
@@ -39,21 +36,48 @@ __global__ void __launch_bounds__(KBLOCK) spmv64_k(const int32_t* __restrict__ l
     double acc = 0.0;
     if (row < n) {
         const int32_t b = lo[row], e = lo[row + 1];
-        for (int32_t p = b + 4 * gl; p < e; p += 4 * KG) {
-            int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
-            double2 v0 = __ldg(reinterpret_cast<const double2*>(sv + p));
-            double2 v1 = __ldg(reinterpret_cast<const double2*>(sv + p + 2));
-            acc = fma(v0.x, ldx(x, c.x), acc);
-            acc = fma(v0.y, ldx(x, c.y), acc);
-            acc = fma(v1.x, ldx(x, c.z), acc);
-            acc = fma(v1.y, ldx(x, c.w), acc);
+        // two chunks of 4 entries per lane and pass, both loaded before either is used, so that a
+        // warp has all of its rows' matrix loads in flight at once (rows of up to 64 entries take
+        // one pass); the additions keep the order of a plain chunk-by-chunk loop
+#pragma unroll 1
+        for (int32_t p = b + 4 * gl; p < e; p += 8 * KG) {
+            const bool two = p + 4 * KG < e;
+            const int4 c0 = __ldcs(reinterpret_cast<const int4*>(sc + p));
+            const double2 v0 = __ldcs(reinterpret_cast<const double2*>(sv + p));
+            const double2 v1 = __ldcs(reinterpret_cast<const double2*>(sv + p + 2));
+            int4 c1 = make_int4(0, 0, 0, 0);
+            double2 v2 = make_double2(0.0, 0.0), v3 = v2;
+            if (two) {
+                c1 = __ldcs(reinterpret_cast<const int4*>(sc + p + 4 * KG));
+                v2 = __ldcs(reinterpret_cast<const double2*>(sv + p + 4 * KG));
+                v3 = __ldcs(reinterpret_cast<const double2*>(sv + p + 4 * KG + 2));
+            }
+            const double x0 = x[c0.x], x1 = x[c0.y], x2 = x[c0.z], x3 = x[c0.w];
+            double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+            if (two) { y0 = x[c1.x]; y1 = x[c1.y]; y2 = x[c1.z]; y3 = x[c1.w]; }
+            acc = fma(v0.x, x0, acc);
+            acc = fma(v0.y, x1, acc);
+            acc = fma(v1.x, x2, acc);
+            acc = fma(v1.y, x3, acc);
+            if (two) {
+                acc = fma(v2.x, y0, acc);
+                acc = fma(v2.y, y1, acc);
+                acc = fma(v3.x, y2, acc);
+                acc = fma(v3.y, y3, acc);
+            }
         }
     }
     for (int o = KG / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (row < n && gl == 0) {
-        double lx = fma(diag[row], ldx(x, (int32_t)row), acc);
+        double lx = fma(diag[row], x[row], acc);
         y[row] = RESID ? f[row] - lx : lx;
     }
+}
+
+// xd = (double) x
+__global__ void widen_k(const float* __restrict__ x, double* __restrict__ xd, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) xd[i] = (double)x[i];
 }
 
 // partial[b * k1 + t] = sum over block b's chunk of V_t . w
@@ -181,11 +205,22 @@ struct Ops {
     int64_t nv;  // length of the outer vectors: n, or n + 1 (bordered: [u; lambda])
     Level& L0() { return H->lv[0]; }
 
+    // An FP32 x is widened once into an FP64 copy first: the product then converts n values
+    // instead of one per stored entry (each conversion is an FP64-pipe instruction, and the FP64
+    // pipe, not HBM, would otherwise bound the product). The result is the same bit for bit.
     template <bool RESID, class TX>
     void spmv(const TX* x, const double* f, double* y) {
         Level& L = L0();
-        spmv64_k<RESID, TX><<<grid_for(n * KG, KBLOCK), KBLOCK, 0, s>>>(L.lo.get(), L.sc.get(), L.sv64.get(), L.diag64.get(),
-                                                                       x, f, y, n);
+        const double* xd;
+        if constexpr (std::is_same<TX, float>::value) {
+            widen_k<<<grid_for(n, 256), 256, 0, s>>>(x, H->zd.get(), n);
+            CK_LAUNCH();
+            xd = H->zd.get();
+        } else {
+            xd = x;
+        }
+        spmv64_k<RESID><<<grid_for(n * KG, KBLOCK), KBLOCK, 0, s>>>(L.lo.get(), L.sc.get(), L.sv64.get(), L.diag64.get(),
+                                                                   xd, f, y, n);
         CK_LAUNCH();
     }
     // y = f - L~ x (RESID) or y = L~ x, with the border of Sec. 4.4 when the hierarchy has one
@@ -312,8 +347,12 @@ static void ensure_workspace(mgm_hierarchy* H, int m) {
     const int64_t n = H->N + (H->bordered ? 1 : 0);
     if (H->krylov_m >= m && H->V.get()) return;
     H->V.alloc((int64_t)(m + 1) * n);
-    if (H->precision == MGM_F32) H->Z32.alloc((int64_t)m * n);
-    else H->Z64.alloc((int64_t)m * n);
+    if (H->precision == MGM_F32) {
+        H->Z32.alloc((int64_t)m * n);
+        H->zd.alloc(n);
+    } else {
+        H->Z64.alloc((int64_t)m * n);
+    }
     H->f.alloc(n); H->u.alloc(n); H->w.alloc(n); H->r.alloc(n);
     H->part.alloc((int64_t)DOT_BLOCKS * (2 * (m + 1) + 2));
     H->hbuf.alloc(2 * (m + 2) + 2);

@@ -9,6 +9,7 @@
 // solution; a zero right-hand side (padding up to R) is converged from the start.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "hier.cuh"
@@ -259,6 +260,7 @@ struct MultiWork {
     Buf<double> V, f, u, w, part, hbuf, inv, y;
     Buf<float> Z32;
     Buf<double> Z64;
+    Buf<double> zd;  // FP64 copy of an FP32 z_k for the outer product
 };
 
 static MultiWork& multi_work(mgm_hierarchy* H, int R, int m) {
@@ -284,8 +286,12 @@ static MultiWork& multi_work(mgm_hierarchy* H, int R, int m) {
     }
     const int64_t nR = H->N * R;
     W.V.alloc((int64_t)(m + 1) * nR);
-    if (f32) W.Z32.alloc((int64_t)m * nR);
-    else W.Z64.alloc((int64_t)m * nR);
+    if (f32) {
+        W.Z32.alloc((int64_t)m * nR);
+        W.zd.alloc(nR);
+    } else {
+        W.Z64.alloc((int64_t)m * nR);
+    }
     W.f.alloc(nR); W.u.alloc(nR); W.w.alloc(nR);
     W.part.alloc((int64_t)RDOT_BLOCKS * (m + 2) * R);
     W.hbuf.alloc((int64_t)(2 * (m + 2) + 2) * R);
@@ -462,7 +468,14 @@ static void solve_multi_t(mgm_hierarchy* H, int nrhs, const double* F, double* U
             double* vk = W.V.get() + (int64_t)k * nR;
             T* zk = Z + (int64_t)k * nR;
             precond(vk, zk);
-            spmv((const T*)zk, nullptr, W.w.get(), false);
+            if constexpr (std::is_same<T, float>::value) {
+                // widened once, so that the product converts nR values instead of one per entry
+                castR_k<float, double><<<grid_for(nR, 256), 256, 0, s>>>(zk, W.zd.get(), nR);
+                CK_LAUNCH();
+                spmv((const double*)W.zd.get(), nullptr, W.w.get(), false);
+            } else {
+                spmv((const T*)zk, nullptr, W.w.get(), false);
+            }
             const int k1 = k + 1;
             double* h1 = W.hbuf.get();
             double* h2 = h1 + (size_t)(m + 1) * R;
