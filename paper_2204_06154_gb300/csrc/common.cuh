@@ -30,7 +30,8 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 #define CK(call) ::mgm::check_cuda((call), #call, __FILE__, __LINE__)
 // every kernel launch site is followed by exactly one CK_LAUNCH, which also counts the launch
 void note_launch(int64_t n = 1);
-int64_t launches();
+int64_t launches();         // all threads of the process
+int64_t thread_launches();  // launches made by the calling thread (graph capture counts)
 #define CK_LAUNCH() (::mgm::note_launch(), ::mgm::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
 #define REQUIRE(cond, msg)                                              \
     do {                                                                \

@@ -211,7 +211,7 @@ struct GraphBatch {
         cudaStream_t cs = nullptr;
         CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
-        const int64_t before = launches();
+        const int64_t before = thread_launches();
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             try {
@@ -224,7 +224,7 @@ struct GraphBatch {
             }
             e = cudaStreamEndCapture(cs, &g);
         }
-        kernels = launches() - before;
+        kernels = thread_launches() - before;
         note_launch(-kernels);
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
         if (g) cudaGraphDestroy(g);
@@ -356,6 +356,146 @@ __global__ void jp_assign_k(const int32_t* rp, const int32_t* adj, int32_t* col,
     }
 }
 
+// ---- greedy colouring in one launch --------------------------------------------------------
+// A JP round gives a selected vertex the smallest colour absent from its coloured neighbours, and
+// those are exactly its neighbours of higher (priority, index): it is selected only once all of
+// them are coloured, and none of its lower neighbours can be coloured before it. The colouring is
+// therefore the evaluation of "smallest colour absent from the higher neighbours" in decreasing
+// priority, and every schedule that respects that order gives the same colours. Vertices are
+// sorted by decreasing (priority, index); blocks take consecutive slices of that order in the
+// order they start (a ticket counter), so a vertex waits only for vertices of blocks that have
+// started or of its own block, and every wait ends. Each wait is bounded all the same: past the
+// limit the kernel records MGM_ERR_TIMEOUT, the other threads stop waiting, and the host colours
+// by JP rounds instead.
+__device__ __forceinline__ bool prio_gt(unsigned long long pu, int32_t u, unsigned long long pv, int32_t v) {
+    return pu > pv || (pu == pv && u > v);
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int32_t* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_i32(int32_t* p, int v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// bucket of a vertex: the top B bits of its priority, reversed so that ascending buckets hold
+// decreasing priorities
+__device__ __forceinline__ int prio_bucket(unsigned long long pv, int B) {
+    return (int)(((1ull << B) - 1ull) - (pv >> (64 - B)));
+}
+__global__ void prio_count_k(int64_t N, unsigned long long seed, int B, int32_t* cnt) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < N) atomicAdd(&cnt[prio_bucket(splitmix64(seed, (unsigned long long)v), B)], 1);
+}
+__global__ void prio_fill_k(int64_t N, unsigned long long seed, int B, const int32_t* start, int32_t* fill,
+                            int32_t* ord) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    const int b = prio_bucket(splitmix64(seed, (unsigned long long)v), B);
+    ord[start[b] + atomicAdd(&fill[b], 1)] = (int32_t)v;
+}
+// each bucket in decreasing (priority, index): insertion sort, one thread per bucket
+__global__ void prio_sort_k(int64_t nb, unsigned long long seed, const int32_t* start, int32_t* ord) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int32_t* o = ord + start[b];
+    const int n = start[b + 1] - start[b];
+    for (int i = 1; i < n; ++i) {
+        const int32_t x = o[i];
+        const unsigned long long px = splitmix64(seed, (unsigned long long)x);
+        int j = i;
+        while (j > 0 && prio_gt(px, x, splitmix64(seed, (unsigned long long)o[j - 1]), o[j - 1])) {
+            o[j] = o[j - 1];
+            --j;
+        }
+        o[j] = x;
+    }
+}
+
+__global__ void __launch_bounds__(256) jp_ordered_k(const int32_t* rp, const int32_t* adj, const int32_t* ord, int64_t N,
+                                                    unsigned long long seed, unsigned* ticket, int32_t* col, int* err,
+                                                    unsigned long long limit) {
+    __shared__ unsigned slice;
+    if (threadIdx.x == 0) slice = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t t = (int64_t)slice * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const int32_t v = ord[t];
+    const unsigned long long pv = splitmix64(seed, (unsigned long long)v);
+    const int32_t b = rp[v], e = rp[v + 1];
+    unsigned long long used = 0;
+    bool more = false;  // a higher neighbour has a colour >= 64
+    for (int32_t p = b; p < e; p += JP_BATCH) {
+        int32_t u[JP_BATCH];
+        int c[JP_BATCH];
+#pragma unroll
+        for (int q = 0; q < JP_BATCH; ++q) u[q] = p + q < e ? adj[p + q] : -1;
+#pragma unroll
+        for (int q = 0; q < JP_BATCH; ++q)
+            if (u[q] >= 0 && !prio_gt(splitmix64(seed, (unsigned long long)u[q]), u[q], pv, v)) u[q] = -1;
+#pragma unroll
+        for (int q = 0; q < JP_BATCH; ++q) c[q] = u[q] >= 0 ? ld_relaxed_i32(col + u[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < JP_BATCH; ++q) {
+            if (u[q] < 0) continue;
+            for (unsigned long long it = 0; c[q] < 0; ++it) {
+                if (*(volatile int*)err) return;
+                if (it >= limit) {
+                    atomicOr(err, MGM_ERR_TIMEOUT);
+                    return;
+                }
+                __nanosleep(64);
+                c[q] = ld_relaxed_i32(col + u[q]);
+            }
+            if (c[q] < 64) used |= 1ull << c[q];
+            else more = true;
+        }
+    }
+    int colour = ~used ? __ffsll((long long)~used) - 1 : -1;
+    // all 64 lowest colours taken: the next windows (every higher neighbour is coloured by now)
+    for (int base = 64; colour < 0 && more; base += 64) {
+        unsigned long long w = 0;
+        for (int32_t p = b; p < e; ++p) {
+            const int32_t u = adj[p];
+            if (!prio_gt(splitmix64(seed, (unsigned long long)u), u, pv, v)) continue;
+            const int c = ld_relaxed_i32(col + u);
+            if (c >= base && c < base + 64) w |= 1ull << (c - base);
+        }
+        if (~w) colour = base + __ffsll((long long)~w) - 1;
+    }
+    if (colour < 0) colour = 64;  // (only when no higher neighbour has a colour >= 64)
+    st_relaxed_i32(col + v, colour);
+}
+
+// Greedy colouring along the priority order in one launch; false when a wait ran out (the
+// colours are then incomplete and the caller colours by rounds).
+static bool color_ordered(int64_t N, const int32_t* rp, const int32_t* adj, uint64_t seed, int32_t* colour,
+                          cudaStream_t s) {
+    int B = 1;
+    while (B < 24 && ((int64_t)1 << B) < N) ++B;
+    const int64_t nb = (int64_t)1 << B;
+    Temp<int32_t> cnt(nb, s), start(nb + 1, s), fill(nb, s), ord(N, s);
+    Temp<unsigned> ticket(1, s);
+    Temp<int> err(1, s);
+    CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * nb, s));
+    CK(cudaMemsetAsync(fill.get(), 0, sizeof(int32_t) * nb, s));
+    CK(cudaMemsetAsync(ticket.get(), 0, sizeof(unsigned), s));
+    CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    prio_count_k<<<grid_for(N, 256), 256, 0, s>>>(N, seed, B, cnt.get());
+    CK_LAUNCH();
+    exclusive_scan_i32(cnt.get(), start.get(), nb, s);
+    prio_fill_k<<<grid_for(N, 256), 256, 0, s>>>(N, seed, B, start.get(), fill.get(), ord.get());
+    CK_LAUNCH();
+    prio_sort_k<<<grid_for(nb, 256), 256, 0, s>>>(nb, seed, start.get(), ord.get());
+    CK_LAUNCH();
+    fill_i32(colour, -1, N, s);
+    jp_ordered_k<<<grid_for(N, 256), 256, 0, s>>>(rp, adj, ord.get(), N, seed, ticket.get(), colour, err.get(),
+                                                  1ull << 22);
+    CK_LAUNCH();
+    return read1(err.get(), s) == 0;
+}
+
 __global__ void max_i32_k(const int32_t* a, int64_t n, int* out) {
     int m = -1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -370,11 +510,12 @@ void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32
     REQUIRE(rp && ci && colour, "null array");
     Temp<int32_t> srp, sci;
     sym_pattern(N, rp, ci, srp, sci, s);
-    Temp<char> sel(N, s);
     Temp<int> ctr(2, s);  // [0] uncoloured vertices remain, [1] max colour
-    fill_i32(colour, -1, N, s);
+    const bool ordered = color_ordered(N, srp.get(), sci.get(), seed, colour, s);
+    Temp<char> sel(ordered ? 1 : N, s);
+    if (!ordered) fill_i32(colour, -1, N, s);
     const unsigned wgrid = grid_for(N, 256);
-    for (int64_t round = 0;; ++round) {
+    for (int64_t round = 0; !ordered; ++round) {
         if (round > N) fail(MGM_ERR_UNSUPPORTED, "colouring did not terminate");
         CK(cudaMemsetAsync(ctr.get(), 0, sizeof(int), s));
         jp_select_k<<<wgrid, 256, 0, s>>>(srp.get(), sci.get(), colour, N, seed, sel.get(), ctr.get());

@@ -12,8 +12,13 @@ namespace mgm {
 // error state
 // ---------------------------------------------------------------------------------------------
 static std::atomic<int64_t> g_launches{0};
-void note_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local int64_t t_launches = 0;
+void note_launch(int64_t n) {
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+    t_launches += n;
+}
 int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+int64_t thread_launches() { return t_launches; }
 static thread_local std::string g_msg;
 static thread_local int64_t g_row = -1;
 void set_error(const std::string& msg) { g_msg = msg; }

@@ -696,7 +696,7 @@ void alloc_work(mgm_hierarchy* H) {
 
 static cudaGraphExec_t capture(mgm_hierarchy* H, bool learned, int64_t* kernels) {
     cudaGraph_t g = nullptr;
-    const int64_t before = launches();
+    const int64_t before = thread_launches();
     CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
     try {
         if (H->precision == MGM_F32) {
@@ -715,7 +715,7 @@ static cudaGraphExec_t capture(mgm_hierarchy* H, bool learned, int64_t* kernels)
         throw;
     }
     CK(cudaStreamEndCapture(H->cap_stream, &g));
-    *kernels = launches() - before;  // captured, not executed: counted per graph launch
+    *kernels = thread_launches() - before;  // captured, not executed: counted per graph launch
     note_launch(-*kernels);
     cudaGraphExec_t ex = nullptr;
     cudaError_t e = cudaGraphInstantiate(&ex, g, 0);

@@ -98,6 +98,11 @@ def test_hierarchy_properties(M, oracle, big, hier):
     row = np.repeat(np.arange(N), np.diff(rp))
     off = ci != row
     assert np.all(col[row[off]] != col[ci[off]])
+    # and it is the oracle's greedy colouring of the RCM-ordered operator, bit for bit
+    import scipy.sparse as sp
+    A0 = sp.csr_matrix((np.ones(ci.size), ci, rp), shape=(N, N))
+    ref, nc = oracle.color(A0, 0)
+    assert np.array_equal(col, ref) and st["ncolors"][0] == nc
     # WSE (Sec. 4.1): N/4 distinct survivors, separated at least as well as the fine nodes
     keep = H(l1["keep"])
     assert keep.size == N // 4 and np.unique(keep).size == keep.size and keep.min() >= 0 and keep.max() < N

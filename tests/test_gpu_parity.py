@@ -206,6 +206,28 @@ def test_color_bitexact(M, oracle, ico5, seed):
     assert gnc == nc and np.array_equal(H(got), ref)
 
 
+def test_color_many_colours_and_ragged(M, oracle):
+    """Greedy colouring where windows above 64 colours are needed (cliques of 70 and 130
+    vertices), with isolated vertices, a non-symmetric pattern and a size that is no multiple of
+    the block size."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(5)
+    N = 3001
+    rows, cols = [], []
+    for c0, k in ((0, 70), (500, 130)):
+        a = np.arange(c0, c0 + k)
+        rows.append(np.repeat(a, k)); cols.append(np.tile(a, k))
+    r = rng.integers(0, N - 40, 20000); c = rng.integers(0, N - 40, 20000)   # last 40: isolated
+    rows.append(r); cols.append(c)
+    A = sp.csr_matrix((np.ones(sum(len(q) for q in rows)), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
+    A.sum_duplicates(); A.sort_indices()
+    for seed in (0, 7):
+        ref, nc = oracle.color(A, seed)
+        assert nc >= 130
+        got, gnc = M.color(T(A.indptr.astype(np.int32)), T(A.indices.astype(np.int32)), seed)
+        assert gnc == nc and np.array_equal(H(got), ref)
+
+
 # ---------------------------------------------------------------------------------- transfers
 def test_interp_transpose_galerkin(M, oracle, ico5):
     x, nrm, idx, w, L = ico5
