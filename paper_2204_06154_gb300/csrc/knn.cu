@@ -111,6 +111,9 @@ __global__ void __launch_bounds__(GRID_PARAMS_THREADS) grid_params_k(const doubl
         if (cnt <= (double)cells) break;
         h = it < 200 ? h * 1.0001 : emax * 2.0 + 1.0;  // the last: one cell
     }
+    double amax = 0.0;
+    for (int c = 0; c < 3; ++c) amax = fmax(amax, fmax(fabs(mn[c]), fabs(mx[c])));
+    g->amax = (amax < 1e300) ? amax : INFINITY;
     g->x0 = mn[0]; g->y0 = mn[1]; g->z0 = mn[2]; g->h = h;
     g->nx = n3[0]; g->ny = n3[1]; g->nz = n3[2];
     g->ncells = (int64_t)g->nx * g->ny * g->nz;
@@ -133,21 +136,24 @@ __global__ void cell_count_k(const double* x, int64_t n, const Grid* gp, int32_t
     atomicAdd(&cnt[c], 1);
 }
 __global__ void cell_place_k(const double* x, int64_t n, const int32_t* cell_of, const int32_t* start, int32_t* fill,
-                             int32_t* sidx, double* sxyz) {
+                             int32_t* sidx, double* sxyz, float4* s32) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t c = cell_of[i];
     int32_t q = start[c] + atomicAdd(&fill[c], 1);
     sidx[q] = (int32_t)i;
-    sxyz[3 * (int64_t)q] = x[3 * i];
-    sxyz[3 * (int64_t)q + 1] = x[3 * i + 1];
-    sxyz[3 * (int64_t)q + 2] = x[3 * i + 2];
+    const double a = x[3 * i], b = x[3 * i + 1], d = x[3 * i + 2];
+    sxyz[3 * (int64_t)q] = a;
+    sxyz[3 * (int64_t)q + 1] = b;
+    sxyz[3 * (int64_t)q + 2] = d;
+    if (s32) s32[q] = make_float4((float)a, (float)b, (float)d, 0.0f);
 }
 
 struct DevGrid {
     Temp<Grid> g;
     Temp<int32_t> start, sidx;
     Temp<double> sxyz;
+    Temp<float4> s32;  // the sorted coordinates rounded to FP32, for culling
     int64_t cells;
 };
 
@@ -171,8 +177,9 @@ static void build_grid(const double* x, int64_t n, int64_t cells, double h_min, 
     CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (cells + 1), s));
     G.sidx.alloc(n, s);
     G.sxyz.alloc(3 * n, s);
+    G.s32.alloc(n, s);
     cell_place_k<<<grid_for(n, 256), 256, 0, s>>>(x, n, cell_of.get(), G.start.get(), cnt.get(), G.sidx.get(),
-                                                    G.sxyz.get());
+                                                    G.sxyz.get(), G.s32.get());
     CK_LAUNCH();
 }
 
@@ -374,12 +381,15 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) knn_k(const Grid* gp, const in
 // same result.
 template <int K>
 __global__ void __launch_bounds__(128) knn_small_k(const Grid* gp, const int32_t* start, const int32_t* sidx,
-                                                   const double* sxyz, const double* q, int64_t nq, int self_first,
-                                                   int32_t* idx_out, double* d2_out, int* err) {
+                                                   const double* sxyz, const float4* s32, const double* q, int64_t nq,
+                                                   int self_first, int32_t* idx_out, double* d2_out, int* err) {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= nq) return;
     const Grid g = *gp;
     const double px = q[3 * qi], py = q[3 * qi + 1], pz = q[3 * qi + 2];
+    const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+    const double A = g.amax + fmax(fabs(px), fmax(fabs(py), fabs(pz)));
+    float far = INFINITY;  // candidates beyond it are farther than the current K-th
     const int cx = cell_coord(px, g.x0, g.h, g.nx), cy = cell_coord(py, g.y0, g.h, g.ny), cz = cell_coord(pz, g.z0, g.h, g.nz);
     const int rfull = max(max(max(cx, g.nx - 1 - cx), max(cy, g.ny - 1 - cy)), max(cz, g.nz - 1 - cz));
     ukey bk[K];
@@ -401,12 +411,13 @@ __global__ void __launch_bounds__(128) knn_small_k(const Grid* gp, const int32_t
                         const int64_t c = ((int64_t)z * g.ny + y) * g.nx + x;
                         const int b = start[c], e = start[c + 1];
                         for (int t = b; t < e; ++t) {
+                            ++found;
+                            if (d2_f32(pxf, pyf, pzf, s32[t]) > far) continue;  // cannot enter the K best
                             const int j = sidx[t];
                             const ukey d = (self_first && j == (int)qi)
                                                ? 0ull
                                                : d2_key(d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1],
                                                                sxyz[3 * (int64_t)t + 2]));
-                            ++found;
                             if (key_lt(d, j, bk[K - 1], bj[K - 1])) {
                                 bk[K - 1] = d;
                                 bj[K - 1] = j;
@@ -416,6 +427,8 @@ __global__ void __launch_bounds__(128) knn_small_k(const Grid* gp, const int32_t
                                         const ukey tk = bk[u]; bk[u] = bk[u - 1]; bk[u - 1] = tk;
                                         const int tj = bj[u]; bj[u] = bj[u - 1]; bj[u - 1] = tj;
                                     }
+                                if (bk[K - 1] != ~0ull)
+                                    far = far_sq_f32(bk[K - 1] ? sqrt(__longlong_as_double((long long)(bk[K - 1] - 1ull))) : 0.0, A);
                             }
                         }
                     }
@@ -485,14 +498,15 @@ void knn_device(const double* data, int64_t nd, const double* query, int64_t nq,
                 G.start = std::move(G2.start);
                 G.sidx = std::move(G2.sidx);
                 G.sxyz = std::move(G2.sxyz);
+                G.s32 = std::move(G2.s32);
                 G.cells = G2.cells;
             }
         }
     }
     if (k <= 4) {
         auto kern = k == 1 ? knn_small_k<1> : k == 2 ? knn_small_k<2> : k == 3 ? knn_small_k<3> : knn_small_k<4>;
-        kern<<<grid_for(nq, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), query, nq, self_first,
-                                               idx_out, d2_out, err.get());
+        kern<<<grid_for(nq, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), G.s32.get(), query,
+                                               nq, self_first, idx_out, d2_out, err.get());
         CK_LAUNCH();
     } else {
         const size_t smem = (sizeof(ukey) + sizeof(int)) * KNN_WARPS * KNN_CAP;
@@ -592,15 +606,19 @@ __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const
 constexpr int RT_CAP = 48;
 template <bool FILL>
 __global__ void __launch_bounds__(128) radius_thread_k(const Grid* gp, const int32_t* start, const int32_t* sidx,
-                                                       const double* sxyz, const double* x, int64_t n, const double* prm,
-                                                       int32_t* cnt, const int32_t* rowptr, int32_t* nbr, double* f,
-                                                       int32_t* longrows, int* nlong) {
+                                                       const double* sxyz, const float4* s32, const double* x, int64_t n,
+                                                       const double* prm, int32_t* cnt, const int32_t* rowptr,
+                                                       int32_t* nbr, double* f, int32_t* longrows, int* nlong) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const Grid g = *gp;
     const double two_rmax = prm[0], rmin = prm[1];
     const double lim_sq = two_rmax * two_rmax * (1.0 + 1e-9);
+    // below in_sq the square root is certainly below 2 r_max (the count pass needs no root there)
+    const double in_sq = two_rmax * two_rmax * (1.0 - 1e-9);
     const double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
+    const float far = far_sq_f32(two_rmax, g.amax + fmax(fabs(px), fmax(fabs(py), fabs(pz))));
     const int cx = cell_coord(px, g.x0, g.h, g.nx), cy = cell_coord(py, g.y0, g.h, g.ny), cz = cell_coord(pz, g.z0, g.h, g.nz);
     const int R = (g.h >= two_rmax * (1.0 + 1e-6)) ? 1 : (int)ceil(two_rmax / g.h) + 1;
     int count = 0;
@@ -612,13 +630,17 @@ __global__ void __launch_bounds__(128) radius_thread_k(const Grid* gp, const int
                 const int64_t c = ((int64_t)z * g.ny + y) * g.nx + xx;
                 const int b = start[c], e = start[c + 1];
                 for (int t = b; t < e; ++t) {
+                    if (d2_f32(pxf, pyf, pzf, s32[t]) > far) continue;  // certainly beyond 2 r_max
                     const int j = sidx[t];
                     if (j == (int)i) continue;
                     const double dd = d2_pts(px, py, pz, sxyz[3 * (int64_t)t], sxyz[3 * (int64_t)t + 1],
                                              sxyz[3 * (int64_t)t + 2]);
                     if (!(dd <= lim_sq)) continue;
-                    const double d = sqrt(dd);
-                    if (!(d < two_rmax)) continue;
+                    double d = 0.0;
+                    if (FILL || !(dd < in_sq)) {
+                        d = sqrt(dd);
+                        if (!(d < two_rmax)) continue;
+                    }
                     if (FILL && count < RT_CAP) {  // insert by index
                         int q = count;
                         while (q > 0 && jl[q - 1] > j) { jl[q] = jl[q - 1]; dl[q] = dl[q - 1]; --q; }
@@ -653,9 +675,9 @@ void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, 
     Temp<int32_t> cnt(n + 1, s), longrows(n, s);
     Temp<int> err(2, s);  // [0] warp-kernel overflow, [1] rows above RT_CAP
     CK(cudaMemsetAsync(err.get(), 0, 2 * sizeof(int), s));
-    radius_thread_k<false><<<grid_for(n, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), x, n,
-                                                            prm, cnt.get(), nullptr, nullptr, nullptr, longrows.get(),
-                                                            err.get() + 1);
+    radius_thread_k<false><<<grid_for(n, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
+                                                            G.s32.get(), x, n, prm, cnt.get(), nullptr, nullptr, nullptr,
+                                                            longrows.get(), err.get() + 1);
     CK_LAUNCH();
     int ecnt[2];
     to_host(ecnt, err.get(), 2, s);
@@ -664,8 +686,9 @@ void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, 
     int64_t nnz = csr_nnz(rowptr.get(), n, s);
     nbr.alloc(nnz > 0 ? nnz : 1, s);
     f.alloc(nnz > 0 ? nnz : 1, s);
-    radius_thread_k<true><<<grid_for(n, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(), x, n, prm,
-                                                           nullptr, rowptr.get(), nbr.get(), f.get(), nullptr, nullptr);
+    radius_thread_k<true><<<grid_for(n, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
+                                                           G.s32.get(), x, n, prm, nullptr, rowptr.get(), nbr.get(), f.get(),
+                                                           nullptr, nullptr);
     CK_LAUNCH();
     if (ecnt[1] > 0) {  // the longer lists, one warp each
         radius_k<true><<<grid_for(ecnt[1], RAD_WARPS), RAD_WARPS * 32, 0, s>>>(

@@ -97,7 +97,7 @@ void knn_noalloc(const double* data, int64_t nd, const double* query, int64_t nq
     scan_one_block_k<<<1, 1024, 0, s>>>(cnt, start, cells);
     CK_LAUNCH();
     CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (cells + 1), s));
-    cell_place_k<<<grid_for(nd, 256), 256, 0, s>>>(data, nd, cell_of, start, cnt, sidx, sxyz);
+    cell_place_k<<<grid_for(nd, 256), 256, 0, s>>>(data, nd, cell_of, start, cnt, sidx, sxyz, nullptr);
     CK_LAUNCH();
     const size_t smem = (sizeof(double) + sizeof(int)) * KNN_WARPS * KNN_CAP;
     CK(cudaFuncSetAttribute(knn_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

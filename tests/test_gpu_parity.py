@@ -58,6 +58,38 @@ def test_knn_bitexact(M, oracle, case):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("case", ["lattice", "offset", "tiny"])
+@pytest.mark.parametrize("k", [2, 3, 50])
+def test_knn_fp32_culling_edges(M, oracle, case, k):
+    """The FP32 culling of distance tests changes no result: exact ties (a lattice: many equal
+    distances, ties by index), coordinates far from the origin relative to the spacing (the
+    culling bound grows with |x|), and a cloud scaled to 1e-20."""
+    if case == "lattice":
+        g = np.arange(18, dtype=np.float64)
+        x = np.stack(np.meshgrid(g, g, g[:6], indexing="ij"), -1).reshape(-1, 3) * 0.25
+    else:
+        x, _ = I.fibonacci_sphere(6007, 0.2, 11)
+        x = x + 1000.0 if case == "offset" else x * 1e-20
+    ref = oracle.knn(x, x, k, self_first=True)
+    got = H(M.knn(T(x), None, k, self_first=True))
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("case", ["offset", "lattice"])
+def test_coarsen_fp32_culling_edges(M, oracle, case):
+    if case == "offset":
+        x, _ = I.fibonacci_sphere(8009, 0.3, 12)
+        x = x + np.array([300.0, -200.0, 50.0])
+    else:
+        g = np.arange(40, dtype=np.float64)
+        x = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2) * 0.1
+        x = np.concatenate([x, np.zeros((x.shape[0], 1))], 1)
+    NH = x.shape[0] // 4
+    ref, _ = oracle.wse(x, NH, mode=1)
+    got = H(M.coarsen(T(x), NH))
+    assert np.array_equal(got, ref)
+
+
 # ------------------------------------------------------------------------------ weights, assembly
 @pytest.mark.parametrize("case", ["c1", "c2like", "k3ell3"])
 def test_phs_weights(M, oracle, case):
