@@ -33,8 +33,9 @@ __global__ void cell_place_k(const double* x, int64_t n, const int32_t* cell_of,
 // coordinate (a NaN distance compares false).
 __device__ __forceinline__ float far_sq_f32(double D, double A) {
     const double u = 0x1p-22;
-    const double r = (1.0 + 2.0 * u) * D + 16.0 * u * A + 1e-36;  // (the last: FP32 subnormal rounding)
-    return __double2float_ru(r * r * (1.0 + 8.0 * u));
+    const double r = (1.0 + 2.0 * u) * D + 16.0 * u * A + 1e-36;  // (the last: subnormal coordinates)
+    // 2^-140: the absolute error of squares and sums that fall into FP32's subnormal range
+    return __double2float_ru(r * r * (1.0 + 8.0 * u) + 0x1p-140);
 }
 __device__ __forceinline__ float d2_f32(float px, float py, float pz, float4 q) {
     const float dx = px - q.x, dy = py - q.y, dz = pz - q.z;
