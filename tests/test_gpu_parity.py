@@ -192,8 +192,9 @@ def test_invalid_arguments(M):
 
 
 # ------------------------------------------------------------------------------------- coarsening
-@pytest.mark.parametrize("case", ["ico5", "fib14561", "fib14634", "torus"])
+@pytest.mark.parametrize("case", ["ico5", "fib14561", "fib14634", "torus", "fib40009"])
 def test_coarsen_bitexact(M, oracle, case):
+    """Bit-exact kept sets, from 9,000 to 40,009 points (ragged sizes, sphere and torus)."""
     if case == "ico5":
         x, _ = I.icosahedral_sphere(5)
     elif case == "torus":
