@@ -5,11 +5,14 @@
 // with partial pivoting (one thread per row; same operation sequence as a sequential solve).
 //
 // SpGEMM C = A B (used as T = L P, then L_H = R T, eq. (galerkin)): one warp per row of C. The
-// pattern is the union of the B rows selected by the A row, collected in a per-warp open-addressing
-// hash set in shared memory, compacted and sorted by rank. Each lane then owns a few output
-// columns j and accumulates sum_p a_ip b_{l_p j} over A's row in ascending order with fused
-// multiply-adds (binary search of j in the sorted B row), which is exactly the order of a
-// row-by-row sequential product: results are bit-reproducible. Built with --fmad=false.
+// warp first gathers the row's products into shared memory with all loads in flight at once
+// (lanes over the A entries for the B row extents, then lanes over the flattened products for
+// their columns and values). The pattern is the union of those columns, collected in a per-warp
+// open-addressing hash set, compacted and sorted by rank. The values are then accumulated from
+// shared memory with A's entries taken one at a time in ascending order and lanes over the B row
+// of each (a B row holds each column once, so no two lanes meet), with fused multiply-adds: every
+// c_ij is the sum over A's row in ascending order, exactly the order of a row-by-row sequential
+// product, so results are bit-reproducible. Built with --fmad=false.
 #include <climits>
 
 #include "common.cuh"
@@ -127,12 +130,14 @@ int64_t interp(const double* xf, int64_t nf, const double* xc, int64_t nc, int m
 // ------------------------------ SpGEMM ---------------------------------------------------------
 // Hash-set size per warp: the next power of two >= 2x the largest product count of any row
 // (64..4096 slots); at most half the slots may be filled (distinct columns of one row).
-constexpr int SG_WARPS = 4;
 constexpr int SG_MAX_HASH = 4096;
 
-__device__ __forceinline__ int sg_insert(int* slots, int hs, int col) {
+__device__ __forceinline__ unsigned sg_hash(int col, int hs) {
     const int shift = 32 - (31 - __clz(hs));
-    unsigned h = ((unsigned)col * 2654435761u) >> shift;
+    return ((unsigned)col * 2654435761u) >> shift;
+}
+__device__ __forceinline__ int sg_insert(int* slots, int hs, int col) {
+    unsigned h = sg_hash(col, hs);
     for (int probe = 0; probe < hs; ++probe) {
         int old = atomicCAS(&slots[h], -1, col);
         if (old == -1) return 1;
@@ -141,21 +146,86 @@ __device__ __forceinline__ int sg_insert(int* slots, int hs, int col) {
     }
     return -1;
 }
+// slot of a column known to be in the set
+__device__ __forceinline__ int sg_find(const int* slots, int hs, int col) {
+    unsigned h = sg_hash(col, hs);
+    for (int probe = 0; probe < hs && slots[h] != col; ++probe) h = (h + 1) & (hs - 1);
+    return (int)h;
+}
 
-// per-warp: build the hash set of row i's columns; returns the unique count (warp-uniform)
-__device__ int sg_collect(int* slots, int hs, const int32_t* arp, const int32_t* aci, const int32_t* brp,
-                          const int32_t* bci, int64_t i, int lane, bool* overflow) {
+// Per-warp shared memory: (numeric) accumulators acc[hs/2] (double); hash slots[hs], then
+// (numeric) rank[hs] and lst[hs/2]; the products' columns pj[mp] and values pv[mp] (double), and
+// per A entry its first product aoff[ma + 1] and value aval[ma] (double). mp: the largest product
+// count of a row, ma: the largest A row.
+struct SgLayout {
+    size_t slots, rank, lst, acc, pj, pv, aoff, aval, bytes;
+};
+__host__ __device__ inline SgLayout sg_layout(int hs, int mp, int ma, bool numeric) {
+    SgLayout o;
+    size_t off = 0;
+    o.acc = off; off += numeric ? 8 * (size_t)(hs / 2) : 0;  // accumulators by rank (double)
+    o.slots = off; off += 4 * (size_t)hs;
+    o.rank = off; off += numeric ? 4 * (size_t)hs : 0;
+    o.lst = off; off += numeric ? 4 * (size_t)(hs / 2) : 0;
+    o.pj = off; off += 4 * (size_t)mp;
+    off = (off + 7) & ~(size_t)7;
+    o.pv = off; off += numeric ? 8 * (size_t)mp : 0;
+    o.aoff = off; off += 4 * (size_t)(ma + 1);
+    off = (off + 7) & ~(size_t)7;
+    o.aval = off; off += numeric ? 8 * (size_t)ma : 0;
+    o.bytes = (off + 15) & ~(size_t)15;
+    return o;
+}
+
+// Gathers row i's products into pj (and pv, aval when av is given) in A-row order, aoff[t] = first
+// product of A entry t; then inserts the columns into the hash set. Returns the number of distinct
+// columns (warp-uniform); *overflow when the set or the product buffer is too small.
+__device__ int sg_gather(int* slots, int hs, int* pj, double* pv, int* aoff, double* aval, int mp, const int32_t* arp,
+                         const int32_t* aci, const double* av, const int32_t* brp, const int32_t* bci, const double* bv,
+                         int64_t i, int lane, bool* overflow) {
     for (int t = lane; t < hs; t += 32) slots[t] = -1;
-    __syncwarp();
-    int added = 0;
-    bool ovf = false;
-    for (int32_t p = arp[i]; p < arp[i + 1]; ++p) {
-        int32_t l = aci[p];
-        for (int32_t q = brp[l] + lane; q < brp[l + 1]; q += 32) {
-            int r = sg_insert(slots, hs, bci[q]);
-            if (r < 0) ovf = true;
-            else added += r;
+    const int32_t ab = arp[i], ae = arp[i + 1];
+    int base = 0;
+    for (int32_t c0 = ab; c0 < ae; c0 += 32) {
+        const int32_t p = c0 + lane;
+        const bool has = p < ae;
+        const int32_t l = has ? aci[p] : 0;
+        const int32_t b0 = has ? brp[l] : 0;
+        const int len = has ? brp[l + 1] - b0 : 0;
+        if (has && av) aval[p - ab] = av[p];
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
+        const int excl = incl - len, tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (has) aoff[p - ab] = base + excl;
+        // lanes over the flattened products of these (up to) 32 A entries
+        for (int e0 = 0; e0 < tot; e0 += 32) {
+            const int e = e0 + lane;
+            // the A entry whose products hold e: the last lane with excl <= e
+            int lo = 0;
+            for (int step = 16; step; step >>= 1) {
+                const int x = __shfl_sync(0xffffffffu, excl, lo + step);
+                if (lo + step < 32 && x <= e) lo += step;
+            }
+            const int32_t sb = __shfl_sync(0xffffffffu, b0, lo), se = __shfl_sync(0xffffffffu, excl, lo);
+            if (e < tot && base + e < mp) {
+                const int32_t q = sb + (e - se);
+                pj[base + e] = bci[q];
+                if (bv) pv[base + e] = bv[q];
+            }
+        }
+        base += tot;
+    }
+    if (lane == 0 && ae > ab) aoff[ae - ab] = base;
+    __syncwarp();
+    bool ovf = base > mp;
+    int added = 0;
+    for (int e = lane; e < base && !ovf; e += 32) {
+        const int r = sg_insert(slots, hs, pj[e]);
+        if (r < 0) ovf = true;
+        else added += r;
     }
     __syncwarp();
     added = warp_sum_i(added);
@@ -163,94 +233,110 @@ __device__ int sg_collect(int* slots, int hs, const int32_t* arp, const int32_t*
     return added;
 }
 
+// largest product count and largest A row over the rows: mx[0], mx[1]
 __global__ void sg_maxprod_k(int64_t nA, const int32_t* arp, const int32_t* aci, const int32_t* brp, int* mx) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nA) return;
     int c = 0;
     for (int32_t p = arp[i]; p < arp[i + 1]; ++p) c += brp[aci[p] + 1] - brp[aci[p]];
     atomicMax(mx, c);
+    atomicMax(mx + 1, arp[i + 1] - arp[i]);
 }
 
-__global__ void __launch_bounds__(SG_WARPS * 32) spgemm_symbolic_k(int64_t nA, const int32_t* arp, const int32_t* aci,
-                                                                   const int32_t* brp, const int32_t* bci, int32_t* cnt,
-                                                                   int hs, int* err) {
-    extern __shared__ int sg_smem[];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t i = (int64_t)blockIdx.x * SG_WARPS + w;
+__global__ void spgemm_symbolic_k(int64_t nA, const int32_t* arp, const int32_t* aci, const int32_t* brp,
+                                  const int32_t* bci, int32_t* cnt, int hs, int mp, int ma, int* err) {
+    extern __shared__ __align__(16) unsigned char sg_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const SgLayout lay = sg_layout(hs, mp, ma, false);
+    unsigned char* base = sg_smem + lay.bytes * w;
+    const int64_t i = (int64_t)blockIdx.x * wpb + w;
     if (i >= nA) return;
     bool ovf;
-    int u = sg_collect(sg_smem + w * hs, hs, arp, aci, brp, bci, i, lane, &ovf);
+    const int u = sg_gather((int*)(base + lay.slots), hs, (int*)(base + lay.pj), nullptr, (int*)(base + lay.aoff), nullptr,
+                            mp, arp, aci, nullptr, brp, bci, nullptr, i, lane, &ovf);
     if (lane == 0) {
         cnt[i] = u;
         if (ovf) atomicOr(err, 1);
     }
 }
 
-__global__ void __launch_bounds__(SG_WARPS * 32) spgemm_numeric_k(int64_t nA, const int32_t* arp, const int32_t* aci,
-                                                                  const double* av, const int32_t* brp, const int32_t* bci,
-                                                                  const double* bv, const int32_t* crp, int32_t* cci,
-                                                                  double* cv, int hs, int* err) {
-    extern __shared__ int sg_smem[];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int* slots = sg_smem + w * hs;
-    int* lst = sg_smem + SG_WARPS * hs + w * (hs / 2);
-    int64_t i = (int64_t)blockIdx.x * SG_WARPS + w;
+__global__ void spgemm_numeric_k(int64_t nA, const int32_t* arp, const int32_t* aci, const double* av,
+                                 const int32_t* brp, const int32_t* bci, const double* bv, const int32_t* crp,
+                                 int32_t* cci, double* cv, int hs, int mp, int ma, int* err) {
+    extern __shared__ __align__(16) unsigned char sg_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const SgLayout lay = sg_layout(hs, mp, ma, true);
+    unsigned char* base = sg_smem + lay.bytes * w;
+    int* slots = (int*)(base + lay.slots);
+    int* rank = (int*)(base + lay.rank);
+    int* lst = (int*)(base + lay.lst);
+    int* pj = (int*)(base + lay.pj);
+    double* pv = (double*)(base + lay.pv);
+    int* aoff = (int*)(base + lay.aoff);
+    double* aval = (double*)(base + lay.aval);
+    const int64_t i = (int64_t)blockIdx.x * wpb + w;
     if (i >= nA) return;
     bool ovf;
-    int u = sg_collect(slots, hs, arp, aci, brp, bci, i, lane, &ovf);
+    const int u = sg_gather(slots, hs, pj, pv, aoff, aval, mp, arp, aci, av, brp, bci, bv, i, lane, &ovf);
     if (ovf || u != crp[i + 1] - crp[i]) {
         if (lane == 0) atomicOr(err, 2);
         return;
     }
     // compact the set into lst
-    int base = 0;
+    int nb = 0;
     for (int t = lane; t - lane < hs; t += 32) {
-        int c = t < hs ? slots[t] : -1;
-        unsigned m = __ballot_sync(0xffffffffu, c >= 0);
-        if (c >= 0) lst[base + __popc(m & ((1u << lane) - 1u))] = c;
-        base += __popc(m);
+        const int c = t < hs ? slots[t] : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, c >= 0);
+        if (c >= 0) lst[nb + __popc(m & ((1u << lane) - 1u))] = c;
+        nb += __popc(m);
     }
     __syncwarp();
-    // rank sort into the slot array (reused as the sorted column list)
-    int* sorted = slots;
+    // rank of each column among the row's columns, kept at its hash slot; the sorted columns out
+    double* acc = (double*)(base + lay.acc);
+    const int32_t c0 = crp[i];
     for (int t = lane; t < u; t += 32) {
-        int c = lst[t];
+        const int c = lst[t];
         int r = 0;
         for (int q = 0; q < u; ++q) r += lst[q] < c ? 1 : 0;
-        sorted[r] = c;
+        rank[sg_find(slots, hs, c)] = r;
+        cci[c0 + r] = c;
+        acc[r] = 0.0;
     }
     __syncwarp();
-    const int32_t c0 = crp[i];
-    const int32_t ab = arp[i], ae = arp[i + 1];
-    for (int t = lane; t < u; t += 32) {
-        int j = sorted[t];
-        double acc = 0.0;
-        for (int32_t p = ab; p < ae; ++p) {
-            int32_t l = aci[p];
-            int32_t lo = brp[l], hi = brp[l + 1] - 1;
-            while (lo <= hi) {
-                int32_t mid = (lo + hi) >> 1;
-                int32_t bc = bci[mid];
-                if (bc == j) { acc = fma(av[p], bv[mid], acc); break; }
-                if (bc < j) lo = mid + 1; else hi = mid - 1;
-            }
+    // A's entries one at a time, in order; lanes over the products of each
+    const int na = arp[i + 1] - arp[i];
+    for (int p = 0; p < na; ++p) {
+        const double a = aval[p];
+        for (int e = aoff[p] + lane; e < aoff[p + 1]; e += 32) {
+            const int r = rank[sg_find(slots, hs, pj[e])];
+            acc[r] = fma(a, pv[e], acc[r]);
         }
-        cci[c0 + t] = j;
-        cv[c0 + t] = acc;
+        __syncwarp();
     }
+    for (int t = lane; t < u; t += 32) cv[c0 + t] = acc[t];
 }
 
-static int sg_hash_size(int64_t nA, const int32_t* arp, const int32_t* aci, const int32_t* brp, cudaStream_t s) {
-    Temp<int> mx(1, s);
-    CK(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
+struct SgShape {
+    int hs, mp, ma;
+};
+static SgShape sg_shape(int64_t nA, const int32_t* arp, const int32_t* aci, const int32_t* brp, cudaStream_t s) {
+    Temp<int> mx(2, s);
+    CK(cudaMemsetAsync(mx.get(), 0, 2 * sizeof(int), s));
     if (nA > 0) {
         sg_maxprod_k<<<grid_for(nA, 256), 256, 0, s>>>(nA, arp, aci, brp, mx.get());
         CK_LAUNCH();
     }
-    int m = read1(mx.get(), s);
+    int h[2];
+    to_host(h, mx.get(), 2, s);
     int hs = 64;
-    while (hs < 2 * m && hs < SG_MAX_HASH) hs *= 2;
-    return hs;
+    while (hs < 2 * h[0] && hs < SG_MAX_HASH) hs *= 2;
+    return {hs, std::max(h[0], 1), std::max(h[1], 1)};
+}
+// warps per block: up to 4, within 200 KB of shared memory
+static int sg_warps(size_t per_warp) {
+    int w = 4;
+    while (w > 1 && per_warp * w > 200 * 1024) --w;
+    return w;
 }
 
 // symbolic phase: fills crp (nA+1), returns nnz
@@ -260,11 +346,13 @@ int64_t spgemm_symbolic(int64_t nA, const int32_t* arp, const int32_t* aci, cons
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
     if (nA > 0) {
-        const int hs = sg_hash_size(nA, arp, aci, brp, s);
-        const size_t smem = sizeof(int) * SG_WARPS * hs;
-        CK(cudaFuncSetAttribute(spgemm_symbolic_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        spgemm_symbolic_k<<<grid_for(nA, SG_WARPS), SG_WARPS * 32, smem, s>>>(nA, arp, aci, brp, bci, cnt.get(), hs,
-                                                                             err.get());
+        const SgShape sh = sg_shape(nA, arp, aci, brp, s);
+        const size_t per = sg_layout(sh.hs, sh.mp, sh.ma, false).bytes;
+        if (per > 200 * 1024) fail(MGM_ERR_UNSUPPORTED, "SpGEMM row has too many products");
+        const int wpb = sg_warps(per);
+        CK(cudaFuncSetAttribute(spgemm_symbolic_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per * wpb)));
+        spgemm_symbolic_k<<<grid_for(nA, wpb), wpb * 32, per * wpb, s>>>(nA, arp, aci, brp, bci, cnt.get(), sh.hs, sh.mp,
+                                                                       sh.ma, err.get());
         CK_LAUNCH();
     }
     if (read1(err.get(), s)) fail(MGM_ERR_UNSUPPORTED, "SpGEMM row exceeds 2048 distinct columns");
@@ -277,11 +365,13 @@ void spgemm_numeric(int64_t nA, const int32_t* arp, const int32_t* aci, const do
     if (nA <= 0) return;
     Temp<int> err(1, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
-    const int hs = sg_hash_size(nA, arp, aci, brp, s);
-    const size_t smem = sizeof(int) * SG_WARPS * (hs + hs / 2);
-    CK(cudaFuncSetAttribute(spgemm_numeric_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    spgemm_numeric_k<<<grid_for(nA, SG_WARPS), SG_WARPS * 32, smem, s>>>(nA, arp, aci, av, brp, bci, bv, crp, cci, cv, hs,
-                                                                        err.get());
+    const SgShape sh = sg_shape(nA, arp, aci, brp, s);
+    const size_t per = sg_layout(sh.hs, sh.mp, sh.ma, true).bytes;
+    if (per > 200 * 1024) fail(MGM_ERR_UNSUPPORTED, "SpGEMM row has too many products");
+    const int wpb = sg_warps(per);
+    CK(cudaFuncSetAttribute(spgemm_numeric_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per * wpb)));
+    spgemm_numeric_k<<<grid_for(nA, wpb), wpb * 32, per * wpb, s>>>(nA, arp, aci, av, brp, bci, bv, crp, cci, cv, sh.hs,
+                                                                  sh.mp, sh.ma, err.get());
     CK_LAUNCH();
     if (read1(err.get(), s)) fail(MGM_ERR_INVALID_ARG, "SpGEMM: row pointer does not match the product pattern");
 }

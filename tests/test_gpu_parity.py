@@ -284,6 +284,29 @@ def test_interp_transpose_galerkin(M, oracle, ico5):
     assert np.max(diff) <= 1e-12 * np.max(np.abs(G.data))
 
 
+def test_spgemm_long_rows(M, oracle):
+    """C = A B with A rows of up to 90 entries (three chunks of 32) and B rows of up to 70, empty
+    rows on both sides; pattern exact, values against the oracle's product."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(21)
+
+    def rand_csr(n, m, maxlen):
+        lens = rng.integers(0, maxlen + 1, n)
+        lens[::17] = 0
+        rows = np.repeat(np.arange(n), lens)
+        cols = np.concatenate([rng.choice(m, k, replace=False) for k in lens])
+        A = sp.csr_matrix((rng.standard_normal(rows.size), (rows, cols)), shape=(n, m))
+        A.sort_indices()
+        return A
+
+    A, B = rand_csr(1500, 2500, 90), rand_csr(2500, 700, 70)
+    C = oracle.spgemm(A, B)
+    dev = lambda X: (T(X.indptr.astype(np.int32)), T(X.indices.astype(np.int32)), T(X.data))
+    g = M.spgemm(A.shape[0], B.shape[0], B.shape[1], dev(A), dev(B))
+    assert np.array_equal(H(g[0]), C.indptr) and np.array_equal(H(g[1]), C.indices)
+    assert np.max(np.abs(H(g[2]) - C.data)) <= 1e-12 * np.max(np.abs(C.data))
+
+
 # ---------------------------------------------------------------------------------- hierarchy
 @pytest.fixture(scope="module")
 def hier(M, oracle, ico5):
