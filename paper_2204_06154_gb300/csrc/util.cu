@@ -321,15 +321,20 @@ __global__ void perm_rowlen_k(const int32_t* rp, const int32_t* perm, int64_t N,
         len[i] = rp[o + 1] - rp[o];
     }
 }
-__global__ void perm_fill_k(const int32_t* rp, const int32_t* ci, const double* v, const int32_t* perm,
-                            const int32_t* inv, int64_t N, const int32_t* brp, int32_t* bci, double* bv) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per row: lanes over the source row's entries, so loads and stores coalesce and the
+// renumbering gathers of a row are in flight together
+constexpr int PF_WARPS = 8;
+__global__ void __launch_bounds__(PF_WARPS * 32) perm_fill_k(const int32_t* rp, const int32_t* ci, const double* v,
+                                                             const int32_t* perm, const int32_t* inv, int64_t N,
+                                                             const int32_t* brp, int32_t* bci, double* bv) {
+    const int64_t i = (int64_t)blockIdx.x * PF_WARPS + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (i >= N) return;
-    int32_t o = perm[i];
-    int32_t q = brp[i];
-    for (int32_t p = rp[o]; p < rp[o + 1]; ++p, ++q) {
-        bci[q] = inv[ci[p]];
-        if (bv) bv[q] = v[p];
+    const int32_t o = perm[i];
+    const int32_t b = rp[o], e = rp[o + 1], q = brp[i] - b;
+    for (int32_t p = b + lane; p < e; p += 32) {
+        bci[q + p] = inv[ci[p]];
+        if (bv) bv[q + p] = v[p];
     }
 }
 void csr_permute(int64_t N, const int32_t* rp, const int32_t* ci, const double* v, const int32_t* perm,
@@ -340,7 +345,7 @@ void csr_permute(int64_t N, const int32_t* rp, const int32_t* ci, const double* 
     CK_LAUNCH();
     exclusive_scan_i32(len.get(), brp, N, s);
     invert_perm(perm, inv.get(), N, s);
-    perm_fill_k<<<grid_for(N, 256), 256, 0, s>>>(rp, ci, v, perm, inv.get(), N, brp, bci, bv);
+    perm_fill_k<<<grid_for(N, PF_WARPS), PF_WARPS * 32, 0, s>>>(rp, ci, v, perm, inv.get(), N, brp, bci, bv);
     CK_LAUNCH();
     sort_rows_k<<<grid_for(N, SR_WARPS), SR_WARPS * 32, 0, s>>>(brp, bci, bv, N);
     CK_LAUNCH();
@@ -349,24 +354,70 @@ void csr_permute(int64_t N, const int32_t* rp, const int32_t* ci, const double* 
 // ---------------------------------------------------------------------------------------------
 // symmetrised pattern: union of row i of A and row i of A^T, diagonal dropped
 // ---------------------------------------------------------------------------------------------
-template <bool WRITE>
-__global__ void union_rows_k(const int32_t* rp, const int32_t* ci, const int32_t* trp, const int32_t* tci, int64_t N,
-                             int32_t* cnt, const int32_t* orp, int32_t* oci) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int32_t a = rp[i], ae = rp[i + 1], b = trp[i], be = trp[i + 1];
-    int32_t c = 0, last = -1;
-    int32_t q = WRITE ? orp[i] : 0;
-    while (a < ae || b < be) {
-        int32_t x;
-        if (b >= be || (a < ae && ci[a] <= tci[b])) x = ci[a++];
-        else x = tci[b++];
-        if (x == i || x == last) continue;
-        last = x;
-        if (WRITE) oci[q + c] = x;
-        ++c;
+// One warp per row. Both sorted rows (of A and of A^T) are staged in shared memory; each entry
+// finds its place in the merged sequence by a binary search in the other row (an entry of A
+// before an equal entry of A^T), and a ballot scan compacts, in order, the entries that are
+// neither the diagonal nor equal to the entry before them. Rows longer than UR_MAX are merged by
+// one lane.
+constexpr int UR_WARPS = 8, UR_MAX = 256;
+__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int32_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
     }
-    if (!WRITE) cnt[i] = c;
+    return lo;
+}
+template <bool WRITE>
+__global__ void __launch_bounds__(UR_WARPS * 32) union_rows_k(const int32_t* rp, const int32_t* ci, const int32_t* trp,
+                                                              const int32_t* tci, int64_t N, int32_t* cnt,
+                                                              const int32_t* orp, int32_t* oci) {
+    __shared__ int32_t sa[UR_WARPS][UR_MAX], st[UR_WARPS][UR_MAX], sm[UR_WARPS][2 * UR_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * UR_WARPS + w;
+    if (i >= N) return;
+    const int32_t a = rp[i], ae = rp[i + 1], b = trp[i], be = trp[i + 1];
+    const int la = ae - a, lt = be - b;
+    const int32_t q = WRITE ? orp[i] : 0;
+    if (la > UR_MAX || lt > UR_MAX) {
+        if (lane == 0) {
+            int32_t c = 0, last = -1, x;
+            for (int32_t p = a, r = b; p < ae || r < be;) {
+                if (r >= be || (p < ae && ci[p] <= tci[r])) x = ci[p++];
+                else x = tci[r++];
+                if (x == i || x == last) continue;
+                last = x;
+                if (WRITE) oci[q + c] = x;
+                ++c;
+            }
+            if (!WRITE) cnt[i] = c;
+        }
+        return;
+    }
+    for (int t = lane; t < la; t += 32) sa[w][t] = ci[a + t];
+    for (int t = lane; t < lt; t += 32) st[w][t] = tci[b + t];
+    __syncwarp();
+    // the merged sequence, duplicates included (equal values end up next to each other)
+    for (int t = lane; t < la; t += 32) {
+        const int32_t x = sa[w][t];
+        sm[w][t + lower_bound_i32(st[w], lt, x)] = x;
+    }
+    for (int t = lane; t < lt; t += 32) {
+        const int32_t y = st[w][t];
+        sm[w][t + lower_bound_i32(sa[w], la, y + 1)] = y;  // after the entries of A <= y
+    }
+    __syncwarp();
+    // kept: not the diagonal, and not equal to the entry before it
+    int32_t c = 0;
+    for (int t0 = 0; t0 < la + lt; t0 += 32) {
+        const int t = t0 + lane;
+        const int32_t x = t < la + lt ? sm[w][t] : -1;
+        const bool keep = t < la + lt && x != (int32_t)i && (t == 0 || sm[w][t - 1] != x);
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (WRITE && keep) oci[q + c + __popc(m & ((1u << lane) - 1u))] = x;
+        c += __popc(m);
+    }
+    if (!WRITE && lane == 0) cnt[i] = c;
 }
 void sym_pattern(int64_t N, const int32_t* rp, const int32_t* ci, Temp<int32_t>& srp, Temp<int32_t>& sci,
                  cudaStream_t s) {
@@ -376,14 +427,16 @@ void sym_pattern(int64_t N, const int32_t* rp, const int32_t* ci, Temp<int32_t>&
     Temp<int32_t> cnt(N + 1, s);
     srp.alloc(N + 1, s);
     if (N > 0) {
-        union_rows_k<false><<<grid_for(N, 256), 256, 0, s>>>(rp, ci, trp.get(), tci.get(), N, cnt.get(), nullptr, nullptr);
+        union_rows_k<false><<<grid_for(N, UR_WARPS), UR_WARPS * 32, 0, s>>>(rp, ci, trp.get(), tci.get(), N, cnt.get(),
+                                                                           nullptr, nullptr);
         CK_LAUNCH();
     }
     exclusive_scan_i32(cnt.get(), srp.get(), N, s);
     int64_t snnz = csr_nnz(srp.get(), N, s);
     sci.alloc(snnz > 0 ? snnz : 1, s);
     if (N > 0) {
-        union_rows_k<true><<<grid_for(N, 256), 256, 0, s>>>(rp, ci, trp.get(), tci.get(), N, nullptr, srp.get(), sci.get());
+        union_rows_k<true><<<grid_for(N, UR_WARPS), UR_WARPS * 32, 0, s>>>(rp, ci, trp.get(), tci.get(), N, nullptr,
+                                                                          srp.get(), sci.get());
         CK_LAUNCH();
     }
 }
