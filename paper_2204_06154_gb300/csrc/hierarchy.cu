@@ -79,63 +79,73 @@ __global__ void fill_ones_k(double* x, int64_t n) {
 }
 
 
-// Gauss-Jordan with partial pivoting on [A | I] (n x 2n): pivot step k
-__global__ void __launch_bounds__(1024) gj_pivot_k(double* A, int64_t n, int64_t k, double* mult, int* err) {
-    __shared__ double sv[32];
-    __shared__ int si[32];
+// Gauss-Jordan with partial pivoting on [A | I] (n x 2n), every step in one cooperative launch.
+// Step k reads buffer `cur` and writes `nxt` (so no block overwrites a row another block still
+// reads), then all blocks meet at a grid barrier. Every block finds the pivot itself (first row
+// of largest |a_ik|, i >= k: the same result everywhere), and updates its rows i = block, block +
+// grid, ...: row k becomes the pivot row divided by a_pk; row p (p != k) takes the old row k, and
+// every row r != k subtracts a_rk times that divided pivot row with a fused multiply-add (rows
+// with a_rk = 0 are copied). These are the operations, in order, of a row swap, a division of
+// the pivot row and one elimination step. Columns left of k are not written: no later step reads
+// them. The waits are bounded (grid_barrier); a singular step leaves err = 1 in every block.
+constexpr int GJ_THREADS = 256;
+__global__ void __launch_bounds__(GJ_THREADS) gj_coop_k(double* A0, double* A1, int64_t n, unsigned* bar, int* err,
+                                                       unsigned long long limit) {
+    __shared__ double sv[GJ_THREADS / 32];
+    __shared__ int si[GJ_THREADS / 32];
+    __shared__ int ok;
     const int64_t ld = 2 * n;
-    double best = -1.0;
-    int64_t piv = k;
-    for (int64_t i = k + threadIdx.x; i < n; i += blockDim.x) {
-        double v = fabs(A[i * ld + k]);
-        if (v > best) { best = v; piv = i; }
-    }
-    for (int o = 16; o; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int64_t op = __shfl_xor_sync(0xffffffffu, piv, o);
-        if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
-    }
-    if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = (int)piv; }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        int nw = blockDim.x >> 5;
-        double b = threadIdx.x < nw ? sv[threadIdx.x] : -1.0;
-        int p = threadIdx.x < nw ? si[threadIdx.x] : 0x7fffffff;
+    double* cur = A0;
+    double* nxt = A1;
+    unsigned target = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        double best = -1.0;
+        int64_t piv = k;
+        for (int64_t i = k + threadIdx.x; i < n; i += blockDim.x) {
+            const double v = fabs(cur[i * ld + k]);
+            if (v > best) { best = v; piv = i; }
+        }
         for (int o = 16; o; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, b, o);
-            int op = __shfl_xor_sync(0xffffffffu, p, o);
-            if (ob > b || (ob == b && op < p)) { b = ob; p = op; }
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int64_t op = __shfl_xor_sync(0xffffffffu, piv, o);
+            if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
         }
-        if (threadIdx.x == 0) { sv[0] = b; si[0] = p; }
-    }
-    __syncthreads();
-    best = sv[0];
-    piv = si[0];
-    if (!(best > 0.0)) {
-        if (threadIdx.x == 0) *err = 1;
-        return;
-    }
-    if (piv != k)
-        for (int64_t j = threadIdx.x; j < ld; j += blockDim.x) {
-            double t = A[k * ld + j];
-            A[k * ld + j] = A[piv * ld + j];
-            A[piv * ld + j] = t;
+        if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = (int)piv; }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int nw = blockDim.x >> 5;
+            double b = threadIdx.x < nw ? sv[threadIdx.x] : -1.0;
+            int p = threadIdx.x < nw ? si[threadIdx.x] : 0x7fffffff;
+            for (int o = 16; o; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, b, o);
+                const int op = __shfl_xor_sync(0xffffffffu, p, o);
+                if (ob > b || (ob == b && op < p)) { b = ob; p = op; }
+            }
+            if (threadIdx.x == 0) { sv[0] = b; si[0] = p; }
         }
-    __syncthreads();
-    double akk = A[k * ld + k];
-    __syncthreads();
-    for (int64_t j = threadIdx.x; j < ld; j += blockDim.x) A[k * ld + j] = A[k * ld + j] / akk;
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mult[i] = (i == k) ? 0.0 : A[i * ld + k];
-}
-
-__global__ void gj_elim_k(double* A, int64_t n, int64_t k, const double* mult) {
-    const int64_t ld = 2 * n;
-    int64_t i = blockIdx.y;
-    double mi = mult[i];
-    if (mi == 0.0) return;
-    for (int64_t j = k + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ld; j += (int64_t)gridDim.x * blockDim.x)
-        A[i * ld + j] = fma(-mi, A[k * ld + j], A[i * ld + j]);
+        __syncthreads();
+        best = sv[0];
+        piv = si[0];
+        __syncthreads();  // everyone has read sv[0], si[0] before the next step overwrites them
+        if (!(best > 0.0)) {
+            if (threadIdx.x == 0) *err = 1;
+            return;
+        }
+        const double akk = cur[piv * ld + k];
+        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+            const double* src = cur + (i == piv ? k : i) * ld;
+            const double m = i == k ? 0.0 : src[k];
+            for (int64_t j = k + threadIdx.x; j < ld; j += blockDim.x) {
+                const double pr = cur[piv * ld + j] / akk;
+                nxt[i * ld + j] = i == k ? pr : (m == 0.0 ? src[j] : fma(-m, pr, src[j]));
+            }
+        }
+        target += gridDim.x;
+        if (!grid_barrier(bar, target, limit, err, &ok)) return;
+        double* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
 }
 
 __global__ void extract_inv_k(const double* A, int64_t n, double* inv) {
@@ -164,26 +174,41 @@ static void dense_inverse(const Level& L, const double* border, Buf<double>& inv
     const int64_t nl = L.n;
     const int64_t n = nl + (border ? 1 : 0);
     if (n > 8192) fail(MGM_ERR_UNSUPPORTED, "coarsest level larger than 8192 rows");
-    Temp<double> A(2 * n * n, s), mult(n, s);
+    Temp<double> A(2 * n * n, s), B(2 * n * n, s);
     Temp<int> err(1, s);
+    Temp<unsigned> bar(1, s);
     CK(cudaMemsetAsync(A.get(), 0, sizeof(double) * 2 * n * n, s));
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+    CK(cudaMemsetAsync(bar.get(), 0, sizeof(unsigned), s));
     csr_to_dense_k<<<grid_for(nl, 128), 128, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), nl, A.get(), 2 * n, n);
     CK_LAUNCH();
     if (border) {
         border_dense_k<<<grid_for(n, 128), 128, 0, s>>>(border, nl, A.get());
         CK_LAUNCH();
     }
-    for (int64_t k = 0; k < n; ++k) {
-        gj_pivot_k<<<1, 1024, 0, s>>>(A.get(), n, k, mult.get(), err.get());
-        CK_LAUNCH();
-        dim3 g((unsigned)std::min<int64_t>((2 * n - k + 255) / 256, 8), (unsigned)n);
-        gj_elim_k<<<g, 256, 0, s>>>(A.get(), n, k, mult.get());
-        CK_LAUNCH();
+    static int mb = 0;
+    if (!mb) {
+        int per_sm = 0, dev = 0, sms = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_coop_k, GJ_THREADS, 0));
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        mb = std::max(1, std::min(per_sm, 1) * sms);  // one block an SM
     }
-    if (read1(err.get(), s)) fail(MGM_ERR_BREAKDOWN, "coarsest operator is singular");
+    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(mb, n));
+    double* a0 = A.get();
+    double* a1 = B.get();
+    unsigned* barp = bar.get();
+    int* errp = err.get();
+    int64_t nn = n;
+    unsigned long long limit = 4000000ull;
+    void* args[] = {(void*)&a0, (void*)&a1, (void*)&nn, (void*)&barp, (void*)&errp, (void*)&limit};
+    CK(cudaLaunchCooperativeKernel((const void*)gj_coop_k, dim3(nblocks), dim3(GJ_THREADS), args, 0, s));
+    CK_LAUNCH();
+    const int e = read1(err.get(), s);
+    if (e == 1) fail(MGM_ERR_BREAKDOWN, "coarsest operator is singular");
+    if (e) fail(MGM_ERR_TIMEOUT, "coarsest factorisation: a grid barrier timed out");
     inv.alloc(n * n);
-    extract_inv_k<<<grid_for(n * n, 256), 256, 0, s>>>(A.get(), n, inv.get());
+    extract_inv_k<<<grid_for(n * n, 256), 256, 0, s>>>((n % 2 == 0) ? A.get() : B.get(), n, inv.get());
     CK_LAUNCH();
 }
 
