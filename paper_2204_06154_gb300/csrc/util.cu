@@ -236,23 +236,18 @@ void validate_csr(int64_t nrows, int64_t ncols, const int32_t* rp, const int32_t
 // ---------------------------------------------------------------------------------------------
 // CSR transpose: count per column, scan, place with atomics, then sort each row by source row
 // ---------------------------------------------------------------------------------------------
-// one warp per row (lanes over its entries, coalesced); the order within a column is fixed
-// afterwards by sorting the transposed rows
-constexpr int TP_WARPS = 8;
-__global__ void __launch_bounds__(TP_WARPS * 32) count_cols_k(const int32_t* rp, const int32_t* ci, int64_t nrows,
-                                                              int32_t* cnt) {
-    const int64_t i = (int64_t)blockIdx.x * TP_WARPS + (threadIdx.x >> 5);
+__global__ void count_cols_k(const int32_t* rp, const int32_t* ci, int64_t nrows, int32_t* cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrows) return;
-    for (int32_t p = rp[i] + (threadIdx.x & 31); p < rp[i + 1]; p += 32) atomicAdd(&cnt[ci[p]], 1);
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) atomicAdd(&cnt[ci[p]], 1);
 }
-__global__ void __launch_bounds__(TP_WARPS * 32) place_t_k(const int32_t* rp, const int32_t* ci, const double* v,
-                                                           int64_t nrows, const int32_t* trp, int32_t* fill,
-                                                           int32_t* tci, double* tv) {
-    const int64_t i = (int64_t)blockIdx.x * TP_WARPS + (threadIdx.x >> 5);
+__global__ void place_t_k(const int32_t* rp, const int32_t* ci, const double* v, int64_t nrows, const int32_t* trp,
+                          int32_t* fill, int32_t* tci, double* tv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrows) return;
-    for (int32_t p = rp[i] + (threadIdx.x & 31); p < rp[i + 1]; p += 32) {
-        const int32_t c = ci[p];
-        const int32_t q = trp[c] + atomicAdd(&fill[c], 1);
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int32_t c = ci[p];
+        int32_t q = trp[c] + atomicAdd(&fill[c], 1);
         tci[q] = (int32_t)i;
         if (v) tv[q] = v[p];
     }
@@ -301,13 +296,13 @@ void csr_transpose(int64_t nrows, int64_t ncols, const int32_t* rp, const int32_
     Temp<int32_t> cnt(ncols + 1, s);
     CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (ncols + 1), s));
     if (nrows > 0) {
-        count_cols_k<<<grid_for(nrows, TP_WARPS), TP_WARPS * 32, 0, s>>>(rp, ci, nrows, cnt.get());
+        count_cols_k<<<grid_for(nrows, 256), 256, 0, s>>>(rp, ci, nrows, cnt.get());
         CK_LAUNCH();
     }
     exclusive_scan_i32(cnt.get(), trp, ncols, s);
     CK(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t) * (ncols + 1), s));
     if (nrows > 0) {
-        place_t_k<<<grid_for(nrows, TP_WARPS), TP_WARPS * 32, 0, s>>>(rp, ci, v, nrows, trp, cnt.get(), tci, tv);
+        place_t_k<<<grid_for(nrows, 256), 256, 0, s>>>(rp, ci, v, nrows, trp, cnt.get(), tci, tv);
         CK_LAUNCH();
     }
     if (ncols > 0) {
