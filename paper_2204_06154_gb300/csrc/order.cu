@@ -11,7 +11,8 @@
 // Colouring: Jones-Plassmann rounds. An uncoloured vertex whose (SplitMix64(seed, i), i) priority
 // exceeds that of all uncoloured neighbours takes the smallest colour absent from its coloured
 // neighbours. Such vertices are never adjacent, and the result equals sequential first-fit
-// colouring in decreasing priority.
+// colouring in decreasing priority. That equality lets one launch compute it directly along the
+// sorted priority order (jp_ordered_k, below); the rounds remain as its fallback.
 #include <algorithm>
 #include <climits>
 
