@@ -239,6 +239,15 @@ def test_color_bitexact(M, oracle, ico5, seed):
     assert gnc == nc and np.array_equal(H(got), ref)
 
 
+def test_color_rounds_fallback_matches(M, oracle, ico5, monkeypatch):
+    """The JP rounds (the fallback of the one-launch colouring) give the same colours."""
+    x, nrm, idx, w, L = ico5
+    ref, nc = oracle.color(L, 3)
+    monkeypatch.setenv("MGM_COLOR_ROUNDS", "1")
+    got, gnc = M.color(T(L.indptr.astype(np.int32)), T(L.indices.astype(np.int32)), 3)
+    assert gnc == nc and np.array_equal(H(got), ref)
+
+
 def test_color_many_colours_and_ragged(M, oracle):
     """Greedy colouring where windows above 64 colours are needed (cliques of 70 and 130
     vertices), with isolated vertices, a non-symmetric pattern and a size that is no multiple of
