@@ -77,17 +77,19 @@ __device__ __forceinline__ double stencil_coords(const PhsArgs& a, int64_t i, in
     double t1[3], t2[3];
     tangent_basis(a.nrm + 3 * i, t1, t2);
     const double* xc = a.xyz + 3 * i;
-    double s = 0.0;
+    // s = max_j sqrt(u_j^2 + v_j^2), taken as sqrt(max_j (u_j^2 + v_j^2)): the correctly rounded
+    // square root is monotone, so the two are the same number, for one root instead of n
+    double s2 = 0.0;
     for (int j = lane; j < n; j += 32) {
         const double* xj = a.xyz + 3 * (int64_t)id[j];
         double d[3] = {xj[0] - xc[0], xj[1] - xc[1], xj[2] - xc[2]};
         double u = dot3d(t1, d), v = dot3d(t2, d);
         xh[j] = u;
         yh[j] = v;
-        double r = sqrt(u * u + v * v);
-        s = fmax(s, r);
+        s2 = fmax(s2, u * u + v * v);
     }
-    s = warp_max_d(s);
+    s2 = warp_max_d(s2);
+    const double s = sqrt(s2);
     if (!(s > 0.0)) return 0.0;
     const double sinv = 1.0 / s;
     __syncwarp();
