@@ -248,15 +248,17 @@ def test_color_rounds_fallback_matches(M, oracle, ico5, monkeypatch):
     assert gnc == nc and np.array_equal(H(got), ref)
 
 
-def test_color_many_colours_and_ragged(M, oracle):
-    """Greedy colouring where windows above 64 colours are needed (cliques of 70 and 130
-    vertices), with isolated vertices, a non-symmetric pattern and a size that is no multiple of
+@pytest.mark.parametrize("cliques", [((0, 70), (500, 130)), ((100, 300),)])
+def test_color_many_colours_and_ragged(M, oracle, cliques):
+    """Greedy colouring where windows above 64 colours are needed (cliques of 70, 130 and 300
+    vertices; the 300-clique also has rows longer than the symmetric-pattern merge keeps in shared
+    memory), with isolated vertices, a non-symmetric pattern and a size that is no multiple of
     the block size."""
     import scipy.sparse as sp
     rng = np.random.default_rng(5)
     N = 3001
     rows, cols = [], []
-    for c0, k in ((0, 70), (500, 130)):
+    for c0, k in cliques:
         a = np.arange(c0, c0 + k)
         rows.append(np.repeat(a, k)); cols.append(np.tile(a, k))
     r = rng.integers(0, N - 40, 20000); c = rng.integers(0, N - 40, 20000)   # last 40: isolated
@@ -265,7 +267,7 @@ def test_color_many_colours_and_ragged(M, oracle):
     A.sum_duplicates(); A.sort_indices()
     for seed in (0, 7):
         ref, nc = oracle.color(A, seed)
-        assert nc >= 130
+        assert nc >= max(k for _, k in cliques)
         got, gnc = M.color(T(A.indptr.astype(np.int32)), T(A.indices.astype(np.int32)), seed)
         assert gnc == nc and np.array_equal(H(got), ref)
 
