@@ -545,6 +545,8 @@ __device__ __forceinline__ float d2f_trunc(double v) {
     return __uint_as_float(sign | ((unsigned)e << 23) | mant);
 }
 
+constexpr int RL_MAXD = 7;  // largest polynomial degree of the register kernel
+
 struct RlLayout {
     size_t kd, xs, bd, xh, yh, rinv, piv, bytes;
 };
@@ -623,13 +625,45 @@ __global__ void __launch_bounds__(256) phs_weights_rl_k(PhsArgs a, int wpb, int3
         Kd[c * LDD + r] = v;
         amaxb = max(amaxb, mag_bits(v));
     }
-    for (int e = lane; e < n * L; e += 32) {  // separate loops: no divergent FP64 paths
-        int r = e / L, t = e - r * L;
-        int pa, pb;
-        mono_pow(t, &pa, &pb);
-        double v = monomial(xh[r], yh[r], pa, pb);
-        Kd[r * LDD + n + t] = v;
-        amaxb = max(amaxb, mag_bits(v));
+    // the monomials of one point a lane, in the order of mono_pow, with the powers of x and y
+    // shared: x^a y^b is x^a (x multiplied in a - 1 times) times y, b times, exactly the
+    // operations of monomial(), so the same numbers, at one multiplication a monomial or less
+    // and with every lane of the warp on the same degree
+    for (int r = lane; r < n; r += 32) {
+        const double x = xh[r], y = yh[r];
+        double px[RL_MAXD + 1], py[RL_MAXD + 1];
+        px[0] = 1.0;
+        py[0] = 1.0;
+#pragma unroll
+        for (int d = 1; d <= RL_MAXD; ++d) {
+            px[d] = 0.0;
+            py[d] = 0.0;
+            if (d <= a.ell) {
+                px[d] = d == 1 ? x : px[d - 1] * x;
+                py[d] = d == 1 ? y : py[d - 1] * y;
+            }
+        }
+        double* row = Kd + r * LDD + n;
+#pragma unroll
+        for (int d = 0; d <= RL_MAXD; ++d) {
+            if (d <= a.ell) {
+#pragma unroll
+                for (int off = 0; off <= d; ++off) {
+                    double v;
+                    if (off == 0) {
+                        v = px[d];
+                    } else if (off == d) {
+                        v = py[d];
+                    } else {
+                        v = px[d - off];
+#pragma unroll
+                        for (int q = 0; q < off; ++q) v = v * y;
+                    }
+                    row[d * (d + 1) / 2 + off] = v;
+                    amaxb = max(amaxb, mag_bits(v));
+                }
+            }
+        }
     }
     for (int r = lane; r < n; r += 32) bd[r] = phs_lap(xh[r] * xh[r] + yh[r] * yh[r], a.k);
     for (int t = lane; t < L; t += 32) {
@@ -955,7 +989,7 @@ static int64_t phs_mixed(const double* xyz, const double* nrm, int64_t N, const 
     Temp<int> nretry(1, s);
     CK(cudaMemsetAsync(nretry.get(), 0, sizeof(int), s));
     PhsArgs a{xyz, nrm, idx, N, n, k, ell, L, m, w, nullptr, 0, bad, nullptr, 0};
-    if (m == 36 || m == 60) {
+    if ((m == 36 || m == 60) && a.ell <= RL_MAXD) {  // (m = 60 allows ell <= 6 with L <= n)
         // four warps a block: m = 60 takes 255 registers a thread (two blocks an SM), m = 36 about
         // 160 (three blocks)
         const RlLayout rl = rl_layout(n, m);
