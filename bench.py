@@ -78,6 +78,7 @@ def parse():
                     help="profiling driver: build the sphere problem of --size, then run this many V-cycles "
                          "(FP32 unless --fp64-cycle; --learned-n attaches an untrained correction of that stencil size)")
     ap.add_argument("--fp64-cycle", action="store_true")
+    ap.add_argument("--sweeps", default="0,3", help="profiling driver: sweep schedules to compare (persistent_sweeps values)")
     ap.add_argument("--learned-n", type=int, default=0)
     return ap.parse_args()
 
@@ -501,15 +502,28 @@ def main():
         X = torch.from_numpy(x).cuda(); Nr = torch.from_numpy(nrm).cuda()
         n, ell = (a.learned_n, 2) if a.learned_n else (50, 3)
         idx, w, rp, ci, v = M.build_stencils(X, Nr, n, "rbf", 1, ell, 1.0)
-        H = M.Hierarchy(X, rp, ci, v, 250, precision="f64" if a.fp64_cycle else "f32")
-        if a.learned_n:
-            H.learned_attach(X, Nr, idx, w)
-            H.learned_enable(M.MLP(a.learned_n, seed=1))
         r = torch.from_numpy(np.random.default_rng(5).standard_normal(a.size)).cuda()
-        for _ in range(a.vcycles):
-            z = H.vcycle(r)
-        torch.cuda.synchronize()
-        print(json.dumps({"vcycles": a.vcycles, "N": a.size, "levels": H.stats()["n"], "max|z|": float(z.abs().max())}))
+        out = {"vcycles": a.vcycles, "N": a.size}
+        for mode in [int(t) for t in a.sweeps.split(",")]:
+            H = M.Hierarchy(X, rp, ci, v, 250, precision="f64" if a.fp64_cycle else "f32", persistent_sweeps=mode)
+            if a.learned_n:
+                H.learned_attach(X, Nr, idx, w)
+                H.learned_enable(M.MLP(a.learned_n, seed=1))
+            for _ in range(a.vcycles):
+                z = H.vcycle(r)
+            torch.cuda.synchronize()
+            pr = H.profile(reps=20)
+            st = H.stats()
+            sched = [H.sweep_config(j) for j in range(st["p"] - 1)]
+            out[f"mode{mode}"] = {"levels": st["n"], "ncolors": st["ncolors"], "max|z|": float(z.abs().max()),
+                                  "schedules": [(c["kind"][0], c["blocks"], c["lanes"], c["stages"], round(c["ms"], 4))
+                                                for c in sched],
+                                  "vcycle_ms": round(pr["vcycle_ms"], 4), "vcycle_kernels": pr["vcycle_kernels"],
+                                  "vcycle_GB/s": round(pr["vcycle_bytes"] / pr["vcycle_ms"] / 1e6, 1),
+                                  "sweep_ms": round(pr["sweep_ms"], 4),
+                                  "sweep_GB/s": round(pr["sweep_bytes"] / pr["sweep_ms"] / 1e6, 1) if pr["sweep_ms"] else None}
+            del H
+        print(json.dumps(out), flush=True)
         return
     if a.single:
         import torch

@@ -81,13 +81,22 @@ typedef struct {
     int nu1, nu2;    /* pre- and post-smoothing sweeps, 0 <= nu <= 8 */
     int precision;   /* MGM_F32 (V-cycle in FP32, coarsest solve FP64) or MGM_F64 */
     uint64_t seed;   /* seed of the multicolour-ordering priorities */
-    int persistent_sweeps; /* How a multicolour Gauss-Seidel sweep is launched; all three give
-                              bit-identical results. 0: one kernel launch per colour (captured in
-                              a CUDA graph). 1: one persistent cooperative launch with a bounded grid
-                              barrier between colours. 2: one persistent cooperative launch in which
-                              each group of rows starts as soon as the rows it reads from earlier
-                              colours carry their ready flags (bounded waits). Other values:
-                              MGM_ERR_INVALID_ARG. */
+    int persistent_sweeps; /* How a multicolour Gauss-Seidel sweep is launched. Modes 0-2 give
+                              bit-identical results. 0 (MGM_SWEEP_LAUNCH): one kernel launch per
+                              colour (captured in a CUDA graph). 1: one persistent cooperative launch
+                              with a bounded grid barrier between colours. 2: one persistent
+                              cooperative launch in which each group of rows starts as soon as the
+                              rows it reads from earlier colours carry their ready flags (bounded
+                              waits). 3 (MGM_SWEEP_STREAM): one cooperative launch per sweep and level
+                              in which each block owns an RCM band of rows, streams its rows' matrix
+                              entries through shared memory with bulk copies, and starts a colour
+                              once the neighbouring bands have finished the earlier colours (bounded
+                              waits); pre-smoothing and its residual share one launch. Mode 3 sums a
+                              row's products in another order than modes 0-2 (same values up to
+                              rounding). Levels with more than 128 colours keep mode 0. 4
+                              (MGM_SWEEP_AUTO): each level takes the faster of mode 0 and mode 3
+                              schedules, timed at set-up by mgm_autotune (decisions cached per
+                              level shape for the process). Other values: MGM_ERR_INVALID_ARG. */
     int constraint;  /* 0: solve L u = f. 1: surface Poisson (L = D, singular; build the operator with
                         mgm_stencil_params.poisson = 1) with the mean-zero constraint of Sec. 4.4: the
                         bordered system [L 1; 1^T 0][u; lambda] = [f; 0] (eq. (saddle_point)), coarse
@@ -105,6 +114,7 @@ typedef struct {
 } mgm_params;
 
 enum { MGM_SMOOTHER_MC = 0, MGM_SMOOTHER_LEX = 1 };
+enum { MGM_SWEEP_LAUNCH = 0, MGM_SWEEP_BARRIER = 1, MGM_SWEEP_FLAGS = 2, MGM_SWEEP_STREAM = 3, MGM_SWEEP_AUTO = 4 };
 enum { MGM_CYCLE_V = 0, MGM_CYCLE_W = 1, MGM_CYCLE_F = 2 };
 
 typedef struct {
@@ -346,6 +356,35 @@ typedef struct {
     int64_t learned_bytes;   /* its algorithmic bytes (0 when no correction is enabled) */
 } mgm_profile_info;
 mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_stream stream);
+
+/* Sweep schedule of one smoothed level (not part of the method: how the multicolour sweeps of
+ * Alg. 3's smoother are launched; the result is the same up to the order of a row's additions).
+ * kind MGM_SCHEDULE_LAUNCH: one kernel per colour (blocks, lanes, stages 0). MGM_SCHEDULE_STREAM:
+ * one cooperative launch per sweep on `blocks` blocks (1 <= blocks <= the co-resident maximum,
+ * one per SM), `lanes` in {1, 2, 4, 8} threads a row, `stages` in 2..8 shared-memory stages.
+ * ms: the autotuner's device time for the level's smoothing in one V-cycle (0 when set by hand). */
+typedef struct {
+    int kind;
+    int blocks, lanes, stages;
+    float ms;
+} mgm_sweep_config;
+enum { MGM_SCHEDULE_LAUNCH = 0, MGM_SCHEDULE_STREAM = 1 };
+
+/* Sets level j's schedule (0 <= j < p-1); the hierarchy must have persistent_sweeps 0, 3 or 4.
+ * MGM_ERR_UNSUPPORTED when a streamed schedule does not fit the level (more than 128 colours, a
+ * row larger than a stage, or more blocks than can be co-resident). Synchronises. */
+mgm_status mgm_sweep_config_set(mgm_hierarchy* H, int j, const mgm_sweep_config* cfg, mgm_stream stream);
+/* Level j's current schedule (0 <= j < p; the coarsest level reports MGM_SCHEDULE_LAUNCH). */
+mgm_status mgm_sweep_config_get(const mgm_hierarchy* H, int j, mgm_sweep_config* out);
+/* Autotuner: for every smoothed level, times the level's smoothing work of one V-cycle
+ * (pre-smoothing with its residual and post-smoothing, captured in a graph, `reps` replays after
+ * two warm-ups, CUDA events) under one launch per colour and under streamed schedules (blocks:
+ * the co-resident maximum and its halvings within [n/16384, n/64]; lanes 1, 2, 4; stages 2, and 3
+ * at the largest block count), and keeps the fastest (read back with mgm_sweep_config_get).
+ * use_cache != 0 reuses, and records, decisions per level shape (precision, smoothing counts,
+ * size, entries a row, colour count) for the life of the process. Overwrites the work vectors;
+ * synchronises. */
+mgm_status mgm_autotune(mgm_hierarchy* H, int reps, int use_cache, mgm_stream stream);
 
 /* Number of kernels this library has launched in the process (a host-side count: each launch of
  * the captured V-cycle graph adds its kernel nodes). */

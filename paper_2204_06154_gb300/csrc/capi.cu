@@ -248,6 +248,18 @@ mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_st
     });
 }
 
+mgm_status mgm_sweep_config_set(mgm_hierarchy* H, int j, const mgm_sweep_config* cfg, mgm_stream stream) {
+    return guarded([&] { sweep_config_set(H, j, cfg, S(stream)); });
+}
+
+mgm_status mgm_sweep_config_get(const mgm_hierarchy* H, int j, mgm_sweep_config* out) {
+    return guarded([&] { sweep_config_get(H, j, out); });
+}
+
+mgm_status mgm_autotune(mgm_hierarchy* H, int reps, int use_cache, mgm_stream stream) {
+    return guarded([&] { autotune(H, reps, use_cache != 0, S(stream)); });
+}
+
 int64_t mgm_kernel_launches(void) { return launches(); }
 
 mgm_status mgm_check_bounded_wait(int nblocks, int64_t spin_limit, int* status_out, mgm_stream stream) {

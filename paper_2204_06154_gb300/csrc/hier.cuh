@@ -4,10 +4,11 @@
 // operator L_j (CSR), the RCM permutation, the coarsening survivors and the interpolation I_{j+1}^j.
 // Levels that are smoothed (all but the coarsest) also carry a "solve order": rows grouped by
 // colour (RCM order inside a colour), so that one multicolour Gauss-Seidel step is a contiguous
-// row range. In that order each row stores its off-diagonal entries split as
-//   [ columns of lower colours | pad to 4 | columns of higher colours | pad to 4 ]
-// with row starts at multiples of 4 (16-byte aligned int4 / float4 loads), the diagonal kept
-// apart (value and inverse). Interpolation rows are stored as fixed-width ELL (width m) and the
+// row range. In that order the off-diagonal entries are stored in two regions of the same arrays:
+//   [ lower parts of rows 0..n-1 (columns of earlier colours) | upper parts of rows 0..n-1 ]
+// each row's part padded to a multiple of 4 entries with (own row, 0), so that every part starts
+// 16-byte aligned (int4 / float4 loads) and a range of rows' parts is one contiguous block (one
+// bulk copy). The diagonal is kept apart (value and inverse). Interpolation rows are stored as fixed-width ELL (width m) and the
 // restriction as CSR, both indexed in the solve orders of the two levels.
 #pragma once
 #include <vector>
@@ -38,11 +39,23 @@ struct Level {
     Buf<int> flag;             // per-row ready flags of the current sweep
     Buf<float> eold32;         // e before a full sweep (read for the upper-part columns)
     Buf<double> eold64;
-    Buf<int32_t> lo, mid;      // row s: lower part [lo[s], mid[s]), upper part [mid[s], lo[s+1])
+    Buf<int32_t> lo, up;       // row s: lower part [lo[s], lo[s+1]), upper part [up[s], up[s+1]); up[0] = lo[n]
     Buf<int32_t> sc;           // padded columns (solve order of this level)
     Buf<float> sv32, diag32, dinv32;
     Buf<double> sv64, diag64, dinv64;
-    int64_t snnz = 0;          // padded entry count
+    int64_t snnz = 0;          // padded entry count (both regions)
+    int64_t nl_pad = 0;        // padded entries of the lower region
+    // streamed sweeps (gs_stream.cu): B blocks, block k owns the rows whose RCM index lies in its band;
+    // split[c * (B + 1) + k] = first solve row of colour c in band k; per block, per colour, its
+    // chunks of consecutive rows: rows {r0, r1} (rrow) and entry ranges {lo[r0], lo[r1], up[r0],
+    // up[r1]} (rec); cchunk[k * (C + 1) + c] = first chunk of colour c, relative to recptr[k]
+    int sB = 0, sD = 0, sG = 0, sNS = 0, sSB = 0;  // blocks, dependency radius, lanes a row, stages, stage bytes
+    Buf<int32_t> split, recptr, cchunk;
+    Buf<int4> rec;
+    Buf<int2> rrow;
+    Buf<unsigned> prog;        // per block: colour steps completed (monotone over launches)
+    int stream = 0;            // this level's sweeps run streamed
+    float tuned_ms = 0.0f;     // the autotuner's time of the chosen schedule (0: not tuned)
     int64_t nlow = 0, nupp = 0; // unpadded lower / upper off-diagonal counts
     // transfers in solve orders
     int pw = 0;                // ELL width of the interpolation (= m)
@@ -120,6 +133,8 @@ namespace mgm {
 void vcycle_core(mgm_hierarchy* H, cudaStream_t s);          // b_0 -> e_0 (graph if captured)
 void vcycle_plain(mgm_hierarchy* H, cudaStream_t s);         // the same without the learned correction
 void vcycle_prepare(mgm_hierarchy* H);                       // capture the graph
+void invalidate_graphs(mgm_hierarchy* H);
+float time_level_smoothing(mgm_hierarchy* H, int j, int reps, cudaStream_t s);
 void load_input(mgm_hierarchy* H, const void* src, int src_dtype, const int32_t* gather, cudaStream_t s);
 void store_output(mgm_hierarchy* H, void* dst, int dst_dtype, const int32_t* scatter, cudaStream_t s);
 void alloc_work(mgm_hierarchy* H);
@@ -130,6 +145,15 @@ void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStrea
 void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
 void solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp, mgm_solve_info* info,
            cudaStream_t s);
+// gs_stream.cu
+bool stream_prepare(mgm_hierarchy* H, Level& L, int B, int G, int NS, cudaStream_t s);
+int stream_blocks_limit(mgm_hierarchy* H);
+template <class T>
+void stream_sweep(mgm_hierarchy* H, Level& L, int mode, bool resid, cudaStream_t s);
+void stream_reset(mgm_hierarchy* H, cudaStream_t s);
+void sweep_config_set(mgm_hierarchy* H, int j, const mgm_sweep_config* cfg, cudaStream_t s);
+void sweep_config_get(const mgm_hierarchy* H, int j, mgm_sweep_config* out);
+void autotune(mgm_hierarchy* H, int reps, bool use_cache, cudaStream_t s);
 // learned.cu
 void learned_correct(mgm_hierarchy* H, cudaStream_t s);     // e_0 += correction from s_0 = b_0 - L_0 e_0
 // multi.cu

@@ -249,11 +249,16 @@ __global__ void colour_bounds_k(const int32_t* off, int nc, int nblocks, int64_t
 
 __device__ __forceinline__ int32_t pad4(int32_t x) { return (x + 3) & ~3; }
 
+__global__ void add_i32_k(int32_t* a, int32_t v, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] += v;
+}
+
 // lengths of the split rows; err bit 1: same colour off-diagonal, bit 2: missing/zero diagonal.
 // One warp per row (lanes over its entries); the block sums its rows' counts before one atomic.
 __global__ void __launch_bounds__(256) split_len_k(const int32_t* rp, const int32_t* ci, const double* v,
                                                    const int32_t* col, const int32_t* ord, int64_t n, int single,
-                                                   int32_t* len, int32_t* nlo, int* err, unsigned long long* tot) {
+                                                   int32_t* lenl, int32_t* lenu, int* err, unsigned long long* tot) {
     __shared__ unsigned long long bt[2];
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -278,8 +283,8 @@ __global__ void __launch_bounds__(256) split_len_k(const int32_t* rp, const int3
         if (lane == 0) {
             if (same) atomicOr(err, 1);
             if (!diag) atomicOr(err, 2);
-            len[s] = pad4(nl) + pad4(nu);
-            nlo[s] = pad4(nl);
+            lenl[s] = pad4(nl);
+            lenu[s] = pad4(nu);
             atomicAdd(&bt[0], (unsigned long long)nl);
             atomicAdd(&bt[1], (unsigned long long)nu);
         }
@@ -288,14 +293,15 @@ __global__ void __launch_bounds__(256) split_len_k(const int32_t* rp, const int3
     if (threadIdx.x < 2 && bt[threadIdx.x]) atomicAdd(&tot[threadIdx.x], bt[threadIdx.x]);
 }
 
-// Rows in solve order: the lower part (earlier colours) then the upper part, each sorted by
-// solve-order column and padded to a multiple of 4 with (own row, 0). One warp per row; the
-// entries are staged in shared memory and placed by rank (rows of up to SPLIT_MAX entries; longer
-// rows take the thread path below).
+// Rows in solve order, split in two regions of the same arrays: the lower parts (columns of earlier
+// colours) of all rows, then the upper parts of all rows; each part sorted by solve-order column and
+// padded to a multiple of 4 with (own row, 0). Row s: lower [lo[s], lo[s+1]), upper [up[s],
+// up[s+1]). One warp per row; the entries are staged in shared memory and placed by rank (rows of up
+// to SPLIT_MAX entries; longer rows take the thread path below).
 constexpr int SPLIT_WARPS = 4, SPLIT_MAX = 256;
 __global__ void __launch_bounds__(SPLIT_WARPS * 32) split_fill_k(
     const int32_t* rp, const int32_t* ci, const double* v, const int32_t* col, const int32_t* ord, const int32_t* inv,
-    int64_t n, int single, const int32_t* lo, int32_t* mid, int32_t* sc, double* sv64, float* sv32, double* diag64,
+    int64_t n, int single, const int32_t* lo, const int32_t* up, int32_t* sc, double* sv64, float* sv32, double* diag64,
     double* dinv64, float* diag32, float* dinv32, int* longrows) {
     __shared__ unsigned long long key[SPLIT_WARPS][SPLIT_MAX];  // (upper?, solve column) of each entry
     __shared__ double val[SPLIT_WARPS][SPLIT_MAX];
@@ -327,7 +333,7 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32) split_fill_k(
     nl = warp_sum_i(nl);
     for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);  // one lane holds it, the others 0
     __syncwarp();
-    const int32_t len = e - b, q0 = lo[s], qm = q0 + pad4(nl);
+    const int32_t len = e - b, q0 = lo[s], qm = up[s];
     for (int32_t t = lane; t < len; t += 32) {
         const unsigned long long k = key[w][t];
         if (k == ~0ull) continue;
@@ -340,11 +346,10 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32) split_fill_k(
         sv32[pos] = (float)val[w][t];
     }
     const int32_t nu = len - nl - 1 >= 0 ? len - nl - 1 : 0;
-    const int32_t qe = qm + pad4(nu);
-    for (int32_t t = q0 + nl + lane; t < qm; t += 32) { sc[t] = (int32_t)s; sv64[t] = 0.0; sv32[t] = 0.0f; }
+    const int32_t ql = q0 + pad4(nl), qe = qm + pad4(nu);
+    for (int32_t t = q0 + nl + lane; t < ql; t += 32) { sc[t] = (int32_t)s; sv64[t] = 0.0; sv32[t] = 0.0f; }
     for (int32_t t = qm + nu + lane; t < qe; t += 32) { sc[t] = (int32_t)s; sv64[t] = 0.0; sv32[t] = 0.0f; }
     if (lane == 0) {
-        mid[s] = qm;
         diag64[s] = d;
         dinv64[s] = 1.0 / d;
         diag32[s] = (float)d;
@@ -355,18 +360,17 @@ __global__ void __launch_bounds__(SPLIT_WARPS * 32) split_fill_k(
 // rows longer than SPLIT_MAX: one thread per row, insertion into place
 __global__ void split_fill_long_k(const int32_t* rp, const int32_t* ci, const double* v, const int32_t* col,
                                   const int32_t* ord, const int32_t* inv, int64_t n, int single, const int32_t* lo,
-                                  int32_t* mid, int32_t* sc, double* sv64, float* sv32, double* diag64, double* dinv64,
-                                  float* diag32, float* dinv32) {
+                                  const int32_t* up, int32_t* sc, double* sv64, float* sv32, double* diag64,
+                                  double* dinv64, float* diag32, float* dinv32) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int32_t r = ord[s];
     if (rp[r + 1] - rp[r] <= SPLIT_MAX) return;
     int32_t cr = single ? 0 : col[r];
-    int32_t b = lo[s];
-    int32_t q = b;
     double d = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-        int32_t start = q;
+        const int32_t start = pass == 0 ? lo[s] : up[s];
+        int32_t q = start;
         for (int32_t p = rp[r]; p < rp[r + 1]; ++p) {
             int32_t j = ci[p];
             if (j == r) { d = v[p]; continue; }
@@ -379,10 +383,9 @@ __global__ void split_fill_long_k(const int32_t* rp, const int32_t* ci, const do
             sc[t] = js;
             sv64[t] = x;
         }
-        while ((q - b) & 3) { sc[q] = (int32_t)s; sv64[q] = 0.0; ++q; }
-        if (pass == 0) mid[s] = q;
+        while ((q - start) & 3) { sc[q] = (int32_t)s; sv64[q] = 0.0; ++q; }
+        for (int32_t t = start; t < q; ++t) sv32[t] = (float)sv64[t];
     }
-    for (int32_t t = b; t < q; ++t) sv32[t] = (float)sv64[t];
     diag64[s] = d;
     dinv64[s] = 1.0 / d;
     diag32[s] = (float)d;
@@ -416,13 +419,13 @@ static void build_solve_layout(Level& L, bool single, cudaStream_t s, bool lex =
         to_host(L.cptr.data(), cp.get(), nc + 1, s);
     }
     invert_perm(L.ord.get(), L.inv.get(), n, s);
-    Temp<int32_t> len(n + 1, s), nlo(n, s);
+    Temp<int32_t> lenl(n + 1, s), lenu(n + 1, s);
     Temp<int> err(1, s);
     Temp<unsigned long long> tot(2, s);
     CK(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
     CK(cudaMemsetAsync(tot.get(), 0, 2 * sizeof(unsigned long long), s));
     split_len_k<<<grid_for(n, 8), 256, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(), n,
-                                               single ? 1 : 0, len.get(), nlo.get(), err.get(), tot.get());
+                                               single ? 1 : 0, lenl.get(), lenu.get(), err.get(), tot.get());
     CK_LAUNCH();
     unsigned long long th[2];
     to_host(th, tot.get(), 2, s);
@@ -432,9 +435,14 @@ static void build_solve_layout(Level& L, bool single, cudaStream_t s, bool lex =
     if (e & 1) fail(MGM_ERR_INVALID_ARG, "colouring is not valid for the operator pattern");
     if (e & 2) fail(MGM_ERR_BREAKDOWN, "a level operator has a zero or missing diagonal entry");
     L.lo.alloc(n + 1);
-    L.mid.alloc(n);
-    exclusive_scan_i32(len.get(), L.lo.get(), n, s);
-    L.snnz = csr_nnz(L.lo.get(), n, s);
+    L.up.alloc(n + 1);
+    exclusive_scan_i32(lenl.get(), L.lo.get(), n, s);
+    exclusive_scan_i32(lenu.get(), L.up.get(), n, s);
+    L.nl_pad = csr_nnz(L.lo.get(), n, s);
+    L.snnz = L.nl_pad + csr_nnz(L.up.get(), n, s);
+    REQUIRE(L.snnz <= INT32_MAX, "level operator too large for 32-bit entry offsets");
+    add_i32_k<<<grid_for(n + 1, 256), 256, 0, s>>>(L.up.get(), (int32_t)L.nl_pad, n + 1);
+    CK_LAUNCH();
     L.sc.alloc(std::max<int64_t>(L.snnz, 4));
     L.sv64.alloc(std::max<int64_t>(L.snnz, 4));
     L.sv32.alloc(std::max<int64_t>(L.snnz, 4));
@@ -443,12 +451,12 @@ static void build_solve_layout(Level& L, bool single, cudaStream_t s, bool lex =
     CK(cudaMemsetAsync(longrows.get(), 0, sizeof(int), s));
     split_fill_k<<<grid_for(n, SPLIT_WARPS), SPLIT_WARPS * 32, 0, s>>>(
         L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(), L.inv.get(), n, single ? 1 : 0, L.lo.get(),
-        L.mid.get(), L.sc.get(), L.sv64.get(), L.sv32.get(), L.diag64.get(), L.dinv64.get(), L.diag32.get(),
+        L.up.get(), L.sc.get(), L.sv64.get(), L.sv32.get(), L.diag64.get(), L.dinv64.get(), L.diag32.get(),
         L.dinv32.get(), longrows.get());
     CK_LAUNCH();
     if (read1(longrows.get(), s) > 0) {
         split_fill_long_k<<<grid_for(n, 128), 128, 0, s>>>(L.rp.get(), L.ci.get(), L.v.get(), L.colour.get(), L.ord.get(),
-                                                           L.inv.get(), n, single ? 1 : 0, L.lo.get(), L.mid.get(),
+                                                           L.inv.get(), n, single ? 1 : 0, L.lo.get(), L.up.get(),
                                                            L.sc.get(), L.sv64.get(), L.sv32.get(), L.diag64.get(),
                                                            L.dinv64.get(), L.diag32.get(), L.dinv32.get());
         CK_LAUNCH();
@@ -558,11 +566,11 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     H->nu2 = prm->nu2;
     H->m = prm->m;
     H->seed = prm->seed;
-    REQUIRE(prm->persistent_sweeps >= 0 && prm->persistent_sweeps <= 2, "persistent_sweeps must be 0, 1 or 2");
+    REQUIRE(prm->persistent_sweeps >= 0 && prm->persistent_sweeps <= 4, "persistent_sweeps must be 0 to 4");
     REQUIRE(prm->smoother == MGM_SMOOTHER_MC || prm->smoother == MGM_SMOOTHER_LEX, "unknown smoother");
     const bool lex = prm->smoother == MGM_SMOOTHER_LEX;
     H->sweep_mode = lex ? 2 : prm->persistent_sweeps;  // lexicographic: one row per group, flag-driven
-    H->persistent = H->sweep_mode != 0;
+    H->persistent = H->sweep_mode != 0;  // error word checked after each solve
     REQUIRE(prm->constraint == 0 || prm->constraint == 1, "constraint must be 0 or 1");
     H->bordered = prm->constraint == 1;
     REQUIRE(prm->cycle >= MGM_CYCLE_V && prm->cycle <= MGM_CYCLE_F, "unknown cycle type");
@@ -698,12 +706,24 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     compose_k<<<grid_for(N, 256), 256, 0, s>>>(H->lv[0].perm.get(), H->lv[0].ord.get(), N, H->ord_caller.get());
     CK_LAUNCH();
     alloc_work(H.get());
+    if (H->sweep_mode == MGM_SWEEP_STREAM) {  // streamed sweeps on every level they fit
+        const int maxb = stream_blocks_limit(H.get());
+        for (int j = 0; j + 1 < p; ++j) {
+            Level& L = H->lv[j];
+            const int B = (int)std::max<int64_t>(1, std::min<int64_t>(maxb, (L.n + 2047) / 2048));
+            stream_prepare(H.get(), L, B, 2, 2, s);
+        }
+        tr.mark("stream-tables", p - 1);
+    } else if (H->sweep_mode == MGM_SWEEP_AUTO) {  // the faster schedule per level, timed
+        autotune(H.get(), 5, true, s);
+        tr.mark("autotune", p - 1);
+    }
     CK(cudaStreamSynchronize(s));
     int64_t bytes = H->Ainv.bytes() + H->ord_caller.bytes();
     for (auto& L : H->lv)
         bytes += L.X.bytes() + L.rp.bytes() + L.ci.bytes() + L.v.bytes() + L.perm.bytes() + L.keep.bytes() + L.P_rp.bytes() +
                  L.P_ci.bytes() + L.P_v.bytes() + L.colour.bytes() + L.ord.bytes() + L.inv.bytes() + L.lo.bytes() +
-                 L.mid.bytes() + L.sc.bytes() + L.sv32.bytes() + L.sv64.bytes() + 3 * L.diag64.bytes() + 3 * L.diag32.bytes() +
+                 L.up.bytes() + L.sc.bytes() + L.sv32.bytes() + L.sv64.bytes() + 3 * L.diag64.bytes() + 3 * L.diag32.bytes() +
                  L.pc.bytes() + L.pv32.bytes() + L.pv64.bytes() + L.r_rp.bytes() + L.r_ci.bytes() + L.r_v32.bytes() +
                  L.r_v64.bytes() + L.b32.bytes() * 3 + L.b64.bytes() * 3;
     H->device_bytes = bytes;

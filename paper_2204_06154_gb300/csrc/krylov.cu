@@ -24,48 +24,54 @@ constexpr int KG = 8;            // lanes per row in the FP64 operator
 constexpr int KBLOCK = 256;
 constexpr int DOT_BLOCKS = 304;  // 2 per SM on 152 SMs
 
-// y = f - L x (RESID) or y = L x, L in solve order (split rows, diagonal apart)
+// acc += the products of entries [b, e) of the FP64 operator with x, lane gl of KG: two chunks of 4
+// entries per lane and pass, both loaded before either is used, so that a warp has all of its rows'
+// matrix loads in flight at once; the additions keep the order of a plain chunk-by-chunk loop
+__device__ __forceinline__ double range_dot64(const int32_t* __restrict__ sc, const double* __restrict__ sv,
+                                              const double* __restrict__ x, int32_t b, int32_t e, int gl, double acc) {
+#pragma unroll 1
+    for (int32_t p = b + 4 * gl; p < e; p += 8 * KG) {
+        const bool two = p + 4 * KG < e;
+        const int4 c0 = __ldcs(reinterpret_cast<const int4*>(sc + p));
+        const double2 v0 = __ldcs(reinterpret_cast<const double2*>(sv + p));
+        const double2 v1 = __ldcs(reinterpret_cast<const double2*>(sv + p + 2));
+        int4 c1 = make_int4(0, 0, 0, 0);
+        double2 v2 = make_double2(0.0, 0.0), v3 = v2;
+        if (two) {
+            c1 = __ldcs(reinterpret_cast<const int4*>(sc + p + 4 * KG));
+            v2 = __ldcs(reinterpret_cast<const double2*>(sv + p + 4 * KG));
+            v3 = __ldcs(reinterpret_cast<const double2*>(sv + p + 4 * KG + 2));
+        }
+        const double x0 = x[c0.x], x1 = x[c0.y], x2 = x[c0.z], x3 = x[c0.w];
+        double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+        if (two) { y0 = x[c1.x]; y1 = x[c1.y]; y2 = x[c1.z]; y3 = x[c1.w]; }
+        acc = fma(v0.x, x0, acc);
+        acc = fma(v0.y, x1, acc);
+        acc = fma(v1.x, x2, acc);
+        acc = fma(v1.y, x3, acc);
+        if (two) {
+            acc = fma(v2.x, y0, acc);
+            acc = fma(v2.y, y1, acc);
+            acc = fma(v3.x, y2, acc);
+            acc = fma(v3.y, y3, acc);
+        }
+    }
+    return acc;
+}
+
+// y = f - L x (RESID) or y = L x, L in solve order (lower and upper parts, diagonal apart)
 template <bool RESID>
-__global__ void __launch_bounds__(KBLOCK) spmv64_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ sc,
-                                                   const double* __restrict__ sv, const double* __restrict__ diag,
-                                                   const double* __restrict__ x, const double* __restrict__ f, double* y,
-                                                   int64_t n) {
+__global__ void __launch_bounds__(KBLOCK) spmv64_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ up,
+                                                   const int32_t* __restrict__ sc, const double* __restrict__ sv,
+                                                   const double* __restrict__ diag, const double* __restrict__ x,
+                                                   const double* __restrict__ f, double* y, int64_t n) {
     const int64_t t = (int64_t)blockIdx.x * KBLOCK + threadIdx.x;
     const int64_t row = t / KG;
     const int gl = (int)(t & (KG - 1));
     double acc = 0.0;
     if (row < n) {
-        const int32_t b = lo[row], e = lo[row + 1];
-        // two chunks of 4 entries per lane and pass, both loaded before either is used, so that a
-        // warp has all of its rows' matrix loads in flight at once (rows of up to 64 entries take
-        // one pass); the additions keep the order of a plain chunk-by-chunk loop
-#pragma unroll 1
-        for (int32_t p = b + 4 * gl; p < e; p += 8 * KG) {
-            const bool two = p + 4 * KG < e;
-            const int4 c0 = __ldcs(reinterpret_cast<const int4*>(sc + p));
-            const double2 v0 = __ldcs(reinterpret_cast<const double2*>(sv + p));
-            const double2 v1 = __ldcs(reinterpret_cast<const double2*>(sv + p + 2));
-            int4 c1 = make_int4(0, 0, 0, 0);
-            double2 v2 = make_double2(0.0, 0.0), v3 = v2;
-            if (two) {
-                c1 = __ldcs(reinterpret_cast<const int4*>(sc + p + 4 * KG));
-                v2 = __ldcs(reinterpret_cast<const double2*>(sv + p + 4 * KG));
-                v3 = __ldcs(reinterpret_cast<const double2*>(sv + p + 4 * KG + 2));
-            }
-            const double x0 = x[c0.x], x1 = x[c0.y], x2 = x[c0.z], x3 = x[c0.w];
-            double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
-            if (two) { y0 = x[c1.x]; y1 = x[c1.y]; y2 = x[c1.z]; y3 = x[c1.w]; }
-            acc = fma(v0.x, x0, acc);
-            acc = fma(v0.y, x1, acc);
-            acc = fma(v1.x, x2, acc);
-            acc = fma(v1.y, x3, acc);
-            if (two) {
-                acc = fma(v2.x, y0, acc);
-                acc = fma(v2.y, y1, acc);
-                acc = fma(v3.x, y2, acc);
-                acc = fma(v3.y, y3, acc);
-            }
-        }
+        acc = range_dot64(sc, sv, x, lo[row], lo[row + 1], gl, acc);
+        acc = range_dot64(sc, sv, x, up[row], up[row + 1], gl, acc);
     }
     for (int o = KG / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (row < n && gl == 0) {
@@ -219,7 +225,7 @@ struct Ops {
         } else {
             xd = x;
         }
-        spmv64_k<RESID><<<grid_for(n * KG, KBLOCK), KBLOCK, 0, s>>>(L.lo.get(), L.sc.get(), L.sv64.get(), L.diag64.get(),
+        spmv64_k<RESID><<<grid_for(n * KG, KBLOCK), KBLOCK, 0, s>>>(L.lo.get(), L.up.get(), L.sc.get(), L.sv64.get(), L.diag64.get(),
                                                                    xd, f, y, n);
         CK_LAUNCH();
     }

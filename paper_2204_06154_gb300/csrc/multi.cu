@@ -30,12 +30,11 @@ __device__ __forceinline__ void load_row(const T* x, int32_t c, T* out) {
     for (int r = 0; r < R; ++r) out[r] = x[(int64_t)c * R + r];
 }
 
-// acc[r] = sum_p v_p x[c_p][r] over [beg, end) (multiples of 4), MG lanes per row
+// acc[r] += this lane's products v_p x[c_p][r] over [beg, end) (multiples of 4), MG lanes per row
+// (the caller sums the lanes)
 template <class T, int R>
 __device__ __forceinline__ void row_sum_R(const int32_t* __restrict__ sc, const T* __restrict__ sv, int32_t beg,
                                           int32_t end, const T* x, int gl, T* acc) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = T(0);
     for (int32_t p = beg + 4 * gl; p < end; p += 4 * MG) {
         int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
         T v[4] = {__ldg(sv + p), __ldg(sv + p + 1), __ldg(sv + p + 2), __ldg(sv + p + 3)};
@@ -48,14 +47,11 @@ __device__ __forceinline__ void row_sum_R(const int32_t* __restrict__ sc, const 
             for (int r = 0; r < R; ++r) acc[r] = fma(v[q], xr[r], acc[r]);
         }
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-        for (int o = MG / 2; o; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
 }
 
 // MODE 0: first sweep from zero (lower part); 1: full sweep; 2: s = -U e; 3: s = b - A e
 template <int MODE, class T, int R>
-__global__ void __launch_bounds__(MBLOCK) rowR_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ mid,
+__global__ void __launch_bounds__(MBLOCK) rowR_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ up,
                                                  const int32_t* __restrict__ sc, const T* __restrict__ sv,
                                                  const T* __restrict__ dv, const T* __restrict__ b, T* e, T* s, int32_t r0,
                                                  int32_t r1) {
@@ -64,13 +60,18 @@ __global__ void __launch_bounds__(MBLOCK) rowR_k(const int32_t* __restrict__ lo,
     const int gl = t & (MG - 1);
     const bool act = row < r1;
     T acc[R];
-    int32_t beg = 0, end = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    int32_t b0 = 0, e0 = 0, b1 = 0, e1 = 0;  // lower part, then upper part
     if (act) {
-        if (MODE == 0) { beg = lo[row]; end = mid[row]; }
-        else if (MODE == 2) { beg = mid[row]; end = lo[row + 1]; }
-        else { beg = lo[row]; end = lo[row + 1]; }
+        if (MODE != 2) { b0 = lo[row]; e0 = lo[row + 1]; }
+        if (MODE != 0) { b1 = up[row]; e1 = up[row + 1]; }
     }
-    row_sum_R<T, R>(sc, sv, beg, end, e, gl, acc);
+    row_sum_R<T, R>(sc, sv, b0, e0, e, gl, acc);
+    row_sum_R<T, R>(sc, sv, b1, e1, e, gl, acc);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        for (int o = MG / 2; o; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
     if (act && gl < R) {
         const int64_t o = (int64_t)row * R + gl;
         T a = acc[0];
@@ -151,7 +152,8 @@ __global__ void castR_k(const TI* a, TO* b, int64_t m) {
 
 // ------------------------------ outer FP64 kernels --------------------------------------------
 template <bool RESID, class TX, int R>
-__global__ void __launch_bounds__(MBLOCK) spmvR_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ sc,
+__global__ void __launch_bounds__(MBLOCK) spmvR_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ up,
+                                                  const int32_t* __restrict__ sc,
                                                   const double* __restrict__ sv, const double* __restrict__ diag,
                                                   const TX* __restrict__ x, const double* __restrict__ f, double* y,
                                                   int64_t n) {
@@ -162,15 +164,17 @@ __global__ void __launch_bounds__(MBLOCK) spmvR_k(const int32_t* __restrict__ lo
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0;
     if (row < n) {
-        const int32_t b = lo[row], e = lo[row + 1];
-        for (int32_t p = b + 4 * gl; p < e; p += 4 * MG) {
-            int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
-            double v[4] = {__ldg(sv + p), __ldg(sv + p + 1), __ldg(sv + p + 2), __ldg(sv + p + 3)};
-            int cc[4] = {c.x, c.y, c.z, c.w};
+        for (int part = 0; part < 2; ++part) {  // lower part, then upper part
+            const int32_t b = part ? up[row] : lo[row], e = part ? up[row + 1] : lo[row + 1];
+            for (int32_t p = b + 4 * gl; p < e; p += 4 * MG) {
+                int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
+                double v[4] = {__ldg(sv + p), __ldg(sv + p + 1), __ldg(sv + p + 2), __ldg(sv + p + 3)};
+                int cc[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] = fma(v[q], (double)x[(int64_t)cc[q] * R + r], acc[r]);
+                    for (int r = 0; r < R; ++r) acc[r] = fma(v[q], (double)x[(int64_t)cc[q] * R + r], acc[r]);
+            }
         }
     }
 #pragma unroll
@@ -327,7 +331,7 @@ static void rows_R(MultiWork& W, Level& L, int j, int32_t r0, int32_t r1, cudaSt
     if (r1 <= r0) return;
     const T* dv = MODE == 3 ? WV<T>::diag(L) : WV<T>::dinv(L);
     rowR_k<MODE, T, R><<<grid_for((int64_t)(r1 - r0) * MG, MBLOCK), MBLOCK, 0, s>>>(
-        L.lo.get(), L.mid.get(), L.sc.get(), WV<T>::sv(L), dv, WV<T>::b(W, j), WV<T>::e(W, j), WV<T>::s(W, j), r0, r1);
+        L.lo.get(), L.up.get(), L.sc.get(), WV<T>::sv(L), dv, WV<T>::b(W, j), WV<T>::e(W, j), WV<T>::s(W, j), r0, r1);
     CK_LAUNCH();
 }
 
@@ -404,9 +408,9 @@ static void solve_multi_t(mgm_hierarchy* H, int nrhs, const double* F, double* U
     };
     auto spmv = [&](const auto* x, const double* f, double* y, bool resid) {
         using TX = std::remove_const_t<std::remove_pointer_t<decltype(x)>>;
-        if (resid) spmvR_k<true, TX, R><<<grid_for(n * MG, MBLOCK), MBLOCK, 0, s>>>(L0.lo.get(), L0.sc.get(), L0.sv64.get(),
+        if (resid) spmvR_k<true, TX, R><<<grid_for(n * MG, MBLOCK), MBLOCK, 0, s>>>(L0.lo.get(), L0.up.get(), L0.sc.get(), L0.sv64.get(),
                                                                                   L0.diag64.get(), x, f, y, n);
-        else spmvR_k<false, TX, R><<<grid_for(n * MG, MBLOCK), MBLOCK, 0, s>>>(L0.lo.get(), L0.sc.get(), L0.sv64.get(),
+        else spmvR_k<false, TX, R><<<grid_for(n * MG, MBLOCK), MBLOCK, 0, s>>>(L0.lo.get(), L0.up.get(), L0.sc.get(), L0.sv64.get(),
                                                                              L0.diag64.get(), x, f, y, n);
         CK_LAUNCH();
     };

@@ -28,8 +28,7 @@ __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 // same sums with L2-coherent loads of x (ld.global.cg): inside one persistent launch, x is written
 // by other blocks between grid barriers, so it must not be served from a stale L1 line
 __device__ __forceinline__ float row_sum_cg(const int32_t* __restrict__ sc, const float* __restrict__ sv, int32_t beg,
-                                            int32_t end, const float* x, int gl) {
-    float acc = 0.0f;
+                                            int32_t end, const float* x, int gl, float acc) {
     for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {
         int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
         float4 v = __ldg(reinterpret_cast<const float4*>(sv + p));
@@ -41,8 +40,7 @@ __device__ __forceinline__ float row_sum_cg(const int32_t* __restrict__ sc, cons
     return acc;
 }
 __device__ __forceinline__ double row_sum_cg(const int32_t* __restrict__ sc, const double* __restrict__ sv, int32_t beg,
-                                             int32_t end, const double* x, int gl) {
-    double acc = 0.0;
+                                             int32_t end, const double* x, int gl, double acc) {
     for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {
         int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
         double2 v0 = __ldg(reinterpret_cast<const double2*>(sv + p));
@@ -146,8 +144,9 @@ __device__ __forceinline__ double fma_t(double a, double b, double c) { return f
 // MODE 1: e = (b - offdiag e) dinv (full sweep)
 // MODE 2: s = -upper e             (residual after a first sweep from zero)
 // MODE 3: s = b - diag e - offdiag e
+// A row's products are summed lane-strided over its lower part, then over its upper part.
 template <int MODE, class T>
-__global__ void __launch_bounds__(VBLOCK) row_kernel(const int32_t* __restrict__ lo, const int32_t* __restrict__ mid,
+__global__ void __launch_bounds__(VBLOCK) row_kernel(const int32_t* __restrict__ lo, const int32_t* __restrict__ up,
                                                      const int32_t* __restrict__ sc, const T* __restrict__ sv,
                                                      const T* __restrict__ dv, const T* __restrict__ b, T* e, T* s,
                                                      int32_t r0, int32_t r1) {
@@ -157,21 +156,21 @@ __global__ void __launch_bounds__(VBLOCK) row_kernel(const int32_t* __restrict__
     const int32_t row = r0 + t / G;
     const int gl = t & (G - 1);
     const bool act = row < r1;
-    int32_t beg = 0, end = 0;
+    // ranges [b0, e0) then [b1, e1)
+    int32_t b0 = 0, e0 = 0, b1 = 0, e1 = 0;
     if (act) {
-        if (MODE == 0) { beg = ld_stream(lo + row, pol); end = ld_stream(mid + row, pol); }
-        else if (MODE == 2) { beg = ld_stream(mid + row, pol); end = ld_stream(lo + row + 1, pol); }
-        else { beg = ld_stream(lo + row, pol); end = ld_stream(lo + row + 1, pol); }
+        if (MODE == 2) { b0 = ld_stream(up + row, pol); e0 = ld_stream(up + row + 1, pol); }
+        else { b0 = ld_stream(lo + row, pol); e0 = ld_stream(lo + row + 1, pol); }
+        if (MODE == 1 || MODE == 3) { b1 = ld_stream(up + row, pol); e1 = ld_stream(up + row + 1, pol); }
     }
-    // the lane's first two quads of columns and values (static data) before the wait
-    const int32_t p0 = beg + 4 * gl, p1 = p0 + 4 * G;
-    const bool h0 = p0 < end, h1 = p1 < end;
+    // the lane's first quad of columns and values of each range (static data) before the wait
+    const int32_t p0 = b0 + 4 * gl, p1 = b1 + 4 * gl;
+    const bool h0 = p0 < e0, h1 = p1 < e1;
     int4 c0 = make_int4(0, 0, 0, 0), c1 = make_int4(0, 0, 0, 0);
     Quad<T> v0{}, v1{};
     if (h0) { c0 = ld_stream(reinterpret_cast<const int4*>(sc + p0), pol); v0 = Quad<T>::load(sv + p0, pol); }
     if (h1) { c1 = ld_stream(reinterpret_cast<const int4*>(sc + p1), pol); v1 = Quad<T>::load(sv + p1, pol); }
     pdl_wait();
-    // the products in storage order: quad p0, quad p1, then the rest
     T acc = T(0);
     if (h0) {
         acc = fma_t(v0.x, e[c0.x], acc);
@@ -179,13 +178,21 @@ __global__ void __launch_bounds__(VBLOCK) row_kernel(const int32_t* __restrict__
         acc = fma_t(v0.z, e[c0.z], acc);
         acc = fma_t(v0.w, e[c0.w], acc);
     }
+    for (int32_t p = p0 + 4 * G; p < e0; p += 4 * G) {
+        const int4 c = ld_stream(reinterpret_cast<const int4*>(sc + p), pol);
+        const Quad<T> v = Quad<T>::load(sv + p, pol);
+        acc = fma_t(v.x, e[c.x], acc);
+        acc = fma_t(v.y, e[c.y], acc);
+        acc = fma_t(v.z, e[c.z], acc);
+        acc = fma_t(v.w, e[c.w], acc);
+    }
     if (h1) {
         acc = fma_t(v1.x, e[c1.x], acc);
         acc = fma_t(v1.y, e[c1.y], acc);
         acc = fma_t(v1.z, e[c1.z], acc);
         acc = fma_t(v1.w, e[c1.w], acc);
     }
-    for (int32_t p = p1 + 4 * G; p < end; p += 4 * G) {
+    for (int32_t p = p1 + 4 * G; p < e1; p += 4 * G) {
         const int4 c = ld_stream(reinterpret_cast<const int4*>(sc + p), pol);
         const Quad<T> v = Quad<T>::load(sv + p, pol);
         acc = fma_t(v.x, e[c.x], acc);
@@ -211,7 +218,7 @@ constexpr unsigned long long PS_SPIN_LIMIT = 4000000ull;
 
 
 template <int MODE, class T>
-__global__ void __launch_bounds__(PS_THREADS) psweep_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ mid,
+__global__ void __launch_bounds__(PS_THREADS) psweep_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ up,
                                                        const int32_t* __restrict__ sc, const T* __restrict__ sv,
                                                        const T* __restrict__ dinv, const T* __restrict__ b, T* e,
                                                        const int32_t* __restrict__ cptr, int ncolors, unsigned* bar,
@@ -227,9 +234,8 @@ __global__ void __launch_bounds__(PS_THREADS) psweep_k(const int32_t* __restrict
             const bool act = row < r1;
             T acc = T(0);
             if (act) {
-                const int32_t beg = lo[row];
-                const int32_t end = MODE == 0 ? mid[row] : lo[row + 1];
-                acc = row_sum_cg(sc, sv, beg, end, e, gl);
+                acc = row_sum_cg(sc, sv, lo[row], lo[row + 1], e, gl, acc);
+                if (MODE != 0) acc = row_sum_cg(sc, sv, up[row], up[row + 1], e, gl, acc);
             }
             acc = group_reduce(acc);
             if (act && gl == 0) e[row] = (b[row] - acc) * dinv[row];
@@ -267,7 +273,7 @@ __device__ __forceinline__ void st_release_i32(int* p, int v) {
 
 
 template <int MODE, class T>
-__global__ void __launch_bounds__(DS_THREADS) dsweep_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ mid,
+__global__ void __launch_bounds__(DS_THREADS) dsweep_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ up,
                                                        const int32_t* __restrict__ sc, const T* __restrict__ sv,
                                                        const T* __restrict__ dinv, const T* __restrict__ b, T* e,
                                                        const T* __restrict__ eold, const int32_t* __restrict__ gptr,
@@ -278,11 +284,11 @@ __global__ void __launch_bounds__(DS_THREADS) dsweep_k(const int32_t* __restrict
     for (int64_t g = (int64_t)blockIdx.x * DS_WARPS + (threadIdx.x >> 5); g < ngroups; g += W) {
         const int32_t row = gptr[g] + lane / G;
         const bool act = row < gptr[g + 1];
-        int32_t beg = 0, m = 0, end = 0;
+        int32_t beg = 0, m = 0, ub = 0, ue = 0;
         if (act) {
             beg = lo[row];
-            m = mid[row];
-            end = MODE == 0 ? m : lo[row + 1];
+            m = lo[row + 1];
+            if (MODE != 0) { ub = up[row]; ue = up[row + 1]; }
         }
         unsigned long long it = 0;
         for (;;) {  // every lower-part column final? (padding entries point at the row itself)
@@ -302,20 +308,21 @@ __global__ void __launch_bounds__(DS_THREADS) dsweep_k(const int32_t* __restrict
             __nanosleep(64);
         }
         T acc = T(0);
-        for (int32_t p = beg + 4 * gl; p < end; p += 4 * G) {  // the order of row_kernel
+        for (int32_t p = beg + 4 * gl; p < m; p += 4 * G) {  // the order of row_kernel
             const int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
             const Quad<T> v = Quad<T>::load(sv + p);
-            if (p < m) {
-                acc = fma_t(v.x, __ldcg(e + c.x), acc);
-                acc = fma_t(v.y, __ldcg(e + c.y), acc);
-                acc = fma_t(v.z, __ldcg(e + c.z), acc);
-                acc = fma_t(v.w, __ldcg(e + c.w), acc);
-            } else {
-                acc = fma_t(v.x, __ldg(eold + c.x), acc);
-                acc = fma_t(v.y, __ldg(eold + c.y), acc);
-                acc = fma_t(v.z, __ldg(eold + c.z), acc);
-                acc = fma_t(v.w, __ldg(eold + c.w), acc);
-            }
+            acc = fma_t(v.x, __ldcg(e + c.x), acc);
+            acc = fma_t(v.y, __ldcg(e + c.y), acc);
+            acc = fma_t(v.z, __ldcg(e + c.z), acc);
+            acc = fma_t(v.w, __ldcg(e + c.w), acc);
+        }
+        for (int32_t p = ub + 4 * gl; p < ue; p += 4 * G) {
+            const int4 c = __ldg(reinterpret_cast<const int4*>(sc + p));
+            const Quad<T> v = Quad<T>::load(sv + p);
+            acc = fma_t(v.x, __ldg(eold + c.x), acc);
+            acc = fma_t(v.y, __ldg(eold + c.y), acc);
+            acc = fma_t(v.z, __ldg(eold + c.z), acc);
+            acc = fma_t(v.w, __ldg(eold + c.w), acc);
         }
         acc = group_reduce(acc);
         if (act && gl == 0) {
@@ -422,7 +429,7 @@ static void launch_rows(Level& L, int32_t r0, int32_t r1, cudaStream_t s) {
     const int64_t threads = (int64_t)(r1 - r0) * G;
     const T* dv = (MODE == 3) ? LV<T>::diag(L) : LV<T>::dinv(L);
     launch_pdl(row_kernel<MODE, T>, grid_for(threads, VBLOCK), VBLOCK, s, (const int32_t*)L.lo.get(),
-               (const int32_t*)L.mid.get(), (const int32_t*)L.sc.get(), LV<T>::sv(L), dv, (const T*)LV<T>::b(L),
+               (const int32_t*)L.up.get(), (const int32_t*)L.sc.get(), LV<T>::sv(L), dv, (const T*)LV<T>::b(L),
                LV<T>::e(L), LV<T>::s(L), r0, r1);
 }
 
@@ -445,7 +452,7 @@ static void launch_psweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
     const int nblocks = std::max(1, std::min(mb, (maxrows + PS_ROWS - 1) / PS_ROWS));
     CK(cudaMemsetAsync(L.bar.get(), 0, sizeof(unsigned), s));
     const int32_t* lo = L.lo.get();
-    const int32_t* mid = L.mid.get();
+    const int32_t* up = L.up.get();
     const int32_t* sc = L.sc.get();
     const T* sv = LV<T>::sv(L);
     const T* dv = LV<T>::dinv(L);
@@ -455,7 +462,7 @@ static void launch_psweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
     unsigned* bar = L.bar.get();
     int* err = H->err.get();
     unsigned long long limit = PS_SPIN_LIMIT;
-    void* args[] = {(void*)&lo, (void*)&mid, (void*)&sc, (void*)&sv, (void*)&dv, (void*)&b, (void*)&e, (void*)&cp,
+    void* args[] = {(void*)&lo, (void*)&up, (void*)&sc, (void*)&sv, (void*)&dv, (void*)&b, (void*)&e, (void*)&cp,
                     (void*)&nc, (void*)&bar, (void*)&err, (void*)&limit};
     CK(cudaLaunchCooperativeKernel((const void*)psweep_k<MODE, T>, dim3(nblocks), dim3(PS_THREADS), args, 0, s));
     CK_LAUNCH();
@@ -478,7 +485,7 @@ static void launch_dsweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
     T* eold = LV<T>::eold(L);
     if (MODE == 1) CK(cudaMemcpyAsync(eold, e, sizeof(T) * L.n, cudaMemcpyDeviceToDevice, s));
     const int32_t* lo = L.lo.get();
-    const int32_t* mid = L.mid.get();
+    const int32_t* up = L.up.get();
     const int32_t* sc = L.sc.get();
     const T* sv = LV<T>::sv(L);
     const T* dv = LV<T>::dinv(L);
@@ -489,7 +496,7 @@ static void launch_dsweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
     int* flag = L.flag.get();
     int* err = H->err.get();
     unsigned long long limit = PS_SPIN_LIMIT;
-    void* args[] = {(void*)&lo, (void*)&mid, (void*)&sc, (void*)&sv, (void*)&dv, (void*)&b, (void*)&e, (void*)&eo,
+    void* args[] = {(void*)&lo, (void*)&up, (void*)&sc, (void*)&sv, (void*)&dv, (void*)&b, (void*)&e, (void*)&eo,
                     (void*)&gp, (void*)&ng, (void*)&flag, (void*)&err, (void*)&limit};
     CK(cudaLaunchCooperativeKernel((const void*)dsweep_k<MODE, T>, dim3(nblocks), dim3(DS_THREADS), args, 0, s));
     CK_LAUNCH();
@@ -503,10 +510,12 @@ static void sweep(Level& L, bool from_zero, cudaStream_t s) {
     }
 }
 
-// Alg. 3 with a zero initial guess on level 1: b_0 -> e_0
+// one forward sweep of level L (from zero: lower parts only)
 template <class T>
 static void sweep_any(mgm_hierarchy* H, Level& L, bool from_zero, cudaStream_t s) {
-    if (H->sweep_mode == 2) {
+    if (L.stream) {
+        stream_sweep<T>(H, L, from_zero ? 0 : 1, false, s);
+    } else if (H->sweep_mode == 2) {
         if (from_zero) launch_dsweep<0, T>(H, L, s);
         else launch_dsweep<1, T>(H, L, s);
     } else if (H->sweep_mode == 1) {
@@ -515,6 +524,21 @@ static void sweep_any(mgm_hierarchy* H, Level& L, bool from_zero, cudaStream_t s
     } else {
         sweep<T>(L, from_zero, s);
     }
+}
+
+// pre-smoothing of level L from a zero initial guess and its residual s = b - L e (Alg. 3's
+// descent at one level): nu1 sweeps, the first from zero; with nu1 = 1 the residual is -U e
+template <class T>
+static const T* presmooth_residual(mgm_hierarchy* H, Level& L, cudaStream_t s) {
+    if (H->nu1 == 1 && L.stream) {
+        stream_sweep<T>(H, L, 0, true, s);  // sweep and residual in one launch
+        return LV<T>::s(L);
+    }
+    sweep_any<T>(H, L, true, s);
+    for (int t = 1; t < H->nu1; ++t) sweep_any<T>(H, L, false, s);
+    if (H->nu1 == 1) launch_rows<2, T>(L, 0, (int32_t)L.n, s);
+    else launch_rows<3, T>(L, 0, (int32_t)L.n, s);
+    return LV<T>::s(L);
 }
 
 // ------------------------------ the bordered cycle (Sec. 4.4) -------------------------------------
@@ -571,11 +595,7 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
         Level& C = H->lv[j + 1];
         const T* rsrc;
         if (H->nu1 >= 1) {
-            sweep_any<T>(H, L, true, s);
-            for (int t = 1; t < H->nu1; ++t) sweep_any<T>(H, L, false, s);
-            if (H->nu1 == 1) launch_rows<2, T>(L, 0, (int32_t)L.n, s);
-            else launch_rows<3, T>(L, 0, (int32_t)L.n, s);
-            rsrc = LV<T>::s(L);
+            rsrc = presmooth_residual<T>(H, L, s);
         } else {
             CK(cudaMemsetAsync(LV<T>::e(L), 0, sizeof(T) * L.n, s));
             rsrc = LV<T>::b(L);
@@ -627,11 +647,7 @@ static void cycle_rec(mgm_hierarchy* H, int j, int type, bool zero_start, cudaSt
     Level& C = H->lv[j + 1];
     const T* rsrc;
     if (zero_start && H->nu1 >= 1) {
-        sweep_any<T>(H, L, true, s);
-        for (int t = 1; t < H->nu1; ++t) sweep_any<T>(H, L, false, s);
-        if (H->nu1 == 1) launch_rows<2, T>(L, 0, (int32_t)L.n, s);
-        else launch_rows<3, T>(L, 0, (int32_t)L.n, s);
-        rsrc = LV<T>::s(L);
+        rsrc = presmooth_residual<T>(H, L, s);
     } else if (zero_start) {
         CK(cudaMemsetAsync(LV<T>::e(L), 0, sizeof(T) * L.n, s));
         rsrc = LV<T>::b(L);
@@ -722,6 +738,58 @@ static cudaGraphExec_t capture(mgm_hierarchy* H, bool learned, int64_t* kernels)
     cudaGraphDestroy(g);
     CK(e);
     return ex;
+}
+
+// drop the captured cycle graphs (after a level's sweep schedule changed); recaptured on next use
+void invalidate_graphs(mgm_hierarchy* H) {
+    if (H->vgraph) { CK(cudaGraphExecDestroy(H->vgraph)); H->vgraph = nullptr; }
+    if (H->lgraph) { CK(cudaGraphExecDestroy(H->lgraph)); H->lgraph = nullptr; }
+}
+
+// Device time (ms) of level j's smoothing work in one V-cycle: pre-smoothing from zero with its
+// residual, then the post-smoothing sweeps, captured in a graph as the cycle runs them and
+// replayed `reps` times after two warm-ups. Overwrites the level's work vectors.
+float time_level_smoothing(mgm_hierarchy* H, int j, int reps, cudaStream_t s) {
+    REQUIRE(j >= 0 && j + 1 < H->p && reps >= 1, "bad level");
+    if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+    Level& L = H->lv[j];
+    cudaGraph_t g = nullptr;
+    const int64_t before = thread_launches();
+    CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
+    try {
+        if (H->precision == MGM_F32) {
+            presmooth_residual<float>(H, L, H->cap_stream);
+            for (int t = 0; t < H->nu2; ++t) sweep_any<float>(H, L, false, H->cap_stream);
+        } else {
+            presmooth_residual<double>(H, L, H->cap_stream);
+            for (int t = 0; t < H->nu2; ++t) sweep_any<double>(H, L, false, H->cap_stream);
+        }
+    } catch (...) {
+        cudaStreamEndCapture(H->cap_stream, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    CK(cudaStreamEndCapture(H->cap_stream, &g));
+    note_launch(-(thread_launches() - before));
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int t = 0; t < 2; ++t) CK(cudaGraphLaunch(ex, s));
+    CK(cudaEventRecord(e0, s));
+    for (int t = 0; t < reps; ++t) CK(cudaGraphLaunch(ex, s));
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ex);
+    check_device_error(H, s);
+    return ms / reps;
 }
 
 void vcycle_prepare(mgm_hierarchy* H) {
@@ -864,7 +932,7 @@ void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStrea
         CK(cudaEventElapsedTime(&ms, e0, e1));
         out->sweep_ms = ms / reps;
         out->sweep_bytes = (L.nlow + L.nupp) * (vs + 4) + L.n * (4 + 3 * vs);
-        out->sweep_launches = H->persistent ? 1 : (int32_t)(L.cptr.size() - 1);  // kernels (copies not counted)
+        out->sweep_launches = (H->persistent || L.stream) ? 1 : (int32_t)(L.cptr.size() - 1);  // kernels (copies not counted)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -875,6 +943,7 @@ void check_device_error(mgm_hierarchy* H, cudaStream_t s) {
     int e = read1(H->err.get(), s);
     if (e) {
         CK(cudaMemsetAsync(H->err.get(), 0, sizeof(int), s));
+        stream_reset(H, s);
         fail(MGM_ERR_TIMEOUT, "a device-side barrier wait gave up (spin limit reached)");
     }
 }

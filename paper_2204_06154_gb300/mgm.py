@@ -65,7 +65,12 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_mlp_size", "mgm_mlp_create", "mgm_mlp_destroy", "mgm_mlp_get", "mgm_mlp_set", "mgm_mlp_forward",
            "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
            "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
-           "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs", "mgm_reaction_rhs"]
+           "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs", "mgm_reaction_rhs",
+           "mgm_sweep_config_set", "mgm_sweep_config_get", "mgm_autotune"]
+
+
+class SweepConfig(C.Structure):
+    _fields_ = [("kind", C.c_int), ("blocks", C.c_int), ("lanes", C.c_int), ("stages", C.c_int), ("ms", C.c_float)]
 
 
 class ProfileInfo(C.Structure):
@@ -103,6 +108,9 @@ def lib():
         L.mgm_hierarchy_level.argtypes = [P, I] + [P] * 10 + [P]
         L.mgm_hierarchy_pnnz.argtypes = [P, I, C.POINTER(C.c_int64)]
         L.mgm_profile.argtypes = [P, I, C.POINTER(ProfileInfo), P]
+        L.mgm_sweep_config_set.argtypes = [P, I, C.POINTER(SweepConfig), P]
+        L.mgm_sweep_config_get.argtypes = [P, I, C.POINTER(SweepConfig)]
+        L.mgm_autotune.argtypes = [P, I, I, P]
         L.mgm_check_bounded_wait.argtypes = [I, I64, C.POINTER(C.c_int), P]
         L.mgm_kernel_launches.argtypes = []
         L.mgm_kernel_launches.restype = C.c_int64
@@ -406,6 +414,22 @@ class Hierarchy:
         pi = ProfileInfo()
         _check(lib().mgm_profile(self._h, reps, C.byref(pi), _stream()))
         return {k: getattr(pi, k) for k, _ in ProfileInfo._fields_}
+
+    def sweep_config(self, level):
+        """Sweep schedule of a level: {"kind": "launch"|"stream", "blocks", "lanes", "stages", "ms"}."""
+        c = SweepConfig()
+        _check(lib().mgm_sweep_config_get(self._h, level, C.byref(c)))
+        return {"kind": "stream" if c.kind == 1 else "launch", "blocks": c.blocks, "lanes": c.lanes,
+                "stages": c.stages, "ms": c.ms}
+
+    def set_sweep_config(self, level, kind="stream", blocks=0, lanes=2, stages=2):
+        c = SweepConfig(1 if kind == "stream" else 0, blocks, lanes, stages, 0.0)
+        _check(lib().mgm_sweep_config_set(self._h, level, C.byref(c), _stream()))
+
+    def autotune(self, reps=5, use_cache=True):
+        """Per-level choice of sweep schedule by timed trials (mgm_autotune); returns the choices."""
+        _check(lib().mgm_autotune(self._h, reps, int(use_cache), _stream()))
+        return [self.sweep_config(j) for j in range(self.stats()["p"] - 1)]
 
     def vcycle(self, r):
         if r.dtype not in (torch.float32, torch.float64):

@@ -1,0 +1,180 @@
+"""Streamed multicolour sweeps (persistent_sweeps = 3): one cooperative launch per sweep and level,
+matrix entries staged in shared memory by bulk copies, colours started on the neighbouring bands'
+progress. The V-cycle (paper Alg. 3 with forward multicolour Gauss-Seidel) must match the
+oracle's as the per-colour launches do: FP64 within 1e-12, FP32 within 1e-4 (normwise); the sums
+of a row run in another order, so agreement with the per-colour schedule is to rounding, not bits."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2204_06154_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+STREAM = 3
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2204_06154_gb300 import mgm
+    mgm.lib()
+    return mgm
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def H(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def ico5(oracle):
+    x, nrm = I.icosahedral_sphere(5)
+    idx, w, L = oracle.build_operator(x, nrm, 30, "rbf", 1, 2, 1.0)
+    return x, nrm, idx, w, L
+
+
+def _csr(L):
+    return T(L.indptr.astype(np.int32)), T(L.indices.astype(np.int32)), T(L.data)
+
+
+@pytest.mark.parametrize("nu", [1, 2])
+def test_stream_vcycle_matches_oracle(M, oracle, ico5, nu):
+    """10,242-point icosahedral sphere, n_min = 125 (four levels): nu pre- and post-sweeps (nu = 1:
+    pre-smoothing and the residual -U e in one launch; nu = 2: separate full sweeps and b - A e)."""
+    x, nrm, idx, w, L = ico5
+    Ho = oracle.setup(x, L, 125, seed=0, nu1=nu, nu2=nu)
+    rng = np.random.default_rng(21)
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-4)):
+        Hg = M.Hierarchy(T(x), *_csr(L), n_min=125, nu1=nu, nu2=nu, precision=prec, persistent_sweeps=STREAM)
+        for _ in range(3):  # repeated launches: the progress counters carry over between them
+            r = rng.standard_normal(x.shape[0])
+            zo = oracle.vcycle(Ho, r)
+            z = H(Hg.vcycle(T(r)))
+            assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo), (prec, nu)
+
+
+def test_stream_vcycle_60k_matches_oracle(M, oracle):
+    """Five levels from GPU stencils of a 60k-point cloud; the finest level spans many blocks (30
+    bands), so neighbouring bands wait on each other's progress."""
+    import scipy.sparse as sp
+    x, nrm = I.fibonacci_sphere(60000, 0.1, 12)
+    _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 30, "rbf", 1, 2, 1.0, keep_weights=False)
+    L = sp.csr_matrix((H(v), H(ci), H(rp)), shape=(60000, 60000))
+    Ho = oracle.setup(x, L, 250, seed=0)
+    r = np.random.default_rng(13).standard_normal(60000)
+    zo = oracle.vcycle(Ho, r)
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-4)):
+        Hg = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec, persistent_sweeps=STREAM)
+        z = H(Hg.vcycle(T(r)))
+        assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo), prec
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_stream_matches_per_colour_at_scale(M, prec, tol):
+    """A 400k-point cloud with n = 50 (the benchmark's stencils): the finest level runs on all
+    co-resident blocks. Streamed and per-colour cycles agree to rounding, and FGMRES reaches
+    1e-10 with the same solution (1e-8) and iteration counts within one."""
+    x, nrm = I.fibonacci_sphere(400000, 0.1, 9)
+    _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 50, "rbf", 1, 3, 1.0, keep_weights=False)
+    Ha = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec)
+    Hb = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec, persistent_sweeps=STREAM)
+    r = T(np.random.default_rng(6).standard_normal(x.shape[0]))
+    for _ in range(3):
+        za, zb = H(Ha.vcycle(r)), H(Hb.vcycle(r))
+        assert np.linalg.norm(za - zb) <= tol * np.linalg.norm(za)
+    f = T(I.random_sh_rhs(x, lmax=12, seed=7))
+    ua, ia = Ha.solve(f, tol=1e-10)
+    ub, ib = Hb.solve(f, tol=1e-10)
+    assert ia["converged"] and ib["converged"] and abs(ia["iters"] - ib["iters"]) <= 1
+    assert np.linalg.norm(H(ua) - H(ub)) <= 1e-8 * np.linalg.norm(H(ua))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_stream_solve_matches_oracle(M, oracle, ico5, prec):
+    x, nrm, idx, w, L = ico5
+    Ho = oracle.setup(x, L, 125, seed=0)
+    f = 21.0 * I.y43(x)
+    uo, _, _ = oracle.fgmres(L, Ho, f, tol=1e-12)
+    Hg = M.Hierarchy(T(x), *_csr(L), n_min=125, precision=prec, persistent_sweeps=STREAM)
+    u, info = Hg.solve(T(f), tol=1e-10)
+    assert info["converged"] and info["rel_res"] <= 1e-10
+    assert np.linalg.norm(H(u) - uo) <= 1e-8 * np.linalg.norm(uo)
+    _, it10, _ = oracle.fgmres(L, Ho, f, tol=1e-10)
+    assert abs(info["iters"] - it10) <= 2, (info["iters"], it10)
+
+
+@pytest.mark.parametrize("cycle", ["W", "F"])
+def test_stream_w_f_cycles_match_oracle(M, oracle, ico5, cycle):
+    """W- and F-cycles revisit coarse levels from a nonzero iterate (full sweeps, full residual)."""
+    x, nrm, idx, w, L = ico5
+    Ho = oracle.setup(x, L, 125, seed=0)
+    r = np.random.default_rng(3).standard_normal(x.shape[0])
+    zo = oracle.mgcycle(Ho, r, cycle=cycle)
+    Hg = M.Hierarchy(T(x), *_csr(L), n_min=125, precision="f64", persistent_sweeps=STREAM, cycle=cycle)
+    z = H(Hg.vcycle(T(r)))
+    assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+def test_stream_bordered_matches_oracle(M, oracle):
+    """Surface Poisson with the mean-zero constraint (Sec. 4.4): the bordered cycle shifts b before
+    post-smoothing; the streamed sweeps read the shifted b."""
+    x, nrm = I.icosahedral_sphere(5)
+    idx, w, L = oracle.build_operator(x, nrm, 30, "rbf", 1, 2, 1.0, poisson=True)
+    Ho = oracle.setup(x, L, 250, seed=0, bordered=True)
+    N = L.shape[0]
+    r, s = np.random.default_rng(7).standard_normal(N), 0.37
+    e, mu = oracle.vcycle_bordered(Ho, r, s)
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-4)):
+        Hg = M.Hierarchy(T(x), *_csr(L), n_min=250, precision=prec, persistent_sweeps=STREAM, constraint=True)
+        z = H(Hg.vcycle(T(np.concatenate([r, [s]]))))
+        assert np.linalg.norm(z[:N] - e) <= tol * np.linalg.norm(e), prec
+        assert abs(z[N] - mu) <= tol * max(abs(mu), np.linalg.norm(e) / np.sqrt(N)), prec
+
+
+def test_schedules_agree_with_oracle(M, oracle):
+    """Every streamed schedule (blocks, lanes a row, stages) set by hand on each level gives the
+    oracle's FP64 cycle within 1e-12; one launch per colour too."""
+    import scipy.sparse as sp
+    x, nrm = I.fibonacci_sphere(60000, 0.1, 14)
+    _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 30, "rbf", 1, 2, 1.0, keep_weights=False)
+    L = sp.csr_matrix((H(v), H(ci), H(rp)), shape=(60000, 60000))
+    Ho = oracle.setup(x, L, 250, seed=0)
+    r = np.random.default_rng(15).standard_normal(60000)
+    zo = oracle.vcycle(Ho, r)
+    Hg = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision="f64", persistent_sweeps=STREAM)
+    p = Hg.stats()["p"]
+    for blocks, lanes, stages in ((1, 1, 2), (7, 4, 3), (64, 2, 2), (152, 8, 4), (33, 1, 8)):
+        for j in range(p - 1):
+            n = Hg.stats()["n"][j]
+            Hg.set_sweep_config(j, "stream", min(blocks, n), lanes, stages)
+            got = Hg.sweep_config(j)
+            assert got["kind"] == "stream" and got["lanes"] == lanes and got["stages"] == stages
+        z = H(Hg.vcycle(T(r)))
+        assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo), (blocks, lanes, stages)
+    for j in range(p - 1):
+        Hg.set_sweep_config(j, "launch")
+    z = H(Hg.vcycle(T(r)))
+    assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-4)])
+def test_autotuned_hierarchy_matches_oracle(M, oracle, prec, tol):
+    """persistent_sweeps = 4: the autotuner times each level's schedules at set-up and records its
+    choice; the tuned cycle matches the oracle's and a solve converges."""
+    import scipy.sparse as sp
+    x, nrm = I.fibonacci_sphere(60000, 0.1, 16)
+    _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 30, "rbf", 1, 2, 1.0, keep_weights=False)
+    L = sp.csr_matrix((H(v), H(ci), H(rp)), shape=(60000, 60000))
+    Ho = oracle.setup(x, L, 250, seed=0)
+    r = np.random.default_rng(17).standard_normal(60000)
+    zo = oracle.vcycle(Ho, r)
+    Hg = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec, persistent_sweeps=4)
+    cfg = [Hg.sweep_config(j) for j in range(Hg.stats()["p"] - 1)]
+    assert all(c["ms"] > 0 for c in cfg), cfg
+    z = H(Hg.vcycle(T(r)))
+    assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo)
+    u, info = Hg.solve(T(I.random_sh_rhs(x, lmax=12, seed=3)), tol=1e-10)
+    assert info["converged"]
