@@ -78,7 +78,7 @@ def parse():
                     help="profiling driver: build the sphere problem of --size, then run this many V-cycles "
                          "(FP32 unless --fp64-cycle; --learned-n attaches an untrained correction of that stencil size)")
     ap.add_argument("--fp64-cycle", action="store_true")
-    ap.add_argument("--sweeps", default="0,3", help="profiling driver: sweep schedules to compare (persistent_sweeps values)")
+    ap.add_argument("--sweeps", default="0,5,4", help="profiling driver: sweep schedules to compare (persistent_sweeps values)")
     ap.add_argument("--learned-n", type=int, default=0)
     return ap.parse_args()
 

@@ -94,9 +94,13 @@ typedef struct {
                               waits); pre-smoothing and its residual share one launch. Mode 3 sums a
                               row's products in another order than modes 0-2 (same values up to
                               rounding). Levels with more than 128 colours keep mode 0. 4
-                              (MGM_SWEEP_AUTO): each level takes the faster of mode 0 and mode 3
-                              schedules, timed at set-up by mgm_autotune (decisions cached per
-                              level shape for the process). Other values: MGM_ERR_INVALID_ARG. */
+                              (MGM_SWEEP_AUTO): each level takes the fastest of the schedules of
+                              mgm_sweep_config, timed at set-up by mgm_autotune (decisions cached per
+                              level shape for the process). 5 (MGM_SWEEP_STAGED): one kernel per
+                              colour whose blocks each copy one RCM band's slice of the colour into
+                              shared memory before the programmatic-launch wait (MGM_SCHEDULE_COLOUR
+                              with a fixed choice of bands and lanes); sums as in mode 3's order.
+                              Other values: MGM_ERR_INVALID_ARG. */
     int constraint;  /* 0: solve L u = f. 1: surface Poisson (L = D, singular; build the operator with
                         mgm_stencil_params.poisson = 1) with the mean-zero constraint of Sec. 4.4: the
                         bordered system [L 1; 1^T 0][u; lambda] = [f; 0] (eq. (saddle_point)), coarse
@@ -114,7 +118,8 @@ typedef struct {
 } mgm_params;
 
 enum { MGM_SMOOTHER_MC = 0, MGM_SMOOTHER_LEX = 1 };
-enum { MGM_SWEEP_LAUNCH = 0, MGM_SWEEP_BARRIER = 1, MGM_SWEEP_FLAGS = 2, MGM_SWEEP_STREAM = 3, MGM_SWEEP_AUTO = 4 };
+enum { MGM_SWEEP_LAUNCH = 0, MGM_SWEEP_BARRIER = 1, MGM_SWEEP_FLAGS = 2, MGM_SWEEP_STREAM = 3, MGM_SWEEP_AUTO = 4,
+       MGM_SWEEP_STAGED = 5 };
 enum { MGM_CYCLE_V = 0, MGM_CYCLE_W = 1, MGM_CYCLE_F = 2 };
 
 typedef struct {
@@ -362,13 +367,18 @@ mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_st
  * kind MGM_SCHEDULE_LAUNCH: one kernel per colour (blocks, lanes, stages 0). MGM_SCHEDULE_STREAM:
  * one cooperative launch per sweep on `blocks` blocks (1 <= blocks <= the co-resident maximum,
  * one per SM), `lanes` in {1, 2, 4, 8} threads a row, `stages` in 2..8 shared-memory stages.
+ * MGM_SCHEDULE_RESIDENT: one block per sweep holding the level's vector in shared memory (levels
+ * of at most 25,600 rows in FP32, 12,800 in FP64; blocks is 1), lanes and stages as above.
+ * MGM_SCHEDULE_COLOUR: one kernel per colour on `blocks` blocks, each owning one RCM band's rows of
+ * the colour, whose entries it copies into shared memory before the programmatic-launch wait
+ * (stages 0); MGM_ERR_UNSUPPORTED when a band's slice of a colour exceeds a block's shared memory.
  * ms: the autotuner's device time for the level's smoothing in one V-cycle (0 when set by hand). */
 typedef struct {
     int kind;
     int blocks, lanes, stages;
     float ms;
 } mgm_sweep_config;
-enum { MGM_SCHEDULE_LAUNCH = 0, MGM_SCHEDULE_STREAM = 1 };
+enum { MGM_SCHEDULE_LAUNCH = 0, MGM_SCHEDULE_STREAM = 1, MGM_SCHEDULE_RESIDENT = 2, MGM_SCHEDULE_COLOUR = 3 };
 
 /* Sets level j's schedule (0 <= j < p-1); the hierarchy must have persistent_sweeps 0, 3 or 4.
  * MGM_ERR_UNSUPPORTED when a streamed schedule does not fit the level (more than 128 colours, a
@@ -385,6 +395,10 @@ mgm_status mgm_sweep_config_get(const mgm_hierarchy* H, int j, mgm_sweep_config*
  * size, entries a row, colour count) for the life of the process. Overwrites the work vectors;
  * synchronises. */
 mgm_status mgm_autotune(mgm_hierarchy* H, int reps, int use_cache, mgm_stream stream);
+/* Measurement: device time (ms, *ms_out) of level j's smoothing work in one V-cycle under its
+ * current schedule, as the autotuner times it (0 <= j < p-1). Overwrites the work vectors;
+ * synchronises. */
+mgm_status mgm_profile_level(mgm_hierarchy* H, int j, int reps, float* ms_out, mgm_stream stream);
 
 /* Number of kernels this library has launched in the process (a host-side count: each launch of
  * the captured V-cycle graph adds its kernel nodes). */

@@ -256,6 +256,13 @@ mgm_status mgm_sweep_config_get(const mgm_hierarchy* H, int j, mgm_sweep_config*
     return guarded([&] { sweep_config_get(H, j, out); });
 }
 
+mgm_status mgm_profile_level(mgm_hierarchy* H, int j, int reps, float* ms_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(H && ms_out && reps >= 1 && j >= 0 && j + 1 < H->p, "bad argument");
+        *ms_out = time_level_smoothing(H, j, reps, S(stream));
+    });
+}
+
 mgm_status mgm_autotune(mgm_hierarchy* H, int reps, int use_cache, mgm_stream stream) {
     return guarded([&] { autotune(H, reps, use_cache != 0, S(stream)); });
 }

@@ -71,6 +71,8 @@ struct StreamArgs {
     int* err;
     int C, B, D, ns, sb;     // colours, blocks, dependency radius, stages, stage bytes
     int resid;               // MODE 0: also write s = -U e
+    int n;                   // rows of the level
+    int eres;                // resident form: bytes of shared memory holding e
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -198,7 +200,10 @@ __device__ __forceinline__ T row_dot(const int32_t* cl, const T* vl, int32_t l0,
     return acc;
 }
 
-template <int MODE, class T, int G>
+// RES: the resident form for a level small enough for one block: B = 1, the level's vector e
+// lives in shared memory for the whole sweep (gathers from shared memory; loaded first for a full
+// sweep, written back at the end), and colours are separated by the consumers' barrier alone.
+template <int MODE, class T, int G, bool RES>
 __global__ void __launch_bounds__(SS_THREADS, 1) gs_stream_k(const StreamArgs<T> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -206,7 +211,8 @@ __global__ void __launch_bounds__(SS_THREADS, 1) gs_stream_k(const StreamArgs<T>
     int32_t* chs = reinterpret_cast<int32_t*>(empty + SS_MAXSTAGES);  // C + 1 chunk starts
     volatile int* abort_flag = reinterpret_cast<volatile int*>(chs + SS_MAXC + 1);
     unsigned* base_s = reinterpret_cast<unsigned*>(chs + SS_MAXC + 2);
-    unsigned char* stages = smem + 2048;
+    T* es = reinterpret_cast<T*>(smem + 2048);                              // RES: e of the level
+    unsigned char* stages = smem + 2048 + (RES ? a.eres : 0);
     const int tid = threadIdx.x;
     const int k = blockIdx.x;
     const int C = a.C, B = a.B, NS = a.ns;
@@ -287,6 +293,12 @@ __global__ void __launch_bounds__(SS_THREADS, 1) gs_stream_k(const StreamArgs<T>
     const int ri = tid / G;  // row within the chunk
     const int gl = tid % G;  // lane within the row
     const int wlo = max(0, k - a.D), whi = min(B - 1, k + a.D);
+    T* ev = RES ? es : a.e;  // the vector the sweep reads and writes
+    if (RES) {  // a full sweep starts from the current e; a first sweep from zero (padding entries
+                // of a row point at the row itself with value 0, so its slot must hold a number)
+        for (int32_t i = tid; i < a.n; i += SS_CONSUMERS) es[i] = MODE == 1 ? a.e[i] : T(0);
+        consumer_sync();
+    }
 
     // row data of chunk ci (block-relative) for a pass
     auto load_meta = [&](int pass, int32_t ci) {
@@ -304,6 +316,7 @@ __global__ void __launch_bounds__(SS_THREADS, 1) gs_stream_k(const StreamArgs<T>
     // neighbours' progress >= target (bounded); the acquires make their writes visible to every
     // consumer after the barrier, which also agrees on whether to stop
     auto dep_wait = [&](unsigned target) {
+        if (RES) return consumer_sync_or(*abort_flag);
         for (int kk = wlo + tid; kk <= whi; kk += SS_CONSUMERS) {
             unsigned long long t0 = 0;
             for (unsigned it = 0;; ++it) {
@@ -350,12 +363,12 @@ __global__ void __launch_bounds__(SS_THREADS, 1) gs_stream_k(const StreamArgs<T>
                     const int32_t* cu = reinterpret_cast<const int32_t*>(stg + (4 + TS) * nL);
                     const T* vu = reinterpret_cast<const T*>(stg + (4 + TS) * nL + 4 * nU);
                     acc = row_dot<T, G>(cl, vl, useL ? m.lb - m.rc.x : 0, useL ? m.le - m.rc.x : 0, cu, vu,
-                                        useU ? m.ub - m.rc.z : 0, useU ? m.ue - m.rc.z : 0, gl, a.e, acc);
+                                        useU ? m.ub - m.rc.z : 0, useU ? m.ue - m.rc.z : 0, gl, ev, acc);
                 }
 #pragma unroll
                 for (int o = G / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                 if (ready && m.row >= 0 && gl == 0) {
-                    if (pass == 0) a.e[m.row] = (m.bv - acc) * m.dv;
+                    if (pass == 0) ev[m.row] = (m.bv - acc) * m.dv;
                     else a.s[m.row] = -acc;
                 }
                 consumer_sync();                     // every consumer is done with the stage
@@ -364,8 +377,12 @@ __global__ void __launch_bounds__(SS_THREADS, 1) gs_stream_k(const StreamArgs<T>
                 m = mn;
             }
             // every row of colour c is written (the chunk loop ends with a barrier)
-            if (pass == 0 && tid == 0) st_rel(a.prog + k, base + (unsigned)c + 1u);
+            if (!RES && pass == 0 && tid == 0) st_rel(a.prog + k, base + (unsigned)c + 1u);
         }
+    }
+    if (RES) {  // the sweep's e back to the level (every consumer passed the last barrier)
+        consumer_sync();
+        for (int32_t i = tid; i < a.n; i += SS_CONSUMERS) a.e[i] = es[i];
     }
 }
 
@@ -439,24 +456,21 @@ __global__ void ss_radius_k(const int32_t* __restrict__ rp, const int32_t* __res
     if ((threadIdx.x & 31) == 0 && d > 0) atomicMax(D, d);
 }
 
-template <int MODE, class T, int G>
-static const void* stream_kernel() { return (const void*)gs_stream_k<MODE, T, G>; }
-
-template <class T>
-static const void* stream_kernel(int mode, int G) {
-    if (mode == 0) {
-        if (G == 1) return stream_kernel<0, T, 1>();
-        if (G == 2) return stream_kernel<0, T, 2>();
-        if (G == 4) return stream_kernel<0, T, 4>();
-        return stream_kernel<0, T, 8>();
-    }
-    if (G == 1) return stream_kernel<1, T, 1>();
-    if (G == 2) return stream_kernel<1, T, 2>();
-    if (G == 4) return stream_kernel<1, T, 4>();
-    return stream_kernel<1, T, 8>();
+template <int MODE, class T, bool RES>
+static const void* stream_kernel_g(int G) {
+    if (G == 1) return (const void*)gs_stream_k<MODE, T, 1, RES>;
+    if (G == 2) return (const void*)gs_stream_k<MODE, T, 2, RES>;
+    if (G == 4) return (const void*)gs_stream_k<MODE, T, 4, RES>;
+    return (const void*)gs_stream_k<MODE, T, 8, RES>;
 }
 
-static int stream_smem(const Level& L) { return 2048 + L.sNS * L.sSB; }
+template <class T>
+static const void* stream_kernel(int mode, int G, bool res) {
+    if (mode == 0) return res ? stream_kernel_g<0, T, true>(G) : stream_kernel_g<0, T, false>(G);
+    return res ? stream_kernel_g<1, T, true>(G) : stream_kernel_g<1, T, false>(G);
+}
+
+static int stream_smem(const Level& L) { return 2048 + L.sEres + L.sNS * L.sSB; }
 
 // largest number of co-resident blocks of the streamed kernels with this stage ring (0: none)
 template <class T>
@@ -466,7 +480,9 @@ static int stream_max_blocks(int smem) {
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     for (int mode = 0; mode < 2; ++mode)
         for (int G : {1, 2, 4, 8}) {
-            const void* k = stream_kernel<T>(mode, G);
+            const void* k = stream_kernel<T>(mode, G, false);
+            const void* kr = stream_kernel<T>(mode, G, true);
+            CK(cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, 2048 + SS_SMEM_BUDGET));
             CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 2048 + SS_SMEM_BUDGET));
             int per = 0;
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, SS_THREADS, smem));
@@ -478,17 +494,21 @@ static int stream_max_blocks(int smem) {
 // Tables of a streamed level for B blocks, G lanes a row (chunks of at most 512 / G rows) and NS
 // stages. Returns false (level left to per-colour launches) when the level has too many colours
 // or a row does not fit one stage.
-bool stream_prepare(mgm_hierarchy* H, Level& L, int B, int G, int NS, cudaStream_t s) {
+bool stream_prepare(mgm_hierarchy* H, Level& L, int B, int G, int NS, cudaStream_t s, bool resident) {
     L.stream = 0;
+    L.csched = 0;
     const int C = (int)L.cptr.size() - 1;
     if (C < 1 || C > SS_MAXC || L.n < 1 || !(G == 1 || G == 2 || G == 4 || G == 8) || NS < 2 || NS > SS_MAXSTAGES)
         return false;
     const int ts = H->precision == MGM_F32 ? 4 : 8;
+    const int eres = resident ? (int)(((int64_t)L.n * ts + 127) / 128 * 128) : 0;
+    if (resident && (eres > SS_SMEM_BUDGET / 2 || L.n > INT32_MAX)) return false;
+    if (resident) B = 1;
     const int rmax = SS_CONSUMERS / G;
-    const int sb = (SS_SMEM_BUDGET / NS / 128) * 128;
+    const int sb = ((SS_SMEM_BUDGET - eres) / NS / 128) * 128;
     const int32_t cap = sb / (4 + ts);
     B = (int)std::max<int64_t>(1, std::min<int64_t>(B, L.n));
-    const int smem = 2048 + NS * sb;
+    const int smem = 2048 + eres + NS * sb;
     const int maxb = H->precision == MGM_F32 ? stream_max_blocks<float>(smem) : stream_max_blocks<double>(smem);
     if (maxb < B) return false;
     L.split.alloc((size_t)C * (B + 1));
@@ -527,6 +547,7 @@ bool stream_prepare(mgm_hierarchy* H, Level& L, int B, int G, int NS, cudaStream
     L.sD = hm[1];
     L.sNS = NS;
     L.sSB = sb;
+    L.sEres = eres;
     L.stream = 1;
     return true;
 }
@@ -560,9 +581,16 @@ void stream_sweep(mgm_hierarchy* H, Level& L, int mode, bool resid, cudaStream_t
     a.ns = L.sNS;
     a.sb = L.sSB;
     a.resid = resid ? 1 : 0;
+    a.n = (int)L.n;
+    a.eres = L.sEres;
     void* args[] = {(void*)&a};
-    CK(cudaLaunchCooperativeKernel(stream_kernel<T>(mode, L.sG), dim3(L.sB), dim3(SS_THREADS), args,
-                                   (size_t)stream_smem(L), s));
+    if (L.sEres) {  // one block: an ordinary launch
+        CK(cudaLaunchKernel(stream_kernel<T>(mode, L.sG, true), dim3(1), dim3(SS_THREADS), args,
+                            (size_t)stream_smem(L), s));
+    } else {
+        CK(cudaLaunchCooperativeKernel(stream_kernel<T>(mode, L.sG, false), dim3(L.sB), dim3(SS_THREADS), args,
+                                       (size_t)stream_smem(L), s));
+    }
     CK_LAUNCH();
 }
 template void stream_sweep<float>(mgm_hierarchy*, Level&, int, bool, cudaStream_t);
@@ -574,21 +602,232 @@ void stream_reset(mgm_hierarchy* H, cudaStream_t s) {
         if (L.stream) CK(cudaMemsetAsync(L.prog.get(), 0, sizeof(unsigned) * L.sB, s));
 }
 
+// ------------------------------ per-colour launches staged through shared memory -------------
+// One kernel per colour as in the plain schedule, but each block owns one band's slice of the
+// colour (the split table above), and before the programmatic-launch wait it copies the slice's
+// columns and values into shared memory with cp.async.bulk and loads its rows' static data. The
+// next colour's kernel is allowed to start as soon as every block of this one has started, so its
+// blocks, co-resident with this kernel's, fetch their slices while this colour computes; after the
+// wait only the gathers of the vector remain. b is read after the wait (the kernel that writes it
+// may still be running before it). MODE 0: lower parts (first sweep from zero); MODE 1: both.
+constexpr int CS_THREADS = 256;
+
+template <class T>
+struct ColourArgs {
+    const int32_t* lo;
+    const int32_t* up;
+    const int32_t* sc;
+    const T* sv;
+    const T* dinv;
+    const T* b;
+    T* e;
+    const int32_t* split;  // this colour's row of the split table: B + 1 slice bounds
+    int* err;
+};
+
+template <int MODE, class T, int G>
+__global__ void __launch_bounds__(CS_THREADS, 4) gs_colour_k(const ColourArgs<T> a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    __shared__ int4 rg;  // {lo[r0], lo[r1], up[r0], up[r1]}
+    pdl_trigger();
+    const int tid = threadIdx.x;
+    const int32_t r0 = a.split[blockIdx.x], r1 = a.split[blockIdx.x + 1];
+    if (r0 >= r1) return;
+    constexpr int TS = (int)sizeof(T);
+    if (tid == 0) {
+        const int4 v = make_int4(a.lo[r0], a.lo[r1], MODE == 1 ? a.up[r0] : 0, MODE == 1 ? a.up[r1] : 0);
+        rg = v;
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const unsigned nL = (unsigned)(v.y - v.x), nU = (unsigned)(v.w - v.z);
+        const uint64_t pol = evict_first_policy();
+        mbar_expect_tx(&bar, (nL + nU) * (4u + TS));
+        if (nL) {
+            bulk_copy(smem, a.sc + v.x, nL * 4u, &bar, pol);
+            bulk_copy(smem + 4u * nL, a.sv + v.x, nL * TS, &bar, pol);
+        }
+        if (nU) {
+            bulk_copy(smem + (4u + TS) * nL, a.sc + v.z, nU * 4u, &bar, pol);
+            bulk_copy(smem + (4u + TS) * nL + 4u * nU, a.sv + v.z, nU * TS, &bar, pol);
+        }
+    }
+    // this thread's first row: its static data (row starts, diagonal inverse) before the wait
+    const int rpp = CS_THREADS / G;  // rows a pass
+    const int gl = tid % G;
+    int32_t row = r0 + tid / G;
+    int32_t lb = 0, le = 0, ub = 0, ue = 0;
+    T dv = T(0);
+    if (row < r1) {
+        lb = a.lo[row];
+        le = a.lo[row + 1];
+        if (MODE == 1) { ub = a.up[row]; ue = a.up[row + 1]; }
+        dv = a.dinv[row];
+    }
+    __syncthreads();
+    const int4 v = rg;
+    const int32_t nL = v.y - v.x, nU = v.w - v.z;
+    const int32_t* cl = reinterpret_cast<const int32_t*>(smem);
+    const T* vl = reinterpret_cast<const T*>(smem + 4 * nL);
+    const int32_t* cu = reinterpret_cast<const int32_t*>(smem + (4 + TS) * nL);
+    const T* vu = reinterpret_cast<const T*>(smem + (4 + TS) * nL + 4 * nU);
+    pdl_wait();
+    // the slice's entries have landed (bounded wait; a timeout abandons the block's rows)
+    bool ready = mbar_try_wait(&bar, 0);
+    if (!ready) {
+        const unsigned long long t0 = gtimer();
+        while (!(ready = mbar_try_wait(&bar, 0)))
+            if (gtimer() - t0 > SS_LIMIT_NS) { if (gl == 0) atomicOr(a.err, MGM_ERR_TIMEOUT); break; }
+    }
+    if (__syncthreads_or(!ready)) {  // copies still in flight land before the block exits
+        if (tid == 0) {
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try_wait(&bar, 0) && gtimer() - t0 < SS_LIMIT_NS) {}
+        }
+        __syncthreads();
+        return;
+    }
+    for (int32_t base = r0; base < r1; base += rpp, row += rpp) {  // (uniform over the block: shuffles below)
+        const bool act = row < r1;
+        if (base > r0 && act) {  // rows of later passes
+            lb = a.lo[row];
+            le = a.lo[row + 1];
+            if (MODE == 1) { ub = a.up[row]; ue = a.up[row + 1]; }
+            dv = a.dinv[row];
+        }
+        T acc = T(0), bv = T(0);
+        if (act) {
+            bv = a.b[row];
+            acc = row_dot<T, G>(cl, vl, lb - v.x, le - v.x, cu, vu, MODE == 1 ? ub - v.z : 0, MODE == 1 ? ue - v.z : 0,
+                                gl, a.e, acc);
+        }
+#pragma unroll
+        for (int o = G / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (act && gl == 0) a.e[row] = (bv - acc) * dv;
+    }
+}
+
+template <int MODE, class T>
+static const void* colour_kernel_g(int G) {
+    if (G == 1) return (const void*)gs_colour_k<MODE, T, 1>;
+    if (G == 2) return (const void*)gs_colour_k<MODE, T, 2>;
+    if (G == 4) return (const void*)gs_colour_k<MODE, T, 4>;
+    return (const void*)gs_colour_k<MODE, T, 8>;
+}
+template <class T>
+static const void* colour_kernel(int mode, int G) {
+    return mode == 0 ? colour_kernel_g<0, T>(G) : colour_kernel_g<1, T>(G);
+}
+
+// largest slice of each colour: lower entries (x) and lower + upper entries (y)
+__global__ void cs_max_k(const int32_t* __restrict__ split, int C, int B, const int32_t* __restrict__ lo,
+                         const int32_t* __restrict__ up, int2* mx) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)C * B) return;
+    const int c = (int)(t / B), k = (int)(t % B);
+    const int32_t s0 = split[(int64_t)c * (B + 1) + k], s1 = split[(int64_t)c * (B + 1) + k + 1];
+    const int32_t l = lo[s1] - lo[s0], u = up[s1] - up[s0];
+    atomicMax(&mx[c].x, l);
+    atomicMax(&mx[c].y, l + u);
+}
+
+// Tables of the staged per-colour schedule for B bands and G lanes a row. False when some slice
+// does not fit the largest shared-memory allocation of a block.
+bool colour_prepare(mgm_hierarchy* H, Level& L, int B, int G, cudaStream_t s) {
+    L.stream = 0;
+    L.csched = 0;
+    const int C = (int)L.cptr.size() - 1;
+    if (C < 1 || L.n < 1 || !(G == 1 || G == 2 || G == 4 || G == 8) || B < 1) return false;
+    const int ts = H->precision == MGM_F32 ? 4 : 8;
+    B = (int)std::max<int64_t>(1, std::min<int64_t>(B, L.n));
+    L.split.alloc((size_t)C * (B + 1));
+    ss_split_k<<<grid_for((int64_t)C * (B + 1), 256), 256, 0, s>>>(L.ord.get(), L.cptr_dev.get(), C, B, L.n,
+                                                                  L.split.get());
+    CK_LAUNCH();
+    Temp<int2> mx(C, s);
+    CK(cudaMemsetAsync(mx.get(), 0, sizeof(int2) * C, s));
+    cs_max_k<<<grid_for((int64_t)C * B, 256), 256, 0, s>>>(L.split.get(), C, B, L.lo.get(), L.up.get(), mx.get());
+    CK_LAUNCH();
+    std::vector<int2> h(C);
+    to_host(h.data(), mx.get(), C, s);
+    int dev = 0, optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int limit = optin - 1024;
+    L.csm0.assign(C, 0);
+    L.csm1.assign(C, 0);
+    for (int c = 0; c < C; ++c) {
+        L.csm0[c] = (int)std::max<int64_t>(16, (int64_t)h[c].x * (4 + ts));
+        L.csm1[c] = (int)std::max<int64_t>(16, (int64_t)h[c].y * (4 + ts));
+        if (L.csm1[c] > limit) return false;
+    }
+    const void* ks[2][4];
+    for (int mode = 0; mode < 2; ++mode)
+        for (int gi = 0; gi < 4; ++gi) {
+            ks[mode][gi] = H->precision == MGM_F32 ? colour_kernel<float>(mode, 1 << gi) : colour_kernel<double>(mode, 1 << gi);
+            CK(cudaFuncSetAttribute(ks[mode][gi], cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+        }
+    L.sB = B;
+    L.sG = G;
+    L.csched = 1;
+    return true;
+}
+
+template <class T>
+void colour_sweep(mgm_hierarchy* H, Level& L, int mode, cudaStream_t s) {
+    ColourArgs<T> a;
+    a.lo = L.lo.get();
+    a.up = L.up.get();
+    a.sc = L.sc.get();
+    if constexpr (sizeof(T) == 4) {
+        a.sv = L.sv32.get(); a.dinv = L.dinv32.get(); a.b = L.b32.get(); a.e = L.e32.get();
+    } else {
+        a.sv = L.sv64.get(); a.dinv = L.dinv64.get(); a.b = L.b64.get(); a.e = L.e64.get();
+    }
+    a.err = H->err.get();
+    const int C = (int)L.cptr.size() - 1;
+    for (int c = 0; c < C; ++c) {
+        if (L.cptr[c + 1] == L.cptr[c]) continue;
+        a.split = L.split.get() + (int64_t)c * (L.sB + 1);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(L.sB);
+        cfg.blockDim = dim3(CS_THREADS);
+        cfg.dynamicSmemBytes = (size_t)(mode == 0 ? L.csm0[c] : L.csm1[c]);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        void* args[] = {(void*)&a};
+        CK(cudaLaunchKernelExC(&cfg, colour_kernel<T>(mode, L.sG), args));
+        CK_LAUNCH();
+    }
+}
+template void colour_sweep<float>(mgm_hierarchy*, Level&, int, cudaStream_t);
+template void colour_sweep<double>(mgm_hierarchy*, Level&, int, cudaStream_t);
+
 // ------------------------------ schedules and the autotuner ----------------------------------
 void sweep_config_get(const mgm_hierarchy* H, int j, mgm_sweep_config* out) {
     REQUIRE(H && out && j >= 0 && j < H->p, "bad argument");
     const Level& L = H->lv[j];
-    out->kind = L.stream ? MGM_SCHEDULE_STREAM : MGM_SCHEDULE_LAUNCH;
-    out->blocks = L.stream ? L.sB : 0;
-    out->lanes = L.stream ? L.sG : 0;
+    out->kind = L.csched ? MGM_SCHEDULE_COLOUR
+                         : (!L.stream ? MGM_SCHEDULE_LAUNCH : (L.sEres ? MGM_SCHEDULE_RESIDENT : MGM_SCHEDULE_STREAM));
+    out->blocks = (L.stream || L.csched) ? L.sB : 0;
+    out->lanes = (L.stream || L.csched) ? L.sG : 0;
     out->stages = L.stream ? L.sNS : 0;
     out->ms = L.tuned_ms;
 }
 
 static void apply_config(mgm_hierarchy* H, Level& L, const mgm_sweep_config& c, cudaStream_t s) {
-    if (c.kind == MGM_SCHEDULE_STREAM) {
-        if (!stream_prepare(H, L, c.blocks, c.lanes, c.stages, s))
-            fail(MGM_ERR_UNSUPPORTED, "streamed schedule does not fit this level (colours, row length or blocks)");
+    L.csched = 0;
+    if (c.kind == MGM_SCHEDULE_STREAM || c.kind == MGM_SCHEDULE_RESIDENT) {
+        if (!stream_prepare(H, L, c.blocks, c.lanes, c.stages, s, c.kind == MGM_SCHEDULE_RESIDENT))
+            fail(MGM_ERR_UNSUPPORTED, "streamed schedule does not fit this level (colours, row length, blocks or size)");
+    } else if (c.kind == MGM_SCHEDULE_COLOUR) {
+        if (!colour_prepare(H, L, c.blocks, c.lanes, s))
+            fail(MGM_ERR_UNSUPPORTED, "staged per-colour schedule: a slice does not fit shared memory");
     } else {
         L.stream = 0;
     }
@@ -596,12 +835,12 @@ static void apply_config(mgm_hierarchy* H, Level& L, const mgm_sweep_config& c, 
 
 void sweep_config_set(mgm_hierarchy* H, int j, const mgm_sweep_config* cfg, cudaStream_t s) {
     REQUIRE(H && cfg && j >= 0 && j + 1 < H->p, "bad argument (level must be smoothed)");
-    REQUIRE(H->sweep_mode == MGM_SWEEP_LAUNCH || H->sweep_mode == MGM_SWEEP_STREAM || H->sweep_mode == MGM_SWEEP_AUTO,
-            "per-level schedules need persistent_sweeps 0, 3 or 4");
-    REQUIRE(cfg->kind == MGM_SCHEDULE_LAUNCH || cfg->kind == MGM_SCHEDULE_STREAM, "unknown schedule kind");
+    REQUIRE(H->sweep_mode == MGM_SWEEP_LAUNCH || H->sweep_mode >= MGM_SWEEP_STREAM,
+            "per-level schedules need persistent_sweeps 0, 3, 4 or 5");
+    REQUIRE(cfg->kind >= MGM_SCHEDULE_LAUNCH && cfg->kind <= MGM_SCHEDULE_COLOUR, "unknown schedule kind");
     apply_config(H, H->lv[j], *cfg, s);
     H->lv[j].tuned_ms = 0.0f;
-    if (H->lv[j].stream) H->persistent = true;  // the error word of the bounded waits is checked
+    if (H->lv[j].stream || H->lv[j].csched) H->persistent = true;  // the error word of the bounded waits is checked
     invalidate_graphs(H);
     CK(cudaStreamSynchronize(s));
 }
@@ -620,9 +859,12 @@ std::mutex g_tuned_mu;
 // G = 1, 2 or 4 lanes a row and 2 stages (3 as well at the largest B) -- and keep the fastest.
 void autotune(mgm_hierarchy* H, int reps, bool use_cache, cudaStream_t s) {
     REQUIRE(H && reps >= 1, "bad argument");
-    REQUIRE(H->sweep_mode == MGM_SWEEP_LAUNCH || H->sweep_mode == MGM_SWEEP_STREAM || H->sweep_mode == MGM_SWEEP_AUTO,
-            "the autotuner chooses between persistent_sweeps 0 and 3 schedules");
+    REQUIRE(H->sweep_mode == MGM_SWEEP_LAUNCH || H->sweep_mode >= MGM_SWEEP_STREAM,
+            "the autotuner chooses among the schedules of persistent_sweeps 0, 3, 4 or 5");
     const int maxb = stream_blocks_limit(H);
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     H->persistent = true;  // candidates include streamed schedules
     for (int j = 0; j + 1 < H->p; ++j) {
         Level& L = H->lv[j];
@@ -642,10 +884,11 @@ void autotune(mgm_hierarchy* H, int reps, bool use_cache, cudaStream_t s) {
         }
         mgm_sweep_config best{MGM_SCHEDULE_LAUNCH, 0, 0, 0, 0.0f};
         L.stream = 0;
+        L.csched = 0;
         best.ms = time_level_smoothing(H, j, reps, s);
         std::vector<int> bs;
         const int64_t bhi = std::min<int64_t>(maxb, std::max<int64_t>(1, L.n / 64));
-        const int64_t blo = std::max<int64_t>(1, L.n / 16384);
+        const int64_t blo = std::max<int64_t>(2, L.n / 16384);
         for (int64_t b = bhi; b >= blo && (int)bs.size() < 6; b /= 2) bs.push_back((int)b);
         for (int b : bs)
             for (int g : {1, 2, 4})
@@ -655,6 +898,20 @@ void autotune(mgm_hierarchy* H, int reps, bool use_cache, cudaStream_t s) {
                     const float ms = time_level_smoothing(H, j, reps, s);
                     if (ms < best.ms) best = mgm_sweep_config{MGM_SCHEDULE_STREAM, b, g, ns, ms};
                 }
+        for (int mult : {1, 2, 3})  // staged per-colour launches, 1-3 bands an SM
+            for (int g : {1, 2, 4}) {
+                const int b = (int)std::min<int64_t>((int64_t)mult * sms, std::max<int64_t>(1, L.n / 32));
+                if (mult > 1 && b < (int64_t)mult * sms) continue;
+                if (!colour_prepare(H, L, b, g, s)) continue;
+                const float ms = time_level_smoothing(H, j, reps, s);
+                if (ms < best.ms) best = mgm_sweep_config{MGM_SCHEDULE_COLOUR, b, g, 0, ms};
+            }
+        for (int g : {1, 2, 4})  // one block with the level's vector in shared memory
+            for (int ns : {2, 4}) {
+                if (!stream_prepare(H, L, 1, g, ns, s, true)) continue;
+                const float ms = time_level_smoothing(H, j, reps, s);
+                if (ms < best.ms) best = mgm_sweep_config{MGM_SCHEDULE_RESIDENT, 1, g, ns, ms};
+            }
         apply_config(H, L, best, s);
         L.tuned_ms = best.ms;
         if (use_cache) {

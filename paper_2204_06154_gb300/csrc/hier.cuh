@@ -50,6 +50,9 @@ struct Level {
     // chunks of consecutive rows: rows {r0, r1} (rrow) and entry ranges {lo[r0], lo[r1], up[r0],
     // up[r1]} (rec); cchunk[k * (C + 1) + c] = first chunk of colour c, relative to recptr[k]
     int sB = 0, sD = 0, sG = 0, sNS = 0, sSB = 0;  // blocks, dependency radius, lanes a row, stages, stage bytes
+    int sEres = 0;             // resident form (one block): shared-memory bytes holding the level's e
+    int csched = 0;            // staged per-colour launches (sB bands, sG lanes a row)
+    std::vector<int> csm0, csm1;  // their shared memory a block per colour: lower parts / both parts
     Buf<int32_t> split, recptr, cchunk;
     Buf<int4> rec;
     Buf<int2> rrow;
@@ -146,11 +149,14 @@ void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_
 void solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp, mgm_solve_info* info,
            cudaStream_t s);
 // gs_stream.cu
-bool stream_prepare(mgm_hierarchy* H, Level& L, int B, int G, int NS, cudaStream_t s);
+bool stream_prepare(mgm_hierarchy* H, Level& L, int B, int G, int NS, cudaStream_t s, bool resident = false);
 int stream_blocks_limit(mgm_hierarchy* H);
 template <class T>
 void stream_sweep(mgm_hierarchy* H, Level& L, int mode, bool resid, cudaStream_t s);
 void stream_reset(mgm_hierarchy* H, cudaStream_t s);
+bool colour_prepare(mgm_hierarchy* H, Level& L, int B, int G, cudaStream_t s);
+template <class T>
+void colour_sweep(mgm_hierarchy* H, Level& L, int mode, cudaStream_t s);
 void sweep_config_set(mgm_hierarchy* H, int j, const mgm_sweep_config* cfg, cudaStream_t s);
 void sweep_config_get(const mgm_hierarchy* H, int j, mgm_sweep_config* out);
 void autotune(mgm_hierarchy* H, int reps, bool use_cache, cudaStream_t s);

@@ -566,7 +566,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     H->nu2 = prm->nu2;
     H->m = prm->m;
     H->seed = prm->seed;
-    REQUIRE(prm->persistent_sweeps >= 0 && prm->persistent_sweeps <= 4, "persistent_sweeps must be 0 to 4");
+    REQUIRE(prm->persistent_sweeps >= 0 && prm->persistent_sweeps <= 5, "persistent_sweeps must be 0 to 5");
     REQUIRE(prm->smoother == MGM_SMOOTHER_MC || prm->smoother == MGM_SMOOTHER_LEX, "unknown smoother");
     const bool lex = prm->smoother == MGM_SMOOTHER_LEX;
     H->sweep_mode = lex ? 2 : prm->persistent_sweeps;  // lexicographic: one row per group, flag-driven
@@ -717,6 +717,19 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     } else if (H->sweep_mode == MGM_SWEEP_AUTO) {  // the faster schedule per level, timed
         autotune(H.get(), 5, true, s);
         tr.mark("autotune", p - 1);
+    } else if (H->sweep_mode == MGM_SWEEP_STAGED) {  // staged per-colour launches on every level
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        for (int j = 0; j + 1 < p; ++j) {
+            Level& L = H->lv[j];
+            // measured on the 1M-point sphere (n = 50): three bands an SM and one lane a row on
+            // levels of 500k rows and more; below, one band an SM, 2 lanes (>= 100k) or 4
+            const int B = L.n >= 100000 ? 3 * sms : sms;
+            const int G = L.n >= 500000 ? 1 : (L.n >= 100000 ? 2 : 4);
+            colour_prepare(H.get(), L, B, G, s);  // (a level that does not fit keeps plain launches)
+        }
+        tr.mark("staged-tables", p - 1);
     }
     CK(cudaStreamSynchronize(s));
     int64_t bytes = H->Ainv.bytes() + H->ord_caller.bytes();

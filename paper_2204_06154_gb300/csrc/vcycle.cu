@@ -515,6 +515,8 @@ template <class T>
 static void sweep_any(mgm_hierarchy* H, Level& L, bool from_zero, cudaStream_t s) {
     if (L.stream) {
         stream_sweep<T>(H, L, from_zero ? 0 : 1, false, s);
+    } else if (L.csched) {
+        colour_sweep<T>(H, L, from_zero ? 0 : 1, s);
     } else if (H->sweep_mode == 2) {
         if (from_zero) launch_dsweep<0, T>(H, L, s);
         else launch_dsweep<1, T>(H, L, s);

@@ -66,7 +66,10 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
            "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
            "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs", "mgm_reaction_rhs",
-           "mgm_sweep_config_set", "mgm_sweep_config_get", "mgm_autotune"]
+           "mgm_sweep_config_set", "mgm_sweep_config_get", "mgm_autotune", "mgm_profile_level"]
+
+
+_SCHEDULES = ["launch", "stream", "resident", "colour"]
 
 
 class SweepConfig(C.Structure):
@@ -111,6 +114,7 @@ def lib():
         L.mgm_sweep_config_set.argtypes = [P, I, C.POINTER(SweepConfig), P]
         L.mgm_sweep_config_get.argtypes = [P, I, C.POINTER(SweepConfig)]
         L.mgm_autotune.argtypes = [P, I, I, P]
+        L.mgm_profile_level.argtypes = [P, I, I, C.POINTER(C.c_float), P]
         L.mgm_check_bounded_wait.argtypes = [I, I64, C.POINTER(C.c_int), P]
         L.mgm_kernel_launches.argtypes = []
         L.mgm_kernel_launches.restype = C.c_int64
@@ -348,9 +352,11 @@ def color(rp, ci, seed):
 class Hierarchy:
     """MGM hierarchy (Alg. 2) owned by the library; V-cycle (Alg. 3) and FGMRES solve on it."""
 
-    def __init__(self, xyz, rp, ci, v, n_min, m=3, nu1=1, nu2=1, precision="f32", seed=0, persistent_sweeps=False,
+    def __init__(self, xyz, rp, ci, v, n_min, m=3, nu1=1, nu2=1, precision="f32", seed=0, persistent_sweeps=5,
                  constraint=False, smoother="mc", cycle="V"):
-        """constraint=True: surface Poisson (L = D) with the mean-zero constraint of Sec. 4.4.
+        """persistent_sweeps: how the multicolour sweeps are launched (mgm_params; default 5, staged
+        per-colour launches; 0 one plain launch per colour; 4 autotuned per level).
+        constraint=True: surface Poisson (L = D) with the mean-zero constraint of Sec. 4.4.
         smoother: "mc" multicolour Gauss-Seidel or "lex" lexicographic Gauss-Seidel (the paper's).
         cycle: "V" (Alg. 3), "W" or "F" (Sec. 4.5)."""
         if smoother not in ("mc", "lex"):
@@ -419,12 +425,20 @@ class Hierarchy:
         """Sweep schedule of a level: {"kind": "launch"|"stream", "blocks", "lanes", "stages", "ms"}."""
         c = SweepConfig()
         _check(lib().mgm_sweep_config_get(self._h, level, C.byref(c)))
-        return {"kind": "stream" if c.kind == 1 else "launch", "blocks": c.blocks, "lanes": c.lanes,
-                "stages": c.stages, "ms": c.ms}
+        return {"kind": _SCHEDULES[c.kind], "blocks": c.blocks, "lanes": c.lanes, "stages": c.stages, "ms": c.ms}
 
     def set_sweep_config(self, level, kind="stream", blocks=0, lanes=2, stages=2):
-        c = SweepConfig(1 if kind == "stream" else 0, blocks, lanes, stages, 0.0)
+        """kind: "launch" (a kernel per colour), "stream" (one cooperative launch a sweep, progress
+        counters), "resident" (one block holding the level's vector) or "colour" (a kernel per colour,
+        each block's slice staged in shared memory before the programmatic-launch wait)."""
+        c = SweepConfig(_SCHEDULES.index(kind), blocks, lanes, stages, 0.0)
         _check(lib().mgm_sweep_config_set(self._h, level, C.byref(c), _stream()))
+
+    def profile_level(self, level, reps=10):
+        """Device time (ms) of a level's smoothing work in one V-cycle under its current schedule."""
+        ms = C.c_float(0.0)
+        _check(lib().mgm_profile_level(self._h, level, reps, C.byref(ms), _stream()))
+        return ms.value
 
     def autotune(self, reps=5, use_cache=True):
         """Per-level choice of sweep schedule by timed trials (mgm_autotune); returns the choices."""

@@ -461,7 +461,7 @@ def test_persistent_and_per_colour_sweeps_identical(M, oracle, ico5, nu):
     Lt = (T(L.indptr.astype(np.int32)), T(L.indices.astype(np.int32)), T(L.data))
     r = T(np.random.default_rng(5).standard_normal(x.shape[0]))
     for prec in ("f32", "f64"):
-        Ha = M.Hierarchy(T(x), *Lt, n_min=125, nu1=nu, nu2=nu, precision=prec)
+        Ha = M.Hierarchy(T(x), *Lt, n_min=125, nu1=nu, nu2=nu, precision=prec, persistent_sweeps=0)
         za = Ha.vcycle(r)
         for mode in (1, 2):
             Hb = M.Hierarchy(T(x), *Lt, n_min=125, nu1=nu, nu2=nu, precision=prec, persistent_sweeps=mode)
@@ -475,7 +475,7 @@ def test_flag_driven_sweeps_identical_at_scale(M, prec):
     launches."""
     x, nrm = I.fibonacci_sphere(300000, 0.1, 9)
     _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 30, "rbf", 1, 2, 1.0, keep_weights=False)
-    Ha = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec)
+    Ha = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec, persistent_sweeps=0)
     Hb = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec, persistent_sweeps=2)
     r = T(np.random.default_rng(6).standard_normal(x.shape[0]))
     for _ in range(3):

@@ -79,7 +79,7 @@ def test_stream_matches_per_colour_at_scale(M, prec, tol):
     1e-10 with the same solution (1e-8) and iteration counts within one."""
     x, nrm = I.fibonacci_sphere(400000, 0.1, 9)
     _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 50, "rbf", 1, 3, 1.0, keep_weights=False)
-    Ha = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec)
+    Ha = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec, persistent_sweeps=0)
     Hb = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec, persistent_sweeps=STREAM)
     r = T(np.random.default_rng(6).standard_normal(x.shape[0]))
     for _ in range(3):
@@ -158,6 +158,37 @@ def test_schedules_agree_with_oracle(M, oracle):
         Hg.set_sweep_config(j, "launch")
     z = H(Hg.vcycle(T(r)))
     assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-4)])
+def test_staged_and_resident_schedules_match_oracle(M, oracle, prec, tol):
+    """Per-colour launches with each band's slice staged in shared memory before the
+    programmatic-launch wait (1-3 bands an SM, 1-4 lanes a row), and one block holding a small
+    level's vector in shared memory: the cycle matches the oracle's, twice in a row."""
+    import scipy.sparse as sp
+    x, nrm = I.fibonacci_sphere(60000, 0.1, 18)
+    _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 30, "rbf", 1, 2, 1.0, keep_weights=False)
+    L = sp.csr_matrix((H(v), H(ci), H(rp)), shape=(60000, 60000))
+    Ho = oracle.setup(x, L, 250, seed=0)
+    rng = np.random.default_rng(19)
+    Hg = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision=prec, persistent_sweeps=0)
+    p = Hg.stats()["p"]
+    for blocks, lanes in ((152, 1), (304, 2), (456, 4), (7, 2)):
+        resident = 0
+        for j in range(p - 1):
+            Hg.set_sweep_config(j, "colour", blocks, lanes)
+            if j >= 1 and lanes in (1, 2):  # coarse levels held by one block where they fit
+                try:
+                    Hg.set_sweep_config(j, "resident", 1, lanes, 2 + 2 * (lanes == 2))
+                    resident += 1
+                except M.MGMError:
+                    pass
+        assert resident >= 1 or lanes == 4
+        for _ in range(2):
+            r = rng.standard_normal(60000)
+            zo = oracle.vcycle(Ho, r)
+            z = H(Hg.vcycle(T(r)))
+            assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo), (blocks, lanes)
 
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-4)])
