@@ -521,7 +521,9 @@ def main():
                                   "vcycle_ms": round(pr["vcycle_ms"], 4), "vcycle_kernels": pr["vcycle_kernels"],
                                   "vcycle_GB/s": round(pr["vcycle_bytes"] / pr["vcycle_ms"] / 1e6, 1),
                                   "sweep_ms": round(pr["sweep_ms"], 4),
-                                  "sweep_GB/s": round(pr["sweep_bytes"] / pr["sweep_ms"] / 1e6, 1) if pr["sweep_ms"] else None}
+                                  "sweep_GB/s": round(pr["sweep_bytes"] / pr["sweep_ms"] / 1e6, 1) if pr["sweep_ms"] else None,
+                                  "spmv_ms": round(pr["spmv_ms"], 4),
+                                  "spmv_GB/s": round(pr["spmv_bytes"] / pr["spmv_ms"] / 1e6, 1)}
             del H
         print(json.dumps(out), flush=True)
         return

@@ -20,46 +20,15 @@ namespace mgm {
 
 void add_output(mgm_hierarchy* H, double* dst, const int32_t* scatter, cudaStream_t s);
 
-constexpr int KG = 8;            // lanes per row in the FP64 operator
+constexpr int KG = 4;            // lanes per row in the FP64 operator (4: 0.189 ms at 1M rows; 8: 0.279; 16: 0.389)
 constexpr int KBLOCK = 256;
 constexpr int DOT_BLOCKS = 304;  // 2 per SM on 152 SMs
 
-// acc += the products of entries [b, e) of the FP64 operator with x, lane gl of KG: two chunks of 4
-// entries per lane and pass, both loaded before either is used, so that a warp has all of its rows'
-// matrix loads in flight at once; the additions keep the order of a plain chunk-by-chunk loop
-__device__ __forceinline__ double range_dot64(const int32_t* __restrict__ sc, const double* __restrict__ sv,
-                                              const double* __restrict__ x, int32_t b, int32_t e, int gl, double acc) {
-#pragma unroll 1
-    for (int32_t p = b + 4 * gl; p < e; p += 8 * KG) {
-        const bool two = p + 4 * KG < e;
-        const int4 c0 = __ldcs(reinterpret_cast<const int4*>(sc + p));
-        const double2 v0 = __ldcs(reinterpret_cast<const double2*>(sv + p));
-        const double2 v1 = __ldcs(reinterpret_cast<const double2*>(sv + p + 2));
-        int4 c1 = make_int4(0, 0, 0, 0);
-        double2 v2 = make_double2(0.0, 0.0), v3 = v2;
-        if (two) {
-            c1 = __ldcs(reinterpret_cast<const int4*>(sc + p + 4 * KG));
-            v2 = __ldcs(reinterpret_cast<const double2*>(sv + p + 4 * KG));
-            v3 = __ldcs(reinterpret_cast<const double2*>(sv + p + 4 * KG + 2));
-        }
-        const double x0 = x[c0.x], x1 = x[c0.y], x2 = x[c0.z], x3 = x[c0.w];
-        double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
-        if (two) { y0 = x[c1.x]; y1 = x[c1.y]; y2 = x[c1.z]; y3 = x[c1.w]; }
-        acc = fma(v0.x, x0, acc);
-        acc = fma(v0.y, x1, acc);
-        acc = fma(v1.x, x2, acc);
-        acc = fma(v1.y, x3, acc);
-        if (two) {
-            acc = fma(v2.x, y0, acc);
-            acc = fma(v2.y, y1, acc);
-            acc = fma(v3.x, y2, acc);
-            acc = fma(v3.y, y3, acc);
-        }
-    }
-    return acc;
-}
-
-// y = f - L x (RESID) or y = L x, L in solve order (lower and upper parts, diagonal apart)
+// y = f - L x (RESID) or y = L x, L in solve order (lower and upper parts, diagonal apart). Lane gl
+// of KG takes every KG-th quad of entries of the row's lower part, then of its upper part; the
+// columns and values of up to two quads, then their gathered x, are loaded before the products,
+// so a warp has all of its rows' loads in flight at once (rows of up to 32 entries a part take one round).
+// The products are added quad by quad in that order.
 template <bool RESID>
 __global__ void __launch_bounds__(KBLOCK) spmv64_k(const int32_t* __restrict__ lo, const int32_t* __restrict__ up,
                                                    const int32_t* __restrict__ sc, const double* __restrict__ sv,
@@ -70,8 +39,42 @@ __global__ void __launch_bounds__(KBLOCK) spmv64_k(const int32_t* __restrict__ l
     const int gl = (int)(t & (KG - 1));
     double acc = 0.0;
     if (row < n) {
-        acc = range_dot64(sc, sv, x, lo[row], lo[row + 1], gl, acc);
-        acc = range_dot64(sc, sv, x, up[row], up[row + 1], gl, acc);
+        const int32_t l0 = lo[row], l1 = lo[row + 1], u0 = up[row], u1 = up[row + 1];
+        const int32_t nql = l1 > l0 + 4 * gl ? (l1 - l0 - 4 * gl + 4 * KG - 1) / (4 * KG) : 0;
+        const int32_t nqu = u1 > u0 + 4 * gl ? (u1 - u0 - 4 * gl + 4 * KG - 1) / (4 * KG) : 0;
+        const int32_t nq = nql + nqu;
+#pragma unroll 1
+        for (int32_t t0 = 0; t0 < nq; t0 += 2) {
+            int4 c[2];
+            double2 va[2], vb[2];
+            double xv[2][4];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int32_t k = t0 + q;
+                if (k < nq) {
+                    const int32_t p = k < nql ? l0 + 4 * (gl + KG * k) : u0 + 4 * (gl + KG * (k - nql));
+                    c[q] = __ldcs(reinterpret_cast<const int4*>(sc + p));
+                    va[q] = __ldcs(reinterpret_cast<const double2*>(sv + p));
+                    vb[q] = __ldcs(reinterpret_cast<const double2*>(sv + p + 2));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (t0 + q < nq) {
+                    xv[q][0] = x[c[q].x];
+                    xv[q][1] = x[c[q].y];
+                    xv[q][2] = x[c[q].z];
+                    xv[q][3] = x[c[q].w];
+                }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (t0 + q < nq) {
+                    acc = fma(va[q].x, xv[q][0], acc);
+                    acc = fma(va[q].y, xv[q][1], acc);
+                    acc = fma(vb[q].x, xv[q][2], acc);
+                    acc = fma(vb[q].y, xv[q][3], acc);
+                }
+        }
     }
     for (int o = KG / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (row < n && gl == 0) {
