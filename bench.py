@@ -67,7 +67,7 @@ def parse():
                          "c5: Schnakenberg pattern formation on a 4M-point bumpy sphere (ms per time step)")
     ap.add_argument("--c5-steps", type=int, default=100, help="time steps timed in the c5 line")
     ap.add_argument("--c5-size", type=int, default=1 << 22, help="points of the c5 bumpy sphere")
-    ap.add_argument("--batch-problems", type=int, default=16, help="surfaces in the batched measurement of the c2 line")
+    ap.add_argument("--batch-problems", type=int, default=64, help="surfaces in the batched measurement of the c2 line")
     ap.add_argument("--eigs", type=int, default=16, help="shift-invert eigenpairs computed on the 1M sphere (0: none)")
     ap.add_argument("--learned-surfaces", type=int, default=24,
                     help="training surfaces of the learned-correction measurement (0 skips it)")

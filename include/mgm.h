@@ -290,11 +290,17 @@ mgm_status mgm_solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* 
 
 /* A batch of independent problems (one hierarchy each, possibly of different sizes), each with
  * nrhs right-hand sides: problem q solves with H[q], F[q], U[q] (device pointers, layout as in
- * mgm_solve_multi); info (may be NULL) has nprob * nrhs entries, problem-major. Problems run one
- * after another on `stream`, each with its right-hand sides batched. Returns the first failing
- * status (the remaining problems are still solved). */
+ * mgm_solve_multi); the hierarchies must be distinct. info (may be NULL) has nprob * nrhs
+ * entries, problem-major; status_out (may be NULL, HOST) receives each problem's status. The
+ * problems run concurrently: a pool of up to 8 host threads takes them from a shared counter, each
+ * thread driving its problems' solves (right-hand sides batched, the V-cycle one captured graph
+ * launch) on a stream of its own, which first waits for the work already queued on `stream`;
+ * `stream` then waits for all of them, and the call returns once every problem is done. Returns
+ * MGM_OK or the most severe failing status (every problem is still attempted); the error message
+ * names that problem. */
 mgm_status mgm_solve_batched(mgm_hierarchy* const* H, int nprob, const double* const* F, double* const* U, int nrhs,
-                             const mgm_solve_params* sp, mgm_solve_info* info, mgm_stream stream);
+                             const mgm_solve_params* sp, mgm_solve_info* info, mgm_status* status_out,
+                             mgm_stream stream);
 
 /* Eigenpairs of the hierarchy's operator L of smallest magnitude (Sec. 6.1: Arnoldi on the shifted
  * inverse, each application of L^-1 an MGM-preconditioned FGMRES solve with sp). With L = I - D

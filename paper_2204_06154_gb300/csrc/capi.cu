@@ -184,15 +184,9 @@ mgm_status mgm_solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* 
 }
 
 mgm_status mgm_solve_batched(mgm_hierarchy* const* H, int nprob, const double* const* F, double* const* U, int nrhs,
-                             const mgm_solve_params* sp, mgm_solve_info* info, mgm_stream stream) {
-    mgm_status first = MGM_OK;
-    mgm_status st = guarded([&] { REQUIRE(H && F && U && nprob >= 1, "bad argument"); });
-    if (st != MGM_OK) return st;
-    for (int q = 0; q < nprob; ++q) {
-        st = guarded([&] { solve_multi(H[q], nrhs, F[q], U[q], sp, info ? info + (size_t)q * nrhs : nullptr, S(stream)); });
-        if (st != MGM_OK && first == MGM_OK) first = st;
-    }
-    return first;
+                             const mgm_solve_params* sp, mgm_solve_info* info, mgm_status* status_out,
+                             mgm_stream stream) {
+    return guarded([&] { solve_batched(H, nprob, F, U, nrhs, sp, info, status_out, S(stream)); });
 }
 
 mgm_status mgm_eigs(mgm_hierarchy* H, int nev, int b, int s, int max_cycles, double tol, const mgm_solve_params* sp,

@@ -166,6 +166,8 @@ void learned_correct(mgm_hierarchy* H, cudaStream_t s);     // e_0 += correction
 void solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* U, const mgm_solve_params* sp, mgm_solve_info* info,
                  cudaStream_t s);
 void free_multi(mgm_hierarchy* H);
+void solve_batched(mgm_hierarchy* const* H, int nprob, const double* const* F, double* const* U, int nrhs,
+                   const mgm_solve_params* sp, mgm_solve_info* info, mgm_status* status, cudaStream_t s);
 // pattern.cu
 void reaction_rhs(int model, int scheme, int64_t n, const double* u, const double* v, const double* up, const double* vp,
                   const double* prm, double dt, double* ru, double* rv, cudaStream_t s);

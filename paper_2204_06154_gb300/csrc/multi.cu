@@ -8,7 +8,10 @@
 // tests per right-hand side on the host. A column that has converged stops contributing to its
 // solution; a zero right-hand side (padding up to R) is converged from the start.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -18,6 +21,7 @@ namespace mgm {
 
 constexpr int MG = 8;          // lanes per row
 constexpr int MBLOCK = 256;
+constexpr int BATCH_THREADS = 8;  // host threads (and streams) of a batched solve
 
 template <int R, class T>
 struct VecR {
@@ -265,12 +269,25 @@ struct MultiWork {
     Buf<float> Z32;
     Buf<double> Z64;
     Buf<double> zd;  // FP64 copy of an FP32 z_k for the outer product
+    // the R-column V-cycle (b_0 -> e_0 of this workspace), captured once into a graph
+    cudaGraphExec_t vgraph = nullptr;
+    int64_t vgraph_kernels = 0;
+    cudaStream_t cap = nullptr;
+    void drop_graph() {
+        if (vgraph) cudaGraphExecDestroy(vgraph);
+        vgraph = nullptr;
+    }
+    ~MultiWork() {
+        drop_graph();
+        if (cap) cudaStreamDestroy(cap);
+    }
 };
 
 static MultiWork& multi_work(mgm_hierarchy* H, int R, int m) {
     if (!H->multi) H->multi = new MultiWork();
     MultiWork& W = *static_cast<MultiWork*>(H->multi);
     if (W.R == R && W.m >= m) return W;
+    W.drop_graph();
     W.R = R;
     W.m = m;
     W.p = H->p;
@@ -377,6 +394,33 @@ static void vcycle_R(mgm_hierarchy* H, MultiWork& W, cudaStream_t s) {
     }
 }
 
+// the R-column V-cycle as one graph launch (captured on first use; the workspace's buffers are fixed
+// until it is reallocated, which drops the graph)
+template <class T, int R>
+static void vcycle_R_graph(mgm_hierarchy* H, MultiWork& W, cudaStream_t s) {
+    if (!W.vgraph) {
+        if (!W.cap) CK(cudaStreamCreateWithFlags(&W.cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        const int64_t before = thread_launches();
+        CK(cudaStreamBeginCapture(W.cap, cudaStreamCaptureModeThreadLocal));
+        try {
+            vcycle_R<T, R>(H, W, W.cap);
+        } catch (...) {
+            cudaStreamEndCapture(W.cap, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        CK(cudaStreamEndCapture(W.cap, &g));
+        W.vgraph_kernels = thread_launches() - before;
+        note_launch(-W.vgraph_kernels);
+        cudaError_t e = cudaGraphInstantiate(&W.vgraph, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+    }
+    CK(cudaGraphLaunch(W.vgraph, s));
+    note_launch(W.vgraph_kernels);
+}
+
 template <class T, int R>
 static void solve_multi_t(mgm_hierarchy* H, int nrhs, const double* F, double* U, const mgm_solve_params* sp,
                           mgm_solve_info* info, cudaStream_t s) {
@@ -417,7 +461,7 @@ static void solve_multi_t(mgm_hierarchy* H, int nrhs, const double* F, double* U
     auto precond = [&](const double* v, T* z) {
         castR_k<double, T><<<grid_for(nR, 256), 256, 0, s>>>(v, WV<T>::b(W, 0), nR);
         CK_LAUNCH();
-        vcycle_R<T, R>(H, W, s);
+        vcycle_R_graph<T, R>(H, W, s);
         castR_k<T, T><<<grid_for(nR, 256), 256, 0, s>>>(WV<T>::e(W, 0), z, nR);
         CK_LAUNCH();
     };
@@ -600,6 +644,67 @@ void solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* U, const m
         MGM_CASE(8)
     }
 #undef MGM_CASE
+}
+
+// Problems of a batch on a pool of host threads, each driving its problems' solves on a stream of
+// its own: the problems' kernels run concurrently on the device (a small problem alone leaves most
+// of the SMs idle between its dependent launches). The pool takes problems from a shared counter.
+void solve_batched(mgm_hierarchy* const* H, int nprob, const double* const* F, double* const* U, int nrhs,
+                   const mgm_solve_params* sp, mgm_solve_info* info, mgm_status* status, cudaStream_t s) {
+    REQUIRE(H && F && U && sp && nprob >= 1, "bad argument");
+    for (int q = 0; q < nprob; ++q) {
+        REQUIRE(H[q] && F[q] && U[q], "null problem");
+        for (int r = 0; r < q; ++r) REQUIRE(H[r] != H[q], "a hierarchy appears twice in the batch");
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaEvent_t start;
+    CK(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    CK(cudaEventRecord(start, s));  // work of the caller's stream before the batch (F, U) comes first
+    const int nthreads = std::min(nprob, BATCH_THREADS);
+    std::atomic<int> next{0};
+    std::vector<mgm_status> st(nprob, MGM_OK);
+    std::vector<std::string> msg(nprob);
+    std::vector<cudaEvent_t> done(nthreads, nullptr);
+    std::vector<std::thread> pool;
+    std::vector<std::string> setup_err(nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        pool.emplace_back([&, t] {
+            cudaStream_t ws = nullptr;
+            const mgm_status ok = guarded([&] {
+                CK(cudaSetDevice(dev));
+                CK(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+                CK(cudaStreamWaitEvent(ws, start, 0));
+                CK(cudaEventCreateWithFlags(&done[t], cudaEventDisableTiming));
+            });
+            if (ok != MGM_OK) { setup_err[t] = error_message(); return; }
+            for (int q = next++; q < nprob; q = next++) {
+                st[q] = guarded([&] { solve_multi(H[q], nrhs, F[q], U[q], sp, info ? info + (size_t)q * nrhs : nullptr, ws); });
+                if (st[q] != MGM_OK) msg[q] = error_message();
+            }
+            cudaEventRecord(done[t], ws);
+            cudaStreamDestroy(ws);
+        });
+    }
+    for (auto& th : pool) th.join();
+    for (int t = 0; t < nthreads; ++t)
+        if (done[t]) {
+            cudaStreamWaitEvent(s, done[t], 0);
+            cudaEventDestroy(done[t]);
+        }
+    cudaEventDestroy(start);
+    for (int t = 0; t < nthreads; ++t)
+        if (!setup_err[t].empty()) fail(MGM_ERR_CUDA, "batched solve: worker set-up failed: " + setup_err[t]);
+    if (status)
+        for (int q = 0; q < nprob; ++q) status[q] = st[q];
+    // the most severe status of the batch (by code: breakdown, CUDA and OOM above non-convergence)
+    int worst = -1;
+    for (int q = 0; q < nprob; ++q)
+        if (st[q] != MGM_OK && (worst < 0 || st[q] > st[worst])) worst = q;
+    if (worst >= 0) {
+        set_error("problem " + std::to_string(worst) + ": " + msg[worst]);
+        throw Fail{st[worst]};
+    }
 }
 
 void free_multi(mgm_hierarchy* H) {

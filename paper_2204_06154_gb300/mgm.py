@@ -106,7 +106,7 @@ def lib():
         L.mgm_solve.argtypes = [P, P, P, C.POINTER(SolveParams), C.POINTER(SolveInfo), P]
         L.mgm_solve_multi.argtypes = [P, I, P, P, C.POINTER(SolveParams), C.POINTER(SolveInfo), P]
         L.mgm_solve_batched.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), I, C.POINTER(SolveParams),
-                                        C.POINTER(SolveInfo), P]
+                                        C.POINTER(SolveInfo), C.POINTER(C.c_int), P]
         L.mgm_hierarchy_stats_get.argtypes = [P, C.POINTER(HierStats)]
         L.mgm_hierarchy_level.argtypes = [P, I] + [P] * 10 + [P]
         L.mgm_hierarchy_pnnz.argtypes = [P, I, C.POINTER(C.c_int64)]
@@ -635,12 +635,14 @@ def solve_batched(Hs, Fs, krylov="fgmres", restart=50, maxit=200, tol=1e-10):
     up = (C.c_void_p * nprob)(*[U.data_ptr() for U in Us])
     sp = SolveParams(MGM_KRYLOV_FGMRES if krylov == "fgmres" else MGM_KRYLOV_NONE, restart, maxit, tol)
     infos, hists = _multi_infos(nprob * nrhs, maxit)
-    st = lib().mgm_solve_batched(hp, nprob, fp, up, nrhs, C.byref(sp), infos, _stream())
+    status = (C.c_int * nprob)()
+    st = lib().mgm_solve_batched(hp, nprob, fp, up, nrhs, C.byref(sp), infos, status, _stream())
     if st not in (0, 3):
         _check(st)
     out = _info_dicts(infos, hists, st, nprob * nrhs)
     for q in range(nprob * nrhs):
         out[q]["converged"] = infos[q].rel_res <= tol
+        out[q]["status"] = STATUS.get(status[q // nrhs], status[q // nrhs])
     return Us, [out[q * nrhs:(q + 1) * nrhs] for q in range(nprob)]
 
 

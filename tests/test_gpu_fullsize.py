@@ -133,3 +133,43 @@ def test_solve_matches_fp64_path(M, big, hier):
     u64h = H(u64)
     assert np.linalg.norm(f - L64 @ u64h) <= 1.0001e-10 * np.linalg.norm(f)
     assert np.linalg.norm(uh - u64h) <= 1e-8 * np.linalg.norm(u64h)
+
+
+def test_rcm_bitexact_full_size(oracle, big, hier):
+    """Alg. 2's RCM of the 1M-point operator: the GPU's level-0 permutation is the oracle's, bit
+    for bit (start at minimum degree, lowest index; neighbours by increasing degree, index)."""
+    import scipy.sparse as sp
+    L = sp.csr_matrix((H(big["v"]), H(big["ci"]), H(big["rp"])), shape=(N, N))
+    ref = oracle.rcm(L)
+    assert np.array_equal(H(hier.level(0)["perm"]), ref)
+
+
+def test_vcycle_full_size_matches_oracle(oracle, hier):
+    """The timed FP32 V-cycle of the 1M-point hierarchy (seven levels, 33 finest-level colours)
+    against the oracle's cycle (Alg. 3, forward multicolour Gauss-Seidel, FP64) run on the GPU
+    hierarchy's own exported levels: operators, interpolations, colourings and the level-0 RCM
+    order. FP32 tolerance 1e-4 normwise, as at the smaller sizes."""
+    import scipy.sparse as sp
+    st = hier.stats()
+    p = st["p"]
+    assert p == 7 and st["ncolors"][0] >= 25
+    Ho = oracle.Hierarchy()
+    for j in range(p):
+        lv = hier.level(j)
+        n = st["n"][j]
+        Ho.L.append(sp.csr_matrix((H(lv["v"]), H(lv["ci"]), H(lv["rp"])), shape=(n, n)))
+        if j == 0:
+            Ho.perm.append(H(lv["perm"]).astype(np.int32))
+        if j + 1 < p:
+            P = sp.csr_matrix((H(lv["pv"]), H(lv["pci"]), H(lv["prp"])), shape=(n, st["n"][j + 1]))
+            Ho.P.append(P)
+            Ho.R.append(oracle.transpose(P))
+            Ho.colors.append(H(lv["colour"]).astype(np.int32))
+            Ho.ncolors.append(st["ncolors"][j])
+    Ho.lu, Ho.piv = oracle.lu_factor(Ho.L[-1])
+    rng = np.random.default_rng(23)
+    for _ in range(2):
+        r = rng.standard_normal(N)
+        zo = oracle.vcycle(Ho, r)
+        z = H(hier.vcycle(T(r)))
+        assert np.linalg.norm(z - zo) <= 1e-4 * np.linalg.norm(zo)

@@ -542,6 +542,39 @@ def test_solve_batched_uneven_problems(M, oracle):
             assert np.linalg.norm(H(U)[r] - uo) <= 1e-8 * np.linalg.norm(uo)
 
 
+def _gfd_batch(M, sizes, seed):
+    Hs, Fs = [], []
+    for q, N in enumerate(sizes):
+        xq, nq = I.bumpy_sphere(N, seed=seed + q)
+        _, _, rp, ci, v = M.build_stencils(T(xq), T(nq), 25, "gfd", ell=2, mu=1e-3, alpha=4.0, keep_weights=False)
+        Hs.append(M.Hierarchy(T(xq), rp, ci, v, n_min=60, precision="f32"))
+        Fs.append(T(np.random.default_rng(seed + q).standard_normal((3, N))))
+    return Hs, Fs
+
+
+def test_solve_batched_concurrent_matches_single(M):
+    """Eleven problems of different sizes, more than the batch's worker threads: each problem's
+    solutions are those of its own many-right-hand-side solve, bit for bit (the same kernels in
+    the same order, on another stream), and every status is MGM_OK."""
+    Hs, Fs = _gfd_batch(M, [2000 + 700 * q for q in range(11)], 50)
+    Us, infos = M.solve_batched(Hs, Fs, tol=1e-10)
+    for Hq, F, U, inf in zip(Hs, Fs, Us, infos):
+        U1, inf1 = M.solve_multi(Hq, F, tol=1e-10)
+        assert all(i["converged"] and i["status"] == "MGM_OK" for i in inf)
+        assert [i["iters"] for i in inf] == [i["iters"] for i in inf1]
+        assert torch.equal(U, U1)
+
+
+def test_solve_batched_reports_each_problem(M):
+    """Per-problem statuses: with one iteration allowed only the problem with zero right-hand
+    sides converges; the call returns MGM_ERR_NOT_CONVERGED for the batch."""
+    Hs, Fs = _gfd_batch(M, [3000, 3500, 4000], 70)
+    Fs[1] = torch.zeros_like(Fs[1])
+    Us, infos = M.solve_batched(Hs, Fs, tol=1e-10, maxit=1)
+    assert [inf[0]["status"] for inf in infos] == ["MGM_ERR_NOT_CONVERGED", "MGM_OK", "MGM_ERR_NOT_CONVERGED"]
+    assert float(Us[1].abs().max()) == 0.0
+
+
 def test_config1_exact_solution(M, oracle, ico5):
     """The small workload as specified: icosahedral level-5 sphere (10,242 points), PHS r^3 +
     degree 2, n = 30, -Lap u + u = 21 Y_4^3 (so u = Y_4^3), FP64 throughout, N_min = 125 (levels
