@@ -269,6 +269,8 @@ def bench_ours(a, rank, world, local_rank):
         res["batched"] = bench_batched(a.batch_problems, dev)
         if a.learned_surfaces > 0:
             res["learned"] = bench_learned(a.learned_surfaces, a.learned_eval_size, dev)
+    if a.c5_steps > 0:
+        res["pattern"] = bench_pattern(a.c5_size, a.c5_steps, 3)
     return res
 
 
@@ -420,16 +422,18 @@ def bench_eigs(torch, H, nev):
             "max_rel_dev_from_l(l+1)": round(max(abs(v - e) / max(e, 1) for v, e in zip(lap, exact)), 5)}
 
 
-def bench_pattern(N, steps, warmup):
+def bench_pattern(N, steps, warmup, host_steps=20):
     """Schnakenberg reaction-diffusion (Sec. 6.2's scheme class; gamma = 1, a = 0.1, b = 0.9) on a
     seeded bumpy sphere: IMEX Euler, dt = 0.01, D = (1, 10), FP32 cycles, FGMRES to 1e-8 from the
-    previous step. Setup (stencils, two hierarchies) and the timed steps are reported apart."""
+    previous step. Every step is one CUDA graph launch (fused right-hand sides, both solves driven on
+    the device); the host-driven stepping is timed beside it on a few steps. Setup (stencils, two
+    hierarchies) and the timed steps are reported apart."""
     import torch
     from paper_2204_06154_gb300 import inputs as I
     from paper_2204_06154_gb300.pattern import ReactionDiffusion
     x, nrm = I.bumpy_sphere(N, seed=3)
     X, NR = torch.from_numpy(x).cuda(), torch.from_numpy(nrm).cuda()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     e[0].record()
     rd = ReactionDiffusion(X, NR, "schnakenberg", (1.0, 0.1, 0.9), 1.0, 10.0, 0.01, scheme="euler", n=60, ell=3,
                            n_min=250, precision="f32")
@@ -439,15 +443,28 @@ def bench_pattern(N, steps, warmup):
     us, vs = 1.0, 0.9
     u0 = torch.from_numpy(us + 0.01 * rng.uniform(-1, 1, N)).cuda()
     v0 = torch.from_numpy(vs + 0.01 * rng.uniform(-1, 1, N)).cuda()
-    u, v, _ = rd.run(u0, v0, warmup, tol=1e-8)
+    u, v, _ = rd.run_graph(u0, v0, warmup, tol=1e-8)
     e[2].record()
-    u, v, its = rd.run(u, v, steps, tol=1e-8)
+    ug, vg, its = rd.run_graph(u, v, steps, tol=1e-8)
     e[3].record()
-    e[3].synchronize()
+    # the same first steps from the same state: graph-driven and host-driven (the solves get
+    # cheaper as the pattern settles, so only equal steps compare)
+    _, _, its_g = rd.run_graph(u, v, host_steps, tol=1e-8)
+    e[4].record()
+    _, _, its_h = rd.run(u, v, host_steps, tol=1e-8)
+    e[5].record()
+    e[5].synchronize()
+    u = ug
     ms = e[2].elapsed_time(e[3])
+    ms_g = e[3].elapsed_time(e[4])
+    ms_h = e[4].elapsed_time(e[5])
     iu = [a for a, _ in its]
     iv = [b for _, b in its]
-    return {"N": N, "setup_ms": round(e[0].elapsed_time(e[1]), 1), "steps": steps, "ms_per_step": round(ms / steps, 3),
+    return {"N": N, "setup_ms": round(e[0].elapsed_time(e[1]), 1), "steps": steps,
+            "ms_per_step": round(ms / steps, 3), "graph_launches_per_step": 1,
+            "first_steps": {"steps": host_steps, "graph_ms_per_step": round(ms_g / host_steps, 3),
+                            "host_driven_ms_per_step": round(ms_h / host_steps, 3),
+                            "iters_graph": sum(a + b for a, b in its_g), "iters_host": sum(a + b for a, b in its_h)},
             "iters_u": {"max": max(iu), "mean": round(sum(iu) / len(iu), 2)},
             "iters_v": {"max": max(iv), "mean": round(sum(iv) / len(iv), 2)},
             "u_range": [round(float(u.min()), 4), round(float(u.max()), 4)]}
@@ -641,6 +658,7 @@ def main():
         "batched": res.get("batched"),
         "learned": res.get("learned"),
         "eigs": res.get("eigs"),
+        "pattern": res.get("pattern"),
         "clocks": res["clocks"],
     }
     if not a.no_cpu_baseline and world == 1:

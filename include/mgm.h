@@ -51,7 +51,12 @@ typedef enum {
 
 enum { MGM_RBF_FD = 0, MGM_GFD = 1 };              /* discretisation (Sec. 2.2 / 2.3) */
 enum { MGM_F64 = 0, MGM_F32 = 1 };                  /* V-cycle arithmetic / vector dtype */
-enum { MGM_KRYLOV_FGMRES = 0, MGM_KRYLOV_NONE = 1, MGM_KRYLOV_BICGSTAB = 2 }; /* outer method (Sec. 4.6 / Sec. 5.1) */
+enum { MGM_KRYLOV_FGMRES = 0, MGM_KRYLOV_NONE = 1, MGM_KRYLOV_BICGSTAB = 2, MGM_KRYLOV_FGMRES_GRAPH = 3 };
+/* outer method (Sec. 4.6 / Sec. 5.1). MGM_KRYLOV_FGMRES_GRAPH: the same FGMRES(restart) driven on the
+   device by one CUDA graph (restart cycles and Arnoldi steps are WHILE conditional nodes; rotations
+   and convergence tests run in kernels), no host synchronisation until the call returns; for
+   hierarchies without a learned correction or constraint, V-cycles, sweep modes 0, 4 or 5 without
+   streamed levels and restart <= 255 -- otherwise it runs as MGM_KRYLOV_FGMRES. */
 
 /* Discretisation parameters (Sec. 2; Table 1). */
 typedef struct {
@@ -330,6 +335,19 @@ mgm_status mgm_eigs(mgm_hierarchy* H, int nev, int b, int s, int max_cycles, dou
 mgm_status mgm_reaction_rhs(int model, int scheme, int64_t N, const double* u, const double* v, const double* u_prev,
                             const double* v_prev, const double* prm, double dt, double* ru, double* rv,
                             mgm_stream stream);
+
+/* IMEX Euler time steps of the same system (Sec. 6.2's scheme class with explicit reactions; the
+ * stepping of config 5), entirely on the device: step n solves (I - dt Du Lap) u^{n+1} = u^n + dt
+ * f(u^n, v^n) and (I - dt Dv Lap) v^{n+1} = v^n + dt g(u^n, v^n), each by FGMRES preconditioned by
+ * the V-cycle and warm started from u^n, v^n. Hu, Hv: distinct hierarchies of I - dt Du D and I - dt
+ * Dv D on the same points (admitting MGM_KRYLOV_FGMRES_GRAPH). Each step is one launch of a CUDA
+ * graph holding the fused right-hand sides, both device-driven solves (restart, maxit, tol of sp;
+ * sp->krylov ignored) and the copies in and out; the host only launches the steps and synchronises
+ * once at the end. u, v: DEVICE, N doubles, caller order, advanced in place. iters_out: HOST, 2 *
+ * steps ints or NULL (iterations of the u and v solves of each step). MGM_ERR_NOT_CONVERGED when a
+ * solve missed tol (all steps are still taken). prm as for mgm_reaction_rhs (HOST). */
+mgm_status mgm_reaction_steps(mgm_hierarchy* Hu, mgm_hierarchy* Hv, int model, const double* prm, double dt, double* u,
+                              double* v, int steps, const mgm_solve_params* sp, int* iters_out, mgm_stream stream);
 enum { MGM_RD_GIERER_MEINHARDT = 0, MGM_RD_SCHNAKENBERG = 1 };
 enum { MGM_RD_EULER = 1, MGM_RD_SBDF2 = 2 };
 

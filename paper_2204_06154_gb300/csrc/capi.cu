@@ -197,6 +197,11 @@ mgm_status mgm_eigs(mgm_hierarchy* H, int nev, int b, int s, int max_cycles, dou
     });
 }
 
+mgm_status mgm_reaction_steps(mgm_hierarchy* Hu, mgm_hierarchy* Hv, int model, const double* prm, double dt, double* u,
+                              double* v, int steps, const mgm_solve_params* sp, int* iters_out, mgm_stream stream) {
+    return guarded([&] { reaction_steps(Hu, Hv, model, prm, dt, u, v, steps, sp, iters_out, S(stream)); });
+}
+
 mgm_status mgm_reaction_rhs(int model, int scheme, int64_t N, const double* u, const double* v, const double* u_prev,
                             const double* v_prev, const double* prm, double dt, double* ru, double* rv,
                             mgm_stream stream) {

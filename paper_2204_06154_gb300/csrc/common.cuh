@@ -226,6 +226,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, uns
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// off for the calling thread while it captures kernels into a graph that does not admit programmatic
+// dependencies (the bodies of conditional nodes); launches are then stream-ordered as usual
+bool& pdl_off();
+
 template <class... KArgs, class... Args>
 inline void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -237,7 +241,7 @@ inline void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, cu
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_off() ? 0 : 1;
     CK(cudaLaunchKernelEx(&cfg, kern, args...));
     CK_LAUNCH();
 }

@@ -799,7 +799,7 @@ void colour_sweep(mgm_hierarchy* H, Level& L, int mode, cudaStream_t s) {
         at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = pdl_off() ? 0 : 1;
         void* args[] = {(void*)&a};
         CK(cudaLaunchKernelExC(&cfg, colour_kernel<T>(mode, L.sG), args));
         CK_LAUNCH();

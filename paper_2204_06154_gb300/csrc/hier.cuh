@@ -113,6 +113,11 @@ struct mgm_hierarchy {
     mgm::Buf<double> Z64;
     mgm::Buf<double> ydev;
     double* hhost = nullptr;    // pinned
+    // FGMRES driven on the device (graph with WHILE conditional nodes; krylov.cu)
+    cudaGraphExec_t sgraph = nullptr;
+    int sgraph_m = 0, sgraph_maxit = 0;
+    mgm::Buf<double> gsd, ghist;  // scalars, Hessenberg, rotations, y; estimates per iteration
+    mgm::Buf<int> gsi;            // k, iterations, convergence flag, maxit, estimates recorded
     void* multi = nullptr;      // workspace of the many-right-hand-side solve (multi.cu)
     // learned correction after the V-cycle (learned.cu); level-0 solve order throughout
     int ln = 0;                          // stencil size of the attached features (0: not attached)
@@ -136,6 +141,7 @@ namespace mgm {
 void vcycle_core(mgm_hierarchy* H, cudaStream_t s);          // b_0 -> e_0 (graph if captured)
 void vcycle_plain(mgm_hierarchy* H, cudaStream_t s);         // the same without the learned correction
 void vcycle_prepare(mgm_hierarchy* H);                       // capture the graph
+void vcycle_enqueue(mgm_hierarchy* H, cudaStream_t s);       // the plain cycle's launches (for captures)
 void invalidate_graphs(mgm_hierarchy* H);
 float time_level_smoothing(mgm_hierarchy* H, int j, int reps, cudaStream_t s);
 void load_input(mgm_hierarchy* H, const void* src, int src_dtype, const int32_t* gather, cudaStream_t s);
@@ -145,6 +151,9 @@ void check_device_error(mgm_hierarchy* H, cudaStream_t s);
 int barrier_timeout_probe(int nblocks, unsigned long long limit, cudaStream_t s);
 void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
 // krylov.cu
+bool solve_graph_supported(const mgm_hierarchy* H, const mgm_solve_params* sp);
+void reaction_steps(mgm_hierarchy* Hu, mgm_hierarchy* Hv, int model, const double* prm, double dt, double* u, double* v,
+                    int steps, const mgm_solve_params* sp, int* iters_out, cudaStream_t s);
 void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
 void solve(mgm_hierarchy* H, const double* f, double* u, const mgm_solve_params* sp, mgm_solve_info* info,
            cudaStream_t s);

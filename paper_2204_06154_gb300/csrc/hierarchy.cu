@@ -770,6 +770,7 @@ mgm_hierarchy::~mgm_hierarchy() {
     mgm::free_multi(this);
     if (vgraph) cudaGraphExecDestroy(vgraph);
     if (lgraph) cudaGraphExecDestroy(lgraph);
+    if (sgraph) cudaGraphExecDestroy(sgraph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (hhost) cudaFreeHost(hhost);
 }

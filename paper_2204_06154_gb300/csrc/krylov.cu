@@ -399,15 +399,519 @@ void profile_spmv(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_
     out->spmv_bytes = (L.nlow + L.nupp) * 12 + n * (4 + 8 + 8 + (f32 ? 4 : 8));
 }
 
+// ------------------------------ FGMRES driven on the device -------------------------------------
+// The same right-preconditioned FGMRES(m) as the host-driven loop below, with no host
+// synchronisation: the restart cycle and the Arnoldi step are the bodies of two nested WHILE
+// conditional nodes of one CUDA graph; one-thread kernels apply the Givens rotations, test
+// convergence and set the loop conditions (cudaGraphSetConditional); the Arnoldi index k lives in
+// device memory and the kernels that depend on it read it there. Launched once per solve (or as a
+// child of a larger graph, e.g. a time step), it leaves the iteration count, the last true relative
+// residual and the estimates in device memory.
+enum { GS_FN = 0, GS_TOL, GS_BETA, GS_REL, GS_EST, GS_INV, GS_G };  // doubles; then g (m+1), cs, sn (m), Hm ((m+1) m), y (m)
+enum { GI_K = 0, GI_IT, GI_CONV, GI_MAXIT, GI_NH };                 // ints
+
+__device__ __forceinline__ double* gs_g(double* d) { return d + GS_G; }
+__device__ __forceinline__ double* gs_cs(double* d, int m) { return d + GS_G + (m + 1); }
+__device__ __forceinline__ double* gs_sn(double* d, int m) { return d + GS_G + (m + 1) + m; }
+__device__ __forceinline__ double* gs_hm(double* d, int m) { return d + GS_G + (m + 1) + 2 * m; }
+__device__ __forceinline__ double* gs_y(double* d, int m) { return d + GS_G + (m + 1) + 2 * m + (m + 1) * m; }
+
+__global__ void gs_start_k(const double* hb, double* d, int* iv, cudaGraphConditionalHandle ho) {
+    double fn = sqrt(hb[0]);
+    iv[GI_IT] = 0;
+    iv[GI_K] = 0;
+    iv[GI_NH] = 0;
+    if (!isfinite(fn)) { iv[GI_CONV] = 2; cudaGraphSetConditional(ho, 0); return; }
+    if (fn == 0.0) fn = 1.0;
+    d[GS_FN] = fn;
+    iv[GI_CONV] = 0;
+    cudaGraphSetConditional(ho, 1);
+}
+// start of a restart cycle from r = f - L u (beta = |r|): converged, out of iterations, or g = beta e1
+__global__ void gs_cycle_k(const double* hb, double* d, int* iv, double* hist, int m, cudaGraphConditionalHandle ho,
+                           cudaGraphConditionalHandle hi) {
+    const double beta = sqrt(hb[0]);
+    const double rel = beta / d[GS_FN];
+    d[GS_REL] = rel;
+    iv[GI_K] = 0;
+    if (iv[GI_NH] == 0) hist[iv[GI_NH]++] = rel;
+    bool stop = false;
+    if (!isfinite(rel)) { iv[GI_CONV] = 2; stop = true; }
+    else if (rel <= d[GS_TOL]) { iv[GI_CONV] = 1; stop = true; }
+    else if (iv[GI_IT] >= iv[GI_MAXIT]) stop = true;
+    if (stop) {
+        cudaGraphSetConditional(ho, 0);
+        cudaGraphSetConditional(hi, 0);
+        return;
+    }
+    double* g = gs_g(d);
+    g[0] = beta;
+    for (int i = 1; i <= m; ++i) g[i] = 0.0;
+    d[GS_INV] = 1.0 / beta;
+    cudaGraphSetConditional(hi, 1);
+}
+// Arnoldi column k from h = h1 + h2 (two Gram-Schmidt passes) and |w|: rotations, estimate, next k
+__global__ void gs_arnoldi_k(const double* hb, double* d, int* iv, double* hist, int m, cudaGraphConditionalHandle hi) {
+    const int k = iv[GI_K], k1 = k + 1;
+    double* Hm = gs_hm(d, m);
+    double* cs = gs_cs(d, m);
+    double* sn = gs_sn(d, m);
+    double* g = gs_g(d);
+    const double* h1 = hb;
+    const double* h2 = hb + (m + 1);
+    for (int i = 0; i < k1; ++i) Hm[(size_t)i * m + k] = h1[i] + h2[i];
+    const double hn = sqrt(hb[2 * (m + 1)]);
+    Hm[(size_t)k1 * m + k] = hn;
+    if (!isfinite(hn)) {
+        iv[GI_CONV] = 2;
+        cudaGraphSetConditional(hi, 0);
+        return;
+    }
+    d[GS_INV] = hn > 0.0 ? 1.0 / hn : 0.0;
+    for (int i = 0; i < k; ++i) {
+        const double a = Hm[(size_t)i * m + k], b = Hm[(size_t)(i + 1) * m + k];
+        Hm[(size_t)i * m + k] = cs[i] * a + sn[i] * b;
+        Hm[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
+    }
+    const double a = Hm[(size_t)k * m + k], b = Hm[(size_t)k1 * m + k];
+    const double rr = sqrt(a * a + b * b);
+    cs[k] = rr == 0.0 ? 1.0 : a / rr;
+    sn[k] = rr == 0.0 ? 0.0 : b / rr;
+    Hm[(size_t)k * m + k] = rr;
+    Hm[(size_t)k1 * m + k] = 0.0;
+    g[k1] = -sn[k] * g[k];
+    g[k] = cs[k] * g[k];
+    const int it = ++iv[GI_IT];
+    const double est = fabs(g[k1]) / d[GS_FN];
+    d[GS_EST] = est;
+    hist[iv[GI_NH]++] = est;
+    iv[GI_K] = k1;
+    cudaGraphSetConditional(hi, (k1 < m && est > d[GS_TOL] && hn != 0.0 && it < iv[GI_MAXIT]) ? 1 : 0);
+}
+// y = H(0:k, 0:k)^-1 g(0:k) (back substitution); a breakdown ends the restart loop
+__global__ void gs_solve_y_k(double* d, const int* iv, int m, cudaGraphConditionalHandle ho) {
+    const int k = iv[GI_K];
+    const double* Hm = gs_hm(d, m);
+    const double* g = gs_g(d);
+    double* y = gs_y(d, m);
+    for (int i = k - 1; i >= 0; --i) {
+        double acc = g[i];
+        for (int j = i + 1; j < k; ++j) acc -= Hm[(size_t)i * m + j] * y[j];
+        y[i] = acc / Hm[(size_t)i * m + i];
+    }
+    if (iv[GI_CONV] == 2) cudaGraphSetConditional(ho, 0);
+}
+// vector kernels indexed by the device-resident k
+template <class T>
+__global__ void gs_loadv_k(const double* V, int64_t nv, const int* kp, T* b0, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b0[i] = (T)V[(int64_t)*kp * nv + i];
+}
+template <class T>
+__global__ void gs_storez_k(const T* e0, T* Z, int64_t nv, const int* kp, double* zd, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T v = e0[i];
+    Z[(int64_t)*kp * nv + i] = v;
+    zd[i] = (double)v;
+}
+__global__ void gs_scale0_k(double* V, const double* inv, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) V[i] = V[i] * *inv;
+}
+__global__ void gs_scalek_k(const double* w, double* V, int64_t nv, const int* kp, const double* inv, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) V[(int64_t)*kp * nv + i] = w[i] * *inv;
+}
+// partial[b * m1 + t] = block b's part of V_t . w, t < k + 1 (k from the device)
+__global__ void __launch_bounds__(256) gs_multidot_k(const double* __restrict__ V, int64_t ldv, const int* kp, int m1,
+                                                     const double* __restrict__ w, int64_t n, double* partial) {
+    __shared__ double red[8];
+    const int k1 = *kp + 1;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    for (int t = 0; t < k1; ++t) {
+        const double* v = V + (int64_t)t * ldv;
+        double acc = 0.0;
+        for (int64_t i = b0 + threadIdx.x; i < b1; i += 256) acc = fma(v[i], w[i], acc);
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int q = 0; q < 8; ++q) s += red[q];
+            partial[(int64_t)blockIdx.x * m1 + t] = s;
+        }
+        __syncthreads();
+    }
+}
+__global__ void gs_reduce_k(const double* partial, int nb, const int* kp, int m1, double* h) {
+    const int t = blockIdx.x;
+    if (t > *kp) return;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) acc += partial[(int64_t)b * m1 + t];
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) h[t] = acc;
+}
+__global__ void gs_multiaxpy_k(const double* __restrict__ V, int64_t ldv, const int* kp, const double* __restrict__ h,
+                               double* w, int64_t n) {
+    __shared__ double sh[256];
+    const int k1 = *kp + 1;
+    for (int t = threadIdx.x; t < k1; t += blockDim.x) sh[t] = h[t];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = w[i];
+    for (int t = 0; t < k1; ++t) acc = fma(-sh[t], V[(int64_t)t * ldv + i], acc);
+    w[i] = acc;
+}
+template <class TZ>
+__global__ void gs_update_x_k(const TZ* __restrict__ Z, int64_t ldz, const int* kp, const double* __restrict__ y,
+                              double* x, int64_t n) {
+    __shared__ double sy[256];
+    const int k = *kp;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) sy[t] = y[t];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = x[i];
+    for (int t = 0; t < k; ++t) acc = fma(sy[t], (double)Z[(int64_t)t * ldz + i], acc);
+    x[i] = acc;
+}
+
+bool solve_graph_supported(const mgm_hierarchy* H, const mgm_solve_params* sp) {
+    if (H->bordered || H->learned || H->cycle != MGM_CYCLE_V || H->sweep_mode == MGM_SWEEP_BARRIER ||
+        H->sweep_mode == MGM_SWEEP_FLAGS || sp->krylov != MGM_KRYLOV_FGMRES_GRAPH || sp->restart > 255)
+        return false;
+    for (int j = 0; j + 1 < H->p; ++j)
+        if (H->lv[j].stream) return false;  // cooperative launches have no place in conditional bodies
+    return true;
+}
+
+// the graph a capture on cs is building
+static cudaGraph_t captured_graph(cudaStream_t cs) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, nullptr, nullptr, nullptr));
+    REQUIRE(st == cudaStreamCaptureStatusActive && g, "no active capture");
+    return g;
+}
+// During a capture on cs: a WHILE node on handle h after the capture's current dependencies; its
+// body graph is returned, to be filled by a capture on another stream.
+static cudaGraph_t add_while(cudaStream_t cs, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+    CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return p.conditional.phGraph_out[0];
+}
+
+// State of the device-driven solve (sized for any restart up to 255 and `maxit` iterations, so
+// that graphs built on it stay valid)
+static void ensure_graph_state(mgm_hierarchy* H, int maxit) {
+    constexpr int MMAX = 255;
+    if (!H->gsd.get()) {
+        H->gsd.alloc(GS_G + (MMAX + 1) + 2 * MMAX + (size_t)(MMAX + 1) * MMAX + MMAX);
+        H->gsi.alloc(8);
+    }
+    if (H->ghist.n < (size_t)maxit + 2) {
+        if (H->sgraph) { cudaGraphExecDestroy(H->sgraph); H->sgraph = nullptr; }
+        H->ghist.alloc((size_t)std::max(maxit + 2, 256));
+    }
+    if (!H->zd.get()) H->zd.alloc(H->N);
+}
+
+// Appends the device-driven FGMRES(m) of H to the capture running on c1 (f and u in H->f, H->u,
+// solve order):
+//   |f|, start; WHILE (restart loop) { r = f - L u, |r|, cycle start, v_0 = r/|r|,
+//   WHILE (Arnoldi) { z_k = M v_k, w = L z_k, CGS2, |w|, rotations, v_{k+1} }, y, u += Z y }
+// The loop bodies are captured on two auxiliary streams. The V-cycle keeps its programmatic
+// dependent launches when `pdl` (the caller retries without them where a driver does not admit
+// them inside conditional bodies); the solve's own kernels are plain launches.
+static void enqueue_solve_graph(mgm_hierarchy* H, int m, cudaStream_t c1, bool pdl) {
+    const int64_t n = H->N;
+    const bool f32 = H->precision == MGM_F32;
+    const int m1 = m + 1;
+    if (H->part.n < (size_t)DOT_BLOCKS * m1) H->part.alloc((size_t)DOT_BLOCKS * m1);
+    double* d = H->gsd.get();
+    int* iv = H->gsi.get();
+    double* hist = H->ghist.get();
+    double* hb = H->hbuf.get();
+    double* V = H->V.get();
+    double* w = H->w.get();
+    double* part = H->part.get();
+    Level& L0 = H->lv[0];
+    const unsigned gb = grid_for(n, 256);
+    cudaStream_t c2 = nullptr, c3 = nullptr;
+    CK(cudaStreamCreateWithFlags(&c2, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c3, cudaStreamNonBlocking));
+    auto dots1 = [&](const double* a, const double* b, double* out, cudaStream_t s) {  // out = a . b
+        multidot_k<<<DOT_BLOCKS, 256, 0, s>>>(a, n, 1, b, n, part);
+        CK_LAUNCH();
+        reduce_partials_k<<<1, 32, 0, s>>>(part, DOT_BLOCKS, 1, out);
+        CK_LAUNCH();
+    };
+    const bool pdl_was = pdl_off();
+    pdl_off() = true;
+    try {
+        dots1(H->f.get(), H->f.get(), hb, c1);
+        cudaGraphConditionalHandle ho, hi;
+        CK(cudaGraphConditionalHandleCreate(&ho, captured_graph(c1), 0, cudaGraphCondAssignDefault));
+        gs_start_k<<<1, 1, 0, c1>>>(hb, d, iv, ho);
+        CK_LAUNCH();
+        cudaGraph_t body_o = add_while(c1, ho);
+        // ---- restart cycle: r = f - L u, beta, start of the cycle, Arnoldi loop, update of u
+        CK(cudaStreamBeginCaptureToGraph(c2, body_o, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        spmv64_k<true><<<grid_for(n * KG, KBLOCK), KBLOCK, 0, c2>>>(L0.lo.get(), L0.up.get(), L0.sc.get(), L0.sv64.get(),
+                                                                  L0.diag64.get(), H->u.get(), H->f.get(), V, n);
+        CK_LAUNCH();
+        dots1(V, V, hb, c2);
+        CK(cudaGraphConditionalHandleCreate(&hi, captured_graph(c2), 0, cudaGraphCondAssignDefault));
+        gs_cycle_k<<<1, 1, 0, c2>>>(hb, d, iv, hist, m, ho, hi);
+        CK_LAUNCH();
+        gs_scale0_k<<<gb, 256, 0, c2>>>(V, d + GS_INV, n);
+        CK_LAUNCH();
+        cudaGraph_t body_i = add_while(c2, hi);
+        // ---- one Arnoldi step: z_k = M v_k, w = L z_k, two Gram-Schmidt passes, |w|, rotations
+        CK(cudaStreamBeginCaptureToGraph(c3, body_i, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        if (f32) gs_loadv_k<float><<<gb, 256, 0, c3>>>(V, n, iv + GI_K, L0.b32.get(), n);
+        else gs_loadv_k<double><<<gb, 256, 0, c3>>>(V, n, iv + GI_K, L0.b64.get(), n);
+        CK_LAUNCH();
+        pdl_off() = !pdl;
+        vcycle_enqueue(H, c3);
+        pdl_off() = true;
+        if (f32) gs_storez_k<float><<<gb, 256, 0, c3>>>(L0.e32.get(), H->Z32.get(), n, iv + GI_K, H->zd.get(), n);
+        else gs_storez_k<double><<<gb, 256, 0, c3>>>(L0.e64.get(), H->Z64.get(), n, iv + GI_K, H->zd.get(), n);
+        CK_LAUNCH();
+        spmv64_k<false><<<grid_for(n * KG, KBLOCK), KBLOCK, 0, c3>>>(L0.lo.get(), L0.up.get(), L0.sc.get(), L0.sv64.get(),
+                                                                    L0.diag64.get(), H->zd.get(), nullptr, w, n);
+        CK_LAUNCH();
+        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice: h1, then h2
+            double* h = hb + pass * m1;
+            gs_multidot_k<<<DOT_BLOCKS, 256, 0, c3>>>(V, n, iv + GI_K, m1, w, n, part);
+            CK_LAUNCH();
+            gs_reduce_k<<<m1, 32, 0, c3>>>(part, DOT_BLOCKS, iv + GI_K, m1, h);
+            CK_LAUNCH();
+            gs_multiaxpy_k<<<gb, 256, 0, c3>>>(V, n, iv + GI_K, h, w, n);
+            CK_LAUNCH();
+        }
+        dots1(w, w, hb + 2 * m1, c3);
+        gs_arnoldi_k<<<1, 1, 0, c3>>>(hb, d, iv, hist, m, hi);
+        CK_LAUNCH();
+        gs_scalek_k<<<gb, 256, 0, c3>>>(w, V, n, iv + GI_K, d + GS_INV, n);
+        CK_LAUNCH();
+        CK(cudaStreamEndCapture(c3, &body_i));
+        // ---- after the Arnoldi loop: y, u += Z y
+        gs_solve_y_k<<<1, 1, 0, c2>>>(d, iv, m, ho);
+        CK_LAUNCH();
+        double* y = d + GS_G + (m + 1) + 2 * m + (size_t)(m + 1) * m;
+        if (f32) gs_update_x_k<float><<<gb, 256, 0, c2>>>(H->Z32.get(), n, iv + GI_K, y, H->u.get(), n);
+        else gs_update_x_k<double><<<gb, 256, 0, c2>>>(H->Z64.get(), n, iv + GI_K, y, H->u.get(), n);
+        CK_LAUNCH();
+        CK(cudaStreamEndCapture(c2, &body_o));
+    } catch (...) {
+        pdl_off() = pdl_was;
+        cudaStreamCaptureStatus st;
+        for (cudaStream_t c : {c3, c2})
+            if (cudaStreamIsCapturing(c, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(c, &g);
+            }
+        cudaStreamDestroy(c2);
+        cudaStreamDestroy(c3);
+        throw;
+    }
+    pdl_off() = pdl_was;
+    cudaStreamDestroy(c2);
+    cudaStreamDestroy(c3);
+}
+
+static void build_solve_graph_pdl(mgm_hierarchy* H, int m, int maxit, bool pdl) {
+    ensure_graph_state(H, maxit);
+    cudaStream_t c1 = nullptr;
+    CK(cudaStreamCreateWithFlags(&c1, cudaStreamNonBlocking));
+    cudaGraph_t top = nullptr;
+    const int64_t before = thread_launches();
+    try {
+        CK(cudaStreamBeginCapture(c1, cudaStreamCaptureModeThreadLocal));
+        enqueue_solve_graph(H, m, c1, pdl);
+        CK(cudaStreamEndCapture(c1, &top));
+    } catch (...) {
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(c1, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaStreamEndCapture(c1, &top);
+            if (top) cudaGraphDestroy(top);
+        }
+        cudaStreamDestroy(c1);
+        throw;
+    }
+    note_launch(-(thread_launches() - before));
+    if (H->sgraph) cudaGraphExecDestroy(H->sgraph);
+    H->sgraph = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&H->sgraph, top, 0);
+    cudaGraphDestroy(top);
+    cudaStreamDestroy(c1);
+    CK(e);
+    H->sgraph_m = m;
+    H->sgraph_maxit = maxit;
+}
+
+// with the V-cycle's programmatic launches first; without them if that graph is refused
+static void build_solve_graph(mgm_hierarchy* H, int m, int maxit) {
+    if (guarded([&] { build_solve_graph_pdl(H, m, maxit, true); }) == MGM_OK) return;
+    (void)cudaGetLastError();
+    build_solve_graph_pdl(H, m, maxit, false);
+}
+
+// one solve through the device-driven graph (f, u already in H->f, H->u)
+static void run_solve_graph(mgm_hierarchy* H, const mgm_solve_params* sp, cudaStream_t s) {
+    const int m = sp->restart;
+    ensure_graph_state(H, std::max(sp->maxit, 1));
+    if (!H->sgraph || H->sgraph_m != m) build_solve_graph(H, m, std::max(sp->maxit, 1));
+    const double tol = sp->tol;
+    const int maxit = sp->maxit;
+    CK(cudaMemcpyAsync(H->gsd.get() + GS_TOL, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(H->gsi.get() + GI_MAXIT, &maxit, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaGraphLaunch(H->sgraph, s));
+    note_launch(1);
+}
+
+// ------------------------------ reaction-diffusion steps as graphs ----------------------------
+// iterations of both solves of step t, and whether both converged
+__global__ void rd_record_k(const int* gu, const int* gv, int* rec, int* step, int* failed) {
+    const int t = *step;
+    rec[2 * t] = gu[GI_IT];
+    rec[2 * t + 1] = gv[GI_IT];
+    if (gu[GI_CONV] != 1 || gv[GI_CONV] != 1) *failed = 1;
+    *step = t + 1;
+}
+
+// IMEX Euler steps of the reaction-diffusion system (Sec. 6.2's scheme class; the time-stepping of
+// config 5): each step one launch of a graph holding the fused right-hand sides, the gathers into
+// the two hierarchies' solve orders (warm start from the current state), both device-driven FGMRES
+// solves and the scatters back. The host launches the graph `steps` times and synchronises once.
+static cudaGraphExec_t reaction_step_graph(mgm_hierarchy* Hu, mgm_hierarchy* Hv, int model, const double* prm, double dt,
+                                           double* u, double* v, double* ru, double* rv, int* rec, int* step, int* failed,
+                                           int m, bool pdl);
+
+void reaction_steps(mgm_hierarchy* Hu, mgm_hierarchy* Hv, int model, const double* prm, double dt, double* u, double* v,
+                    int steps, const mgm_solve_params* sp, int* iters_out, cudaStream_t s) {
+    REQUIRE(Hu && Hv && Hu != Hv && prm && u && v && sp && steps >= 0, "bad argument");
+    REQUIRE(Hu->N == Hv->N, "the two hierarchies must have the same points");
+    REQUIRE(sp->restart >= 1 && sp->restart <= 200 && sp->maxit >= 1 && sp->tol >= 0.0, "bad solve parameters");
+    mgm_solve_params gp = *sp;
+    gp.krylov = MGM_KRYLOV_FGMRES_GRAPH;
+    REQUIRE(solve_graph_supported(Hu, &gp) && solve_graph_supported(Hv, &gp),
+            "hierarchies must admit the device-driven solve (see MGM_KRYLOV_FGMRES_GRAPH)");
+    if (steps == 0) return;
+    const int64_t n = Hu->N;
+    const int m = sp->restart;
+    for (mgm_hierarchy* H : {Hu, Hv}) {
+        ensure_workspace(H, m);
+        vcycle_prepare(H);
+        ensure_graph_state(H, sp->maxit);
+        CK(cudaMemcpyAsync(H->gsd.get() + GS_TOL, &sp->tol, sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(H->gsi.get() + GI_MAXIT, &sp->maxit, sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    Temp<double> ru(n, s), rv(n, s);
+    Temp<int> rec((size_t)2 * steps + 2, s);
+    CK(cudaMemsetAsync(rec.get(), 0, sizeof(int) * (2 * (size_t)steps + 2), s));
+    int* step = rec.get() + 2 * steps;
+    int* failed = step + 1;
+    cudaGraphExec_t ex = nullptr;
+    if (guarded([&] { ex = reaction_step_graph(Hu, Hv, model, prm, dt, u, v, ru.get(), rv.get(), rec.get(), step, failed, m,
+                                               true); }) != MGM_OK) {
+        (void)cudaGetLastError();
+        ex = reaction_step_graph(Hu, Hv, model, prm, dt, u, v, ru.get(), rv.get(), rec.get(), step, failed, m, false);
+    }
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < steps; ++t) {
+        e = cudaGraphLaunch(ex, s);
+        if (e != cudaSuccess) break;
+        note_launch(1);
+    }
+    std::vector<int> h((size_t)2 * steps + 2);
+    cudaError_t e2 = cudaMemcpyAsync(h.data(), rec.get(), sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(ex);
+    CK(e);
+    CK(e2);
+    CK(e3);
+    for (mgm_hierarchy* H : {Hu, Hv})
+        if (H->persistent) check_device_error(H, s);
+    if (iters_out)
+        for (int t = 0; t < 2 * steps; ++t) iters_out[t] = h[t];
+    if (h[2 * steps + 1]) fail(MGM_ERR_NOT_CONVERGED, "a reaction-diffusion solve did not reach tol (or broke down)");
+}
+
+static cudaGraphExec_t reaction_step_graph(mgm_hierarchy* Hu, mgm_hierarchy* Hv, int model, const double* prm, double dt,
+                                           double* u, double* v, double* ru, double* rv, int* rec, int* step, int* failed,
+                                           int m, bool pdl) {
+    const int64_t n = Hu->N;
+    const unsigned gb = grid_for(n, 256);
+    cudaStream_t c1 = nullptr;
+    CK(cudaStreamCreateWithFlags(&c1, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    const int64_t before = thread_launches();
+    try {
+        CK(cudaStreamBeginCapture(c1, cudaStreamCaptureModeThreadLocal));
+        reaction_rhs(model, MGM_RD_EULER, n, u, v, nullptr, nullptr, prm, dt, ru, rv, c1);
+        gather64_k<<<gb, 256, 0, c1>>>(ru, Hu->ord_caller.get(), Hu->f.get(), n);
+        CK_LAUNCH();
+        gather64_k<<<gb, 256, 0, c1>>>(u, Hu->ord_caller.get(), Hu->u.get(), n);
+        CK_LAUNCH();
+        gather64_k<<<gb, 256, 0, c1>>>(rv, Hv->ord_caller.get(), Hv->f.get(), n);
+        CK_LAUNCH();
+        gather64_k<<<gb, 256, 0, c1>>>(v, Hv->ord_caller.get(), Hv->u.get(), n);
+        CK_LAUNCH();
+        enqueue_solve_graph(Hu, m, c1, pdl);
+        enqueue_solve_graph(Hv, m, c1, pdl);
+        scatter64_k<<<gb, 256, 0, c1>>>(Hu->u.get(), Hu->ord_caller.get(), u, n);
+        CK_LAUNCH();
+        scatter64_k<<<gb, 256, 0, c1>>>(Hv->u.get(), Hv->ord_caller.get(), v, n);
+        CK_LAUNCH();
+        rd_record_k<<<1, 1, 0, c1>>>(Hu->gsi.get(), Hv->gsi.get(), rec, step, failed);
+        CK_LAUNCH();
+        CK(cudaStreamEndCapture(c1, &g));
+    } catch (...) {
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(c1, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaStreamEndCapture(c1, &g);
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaStreamDestroy(c1);
+        throw;
+    }
+    note_launch(-(thread_launches() - before));
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(c1);
+    CK(e);
+    return ex;
+}
+
 void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_params* sp, mgm_solve_info* info,
            cudaStream_t s) {
     REQUIRE(H && f_in && u_io && sp, "null argument");
-    REQUIRE(sp->krylov == MGM_KRYLOV_FGMRES || sp->krylov == MGM_KRYLOV_NONE || sp->krylov == MGM_KRYLOV_BICGSTAB,
+    REQUIRE(sp->krylov == MGM_KRYLOV_FGMRES || sp->krylov == MGM_KRYLOV_NONE || sp->krylov == MGM_KRYLOV_BICGSTAB ||
+                sp->krylov == MGM_KRYLOV_FGMRES_GRAPH,
             "unknown krylov method");
     REQUIRE(sp->maxit >= 0 && sp->tol >= 0.0, "maxit and tol must be >= 0");
-    REQUIRE(sp->krylov != MGM_KRYLOV_FGMRES || (sp->restart >= 1 && sp->restart <= 200), "restart must be in [1, 200]");
-    REQUIRE(!H->bordered || sp->krylov == MGM_KRYLOV_FGMRES, "a constrained hierarchy is solved with FGMRES");
-    const int m = sp->krylov == MGM_KRYLOV_FGMRES ? sp->restart : sp->krylov == MGM_KRYLOV_BICGSTAB ? 8 : 1;
+    const bool fgmres = sp->krylov == MGM_KRYLOV_FGMRES || sp->krylov == MGM_KRYLOV_FGMRES_GRAPH;
+    REQUIRE(!fgmres || (sp->restart >= 1 && sp->restart <= 200), "restart must be in [1, 200]");
+    REQUIRE(!H->bordered || fgmres, "a constrained hierarchy is solved with FGMRES");
+    const bool on_graph = sp->krylov == MGM_KRYLOV_FGMRES_GRAPH && solve_graph_supported(H, sp);
+    const int m = fgmres ? sp->restart : sp->krylov == MGM_KRYLOV_BICGSTAB ? 8 : 1;
     ensure_workspace(H, m);
     vcycle_prepare(H);
     const int64_t n = H->N;
@@ -446,7 +950,19 @@ void solve(mgm_hierarchy* H, const double* f_in, double* u_io, const mgm_solve_p
             ++H->learned_fallbacks;
         }
     };
-    if (sp->krylov == MGM_KRYLOV_BICGSTAB) {
+    if (on_graph) {
+        run_solve_graph(H, sp, s);
+        int ivh[8];
+        double dh[GS_G];
+        to_host(ivh, H->gsi.get(), 8, s);
+        to_host(dh, H->gsd.get(), (size_t)GS_G, s);
+        it = ivh[GI_IT];
+        rel = dh[GS_REL];
+        hist.resize(std::max(0, ivh[GI_NH]));
+        to_host(hist.data(), H->ghist.get(), hist.size(), s);
+        status = ivh[GI_CONV] == 1 ? MGM_OK : ivh[GI_CONV] == 2 ? MGM_ERR_BREAKDOWN : MGM_ERR_NOT_CONVERGED;
+        if (ivh[GI_CONV] == 2 && !std::isfinite(fn)) fail(MGM_ERR_INVALID_ARG, "right-hand side is not finite");
+    } else if (sp->krylov == MGM_KRYLOV_BICGSTAB) {
         H->learned_active = false;  // BiCGSTAB needs a linear preconditioner
         status = bicgstab(H, op, sp, fn, hist, it, rel);
     } else if (sp->krylov == MGM_KRYLOV_NONE) {

@@ -712,6 +712,17 @@ void alloc_work(mgm_hierarchy* H) {
     }
 }
 
+// the plain cycle's launches on s (into a capture the caller runs)
+void vcycle_enqueue(mgm_hierarchy* H, cudaStream_t s) {
+    if (H->precision == MGM_F32) vcycle_launches<float>(H, s);
+    else vcycle_launches<double>(H, s);
+}
+
+bool& pdl_off() {
+    static thread_local bool off = false;
+    return off;
+}
+
 static cudaGraphExec_t capture(mgm_hierarchy* H, bool learned, int64_t* kernels) {
     cudaGraph_t g = nullptr;
     const int64_t before = thread_launches();

@@ -18,7 +18,7 @@ _lib = None
 MGM_RBF_FD, MGM_GFD = 0, 1
 MGM_F64, MGM_F32 = 0, 1
 MGM_KRYLOV_FGMRES, MGM_KRYLOV_NONE, MGM_KRYLOV_BICGSTAB = 0, 1, 2
-_KRYLOV = {"fgmres": MGM_KRYLOV_FGMRES, "none": MGM_KRYLOV_NONE, "bicgstab": MGM_KRYLOV_BICGSTAB}
+_KRYLOV = {"fgmres": MGM_KRYLOV_FGMRES, "none": MGM_KRYLOV_NONE, "bicgstab": MGM_KRYLOV_BICGSTAB, "fgmres_graph": 3}
 
 STATUS = {0: "MGM_OK", 1: "MGM_ERR_INVALID_ARG", 2: "MGM_ERR_SINGULAR_STENCIL", 3: "MGM_ERR_NOT_CONVERGED",
           4: "MGM_ERR_BREAKDOWN", 5: "MGM_ERR_TIMEOUT", 6: "MGM_ERR_CUDA", 7: "MGM_ERR_OOM", 8: "MGM_ERR_UNSUPPORTED"}
@@ -66,7 +66,7 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
            "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
            "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs", "mgm_reaction_rhs",
-           "mgm_sweep_config_set", "mgm_sweep_config_get", "mgm_autotune", "mgm_profile_level"]
+           "mgm_sweep_config_set", "mgm_sweep_config_get", "mgm_autotune", "mgm_profile_level", "mgm_reaction_steps"]
 
 
 _SCHEDULES = ["launch", "stream", "resident", "colour"]
@@ -143,6 +143,8 @@ def lib():
         L.mgm_eigs.argtypes = [P, I, I, I, I, C.c_double, C.POINTER(SolveParams), C.c_uint64, P, P, P, P,
                                C.POINTER(C.c_int), C.POINTER(C.c_int), P]
         L.mgm_reaction_rhs.argtypes = [I, I, I64, P, P, P, P, C.POINTER(C.c_double), C.c_double, P, P, P]
+        L.mgm_reaction_steps.argtypes = [P, P, I, C.POINTER(C.c_double), C.c_double, P, P, I, C.POINTER(SolveParams),
+                                         C.POINTER(C.c_int), P]
         L.mgm_status_string.restype = C.c_char_p
         L.mgm_last_error_message.restype = C.c_char_p
         L.mgm_last_error_row.restype = C.c_int64
@@ -237,6 +239,18 @@ def reaction_rhs(model, scheme, u, v, prm, dt, u_prev=None, v_prev=None, out=Non
                                   _p(u_prev) if u_prev is not None else None, _p(v_prev) if v_prev is not None else None,
                                   p3, float(dt), _p(ru), _p(rv), _stream()))
     return ru, rv
+
+
+def reaction_steps(Hu, Hv, model, prm, dt, u, v, steps, tol=1e-8, restart=50, maxit=200):
+    """IMEX Euler steps on the device, each one graph launch (see mgm_reaction_steps); u and v (CUDA
+    float64, caller order) are advanced in place. Returns the (u, v) iteration counts per step."""
+    u = _dev(u, torch.float64, "u"); v = _dev(v, torch.float64, "v")
+    p3 = (C.c_double * 3)(*[float(t) for t in prm])
+    sp = SolveParams(MGM_KRYLOV_FGMRES, restart, maxit, tol)
+    its = (C.c_int * (2 * max(steps, 1)))()
+    _check(lib().mgm_reaction_steps(Hu._h, Hv._h, _RD_MODEL[model], p3, float(dt), _p(u), _p(v), steps, C.byref(sp),
+                                    its, _stream()))
+    return [(its[2 * t], its[2 * t + 1]) for t in range(steps)]
 
 
 def gradient_weights(xyz, nrm, idx, k=1, ell=2):
