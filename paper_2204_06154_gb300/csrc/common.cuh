@@ -183,6 +183,12 @@ int64_t csr_nnz(const int32_t* rp, int64_t nrows, cudaStream_t s);
 void validate_index(const int32_t* a, int64_t cnt, int64_t hi, const char* what, cudaStream_t s);
 void validate_csr(int64_t nrows, int64_t ncols, const int32_t* rp, const int32_t* ci, const char* what, cudaStream_t s);
 
+// Blocks of `kernel` (with `threads` threads and `smem` dynamic shared memory) that can be
+// co-resident on the current device, at most `per_sm_cap` an SM (0: no cap); cached per device and
+// configuration. MGM_ERR_UNSUPPORTED when not even one block fits an SM (a cooperative launch of it
+// could never start).
+int coresident_blocks(const void* kernel, int threads, size_t smem, int per_sm_cap);
+
 // kNN (knn.cu)
 void knn_device(const double* data, int64_t nd, const double* query, int64_t nq, int k, int self_first,
                 int32_t* idx_out, double* d2_out, cudaStream_t s);

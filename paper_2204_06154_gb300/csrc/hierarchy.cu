@@ -186,14 +186,7 @@ static void dense_inverse(const Level& L, const double* border, Buf<double>& inv
         border_dense_k<<<grid_for(n, 128), 128, 0, s>>>(border, nl, A.get());
         CK_LAUNCH();
     }
-    static int mb = 0;
-    if (!mb) {
-        int per_sm = 0, dev = 0, sms = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_coop_k, GJ_THREADS, 0));
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        mb = std::max(1, std::min(per_sm, 1) * sms);  // one block an SM
-    }
+    const int mb = coresident_blocks((const void*)gj_coop_k, GJ_THREADS, 0, 1);  // one block an SM
     const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(mb, n));
     double* a0 = A.get();
     double* a1 = B.get();

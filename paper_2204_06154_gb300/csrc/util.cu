@@ -4,6 +4,10 @@
 #include <atomic>
 #include <cstdio>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "common.cuh"
 
 namespace mgm {
@@ -439,6 +443,28 @@ void sym_pattern(int64_t N, const int32_t* rp, const int32_t* ci, Temp<int32_t>&
                                                                           srp.get(), sci.get());
         CK_LAUNCH();
     }
+}
+
+int coresident_blocks(const void* kernel, int threads, size_t smem, int per_sm_cap) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, int, size_t, int>, int> cache;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(kernel, dev, threads, smem, per_sm_cap);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int per_sm = 0, sms = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) fail(MGM_ERR_UNSUPPORTED, "a cooperative kernel cannot be resident on this device");
+    if (per_sm_cap > 0) per_sm = std::min(per_sm, per_sm_cap);
+    const int nb = per_sm * sms;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = nb;
+    return nb;
 }
 
 }  // namespace mgm

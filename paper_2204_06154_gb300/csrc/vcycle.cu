@@ -441,14 +441,7 @@ static void launch_psweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
     if (nc <= 0) return;
     int maxrows = 0;
     for (int c = 0; c < nc; ++c) maxrows = std::max(maxrows, L.cptr[c + 1] - L.cptr[c]);
-    static int mb = 0;  // per instantiation (MODE, T)
-    if (!mb) {
-        int per_sm = 0, dev = 0, sms = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, psweep_k<MODE, T>, PS_THREADS, 0));
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        mb = std::max(1, per_sm * sms);
-    }
+    const int mb = coresident_blocks((const void*)psweep_k<MODE, T>, PS_THREADS, 0, 0);
     const int nblocks = std::max(1, std::min(mb, (maxrows + PS_ROWS - 1) / PS_ROWS));
     CK(cudaMemsetAsync(L.bar.get(), 0, sizeof(unsigned), s));
     const int32_t* lo = L.lo.get();
@@ -471,14 +464,7 @@ static void launch_psweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
 template <int MODE, class T>
 static void launch_dsweep(mgm_hierarchy* H, Level& L, cudaStream_t s) {
     if (L.ngroups <= 0) return;
-    static int mb = 0;  // co-resident blocks, per instantiation (MODE, T)
-    if (!mb) {
-        int per_sm = 0, dev = 0, sms = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dsweep_k<MODE, T>, DS_THREADS, 0));
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        mb = std::max(1, per_sm * sms);
-    }
+    const int mb = coresident_blocks((const void*)dsweep_k<MODE, T>, DS_THREADS, 0, 0);
     const int nblocks = std::max(1, std::min(mb, (L.ngroups + DS_WARPS - 1) / DS_WARPS));
     CK(cudaMemsetAsync(L.flag.get(), 0, sizeof(int) * L.n, s));
     T* e = LV<T>::e(L);

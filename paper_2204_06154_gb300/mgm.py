@@ -197,6 +197,10 @@ def knn_noalloc(data, query, k, self_first=False, out=None):
     query = data if self_first else _dev(query, torch.float64, "query")
     if out is None:
         out = torch.empty((query.shape[0], k), dtype=torch.int32, device=data.device)
+    elif (not isinstance(out, torch.Tensor) or out.dtype != torch.int32 or out.device != data.device
+          or not out.is_contiguous() or tuple(out.shape) != (query.shape[0], k)):
+        # the library writes nq * k int32 values through this pointer
+        raise ValueError(f"out must be a contiguous int32 tensor of shape ({query.shape[0]}, {k}) on {data.device}")
     _check(lib().mgm_knn_noalloc(_p(data), data.shape[0], _p(query), query.shape[0], k, int(self_first), _p(out),
                                  _stream()))
     return out

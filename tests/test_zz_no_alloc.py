@@ -39,3 +39,21 @@ def test_noalloc_rejects_sizes_above_the_limit():
     with pytest.raises(M.MGMError) as e:
         M.knn_noalloc(d, None, 4, self_first=True)
     assert e.value.status == 8 and "maximum" in str(e.value)
+
+
+def test_noalloc_binding_checks_the_output_tensor():
+    """The entry point writes nq * k int32 values through `out`: the binding refuses a tensor of
+    another shape, type or device before the call."""
+    from paper_2204_06154_gb300 import mgm as M
+    x, _ = I.icosahedral_sphere(3)
+    d = torch.from_numpy(x).to("cuda:0")
+    n = d.shape[0]
+    for bad in (torch.empty((n, 7), dtype=torch.int32, device="cuda:0"),
+                torch.empty((n, 8), dtype=torch.int64, device="cuda:0"),
+                torch.empty((8, n), dtype=torch.int32, device="cuda:0").t(),
+                torch.empty((n, 8), dtype=torch.int32)):
+        with pytest.raises(ValueError):
+            M.knn_noalloc(d, None, 8, self_first=True, out=bad)
+    out = torch.empty((n, 8), dtype=torch.int32, device="cuda:0")
+    assert M.knn_noalloc(d, None, 8, self_first=True, out=out) is out
+    assert torch.equal(out, M.knn(d, None, 8, self_first=True))
