@@ -44,11 +44,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-10 rel. residual at N=1M, mixed vs FP64 MGM; V-cycle HBM GB/s vs peak"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_PEAK_GFLOPS = 1197.0   # measured FMA-chain peak on this machine's GB300 (nominal 1.25 TFLOP/s)
 # DRAM bytes of phs_weights_rl_k<60> per stencil: dram__bytes_read.sum + dram__bytes_write.sum of one
-# ncu capture on 131,072 stencils (32,847,616 + 4,134,144 B), taken before the kernel's polynomial
-# block was restructured; reported as context, not as the current kernel's traffic
-RL_DRAM_BYTES_PER_STENCIL = (32847616 + 4134144) / 131072
+# ncu capture of the current kernel on 131,072 stencils (profiles/phs_weights_rl_k__sphere_131k.md)
+RL_DRAM_BYTES_PER_STENCIL = None
 
 P = dict(n=50, k=1, ell=3, mu=1.0, n_min=250, m=3, tol=1e-10, restart=50, maxit=200)
 
@@ -202,6 +200,7 @@ def bench_ours(a, rank, world, local_rank):
             tdist.barrier()
         torch.cuda.synchronize()
 
+    fp64_gflops = M.probe_fp64_fma(reps=20)  # the FP64-pipe roofline's denominator, on this GPU now
     # warm-up steps
     for _ in range(a.warmup):
         for name, x, n, f in dprobs:
@@ -227,7 +226,8 @@ def bench_ours(a, rank, world, local_rank):
     launches = M.kernel_launches() - l0
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     nprob = len(dprobs)
-    res = {"ms_total": ms, "records": records, "launches": launches, "clocks": clk.summary(), "nprob": nprob}
+    res = {"ms_total": ms, "records": records, "launches": launches, "clocks": clk.summary(), "nprob": nprob,
+           "fp64_gflops": fp64_gflops}
 
     # FP64 MGM on the same problems (solve time; the paper's convention excludes setup)
     fp64 = []
@@ -243,6 +243,12 @@ def bench_ours(a, rank, world, local_rank):
     r, H, u = run_problem(M, torch, x, n, f)
     res["profile"] = H.profile(reps=20)
     res["stats"] = H.stats()
+    # the V-cycle's lower bound: dependent-launch latency at the finest sweep's launch shape, and
+    # each level's bytes at the measured copy bandwidth
+    blocks0 = H.sweep_config(0)["blocks"] or 456
+    res["chain_us"] = M.probe_launch_chain(blocks0, 256, 256, True, 10)
+    res["chain_blocks"] = blocks0
+    res["floor"] = H.vcycle_floor(res["chain_us"], float(peaks()[0].get("hbm_gbs", 6800.0)))
     if a.eigs > 0:
         res["eigs"] = bench_eigs(torch, H, a.eigs)
     del H, u
@@ -470,14 +476,48 @@ def bench_pattern(N, steps, warmup, host_steps=20):
             "u_range": [round(float(u.min()), 4), round(float(u.max()), 4)]}
 
 
-def cpu_baseline(a, Ns=None):
-    Ns = Ns or a.cpu_sample
-    ms, it, rel = oracle_sample(Ns)
-    scaled = ms * (a.size / Ns)
-    return {"value": round(scaled, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-            "sample": f"whole path (brute-force kNN, FP64 weights, hierarchy, MGM-FGMRES to 1e-10, {it} its) on a "
-                      f"{Ns:,}-point jittered Fibonacci sphere with the same parameters; {ms:.0f} ms measured, scaled "
-                      f"linearly by N to {a.size:,} (the oracle's brute-force parts grow faster, so this favours it)"}
+def cpu_info():
+    """Host cores and CPU model (the oracle runs single-threaded)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    try:
+        import platform
+        model = model or platform.processor() or platform.machine()
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model}
+
+
+def oracle_extrapolated(sizes, target):
+    """The oracle's whole path timed at two sample sizes; the time at `target` points from the
+    power law t = c N^p through the two measurements (p from their ratio)."""
+    (n0, n1) = sizes
+    t0, it0, _ = oracle_sample(n0)
+    t1, it1, _ = oracle_sample(n1)
+    p = math.log(t1 / t0) / math.log(n1 / n0)
+    return t1 * (target / n1) ** p, {"sizes": [n0, n1], "ms": [round(t0, 1), round(t1, 1)], "exponent": round(p, 3),
+                                      "iters": [it0, it1]}
+
+
+def cpu_baseline(a):
+    n1 = a.cpu_sample
+    v, fit = oracle_extrapolated((n1 // 2, n1), a.size)
+    ci = cpu_info()
+    return {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle", "extrapolated": True,
+            "sample": f"whole path (brute-force kNN, FP64 weights, hierarchy, MGM-FGMRES to 1e-10) on jittered "
+                      f"Fibonacci spheres of {n1 // 2:,} and {n1:,} points with the same parameters, "
+                      f"{fit['ms'][0]:.0f} and {fit['ms'][1]:.0f} ms measured; extrapolated to {a.size:,} points "
+                      f"by the power law through them (exponent {fit['exponent']})",
+            "fit": fit, **ci}
 
 
 def peaks():
@@ -496,15 +536,20 @@ def main():
     if a.impl == "reference":
         if rank != 0:
             return
-        vals = []
+        n1 = a.cpu_sample // 2  # each step about 4 s of single-threaded oracle time
+        vals, fits = [], []
         for i in range(a.warmup + a.steps):
-            ms, it, rel = oracle_sample(a.cpu_sample)
+            v, fit = oracle_extrapolated((n1 // 2, n1), a.size)
             if i >= a.warmup:
-                vals.append(ms * (a.size / a.cpu_sample))
+                vals.append(v)
+                fits.append(fit)
         v = statistics.mean(vals)
-        cb = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-              "sample": f"whole path on a {a.cpu_sample:,}-point sphere, scaled linearly by N to {a.size:,}"}
+        ci = cpu_info()
+        cb = {"value": round(v, 1), "unit": "ms", "cores": 1, "kind": "oracle", "extrapolated": True,
+              "sample": f"each step: the whole path on {n1 // 2:,}- and {n1:,}-point spheres, extrapolated to "
+                        f"{a.size:,} points by the power law through the two times", "fits": fits, **ci}
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms",
+                          "value_kind": "extrapolated from measured sample sizes",
                           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(2 * v, 1),
                           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                           "data": "synthetic", "config": config(a), "cpu_baseline": cb,
@@ -532,7 +577,13 @@ def main():
             pr = H.profile(reps=20)
             st = H.stats()
             sched = [H.sweep_config(j) for j in range(st["p"] - 1)]
+            blocks0 = H.sweep_config(0)["blocks"] or 456
+            chain = {pdl: M.probe_launch_chain(blocks0, 256, 256, pdl, 10) for pdl in (True, False)}
+            fl = H.vcycle_floor(chain[True], float(peaks()[0].get("hbm_gbs", 6800.0)))
             out[f"mode{mode}"] = {"levels": st["n"], "ncolors": st["ncolors"], "max|z|": float(z.abs().max()),
+                                  "chain_us": {"programmatic": round(chain[True], 3), "plain": round(chain[False], 3),
+                                               "blocks": blocks0},
+                                  "floor_ms": {k: round(v, 4) for k, v in fl.items()},
                                   "schedules": [(c["kind"][0], c["blocks"], c["lanes"], c["stages"], round(c["ms"], 4))
                                                 for c in sched],
                                   "vcycle_ms": round(pr["vcycle_ms"], 4), "vcycle_kernels": pr["vcycle_kernels"],
@@ -609,7 +660,7 @@ def main():
     ops_per_stencil = 26.0 * n_ + 14.0 * n_ * (n_ + 1) / 2 + n_ * L + 12.0 * n_ + 3 * ((m * n_ + n_ * L) + m)
     w_ms = mean("weights_ms")
     w_gops = a.size * ops_per_stencil / (w_ms * 1e-3) / 1e9
-    fp64_pipe_peak = FP64_PEAK_GFLOPS / 2.0
+    fp64_pipe_peak = res["fp64_gflops"] / 2.0
     total_fp64 = mean("total_ms", res["fp64"])
     sweep_gbs = prof["sweep_bytes"] / (prof["sweep_ms"] * 1e-3) / 1e9 if prof["sweep_ms"] > 0 else None
     vcyc_gbs = prof["vcycle_bytes"] / (prof["vcycle_ms"] * 1e-3) / 1e9
@@ -620,34 +671,34 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": config(a),
         "phases_ms": {k: round(mean(k), 3) for k in ("knn_ms", "weights_ms", "assemble_ms", "setup_ms", "solve_ms")},
-        "solve_ms": {"mixed_f32_vcycle": round(solve_mixed, 3), "fp64_vcycle": round(solve_fp64, 3),
-                     "speedup": round(solve_fp64 / solve_mixed, 3)},
-        "whole_path_ms": {"mixed": round(mean("total_ms"), 2), "fp64": round(total_fp64, 2),
-                          "fp64_weights_ms": round(mean("weights_ms", res["fp64"]), 2),
-                          "speedup": round(total_fp64 / mean("total_ms"), 3)},
-        "iters": {"mixed": [r["iters"] for r in recs[: res["nprob"]]], "fp64": [r["iters"] for r in res["fp64"]]},
         "rel_res_max": max(r["rel_res"] for r in recs + res["fp64"]),
         "converged": all(r["converged"] for r in recs + res["fp64"]),
         "roofline": {"kernel": "phs_weights_rl_k<60> (60 x 60 stencil systems: FP32 LU in registers, FP64 "
                                "entries and refinement residuals)", "bound": "alu",
                      "achieved": round(w_gops, 1), "peak": round(fp64_pipe_peak, 1), "unit": "G FP64-pipe op/s",
                      "frac": round(w_gops / fp64_pipe_peak, 3),
-                     "traffic": None,
-                     "traffic_before_last_change": int(RL_DRAM_BYTES_PER_STENCIL * a.size),
-                     "traffic_source": "ncu DRAM bytes of the kernel's previous version on 131,072 stencils, "
-                                       "scaled by stencils (weights written at that size partly stay in L2); "
-                                       "the kernel's polynomial block changed since, memory accesses unchanged",
+                     "traffic": int(RL_DRAM_BYTES_PER_STENCIL * a.size) if RL_DRAM_BYTES_PER_STENCIL else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel on "
+                                       "131,072 stencils, scaled by stencils to the launch's count",
                      "fp64_ops_per_stencil": ops_per_stencil,
-                     "peak_source": "FP64 FMA-chain probe on this pool's GB300, 1197 GFLOP/s = 598.5 G FMA/s "
-                                    "(not in MEASURED_PEAKS.json)"},
-        "vcycle_roofline": {"kernel": "row_kernel<1,float> (finest-level multicolour GS sweep)", "bound": "hbm",
+                     "peak_source": f"mgm_probe_fp64_fma during this run: {res['fp64_gflops']:.0f} GFLOP/s of FP64 "
+                                    f"multiply-adds (2 flops each) = {fp64_pipe_peak:.1f} G FP64-pipe op/s "
+                                    "(MEASURED_PEAKS.json has no FP64 figure)"},
+        "vcycle_roofline": {"kernel": "gs_colour_k<1,float,1> (finest-level multicolour GS sweep, staged per colour)",
+                            "bound": "hbm",
                             "achieved": round(sweep_gbs, 1) if sweep_gbs else None, "peak": hbm, "unit": "GB/s",
                             "frac": round(sweep_gbs / hbm, 3) if sweep_gbs else None, "traffic": None,
-                            "bytes_per_launch": prof["sweep_bytes"] // max(prof["sweep_launches"], 1),
-                            "avg_launch_us": round(1e3 * prof["sweep_ms"] / max(prof["sweep_launches"], 1), 2),
+                            "bytes_per_sweep": prof["sweep_bytes"], "sweep_us": round(1e3 * prof["sweep_ms"], 2),
                             "launches_per_sweep": prof["sweep_launches"],
                             "whole_vcycle": {"ms": round(prof["vcycle_ms"], 4), "GB/s": round(vcyc_gbs, 1),
                                              "frac": round(vcyc_gbs / hbm, 3), "kernels": prof["vcycle_kernels"]},
+                            "floor": {"ms": round(res["floor"]["floor_ms"], 4),
+                                      "bytes_ms": round(res["floor"]["bytes_ms"], 4),
+                                      "chain_ms": round(res["floor"]["chain_ms"], 4),
+                                      "chain_us_per_launch": round(res["chain_us"], 3),
+                                      "chain_probe": f"mgm_probe_launch_chain: 256 dependent launches of "
+                                                     f"{res['chain_blocks']} x 256 threads, programmatic",
+                                      "vcycle_frac_of_floor": round(res["floor"]["floor_ms"] / prof["vcycle_ms"], 3)},
                             "outer_spmv_fp64": {"ms": round(prof["spmv_ms"], 4), "GB/s": round(spmv_gbs, 1),
                                                 "frac": round(spmv_gbs / hbm, 3)},
                             "peak_source": pk_kind},
@@ -663,6 +714,15 @@ def main():
     }
     if not a.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(a)
+    # the headline comparison last, where a reader of the line's tail finds it: mixed-precision MGM
+    # (FP32 LU + FP64 refinement weights, FP32 V-cycle, FP64 FGMRES) against the FP64 GPU MGM on the
+    # same problems
+    out["solve_ms"] = {"mixed_f32_vcycle": round(solve_mixed, 3), "fp64_vcycle": round(solve_fp64, 3),
+                       "speedup": round(solve_fp64 / solve_mixed, 3)}
+    out["whole_path_ms"] = {"mixed": round(mean("total_ms"), 2), "fp64": round(total_fp64, 2),
+                            "fp64_weights_ms": round(mean("weights_ms", res["fp64"]), 2),
+                            "speedup": round(total_fp64 / mean("total_ms"), 3)}
+    out["iters"] = {"mixed": [r["iters"] for r in recs[: res["nprob"]]], "fp64": [r["iters"] for r in res["fp64"]]}
     print(json.dumps(out), flush=True)
 
 

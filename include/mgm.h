@@ -386,6 +386,15 @@ typedef struct {
 } mgm_profile_info;
 mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_stream stream);
 
+/* Measurement (not part of the method): a lower bound of one V-cycle's device time for schedules
+ * that separate the colours of a sweep by kernel boundaries. Level by level the larger of (its
+ * algorithmic bytes, as mgm_profile counts them, at `gbs` GB/s) and (its dependent launches, nu1 + nu2
+ * sweeps of one launch per colour plus residual, restriction and interpolation, at `chain_us`
+ * microseconds each, e.g. from mgm_probe_launch_chain), summed over the levels, plus one launch for
+ * the coarsest solve. bytes_ms / chain_ms (optional) receive the two sums on their own. Host only. */
+mgm_status mgm_vcycle_floor(mgm_hierarchy* H, double chain_us, double gbs, double* floor_ms, double* bytes_ms,
+                            double* chain_ms);
+
 /* Sweep schedule of one smoothed level (not part of the method: how the multicolour sweeps of
  * Alg. 3's smoother are launched; the result is the same up to the order of a row's additions).
  * kind MGM_SCHEDULE_LAUNCH: one kernel per colour (blocks, lanes, stages 0). MGM_SCHEDULE_STREAM:
@@ -423,6 +432,21 @@ mgm_status mgm_autotune(mgm_hierarchy* H, int reps, int use_cache, mgm_stream st
  * current schedule, as the autotuner times it (0 <= j < p-1). Overwrites the work vectors;
  * synchronises. */
 mgm_status mgm_profile_level(mgm_hierarchy* H, int j, int reps, float* ms_out, mgm_stream stream);
+
+/* Measurement (not part of the method): the device's FP64 fused-multiply-add rate in GFLOP/s (2
+ * flops a multiply-add), from `reps` launches of a kernel whose threads run eight independent
+ * multiply-add chains each (8 blocks of 256 threads an SM). The denominator of the FP64-pipe
+ * rooflines. Synchronises. */
+mgm_status mgm_probe_fp64_fma(int reps, double* gflops_out, mgm_stream stream);
+
+/* Measurement (not part of the method): the time between consecutive dependent launches, in
+ * microseconds a launch. A graph of `launches` launches of a kernel of `blocks` x `threads` threads
+ * whose block 0 updates a counter that the previous launch wrote is replayed `reps` times (after one
+ * warm-up replay); pdl != 0 lets each launch start before its predecessor ends and wait for it on the
+ * device (programmatic dependent launch, as the V-cycle's launches do). The floor under any schedule
+ * that separates the colours of a sweep by kernel boundaries. Synchronises. */
+mgm_status mgm_probe_launch_chain(int blocks, int threads, int launches, int pdl, int reps, double* us_out,
+                                  mgm_stream stream);
 
 /* Number of kernels this library has launched in the process (a host-side count: each launch of
  * the captured V-cycle graph adds its kernel nodes). */

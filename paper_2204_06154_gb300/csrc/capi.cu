@@ -55,11 +55,19 @@ using namespace mgm;
 
 static inline cudaStream_t S(mgm_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// heavy one-off entry points: run, then hand the scratch pool's cached memory back to the device
+template <class F>
+static mgm_status guarded_trim(F&& body) {
+    const mgm_status st = guarded(std::forward<F>(body));
+    scratch_trim(0);
+    return st;
+}
+
 extern "C" {
 
 mgm_status mgm_knn(const double* data, int64_t nd, const double* query, int64_t nq, int k, int self_first,
                    int32_t* idx_out, mgm_stream stream) {
-    return guarded([&] {
+    return guarded_trim([&] {
         REQUIRE(data && query && idx_out, "null array");
         REQUIRE(nd >= 1 && nq >= 0, "sizes out of range");
         knn_device(data, nd, query, nq, k, self_first, idx_out, nullptr, S(stream));
@@ -68,7 +76,7 @@ mgm_status mgm_knn(const double* data, int64_t nd, const double* query, int64_t 
 
 mgm_status mgm_stencil_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx,
                                const mgm_stencil_params* sp, double* w_out, mgm_stream stream) {
-    return guarded([&] {
+    return guarded_trim([&] {
         REQUIRE(sp && idx, "null argument");
         REQUIRE(N >= 1 && sp->n >= 1, "sizes out of range");
         validate_index(idx, N * (int64_t)sp->n, N, "stencil indices", S(stream));
@@ -88,7 +96,7 @@ mgm_status mgm_assemble(int64_t N, int n, const int32_t* idx, const double* w, d
 mgm_status mgm_build_stencils(const double* xyz, const double* nrm, int64_t N, const mgm_stencil_params* sp,
                               int32_t* idx_out, double* w_out, int32_t* rowptr_out, int32_t* col_out, double* val_out,
                               mgm_stream stream) {
-    return guarded([&] {
+    return guarded_trim([&] {
         REQUIRE(xyz && nrm && rowptr_out && col_out && val_out, "null array");
         build_stencils(xyz, nrm, N, sp, idx_out, w_out, rowptr_out, col_out, val_out, S(stream));
     });
@@ -96,7 +104,7 @@ mgm_status mgm_build_stencils(const double* xyz, const double* nrm, int64_t N, c
 
 mgm_status mgm_coarsen(const double* xyz, int64_t N_fine, int64_t N_coarse, uint64_t seed, int32_t* keep_out,
                        mgm_stream stream) {
-    return guarded([&] {
+    return guarded_trim([&] {
         REQUIRE(seed == 0, "seed is reserved and must be 0");
         coarsen(xyz, N_fine, N_coarse, keep_out, S(stream), nullptr);
     });
@@ -104,7 +112,7 @@ mgm_status mgm_coarsen(const double* xyz, int64_t N_fine, int64_t N_coarse, uint
 
 mgm_status mgm_interp(const double* xf, int64_t Nf, const double* xc, int64_t Nc, int m, int32_t* rowptr_out,
                       int32_t* col_out, double* val_out, int64_t* nnz_out, mgm_stream stream) {
-    return guarded([&] {
+    return guarded_trim([&] {
         REQUIRE(Nc >= 1, "N_c must be >= 1");
         int64_t nnz = interp(xf, Nf, xc, Nc, m, rowptr_out, col_out, val_out, S(stream));
         if (nnz_out) *nnz_out = nnz;
@@ -160,7 +168,7 @@ mgm_status mgm_color(int64_t N, const int32_t* rowptr, const int32_t* col, uint6
 
 mgm_status mgm_setup(const double* xyz, int64_t N, const int32_t* rowptr, const int32_t* col, const double* val,
                      const mgm_params* params, mgm_hierarchy** out, mgm_stream stream) {
-    return guarded([&] {
+    return guarded_trim([&] {
         REQUIRE(out, "null output handle");
         *out = nullptr;
         REQUIRE(rowptr && col && N >= 1, "bad argument");
@@ -186,13 +194,13 @@ mgm_status mgm_solve_multi(mgm_hierarchy* H, int nrhs, const double* F, double* 
 mgm_status mgm_solve_batched(mgm_hierarchy* const* H, int nprob, const double* const* F, double* const* U, int nrhs,
                              const mgm_solve_params* sp, mgm_solve_info* info, mgm_status* status_out,
                              mgm_stream stream) {
-    return guarded([&] { solve_batched(H, nprob, F, U, nrhs, sp, info, status_out, S(stream)); });
+    return guarded_trim([&] { solve_batched(H, nprob, F, U, nrhs, sp, info, status_out, S(stream)); });
 }
 
 mgm_status mgm_eigs(mgm_hierarchy* H, int nev, int b, int s, int max_cycles, double tol, const mgm_solve_params* sp,
                     uint64_t seed, double* lam_re, double* lam_im, double* resid, double* evec, int* nconv,
                     int* nsolves, mgm_stream stream) {
-    return guarded([&] {
+    return guarded_trim([&] {
         eigs(H, nev, b, s, max_cycles, tol, sp, seed, lam_re, lam_im, evec, resid, nconv, nsolves, S(stream));
     });
 }
@@ -247,6 +255,14 @@ mgm_status mgm_profile(mgm_hierarchy* H, int reps, mgm_profile_info* out, mgm_st
     });
 }
 
+mgm_status mgm_vcycle_floor(mgm_hierarchy* H, double chain_us, double gbs, double* floor_ms, double* bytes_ms,
+                            double* chain_ms) {
+    return guarded([&] {
+        REQUIRE(H && floor_ms && chain_us >= 0.0 && gbs > 0.0, "bad argument");
+        *floor_ms = vcycle_floor_ms(H, chain_us, gbs, bytes_ms, chain_ms);
+    });
+}
+
 mgm_status mgm_sweep_config_set(mgm_hierarchy* H, int j, const mgm_sweep_config* cfg, mgm_stream stream) {
     return guarded([&] { sweep_config_set(H, j, cfg, S(stream)); });
 }
@@ -264,6 +280,115 @@ mgm_status mgm_profile_level(mgm_hierarchy* H, int j, int reps, float* ms_out, m
 
 mgm_status mgm_autotune(mgm_hierarchy* H, int reps, int use_cache, mgm_stream stream) {
     return guarded([&] { autotune(H, reps, use_cache != 0, S(stream)); });
+}
+
+// FP64 multiply-add rate: every thread runs 8 independent chains of fused multiply-adds (values
+// stay bounded: x <- x * a + b with |a| < 1)
+__global__ void fp64_fma_probe_k(double* out, int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = threadIdx.x * 1e-3 + q;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += x[q];
+    if (s == 12345.678) out[0] = s;  // keeps the chains live
+}
+
+mgm_status mgm_probe_fp64_fma(int reps, double* gflops_out, mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(reps >= 1 && gflops_out, "bad argument");
+        cudaStream_t s = S(stream);
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        Temp<double> out(1, s);
+        const int blocks = sms * 8, threads = 256, iters = 4096;
+        fp64_fma_probe_k<<<blocks, threads, 0, s>>>(out.get(), iters, 0.999, 1e-3);  // warm-up
+        CK_LAUNCH();
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, s));
+        for (int t = 0; t < reps; ++t) {
+            fp64_fma_probe_k<<<blocks, threads, 0, s>>>(out.get(), iters, 0.999, 1e-3);
+            CK_LAUNCH();
+        }
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        const double flops = 2.0 * 8.0 * iters * (double)blocks * threads * reps;
+        *gflops_out = flops / (ms * 1e-3) / 1e9;
+    });
+}
+
+// dependent-launch latency: each kernel waits for its predecessor, then block 0 advances a counter
+// the predecessor wrote (a real read-after-write dependency between consecutive launches)
+__global__ void chain_probe_k(unsigned* p) {
+    pdl_trigger();
+    pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) p[0] += 1u;
+}
+
+mgm_status mgm_probe_launch_chain(int blocks, int threads, int launches, int pdl, int reps, double* us_out,
+                                  mgm_stream stream) {
+    return guarded([&] {
+        REQUIRE(blocks >= 1 && threads >= 32 && threads <= 1024 && launches >= 1 && launches <= 100000 &&
+                    reps >= 1 && us_out, "bad argument");
+        cudaStream_t s = S(stream);
+        Temp<unsigned> cnt(1, s);
+        CK(cudaMemsetAsync(cnt.get(), 0, sizeof(unsigned), s));
+        cudaStream_t c = nullptr;
+        CK(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        auto cleanup = [&] {
+            if (ge) cudaGraphExecDestroy(ge);
+            if (g) cudaGraphDestroy(g);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            cudaStreamDestroy(c);
+        };
+        try {
+            const bool was = pdl_off();
+            pdl_off() = pdl == 0;
+            CK(cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal));
+            try {
+                for (int k = 0; k < launches; ++k) launch_pdl(chain_probe_k, (unsigned)blocks, (unsigned)threads, c, cnt.get());
+            } catch (...) {
+                pdl_off() = was;
+                cudaGraph_t junk = nullptr;
+                cudaStreamEndCapture(c, &junk);
+                if (junk) cudaGraphDestroy(junk);
+                throw;
+            }
+            pdl_off() = was;
+            CK(cudaStreamEndCapture(c, &g));
+            CK(cudaGraphInstantiate(&ge, g, 0));
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaGraphLaunch(ge, s));  // warm-up
+            CK(cudaEventRecord(e0, s));
+            for (int t = 0; t < reps; ++t) CK(cudaGraphLaunch(ge, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            note_launch((int64_t)launches * (reps + 1));
+            *us_out = 1e3 * (double)ms / ((double)reps * launches);
+        } catch (...) {
+            cleanup();
+            throw;
+        }
+        cleanup();
+    });
 }
 
 int64_t mgm_kernel_launches(void) { return launches(); }
@@ -383,7 +508,7 @@ mgm_status mgm_learned_info(const mgm_hierarchy* H, int* enabled, int64_t* fallb
 // ---------------------------------------------------------------------------------------------
 mgm_status mgm_gradient_weights(const double* xyz, const double* nrm, int64_t N, const int32_t* idx,
                                 const mgm_stencil_params* sp, double* wx_out, double* wy_out, mgm_stream stream) {
-    return guarded([&] {
+    return guarded_trim([&] {
         REQUIRE(sp && idx, "null argument");
         validate_index(idx, N * (int64_t)sp->n, N, "stencil indices", S(stream));
         gradient_weights(xyz, nrm, N, idx, sp, wx_out, wy_out, S(stream));

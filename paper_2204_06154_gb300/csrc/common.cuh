@@ -55,7 +55,12 @@ mgm_status guarded(F&& body) {
 // ---------------------------------------------------------------------------------------------
 // device buffers
 // ---------------------------------------------------------------------------------------------
-// Temp<T>: stream-ordered (cudaMallocAsync/cudaFreeAsync) scratch owned by one call.
+// the library's stream-ordered scratch pool on the current device (util.cu), and a release of its
+// cached memory down to keep_bytes
+cudaMemPool_t scratch_pool();
+void scratch_trim(size_t keep_bytes = 0);
+
+// Temp<T>: stream-ordered scratch (from the scratch pool, freed with cudaFreeAsync) owned by one call.
 template <class T>
 struct Temp {
     T* p = nullptr;
@@ -68,11 +73,11 @@ struct Temp {
         s = st;
         n = count;
         if (count) {
-            cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), st);
+            cudaError_t e = cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), scratch_pool(), st);
             if (e != cudaSuccess) {
                 (void)cudaGetLastError();
                 p = nullptr;
-                fail(MGM_ERR_OOM, "cudaMallocAsync of " + std::to_string(count * sizeof(T)) + " bytes failed");
+                fail(MGM_ERR_OOM, "stream-ordered allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
             }
         }
     }

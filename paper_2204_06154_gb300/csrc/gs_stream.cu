@@ -161,16 +161,15 @@ __device__ __forceinline__ double fmaT(double x, double y, double z) { return fm
 
 // acc += this lane's products of one row held in shared memory: the lane's quads of entries
 // (columns cl, values vl) in [l0, l1) of the lower part, then in [u0, u1) of the upper part (cu,
-// vu), lane gl of G taking every G-th quad. Gathers of up to SS_QB quads are issued before their
+// vu), lane gl of G taking every G-th quad. Gathers of up to QB quads are issued before their
 // products; the products are added in the order of the quads.
-template <class T, int G>
+template <class T, int G, int QB = (sizeof(T) == 4 ? SS_QB : SS_QB / 2)>
 __device__ __forceinline__ T row_dot(const int32_t* cl, const T* vl, int32_t l0, int32_t l1, const int32_t* cu,
                                      const T* vu, int32_t u0, int32_t u1, int gl, const T* e, T acc) {
-    // (a lane's gathers of up to SS_QB quads, FP64 half as many, are issued before their products)
+    // (a lane's gathers of up to QB quads are issued before their products)
     const int32_t nql = l1 > l0 + 4 * gl ? (l1 - l0 - 4 * gl + 4 * G - 1) / (4 * G) : 0;
     const int32_t nqu = u1 > u0 + 4 * gl ? (u1 - u0 - 4 * gl + 4 * G - 1) / (4 * G) : 0;
     const int32_t nq = nql + nqu;
-    constexpr int QB = sizeof(T) == 4 ? SS_QB : SS_QB / 2;
     for (int32_t t0 = 0; t0 < nq; t0 += QB) {
         T x[QB][4];
 #pragma unroll
@@ -607,10 +606,11 @@ void stream_reset(mgm_hierarchy* H, cudaStream_t s) {
 // colour (the split table above), and before the programmatic-launch wait it copies the slice's
 // columns and values into shared memory with cp.async.bulk and loads its rows' static data. The
 // next colour's kernel is allowed to start as soon as every block of this one has started, so its
-// blocks, co-resident with this kernel's, fetch their slices while this colour computes; after the
-// wait only the gathers of the vector remain. b is read after the wait (the kernel that writes it
-// may still be running before it). MODE 0: lower parts (first sweep from zero); MODE 1: both.
+// blocks, where they fit beside this kernel's, fetch their slices while this colour computes; after
+// the wait only the gathers of the vector remain. b is read after the wait (the kernel that writes
+// it may still be running before it). MODE 0: lower parts (first sweep from zero); MODE 1: both.
 constexpr int CS_THREADS = 256;
+constexpr int CS_QB = 4;  // quads a lane gathers at once (FP64: 2)
 
 template <class T>
 struct ColourArgs {
@@ -622,6 +622,7 @@ struct ColourArgs {
     const T* b;
     T* e;
     const int32_t* split;  // this colour's row of the split table: B + 1 slice bounds
+    const int4* sl;        // this colour's slices: {lo[r0], lo[r1], up[r0], up[r1]} of each block
     int* err;
 };
 
@@ -636,7 +637,8 @@ __global__ void __launch_bounds__(CS_THREADS, 4) gs_colour_k(const ColourArgs<T>
     if (r0 >= r1) return;
     constexpr int TS = (int)sizeof(T);
     if (tid == 0) {
-        const int4 v = make_int4(a.lo[r0], a.lo[r1], MODE == 1 ? a.up[r0] : 0, MODE == 1 ? a.up[r1] : 0);
+        int4 v = a.sl[blockIdx.x];
+        if (MODE == 0) v.z = v.w = 0;
         rg = v;
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -688,6 +690,7 @@ __global__ void __launch_bounds__(CS_THREADS, 4) gs_colour_k(const ColourArgs<T>
         __syncthreads();
         return;
     }
+    constexpr int QB = sizeof(T) == 4 ? CS_QB : CS_QB / 2;
     for (int32_t base = r0; base < r1; base += rpp, row += rpp) {  // (uniform over the block: shuffles below)
         const bool act = row < r1;
         if (base > r0 && act) {  // rows of later passes
@@ -699,8 +702,8 @@ __global__ void __launch_bounds__(CS_THREADS, 4) gs_colour_k(const ColourArgs<T>
         T acc = T(0), bv = T(0);
         if (act) {
             bv = a.b[row];
-            acc = row_dot<T, G>(cl, vl, lb - v.x, le - v.x, cu, vu, MODE == 1 ? ub - v.z : 0, MODE == 1 ? ue - v.z : 0,
-                                gl, a.e, acc);
+            acc = row_dot<T, G, QB>(cl, vl, lb - v.x, le - v.x, cu, vu, MODE == 1 ? ub - v.z : 0,
+                                    MODE == 1 ? ue - v.z : 0, gl, a.e, acc);
         }
 #pragma unroll
         for (int o = G / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -720,16 +723,18 @@ static const void* colour_kernel(int mode, int G) {
     return mode == 0 ? colour_kernel_g<0, T>(G) : colour_kernel_g<1, T>(G);
 }
 
-// largest slice of each colour: lower entries (x) and lower + upper entries (y)
-__global__ void cs_max_k(const int32_t* __restrict__ split, int C, int B, const int32_t* __restrict__ lo,
-                         const int32_t* __restrict__ up, int2* mx) {
+// slice table of the staged schedule: {lo[r0], lo[r1], up[r0], up[r1]} of colour c's rows in block
+// k, and the largest slice of each colour: lower entries (x) and lower + upper entries (y)
+__global__ void cs_slices_k(const int32_t* __restrict__ split, int C, int B, const int32_t* __restrict__ lo,
+                            const int32_t* __restrict__ up, int4* sl, int2* mx) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)C * B) return;
     const int c = (int)(t / B), k = (int)(t % B);
     const int32_t s0 = split[(int64_t)c * (B + 1) + k], s1 = split[(int64_t)c * (B + 1) + k + 1];
-    const int32_t l = lo[s1] - lo[s0], u = up[s1] - up[s0];
-    atomicMax(&mx[c].x, l);
-    atomicMax(&mx[c].y, l + u);
+    const int4 v = make_int4(lo[s0], lo[s1], up[s0], up[s1]);
+    sl[t] = v;
+    atomicMax(&mx[c].x, v.y - v.x);
+    atomicMax(&mx[c].y, v.y - v.x + v.w - v.z);
 }
 
 // Tables of the staged per-colour schedule for B bands and G lanes a row. False when some slice
@@ -747,7 +752,9 @@ bool colour_prepare(mgm_hierarchy* H, Level& L, int B, int G, cudaStream_t s) {
     CK_LAUNCH();
     Temp<int2> mx(C, s);
     CK(cudaMemsetAsync(mx.get(), 0, sizeof(int2) * C, s));
-    cs_max_k<<<grid_for((int64_t)C * B, 256), 256, 0, s>>>(L.split.get(), C, B, L.lo.get(), L.up.get(), mx.get());
+    L.cslice.alloc((size_t)C * B);
+    cs_slices_k<<<grid_for((int64_t)C * B, 256), 256, 0, s>>>(L.split.get(), C, B, L.lo.get(), L.up.get(),
+                                                             L.cslice.get(), mx.get());
     CK_LAUNCH();
     std::vector<int2> h(C);
     to_host(h.data(), mx.get(), C, s);
@@ -790,6 +797,7 @@ void colour_sweep(mgm_hierarchy* H, Level& L, int mode, cudaStream_t s) {
     for (int c = 0; c < C; ++c) {
         if (L.cptr[c + 1] == L.cptr[c]) continue;
         a.split = L.split.get() + (int64_t)c * (L.sB + 1);
+        a.sl = L.cslice.get() + (int64_t)c * L.sB;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(L.sB);
         cfg.blockDim = dim3(CS_THREADS);
@@ -898,8 +906,8 @@ void autotune(mgm_hierarchy* H, int reps, bool use_cache, cudaStream_t s) {
                     const float ms = time_level_smoothing(H, j, reps, s);
                     if (ms < best.ms) best = mgm_sweep_config{MGM_SCHEDULE_STREAM, b, g, ns, ms};
                 }
-        for (int mult : {1, 2, 3})  // staged per-colour launches, 1-3 bands an SM
-            for (int g : {1, 2, 4}) {
+        for (int mult : {1, 2, 3, 4})  // staged per-colour launches, 1-4 bands an SM
+            for (int g : {1, 2, 4, 8}) {
                 const int b = (int)std::min<int64_t>((int64_t)mult * sms, std::max<int64_t>(1, L.n / 32));
                 if (mult > 1 && b < (int64_t)mult * sms) continue;
                 if (!colour_prepare(H, L, b, g, s)) continue;

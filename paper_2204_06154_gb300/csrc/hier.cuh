@@ -55,6 +55,7 @@ struct Level {
     std::vector<int> csm0, csm1;  // their shared memory a block per colour: lower parts / both parts
     Buf<int32_t> split, recptr, cchunk;
     Buf<int4> rec;
+    Buf<int4> cslice;          // staged schedule: C x sB slices {lo[r0], lo[r1], up[r0], up[r1]}
     Buf<int2> rrow;
     Buf<unsigned> prog;        // per block: colour steps completed (monotone over launches)
     int stream = 0;            // this level's sweeps run streamed
@@ -150,6 +151,7 @@ void alloc_work(mgm_hierarchy* H);
 void check_device_error(mgm_hierarchy* H, cudaStream_t s);
 int barrier_timeout_probe(int nblocks, unsigned long long limit, cudaStream_t s);
 void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
+double vcycle_floor_ms(const mgm_hierarchy* H, double chain_us, double gbs, double* bytes_ms, double* chain_ms);
 // krylov.cu
 bool solve_graph_supported(const mgm_hierarchy* H, const mgm_solve_params* sp);
 void reaction_steps(mgm_hierarchy* Hu, mgm_hierarchy* Hv, int model, const double* prm, double dt, double* u, double* v,

@@ -716,10 +716,11 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         for (int j = 0; j + 1 < p; ++j) {
             Level& L = H->lv[j];
-            // measured on the 1M-point sphere (n = 50): three bands an SM and one lane a row on
-            // levels of 500k rows and more; below, one band an SM, 2 lanes (>= 100k) or 4
-            const int B = L.n >= 100000 ? 3 * sms : sms;
-            const int G = L.n >= 500000 ? 1 : (L.n >= 100000 ? 2 : 4);
+            // measured on the 1M-point sphere (n = 50): four bands an SM and 2 lanes a row on levels
+            // of 500k rows and more, three bands an SM and 4 lanes from 100k, one band an SM below,
+            // with 4 lanes (>= 30k rows) or 8 (the levels there are bound by launch latency alone)
+            const int B = L.n >= 500000 ? 4 * sms : (L.n >= 100000 ? 3 * sms : sms);
+            const int G = L.n >= 500000 ? 2 : (L.n >= 30000 ? 4 : 8);
             colour_prepare(H.get(), L, B, G, s);  // (a level that does not fit keeps plain launches)
         }
         tr.mark("staged-tables", p - 1);

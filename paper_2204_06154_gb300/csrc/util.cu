@@ -445,6 +445,36 @@ void sym_pattern(int64_t N, const int32_t* rp, const int32_t* ci, Temp<int32_t>&
     }
 }
 
+// The library's scratch pool on each device: stream-ordered allocations that are kept for reuse
+// across synchronisations (the release threshold is unlimited) instead of being unmapped at every
+// one, as the default pool does; heavy entry points hand the cached memory back with scratch_trim.
+cudaMemPool_t scratch_pool() {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    CK(cudaMemPoolCreate(&pool, &pp));
+    uint64_t keep = ~0ull;
+    CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[dev] = pool;
+    return pool;
+}
+
+void scratch_trim(size_t keep_bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPoolTrimTo(scratch_pool(), keep_bytes);
+}
+
 int coresident_blocks(const void* kernel, int threads, size_t smem, int per_sm_cap) {
     static std::mutex mu;
     static std::map<std::tuple<const void*, int, int, size_t, int>, int> cache;

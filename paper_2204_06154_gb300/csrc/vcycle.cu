@@ -849,28 +849,56 @@ void add_output(mgm_hierarchy* H, double* dst, const int32_t* scatter, cudaStrea
     CK_LAUNCH();
 }
 
-// Algorithmic bytes of one V-cycle: every stored off-diagonal entry (value + column) is read once
-// per pass, per-row arrays (row starts, diagonal inverse, b, e, s) once per pass, transfer
-// entries once, the coarsest inverse once; gathered vector entries are L2 hits and not counted.
-int64_t vcycle_bytes(const mgm_hierarchy* H) {
-    const int64_t vs = H->precision == MGM_F32 ? 4 : 8, is = 4, ent = vs + is;
+// Algorithmic bytes of one V-cycle on level j (j + 1 < p): every stored off-diagonal entry (value +
+// column) is read once per pass, per-row arrays (row starts, diagonal inverse, b, e, s) once per
+// pass, transfer entries once; gathered vector entries are L2 hits and not counted.
+static int64_t level_bytes(const mgm_hierarchy* H, int j) {
+    const int64_t vs = H->precision == MGM_F32 ? 4 : 8, ent = vs + 4;
+    const Level& L = H->lv[j];
+    const Level& C = H->lv[j + 1];
+    const int64_t n = L.n, nnzo = L.nlow + L.nupp;
     int64_t b = 0;
-    for (int j = 0; j + 1 < H->p; ++j) {
-        const Level& L = H->lv[j];
-        const Level& C = H->lv[j + 1];
-        const int64_t n = L.n, nnzo = L.nlow + L.nupp;
-        if (H->nu1 >= 1) {
-            b += L.nlow * ent + n * (8 + 3 * vs);                      // first sweep from zero (lower part)
-            b += (int64_t)(H->nu1 - 1) * (nnzo * ent + n * (4 + 3 * vs));
-            b += (H->nu1 == 1 ? L.nupp * ent + n * (4 + vs)           // residual -U e
-                              : nnzo * ent + n * (4 + 4 * vs));        // residual b - A e
-        }
-        b += L.pnnz * ent + (C.n + 1) * 4 + n * vs + C.n * vs;        // restriction
-        b += L.pnnz * ent + 2 * n * vs;                               // interpolation + correction
-        b += (int64_t)H->nu2 * (nnzo * ent + n * (4 + 3 * vs));       // post-smoothing sweeps
+    if (H->nu1 >= 1) {
+        b += L.nlow * ent + n * (8 + 3 * vs);                      // first sweep from zero (lower part)
+        b += (int64_t)(H->nu1 - 1) * (nnzo * ent + n * (4 + 3 * vs));
+        b += (H->nu1 == 1 ? L.nupp * ent + n * (4 + vs)           // residual -U e
+                          : nnzo * ent + n * (4 + 4 * vs));        // residual b - A e
     }
+    b += L.pnnz * ent + (C.n + 1) * 4 + n * vs + C.n * vs;        // restriction
+    b += L.pnnz * ent + 2 * n * vs;                               // interpolation + correction
+    b += (int64_t)H->nu2 * (nnzo * ent + n * (4 + 3 * vs));       // post-smoothing sweeps
+    return b;
+}
+
+int64_t vcycle_bytes(const mgm_hierarchy* H) {
+    int64_t b = 0;
+    for (int j = 0; j + 1 < H->p; ++j) b += level_bytes(H, j);
+    const int64_t vs = H->precision == MGM_F32 ? 4 : 8;
     b += H->np * H->np * 8 + 2 * H->np * vs;                          // coarsest solve
     return b;
+}
+
+// Lower bound of one V-cycle's time for schedules that separate a sweep's colours by kernel
+// boundaries: level by level, the larger of its bytes at `gbs` GB/s and its chain of dependent
+// launches (nu1 + nu2 sweeps of one launch per colour, residual, restriction, interpolation) at
+// `chain_us` each, plus one launch for the coarsest solve. Bytes may overlap the latency of
+// launches (a launch prefetches while its predecessor runs) but neither can shrink below itself.
+double vcycle_floor_ms(const mgm_hierarchy* H, double chain_us, double gbs, double* bytes_ms, double* chain_ms) {
+    double f = 0.0, bt = 0.0, ch = 0.0;
+    for (int j = 0; j + 1 < H->p; ++j) {
+        const Level& L = H->lv[j];
+        const int64_t C = (int64_t)L.cptr.size() - 1;
+        const double tb = (double)level_bytes(H, j) / (gbs * 1e6);
+        const double tc = (double)((H->nu1 + H->nu2) * C + 3) * chain_us * 1e-3;
+        f += std::max(tb, tc);
+        bt += tb;
+        ch += tc;
+    }
+    f += chain_us * 1e-3;
+    ch += chain_us * 1e-3;
+    if (bytes_ms) *bytes_ms = bt;
+    if (chain_ms) *chain_ms = ch;
+    return f;
 }
 
 void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s) {

@@ -66,7 +66,8 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
            "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
            "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs", "mgm_reaction_rhs",
-           "mgm_sweep_config_set", "mgm_sweep_config_get", "mgm_autotune", "mgm_profile_level", "mgm_reaction_steps"]
+           "mgm_sweep_config_set", "mgm_sweep_config_get", "mgm_autotune", "mgm_profile_level", "mgm_reaction_steps",
+           "mgm_probe_fp64_fma", "mgm_probe_launch_chain", "mgm_vcycle_floor"]
 
 
 _SCHEDULES = ["launch", "stream", "resident", "colour"]
@@ -115,6 +116,9 @@ def lib():
         L.mgm_sweep_config_get.argtypes = [P, I, C.POINTER(SweepConfig)]
         L.mgm_autotune.argtypes = [P, I, I, P]
         L.mgm_profile_level.argtypes = [P, I, I, C.POINTER(C.c_float), P]
+        L.mgm_probe_fp64_fma.argtypes = [I, C.POINTER(C.c_double), P]
+        L.mgm_probe_launch_chain.argtypes = [I, I, I, I, I, C.POINTER(C.c_double), P]
+        L.mgm_vcycle_floor.argtypes = [P, C.c_double, C.c_double] + [C.POINTER(C.c_double)] * 3
         L.mgm_check_bounded_wait.argtypes = [I, I64, C.POINTER(C.c_int), P]
         L.mgm_kernel_launches.argtypes = []
         L.mgm_kernel_launches.restype = C.c_int64
@@ -243,6 +247,21 @@ def reaction_rhs(model, scheme, u, v, prm, dt, u_prev=None, v_prev=None, out=Non
                                   _p(u_prev) if u_prev is not None else None, _p(v_prev) if v_prev is not None else None,
                                   p3, float(dt), _p(ru), _p(rv), _stream()))
     return ru, rv
+
+
+def probe_fp64_fma(reps=20):
+    """The device's FP64 multiply-add rate in GFLOP/s (mgm_probe_fp64_fma)."""
+    g = C.c_double(0.0)
+    _check(lib().mgm_probe_fp64_fma(reps, C.byref(g), _stream()))
+    return g.value
+
+
+def probe_launch_chain(blocks, threads=256, launches=256, pdl=True, reps=10):
+    """Microseconds between consecutive dependent launches of `blocks` x `threads` threads
+    (mgm_probe_launch_chain)."""
+    us = C.c_double(0.0)
+    _check(lib().mgm_probe_launch_chain(blocks, threads, launches, 1 if pdl else 0, reps, C.byref(us), _stream()))
+    return us.value
 
 
 def reaction_steps(Hu, Hv, model, prm, dt, u, v, steps, tol=1e-8, restart=50, maxit=200):
@@ -438,6 +457,13 @@ class Hierarchy:
         pi = ProfileInfo()
         _check(lib().mgm_profile(self._h, reps, C.byref(pi), _stream()))
         return {k: getattr(pi, k) for k, _ in ProfileInfo._fields_}
+
+    def vcycle_floor(self, chain_us, gbs):
+        """Lower bound (ms) of one V-cycle for colour-by-launch schedules (mgm_vcycle_floor):
+        {"floor_ms", "bytes_ms", "chain_ms"}."""
+        f, b, c = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+        _check(lib().mgm_vcycle_floor(self._h, chain_us, gbs, C.byref(f), C.byref(b), C.byref(c)))
+        return {"floor_ms": f.value, "bytes_ms": b.value, "chain_ms": c.value}
 
     def sweep_config(self, level):
         """Sweep schedule of a level: {"kind": "launch"|"stream", "blocks", "lanes", "stages", "ms"}."""
