@@ -548,7 +548,7 @@ __device__ __forceinline__ float d2f_trunc(double v) {
 constexpr int RL_MAXD = 7;  // largest polynomial degree of the register kernel
 
 struct RlLayout {
-    size_t kd, xs, bd, xh, yh, rinv, piv, bytes;
+    size_t kd, xs, bd, xh, yh, rinv, piv, prow, bytes;
 };
 __host__ __device__ inline RlLayout rl_layout(int n, int m) {
     RlLayout o;
@@ -561,28 +561,37 @@ __host__ __device__ inline RlLayout rl_layout(int n, int m) {
     o.yh = off; off += 8 * (size_t)n;
     o.rinv = off; off += 4 * (size_t)m;
     o.piv = off; off += 4 * (size_t)m;
+    o.prow = (off + 15) & ~(size_t)15; off = o.prow + 4 * (size_t)m;  // the pivot row of one elimination step
     o.bytes = (off + 15) & ~(size_t)15;
     return o;
+}
+
+// column c of a row held as pairs of adjacent columns (c static after unrolling)
+__device__ __forceinline__ float col_of(const float2* a, int c) { return (c & 1) ? a[c >> 1].y : a[c >> 1].x; }
+__device__ __forceinline__ void set_col(float2* a, int c, float v) {
+    if (c & 1) a[c >> 1].y = v;
+    else a[c >> 1].x = v;
 }
 
 // z <- U^-1 L^-1 P z with the register factors; on return x0, x1 hold solution components lane and
 // lane + 32. s0, s1: the step at which each row became the pivot (M: never).
 template <int M>
-__device__ __forceinline__ void rl_solve(const float (&a0)[M], const float (&a1)[M], int s0, int s1, const int* piv,
-                                         const float* rinv, float z0, float z1, float& x0, float& x1, int lane) {
+__device__ __forceinline__ void rl_solve(const float2 (&a0)[M / 2], const float2 (&a1)[M / 2], int s0, int s1,
+                                         const int* piv, const float* rinv, float z0, float z1, float& x0, float& x1,
+                                         int lane) {
 #pragma unroll
     for (int kk = 0; kk < M; ++kk) {
         const int p = piv[kk];
         const float y = __shfl_sync(0xffffffffu, p >= 32 ? z1 : z0, p & 31);
-        if (s0 > kk) z0 = fmaf(-a0[kk], y, z0);
-        if (s1 > kk) z1 = fmaf(-a1[kk], y, z1);
+        if (s0 > kk) z0 = fmaf(-col_of(a0, kk), y, z0);
+        if (s1 > kk) z1 = fmaf(-col_of(a1, kk), y, z1);
     }
 #pragma unroll
     for (int kk = M - 1; kk >= 0; --kk) {
         const int p = piv[kk];
         const float xk = __shfl_sync(0xffffffffu, p >= 32 ? z1 : z0, p & 31) * rinv[kk];
-        if (s0 < kk) z0 = fmaf(-a0[kk], xk, z0);
-        if (s1 < kk) z1 = fmaf(-a1[kk], xk, z1);
+        if (s0 < kk) z0 = fmaf(-col_of(a0, kk), xk, z0);
+        if (s1 < kk) z1 = fmaf(-col_of(a1, kk), xk, z1);
         if (lane == (kk & 31)) {
             if (kk < 32) x0 = xk;
             else x1 = xk;
@@ -606,6 +615,7 @@ __global__ void __launch_bounds__(256) phs_weights_rl_k(PhsArgs a, int wpb, int3
     double* yh = (double*)(base + lay.yh);
     float* rinv = (float*)(base + lay.rinv);
     int* piv = (int*)(base + lay.piv);
+    float4* prow = (float4*)(base + lay.prow);
     const int64_t i = (int64_t)blockIdx.x * wpb + wi;
     if (i >= a.N) return;
     const double s = stencil_coords(a, i, lane, xh, yh);
@@ -674,29 +684,36 @@ __global__ void __launch_bounds__(256) phs_weights_rl_k(PhsArgs a, int wpb, int3
     for (int o = 16; o; o >>= 1) amaxb = max(amaxb, __shfl_xor_sync(0xffffffffu, amaxb, o));
     const unsigned tolb = __float_as_uint(ldexpf((float)__longlong_as_double((long long)amaxb), -20));
     __syncwarp();
-    // FP32 copy into registers: row r < n is row r of [A P]; row n + t is column n + t of it
-    // (P^T, then the zero block); rows >= M are absent
+    // FP32 copy into registers, as pairs of adjacent columns: row r < n is row r of [A P]; row n + t
+    // is column n + t of it (P^T, then the zero block); rows >= M are absent
+    static_assert(M % 4 == 0, "rows are stored as pairs of columns, published four columns at a time");
+    constexpr int MP = M / 2;
     const int r0 = lane, r1 = lane + 32;
-    float a0[M], a1[M];
+    float2 a0[MP], a1[MP];
     {
         const double* p0 = r0 < n ? Kd + r0 * LDD : Kd + r0;
         const double* p1 = r1 < n ? Kd + r1 * LDD : Kd + r1;
         const int st0 = r0 < n ? 1 : LDD, st1 = r1 < n ? 1 : LDD;
         const int lim0 = r0 < n ? M : (r0 < M ? n : 0), lim1 = r1 < n ? M : (r1 < M ? n : 0);
 #pragma unroll
-        for (int c = 0; c < M; ++c) {
-            a0[c] = c < lim0 ? d2f_trunc(p0[c * st0]) : 0.0f;
-            a1[c] = c < lim1 ? d2f_trunc(p1[c * st1]) : 0.0f;
+        for (int q = 0; q < MP; ++q) {
+            const int c = 2 * q;
+            a0[q] = make_float2(c < lim0 ? d2f_trunc(p0[c * st0]) : 0.0f, c + 1 < lim0 ? d2f_trunc(p0[(c + 1) * st0]) : 0.0f);
+            a1[q] = make_float2(c < lim1 ? d2f_trunc(p1[c * st1]) : 0.0f, c + 1 < lim1 ? d2f_trunc(p1[(c + 1) * st1]) : 0.0f);
         }
     }
-    // FP32 LU with implicit partial pivoting (first row of maximal |a_rk| among rows not yet used)
+    // FP32 LU with implicit partial pivoting (first row of maximal |a_rk| among rows not yet used).
+    // The pivot row's lane publishes the row's remaining columns in shared memory (four a store),
+    // every lane reads them back as a broadcast and updates both of its rows with paired FMAs.
     bool d0 = r0 >= M, d1 = r1 >= M;
     int s0 = M, s1 = M;
     bool ok = true;
+    const float* prowf = reinterpret_cast<const float*>(prow);
 #pragma unroll
     for (int kk = 0; kk < M; ++kk) {
-        const unsigned b0 = d0 ? 0u : mag_bits_f(a0[kk]);
-        const unsigned b1 = d1 ? 0u : mag_bits_f(a1[kk]);
+        const float f0 = col_of(a0, kk), f1 = col_of(a1, kk);
+        const unsigned b0 = d0 ? 0u : mag_bits_f(f0);
+        const unsigned b1 = d1 ? 0u : mag_bits_f(f1);
         // warp maximum in one reduction; the first row holding it (rows lane, then lane + 32)
         const unsigned best = __reduce_max_sync(0xffffffffu, max(b0, b1));
         const unsigned m0 = __ballot_sync(0xffffffffu, !d0 && b0 == best);
@@ -706,23 +723,38 @@ __global__ void __launch_bounds__(256) phs_weights_rl_k(PhsArgs a, int wpb, int3
         const bool hi = p >= 32;
         if (p == r0) { d0 = true; s0 = kk; }
         if (p == r1) { d1 = true; s1 = kk; }
-        const float rk = 1.0f / __shfl_sync(0xffffffffu, hi ? a1[kk] : a0[kk], pl);
+        // columns kk.. of the pivot row, from the first group of four that holds column kk
+        const int g0 = (kk / 4) * 2;  // first pair published
+        if (lane == pl) {
+            if (hi) {
+#pragma unroll
+                for (int q = g0; q < MP; q += 2) prow[q >> 1] = make_float4(a1[q].x, a1[q].y, a1[q + 1].x, a1[q + 1].y);
+            } else {
+#pragma unroll
+                for (int q = g0; q < MP; q += 2) prow[q >> 1] = make_float4(a0[q].x, a0[q].y, a0[q + 1].x, a0[q + 1].y);
+            }
+        }
+        __syncwarp();
+        const float rk = 1.0f / prowf[kk];
         if (lane == 0) {
             piv[kk] = p;
             rinv[kk] = rk;
         }
-        const float l0 = d0 ? 0.0f : a0[kk] * rk;
-        const float l1 = d1 ? 0.0f : a1[kk] * rk;
-        if (!d0) a0[kk] = l0;
-        if (!d1) a1[kk] = l1;
+        const float l0 = d0 ? 0.0f : f0 * rk;
+        const float l1 = d1 ? 0.0f : f1 * rk;
+        const float2 n0 = make_float2(-l0, -l0), n1 = make_float2(-l1, -l1);
+        // columns > kk: the pairs from (kk + 1) / 2; for even kk the first pair also holds column kk,
+        // which the multiplier overwrites below (done rows have l = 0 and keep their entries)
 #pragma unroll
-        for (int c = 1; c < M; ++c) {  // constant bounds, so that both loops unroll fully
-            if (c > kk) {
-                const float v = __shfl_sync(0xffffffffu, hi ? a1[c] : a0[c], pl);
-                a0[c] = fmaf(-l0, v, a0[c]);
-                a1[c] = fmaf(-l1, v, a1[c]);
-            }
+        for (int q = (kk + 1) / 2; q < MP; ++q) {
+            const float4 v4 = prow[q >> 1];
+            const float2 v = (q & 1) ? make_float2(v4.z, v4.w) : make_float2(v4.x, v4.y);
+            a0[q] = __ffma2_rn(n0, v, a0[q]);
+            a1[q] = __ffma2_rn(n1, v, a1[q]);
         }
+        if (!d0) set_col(a0, kk, l0);
+        if (!d1) set_col(a1, kk, l1);
+        __syncwarp();  // the pivot row is read before the next step overwrites it
     }
     __syncwarp();
     bool conv = false;
