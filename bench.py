@@ -45,8 +45,9 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-10 rel. residual at N=1M, mixed vs FP64 MGM; V-cycle HBM GB/s vs peak"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes of phs_weights_rl_k<60> per stencil: dram__bytes_read.sum + dram__bytes_write.sum of one
-# ncu capture of the current kernel on 131,072 stencils (profiles/phs_weights_rl_k__sphere_131k.md)
-RL_DRAM_BYTES_PER_STENCIL = None
+# ncu capture of the current kernel on 524,288 stencils (136.3 MB + 160.6 MB; its 210 MB of output
+# exceed L2, so most writes reach DRAM within the launch), divided by the stencils
+RL_DRAM_BYTES_PER_STENCIL = (136305664 + 160632064) / 524288
 
 P = dict(n=50, k=1, ell=3, mu=1.0, n_min=250, m=3, tol=1e-10, restart=50, maxit=200)
 
@@ -76,6 +77,7 @@ def parse():
                     help="profiling driver: build the sphere problem of --size, then run this many V-cycles "
                          "(FP32 unless --fp64-cycle; --learned-n attaches an untrained correction of that stencil size)")
     ap.add_argument("--fp64-cycle", action="store_true")
+    ap.add_argument("--transfer-bf16", action="store_true", help="profiling driver: BF16-stored P/R weights")
     ap.add_argument("--sweeps", default="0,5,4", help="profiling driver: sweep schedules to compare (persistent_sweeps values)")
     ap.add_argument("--learned-n", type=int, default=0)
     return ap.parse_args()
@@ -567,7 +569,8 @@ def main():
         r = torch.from_numpy(np.random.default_rng(5).standard_normal(a.size)).cuda()
         out = {"vcycles": a.vcycles, "N": a.size}
         for mode in [int(t) for t in a.sweeps.split(",")]:
-            H = M.Hierarchy(X, rp, ci, v, 250, precision="f64" if a.fp64_cycle else "f32", persistent_sweeps=mode)
+            H = M.Hierarchy(X, rp, ci, v, 250, precision="f64" if a.fp64_cycle else "f32", persistent_sweeps=mode,
+                            transfer_bf16=a.transfer_bf16)
             if a.learned_n:
                 H.learned_attach(X, Nr, idx, w)
                 H.learned_enable(M.MLP(a.learned_n, seed=1))
@@ -679,7 +682,7 @@ def main():
                      "frac": round(w_gops / fp64_pipe_peak, 3),
                      "traffic": int(RL_DRAM_BYTES_PER_STENCIL * a.size) if RL_DRAM_BYTES_PER_STENCIL else None,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel on "
-                                       "131,072 stencils, scaled by stencils to the launch's count",
+                                       "524,288 stencils, scaled by stencils to the launch's count",
                      "fp64_ops_per_stencil": ops_per_stencil,
                      "peak_source": f"mgm_probe_fp64_fma during this run: {res['fp64_gflops']:.0f} GFLOP/s of FP64 "
                                     f"multiply-adds (2 flops each) = {fp64_pipe_peak:.1f} G FP64-pipe op/s "

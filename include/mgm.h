@@ -120,6 +120,11 @@ typedef struct {
                         every coarse level from each finer one (the second from the first's result).
                         MGM_CYCLE_F (2): F-cycle, an F-cycle then a V-cycle on each coarse level
                         (Sec. 4.5 names both). Not for constrained hierarchies. */
+    int transfer_bf16; /* 0: the FP32 cycle reads FP32 interpolation and restriction weights. 1: it
+                          reads them stored as BF16 (each weight the FP32 value rounded to nearest even
+                          in its top 16 bits), with FP32 products and sums; a storage option, not of the
+                          paper. Ignored by FP64 hierarchies; the many-right-hand-side cycle of
+                          mgm_solve_multi / mgm_solve_batched keeps FP32 weights. */
 } mgm_params;
 
 enum { MGM_SMOOTHER_MC = 0, MGM_SMOOTHER_LEX = 1 };

@@ -65,6 +65,7 @@ struct Level {
     int pw = 0;                // ELL width of the interpolation (= m)
     Buf<int32_t> pc;           // n * pw
     Buf<float> pv32;
+    Buf<uint16_t> pv16, r_v16;  // BF16 bit patterns of pv32 / r_v32 (transfer_bf16)
     Buf<double> pv64;
     Buf<int32_t> r_rp, r_ci;   // restriction: rows = next level's solve order
     Buf<float> r_v32;
@@ -85,6 +86,7 @@ struct Level {
 struct mgm_hierarchy {
     int p = 0;
     int cycle = 0;     // MGM_CYCLE_V / W / F
+    bool transfer_bf16 = false;  // FP32 cycle: BF16-stored P and R weights
     int precision = MGM_F32;
     int nu1 = 1, nu2 = 1, m = 3;
     uint64_t seed = 0;

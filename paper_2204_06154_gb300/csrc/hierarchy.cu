@@ -521,6 +521,14 @@ static void build_transfers(Level& F, const Level* C, int64_t nc, int m, cudaStr
     }
 }
 
+// BF16 bit patterns of FP32 weights: the top 16 bits rounded to nearest, ties to even (finite inputs)
+__global__ void to_bf16_bits_k(const float* in, int64_t n, uint16_t* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned u = __float_as_uint(in[i]);
+    out[i] = (uint16_t)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+
 __global__ void compose_k(const int32_t* a, const int32_t* b, int64_t n, int32_t* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a[b[i]];
@@ -569,6 +577,8 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     REQUIRE(prm->cycle >= MGM_CYCLE_V && prm->cycle <= MGM_CYCLE_F, "unknown cycle type");
     REQUIRE(prm->cycle == MGM_CYCLE_V || !H->bordered, "W and F cycles: not for constrained hierarchies");
     H->cycle = prm->cycle;
+    REQUIRE(prm->transfer_bf16 == 0 || prm->transfer_bf16 == 1, "transfer_bf16 must be 0 or 1");
+    H->transfer_bf16 = prm->transfer_bf16 == 1 && prm->precision == MGM_F32;
     H->N = N;
     int p = num_levels(N, prm->n_min);
     if (p > 16) fail(MGM_ERR_UNSUPPORTED, "more than 16 levels");
@@ -664,6 +674,19 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     if (p == 1) build_solve_layout(H->lv[0], true, s);  // one group: serves the outer operator only
     for (int j = 0; j + 1 < p; ++j)
         build_transfers(H->lv[j], (j + 2 < p) ? &H->lv[j + 1] : nullptr, H->lv[j + 1].n, prm->m, s);
+    if (H->transfer_bf16) {  // BF16 copies of the FP32 transfer weights
+        for (int j = 0; j + 1 < p; ++j) {
+            Level& L = H->lv[j];
+            L.pv16.alloc(L.n * L.pw);
+            to_bf16_bits_k<<<grid_for(L.n * L.pw, 256), 256, 0, s>>>(L.pv32.get(), L.n * L.pw, L.pv16.get());
+            CK_LAUNCH();
+            L.r_v16.alloc(std::max<int64_t>(L.pnnz, 1));
+            if (L.pnnz > 0) {
+                to_bf16_bits_k<<<grid_for(L.pnnz, 256), 256, 0, s>>>(L.r_v32.get(), L.pnnz, L.r_v16.get());
+                CK_LAUNCH();
+            }
+        }
+    }
     tr.mark("transfers", -1);
     // constrained Poisson (Sec. 4.4): border vectors c_0 = 1, c_{j+1} = R_j c_j (eq. (gco_saddle_point))
     if (H->bordered) {
@@ -731,7 +754,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         bytes += L.X.bytes() + L.rp.bytes() + L.ci.bytes() + L.v.bytes() + L.perm.bytes() + L.keep.bytes() + L.P_rp.bytes() +
                  L.P_ci.bytes() + L.P_v.bytes() + L.colour.bytes() + L.ord.bytes() + L.inv.bytes() + L.lo.bytes() +
                  L.up.bytes() + L.sc.bytes() + L.sv32.bytes() + L.sv64.bytes() + 3 * L.diag64.bytes() + 3 * L.diag32.bytes() +
-                 L.pc.bytes() + L.pv32.bytes() + L.pv64.bytes() + L.r_rp.bytes() + L.r_ci.bytes() + L.r_v32.bytes() +
+                 L.pc.bytes() + L.pv32.bytes() + L.pv16.bytes() + L.r_v16.bytes() + L.pv64.bytes() + L.r_rp.bytes() + L.r_ci.bytes() + L.r_v32.bytes() +
                  L.r_v64.bytes() + L.b32.bytes() * 3 + L.b64.bytes() * 3;
     H->device_bytes = bytes;
     return H.release();

@@ -109,6 +109,15 @@ __device__ __forceinline__ double ld_stream_t(const double* q, uint64_t pol) {
     return v;
 }
 
+// a transfer weight: FP32 as stored, or a BF16 bit pattern widened to FP32 (exact)
+__device__ __forceinline__ float ld_weight(const float* q, uint64_t pol) { return ld_stream_t(q, pol); }
+__device__ __forceinline__ double ld_weight(const double* q, uint64_t pol) { return ld_stream_t(q, pol); }
+__device__ __forceinline__ float ld_weight(const uint16_t* q, uint64_t pol) {
+    unsigned short v;
+    asm("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(q), "l"(pol));
+    return __uint_as_float((unsigned)v << 16);
+}
+
 template <class T>
 struct Quad;
 template <>
@@ -338,8 +347,9 @@ __global__ void barrier_timeout_probe_k(unsigned* bar, int* err, unsigned long l
     grid_barrier(bar, gridDim.x + 1, limit, err, &ok);
 }
 
-template <class T>
-__global__ void restrict_k(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
+// W: the stored weight type (T, or uint16_t BF16 bit patterns for the FP32 cycle)
+template <class T, class W = T>
+__global__ void restrict_k(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const W* __restrict__ v,
                            const T* __restrict__ s, T* bn, int64_t nc) {
     pdl_trigger();
     pdl_wait();
@@ -347,12 +357,12 @@ __global__ void restrict_k(const int32_t* __restrict__ rp, const int32_t* __rest
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
     T acc = T(0);
-    for (int32_t q = rp[c]; q < rp[c + 1]; ++q) acc += ld_stream_t(v + q, pol) * s[ld_stream(ci + q, pol)];
+    for (int32_t q = rp[c]; q < rp[c + 1]; ++q) acc += (T)ld_weight(v + q, pol) * s[ld_stream(ci + q, pol)];
     bn[c] = acc;
 }
 
-template <class T>
-__global__ void interp_k(const int32_t* __restrict__ pc, const T* __restrict__ pv, int pw, const T* __restrict__ en, T* e,
+template <class T, class W = T>
+__global__ void interp_k(const int32_t* __restrict__ pc, const W* __restrict__ pv, int pw, const T* __restrict__ en, T* e,
                          int64_t n) {
     pdl_trigger();
     pdl_wait();
@@ -360,9 +370,15 @@ __global__ void interp_k(const int32_t* __restrict__ pc, const T* __restrict__ p
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T acc = e[i];
-    for (int t = 0; t < pw; ++t) acc += ld_stream_t(pv + i * pw + t, pol) * en[ld_stream(pc + i * pw + t, pol)];
+    for (int t = 0; t < pw; ++t) acc += (T)ld_weight(pv + i * pw + t, pol) * en[ld_stream(pc + i * pw + t, pol)];
     e[i] = acc;
 }
+
+// restriction / interpolation launches of one level pair, with the level's stored weight type
+template <class T>
+static void launch_restrict(mgm_hierarchy* H, Level& L, Level& C, const T* rsrc, cudaStream_t s);
+template <class T>
+static void launch_interp(mgm_hierarchy* H, Level& L, Level& C, cudaStream_t s);
 
 template <class T>
 __global__ void coarse_k(const double* __restrict__ Ainv, const T* __restrict__ b, T* e, int64_t n) {
@@ -422,6 +438,32 @@ template <> struct LV<double> {
     static double* eold(Level& L) { return L.eold64.get(); }
     static const double* c(Level& L) { return L.c64.get(); }
 };
+
+template <class T>
+static void launch_restrict(mgm_hierarchy* H, Level& L, Level& C, const T* rsrc, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (H->transfer_bf16) {
+            launch_pdl(restrict_k<float, uint16_t>, grid_for(C.n, 256), 256, s, (const int32_t*)L.r_rp.get(),
+                       (const int32_t*)L.r_ci.get(), (const uint16_t*)L.r_v16.get(), rsrc, LV<T>::b(C), (int64_t)C.n);
+            return;
+        }
+    }
+    launch_pdl(restrict_k<T>, grid_for(C.n, 256), 256, s, (const int32_t*)L.r_rp.get(), (const int32_t*)L.r_ci.get(),
+               LV<T>::rv(L), rsrc, LV<T>::b(C), (int64_t)C.n);
+}
+
+template <class T>
+static void launch_interp(mgm_hierarchy* H, Level& L, Level& C, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (H->transfer_bf16) {
+            launch_pdl(interp_k<float, uint16_t>, grid_for(L.n, 256), 256, s, (const int32_t*)L.pc.get(),
+                       (const uint16_t*)L.pv16.get(), L.pw, (const T*)LV<T>::e(C), LV<T>::e(L), (int64_t)L.n);
+            return;
+        }
+    }
+    launch_pdl(interp_k<T>, grid_for(L.n, 256), 256, s, (const int32_t*)L.pc.get(), LV<T>::pv(L), L.pw,
+               (const T*)LV<T>::e(C), LV<T>::e(L), (int64_t)L.n);
+}
 
 template <int MODE, class T>
 static void launch_rows(Level& L, int32_t r0, int32_t r1, cudaStream_t s) {
@@ -595,8 +637,7 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
                                              j + 2 == p ? LV<T>::b(C) + C.n : nullptr);
             CK_LAUNCH();
         }
-        launch_pdl(restrict_k<T>, grid_for(C.n, 256), 256, s, (const int32_t*)L.r_rp.get(), (const int32_t*)L.r_ci.get(),
-                   LV<T>::rv(L), rsrc, LV<T>::b(C), (int64_t)C.n);
+        launch_restrict<T>(H, L, C, rsrc, s);
     }
     {   // coarsest defect (bordered: with the multiplier in the last entry)
         Level& C = H->lv[p - 1];
@@ -606,8 +647,7 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
     for (int j = p - 2; j >= 0; --j) {  // interpolate / correct, post-smooth
         Level& L = H->lv[j];
         Level& C = H->lv[j + 1];
-        launch_pdl(interp_k<T>, grid_for(L.n, 256), 256, s, (const int32_t*)L.pc.get(), LV<T>::pv(L), L.pw,
-                   (const T*)LV<T>::e(C), LV<T>::e(L), (int64_t)L.n);
+        launch_interp<T>(H, L, C, s);
         if (H->bordered) {  // smooth u only: b_j <- b_j - c_j mu
             const T* mu = LV<T>::e(H->lv[p - 1]) + H->np;
             bshift_k<T><<<grid_for(L.n, 256), 256, 0, s>>>(LV<T>::b(L), LV<T>::c(L), mu, L.n);
@@ -644,8 +684,7 @@ static void cycle_rec(mgm_hierarchy* H, int j, int type, bool zero_start, cudaSt
         launch_rows<3, T>(L, 0, (int32_t)L.n, s);  // s = b - L e
         rsrc = LV<T>::s(L);
     }
-    launch_pdl(restrict_k<T>, grid_for(C.n, 256), 256, s, (const int32_t*)L.r_rp.get(), (const int32_t*)L.r_ci.get(),
-               LV<T>::rv(L), rsrc, LV<T>::b(C), (int64_t)C.n);
+    launch_restrict<T>(H, L, C, rsrc, s);
     if (type == MGM_CYCLE_V) {
         cycle_rec<T>(H, j + 1, MGM_CYCLE_V, true, s);
     } else if (type == MGM_CYCLE_W) {
@@ -655,8 +694,7 @@ static void cycle_rec(mgm_hierarchy* H, int j, int type, bool zero_start, cudaSt
         cycle_rec<T>(H, j + 1, MGM_CYCLE_F, true, s);
         cycle_rec<T>(H, j + 1, MGM_CYCLE_V, false, s);
     }
-    launch_pdl(interp_k<T>, grid_for(L.n, 256), 256, s, (const int32_t*)L.pc.get(), LV<T>::pv(L), L.pw,
-               (const T*)LV<T>::e(C), LV<T>::e(L), (int64_t)L.n);
+    launch_interp<T>(H, L, C, s);
     for (int t = 0; t < H->nu2; ++t) sweep_any<T>(H, L, false, s);
 }
 
@@ -854,6 +892,7 @@ void add_output(mgm_hierarchy* H, double* dst, const int32_t* scatter, cudaStrea
 // pass, transfer entries once; gathered vector entries are L2 hits and not counted.
 static int64_t level_bytes(const mgm_hierarchy* H, int j) {
     const int64_t vs = H->precision == MGM_F32 ? 4 : 8, ent = vs + 4;
+    const int64_t went = (H->transfer_bf16 ? 2 : vs) + 4;  // a transfer entry: weight + column
     const Level& L = H->lv[j];
     const Level& C = H->lv[j + 1];
     const int64_t n = L.n, nnzo = L.nlow + L.nupp;
@@ -864,8 +903,8 @@ static int64_t level_bytes(const mgm_hierarchy* H, int j) {
         b += (H->nu1 == 1 ? L.nupp * ent + n * (4 + vs)           // residual -U e
                           : nnzo * ent + n * (4 + 4 * vs));        // residual b - A e
     }
-    b += L.pnnz * ent + (C.n + 1) * 4 + n * vs + C.n * vs;        // restriction
-    b += L.pnnz * ent + 2 * n * vs;                               // interpolation + correction
+    b += L.pnnz * went + (C.n + 1) * 4 + n * vs + C.n * vs;       // restriction
+    b += L.pnnz * went + 2 * n * vs;                              // interpolation + correction
     b += (int64_t)H->nu2 * (nnzo * ent + n * (4 + 3 * vs));       // post-smoothing sweeps
     return b;
 }

@@ -39,7 +39,7 @@ class StencilParams(C.Structure):
 class Params(C.Structure):
     _fields_ = [("n_min", C.c_int64), ("m", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int),
                 ("seed", C.c_uint64), ("persistent_sweeps", C.c_int), ("constraint", C.c_int), ("smoother", C.c_int),
-                ("cycle", C.c_int)]
+                ("cycle", C.c_int), ("transfer_bf16", C.c_int)]
 
 
 class SolveParams(C.Structure):
@@ -390,12 +390,13 @@ class Hierarchy:
     """MGM hierarchy (Alg. 2) owned by the library; V-cycle (Alg. 3) and FGMRES solve on it."""
 
     def __init__(self, xyz, rp, ci, v, n_min, m=3, nu1=1, nu2=1, precision="f32", seed=0, persistent_sweeps=5,
-                 constraint=False, smoother="mc", cycle="V"):
+                 constraint=False, smoother="mc", cycle="V", transfer_bf16=False):
         """persistent_sweeps: how the multicolour sweeps are launched (mgm_params; default 5, staged
         per-colour launches; 0 one plain launch per colour; 4 autotuned per level).
         constraint=True: surface Poisson (L = D) with the mean-zero constraint of Sec. 4.4.
         smoother: "mc" multicolour Gauss-Seidel or "lex" lexicographic Gauss-Seidel (the paper's).
-        cycle: "V" (Alg. 3), "W" or "F" (Sec. 4.5)."""
+        cycle: "V" (Alg. 3), "W" or "F" (Sec. 4.5).
+        transfer_bf16: the FP32 cycle reads its interpolation/restriction weights stored as BF16."""
         if smoother not in ("mc", "lex"):
             raise ValueError("smoother must be 'mc' or 'lex'")
         if cycle not in ("V", "W", "F"):
@@ -406,7 +407,8 @@ class Hierarchy:
         self.device = xyz.device
         self.constraint = bool(constraint)
         prm = Params(n_min, m, nu1, nu2, MGM_F32 if precision == "f32" else MGM_F64, seed, int(persistent_sweeps),
-                     int(constraint), 1 if smoother == "lex" else 0, {"V": 0, "W": 1, "F": 2}[cycle])
+                     int(constraint), 1 if smoother == "lex" else 0, {"V": 0, "W": 1, "F": 2}[cycle],
+                     int(bool(transfer_bf16)))
         h = C.c_void_p()
         self._h = None
         _check(lib().mgm_setup(_p(xyz), self.N, _p(rp), _p(ci), _p(v), C.byref(prm), C.byref(h), _stream()))

@@ -372,6 +372,39 @@ def test_vcycle_f32_matches_oracle(M, oracle, hier):
     assert np.linalg.norm(z32 - zo) <= 1e-4 * np.linalg.norm(zo)
 
 
+def _bf16(a):
+    """FP64 -> FP32 (nearest) -> BF16 (nearest, ties to even), as stored by transfer_bf16."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_vcycle_bf16_transfers_match_oracle(M, oracle, ico5, hier):
+    """FP32 cycle reading BF16-stored interpolation and restriction weights: within the FP32 cycle's
+    1e-4 of the oracle's cycle run with the same BF16-rounded weights; FGMRES converges in the same
+    iterations as with FP32 weights, to the same solution."""
+    import copy
+    x, nrm, idx, w, L = ico5
+    Hg, Ho = hier
+    Hb = copy.copy(Ho)
+    Hb.P = [P.copy() for P in Ho.P]
+    Hb.R = [R.copy() for R in Ho.R]
+    for P, R in zip(Hb.P, Hb.R):
+        P.data = _bf16(P.data)
+        R.data = _bf16(R.data)
+    Lt = (T(L.indptr.astype(np.int32)), T(L.indices.astype(np.int32)), T(L.data))
+    Gb = M.Hierarchy(T(x), *Lt, n_min=125, precision="f32", transfer_bf16=True)
+    r = np.random.default_rng(14).standard_normal(x.shape[0])
+    zo = oracle.vcycle(Hb, r)
+    z = H(Gb.vcycle(T(r)))
+    assert np.linalg.norm(z - zo) <= 1e-4 * np.linalg.norm(zo)
+    assert not np.array_equal(z, H(Hg["f32"].vcycle(T(r))))   # the option changes the weights read
+    f = 21.0 * I.y43(x)
+    u, info = Gb.solve(T(f), tol=1e-10)
+    u32, info32 = Hg["f32"].solve(T(f), tol=1e-10)
+    assert info["converged"] and abs(info["iters"] - info32["iters"]) <= 1, (info["iters"], info32["iters"])
+    assert np.linalg.norm(H(u) - H(u32)) <= 1e-8 * np.linalg.norm(H(u32))
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_solve_matches_oracle(M, oracle, ico5, hier, prec):
     x, nrm, idx, w, L = ico5

@@ -502,3 +502,41 @@ def test_w_and_f_cycles_contract_at_least_as_well_as_v(oracle):
     for cyc in "WF":
         u, it, rel = oracle.fgmres(L, H, f, tol=1e-10, cycle=cyc)
         assert rel <= 1e-10
+
+
+def test_bf16_weight_storage_keeps_fgmres_iterations(oracle):
+    """Storage precision of the preconditioner's operands (a design reading for the FP32 cycle, not
+    in the paper): with the interpolation/restriction weights rounded to BF16 the MGM-FGMRES
+    iteration count to 1e-10 is unchanged, and with the level operators' values also in BF16 it
+    rises by at most one (N = 16,384 sphere, PHS r^3 + degree 3, n = 50). FP16 is not an option for
+    the operators: their entries grow like 1/h^2 and overflow FP16's range at N = 65,536."""
+    x, nrm = I.fibonacci_sphere(16384, jitter=0.1, seed=2)
+    _, _, A = oracle.build_operator(x, nrm, 50, "rbf", 1, 3, 1.0)
+    H = oracle.setup(x, A, 250)
+    f = I.random_sh_rhs(x, 20, 2)
+
+    def bf16(a):
+        u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+        return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16).astype(np.uint32).view(np.float32).astype(np.float64)
+
+    def run(round_L, round_PR):
+        import copy
+        G = copy.copy(H)
+        G.L = [L.copy() for L in H.L]
+        G.P = [P.copy() for P in H.P]
+        G.R = [R.copy() for R in H.R]
+        for j in range(len(G.L) - 1):
+            if round_L:
+                G.L[j].data = bf16(G.L[j].data)
+        for P, R in zip(G.P, G.R):
+            if round_PR:
+                P.data = bf16(P.data)
+                R.data = bf16(R.data)
+        _, it, rel = oracle.fgmres(A, G, f, tol=1e-10)
+        assert rel <= 1e-10
+        return it
+
+    it64 = run(False, False)
+    assert run(False, True) == it64
+    assert it64 <= run(True, True) <= it64 + 1
+    assert np.max(np.abs(H.L[0].data)) > np.finfo(np.float16).max / 100   # 1/h^2 scale: ~1e3 here
