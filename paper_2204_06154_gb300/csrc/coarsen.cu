@@ -11,6 +11,7 @@
 // weight from scratch in ascending neighbour order, so every weight is the same IEEE sum as a
 // sequential recomputation and the kept set is bit-reproducible. Built with --fmad=false.
 #include <algorithm>
+#include <cstdio>
 
 #include "common.cuh"
 
@@ -199,6 +200,7 @@ void coarsen(const double* x, int64_t N, int64_t NH, int32_t* keep, cudaStream_t
     knn_device(x, N, x, N, 2, 1, idx2.get(), nullptr, s);
     Temp<unsigned long long> S(1, s);
     CK(cudaMemsetAsync(S.get(), 0, sizeof(unsigned long long), s));
+    trace_mark(s, "  wse:knn2");
     nn_fixed_sum_k<<<grid_for(N, 256), 256, 0, s>>>(x, idx2.get(), N, S.get());
     CK_LAUNCH();
     Temp<double> prm(3, s);
@@ -213,7 +215,9 @@ void coarsen(const double* x, int64_t N, int64_t NH, int32_t* keep, cudaStream_t
     }
     Temp<int32_t> rp, nbr;
     Temp<double> f;
+    trace_mark(s, "  wse:params");
     radius_graph(x, N, prm.get(), hp[0], rp, nbr, f, s);
+    trace_mark(s, "  wse:radius");
     Temp<char> live(N, s), dirty(N, s), sel(N, s);
     Temp<double> w(N, s);
     Temp<int32_t> cand(N, s);
@@ -225,29 +229,41 @@ void coarsen(const double* x, int64_t N, int64_t NH, int32_t* keep, cudaStream_t
     weights_k<<<grid_for(N, 256), 256, 0, s>>>(rp.get(), nbr.get(), f.get(), live.get(), dirty.get(), N, 0, w.get());
     CK_LAUNCH();
     const unsigned grid = (unsigned)std::min<int64_t>(grid_for(N, 256), 152 * 8);
-    for (int64_t round = 0;; ++round) {
-        if (round % WSE_BATCH == 0) {
-            WseState h;
-            to_host(&h, st.get(), 1, s);
-            if (h.nlive <= NH) break;
-            if (round > 0 && h.ncand <= 0 && h.need > 0) fail(MGM_ERR_UNSUPPORTED, "elimination round without candidates");
-            if (round > N + WSE_BATCH) fail(MGM_ERR_UNSUPPORTED, "elimination did not terminate");
-        }
-        wse_round_begin_k<<<1, 1, 0, s>>>(st.get(), (long long)NH);
+    // one elimination round: seven kernels that return at once when nothing is left to remove
+    auto round_on = [&](cudaStream_t q) {
+        wse_round_begin_k<<<1, 1, 0, q>>>(st.get(), (long long)NH);
         CK_LAUNCH();
-        count_pos_k<<<grid, 256, 0, s>>>(live.get(), w.get(), N, st.get());
+        count_pos_k<<<grid, 256, 0, q>>>(live.get(), w.get(), N, st.get());
         CK_LAUNCH();
-        candidates_k<<<grid, 256, 0, s>>>(rp.get(), nbr.get(), live.get(), w.get(), N, st.get(), cand.get());
+        candidates_k<<<grid, 256, 0, q>>>(rp.get(), nbr.get(), live.get(), w.get(), N, st.get(), cand.get());
         CK_LAUNCH();
-        select_top_k<<<1, 1024, 0, s>>>(cand.get(), w.get(), st.get(), sel.get());
+        select_top_k<<<1, 1024, 0, q>>>(cand.get(), w.get(), st.get(), sel.get());
         CK_LAUNCH();
-        remove_k<<<grid, 256, 0, s>>>(cand.get(), sel.get(), st.get(), rp.get(), nbr.get(), live.get(), dirty.get());
+        remove_k<<<grid, 256, 0, q>>>(cand.get(), sel.get(), st.get(), rp.get(), nbr.get(), live.get(), dirty.get());
         CK_LAUNCH();
-        weights_k<<<grid_for(N, 256), 256, 0, s>>>(rp.get(), nbr.get(), f.get(), live.get(), dirty.get(), N, 1, w.get());
+        weights_k<<<grid_for(N, 256), 256, 0, q>>>(rp.get(), nbr.get(), f.get(), live.get(), dirty.get(), N, 1, w.get());
         CK_LAUNCH();
-        wse_round_end_k<<<1, 1, 0, s>>>(st.get());
+        wse_round_end_k<<<1, 1, 0, q>>>(st.get());
         CK_LAUNCH();
+    };
+    // WSE_BATCH rounds captured once as a CUDA graph and replayed; the host reads the state between
+    // replays (rounds after the last useful one are no-ops)
+    GraphBatch gb;
+    gb.capture([&](cudaStream_t q) {
+        for (int r = 0; r < WSE_BATCH; ++r) round_on(q);
+    });
+    int64_t rounds_done = 0;
+    for (int64_t batch = 0;; ++batch) {
+        WseState h;
+        to_host(&h, st.get(), 1, s);
+        rounds_done = batch * WSE_BATCH;
+        if (h.nlive <= NH) break;
+        if (batch > 0 && h.ncand <= 0 && h.need > 0) fail(MGM_ERR_UNSUPPORTED, "elimination round without candidates");
+        if (rounds_done > N + WSE_BATCH) fail(MGM_ERR_UNSUPPORTED, "elimination did not terminate");
+        gb.launch(s);
     }
+    if (trace_on()) std::fprintf(stderr, "[mgm setup] wse rounds: %lld\n", (long long)rounds_done);
+    trace_mark(s, "  wse:rounds");
     Temp<int32_t> fl(N, s), pos(N + 1, s);
     live_flags_k<<<grid_for(N, 256), 256, 0, s>>>(live.get(), N, fl.get());
     CK_LAUNCH();

@@ -55,6 +55,10 @@ mgm_status guarded(F&& body) {
 // ---------------------------------------------------------------------------------------------
 // device buffers
 // ---------------------------------------------------------------------------------------------
+// set-up tracing (util.cu): with MGM_TRACE set, synchronise and print the time since the last mark
+bool trace_on();
+void trace_mark(cudaStream_t s, const char* what, int level = -1);
+
 // the library's stream-ordered scratch pool on the current device (util.cu), and a release of its
 // cached memory down to keep_bytes
 cudaMemPool_t scratch_pool();
@@ -187,6 +191,45 @@ int64_t csr_nnz(const int32_t* rp, int64_t nrows, cudaStream_t s);
 // argument validation (synchronise): all a[i] in [0, hi); CSR row pointers monotone from 0
 void validate_index(const int32_t* a, int64_t cnt, int64_t hi, const char* what, cudaStream_t s);
 void validate_csr(int64_t nrows, int64_t ncols, const int32_t* rp, const int32_t* ci, const char* what, cudaStream_t s);
+
+// A fixed sequence of launches captured once on a private stream and replayed as a CUDA graph.
+// Captured launches are not counted; each replay counts them.
+struct GraphBatch {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    template <class F>
+    void capture(F&& body) {
+        cudaStream_t cs = nullptr;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        const int64_t before = thread_launches();
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            try {
+                body(cs);
+            } catch (...) {
+                cudaStreamEndCapture(cs, &g);
+                if (g) cudaGraphDestroy(g);
+                cudaStreamDestroy(cs);
+                throw;
+            }
+            e = cudaStreamEndCapture(cs, &g);
+        }
+        kernels = thread_launches() - before;
+        note_launch(-kernels);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        CK(e);
+    }
+    void launch(cudaStream_t s) {
+        CK(cudaGraphLaunch(exec, s));
+        note_launch(kernels);
+    }
+    ~GraphBatch() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
 
 // Blocks of `kernel` (with `threads` threads and `smem` dynamic shared memory) that can be
 // co-resident on the current device, at most `per_sm_cap` an SM (0: no cap); cached per device and

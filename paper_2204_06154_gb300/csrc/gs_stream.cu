@@ -769,12 +769,21 @@ bool colour_prepare(mgm_hierarchy* H, Level& L, int B, int G, cudaStream_t s) {
         L.csm1[c] = (int)std::max<int64_t>(16, (int64_t)h[c].y * (4 + ts));
         if (L.csm1[c] > limit) return false;
     }
-    const void* ks[2][4];
-    for (int mode = 0; mode < 2; ++mode)
-        for (int gi = 0; gi < 4; ++gi) {
-            ks[mode][gi] = H->precision == MGM_F32 ? colour_kernel<float>(mode, 1 << gi) : colour_kernel<double>(mode, 1 << gi);
-            CK(cudaFuncSetAttribute(ks[mode][gi], cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    {   // the kernels' shared-memory limit, once per device and precision for the process
+        static std::mutex mu;
+        static std::map<std::pair<int, int>, bool> done;
+        std::lock_guard<std::mutex> lk(mu);
+        bool& d = done[{dev, H->precision}];
+        if (!d) {
+            for (int mode = 0; mode < 2; ++mode)
+                for (int gi = 0; gi < 4; ++gi) {
+                    const void* k = H->precision == MGM_F32 ? colour_kernel<float>(mode, 1 << gi)
+                                                            : colour_kernel<double>(mode, 1 << gi);
+                    CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+                }
+            d = true;
         }
+    }
     L.sB = B;
     L.sG = G;
     L.csched = 1;

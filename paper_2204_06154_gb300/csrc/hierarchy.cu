@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <memory>
+#include <string>
+#include <vector>
 
 #include "hier.cuh"
 
@@ -131,12 +133,12 @@ __global__ void __launch_bounds__(GJ_THREADS) gj_coop_k(double* A0, double* A1, 
             if (threadIdx.x == 0) *err = 1;
             return;
         }
-        const double akk = cur[piv * ld + k];
+        const double rk = 1.0 / cur[piv * ld + k];  // the pivot row scaled by the reciprocal (dgetf2's form)
         for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
             const double* src = cur + (i == piv ? k : i) * ld;
             const double m = i == k ? 0.0 : src[k];
             for (int64_t j = k + threadIdx.x; j < ld; j += blockDim.x) {
-                const double pr = cur[piv * ld + j] / akk;
+                const double pr = cur[piv * ld + j] * rk;
                 nxt[i * ld + j] = i == k ? pr : (m == 0.0 ? src[j] : fma(-m, pr, src[j]));
             }
         }
@@ -186,7 +188,7 @@ static void dense_inverse(const Level& L, const double* border, Buf<double>& inv
         border_dense_k<<<grid_for(n, 128), 128, 0, s>>>(border, nl, A.get());
         CK_LAUNCH();
     }
-    const int mb = coresident_blocks((const void*)gj_coop_k, GJ_THREADS, 0, 1);  // one block an SM
+    const int mb = coresident_blocks((const void*)gj_coop_k, GJ_THREADS, 0, 1);
     const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(mb, n));
     double* a0 = A.get();
     double* a1 = B.get();
@@ -538,18 +540,9 @@ __global__ void compose_k(const int32_t* a, const int32_t* b, int64_t n, int32_t
 // With MGM_TRACE set in the environment, setup synchronises at each phase boundary and prints the
 // phase's wall time to stderr (tracing only; off by default, no effect on results).
 struct Trace {
-    bool on;
     cudaStream_t s;
-    std::chrono::steady_clock::time_point t;
-    explicit Trace(cudaStream_t st) : on(std::getenv("MGM_TRACE") != nullptr), s(st), t(std::chrono::steady_clock::now()) {}
-    void mark(const char* what, int level) {
-        if (!on) return;
-        cudaStreamSynchronize(s);
-        auto now = std::chrono::steady_clock::now();
-        double ms = std::chrono::duration<double, std::milli>(now - t).count();
-        std::fprintf(stderr, "[mgm setup] level %d %-12s %9.3f ms\n", level, what, ms);
-        t = now;
-    }
+    explicit Trace(cudaStream_t st) : s(st) { trace_mark(s, "start"); }
+    void mark(const char* what, int level) { trace_mark(s, what, level); }
 };
 
 mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int32_t* ci, const double* v,
@@ -594,6 +587,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         L.nnz = nnz;
         L.perm.alloc(N);
         rcm(N, rp, ci, L.perm.get(), s);
+        tr.mark("  rcm", 0);
         L.X.alloc(3 * N);
         gather_xyz(xyz, L.perm.get(), L.X.get(), N, s);
         L.rp.alloc(N + 1);
@@ -619,6 +613,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         Temp<int32_t> R_rp(NH + 1, s), R_ci(std::max<int64_t>(pnnz, 1), s);
         Temp<double> R_v(std::max<int64_t>(pnnz, 1), s);
         csr_transpose(F.n, NH, P_rp.get(), P_ci.get(), P_v.get(), R_rp.get(), R_ci.get(), R_v.get(), s);  // restriction
+        tr.mark("  transpose", j);
         // Galerkin operator L_{j+1} = R (L_j P)
         Temp<int32_t> T_rp(F.n + 1, s);
         int64_t tnnz = spgemm_symbolic(F.n, F.rp.get(), F.ci.get(), P_rp.get(), P_ci.get(), T_rp.get(), s);
@@ -626,6 +621,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         Temp<double> T_v(std::max<int64_t>(tnnz, 1), s);
         spgemm_numeric(F.n, F.rp.get(), F.ci.get(), F.v.get(), P_rp.get(), P_ci.get(), P_v.get(), T_rp.get(), T_ci.get(),
                        T_v.get(), s);
+        tr.mark("  galerkin:LP", j);
         Temp<int32_t> G_rp(NH + 1, s);
         int64_t gnnz = spgemm_symbolic(NH, R_rp.get(), R_ci.get(), T_rp.get(), T_ci.get(), G_rp.get(), s);
         Temp<int32_t> G_ci(std::max<int64_t>(gnnz, 1), s);
@@ -636,6 +632,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         // RCM of L_{j+1}; renumber coarse points and the interpolation's columns
         C.perm.alloc(NH);
         rcm(NH, G_rp.get(), G_ci.get(), C.perm.get(), s);
+        tr.mark("  rcm", j);
         C.X.alloc(3 * NH);
         gather_xyz(Xc.get(), C.perm.get(), C.X.get(), NH, s);
         C.nnz = gnnz;
@@ -655,7 +652,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         CK_LAUNCH();
         tr.mark("rcm+permute", j);
     }
-    // colourings, solve orders, transfers
+    // colourings and solve orders
     for (int j = 0; j + 1 < p; ++j) {
         Level& L = H->lv[j];
         L.colour.alloc(L.n);
@@ -671,6 +668,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         build_solve_layout(L, false, s, lex);
         tr.mark("layout", j);
     }
+    // transfers
     if (p == 1) build_solve_layout(H->lv[0], true, s);  // one group: serves the outer operator only
     for (int j = 0; j + 1 < p; ++j)
         build_transfers(H->lv[j], (j + 2 < p) ? &H->lv[j + 1] : nullptr, H->lv[j + 1].n, prm->m, s);

@@ -604,7 +604,9 @@ __global__ void __launch_bounds__(RAD_WARPS * 32) radius_k(const Grid* gp, const
 // sorted by index in local memory as it is found and writes rows of at most RT_CAP entries (the
 // warp kernel above fills the listed longer ones). Same candidates and tests, so the same lists.
 constexpr int RT_CAP = 48;
-template <bool FILL>
+// STAGE (with FILL): one pass that also counts, writing each row of at most RT_CAP entries to its
+// fixed slot i * RT_CAP of nbr / f (compacted after the scan of the counts)
+template <bool FILL, bool STAGE = false>
 __global__ void __launch_bounds__(128) radius_thread_k(const Grid* gp, const int32_t* start, const int32_t* sidx,
                                                        const double* sxyz, const float4* s32, const double* x, int64_t n,
                                                        const double* prm, int32_t* cnt, const int32_t* rowptr,
@@ -650,13 +652,13 @@ __global__ void __launch_bounds__(128) radius_thread_k(const Grid* gp, const int
                     ++count;
                 }
             }
-    if (!FILL) {
+    if (!FILL || STAGE) {
         cnt[i] = count;
         if (count > RT_CAP) longrows[atomicAdd(nlong, 1)] = (int32_t)i;
-        return;
+        if (!FILL) return;
     }
     if (count > RT_CAP) return;
-    const int64_t base = rowptr[i];
+    const int64_t base = STAGE ? i * RT_CAP : (int64_t)rowptr[i];
     for (int q = 0; q < count; ++q) {
         const double dh = dl[q] > rmin ? dl[q] : rmin;
         const double tt = 1.0 - dh / two_rmax;
@@ -666,8 +668,21 @@ __global__ void __launch_bounds__(128) radius_thread_k(const Grid* gp, const int
     }
 }
 
+// rows of at most RT_CAP entries from their fixed slots to their CSR positions
+__global__ void radius_compact_k(const int32_t* cnt, const int32_t* rowptr, const int32_t* snbr, const double* sf, int64_t n,
+                                 int32_t* nbr, double* f) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / RT_CAP;
+    const int q = (int)(t % RT_CAP);
+    if (i >= n || q >= cnt[i] || cnt[i] > RT_CAP) return;
+    nbr[rowptr[i] + q] = snbr[t];
+    f[rowptr[i] + q] = sf[t];
+}
+
 // Builds the neighbour graph for the elimination. prm: device {two_rmax, rmin}; h_hint: a host
-// estimate of two_rmax used to size the grid cells.
+// estimate of two_rmax used to size the grid cells. One search pass writes the lists of at most
+// RT_CAP entries to fixed slots and counts every row; after the scan they are compacted, and the
+// longer lists are searched again by a warp each.
 void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, Temp<int32_t>& rowptr,
                   Temp<int32_t>& nbr, Temp<double>& f, cudaStream_t s) {
     DevGrid G;
@@ -675,9 +690,11 @@ void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, 
     Temp<int32_t> cnt(n + 1, s), longrows(n, s);
     Temp<int> err(2, s);  // [0] warp-kernel overflow, [1] rows above RT_CAP
     CK(cudaMemsetAsync(err.get(), 0, 2 * sizeof(int), s));
-    radius_thread_k<false><<<grid_for(n, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
-                                                            G.s32.get(), x, n, prm, cnt.get(), nullptr, nullptr, nullptr,
-                                                            longrows.get(), err.get() + 1);
+    Temp<int32_t> snbr(n * RT_CAP, s);
+    Temp<double> sf(n * RT_CAP, s);
+    radius_thread_k<true, true><<<grid_for(n, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
+                                                                 G.s32.get(), x, n, prm, cnt.get(), nullptr, snbr.get(),
+                                                                 sf.get(), longrows.get(), err.get() + 1);
     CK_LAUNCH();
     int ecnt[2];
     to_host(ecnt, err.get(), 2, s);
@@ -686,9 +703,8 @@ void radius_graph(const double* x, int64_t n, const double* prm, double h_hint, 
     int64_t nnz = csr_nnz(rowptr.get(), n, s);
     nbr.alloc(nnz > 0 ? nnz : 1, s);
     f.alloc(nnz > 0 ? nnz : 1, s);
-    radius_thread_k<true><<<grid_for(n, 128), 128, 0, s>>>(G.g.get(), G.start.get(), G.sidx.get(), G.sxyz.get(),
-                                                           G.s32.get(), x, n, prm, nullptr, rowptr.get(), nbr.get(), f.get(),
-                                                           nullptr, nullptr);
+    radius_compact_k<<<grid_for(n * RT_CAP, 256), 256, 0, s>>>(cnt.get(), rowptr.get(), snbr.get(), sf.get(), n, nbr.get(),
+                                                             f.get());
     CK_LAUNCH();
     if (ecnt[1] > 0) {  // the longer lists, one warp each
         radius_k<true><<<grid_for(ecnt[1], RAD_WARPS), RAD_WARPS * 32, 0, s>>>(

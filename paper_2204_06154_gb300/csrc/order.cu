@@ -203,45 +203,6 @@ __global__ void reverse_k(const int32_t* order, int64_t N, int32_t* perm) {
     if (i < N) perm[i] = order[N - 1 - i];
 }
 
-// A fixed sequence of launches captured once on a private stream and replayed as a CUDA graph.
-// Captured launches are not counted; each replay counts them.
-struct GraphBatch {
-    cudaGraphExec_t exec = nullptr;
-    int64_t kernels = 0;
-    template <class F>
-    void capture(F&& body) {
-        cudaStream_t cs = nullptr;
-        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        const int64_t before = thread_launches();
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            try {
-                body(cs);
-            } catch (...) {
-                cudaStreamEndCapture(cs, &g);
-                if (g) cudaGraphDestroy(g);
-                cudaStreamDestroy(cs);
-                throw;
-            }
-            e = cudaStreamEndCapture(cs, &g);
-        }
-        kernels = thread_launches() - before;
-        note_launch(-kernels);
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
-        if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cs);
-        CK(e);
-    }
-    void launch(cudaStream_t s) {
-        CK(cudaGraphLaunch(exec, s));
-        note_launch(kernels);
-    }
-    ~GraphBatch() {
-        if (exec) cudaGraphExecDestroy(exec);
-    }
-};
-
 void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStream_t s) {
     REQUIRE(N >= 1 && N < 0x7fffffff, "N out of range");
     REQUIRE(rp && ci && perm, "null array");
@@ -251,6 +212,7 @@ void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStr
     Temp<int32_t> adj(snnz > 0 ? snnz : 1, s);
     sort_by_degree_k<<<grid_for(N, SBD_WARPS), SBD_WARPS * 32, 0, s>>>(srp.get(), sci.get(), N, adj.get());
     CK_LAUNCH();
+    trace_mark(s, "  rcm:pattern");
     Temp<int32_t> order(N, s), pos(N, s), claim(N, s), cnt(N + 1, s), off(N + 1, s);
     fill_i32(pos.get(), -1, N, s);
     fill_i32(claim.get(), INT_MAX, N, s);
@@ -285,6 +247,7 @@ void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStr
         else
             for (int l = 0; l < RCM_BATCH; ++l) level(s);
     }
+    trace_mark(s, "  rcm:bfs");
     reverse_k<<<grid_for(N, 256), 256, 0, s>>>(order.get(), N, perm);
     CK_LAUNCH();
 }
@@ -512,6 +475,7 @@ void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32
     REQUIRE(rp && ci && colour, "null array");
     Temp<int32_t> srp, sci;
     sym_pattern(N, rp, ci, srp, sci, s);
+    trace_mark(s, "  colour:pattern");
     Temp<int> ctr(2, s);  // [0] uncoloured vertices remain, [1] max colour
     // MGM_COLOR_ROUNDS in the environment selects the JP rounds directly (they are otherwise the
     // fallback only; the tests use it to check that both give the same colours)

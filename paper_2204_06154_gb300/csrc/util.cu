@@ -2,6 +2,8 @@
 // permutation, the symmetrised pattern used by RCM and colouring. Every output is deterministic
 // (independent of thread scheduling): where atomics place entries, the rows are sorted afterwards.
 #include <atomic>
+#include <chrono>
+#include <cstdlib>
 #include <cstdio>
 
 #include <map>
@@ -443,6 +445,22 @@ void sym_pattern(int64_t N, const int32_t* rp, const int32_t* ci, Temp<int32_t>&
                                                                           srp.get(), sci.get());
         CK_LAUNCH();
     }
+}
+
+// Set-up tracing: with MGM_TRACE set in the environment, synchronise `s` and print the wall time
+// since the calling thread's previous mark (off by default; no effect on results).
+bool trace_on() {
+    static const bool on = std::getenv("MGM_TRACE") != nullptr;
+    return on;
+}
+void trace_mark(cudaStream_t s, const char* what, int level) {
+    if (!trace_on()) return;
+    static thread_local std::chrono::steady_clock::time_point last = std::chrono::steady_clock::now();
+    cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[mgm setup] level %d %-16s %9.3f ms\n", level, what,
+                 std::chrono::duration<double, std::milli>(now - last).count());
+    last = now;
 }
 
 // The library's scratch pool on each device: stream-ordered allocations that are kept for reuse
