@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--c5-size", type=int, default=1 << 22, help="points of the c5 bumpy sphere")
     ap.add_argument("--batch-problems", type=int, default=64, help="surfaces in the batched measurement of the c2 line")
     ap.add_argument("--eigs", type=int, default=16, help="shift-invert eigenpairs computed on the 1M sphere (0: none)")
-    ap.add_argument("--learned-surfaces", type=int, default=24,
+    ap.add_argument("--learned-surfaces", type=int, default=200,
                     help="training surfaces of the learned-correction measurement (0 skips it)")
     ap.add_argument("--learned-eval-size", type=int, default=1 << 20, help="points of the held-out bumpy torus")
     ap.add_argument("--single", action="store_true",
@@ -687,7 +687,7 @@ def main():
                      "peak_source": f"mgm_probe_fp64_fma during this run: {res['fp64_gflops']:.0f} GFLOP/s of FP64 "
                                     f"multiply-adds (2 flops each) = {fp64_pipe_peak:.1f} G FP64-pipe op/s "
                                     "(MEASURED_PEAKS.json has no FP64 figure)"},
-        "vcycle_roofline": {"kernel": "gs_colour_k<1,float,1> (finest-level multicolour GS sweep, staged per colour)",
+        "vcycle_roofline": {"kernel": "gs_colour_k<1,float,2> (finest-level multicolour GS sweep, staged per colour)",
                             "bound": "hbm",
                             "achieved": round(sweep_gbs, 1) if sweep_gbs else None, "peak": hbm, "unit": "GB/s",
                             "frac": round(sweep_gbs / hbm, 3) if sweep_gbs else None, "traffic": None,

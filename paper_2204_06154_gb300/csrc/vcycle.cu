@@ -998,7 +998,10 @@ void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStrea
         CK(cudaEventElapsedTime(&ms, e0, e1));
         out->sweep_ms = ms / reps;
         out->sweep_bytes = (L.nlow + L.nupp) * (vs + 4) + L.n * (4 + 3 * vs);
-        out->sweep_launches = (H->persistent || L.stream) ? 1 : (int32_t)(L.cptr.size() - 1);  // kernels (copies not counted)
+        // kernels a sweep (copies not counted): one for the persistent and streamed schedules, one a
+        // colour for the per-colour launches (plain or staged)
+        const bool one = L.stream || (!L.csched && (H->sweep_mode == 1 || H->sweep_mode == 2));
+        out->sweep_launches = one ? 1 : (int32_t)(L.cptr.size() - 1);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
