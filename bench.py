@@ -478,24 +478,29 @@ def bench_pattern(N, steps, warmup, host_steps=20):
             "u_range": [round(float(u.min()), 4), round(float(u.max()), 4)]}
 
 
+# Arm (implementer 0x41) part numbers of the cores this runs on, as /proc/cpuinfo reports them
+ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+             "0xd49": "Arm Neoverse N2", "0xd8e": "Arm Neoverse N3", "0xd84": "Arm Neoverse V3"}
+
+
 def cpu_info():
     """Host cores and CPU model (the oracle runs single-threaded)."""
-    model = None
+    fields = {}
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
-                key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu part", "hardware") and ":" in line:
-                    model = line.split(":", 1)[1].strip()
-                    if key == "model name":
-                        break
+                if ":" in line:
+                    key, val = line.split(":", 1)
+                    fields.setdefault(key.strip().lower(), val.strip())
     except OSError:
         pass
-    try:
+    model = fields.get("model name")
+    if not model and "cpu part" in fields:
+        part = fields["cpu part"].lower()
+        model = ARM_PARTS.get(part, f"Arm CPU part {part}") + f" (implementer {fields.get('cpu implementer', '?')})"
+    if not model:
         import platform
-        model = model or platform.processor() or platform.machine()
-    except Exception:
-        pass
+        model = platform.processor() or platform.machine()
     return {"nproc": os.cpu_count(), "cpu": model}
 
 
