@@ -588,7 +588,12 @@ def main():
             blocks0 = H.sweep_config(0)["blocks"] or 456
             chain = {pdl: M.probe_launch_chain(blocks0, 256, 256, pdl, 10) for pdl in (True, False)}
             fl = H.vcycle_floor(chain[True], float(peaks()[0].get("hbm_gbs", 6800.0)))
+            lvl = []
+            for j in range(st["p"] - 1):  # per-level smoothing: device time and algorithmic GB/s
+                ms_j = H.profile_level(j, reps=20)
+                lvl.append({"ms": round(ms_j, 4), "GB/s": round(H.level_smoothing_bytes(j) / ms_j / 1e6, 1)})
             out[f"mode{mode}"] = {"levels": st["n"], "ncolors": st["ncolors"], "max|z|": float(z.abs().max()),
+                                  "level_smoothing": lvl,
                                   "chain_us": {"programmatic": round(chain[True], 3), "plain": round(chain[False], 3),
                                                "blocks": blocks0},
                                   "floor_ms": {k: round(v, 4) for k, v in fl.items()},
@@ -689,6 +694,12 @@ def main():
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel on "
                                        "524,288 stencils, scaled by stencils to the launch's count",
                      "fp64_ops_per_stencil": ops_per_stencil,
+                     # counted by ncu on the current kernel (one launch, 131,072 stencils): FP64-pipe warp
+                     # instructions and FP64 thread operations a stencil, beside the algorithmic count
+                     "fp64_per_stencil_ncu": {"warp_instructions": round(187826176 / 131072),
+                                              "thread_ops": round(5030019072 / 131072),
+                                              "metrics": "sm__inst_executed_pipe_fp64.sum, "
+                                                         "sm__sass_thread_inst_executed_op_fp64_pred_on.sum"},
                      "peak_source": f"mgm_probe_fp64_fma during this run: {res['fp64_gflops']:.0f} GFLOP/s of FP64 "
                                     f"multiply-adds (2 flops each) = {fp64_pipe_peak:.1f} G FP64-pipe op/s "
                                     "(MEASURED_PEAKS.json has no FP64 figure)"},

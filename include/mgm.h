@@ -438,6 +438,11 @@ mgm_status mgm_autotune(mgm_hierarchy* H, int reps, int use_cache, mgm_stream st
  * synchronises. */
 mgm_status mgm_profile_level(mgm_hierarchy* H, int j, int reps, float* ms_out, mgm_stream stream);
 
+/* Measurement (not part of the method): the algorithmic bytes of level j's smoothing work in one
+ * V-cycle, the work mgm_profile_level times (pre-smoothing sweeps with their residual, and the
+ * post-smoothing sweeps; counted as mgm_profile counts them). Host only. */
+mgm_status mgm_level_smoothing_bytes(const mgm_hierarchy* H, int j, int64_t* bytes_out);
+
 /* Measurement (not part of the method): the device's FP64 fused-multiply-add rate in GFLOP/s (2
  * flops a multiply-add), from `reps` launches of a kernel whose threads run eight independent
  * multiply-add chains each (8 blocks of 256 threads an SM). The denominator of the FP64-pipe

@@ -271,6 +271,13 @@ mgm_status mgm_sweep_config_get(const mgm_hierarchy* H, int j, mgm_sweep_config*
     return guarded([&] { sweep_config_get(H, j, out); });
 }
 
+mgm_status mgm_level_smoothing_bytes(const mgm_hierarchy* H, int j, int64_t* bytes_out) {
+    return guarded([&] {
+        REQUIRE(H && bytes_out && j >= 0 && j + 1 < H->p, "bad argument");
+        *bytes_out = level_smoothing_bytes(H, j);
+    });
+}
+
 mgm_status mgm_profile_level(mgm_hierarchy* H, int j, int reps, float* ms_out, mgm_stream stream) {
     return guarded([&] {
         REQUIRE(H && ms_out && reps >= 1 && j >= 0 && j + 1 < H->p, "bad argument");

@@ -154,6 +154,7 @@ void check_device_error(mgm_hierarchy* H, cudaStream_t s);
 int barrier_timeout_probe(int nblocks, unsigned long long limit, cudaStream_t s);
 void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
 double vcycle_floor_ms(const mgm_hierarchy* H, double chain_us, double gbs, double* bytes_ms, double* chain_ms);
+int64_t level_smoothing_bytes(const mgm_hierarchy* H, int j);
 // krylov.cu
 bool solve_graph_supported(const mgm_hierarchy* H, const mgm_solve_params* sp);
 void reaction_steps(mgm_hierarchy* Hu, mgm_hierarchy* Hv, int model, const double* prm, double dt, double* u, double* v,

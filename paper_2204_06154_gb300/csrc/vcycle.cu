@@ -909,6 +909,17 @@ static int64_t level_bytes(const mgm_hierarchy* H, int j) {
     return b;
 }
 
+// the smoothing part of level_bytes: the pre-smoothing sweeps with their residual and the
+// post-smoothing sweeps (what time_level_smoothing times)
+int64_t level_smoothing_bytes(const mgm_hierarchy* H, int j) {
+    const Level& L = H->lv[j];
+    const Level& C = H->lv[j + 1];
+    const int64_t vs = H->precision == MGM_F32 ? 4 : 8;
+    const int64_t went = (H->transfer_bf16 ? 2 : vs) + 4;
+    const int64_t transfers = L.pnnz * went + (C.n + 1) * 4 + L.n * vs + C.n * vs + L.pnnz * went + 2 * L.n * vs;
+    return level_bytes(H, j) - transfers;
+}
+
 int64_t vcycle_bytes(const mgm_hierarchy* H) {
     int64_t b = 0;
     for (int j = 0; j + 1 < H->p; ++j) b += level_bytes(H, j);

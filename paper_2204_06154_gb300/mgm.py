@@ -67,7 +67,7 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
            "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs", "mgm_reaction_rhs",
            "mgm_sweep_config_set", "mgm_sweep_config_get", "mgm_autotune", "mgm_profile_level", "mgm_reaction_steps",
-           "mgm_probe_fp64_fma", "mgm_probe_launch_chain", "mgm_vcycle_floor"]
+           "mgm_probe_fp64_fma", "mgm_probe_launch_chain", "mgm_vcycle_floor", "mgm_level_smoothing_bytes"]
 
 
 _SCHEDULES = ["launch", "stream", "resident", "colour"]
@@ -119,6 +119,7 @@ def lib():
         L.mgm_probe_fp64_fma.argtypes = [I, C.POINTER(C.c_double), P]
         L.mgm_probe_launch_chain.argtypes = [I, I, I, I, I, C.POINTER(C.c_double), P]
         L.mgm_vcycle_floor.argtypes = [P, C.c_double, C.c_double] + [C.POINTER(C.c_double)] * 3
+        L.mgm_level_smoothing_bytes.argtypes = [P, I, C.POINTER(C.c_int64)]
         L.mgm_check_bounded_wait.argtypes = [I, I64, C.POINTER(C.c_int), P]
         L.mgm_kernel_launches.argtypes = []
         L.mgm_kernel_launches.restype = C.c_int64
@@ -485,6 +486,12 @@ class Hierarchy:
         ms = C.c_float(0.0)
         _check(lib().mgm_profile_level(self._h, level, reps, C.byref(ms), _stream()))
         return ms.value
+
+    def level_smoothing_bytes(self, level):
+        """Algorithmic bytes of a level's smoothing work in one V-cycle (what profile_level times)."""
+        b = C.c_int64(0)
+        _check(lib().mgm_level_smoothing_bytes(self._h, level, C.byref(b)))
+        return b.value
 
     def autotune(self, reps=5, use_cache=True):
         """Per-level choice of sweep schedule by timed trials (mgm_autotune); returns the choices."""
