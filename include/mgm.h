@@ -438,6 +438,14 @@ mgm_status mgm_autotune(mgm_hierarchy* H, int reps, int use_cache, mgm_stream st
  * synchronises. */
 mgm_status mgm_profile_level(mgm_hierarchy* H, int j, int reps, float* ms_out, mgm_stream stream);
 
+/* The cluster-resident coarse tail of the FP32 V-cycle (persistent_sweeps = 5, unconstrained
+ * V(1,1)-cycles; not of the paper: how Alg. 3's coarse levels are launched). Levels top..p-1 run as
+ * one launch of a thread-block cluster of `cluster` CTAs: each CTA keeps its rows' matrix entries,
+ * transfer weights and a copy of every vector the steps gather from in its shared memory, writes
+ * new values into all copies through distributed shared memory, and cluster barriers separate the
+ * colours and the transfers. top is the highest level whose data fit (0: no tail). Host only. */
+mgm_status mgm_tail_info(const mgm_hierarchy* H, int* top_out, int* cluster_out);
+
 /* Measurement (not part of the method): the algorithmic bytes of level j's smoothing work in one
  * V-cycle, the work mgm_profile_level times (pre-smoothing sweeps with their residual, and the
  * post-smoothing sweeps; counted as mgm_profile counts them). Host only. */

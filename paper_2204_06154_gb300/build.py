@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "libmgm.so")
 BUILD = os.path.join(HERE, "_build")
 
 EXACT = ["util", "knn", "knn_noalloc", "stencil", "coarsen", "order", "transfer", "hierarchy"]
-FAST = ["vcycle", "gs_stream", "krylov", "multi", "learned", "eigs", "pattern", "capi"]
+FAST = ["vcycle", "gs_stream", "tail", "krylov", "multi", "learned", "eigs", "pattern", "capi"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -271,6 +271,14 @@ mgm_status mgm_sweep_config_get(const mgm_hierarchy* H, int j, mgm_sweep_config*
     return guarded([&] { sweep_config_get(H, j, out); });
 }
 
+mgm_status mgm_tail_info(const mgm_hierarchy* H, int* top_out, int* cluster_out) {
+    return guarded([&] {
+        REQUIRE(H && top_out && cluster_out, "bad argument");
+        *top_out = H->tail_top;
+        *cluster_out = H->tail_cl;
+    });
+}
+
 mgm_status mgm_level_smoothing_bytes(const mgm_hierarchy* H, int j, int64_t* bytes_out) {
     return guarded([&] {
         REQUIRE(H && bytes_out && j >= 0 && j + 1 < H->p, "bad argument");

@@ -104,6 +104,14 @@ struct mgm_hierarchy {
     int sweep_mode = 0;         // 0: a launch per colour, 1: grid barriers, 2: per-row ready flags
     bool persistent = false;    // sweep_mode != 0
     mgm::Buf<int> err;
+    // cluster-resident coarse tail of the FP32 V-cycle (tail.cu): levels tail_top..p-1 in one
+    // thread-block-cluster launch (0: none)
+    int tail_top = 0;
+    int tail_cl = 0;                 // CTAs of the cluster
+    size_t tail_smem = 0;            // dynamic shared memory a CTA
+    size_t tail_stride = 0;          // bytes between the CTAs' blobs
+    std::vector<unsigned> tail_bytes;  // each CTA's blob size
+    mgm::Buf<unsigned char> tail_blob;
     // V-cycle graph (captured lazily)
     cudaGraphExec_t vgraph = nullptr;
     int64_t graph_kernels = 0;  // kernel nodes in vgraph
@@ -155,6 +163,9 @@ int barrier_timeout_probe(int nblocks, unsigned long long limit, cudaStream_t s)
 void profile_vcycle(mgm_hierarchy* H, int reps, mgm_profile_info* out, cudaStream_t s);
 double vcycle_floor_ms(const mgm_hierarchy* H, double chain_us, double gbs, double* bytes_ms, double* chain_ms);
 int64_t level_smoothing_bytes(const mgm_hierarchy* H, int j);
+// cluster-resident coarse tail (tail.cu)
+void tail_prepare(mgm_hierarchy* H, cudaStream_t s);
+void tail_launch(mgm_hierarchy* H, cudaStream_t s);
 // krylov.cu
 bool solve_graph_supported(const mgm_hierarchy* H, const mgm_solve_params* sp);
 void reaction_steps(mgm_hierarchy* Hu, mgm_hierarchy* Hv, int model, const double* prm, double dt, double* u, double* v,

@@ -744,6 +744,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
             const int G = L.n >= 500000 ? 2 : (L.n >= 30000 ? 4 : 8);
             colour_prepare(H.get(), L, B, G, s);  // (a level that does not fit keeps plain launches)
         }
+        tail_prepare(H.get(), s);  // the coarse levels in one cluster launch, where they fit
         tr.mark("staged-tables", p - 1);
     }
     CK(cudaStreamSynchronize(s));

@@ -620,7 +620,10 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
         return;
     }
     const int p = H->p;
-    for (int j = 0; j + 1 < p; ++j) {  // pre-smoothing and restricted residuals
+    // levels tail_top..p-1 in one cluster launch (FP32 unconstrained V(1,1)-cycles; tail.cu)
+    const int top = (sizeof(T) == 4 && !H->bordered) ? H->tail_top : 0;
+    const int jd = top ? top : p - 1;  // levels smoothed by per-colour launches: 0..jd-1
+    for (int j = 0; j < jd; ++j) {  // pre-smoothing and restricted residuals
         Level& L = H->lv[j];
         Level& C = H->lv[j + 1];
         const T* rsrc;
@@ -639,12 +642,14 @@ static void vcycle_launches(mgm_hierarchy* H, cudaStream_t s) {
         }
         launch_restrict<T>(H, L, C, rsrc, s);
     }
-    {   // coarsest defect (bordered: with the multiplier in the last entry)
+    if (top) {
+        tail_launch(H, s);
+    } else {   // coarsest defect (bordered: with the multiplier in the last entry)
         Level& C = H->lv[p - 1];
         launch_pdl(coarse_k<T>, grid_for(H->nb * 32, 256), 256, s, (const double*)H->Ainv.get(), (const T*)LV<T>::b(C),
                    LV<T>::e(C), (int64_t)H->nb);
     }
-    for (int j = p - 2; j >= 0; --j) {  // interpolate / correct, post-smooth
+    for (int j = jd - 1; j >= 0; --j) {  // interpolate / correct, post-smooth
         Level& L = H->lv[j];
         Level& C = H->lv[j + 1];
         launch_interp<T>(H, L, C, s);

@@ -67,7 +67,7 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_learned_train_step", "mgm_learned_enable", "mgm_learned_correction", "mgm_learned_info",
            "mgm_gradient_weights", "mgm_surface_gradient", "mgm_surface_divergence", "mgm_eigs", "mgm_reaction_rhs",
            "mgm_sweep_config_set", "mgm_sweep_config_get", "mgm_autotune", "mgm_profile_level", "mgm_reaction_steps",
-           "mgm_probe_fp64_fma", "mgm_probe_launch_chain", "mgm_vcycle_floor", "mgm_level_smoothing_bytes"]
+           "mgm_probe_fp64_fma", "mgm_probe_launch_chain", "mgm_vcycle_floor", "mgm_level_smoothing_bytes", "mgm_tail_info"]
 
 
 _SCHEDULES = ["launch", "stream", "resident", "colour"]
@@ -120,6 +120,7 @@ def lib():
         L.mgm_probe_launch_chain.argtypes = [I, I, I, I, I, C.POINTER(C.c_double), P]
         L.mgm_vcycle_floor.argtypes = [P, C.c_double, C.c_double] + [C.POINTER(C.c_double)] * 3
         L.mgm_level_smoothing_bytes.argtypes = [P, I, C.POINTER(C.c_int64)]
+        L.mgm_tail_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.mgm_check_bounded_wait.argtypes = [I, I64, C.POINTER(C.c_int), P]
         L.mgm_kernel_launches.argtypes = []
         L.mgm_kernel_launches.restype = C.c_int64
@@ -486,6 +487,12 @@ class Hierarchy:
         ms = C.c_float(0.0)
         _check(lib().mgm_profile_level(self._h, level, reps, C.byref(ms), _stream()))
         return ms.value
+
+    def tail_info(self):
+        """(top level, cluster CTAs) of the cluster-resident coarse tail of the FP32 cycle; top 0: none."""
+        t, c = C.c_int(0), C.c_int(0)
+        _check(lib().mgm_tail_info(self._h, C.byref(t), C.byref(c)))
+        return t.value, c.value
 
     def level_smoothing_bytes(self, level):
         """Algorithmic bytes of a level's smoothing work in one V-cycle (what profile_level times)."""

@@ -209,3 +209,33 @@ def test_autotuned_hierarchy_matches_oracle(M, oracle, prec, tol):
     assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo)
     u, info = Hg.solve(T(I.random_sh_rhs(x, lmax=12, seed=3)), tol=1e-10)
     assert info["converged"]
+
+
+def test_cluster_tail_matches_oracle(M, oracle):
+    """The FP32 cycle of persistent_sweeps = 5 runs its coarse levels (from the highest whose data fit
+    a CTA's shared memory) in one thread-block-cluster launch. The cycle matches the oracle's within
+    the FP32 bound, twice in a row, agrees with the per-colour launches of mode 0 to rounding, and
+    FGMRES takes the same iterations."""
+    import scipy.sparse as sp
+    x, nrm = I.fibonacci_sphere(60000, 0.1, 21)
+    _, _, rp, ci, v = M.build_stencils(T(x), T(nrm), 30, "rbf", 1, 2, 1.0, keep_weights=False)
+    L = sp.csr_matrix((H(v), H(ci), H(rp)), shape=(60000, 60000))
+    Ho = oracle.setup(x, L, 250, seed=0)
+    G5 = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision="f32", persistent_sweeps=5)
+    G0 = M.Hierarchy(T(x), rp, ci, v, n_min=250, precision="f32", persistent_sweeps=0)
+    top, cl = G5.tail_info()
+    assert 1 <= top <= G5.stats()["p"] - 2 and cl in (8, 16), (top, cl)
+    assert G0.tail_info()[0] == 0
+    rng = np.random.default_rng(22)
+    for _ in range(2):
+        r = rng.standard_normal(60000)
+        zo = oracle.vcycle(Ho, r)
+        z5 = H(G5.vcycle(T(r)))
+        z0 = H(G0.vcycle(T(r)))
+        assert np.linalg.norm(z5 - zo) <= 1e-4 * np.linalg.norm(zo)
+        assert np.linalg.norm(z5 - z0) <= 1e-5 * np.linalg.norm(z0)
+    f = T(I.random_sh_rhs(x, lmax=12, seed=5))
+    u5, i5 = G5.solve(f, tol=1e-10)
+    u0, i0 = G0.solve(f, tol=1e-10)
+    assert i5["converged"] and abs(i5["iters"] - i0["iters"]) <= 1, (i5["iters"], i0["iters"])
+    assert np.linalg.norm(H(u5) - H(u0)) <= 1e-8 * np.linalg.norm(H(u0))
