@@ -22,8 +22,14 @@
 namespace mgm {
 
 void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStream_t s);
+void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStream_t s, Temp<int32_t>* keep_rp,
+         Temp<int32_t>* keep_ci);
+void permute_pattern(int64_t N, const int32_t* srp, const int32_t* sci, const int32_t* perm, Temp<int32_t>& nrp,
+                     Temp<int32_t>& nci, cudaStream_t s);
 void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32_t* colour, int32_t* ncolors,
            cudaStream_t s);
+void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32_t* colour, int32_t* ncolors,
+           cudaStream_t s, const int32_t* sym_rp, const int32_t* sym_ci);
 void coarsen(const double* x, int64_t N, int64_t NH, int32_t* keep, cudaStream_t s, double* rmax_out);
 int64_t interp(const double* xf, int64_t nf, const double* xc, int64_t nc, int m, int32_t* rp, int32_t* col, double* val,
                cudaStream_t s);
@@ -581,12 +587,30 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
     H->lv.resize(p);
     const int64_t nnz = csr_nnz(rp, N, s);
     Trace tr(s);
+    // The symmetric pattern RCM builds for a level's operator, renumbered by the RCM permutation,
+    // is the pattern of the level's final (permuted) operator: the multicolour colouring takes it
+    // from there instead of building it again (smoothed levels; the colours are a function of the
+    // pattern as a set).
+    Temp<int32_t> sym_rp, sym_ci;
+    auto colour_level = [&](int j) {
+        Level& L = H->lv[j];
+        if (lex || j + 1 >= p) return;
+        Temp<int32_t> nrp, nci;
+        permute_pattern(L.n, sym_rp.get(), sym_ci.get(), L.perm.get(), nrp, nci, s);
+        sym_rp.release();
+        sym_ci.release();
+        L.colour.alloc(L.n);
+        int32_t nc = 0;
+        color(L.n, L.rp.get(), L.ci.get(), prm->seed, L.colour.get(), &nc, s, nrp.get(), nci.get());
+        L.ncolors = nc;
+        tr.mark("colour", j);
+    };
     {   // level 1: RCM of L_1 and X_1 (Alg. 2)
         Level& L = H->lv[0];
         L.n = N;
         L.nnz = nnz;
         L.perm.alloc(N);
-        rcm(N, rp, ci, L.perm.get(), s);
+        rcm(N, rp, ci, L.perm.get(), s, &sym_rp, &sym_ci);
         tr.mark("  rcm", 0);
         L.X.alloc(3 * N);
         gather_xyz(xyz, L.perm.get(), L.X.get(), N, s);
@@ -595,6 +619,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         L.v.alloc(nnz);
         csr_permute(N, rp, ci, v, L.perm.get(), L.rp.get(), L.ci.get(), L.v.get(), s);
         tr.mark("rcm+permute", 0);
+        colour_level(0);
     }
     for (int j = 1; j < p; ++j) {
         Level& F = H->lv[j - 1];
@@ -631,7 +656,7 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
         tr.mark("galerkin", j);
         // RCM of L_{j+1}; renumber coarse points and the interpolation's columns
         C.perm.alloc(NH);
-        rcm(NH, G_rp.get(), G_ci.get(), C.perm.get(), s);
+        rcm(NH, G_rp.get(), G_ci.get(), C.perm.get(), s, &sym_rp, &sym_ci);
         tr.mark("  rcm", j);
         C.X.alloc(3 * NH);
         gather_xyz(Xc.get(), C.perm.get(), C.X.get(), NH, s);
@@ -651,20 +676,17 @@ mgm_hierarchy* setup(const double* xyz, int64_t N, const int32_t* rp, const int3
                                                       F.P_v.get());
         CK_LAUNCH();
         tr.mark("rcm+permute", j);
+        colour_level(j);
     }
-    // colourings and solve orders
+    // colourings (multicolour: done above, level by level) and solve orders
     for (int j = 0; j + 1 < p; ++j) {
         Level& L = H->lv[j];
-        L.colour.alloc(L.n);
-        int32_t nc = 0;
         if (lex) {  // every row its own class, in the level's (RCM) order
+            L.colour.alloc(L.n);
             iota_i32(L.colour.get(), L.n, s);
-            nc = (int32_t)L.n;
-        } else {
-            color(L.n, L.rp.get(), L.ci.get(), prm->seed, L.colour.get(), &nc, s);
+            L.ncolors = (int32_t)L.n;
+            tr.mark("colour", j);
         }
-        L.ncolors = nc;
-        tr.mark("colour", j);
         build_solve_layout(L, false, s, lex);
         tr.mark("layout", j);
     }

@@ -203,7 +203,8 @@ __global__ void reverse_k(const int32_t* order, int64_t N, int32_t* perm) {
     if (i < N) perm[i] = order[N - 1 - i];
 }
 
-void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStream_t s) {
+void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStream_t s, Temp<int32_t>* keep_rp,
+         Temp<int32_t>* keep_ci) {
     REQUIRE(N >= 1 && N < 0x7fffffff, "N out of range");
     REQUIRE(rp && ci && perm, "null array");
     Temp<int32_t> srp, sci;
@@ -249,6 +250,43 @@ void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStr
     }
     trace_mark(s, "  rcm:bfs");
     reverse_k<<<grid_for(N, 256), 256, 0, s>>>(order.get(), N, perm);
+    CK_LAUNCH();
+    if (keep_rp && keep_ci) {  // the symmetric pattern, for the colouring of the permuted operator
+        *keep_rp = std::move(srp);
+        *keep_ci = std::move(sci);
+    }
+}
+
+void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStream_t s) {
+    rcm(N, rp, ci, perm, s, nullptr, nullptr);
+}
+
+// the symmetric pattern (srp, sci) of an operator, renumbered by perm (perm[new] = old, inv its
+// inverse): row r of the result is row perm[r] with its columns mapped by inv (order within a row
+// kept; the colouring treats a row as a set)
+__global__ void perm_len_k(const int32_t* srp, const int32_t* perm, int64_t N, int32_t* len) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < N) len[r] = srp[perm[r] + 1] - srp[perm[r]];
+}
+__global__ void perm_fill_pattern_k(const int32_t* srp, const int32_t* sci, const int32_t* perm, const int32_t* inv,
+                                    const int32_t* nrp, int64_t N, int32_t* nci) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = t >> 5;
+    if (r >= N) return;
+    const int32_t b = srp[perm[r]], e = srp[perm[r] + 1], o = nrp[r];
+    for (int32_t q = b + (int32_t)(t & 31); q < e; q += 32) nci[o + (q - b)] = inv[sci[q]];
+}
+void permute_pattern(int64_t N, const int32_t* srp, const int32_t* sci, const int32_t* perm, Temp<int32_t>& nrp,
+                     Temp<int32_t>& nci, cudaStream_t s) {
+    Temp<int32_t> inv(N, s), len(N + 1, s);
+    invert_perm(perm, inv.get(), N, s);
+    perm_len_k<<<grid_for(N, 256), 256, 0, s>>>(srp, perm, N, len.get());
+    CK_LAUNCH();
+    nrp.alloc(N + 1, s);
+    exclusive_scan_i32(len.get(), nrp.get(), N, s);
+    const int64_t nnz = csr_nnz(nrp.get(), N, s);
+    nci.alloc(nnz > 0 ? nnz : 1, s);
+    perm_fill_pattern_k<<<grid_for(N * 32, 256), 256, 0, s>>>(srp, sci, perm, inv.get(), nrp.get(), N, nci.get());
     CK_LAUNCH();
 }
 
@@ -470,34 +508,45 @@ __global__ void max_i32_k(const int32_t* a, int64_t n, int* out) {
 }
 
 void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32_t* colour, int32_t* ncolors,
-           cudaStream_t s) {
+           cudaStream_t s, const int32_t* sym_rp, const int32_t* sym_ci) {
     REQUIRE(N >= 1 && N < 0x7fffffff, "N out of range");
     REQUIRE(rp && ci && colour, "null array");
-    Temp<int32_t> srp, sci;
-    sym_pattern(N, rp, ci, srp, sci, s);
+    Temp<int32_t> srp_t, sci_t;
+    const int32_t* srp_p = sym_rp;  // the symmetric pattern, given or built here
+    const int32_t* sci_p = sym_ci;
+    if (!srp_p || !sci_p) {
+        sym_pattern(N, rp, ci, srp_t, sci_t, s);
+        srp_p = srp_t.get();
+        sci_p = sci_t.get();
+    }
     trace_mark(s, "  colour:pattern");
     Temp<int> ctr(2, s);  // [0] uncoloured vertices remain, [1] max colour
     // MGM_COLOR_ROUNDS in the environment selects the JP rounds directly (they are otherwise the
     // fallback only; the tests use it to check that both give the same colours)
-    const bool ordered = !std::getenv("MGM_COLOR_ROUNDS") && color_ordered(N, srp.get(), sci.get(), seed, colour, s);
+    const bool ordered = !std::getenv("MGM_COLOR_ROUNDS") && color_ordered(N, srp_p, sci_p, seed, colour, s);
     Temp<char> sel(ordered ? 1 : N, s);
     if (!ordered) fill_i32(colour, -1, N, s);
     const unsigned wgrid = grid_for(N, 256);
     for (int64_t round = 0; !ordered; ++round) {
         if (round > N) fail(MGM_ERR_UNSUPPORTED, "colouring did not terminate");
         CK(cudaMemsetAsync(ctr.get(), 0, sizeof(int), s));
-        jp_select_k<<<wgrid, 256, 0, s>>>(srp.get(), sci.get(), colour, N, seed, sel.get(), ctr.get());
+        jp_select_k<<<wgrid, 256, 0, s>>>(srp_p, sci_p, colour, N, seed, sel.get(), ctr.get());
         CK_LAUNCH();
         if (round % 4 == 3 || round < 2) {
             if (read1(ctr.get(), s) == 0) break;
         }
-        jp_assign_k<<<wgrid, 256, 0, s>>>(srp.get(), sci.get(), colour, sel.get(), N);
+        jp_assign_k<<<wgrid, 256, 0, s>>>(srp_p, sci_p, colour, sel.get(), N);
         CK_LAUNCH();
     }
     CK(cudaMemsetAsync(ctr.get() + 1, 0xff, sizeof(int), s));
     max_i32_k<<<(unsigned)std::min<int64_t>(grid_for(N, 256), 152 * 4), 256, 0, s>>>(colour, N, ctr.get() + 1);
     CK_LAUNCH();
     *ncolors = read1(ctr.get() + 1, s) + 1;
+}
+
+void color(int64_t N, const int32_t* rp, const int32_t* ci, uint64_t seed, int32_t* colour, int32_t* ncolors,
+           cudaStream_t s) {
+    color(N, rp, ci, seed, colour, ncolors, s, nullptr, nullptr);
 }
 
 }  // namespace mgm
