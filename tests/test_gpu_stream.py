@@ -239,3 +239,18 @@ def test_cluster_tail_matches_oracle(M, oracle):
     u0, i0 = G0.solve(f, tol=1e-10)
     assert i5["converged"] and abs(i5["iters"] - i0["iters"]) <= 1, (i5["iters"], i0["iters"])
     assert np.linalg.norm(H(u5) - H(u0)) <= 1e-8 * np.linalg.norm(H(u0))
+
+
+@pytest.mark.parametrize("n_min", [125, 640])
+def test_cluster_tail_small_hierarchies(M, oracle, ico5, n_min):
+    """The cluster tail on small hierarchies: from level 1 down (four levels, and three: one smoothed
+    level above the coarsest); the cycle within 1e-4 of the oracle's."""
+    x, nrm, idx, w, L = ico5
+    Ho = oracle.setup(x, L, n_min, seed=0)
+    G = M.Hierarchy(T(x), *_csr(L), n_min=n_min, precision="f32", persistent_sweeps=5)
+    assert G.stats()["p"] == Ho.p == (4 if n_min == 125 else 3)
+    assert G.tail_info()[0] == 1
+    r = np.random.default_rng(23).standard_normal(x.shape[0])
+    zo = oracle.vcycle(Ho, r)
+    z = H(G.vcycle(T(r)))
+    assert np.linalg.norm(z - zo) <= 1e-4 * np.linalg.norm(zo)
