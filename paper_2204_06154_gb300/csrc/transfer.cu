@@ -153,34 +153,33 @@ __device__ __forceinline__ int sg_find(const int* slots, int hs, int col) {
     return (int)h;
 }
 
-// Per-warp shared memory: (numeric) accumulators acc[hs/2] (double); hash slots[hs], then
-// (numeric) rank[hs] and lst[hs/2]; the products' columns pj[mp] and values pv[mp] (double), and
-// per A entry its first product aoff[ma + 1] and value aval[ma] (double). mp: the largest product
-// count of a row, ma: the largest A row.
+// Per-warp shared memory: hash slots[hs]; (numeric) rank[hs], reused after the ranking as the
+// per-column counts and segment ends; the products' columns pj[mp] (in the numeric phase replaced
+// by their columns' ranks), (numeric) their B values pv[mp] and A values pa[mp] (double), and the
+// products sorted by column srt[mp] (first the compacted columns); per A entry its first product
+// aoff[ma + 1]. mp: the largest product count of a row, ma: the largest A row.
 struct SgLayout {
-    size_t slots, rank, lst, acc, pj, pv, aoff, aval, bytes;
+    size_t slots, rank, pj, pv, pa, srt, aoff, bytes;
 };
 __host__ __device__ inline SgLayout sg_layout(int hs, int mp, int ma, bool numeric) {
     SgLayout o;
     size_t off = 0;
-    o.acc = off; off += numeric ? 8 * (size_t)(hs / 2) : 0;  // accumulators by rank (double)
+    o.pv = off; off += numeric ? 8 * (size_t)mp : 0;
+    o.pa = off; off += numeric ? 8 * (size_t)mp : 0;
     o.slots = off; off += 4 * (size_t)hs;
     o.rank = off; off += numeric ? 4 * (size_t)hs : 0;
-    o.lst = off; off += numeric ? 4 * (size_t)(hs / 2) : 0;
     o.pj = off; off += 4 * (size_t)mp;
-    off = (off + 7) & ~(size_t)7;
-    o.pv = off; off += numeric ? 8 * (size_t)mp : 0;
+    o.srt = off; off += numeric ? 4 * (size_t)mp : 0;
     o.aoff = off; off += 4 * (size_t)(ma + 1);
-    off = (off + 7) & ~(size_t)7;
-    o.aval = off; off += numeric ? 8 * (size_t)ma : 0;
     o.bytes = (off + 15) & ~(size_t)15;
     return o;
 }
 
-// Gathers row i's products into pj (and pv, aval when av is given) in A-row order, aoff[t] = first
-// product of A entry t; then inserts the columns into the hash set. Returns the number of distinct
-// columns (warp-uniform); *overflow when the set or the product buffer is too small.
-__device__ int sg_gather(int* slots, int hs, int* pj, double* pv, int* aoff, double* aval, int mp, const int32_t* arp,
+// Gathers row i's products into pj (and their B and A values into pv, pa when av is given) in
+// A-row order, aoff[t] = first product of A entry t; then inserts the columns into the hash set.
+// Returns the number of distinct columns (warp-uniform); *overflow when the set or the product
+// buffer is too small.
+__device__ int sg_gather(int* slots, int hs, int* pj, double* pv, int* aoff, double* pa, int mp, const int32_t* arp,
                          const int32_t* aci, const double* av, const int32_t* brp, const int32_t* bci, const double* bv,
                          int64_t i, int lane, bool* overflow) {
     for (int t = lane; t < hs; t += 32) slots[t] = -1;
@@ -192,7 +191,7 @@ __device__ int sg_gather(int* slots, int hs, int* pj, double* pv, int* aoff, dou
         const int32_t l = has ? aci[p] : 0;
         const int32_t b0 = has ? brp[l] : 0;
         const int len = has ? brp[l + 1] - b0 : 0;
-        if (has && av) aval[p - ab] = av[p];
+        const double al = has && av ? av[p] : 0.0;
         int incl = len;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -210,10 +209,12 @@ __device__ int sg_gather(int* slots, int hs, int* pj, double* pv, int* aoff, dou
                 if (lo + step < 32 && x <= e) lo += step;
             }
             const int32_t sb = __shfl_sync(0xffffffffu, b0, lo), se = __shfl_sync(0xffffffffu, excl, lo);
+            const double ae = __shfl_sync(0xffffffffu, al, lo);
             if (e < tot && base + e < mp) {
                 const int32_t q = sb + (e - se);
                 pj[base + e] = bci[q];
                 if (bv) pv[base + e] = bv[q];
+                if (pa) pa[base + e] = ae;
             }
         }
         base += tot;
@@ -260,6 +261,10 @@ __global__ void spgemm_symbolic_k(int64_t nA, const int32_t* arp, const int32_t*
     }
 }
 
+// Row i of C = A B, a warp per row. Each column's sum takes its products in A-row order,
+// c = fma(a_p, b, c) from c = 0, the order of the oracle's product: the products are ranked by
+// column, stably sorted by rank (a chunk of 32 products at a time, equal ranks within a chunk
+// placed by lane), and a lane a column then adds its segment in that order.
 __global__ void spgemm_numeric_k(int64_t nA, const int32_t* arp, const int32_t* aci, const double* av,
                                  const int32_t* brp, const int32_t* bci, const double* bv, const int32_t* crp,
                                  int32_t* cci, double* cv, int hs, int mp, int ma, int* err) {
@@ -269,20 +274,23 @@ __global__ void spgemm_numeric_k(int64_t nA, const int32_t* arp, const int32_t* 
     unsigned char* base = sg_smem + lay.bytes * w;
     int* slots = (int*)(base + lay.slots);
     int* rank = (int*)(base + lay.rank);
-    int* lst = (int*)(base + lay.lst);
     int* pj = (int*)(base + lay.pj);
     double* pv = (double*)(base + lay.pv);
+    double* pa = (double*)(base + lay.pa);
+    int* srt = (int*)(base + lay.srt);
     int* aoff = (int*)(base + lay.aoff);
-    double* aval = (double*)(base + lay.aval);
     const int64_t i = (int64_t)blockIdx.x * wpb + w;
     if (i >= nA) return;
     bool ovf;
-    const int u = sg_gather(slots, hs, pj, pv, aoff, aval, mp, arp, aci, av, brp, bci, bv, i, lane, &ovf);
+    const int u = sg_gather(slots, hs, pj, pv, aoff, pa, mp, arp, aci, av, brp, bci, bv, i, lane, &ovf);
     if (ovf || u != crp[i + 1] - crp[i]) {
         if (lane == 0) atomicOr(err, 2);
         return;
     }
-    // compact the set into lst
+    const int na = arp[i + 1] - arp[i];
+    const int tot = na > 0 ? aoff[na] : 0;  // products of the row
+    // compact the set (into srt, free until the sort)
+    int* lst = srt;
     int nb = 0;
     for (int t = lane; t - lane < hs; t += 32) {
         const int c = t < hs ? slots[t] : -1;
@@ -292,7 +300,6 @@ __global__ void spgemm_numeric_k(int64_t nA, const int32_t* arp, const int32_t* 
     }
     __syncwarp();
     // rank of each column among the row's columns, kept at its hash slot; the sorted columns out
-    double* acc = (double*)(base + lay.acc);
     const int32_t c0 = crp[i];
     for (int t = lane; t < u; t += 32) {
         const int c = lst[t];
@@ -300,20 +307,53 @@ __global__ void spgemm_numeric_k(int64_t nA, const int32_t* arp, const int32_t* 
         for (int q = 0; q < u; ++q) r += lst[q] < c ? 1 : 0;
         rank[sg_find(slots, hs, c)] = r;
         cci[c0 + r] = c;
-        acc[r] = 0.0;
     }
     __syncwarp();
-    // A's entries one at a time, in order; lanes over the products of each
-    const int na = arp[i + 1] - arp[i];
-    for (int p = 0; p < na; ++p) {
-        const double a = aval[p];
-        for (int e = aoff[p] + lane; e < aoff[p + 1]; e += 32) {
-            const int r = rank[sg_find(slots, hs, pj[e])];
-            acc[r] = fma(a, pv[e], acc[r]);
+    // each product's column rank, over its column
+    for (int e = lane; e < tot; e += 32) pj[e] = rank[sg_find(slots, hs, pj[e])];
+    __syncwarp();
+    int* cnt = rank;            // products a column
+    int* seg = rank + hs / 2;   // start, then end, of each column's segment in srt
+    for (int t = lane; t < u; t += 32) cnt[t] = 0;
+    __syncwarp();
+    for (int e = lane; e < tot; e += 32) atomicAdd(&cnt[pj[e]], 1);
+    __syncwarp();
+    int carry = 0;
+    for (int t0 = 0; t0 < u; t0 += 32) {
+        const int t = t0 + lane;
+        const int c = t < u ? cnt[t] : 0;
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (t < u) seg[t] = carry + incl - c;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    for (int e0 = 0; e0 < tot; e0 += 32) {
+        const int e = e0 + lane;
+        const int r = e < tot ? pj[e] : -1 - lane;  // idle lanes: keys of their own
+        const unsigned grp = __match_any_sync(0xffffffffu, r);
+        const int before = __popc(grp & ((1u << lane) - 1u));
+        int at = 0;
+        if (e < tot) at = seg[r] + before;
+        __syncwarp();
+        if (e < tot) {
+            srt[at] = e;
+            if (before == __popc(grp) - 1) seg[r] = at + 1;  // the group's last lane moves the cursor
         }
         __syncwarp();
     }
-    for (int t = lane; t < u; t += 32) cv[c0 + t] = acc[t];
+    for (int t = lane; t < u; t += 32) {
+        const int e1 = seg[t], e0 = e1 - cnt[t];
+        double acc = 0.0;
+        for (int j = e0; j < e1; ++j) {
+            const int e = srt[j];
+            acc = fma(pa[e], pv[e], acc);
+        }
+        cv[c0 + t] = acc;
+    }
 }
 
 struct SgShape {
