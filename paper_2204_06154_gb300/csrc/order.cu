@@ -5,8 +5,8 @@
 // Cuthill-McKee order exactly. Within a level, a frontier node v (in CM order) appends its
 // unvisited neighbours in increasing (degree, index); a node adjacent to several frontier nodes
 // is appended by the first of them. So each unvisited neighbour takes the minimum CM position
-// of its frontier neighbours (atomicMin), frontier nodes count the children they own, a scan
-// gives offsets, and each frontier node writes its children in its (degree, index) order.
+// of its frontier neighbours (atomicMin), the children are counted by owner, a scan gives
+// offsets, and each frontier node writes its children in its (degree, index) order.
 //
 // Colouring: Jones-Plassmann rounds. An uncoloured vertex whose (SplitMix64(seed, i), i) priority
 // exceeds that of all uncoloured neighbours takes the smallest colour absent from its coloured
@@ -53,42 +53,21 @@ __global__ void __launch_bounds__(SBD_WARPS * 32) sort_by_degree_k(const int32_t
 
 // Device-resident BFS state: the host enqueues levels without reading anything back and checks
 // for completion only every RCM_BATCH levels; kernels of an exhausted search return at once.
+// A level is three launches: claim (frontier nodes claim their unvisited neighbours; a node's first
+// claim lists it as touched), scan (one block: children counted from the touched list, offsets,
+// the next frontier; when that is empty and nodes remain, the next component's start), write.
 struct RcmState {
-    int32_t fs, fe, tail, total;   // current frontier [fs, fe) in `order`, next free slot, children found
-    unsigned long long best;       // (degree, index) key of the next component's start
+    int32_t fs, fe, tail;     // current frontier [fs, fe) in `order`, next free slot
+    int32_t wfs, wfe, wtail;  // the frontier and first slot of the level being written
+    int32_t ntouched;         // nodes first claimed at this level (listed in `touched`)
 };
 constexpr int RCM_BATCH = 16;
 constexpr int RCM_GRID = 152 * 8;  // blocks of 128 threads: 4 frontier nodes a block at a time
 
-__global__ void rcm_start_k(const int32_t* rp, const int32_t* pos, int64_t N, RcmState* st) {
-    pdl_trigger();
-    pdl_wait();
-    if (st->fs != st->fe || st->tail >= N) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        if (pos[i] >= 0) continue;
-        unsigned long long key = ((unsigned long long)(uint32_t)(rp[i + 1] - rp[i]) << 32) | (uint32_t)i;
-        atomicMin(&st->best, key);
-    }
-}
-
-__global__ void rcm_seed_k(int32_t* order, int32_t* pos, int64_t N, RcmState* st) {
-    pdl_trigger();
-    pdl_wait();
-    if (st->fs != st->fe || st->tail >= N) return;
-    int32_t s = (int32_t)(st->best & 0xffffffffull);
-    order[st->tail] = s;
-    pos[s] = st->tail;
-    st->fs = st->tail;
-    st->fe = st->tail + 1;
-    st->tail += 1;
-    st->best = ~0ull;
-}
-
-// claim / count / write: one warp per frontier node, lanes over its (degree, index)-sorted
-// neighbours, so the dependent loads of a node's neighbours overlap instead of forming one long
-// chain per thread
+// claim: one warp per frontier node, lanes over its (degree, index)-sorted neighbours, so the
+// dependent loads of a node's neighbours overlap instead of forming one long chain per thread
 __global__ void rcm_claim_k(const int32_t* rp, const int32_t* adj, const int32_t* order, const int32_t* pos,
-                            const RcmState* st, int32_t* claim) {
+                            RcmState* st, int32_t* claim, int32_t* touched) {
     pdl_trigger();
     pdl_wait();
     const int32_t fs = st->fs, fe = st->fe;
@@ -96,43 +75,42 @@ __global__ void rcm_claim_k(const int32_t* rp, const int32_t* adj, const int32_t
     const int32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (int32_t t = fs + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < fe; t += nw) {
         const int32_t v = order[t];
-        for (int32_t p = rp[v] + lane; p < rp[v + 1]; p += 32) {
-            const int32_t u = adj[p];
-            if (pos[u] < 0) atomicMin(&claim[u], t);
-        }
-    }
-}
-
-__global__ void rcm_count_k(const int32_t* rp, const int32_t* adj, const int32_t* order, const int32_t* pos,
-                            const int32_t* claim, const RcmState* st, int32_t* cnt) {
-    pdl_trigger();
-    pdl_wait();
-    const int32_t fs = st->fs, fe = st->fe;
-    const int lane = threadIdx.x & 31;
-    const int32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (int32_t t = fs + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < fe; t += nw) {
-        const int32_t v = order[t];
-        int32_t c = 0;
         for (int32_t p0 = rp[v]; p0 < rp[v + 1]; p0 += 32) {
             const int32_t p = p0 + lane;
-            bool mine = false;
+            int32_t u = -1;
+            bool first = false;
             if (p < rp[v + 1]) {
-                const int32_t u = adj[p];
-                mine = pos[u] < 0 && claim[u] == t;
+                u = adj[p];
+                if (pos[u] < 0) first = atomicMin(&claim[u], t) == INT_MAX;
             }
-            c += __popc(__ballot_sync(0xffffffffu, mine));
+            const unsigned m = __ballot_sync(0xffffffffu, first);
+            if (m) {
+                int32_t at = 0;
+                if (lane == __ffs(m) - 1) at = atomicAdd(&st->ntouched, __popc(m));
+                at = __shfl_sync(0xffffffffu, at, __ffs(m) - 1);
+                if (first) touched[at + __popc(m & ((1u << lane) - 1u))] = u;
+            }
         }
-        if (lane == 0) cnt[t - fs] = c;
     }
 }
 
-// exclusive scan of the frontier's child counts by one block (chunk sums, then a two-level
-// shuffle scan of the 1024 chunk sums); total into the state
-__global__ void __launch_bounds__(1024) rcm_scan_k(const int32_t* cnt, int32_t* off, RcmState* st) {
+// one block: each touched node counts for the frontier node that claimed it; exclusive scan of
+// the counts (chunk sums, then a two-level shuffle scan of the 1024 chunk sums); the next
+// frontier; if it is empty and nodes remain, the unvisited node of least (degree, index) starts
+// the next component (the first level of the search only does this)
+__global__ void __launch_bounds__(1024) rcm_scan_k(const int32_t* rp, const int32_t* claim, const int32_t* touched,
+                                                   int32_t* cnt, int32_t* off, int32_t* order, int32_t* pos, int64_t N,
+                                                   RcmState* st) {
     pdl_trigger();
     pdl_wait();
     __shared__ int32_t wsum[32];
-    const int32_t n = st->fe - st->fs;
+    __shared__ unsigned long long wbest[32];
+    const int32_t fs = st->fs, fe = st->fe, tail = st->tail, nt = st->ntouched;
+    const int32_t n = fe - fs;
+    for (int32_t i = threadIdx.x; i < n; i += 1024) cnt[i] = 0;
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < nt; i += 1024) atomicAdd(&cnt[claim[touched[i]] - fs], 1);
+    __syncthreads();
     const int32_t per = (n + 1023) / 1024;
     const int32_t b = threadIdx.x * per, e = min(n, b + per);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -152,18 +130,46 @@ __global__ void __launch_bounds__(1024) rcm_scan_k(const int32_t* cnt, int32_t* 
             if (lane >= o) t += y;
         }
         wsum[lane] = t;  // inclusive over warps
-        if (lane == 31) st->total = t;
     }
     __syncthreads();
+    const int32_t total = wsum[31];
     int32_t acc = (w > 0 ? wsum[w - 1] : 0) + x - sum;
     for (int32_t i = b; i < e; ++i) { off[i] = acc; acc += cnt[i]; }
+    if (threadIdx.x == 0) {
+        st->wfs = fs;
+        st->wfe = fe;
+        st->wtail = tail;
+        st->fs = tail;
+        st->fe = tail + total;
+        st->tail = tail + total;
+        st->ntouched = 0;
+    }
+    if (total > 0 || tail >= N) return;  // (block-uniform)
+    unsigned long long best = ~0ull;
+    for (int64_t i = threadIdx.x; i < N; i += 1024)
+        if (pos[i] < 0) best = min(best, ((unsigned long long)(uint32_t)(rp[i + 1] - rp[i]) << 32) | (uint32_t)i);
+    for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) wbest[w] = best;
+    __syncthreads();
+    if (w == 0) {
+        best = wbest[lane];
+        for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) {
+            const int32_t s0 = (int32_t)(best & 0xffffffffull);
+            order[tail] = s0;
+            pos[s0] = tail;
+            st->fs = tail;
+            st->fe = tail + 1;
+            st->tail = tail + 1;
+        }
+    }
 }
 
 __global__ void rcm_write_k(const int32_t* rp, const int32_t* adj, int32_t* order, int32_t* pos, const int32_t* claim,
                             const int32_t* off, const RcmState* st) {
     pdl_trigger();
     pdl_wait();
-    const int32_t fs = st->fs, fe = st->fe, tail = st->tail;
+    const int32_t fs = st->wfs, fe = st->wfe, tail = st->wtail;
     const int lane = threadIdx.x & 31;
     const int32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (int32_t t = fs + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < fe; t += nw) {
@@ -188,16 +194,6 @@ __global__ void rcm_write_k(const int32_t* rp, const int32_t* adj, int32_t* orde
     }
 }
 
-__global__ void rcm_advance_k(RcmState* st) {
-    pdl_trigger();
-    pdl_wait();
-    if (st->fs == st->fe) return;
-    st->fs = st->tail;
-    st->fe = st->tail + st->total;
-    st->tail += st->total;
-    st->total = 0;
-}
-
 __global__ void reverse_k(const int32_t* order, int64_t N, int32_t* perm) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) perm[i] = order[N - 1 - i];
@@ -214,26 +210,21 @@ void rcm(int64_t N, const int32_t* rp, const int32_t* ci, int32_t* perm, cudaStr
     sort_by_degree_k<<<grid_for(N, SBD_WARPS), SBD_WARPS * 32, 0, s>>>(srp.get(), sci.get(), N, adj.get());
     CK_LAUNCH();
     trace_mark(s, "  rcm:pattern");
-    Temp<int32_t> order(N, s), pos(N, s), claim(N, s), cnt(N + 1, s), off(N + 1, s);
+    Temp<int32_t> order(N, s), pos(N, s), claim(N, s), cnt(N + 1, s), off(N + 1, s), touched(N, s);
     fill_i32(pos.get(), -1, N, s);
     fill_i32(claim.get(), INT_MAX, N, s);
     Temp<RcmState> st(1, s);
-    RcmState init{0, 0, 0, 0, ~0ull};
+    RcmState init{0, 0, 0, 0, 0, 0, 0};  // empty frontier: the first level's scan seeds the search
     CK(cudaMemcpyAsync(st.get(), &init, sizeof(RcmState), cudaMemcpyHostToDevice, s));
     const unsigned grid = (unsigned)std::min<int64_t>(grid_for(N, 4), RCM_GRID);
-    // one BFS level: seven kernels chained by programmatic dependent launch
+    // one BFS level: three kernels chained by programmatic dependent launch
     auto level = [&](cudaStream_t q) {
-        launch_pdl(rcm_start_k, grid, 128, q, (const int32_t*)srp.get(), (const int32_t*)pos.get(), N, st.get());
-        launch_pdl(rcm_seed_k, 1, 1, q, order.get(), pos.get(), N, st.get());
         launch_pdl(rcm_claim_k, grid, 128, q, (const int32_t*)srp.get(), (const int32_t*)adj.get(),
-                   (const int32_t*)order.get(), (const int32_t*)pos.get(), (const RcmState*)st.get(), claim.get());
-        launch_pdl(rcm_count_k, grid, 128, q, (const int32_t*)srp.get(), (const int32_t*)adj.get(),
-                   (const int32_t*)order.get(), (const int32_t*)pos.get(), (const int32_t*)claim.get(),
-                   (const RcmState*)st.get(), cnt.get());
-        launch_pdl(rcm_scan_k, 1, 1024, q, (const int32_t*)cnt.get(), off.get(), st.get());
+                   (const int32_t*)order.get(), (const int32_t*)pos.get(), st.get(), claim.get(), touched.get());
+        launch_pdl(rcm_scan_k, 1, 1024, q, (const int32_t*)srp.get(), (const int32_t*)claim.get(),
+                   (const int32_t*)touched.get(), cnt.get(), off.get(), order.get(), pos.get(), N, st.get());
         launch_pdl(rcm_write_k, grid, 128, q, (const int32_t*)srp.get(), (const int32_t*)adj.get(), order.get(),
                    pos.get(), (const int32_t*)claim.get(), (const int32_t*)off.get(), (const RcmState*)st.get());
-        launch_pdl(rcm_advance_k, 1, 1, q, st.get());
     };
     // Large graphs: RCM_BATCH levels captured once as a CUDA graph and replayed (levels after the
     // last are no-ops); the host reads the state between replays.
