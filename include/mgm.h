@@ -22,7 +22,11 @@
  *    a device result to continue (noted per call), in which case it synchronises `stream`.
  *  - Calls never abort: they return a status. On error the outputs are unspecified, and
  *    mgm_last_error_message() gives a one-line description (thread-local).
- *  - Temporaries are allocated with cudaMallocAsync on `stream` and freed before return.
+ *  - Temporaries are allocated stream-ordered on `stream` from the library's pool on the current
+ *    device and freed before return. Between calls the pool keeps up to 1/32 of the device's
+ *    memory mapped for the next call, and mgm_destroy keeps a destroyed hierarchy's blocks (within
+ *    the same budget) for the next hierarchy; a failed allocation hands both back to the device
+ *    and is tried once more. mgm_release_cached_memory() hands them back on request.
  */
 #ifndef MGM_H
 #define MGM_H
@@ -476,7 +480,13 @@ int64_t mgm_kernel_launches(void);
  * it: MGM_ERR_TIMEOUT when the bounded wait gave up and returned, as it must. Synchronises. */
 mgm_status mgm_check_bounded_wait(int nblocks, int64_t spin_limit, int* status_out, mgm_stream stream);
 
+/* Frees a hierarchy (NULL: no-op). Synchronises the device first; the hierarchy's device blocks
+ * are kept for reuse by later hierarchies on the same device, within the cache budget above. */
 void mgm_destroy(mgm_hierarchy* H);
+
+/* Synchronises the current device and returns to it the memory the library keeps cached there:
+ * the scratch pool's unused memory and the blocks of destroyed hierarchies. Never fails. */
+void mgm_release_cached_memory(void);
 
 /* ------------------------------------------------------------------------------------------- */
 /* Surface gradient and divergence (Sec. 6.3, the heat method)                                  */

@@ -55,11 +55,12 @@ using namespace mgm;
 
 static inline cudaStream_t S(mgm_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// heavy one-off entry points: run, then hand the scratch pool's cached memory back to the device
+// heavy entry points: run, then trim the scratch pool's cached memory to the cache budget, so a
+// call that needed more hands the excess back while the next call of the same size maps nothing
 template <class F>
 static mgm_status guarded_trim(F&& body) {
     const mgm_status st = guarded(std::forward<F>(body));
-    scratch_trim(0);
+    scratch_trim(cache_budget());
     return st;
 }
 
@@ -419,8 +420,14 @@ mgm_status mgm_check_bounded_wait(int nblocks, int64_t spin_limit, int* status_o
 void mgm_destroy(mgm_hierarchy* H) {
     if (!H) return;
     cudaDeviceSynchronize();
-    delete H;
+    {  // the hierarchy's blocks stay mapped for the next one, within the cache budget
+        BufCacheScope keep;
+        delete H;
+    }
+    buf_cache_trim(cache_budget());
 }
+
+void mgm_release_cached_memory(void) { release_cached_memory(); }
 
 const char* mgm_status_string(mgm_status s) {
     switch (s) {

@@ -59,6 +59,21 @@ mgm_status guarded(F&& body) {
 bool trace_on();
 void trace_mark(cudaStream_t s, const char* what, int level = -1);
 
+// Persistent device blocks (util.cu): buf_alloc takes the smallest cached block of the current
+// device that fits (up to twice the size asked for) or calls cudaMalloc (on failure it hands the
+// caches back and tries once more, then fails with MGM_ERR_OOM); buf_free calls cudaFree, or,
+// inside a BufCacheScope, keeps the block for reuse. A scope is opened only after a device
+// synchronisation (mgm_destroy), so no work in flight uses a cached block. buf_cache_trim frees
+// cached blocks, largest first, down to keep_bytes; buf_cache_flush frees them all.
+// cache_budget: what the scratch pool and the block cache may each keep mapped on the current
+// device between calls (1/32 of its memory). release_cached_memory: synchronise the device and
+// hand both back.
+void* buf_alloc(size_t bytes);
+void buf_free(void* p);
+void buf_cache_trim(size_t keep_bytes);
+void buf_cache_flush();
+size_t cache_budget();
+void release_cached_memory();
 // the library's stream-ordered scratch pool on the current device (util.cu), and a release of its
 // cached memory down to keep_bytes
 cudaMemPool_t scratch_pool();
@@ -78,6 +93,11 @@ struct Temp {
         n = count;
         if (count) {
             cudaError_t e = cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), scratch_pool(), st);
+            if (e != cudaSuccess) {  // hand the caches back to the device and try once more
+                (void)cudaGetLastError();
+                release_cached_memory();
+                e = cudaMallocFromPoolAsync((void**)&p, count * sizeof(T), scratch_pool(), st);
+            }
             if (e != cudaSuccess) {
                 (void)cudaGetLastError();
                 p = nullptr;
@@ -103,7 +123,12 @@ struct Temp {
     T* get() const { return p; }
 };
 
-// Buf<T>: persistent device memory (cudaMalloc) owned by a hierarchy.
+struct BufCacheScope {
+    BufCacheScope();
+    ~BufCacheScope();
+};
+
+// Buf<T>: persistent device memory owned by a hierarchy.
 template <class T>
 struct Buf {
     T* p = nullptr;
@@ -113,17 +138,10 @@ struct Buf {
     void alloc(size_t count) {
         release();
         n = count;
-        if (count) {
-            cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
-            if (e != cudaSuccess) {
-                (void)cudaGetLastError();
-                p = nullptr;
-                fail(MGM_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
-            }
-        }
+        if (count) p = (T*)buf_alloc(count * sizeof(T));
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) buf_free(p);
         p = nullptr;
         n = 0;
     }

@@ -7,6 +7,7 @@
 #include <cstdio>
 
 #include <map>
+#include <unordered_map>
 #include <mutex>
 #include <tuple>
 
@@ -491,6 +492,123 @@ void scratch_trim(size_t keep_bytes) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return;
     cudaMemPoolTrimTo(scratch_pool(), keep_bytes);
+}
+
+namespace {
+struct BufCache {
+    std::mutex mu;
+    std::unordered_map<void*, std::pair<int, size_t>> live;      // block -> (device, bytes)
+    std::map<int, std::multimap<size_t, void*>> free_blocks;      // device -> (bytes, block)
+};
+BufCache& buf_cache() {
+    static BufCache* c = new BufCache();  // (never destroyed: buffers may be released at exit)
+    return *c;
+}
+thread_local int g_cache_scope = 0;
+}  // namespace
+
+BufCacheScope::BufCacheScope() { ++g_cache_scope; }
+BufCacheScope::~BufCacheScope() { --g_cache_scope; }
+
+void* buf_alloc(size_t bytes) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    BufCache& c = buf_cache();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto& fb = c.free_blocks[dev];
+        auto it = fb.lower_bound(bytes);
+        if (it != fb.end() && it->first <= 2 * bytes) {
+            void* p = it->second;
+            c.live[p] = {dev, it->first};
+            fb.erase(it);
+            return p;
+        }
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        release_cached_memory();
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            fail(MGM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        }
+    }
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.live[p] = {dev, bytes};
+    return p;
+}
+
+void buf_free(void* p) {
+    BufCache& c = buf_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.live.find(p);
+    if (it == c.live.end()) return;
+    const int dev = it->second.first;
+    const size_t bytes = it->second.second;
+    c.live.erase(it);
+    if (g_cache_scope > 0) {
+        c.free_blocks[dev].emplace(bytes, p);
+    } else {
+        cudaFree(p);
+    }
+}
+
+// Memory the caches may keep on a device between calls: 1/32 of its memory (8.9 GB on a GB300).
+size_t cache_budget() {
+    static std::mutex mu;
+    static std::map<int, size_t> budget;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = budget.find(dev);
+    if (it != budget.end()) return it->second;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        (void)cudaGetLastError();
+        tot = 0;
+    }
+    return budget[dev] = tot / 32;
+}
+
+void buf_cache_trim(size_t keep_bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    BufCache& c = buf_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto& fb = c.free_blocks[dev];
+    size_t total = 0;
+    for (auto& b : fb) total += b.first;
+    while (total > keep_bytes && !fb.empty()) {  // largest blocks first
+        auto it = std::prev(fb.end());
+        total -= it->first;
+        cudaFree(it->second);
+        fb.erase(it);
+    }
+}
+
+void release_cached_memory() {
+    cudaDeviceSynchronize();
+    scratch_trim(0);
+    buf_cache_flush();
+}
+
+void buf_cache_flush() {
+    BufCache& c = buf_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (c.free_blocks.empty()) return;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) cur = 0;
+    for (auto& d : c.free_blocks) {
+        if (d.second.empty()) continue;
+        cudaSetDevice(d.first);
+        cudaDeviceSynchronize();
+        for (auto& b : d.second) cudaFree(b.second);
+        d.second.clear();
+    }
+    cudaSetDevice(cur);
 }
 
 int coresident_blocks(const void* kernel, int threads, size_t smem, int per_sm_cap) {

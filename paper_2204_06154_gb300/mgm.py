@@ -60,7 +60,7 @@ EXPORTS = ["mgm_knn", "mgm_knn_noalloc", "mgm_stencil_weights", "mgm_assemble", 
            "mgm_transpose", "mgm_spgemm", "mgm_rcm", "mgm_color", "mgm_setup", "mgm_vcycle", "mgm_solve", "mgm_solve_multi",
            "mgm_solve_batched",
            "mgm_hierarchy_stats_get", "mgm_hierarchy_level", "mgm_hierarchy_pnnz", "mgm_profile",
-           "mgm_kernel_launches", "mgm_check_bounded_wait", "mgm_destroy", "mgm_status_string", "mgm_last_error_message",
+           "mgm_kernel_launches", "mgm_check_bounded_wait", "mgm_destroy", "mgm_release_cached_memory", "mgm_status_string", "mgm_last_error_message",
            "mgm_last_error_row", "mgm_last_weights_fp64_rows",
            "mgm_mlp_size", "mgm_mlp_create", "mgm_mlp_destroy", "mgm_mlp_get", "mgm_mlp_set", "mgm_mlp_forward",
            "mgm_mlp_vjp", "mgm_learned_attach", "mgm_learned_features", "mgm_learned_cycle_residual", "mgm_learned_loss",
@@ -126,6 +126,8 @@ def lib():
         L.mgm_kernel_launches.restype = C.c_int64
         L.mgm_destroy.argtypes = [P]
         L.mgm_destroy.restype = None
+        L.mgm_release_cached_memory.argtypes = []
+        L.mgm_release_cached_memory.restype = None
         L.mgm_gradient_weights.argtypes = [P, P, I64, P, C.POINTER(StencilParams), P, P, P]
         L.mgm_surface_gradient.argtypes = [P, I64, P, I, P, P, P, P, I, P]
         L.mgm_surface_divergence.argtypes = [P, I64, P, I, P, P, P, P, P]
@@ -157,8 +159,8 @@ def lib():
         L.mgm_last_weights_fp64_rows.argtypes = []
         L.mgm_last_weights_fp64_rows.restype = C.c_int64
         for name in EXPORTS:
-            if name not in ("mgm_destroy", "mgm_status_string", "mgm_last_error_message", "mgm_last_error_row",
-                            "mgm_last_weights_fp64_rows",
+            if name not in ("mgm_destroy", "mgm_release_cached_memory", "mgm_status_string", "mgm_last_error_message",
+                            "mgm_last_error_row", "mgm_last_weights_fp64_rows",
                             "mgm_kernel_launches", "mgm_mlp_size", "mgm_mlp_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
@@ -225,6 +227,11 @@ def _sp(n, method="rbf", k=1, ell=2, mu=1.0, alpha=4.0, poisson=False, weights="
 def last_weights_fp64_rows():
     """Stencils that the last weights call with weights="mixed" solved again in FP64."""
     return int(lib().mgm_last_weights_fp64_rows())
+
+
+def release_cached_memory():
+    """mgm_release_cached_memory: hand the library's cached device memory back to the device."""
+    lib().mgm_release_cached_memory()
 
 
 def stencil_weights(xyz, nrm, idx, method="rbf", k=1, ell=2, alpha=4.0, weights="f64"):
