@@ -75,6 +75,20 @@ def test_knn_fp32_culling_edges(M, oracle, case, k):
     assert np.array_equal(got, ref)
 
 
+def test_knn_dense_cluster_compaction(M, oracle):
+    """A tight cluster of 6,000 points in a sphere of 10,000: the cluster's queries gather far more
+    than the 1,024 candidates a warp buffers, so the buffer is compacted to the k best (with every
+    pending FP32 distance made exact first) before the search goes on. Bit-exact against the
+    oracle's brute force."""
+    rng = np.random.default_rng(13)
+    x, _ = I.fibonacci_sphere(10000, 0.1, 12)
+    c = x[0] + 1e-3 * rng.standard_normal((6000, 3))
+    x = np.concatenate([x, c])
+    ref = oracle.knn(x, x, 50, self_first=True)
+    got = H(M.knn(T(x), None, 50, self_first=True))
+    assert np.array_equal(got, ref)
+
+
 @pytest.mark.parametrize("case", ["offset", "lattice"])
 def test_coarsen_fp32_culling_edges(M, oracle, case):
     if case == "offset":
