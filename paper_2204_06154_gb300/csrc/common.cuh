@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -166,10 +167,22 @@ inline unsigned grid_for(int64_t n, int block) {
     return (unsigned)g;
 }
 
+// the calling thread's pinned host buffer of HOST_STAGE_BYTES (util.cu; nullptr if it cannot be
+// allocated), through which to_host reads small results
+constexpr size_t HOST_STAGE_BYTES = 64 * 1024;
+void* host_stage();
 template <class T>
 inline void to_host(T* dst, const T* src, size_t count, cudaStream_t s) {
     if (!count) return;
-    CK(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    const size_t bytes = count * sizeof(T);
+    void* stage = bytes <= HOST_STAGE_BYTES ? host_stage() : nullptr;
+    if (stage) {  // small reads through the calling thread's pinned buffer (no pageable staging)
+        CK(cudaMemcpyAsync(stage, src, bytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::memcpy(dst, stage, bytes);
+        return;
+    }
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
 }
 template <class T>

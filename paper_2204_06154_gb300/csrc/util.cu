@@ -556,6 +556,19 @@ void buf_free(void* p) {
     }
 }
 
+void* host_stage() {
+    thread_local void* p = nullptr;
+    thread_local bool tried = false;
+    if (!tried) {
+        tried = true;
+        if (cudaMallocHost(&p, HOST_STAGE_BYTES) != cudaSuccess) {
+            (void)cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    return p;
+}
+
 // Memory the caches may keep on a device between calls: 1/32 of its memory (8.9 GB on a GB300).
 size_t cache_budget() {
     static std::mutex mu;
