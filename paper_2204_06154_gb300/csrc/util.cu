@@ -549,7 +549,9 @@ void buf_free(void* p) {
     const int dev = it->second.first;
     const size_t bytes = it->second.second;
     c.live.erase(it);
-    if (g_cache_scope > 0) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) cur = -1;
+    if (g_cache_scope > 0 && dev == cur) {  // (the scope's synchronisation covered this device only)
         c.free_blocks[dev].emplace(bytes, p);
     } else {
         cudaFree(p);
