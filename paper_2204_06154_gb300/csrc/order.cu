@@ -62,6 +62,7 @@ struct RcmState {
     int32_t ntouched;         // nodes first claimed at this level (listed in `touched`)
 };
 constexpr int RCM_BATCH = 16;
+constexpr int RCM_SCAN_SMEM = 11264;  // frontier counts kept in the scan block's shared memory (44 KB)
 constexpr int RCM_GRID = 152 * 8;  // blocks of 128 threads: 4 frontier nodes a block at a time
 
 // claim: one warp per frontier node, lanes over its (degree, index)-sorted neighbours, so the
@@ -105,8 +106,10 @@ __global__ void __launch_bounds__(1024) rcm_scan_k(const int32_t* rp, const int3
     pdl_wait();
     __shared__ int32_t wsum[32];
     __shared__ unsigned long long wbest[32];
+    __shared__ int32_t scnt[RCM_SCAN_SMEM];
     const int32_t fs = st->fs, fe = st->fe, tail = st->tail, nt = st->ntouched;
     const int32_t n = fe - fs;
+    if (n <= RCM_SCAN_SMEM) cnt = scnt;  // (block-uniform) the counts of a frontier that fits stay on chip
     for (int32_t i = threadIdx.x; i < n; i += 1024) cnt[i] = 0;
     __syncthreads();
     for (int32_t i = threadIdx.x; i < nt; i += 1024) atomicAdd(&cnt[claim[touched[i]] - fs], 1);
